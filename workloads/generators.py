@@ -1,0 +1,179 @@
+"""Seeded generators for the synthetic MSP workloads.
+
+Every array is produced in FP64 on the host with NumPy's PCG64
+(``numpy.random.default_rng``), keyed by ``(seed, tag)`` so that the matrix,
+the right-hand side and any per-instance draw come from independent streams.
+The paper (Section 3, kernel ridge regression; Problem 1.1, matrices with a few
+large singular values) names no public dataset; these generators stand in for
+its two workload shapes:
+
+* ``spectrum_matrix``: A = Q diag(sigma) Q^T with a prescribed spectrum (a few
+  large outliers over a decaying or flat tail) -- the "k large singular values"
+  shape of Problem 1.1.
+* ``rbf_kernel``: a Gaussian (RBF) kernel matrix on uniform points in [0,1]^3 --
+  the kernel ridge regression shape (K + lambda I) x = y.
+
+Rounding to the storage precision (FP32 or BF16) is the caller's business; the
+generated FP64 values are the definition of the problem.
+"""
+
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# Stream tags for default_rng([seed, tag]).
+_TAG_MATRIX = 0
+_TAG_RHS = 1
+_TAG_TAIL = 2
+_TAG_INSTANCE = 3
+
+
+def _rng(seed: int, tag: int) -> np.random.Generator:
+    return np.random.default_rng([int(seed), int(tag)])
+
+
+def outlier_spectrum(n: int, k: int, hi: float = 1e4, lo: float = 1e2,
+                     tail_exp: float = 1.5) -> np.ndarray:
+    """k outliers log-spaced from ``hi`` down to ``lo``, then sigma_i = i^-tail_exp
+    for i = k+1..n (1-based i). Returned in non-increasing order."""
+    if not (0 <= k <= n):
+        raise ValueError("need 0 <= k <= n")
+    out = np.logspace(math.log10(hi), math.log10(lo), k) if k > 0 else np.zeros(0)
+    i = np.arange(k + 1, n + 1, dtype=np.float64)
+    tail = i ** (-tail_exp)
+    return np.concatenate([out, tail])
+
+
+def householder_spectrum(n: int, k: int, seed: int, hi: float = 1e6,
+                         lo: float = 1e2) -> np.ndarray:
+    """k outliers log-spaced hi -> lo, then a flat tail 0.5 + 0.5 u, u ~ U(0,1),
+    drawn in index order."""
+    out = np.logspace(math.log10(hi), math.log10(lo), k)
+    u = _rng(seed, _TAG_TAIL).random(n - k)
+    return np.concatenate([out, 0.5 + 0.5 * u])
+
+
+def spectrum_matrix(sigma: np.ndarray, seed: int) -> np.ndarray:
+    """A = Q diag(sigma) Q^T with Q the orthogonal factor of a seeded N(0,1)
+    n x n matrix (numpy.linalg.qr). sigma[i] is attached to column i of Q.
+    The result is symmetrised exactly."""
+    n = sigma.shape[0]
+    G = _rng(seed, _TAG_MATRIX).standard_normal((n, n))
+    Q, _ = np.linalg.qr(G)
+    A = (Q * sigma[None, :]) @ Q.T
+    return 0.5 * (A + A.T)
+
+
+def householder_matrix(sigma: np.ndarray, seed: int, reflectors: int = 64) -> np.ndarray:
+    """A = Q diag(sigma) Q^T with Q = H_1 H_2 ... H_r, H_i = I - 2 v v^T / |v|^2,
+    v_i ~ N(0, I). Built by applying the reflectors to diag(sigma) on both sides
+    (O(r n^2)), then symmetrised exactly."""
+    n = sigma.shape[0]
+    V = _rng(seed, _TAG_MATRIX).standard_normal((reflectors, n))
+    A = np.diag(sigma.astype(np.float64))
+    # Q A Q^T with Q = H_1 ... H_r: apply H_r first (innermost), H_1 last.
+    for i in range(reflectors - 1, -1, -1):
+        v = V[i]
+        beta = 2.0 / float(v @ v)
+        Av = A @ v
+        A = A - beta * np.outer(v, Av)          # H A
+        vA = v @ A
+        A = A - beta * np.outer(vA, v)          # (H A) H
+    return 0.5 * (A + A.T)
+
+
+def rbf_points(n: int, seed: int, dim: int = 3) -> np.ndarray:
+    """n points uniform in [0,1]^dim, FP64, shape (n, dim)."""
+    return _rng(seed, _TAG_MATRIX).random((n, dim))
+
+
+def rbf_kernel(P: np.ndarray, ell: float, out_dtype=np.float64,
+               block: int = 2048) -> np.ndarray:
+    """K_ij = exp(-|p_i - p_j|^2 / (2 ell^2)) evaluated in FP64 and rounded once to
+    ``out_dtype``. Built in row blocks to bound host memory."""
+    n = P.shape[0]
+    K = np.empty((n, n), dtype=out_dtype)
+    sq = np.einsum("ij,ij->i", P, P)
+    inv = 1.0 / (2.0 * ell * ell)
+    for i0 in range(0, n, block):
+        i1 = min(n, i0 + block)
+        d2 = sq[i0:i1, None] + sq[None, :] - 2.0 * (P[i0:i1] @ P.T)
+        # exact diagonal and no negative round-off
+        np.maximum(d2, 0.0, out=d2)
+        for i in range(i0, i1):
+            d2[i - i0, i] = 0.0
+        K[i0:i1] = np.exp(-d2 * inv).astype(out_dtype)
+    return K
+
+
+def rhs(n: int, seed: int, m: int = 1) -> np.ndarray:
+    """b ~ N(0, I), shape (n,) for m == 1 else (n, m) (column j = right-hand side j)."""
+    g = _rng(seed, _TAG_RHS).standard_normal((n, m))
+    return g[:, 0].copy() if m == 1 else g
+
+
+@dataclasses.dataclass
+class Workload:
+    """One synthetic problem instance (A + lam I) x = b."""
+    name: str
+    A: np.ndarray            # FP64 (or the storage dtype for RBF), n x n, symmetric
+    b: np.ndarray            # FP64, (n,) or (n, m)
+    lam: float
+    s: int                   # sketch size
+    gamma: int               # nonzeros per row of Pi = S^T
+    sigma: np.ndarray | None = None   # exact spectrum when known
+    points: np.ndarray | None = None  # RBF points when applicable
+    ell: float | None = None
+
+    @property
+    def n(self) -> int:
+        return self.A.shape[0]
+
+
+def make_workload(name: str, seed: int = 0, n: int | None = None,
+                  m: int = 1, rbf_dtype=np.float32) -> Workload:
+    """Build one of the named synthetic workloads.
+
+    ``outlier``  : config-0 shape, n=1024 default, 32 outliers 1e4->1e2, tail i^-1.5,
+                   lam=1e-3, s=64, gamma=8 (FP64).
+    ``rbf``      : GP-regression shape, n=16384 default, ell=0.1, lam=1e-2, s=1024,
+                   gamma=8; the kernel is rounded once to ``rbf_dtype``.
+    ``outlier256``: Schatten-1 shape, n=16384 default, 256 outliers, tail i^-1.5.
+    ``householder``: n=32768 default, 1024 outliers 1e6->1e2, tail 0.5+0.5u,
+                   lam=1e-4, s=2048.
+    ``n`` rescales the size; ``s`` keeps the default ratio n/s (at least 16).
+    """
+    if name == "outlier":
+        n = n or 1024
+        k = max(1, (32 * n) // 1024)
+        sig = outlier_spectrum(n, min(k, n))
+        A = spectrum_matrix(sig, seed)
+        s = max(16, (64 * n) // 1024)
+        return Workload(name, A, rhs(n, seed, m), 1e-3, s, 8, sigma=sig)
+    if name == "rbf":
+        n = n or 16384
+        P = rbf_points(n, seed)
+        K = rbf_kernel(P, 0.1, out_dtype=rbf_dtype)
+        s = max(16, (1024 * n) // 16384)
+        return Workload(name, K, rhs(n, seed, m), 1e-2, s, 8, points=P, ell=0.1)
+    if name == "outlier256":
+        n = n or 16384
+        k = max(1, (256 * n) // 16384)
+        sig = outlier_spectrum(n, k)
+        A = spectrum_matrix(sig, seed)
+        s = max(16, (1024 * n) // 16384)
+        return Workload(name, A, rhs(n, seed, m), 1e-3, s, 8, sigma=sig)
+    if name == "householder":
+        n = n or 32768
+        k = max(1, (1024 * n) // 32768)
+        sig = householder_spectrum(n, k, seed)
+        A = householder_matrix(sig, seed)
+        s = max(16, (2048 * n) // 32768)
+        return Workload(name, A, rhs(n, seed, m), 1e-4, s, 8, sigma=sig)
+    raise ValueError(f"unknown workload {name!r}")
+
+
+WORKLOADS = ("outlier", "rbf", "outlier256", "householder")
