@@ -1,0 +1,370 @@
+"""Benchmark: MSP solves/s on one GB300 (per rank), GP-regression workload.
+
+One step = one complete two-level MSP solve (Algorithm 1 with SolveM1 of
+Algorithm 2) of (K + lam I) x = b: sparse sketch C = K S^T, Nystrom factor
+(W, C~, M2 and its FP64 Cholesky inverse), then the level-1 iteration wrapped
+in FP64 iterative refinement until |b - (K + lam I) x| / |b| <= 1e-10 (which
+bounds the normwise backward error by 1e-10).
+
+Workload (default): RBF kernel K_ij = exp(-|p_i - p_j|^2 / (2 l^2)) on n=16384
+seeded uniform points in [0,1]^3, l = 0.1, lam = 1e-2, K stored FP32 (1.07 GB,
+larger than L2, so no flush is needed between steps), sketch s = 1024 with 8
+nonzeros per row of Pi, level-2 sketch phi = 4 s, b ~ N(0, I).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl msp|reference]
+
+Multi-GPU: each rank solves its own independent instance (seed = rank); no
+data-path collective; value = all solves / max-over-ranks time ("weak").
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "solves/s to 1e-10 backward err, n=16384, mixed vs plain FP32; % HBM roofline"
+SEED = 0x4D5350
+# Level-1 iterations the FP64 oracle needs for this workload at these settings
+# (inner tolerance 1e-6, phi = 4 s, relative residual 1e-10); used to scale the
+# oracle's per-iteration time in the bounded CPU sample.
+ORACLE_ITERS_RBF16K = 103
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="msp", choices=["msp", "reference"])
+    ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--s", type=int, default=1024)
+    ap.add_argument("--phi-mult", type=int, default=4)
+    ap.add_argument("--inner-tol", type=float, default=1e-6)
+    ap.add_argument("--refine-tol", type=float, default=1e-6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=5, help="level-1 iterations in the CPU sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons while active."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+
+def measured_peaks() -> tuple[float, str]:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def gemv_traffic_bytes(n: int) -> float | None:
+    """DRAM bytes per A-pass launch from the committed ncu summary, if it was taken
+    on the current kernel source (sha256 of csrc/krylov.cu matches)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_2405_05865_gb300", "csrc", "krylov.cu")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)["gemv"]
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if d.get("krylov_cu_sha256") != sha:
+            return None
+        # scale the captured case to this n (traffic grows with n^2)
+        return float(d["bytes_per_launch"]) * (n / d["n"]) ** 2
+    except Exception:
+        return None
+
+
+def make_problem(n: int, seed: int):
+    from workloads import make_workload
+    w = make_workload("rbf", seed=seed, n=n)
+    return w.A.astype(np.float32, copy=False), w.b, w.lam
+
+
+# ------------------------------------------------------------ oracle (CPU)
+
+def oracle_sample(A32: np.ndarray, b: np.ndarray, lam: float, s: int, phi: int,
+                  inner_tol: float, iters: int, scale_iters: int) -> dict:
+    """Bounded sample of the FP64 oracle on the same workload: Algorithm 1 setup
+    plus `iters` level-1 iterations; solves/s extrapolated to `scale_iters`."""
+    from oracle import msp as omsp
+    A = A32.astype(np.float64)
+    p = omsp.MspParams(s=s, phi=phi, lam0=0.0, inner_tol=inner_tol, tol=0.0, max_outer=iters)
+    t0 = time.perf_counter()
+    st = omsp.setup(A, lam, p)
+    t1 = time.perf_counter()
+    omsp.solve(A, b, lam, p, st=st)
+    t2 = time.perf_counter()
+    t_setup, t_iter = t1 - t0, (t2 - t1) / iters
+    t_solve = t_setup + scale_iters * t_iter
+    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": (f"FP64 oracle (NumPy/SciPy) on the same n={A.shape[0]} RBF system: "
+                       f"Algorithm 1 setup ({t_setup:.2f} s) + {iters} level-1 iterations "
+                       f"({t_iter:.2f} s each), extrapolated to {scale_iters} iterations"),
+            "seconds": t2 - t0}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    A32, b, lam = make_problem(args.n, 0)
+    vals = []
+    t_all = time.perf_counter()
+    for k in range(args.warmup + args.steps):
+        r = oracle_sample(A32, b, lam, args.s, args.phi_mult * args.s, args.inner_tol,
+                          max(1, args.cpu_iters), ORACLE_ITERS_RBF16K)
+        if k >= args.warmup:
+            vals.append(r)
+    wall = time.perf_counter() - t_all
+    v = statistics.median([r["value"] for r in vals])
+    out = {"metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": f"rbf n={args.n} l=0.1 lam=1e-2 s={args.s} gamma=8 "
+                                  f"phi={args.phi_mult}s FP32-stored K", "parallelism": "replicas"},
+           "cpu_baseline": {**vals[-1], "value": v},
+           "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "wall_s": wall}
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_msp(args, rank, world, local):
+    import torch
+    from paper_2405_05865_gb300 import Context
+
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    n, s, phi = args.n, args.s, args.phi_mult * args.s
+    A32, b, lam = make_problem(n, rank)
+    A = torch.from_numpy(A32).to(dev)
+    bd = torch.from_numpy(b).to(dev)
+    ctx = Context(local)
+    stream = ctx.stream
+
+    def step(prec="mixed", tol=1e-10, profile=0):
+        sk = ctx.sketch(A, s, 8, SEED)
+        f = ctx.nystrom(sk, lam, 0.0, phi=phi, gamma_phi=8, seed=SEED)
+        x, info = ctx.solve(f, A, bd, lam, precision=prec, tol=tol, inner_tol=args.inner_tol,
+                            refine_tol=args.refine_tol, profile=profile)
+        f.close()
+        sk.close()
+        return x, info
+
+    def barrier():
+        if dist:
+            torch.distributed.barrier()
+
+    def timed(nsteps, **kw):
+        barrier()
+        torch.cuda.synchronize(dev)
+        l0 = ctx.lib.msp_launch_count(ctx.ptr)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        infos = []
+        for _ in range(nsteps):
+            _, info = step(**kw)
+            infos.append(info)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        launches = ctx.lib.msp_launch_count(ctx.ptr) - l0
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, infos, launches
+
+    for _ in range(args.warmup):
+        step()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, infos, launches = timed(args.steps, profile=1)
+    clk = clocks.stop()
+    total = args.steps * world
+    value = total / (ms / 1000.0)
+    ok = all(i["rel_resid"] <= 1e-10 for i in infos)
+
+    # plain FP32 (no refinement) to 1e-5 relative residual
+    fp32 = None
+    if not args.no_fp32:
+        for _ in range(max(1, args.warmup // 2)):
+            step(prec="fp32", tol=1e-5)
+        ms32, inf32, _ = timed(args.steps, prec="fp32", tol=1e-5)
+        fp32 = {"value": total / (ms32 / 1000.0), "unit": "solves/s",
+                "rel_resid_max": max(i["rel_resid"] for i in inf32),
+                "outer_iters": inf32[-1]["outer_iters"], "ms_per_step": ms32 / args.steps}
+
+    # roofline of the dominant kernel: the A pass q = (A + lam I) p
+    g_ms = sum(i["gemv_ms"] for i in infos)
+    g_n = sum(i["gemv_launches"] for i in infos)
+    l2_ms = sum(i["level2_ms"] for i in infos)
+    r_ms = sum(i["resid_ms"] for i in infos)
+    avg_ms = g_ms / max(1, g_n)
+    alg_bytes = 4.0 * n * n + 3 * 4.0 * n           # A (FP32) + p read + q write
+    achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
+    peak, peak_src = measured_peaks()
+    traffic = gemv_traffic_bytes(n)
+
+    # end to end through the C ABI with host (pinned) buffers
+    e2e = None
+    if not args.no_e2e:
+        Ah = torch.from_numpy(A32).pin_memory()
+        bh = torch.from_numpy(b).pin_memory()
+        xh = torch.empty(n, dtype=torch.float64).pin_memory()
+        ctx.solve_full(Ah, bh, lam, s, 8, 0.0, phi, 8, SEED, out=xh, inner_tol=args.inner_tol)
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.solve_full(Ah, bh, lam, s, 8, 0.0, phi, 8, SEED, out=xh, inner_tol=args.inner_tol)
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        et = t1 - t0
+        if dist:
+            t = torch.tensor([et], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            et = float(t.item())
+        e2e = {"value": total / et, "unit": "solves/s", "h2d_bytes_per_step": 4 * n * n + 8 * n,
+               "d2h_bytes_per_step": 8 * n}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        per_solve_iters = infos[-1]["outer_iters"]
+        cpu = oracle_sample(A32, b, lam, s, phi, args.inner_tol, max(1, args.cpu_iters),
+                            per_solve_iters)
+        cpu["sample"] += " (the GPU's level-1 iteration count per solve)"
+
+    last = infos[-1]
+    out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": f"rbf n={n} l=0.1 lam=1e-2 s={s} gamma=8 phi={args.phi_mult}s "
+                                  f"FP32-stored K, 1 RHS, mixed precision (FP32 Krylov + FP64 "
+                                  f"refinement) to relative residual 1e-10",
+                      "l2": "inputs larger than L2 (K is 1.07 GB)",
+                      "parallelism": "replicas" if world > 1 else "single"},
+           "accuracy": {"rel_resid_max": max(i["rel_resid"] for i in infos), "all_converged": ok,
+                        "outer_iters": last["outer_iters"], "inner_iters": last["inner_iters"],
+                        "refine_steps": last["refine_steps"]},
+           "fp32_plain": fp32,
+           "phase_ms_per_step": {"a_pass": g_ms / args.steps, "level2": l2_ms / args.steps,
+                                 "fp64_residual": r_ms / args.steps},
+           "roofline": {"bound": "hbm", "kernel": "k_gemv (q = (A + lam I) p)",
+                        "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                        "alg_bytes_per_launch": alg_bytes, "avg_launch_us": avg_ms * 1e3,
+                        "launches": g_n},
+           "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if dist:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_msp(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,245 @@
+/*
+ * msp.h -- C ABI of the GB300 (sm_103a) implementation of two-level
+ * Multi-level Sketched Preconditioning (MSP) for the regularised PSD system
+ *
+ *     (A + lambda I) x = b,     A in S_n^+ dense, lambda > 0,
+ *
+ * from Derezinski, Musco and Yang, "Faster Linear Systems and Matrix Norm
+ * Approximation via Multi-level Sketched Preconditioning" (arXiv 2405.05865),
+ * Section 4 (Algorithm 1 with SolveM1 of Algorithm 2, Theorem 4.2).
+ *
+ * Conventions for every entry point
+ *   - Matrices are dense row-major with a leading dimension in elements.
+ *     A is symmetric, so row-major and column-major storage coincide.
+ *   - Array arguments are DEVICE pointers unless the entry point says that it
+ *     also accepts host memory. The library never frees caller memory and
+ *     keeps no pointer to it after the call returns.
+ *   - Work is issued on the context's stream. Entry points that return
+ *     scalars (iteration counts, status) synchronise that stream before they
+ *     return; the others are asynchronous with respect to the host.
+ *   - Handles (msp_ctx, msp_sketch_t, msp_factor_t) own device memory
+ *     allocated by the library; release them with the matching *_destroy.
+ *     A factor keeps a reference to its sketch: destroy the factor first.
+ *   - Errors: every entry point returns an msp_status. MSP_OK is 0. On any
+ *     other value a message is available from msp_last_error(ctx). The
+ *     library never aborts, traps or prints. Device-side loops carry
+ *     iteration and wall-clock limits and report MSP_ETIMEOUT instead of
+ *     hanging.
+ *   - Determinism: the same seed gives bit-identical sketch patterns; all
+ *     reductions use a fixed order, so repeated calls give identical results
+ *     on the same device.
+ */
+#ifndef MSP_H
+#define MSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MSP_API __attribute__((visibility("default")))
+#else
+#define MSP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MSP_F64 = 0,   /* IEEE binary64 */
+    MSP_F32 = 1    /* IEEE binary32 */
+} msp_dtype;
+
+typedef enum {
+    MSP_OK = 0,
+    MSP_EINVAL = 1,      /* bad argument (size, pointer, dtype, option)       */
+    MSP_ENOMEM = 2,      /* device allocation failed                          */
+    MSP_ECUDA = 3,       /* a CUDA runtime call failed                        */
+    MSP_ENOTPD = 4,      /* M2 not positive definite after all shift retries,
+                            or p^T (A + lam I) p <= 0 in the outer iteration  */
+    MSP_ENOCONV = 5,     /* iteration cap reached before the tolerance; the
+                            best iterate is returned and msp_info is filled   */
+    MSP_ENONFINITE = 6,  /* NaN/Inf in the input or in the iteration          */
+    MSP_ETIMEOUT = 7     /* a device-side wait exceeded its wall-clock limit  */
+} msp_status;
+
+/* Arithmetic of the Krylov levels (the level-1 outer iteration and the
+ * level-2 SolveM1 iteration).
+ *   MSP_PREC_FP64  : FP64 A, FP64 sketch data and vectors.
+ *   MSP_PREC_FP32  : FP32 A and sketch data, FP32 vectors, FP64 dot
+ *                    products; no refinement ("plain FP32").
+ *   MSP_PREC_MIXED : the FP32 solve wrapped in FP64 iterative refinement:
+ *                    r = b - (A + lam I) x with FP64 accumulation, solve
+ *                    for the correction in FP32, x += d (FP64 x). */
+typedef enum {
+    MSP_PREC_FP64 = 0,
+    MSP_PREC_FP32 = 1,
+    MSP_PREC_MIXED = 2
+} msp_precision;
+
+typedef struct msp_ctx msp_ctx;
+typedef struct msp_sketch_s msp_sketch_t;
+typedef struct msp_factor_s msp_factor_t;
+
+/* Solver options. Zero-initialise and call msp_default_opts() to get the
+ * defaults listed beside each field. */
+typedef struct {
+    double tol;           /* stop when |b - (A+lam I)x|_2 <= tol |b|_2, the form of
+                             Theorem 1.2 (implies normwise backward error <= tol).
+                             Default 1e-10.                                      */
+    int max_outer;        /* cap on level-1 iterations per Krylov solve. 2000.   */
+    int max_refine;       /* cap on FP64 refinement steps (MIXED). 20.            */
+    double refine_tol;    /* MIXED: each FP32 correction solve stops at relative
+                             residual refine_tol. Default 1e-6.                  */
+    double inner_tol;     /* level-2 (SolveM1) solve stops at
+                             |res| <= inner_tol |C^T r|. Default 1e-6.           */
+    int max_inner;        /* cap on level-2 iterations per SolveM1. 50.          */
+    int precision;        /* msp_precision. Default MSP_PREC_MIXED.              */
+    int check_every;      /* level-1 iterations between host checks of the
+                             device-side convergence flag. Default 8.            */
+    int profile;          /* 1: time every A-pass and level-2 launch with CUDA
+                             events on the context stream (msp_info *_ms).
+                             Default 0.                                          */
+} msp_opts;
+
+typedef struct {
+    int outer_iters;      /* total level-1 iterations (all refinement steps)     */
+    int inner_iters;      /* total level-2 iterations                            */
+    int refine_steps;     /* FP64 refinement steps taken (MIXED)                 */
+    int shift_retries;    /* Cholesky retries with a stabilising shift           */
+    double rel_resid;     /* final |b - (A+lam I)x| / |b| (FP64 accumulation)    */
+    double lambda_tilde;  /* lambda + lambda_0 used by the preconditioner        */
+    double shift;         /* stabilising shift added to M2 (0 if none)           */
+    int status;           /* msp_status of the solve                             */
+    /* with opts.profile = 1: summed CUDA-event durations (ms) and launch counts */
+    int gemv_launches;    /* q = (A + lam I) p passes (level 1)                  */
+    int level2_launches;  /* persistent level-1 update + SolveM1 kernels         */
+    int resid_launches;   /* FP64 residual passes (refinement)                   */
+    int pad_;
+    double gemv_ms;
+    double level2_ms;
+    double resid_ms;
+} msp_info;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`, issuing all work on `stream`
+ * (a cudaStream_t; NULL means the legacy default stream). */
+MSP_API msp_status msp_create(msp_ctx** out, int device, void* stream);
+MSP_API void msp_destroy(msp_ctx* ctx);
+MSP_API const char* msp_last_error(const msp_ctx* ctx);
+MSP_API void msp_default_opts(msp_opts* opts);
+/* Library version string, e.g. "msp-gb300 0.1 sm_103a". */
+MSP_API const char* msp_version(void);
+/* Number of CUDA kernels this context has launched since it was created. */
+MSP_API int64_t msp_launch_count(const msp_ctx* ctx);
+
+/* ------------------------------------------------- a1: sketch index draw */
+
+/* Definition 2.1 (sparse embedding matrix, Section 2): the pattern of an
+ * `rows` x n matrix with `gamma` nonzeros +-1/sqrt(gamma) per column, the
+ * gamma row indices of each column drawn uniformly without replacement and
+ * the signs independently. Column j of the embedding is written as
+ *   idx[j*gamma + q] (int32, ascending in q) and sgn[j*gamma + q] (+1/-1, int8).
+ * For the sketch S of Algorithm 1, Pi = S^T is n x s and idx[j*gamma..] are
+ * the columns of Pi's row j.
+ * Draws: counter-based SplitMix64 (Steele, Lea, Flood 2014) with counter
+ * (stream << 56) | (j << 8) | q, Floyd's sampling, sign from the top bit of
+ * the draw on stream+1. stream 0 is S, stream 2 is Phi.
+ * Requires 1 <= gamma <= min(rows, 255), n < 2^31, rows < 2^31.
+ * idx, sgn: device arrays of n*gamma elements, caller-owned. */
+MSP_API msp_status msp_sketch_pattern(msp_ctx* ctx, int64_t n, int64_t rows, int gamma,
+                              uint64_t seed, int stream, int32_t* idx, int8_t* sgn);
+
+/* ---------------------------------------------- a1-a2: the sketch C = A Pi */
+
+/* Algorithm 1, steps 2-3: draw S (s x n, gamma nonzeros per column, seed
+ * `seed`, stream 0) and compute C = A S^T (n x s) in one pass over A.
+ * A: device, n x n, leading dimension lda >= n, dtype MSP_F32 or MSP_F64.
+ * The C of the handle has the dtype of A. s is padded internally to a
+ * multiple of 128 with zero columns (sizes reported by msp_sketch_info).
+ * Requires 1 <= gamma <= min(s, 255), 16 <= s <= 4096, s <= n. */
+MSP_API msp_status msp_sketch(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n,
+                      int64_t lda, int64_t s, int gamma, uint64_t seed,
+                      msp_sketch_t** out);
+MSP_API void msp_sketch_destroy(msp_sketch_t* sk);
+/* n, s, padded s (the leading dimension of C), gamma, dtype. */
+MSP_API msp_status msp_sketch_info(const msp_sketch_t* sk, int64_t* n, int64_t* s,
+                           int64_t* s_pad, int* gamma, int* dtype);
+/* Copy C (n x s, row-major, ldc >= s, dtype of the sketch) into a caller
+ * device buffer. */
+MSP_API msp_status msp_sketch_get_C(msp_ctx* ctx, const msp_sketch_t* sk, void* C, int64_t ldc);
+
+/* ------------------------------------------- a3-a5: Nystrom core and M2 */
+
+/* Algorithm 1, steps 3-4: W = S C (s x s, symmetrised), lambda~ = lambda +
+ * lambda0, C~ = Phi C with Phi a phi x n sparse embedding (gamma_phi
+ * nonzeros per column, stream 2), M2 = C~^T C~ + lambda~ W, and the FP64
+ * Cholesky factor M2 + nu I = L L^T (nu = 0 first; on failure
+ * nu = s 2^-52 |M2|_F for FP64 data or 2^-24 |M2|_F for FP32 data, times 100
+ * per retry, at most 4 retries, else MSP_ENOTPD). The level-2 preconditioner is applied as
+ * M2^{-1} v = L^{-T} (L^{-1} v) with L^{-1} stored explicitly
+ * ("pre-compute M2^{-1} exactly", Section 4, Part 3).
+ * phi == 0 selects Phi = I_n (C~ = C, M2 = C^T C + lambda~ W exactly: the
+ * perfect embedding; the level-2 solve then converges in a few steps).
+ * C~^T C~ is accumulated in the working precision; M2 only preconditions the
+ * level-2 solve, whose operator C^T C + lambda~ W is always applied in the
+ * working precision.
+ * Requires lambda > 0, lambda0 >= 0, 0 <= phi, gamma_phi <= min(phi,255). */
+MSP_API msp_status msp_nystrom(msp_ctx* ctx, const msp_sketch_t* sk, double lambda,
+                       double lambda0, int64_t phi, int gamma_phi, uint64_t seed,
+                       msp_factor_t** out);
+MSP_API void msp_factor_destroy(msp_factor_t* f);
+/* Copies of the factor's pieces into caller device buffers (FP64, row-major,
+ * leading dimension s): W, M2 (before the shift), L^{-1} (lower triangle).
+ * Any pointer may be NULL. lam_tilde/shift/retries may be NULL. */
+MSP_API msp_status msp_factor_get(msp_ctx* ctx, const msp_factor_t* f, double* W,
+                          double* M2, double* Linv, double* lam_tilde,
+                          double* shift, int* retries);
+
+/* Apply the level-1 preconditioner once: w = SolveM1(r) (Algorithm 2), i.e.
+ * w ~ M^{-1} r with M = C W^{-1} C^T + lambda~ I via
+ * M^{-1} = (1/lambda~)(I - C (C^T C + lambda~ W)^{-1} C^T) (Eq. M_inverse),
+ * the level-2 system solved by PCG preconditioned with M2^{-1}.
+ * r, w: device vectors of n elements in the sketch's dtype. inner_iters may
+ * be NULL. */
+MSP_API msp_status msp_solve_m1(msp_ctx* ctx, const msp_factor_t* f, const void* r,
+                        void* w, const msp_opts* opts, int* inner_iters);
+
+/* ------------------------------------------------ a6-a8: the MSP solve */
+
+/* Algorithm 1 step 5: solve (A + lambda I) x = b by the level-1 iteration
+ * (flexible PCG, equal to Algorithm 6 in exact arithmetic, Section 6) with
+ * SolveM1 as the preconditioner; in MSP_PREC_MIXED the solve is wrapped in
+ * FP64 iterative refinement.
+ * A: device, n x n, lda >= n; FP64 with MSP_PREC_FP64, FP32 otherwise; it
+ *    must be the matrix the factor was built from.
+ * b, x: device FP64 vectors of n elements (x is overwritten; no initial
+ *    guess). info may be NULL.
+ * Returns MSP_ENOCONV (with x the last iterate) if the caps are reached. */
+MSP_API msp_status msp_solve(msp_ctx* ctx, const msp_factor_t* f, const void* A,
+                     msp_dtype dtype, int64_t n, int64_t lda, double lambda,
+                     const double* b, double* x, const msp_opts* opts,
+                     msp_info* info);
+
+/* The whole of Algorithm 1 in one call: sketch, Nystrom factor, solve.
+ * A, b and x may each be device or host memory (host buffers are staged
+ * through device buffers owned by the context; pinned host memory is
+ * fastest). Parameters as for msp_sketch / msp_nystrom / msp_solve. */
+MSP_API msp_status msp_solve_full(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n,
+                          int64_t lda, double lambda, const double* b, double* x,
+                          int64_t s, int gamma, double lambda0, int64_t phi,
+                          int gamma_phi, uint64_t seed, const msp_opts* opts,
+                          msp_info* info);
+
+/* ----------------------------------------------------- helpers (tests) */
+
+/* y = (A + lambda I) x, FP64 accumulation, FP64 x and y; A FP32 or FP64.
+ * The residual operator of the refinement step (one pass over A). */
+MSP_API msp_status msp_matvec_f64(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n,
+                          int64_t lda, double lambda, const double* x, double* y);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MSP_H */

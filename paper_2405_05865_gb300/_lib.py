@@ -1,0 +1,106 @@
+"""ctypes binding of libmsp (include/msp.h): argument marshalling only.
+
+Every array argument is passed as a raw pointer; every computation happens in
+the library's CUDA kernels. Loading fails loudly if the shared library has not
+been built (``python -m paper_2405_05865_gb300.build``); there is no fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libmsp.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "msp.h")
+
+MSP_F64, MSP_F32 = 0, 1
+MSP_PREC_FP64, MSP_PREC_FP32, MSP_PREC_MIXED = 0, 1, 2
+STATUS = {0: "MSP_OK", 1: "MSP_EINVAL", 2: "MSP_ENOMEM", 3: "MSP_ECUDA", 4: "MSP_ENOTPD",
+          5: "MSP_ENOCONV", 6: "MSP_ENONFINITE", 7: "MSP_ETIMEOUT"}
+
+
+class MspOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_outer", C.c_int), ("max_refine", C.c_int),
+                ("refine_tol", C.c_double), ("inner_tol", C.c_double), ("max_inner", C.c_int),
+                ("precision", C.c_int), ("check_every", C.c_int), ("profile", C.c_int)]
+
+
+class MspInfo(C.Structure):
+    _fields_ = [("outer_iters", C.c_int), ("inner_iters", C.c_int), ("refine_steps", C.c_int),
+                ("shift_retries", C.c_int), ("rel_resid", C.c_double),
+                ("lambda_tilde", C.c_double), ("shift", C.c_double), ("status", C.c_int),
+                ("gemv_launches", C.c_int), ("level2_launches", C.c_int), ("resid_launches", C.c_int),
+                ("pad_", C.c_int), ("gemv_ms", C.c_double), ("level2_ms", C.c_double),
+                ("resid_ms", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class MspError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+P = C.c_void_p
+I64 = C.c_int64
+_SIGS = {
+    "msp_create": (C.c_int, [C.POINTER(P), C.c_int, P]),
+    "msp_destroy": (None, [P]),
+    "msp_last_error": (C.c_char_p, [P]),
+    "msp_default_opts": (None, [C.POINTER(MspOpts)]),
+    "msp_version": (C.c_char_p, []),
+    "msp_launch_count": (C.c_int64, [P]),
+    "msp_sketch_pattern": (C.c_int, [P, I64, I64, C.c_int, C.c_uint64, C.c_int, P, P]),
+    "msp_sketch": (C.c_int, [P, P, C.c_int, I64, I64, I64, C.c_int, C.c_uint64, C.POINTER(P)]),
+    "msp_sketch_destroy": (None, [P]),
+    "msp_sketch_info": (C.c_int, [P, C.POINTER(I64), C.POINTER(I64), C.POINTER(I64),
+                                  C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "msp_sketch_get_C": (C.c_int, [P, P, P, I64]),
+    "msp_nystrom": (C.c_int, [P, P, C.c_double, C.c_double, I64, C.c_int, C.c_uint64,
+                              C.POINTER(P)]),
+    "msp_factor_destroy": (None, [P]),
+    "msp_factor_get": (C.c_int, [P, P, P, P, P, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                 C.POINTER(C.c_int)]),
+    "msp_solve_m1": (C.c_int, [P, P, P, P, C.POINTER(MspOpts), C.POINTER(C.c_int)]),
+    "msp_solve": (C.c_int, [P, P, P, C.c_int, I64, I64, C.c_double, P, P, C.POINTER(MspOpts),
+                            C.POINTER(MspInfo)]),
+    "msp_solve_full": (C.c_int, [P, P, C.c_int, I64, I64, C.c_double, P, P, I64, C.c_int,
+                                 C.c_double, I64, C.c_int, C.c_uint64, C.POINTER(MspOpts),
+                                 C.POINTER(MspInfo)]),
+    "msp_matvec_f64": (C.c_int, [P, P, C.c_int, I64, I64, C.c_double, P, P]),
+}
+
+_lib = None
+
+
+def header_symbols() -> list[str]:
+    """Function names declared in include/msp.h."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^MSP_API\s+[\w\s\*]+?\b(msp_\w+)\s*\(", txt, flags=re.M)))
+
+
+def load() -> C.CDLL:
+    """Load libmsp.so (built in-tree) and declare its signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libmsp.so is not built ({LIB_PATH}); run "
+                          "`python -m paper_2405_05865_gb300.build` (needs nvcc)")
+    lib = C.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(ctx, status: int) -> None:
+    if status != 0:
+        msg = load().msp_last_error(ctx)
+        raise MspError(status, msg.decode() if msg else "")

@@ -1,0 +1,204 @@
+"""Python API over libmsp: PyTorch supplies device memory and the stream; every
+step of MSP runs in the library's CUDA kernels (see include/msp.h).
+
+    ctx = Context()                         # device 0, torch's current stream
+    sk = ctx.sketch(A, s=1024, gamma=8)     # Algorithm 1 steps 2-3: C = A S^T
+    f = ctx.nystrom(sk, lam=1e-2)           # steps 3-4: W, C~, M2 and its factor
+    x, info = ctx.solve(f, A, b, lam=1e-2)  # step 5 (+ FP64 refinement)
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _lib as L
+
+DEFAULT_SEED = 0x4D5350      # "MSP"
+
+_DT = {torch.float32: L.MSP_F32, torch.float64: L.MSP_F64}
+_PREC = {"fp64": L.MSP_PREC_FP64, "fp32": L.MSP_PREC_FP32, "mixed": L.MSP_PREC_MIXED}
+
+
+def _ptr(t: torch.Tensor) -> C.c_void_p:
+    return C.c_void_p(t.data_ptr())
+
+
+def make_opts(lib, **kw) -> L.MspOpts:
+    o = L.MspOpts()
+    lib.msp_default_opts(C.byref(o))
+    for k, v in kw.items():
+        if v is None:
+            continue
+        if k == "precision" and isinstance(v, str):
+            v = _PREC[v]
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k!r}")
+        setattr(o, k, v)
+    return o
+
+
+def _check_matrix(A: torch.Tensor, need_cuda: bool = True) -> tuple[int, int, int]:
+    if A.dim() != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError("A must be a square 2-D tensor")
+    if A.dtype not in _DT:
+        raise TypeError("A must be float32 or float64")
+    if need_cuda and not A.is_cuda:
+        raise ValueError("A must be a CUDA tensor")
+    if A.stride(1) != 1:
+        raise ValueError("A must be row-major with unit column stride")
+    return A.shape[0], A.stride(0), _DT[A.dtype]
+
+
+class Sketch:
+    def __init__(self, ctx: "Context", handle: C.c_void_p, n: int, s: int, dtype: torch.dtype):
+        self.ctx, self.handle, self.n, self.s, self.dtype = ctx, handle, n, s, dtype
+
+    def C(self) -> torch.Tensor:
+        out = torch.empty((self.n, self.s), dtype=self.dtype, device=self.ctx.device)
+        L.check(self.ctx.ptr, self.ctx.lib.msp_sketch_get_C(self.ctx.ptr, self.handle, _ptr(out), self.s))
+        return out
+
+    def close(self) -> None:
+        if self.handle:
+            self.ctx.lib.msp_sketch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Factor:
+    def __init__(self, ctx: "Context", handle: C.c_void_p, sketch: Sketch):
+        self.ctx, self.handle, self.sketch = ctx, handle, sketch
+
+    def parts(self) -> dict:
+        s = self.sketch.s
+        dev = self.ctx.device
+        W = torch.empty((s, s), dtype=torch.float64, device=dev)
+        M2 = torch.empty_like(W)
+        Li = torch.empty_like(W)
+        lt, sh, rt = C.c_double(), C.c_double(), C.c_int()
+        L.check(self.ctx.ptr, self.ctx.lib.msp_factor_get(self.ctx.ptr, self.handle, _ptr(W), _ptr(M2),
+                                                          _ptr(Li), C.byref(lt), C.byref(sh), C.byref(rt)))
+        return {"W": W, "M2": M2, "Linv": Li, "lambda_tilde": lt.value, "shift": sh.value,
+                "retries": rt.value}
+
+    def close(self) -> None:
+        if self.handle:
+            self.ctx.lib.msp_factor_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context:
+    """An MSP context bound to one CUDA device and one stream."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("MSP needs a CUDA device; none is available")
+        self.lib = L.load()
+        self.device = torch.device("cuda", device)
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        self.ptr = C.c_void_p()
+        L.check(None, self.lib.msp_create(C.byref(self.ptr), device, C.c_void_p(self.stream.cuda_stream)))
+
+    def close(self) -> None:
+        if self.ptr:
+            self.lib.msp_destroy(self.ptr)
+            self.ptr = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- a1
+    def sketch_pattern(self, n: int, rows: int, gamma: int, seed: int = DEFAULT_SEED,
+                       stream: int = 0) -> tuple[torch.Tensor, torch.Tensor]:
+        idx = torch.empty((n, gamma), dtype=torch.int32, device=self.device)
+        sgn = torch.empty((n, gamma), dtype=torch.int8, device=self.device)
+        L.check(self.ptr, self.lib.msp_sketch_pattern(self.ptr, n, rows, gamma, seed, stream,
+                                                      _ptr(idx), _ptr(sgn)))
+        return idx, sgn
+
+    # -- a1-a2
+    def sketch(self, A: torch.Tensor, s: int, gamma: int = 8, seed: int = DEFAULT_SEED) -> Sketch:
+        n, lda, dt = _check_matrix(A)
+        h = C.c_void_p()
+        L.check(self.ptr, self.lib.msp_sketch(self.ptr, _ptr(A), dt, n, lda, s, gamma, seed, C.byref(h)))
+        return Sketch(self, h, n, s, A.dtype)
+
+    # -- a3-a5
+    def nystrom(self, sk: Sketch, lam: float, lam0: float = 0.0, phi: int | None = None,
+                gamma_phi: int = 8, seed: int = DEFAULT_SEED) -> Factor:
+        if phi is None:
+            phi = 4 * sk.s
+        h = C.c_void_p()
+        L.check(self.ptr, self.lib.msp_nystrom(self.ptr, sk.handle, lam, lam0, phi, gamma_phi, seed,
+                                               C.byref(h)))
+        return Factor(self, h, sk)
+
+    def solve_m1(self, f: Factor, r: torch.Tensor, **opts) -> tuple[torch.Tensor, int]:
+        if not r.is_cuda or r.dtype != f.sketch.dtype or r.numel() != f.sketch.n:
+            raise ValueError("r must be a CUDA vector of the sketch's dtype and length n")
+        w = torch.empty_like(r)
+        o = make_opts(self.lib, **opts)
+        it = C.c_int()
+        L.check(self.ptr, self.lib.msp_solve_m1(self.ptr, f.handle, _ptr(r.contiguous()), _ptr(w),
+                                                C.byref(o), C.byref(it)))
+        return w, it.value
+
+    # -- a6-a8
+    def solve(self, f: Factor, A: torch.Tensor, b: torch.Tensor, lam: float,
+              raise_on_noconv: bool = True, **opts) -> tuple[torch.Tensor, dict]:
+        n, lda, dt = _check_matrix(A)
+        if not b.is_cuda or b.dtype != torch.float64 or b.numel() != n:
+            raise ValueError("b must be a CUDA float64 vector of length n")
+        b = b.contiguous()
+        x = torch.empty_like(b)
+        o = make_opts(self.lib, **opts)
+        info = L.MspInfo()
+        st = self.lib.msp_solve(self.ptr, f.handle, _ptr(A), dt, n, lda, lam, _ptr(b), _ptr(x),
+                                C.byref(o), C.byref(info))
+        if st != 0 and not (st == 5 and not raise_on_noconv):
+            L.check(self.ptr, st)
+        return x, info.as_dict()
+
+    def solve_full(self, A: torch.Tensor, b: torch.Tensor, lam: float, s: int, gamma: int = 8,
+                   lam0: float = 0.0, phi: int | None = None, gamma_phi: int = 8,
+                   seed: int = DEFAULT_SEED, out: torch.Tensor | None = None,
+                   **opts) -> tuple[torch.Tensor, dict]:
+        """Algorithm 1 end to end; A, b, out may live on the host (pinned is fastest)
+        or on the device."""
+        n, lda, dt = _check_matrix(A, need_cuda=False)
+        if b.dtype != torch.float64 or b.numel() != n:
+            raise ValueError("b must be a float64 vector of length n")
+        if phi is None:
+            phi = 4 * s
+        x = out if out is not None else torch.empty(n, dtype=torch.float64,
+                                                    pin_memory=not b.is_cuda,
+                                                    device=b.device if b.is_cuda else "cpu")
+        o = make_opts(self.lib, **opts)
+        info = L.MspInfo()
+        L.check(self.ptr, self.lib.msp_solve_full(self.ptr, _ptr(A), dt, n, lda, lam, _ptr(b.contiguous()),
+                                                  _ptr(x), s, gamma, lam0, phi, gamma_phi, seed,
+                                                  C.byref(o), C.byref(info)))
+        return x, info.as_dict()
+
+    def matvec_f64(self, A: torch.Tensor, x: torch.Tensor, lam: float = 0.0) -> torch.Tensor:
+        n, lda, dt = _check_matrix(A)
+        y = torch.empty_like(x)
+        L.check(self.ptr, self.lib.msp_matvec_f64(self.ptr, _ptr(A), dt, n, lda, lam, _ptr(x.contiguous()),
+                                                  _ptr(y)))
+        return y

@@ -1,0 +1,564 @@
+// Entry points of libmsp (include/msp.h): contexts, handles, argument checks,
+// staging of host buffers and the FP64 refinement driver.
+#include "msp_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <new>
+
+namespace {
+
+thread_local std::string g_noctx_error;
+
+// Switch to the context's device for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = (cudaSetDevice(dev) == cudaSuccess);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+msp_status msp_set_error(msp_ctx* ctx, msp_status st, const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->last_error = buf;
+    else g_noctx_error = buf;
+    return st;
+}
+
+msp_status msp_alloc(msp_ctx* ctx, void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    MSP_CUDA_TRY(ctx, cudaMallocAsync(p, bytes, ctx->stream));
+    return MSP_OK;
+}
+
+// Stream-ordered free; the pool keeps the memory for reuse.
+static void free_on(msp_ctx* ctx, void* p) {
+    if (p) cudaFreeAsync(p, ctx ? ctx->stream : nullptr);
+}
+
+void msp_free(void* p) {
+    if (p) cudaFreeAsync(p, nullptr);
+}
+
+msp_status msp_scratch(msp_ctx* ctx, size_t bytes, void** out) {
+    if (bytes > ctx->scratch_bytes) {
+        free_on(ctx, ctx->scratch);
+        ctx->scratch = nullptr;
+        ctx->scratch_bytes = 0;
+        size_t want = std::max(bytes, ctx->scratch_bytes + ctx->scratch_bytes / 2);
+        MSP_TRY(msp_alloc(ctx, &ctx->scratch, want));
+        ctx->scratch_bytes = want;
+    }
+    *out = ctx->scratch;
+    return MSP_OK;
+}
+
+static msp_status stage_alloc(msp_ctx* ctx, size_t bytes) {
+    if (bytes > ctx->stage_bytes) {
+        free_on(ctx, ctx->stage);
+        ctx->stage = nullptr;
+        ctx->stage_bytes = 0;
+        MSP_TRY(msp_alloc(ctx, &ctx->stage, bytes));
+        ctx->stage_bytes = bytes;
+    }
+    return MSP_OK;
+}
+
+extern "C" {
+
+const char* msp_version(void) { return "msp-gb300 0.1 sm_103a"; }
+
+int64_t msp_launch_count(const msp_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+void msp_default_opts(msp_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->tol = 1e-10;
+    o->max_outer = 2000;
+    o->max_refine = 20;
+    o->refine_tol = 1e-6;
+    o->inner_tol = 1e-6;
+    o->max_inner = 50;
+    o->precision = MSP_PREC_MIXED;
+    o->check_every = 8;
+}
+
+const char* msp_last_error(const msp_ctx* ctx) {
+    return ctx ? ctx->last_error.c_str() : g_noctx_error.c_str();
+}
+
+msp_status msp_create(msp_ctx** out, int device, void* stream) {
+    if (!out) return msp_set_error(nullptr, MSP_EINVAL, "msp_create: out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return msp_set_error(nullptr, MSP_EINVAL, "msp_create: no CUDA device %d", device);
+    }
+    DeviceGuard g(device);
+    msp_ctx* ctx = new (std::nothrow) msp_ctx();
+    if (!ctx) return msp_set_error(nullptr, MSP_ENOMEM, "msp_create: out of host memory");
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)stream;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        delete ctx;
+        return msp_set_error(nullptr, MSP_ECUDA, "msp_create: cudaGetDeviceProperties failed");
+    }
+    ctx->num_sms = prop.multiProcessorCount;
+    ctx->smem_optin = prop.sharedMemPerBlockOptin;
+    // keep freed pool memory for reuse (stream-ordered allocations are made
+    // and released once per solve)
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    if (cudaMalloc(&ctx->ctl, sizeof(CtlBlock)) != cudaSuccess ||
+        cudaMallocHost(&ctx->host_flags, 256) != cudaSuccess) {
+        cudaGetLastError();
+        msp_destroy(ctx);
+        return msp_set_error(nullptr, MSP_ENOMEM, "msp_create: allocation failed");
+    }
+    cudaMemset(ctx->ctl, 0, sizeof(CtlBlock));
+    *out = ctx;
+    return MSP_OK;
+}
+
+void msp_destroy(msp_ctx* ctx) {
+    if (!ctx) return;
+    DeviceGuard g(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->stage) cudaFree(ctx->stage);
+    if (ctx->ctl) cudaFree(ctx->ctl);
+    if (ctx->host_flags) cudaFreeHost(ctx->host_flags);
+    for (int i = 0; i < ctx->n_events; ++i) cudaEventDestroy(ctx->events[i]);
+    delete[] ctx->events;
+    delete ctx;
+}
+
+// ------------------------------------------------------------------ a1
+
+msp_status msp_sketch_pattern(msp_ctx* ctx, int64_t n, int64_t rows, int gamma, uint64_t seed,
+                              int stream, int32_t* idx, int8_t* sgn) {
+    if (!ctx) return msp_set_error(nullptr, MSP_EINVAL, "ctx is NULL");
+    if (!idx || !sgn) return msp_set_error(ctx, MSP_EINVAL, "pattern: NULL output");
+    DeviceGuard g(ctx->device);
+    return msp_pattern_launch(ctx, n, rows, gamma, seed, stream, idx, sgn, nullptr);
+}
+
+// --------------------------------------------------------------- a1-a2
+
+void msp_sketch_destroy(msp_sketch_t* sk) {
+    if (!sk) return;
+    for (void* p : {(void*)sk->idx, (void*)sk->sgn, (void*)sk->csr_ptr, (void*)sk->csr_ent, sk->C})
+        if (p) cudaFreeAsync(p, sk->stream);
+    delete sk;
+}
+
+static msp_status sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n,
+                              int64_t lda, int64_t s, int gamma, uint64_t seed,
+                              msp_sketch_t** out) {
+    if (dtype != MSP_F32 && dtype != MSP_F64)
+        return msp_set_error(ctx, MSP_EINVAL, "sketch: dtype must be MSP_F32 or MSP_F64");
+    if (n < 1 || lda < n || s < 16 || s > MSP_MAX_S || s > n || gamma < 1 ||
+        gamma > MSP_MAX_GAMMA || gamma > s || n >= (1ll << 30))
+        return msp_set_error(ctx, MSP_EINVAL,
+                             "sketch: need 16 <= s <= min(n, %d), 1 <= gamma <= min(s, %d), "
+                             "lda >= n (n=%lld lda=%lld s=%lld gamma=%d)",
+                             MSP_MAX_S, MSP_MAX_GAMMA, (long long)n, (long long)lda,
+                             (long long)s, gamma);
+    const int64_t sp = round_up(s, MSP_S_ALIGN);
+    if (dtype == MSP_F64 && sp > 1024)
+        return msp_set_error(ctx, MSP_EINVAL, "sketch: FP64 supports s <= 1024");
+    msp_sketch_s* sk = new (std::nothrow) msp_sketch_s();
+    if (!sk) return msp_set_error(ctx, MSP_ENOMEM, "sketch: host allocation failed");
+    sk->n = n; sk->s = s; sk->s_pad = sp; sk->gamma = gamma; sk->dtype = dtype; sk->seed = seed;
+    sk->stream = ctx->stream;
+    const size_t ts = dtype_size(dtype);
+    msp_status st = MSP_OK;
+    if ((st = msp_alloc(ctx, (void**)&sk->idx, (size_t)n * gamma * 4)) != MSP_OK ||
+        (st = msp_alloc(ctx, (void**)&sk->sgn, (size_t)n * gamma)) != MSP_OK ||
+        (st = msp_alloc(ctx, (void**)&sk->csr_ptr, (size_t)(sp + 1) * 4)) != MSP_OK ||
+        (st = msp_alloc(ctx, (void**)&sk->csr_ent, (size_t)n * gamma * 4)) != MSP_OK ||
+        (st = msp_alloc(ctx, &sk->C, (size_t)n * sp * ts)) != MSP_OK ||
+        (st = msp_pattern_launch(ctx, n, s, gamma, seed, 0, sk->idx, sk->sgn, nullptr)) != MSP_OK ||
+        (st = msp_build_csr(ctx, n, sp, gamma, sk->idx, sk->sgn, sk->csr_ptr, sk->csr_ent)) !=
+            MSP_OK ||
+        (st = msp_sketch_apply(ctx, A, dtype, n, lda, sp, sk->csr_ptr, sk->csr_ent, gamma,
+                               sk->C)) != MSP_OK) {
+        cudaStreamSynchronize(ctx->stream);
+        msp_sketch_destroy(sk);
+        return st;
+    }
+    *out = sk;
+    return MSP_OK;
+}
+
+msp_status msp_sketch(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n, int64_t lda,
+                      int64_t s, int gamma, uint64_t seed, msp_sketch_t** out) {
+    if (!ctx) return msp_set_error(nullptr, MSP_EINVAL, "ctx is NULL");
+    if (!A || !out) return msp_set_error(ctx, MSP_EINVAL, "sketch: NULL argument");
+    DeviceGuard g(ctx->device);
+    *out = nullptr;
+    return sketch_impl(ctx, A, dtype, n, lda, s, gamma, seed, out);
+}
+
+msp_status msp_sketch_info(const msp_sketch_t* sk, int64_t* n, int64_t* s, int64_t* s_pad,
+                           int* gamma, int* dtype) {
+    if (!sk) return msp_set_error(nullptr, MSP_EINVAL, "sketch is NULL");
+    if (n) *n = sk->n;
+    if (s) *s = sk->s;
+    if (s_pad) *s_pad = sk->s_pad;
+    if (gamma) *gamma = sk->gamma;
+    if (dtype) *dtype = sk->dtype;
+    return MSP_OK;
+}
+
+msp_status msp_sketch_get_C(msp_ctx* ctx, const msp_sketch_t* sk, void* C, int64_t ldc) {
+    if (!ctx || !sk || !C || ldc < sk->s) return msp_set_error(ctx, MSP_EINVAL, "get_C: bad argument");
+    DeviceGuard g(ctx->device);
+    const size_t ts = dtype_size(sk->dtype);
+    MSP_CUDA_TRY(ctx, cudaMemcpy2DAsync(C, ldc * ts, sk->C, sk->s_pad * ts, sk->s * ts, sk->n,
+                                        cudaMemcpyDeviceToDevice, ctx->stream));
+    return MSP_OK;
+}
+
+// --------------------------------------------------------------- a3-a5
+
+void msp_factor_destroy(msp_factor_t* f) {
+    if (!f) return;
+    for (void* p : {f->W, f->B, f->Bt, (void*)f->W64, (void*)f->M2, (void*)f->Linv64})
+        if (p) cudaFreeAsync(p, f->stream);
+    delete f;
+}
+
+static msp_status nystrom_impl(msp_ctx* ctx, const msp_sketch_s* sk, double lambda, double lambda0,
+                               int64_t phi, int gamma_phi, uint64_t seed, msp_factor_t** out) {
+    if (!(lambda > 0.0) || !(lambda0 >= 0.0) || !std::isfinite(lambda) || !std::isfinite(lambda0))
+        return msp_set_error(ctx, MSP_EINVAL, "nystrom: need lambda > 0 and lambda0 >= 0");
+    if (phi < 0 || (phi > 0 && (gamma_phi < 1 || gamma_phi > MSP_MAX_GAMMA || gamma_phi > phi ||
+                                phi >= (1ll << 30))))
+        return msp_set_error(ctx, MSP_EINVAL, "nystrom: need phi >= 0 and 1 <= gamma_phi <= min(phi, %d)",
+                             MSP_MAX_GAMMA);
+    const int64_t n = sk->n, sp = sk->s_pad;
+    const size_t ts = dtype_size(sk->dtype);
+    msp_factor_s* f = new (std::nothrow) msp_factor_s();
+    if (!f) return msp_set_error(ctx, MSP_ENOMEM, "nystrom: host allocation failed");
+    f->sk = sk; f->s = sk->s; f->s_pad = sp; f->phi = phi; f->dtype = sk->dtype;
+    f->stream = ctx->stream;
+    f->lambda = lambda; f->lambda0 = lambda0; f->lam_tilde = lambda + lambda0;
+    const size_t mat_t = (size_t)sp * sp * ts, mat_d = (size_t)sp * sp * 8;
+    msp_status st = MSP_OK;
+    void* phi_mem = nullptr;
+    auto fail = [&](msp_status s2) {
+        cudaStreamSynchronize(ctx->stream);
+        if (phi_mem) free_on(ctx, phi_mem);
+        msp_factor_destroy(f);
+        return s2;
+    };
+    if ((st = msp_alloc(ctx, &f->W, mat_t)) != MSP_OK || (st = msp_alloc(ctx, &f->B, mat_t)) != MSP_OK ||
+        (st = msp_alloc(ctx, &f->Bt, mat_t)) != MSP_OK ||
+        (st = msp_alloc(ctx, (void**)&f->W64, mat_d)) != MSP_OK ||
+        (st = msp_alloc(ctx, (void**)&f->M2, mat_d)) != MSP_OK ||
+        (st = msp_alloc(ctx, (void**)&f->Linv64, mat_d)) != MSP_OK)
+        return fail(st);
+    // W = S C = Pi^T C: row c of W gathers the rows j of C listed for column c
+    const double sc = 1.0 / std::sqrt((double)sk->gamma);
+    if ((st = msp_gather_rows(ctx, sk->dtype, sp, sp, sk->csr_ptr, sk->csr_ent, sk->C, sp, sc, f->W,
+                              sp)) != MSP_OK)
+        return fail(st);
+    const void* Ct = sk->C;
+    int64_t phi_rows = n;
+    if (phi > 0) {
+        // Phi: phi x n sparse embedding (stream 2); C~ = Phi C
+        size_t b_idx = round_up((int64_t)n * gamma_phi * 4, 256);
+        size_t b_sgn = round_up((int64_t)n * gamma_phi, 256);
+        size_t b_ptr = round_up((phi + 1) * 4, 256);
+        size_t b_ent = round_up((int64_t)n * gamma_phi * 4, 256);
+        size_t b_ct = (size_t)phi * sp * ts;
+        if ((st = msp_alloc(ctx, &phi_mem, b_idx + b_sgn + b_ptr + b_ent + b_ct)) != MSP_OK)
+            return fail(st);
+        char* c = (char*)phi_mem;
+        int32_t* pidx = (int32_t*)c; c += b_idx;
+        int8_t* psgn = (int8_t*)c; c += b_sgn;
+        int32_t* pptr = (int32_t*)c; c += b_ptr;
+        int32_t* pent = (int32_t*)c; c += b_ent;
+        void* ct = c;
+        if ((st = msp_pattern_launch(ctx, n, phi, gamma_phi, seed, 2, pidx, psgn, nullptr)) != MSP_OK ||
+            (st = msp_build_csr(ctx, n, phi, gamma_phi, pidx, psgn, pptr, pent)) != MSP_OK ||
+            (st = msp_gather_rows(ctx, sk->dtype, phi, sp, pptr, pent, sk->C, sp,
+                                  1.0 / std::sqrt((double)gamma_phi), ct, sp)) != MSP_OK)
+            return fail(st);
+        Ct = ct;
+        phi_rows = phi;
+    }
+    if ((st = msp_build_factor(ctx, f, Ct, phi_rows)) != MSP_OK) return fail(st);
+    if (phi_mem) free_on(ctx, phi_mem);
+    *out = f;
+    return MSP_OK;
+}
+
+msp_status msp_nystrom(msp_ctx* ctx, const msp_sketch_t* sk, double lambda, double lambda0,
+                       int64_t phi, int gamma_phi, uint64_t seed, msp_factor_t** out) {
+    if (!ctx) return msp_set_error(nullptr, MSP_EINVAL, "ctx is NULL");
+    if (!sk || !out) return msp_set_error(ctx, MSP_EINVAL, "nystrom: NULL argument");
+    DeviceGuard g(ctx->device);
+    *out = nullptr;
+    return nystrom_impl(ctx, sk, lambda, lambda0, phi, gamma_phi, seed, out);
+}
+
+msp_status msp_factor_get(msp_ctx* ctx, const msp_factor_t* f, double* W, double* M2, double* Linv,
+                          double* lam_tilde, double* shift, int* retries) {
+    if (!ctx || !f) return msp_set_error(ctx, MSP_EINVAL, "factor_get: NULL argument");
+    DeviceGuard g(ctx->device);
+    const int64_t s = f->s, sp = f->s_pad;
+    if (W) MSP_CUDA_TRY(ctx, cudaMemcpy2DAsync(W, s * 8, f->W64, sp * 8, s * 8, s,
+                                               cudaMemcpyDeviceToDevice, ctx->stream));
+    if (M2) MSP_CUDA_TRY(ctx, cudaMemcpy2DAsync(M2, s * 8, f->M2, sp * 8, s * 8, s,
+                                                cudaMemcpyDeviceToDevice, ctx->stream));
+    if (Linv) MSP_CUDA_TRY(ctx, cudaMemcpy2DAsync(Linv, s * 8, f->Linv64, sp * 8, s * 8, s,
+                                                  cudaMemcpyDeviceToDevice, ctx->stream));
+    if (lam_tilde) *lam_tilde = f->lam_tilde;
+    if (shift) *shift = f->shift;
+    if (retries) *retries = f->retries;
+    return MSP_OK;
+}
+
+msp_status msp_solve_m1(msp_ctx* ctx, const msp_factor_t* f, const void* r, void* w,
+                        const msp_opts* opts, int* inner_iters) {
+    if (!ctx) return msp_set_error(nullptr, MSP_EINVAL, "ctx is NULL");
+    if (!f || !r || !w) return msp_set_error(ctx, MSP_EINVAL, "solve_m1: NULL argument");
+    DeviceGuard g(ctx->device);
+    msp_opts o;
+    if (opts) o = *opts; else msp_default_opts(&o);
+    return msp_solve_m1_impl(ctx, f, r, w, &o, inner_iters);
+}
+
+// --------------------------------------------------------------- a6-a8
+
+static msp_status solve_impl(msp_ctx* ctx, const msp_factor_s* f, const void* A, msp_dtype dtype,
+                             int64_t n, int64_t lda, double lambda, const double* b, double* x,
+                             const msp_opts* o, msp_info* info) {
+    msp_info inf{};
+    inf.lambda_tilde = f->lam_tilde;
+    inf.shift = f->shift;
+    inf.shift_retries = f->retries;
+    if (n != f->sk->n || lda < n)
+        return msp_set_error(ctx, MSP_EINVAL, "solve: n does not match the factor, or lda < n");
+    if (!(lambda > 0.0) || !std::isfinite(lambda))
+        return msp_set_error(ctx, MSP_EINVAL, "solve: need lambda > 0");
+    const int prec = o->precision;
+    if (prec == MSP_PREC_FP64) {
+        if (dtype != MSP_F64 || f->dtype != MSP_F64)
+            return msp_set_error(ctx, MSP_EINVAL, "solve: MSP_PREC_FP64 needs an FP64 A and factor");
+    } else if (prec == MSP_PREC_FP32 || prec == MSP_PREC_MIXED) {
+        if (dtype != MSP_F32 || f->dtype != MSP_F32)
+            return msp_set_error(ctx, MSP_EINVAL, "solve: FP32/MIXED precision needs an FP32 A and factor");
+    } else {
+        return msp_set_error(ctx, MSP_EINVAL, "solve: unknown precision %d", prec);
+    }
+    if (!(o->tol > 0.0) || o->max_outer < 1 || o->max_inner < 1 || o->max_refine < 0)
+        return msp_set_error(ctx, MSP_EINVAL, "solve: bad options");
+    const msp_dtype wt = f->dtype;
+    const size_t ts = dtype_size(wt);
+    // per-solve buffers: r64 (n), rhs_w (n), sol_w (n), scalars
+    void* mem = nullptr;
+    size_t b_r = round_up(n * 8, 256), b_w = round_up(n * ts, 256);
+    MSP_TRY(msp_alloc(ctx, &mem, b_r + 2 * b_w + 256));
+    char* c = (char*)mem;
+    double* r64 = (double*)c; c += b_r;
+    void* rhs_w = c; c += b_w;
+    void* sol_w = c; c += b_w;
+    double* scal = (double*)c;    // [0] |b|^2, [1] |r|^2
+    double* hs = (double*)ctx->host_flags + 8;
+    msp_status st = MSP_OK;
+    int outer_total = 0, inner_total = 0, steps = 0;
+    double bb = 0.0, rr = 0.0;
+    ProfSlot slots[3];
+    Profiler pr;
+    pr.ctx = ctx;
+    pr.on = o->profile != 0;
+    if (pr.on) MSP_TRY(msp_profiler_reserve(ctx, 4096));
+    auto finish = [&](msp_status s2) {
+        cudaStreamSynchronize(ctx->stream);
+        if (pr.on) {
+            inf.gemv_launches = slots[0].launches;
+            inf.gemv_ms = slots[0].ms;
+            inf.level2_launches = slots[1].launches;
+            inf.level2_ms = slots[1].ms;
+            inf.resid_launches = slots[2].launches;
+            inf.resid_ms = slots[2].ms;
+        }
+        free_on(ctx, mem);
+        inf.outer_iters = outer_total;
+        inf.inner_iters = inner_total;
+        inf.refine_steps = steps;
+        inf.status = s2;
+        if (info) *info = inf;
+        return s2;
+    };
+    auto read2 = [&](double* a0, double* a1) -> msp_status {
+        MSP_CUDA_TRY(ctx, cudaMemcpyAsync(hs, scal, 16, cudaMemcpyDeviceToHost, ctx->stream));
+        MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        *a0 = hs[0];
+        *a1 = hs[1];
+        return MSP_OK;
+    };
+    if ((st = msp_norm2(ctx, b, n, scal + 0)) != MSP_OK) return finish(st);
+    MSP_CUDA_TRY(ctx, cudaMemcpyAsync(r64, b, n * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    MSP_CUDA_TRY(ctx, cudaMemcpyAsync(scal + 1, scal + 0, 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    if ((st = read2(&bb, &rr)) != MSP_OK) return finish(st);
+    if (!std::isfinite(bb)) return finish(msp_set_error(ctx, MSP_ENONFINITE, "solve: b is not finite"));
+    MSP_CUDA_TRY(ctx, cudaMemsetAsync(x, 0, n * 8, ctx->stream));
+    if (bb == 0.0) {
+        inf.rel_resid = 0.0;
+        return finish(MSP_OK);
+    }
+    const int max_steps = (prec == MSP_PREC_MIXED) ? o->max_refine + 1 : 1;
+    const double step_tol = (prec == MSP_PREC_MIXED) ? std::max(o->refine_tol, o->tol) : o->tol;
+    msp_status kst = MSP_OK;
+    bool have_resid = true;   // r64 / rr hold the residual of the current x (x = 0: r = b)
+    for (int k = 0; k < max_steps; ++k) {
+        if (!have_resid) {
+            // r = b - (A + lam I) x, FP64 accumulation
+            if ((st = pr.begin(0)) != MSP_OK) return finish(st);
+            if ((st = msp_matvec64(ctx, A, dtype, n, lda, lambda, x, b, r64, scal + 1)) != MSP_OK)
+                return finish(st);
+            if ((st = pr.end()) != MSP_OK) return finish(st);
+            if ((st = pr.finish(&slots[2], 1)) != MSP_OK) return finish(st);
+            if ((st = read2(&bb, &rr)) != MSP_OK) return finish(st);
+            if (!std::isfinite(rr))
+                return finish(msp_set_error(ctx, MSP_ENONFINITE, "solve: residual is not finite"));
+            have_resid = true;
+        }
+        if (rr <= o->tol * o->tol * bb) break;
+        // correction solve on the normalised residual: (A + lam I) d = r / |r|
+        if ((st = msp_scale_cast(ctx, r64, scal + 1, n, wt, rhs_w)) != MSP_OK) return finish(st);
+        int it = 0, in = 0;
+        kst = msp_krylov_solve(ctx, f, A, dtype, n, lda, lambda, rhs_w, sol_w, step_tol,
+                               o->max_outer, o, &it, &in, pr.on ? slots : nullptr);
+        outer_total += it;
+        inner_total += in;
+        if (kst != MSP_OK && kst != MSP_ENOCONV) return finish(kst);
+        if ((st = msp_axpy_back(ctx, x, sol_w, wt, scal + 1, n, k > 0)) != MSP_OK) return finish(st);
+        steps = k + 1;
+        have_resid = false;
+        if (prec != MSP_PREC_MIXED) break;
+    }
+    if (!have_resid) {
+        if ((st = pr.begin(0)) != MSP_OK) return finish(st);
+        if ((st = msp_matvec64(ctx, A, dtype, n, lda, lambda, x, b, r64, scal + 1)) != MSP_OK)
+            return finish(st);
+        if ((st = pr.end()) != MSP_OK) return finish(st);
+        if ((st = pr.finish(&slots[2], 1)) != MSP_OK) return finish(st);
+        if ((st = read2(&bb, &rr)) != MSP_OK) return finish(st);
+    }
+    inf.rel_resid = std::sqrt(rr / bb);
+    if (!(inf.rel_resid <= o->tol) && prec != MSP_PREC_FP32)
+        return finish(msp_set_error(ctx, MSP_ENOCONV,
+                                    "solve: relative residual %.3e above tol %.3e after %d steps",
+                                    inf.rel_resid, o->tol, steps));
+    if (kst == MSP_ENOCONV) return finish(kst);
+    return finish(MSP_OK);
+}
+
+msp_status msp_solve(msp_ctx* ctx, const msp_factor_t* f, const void* A, msp_dtype dtype, int64_t n,
+                     int64_t lda, double lambda, const double* b, double* x, const msp_opts* opts,
+                     msp_info* info) {
+    if (!ctx) return msp_set_error(nullptr, MSP_EINVAL, "ctx is NULL");
+    if (!f || !A || !b || !x) return msp_set_error(ctx, MSP_EINVAL, "solve: NULL argument");
+    DeviceGuard g(ctx->device);
+    msp_opts o;
+    if (opts) o = *opts; else msp_default_opts(&o);
+    return solve_impl(ctx, f, A, dtype, n, lda, lambda, b, x, &o, info);
+}
+
+msp_status msp_solve_full(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n, int64_t lda,
+                          double lambda, const double* b, double* x, int64_t s, int gamma,
+                          double lambda0, int64_t phi, int gamma_phi, uint64_t seed,
+                          const msp_opts* opts, msp_info* info) {
+    if (!ctx) return msp_set_error(nullptr, MSP_EINVAL, "ctx is NULL");
+    if (!A || !b || !x) return msp_set_error(ctx, MSP_EINVAL, "solve_full: NULL argument");
+    if (n < 1 || lda < n) return msp_set_error(ctx, MSP_EINVAL, "solve_full: need lda >= n >= 1");
+    DeviceGuard g(ctx->device);
+    msp_opts o;
+    if (opts) o = *opts; else msp_default_opts(&o);
+    const size_t ts = dtype_size(dtype);
+    const bool dA = is_device_ptr(A), db = is_device_ptr(b), dx = is_device_ptr(x);
+    size_t need = (dA ? 0 : round_up(n * n * ts, 256)) + (db ? 0 : round_up(n * 8, 256)) +
+                  (dx ? 0 : round_up(n * 8, 256));
+    const void* Ad = A;
+    const double* bd = b;
+    double* xd = x;
+    int64_t ldd = lda;
+    if (need) {
+        MSP_TRY(stage_alloc(ctx, need));
+        char* c = (char*)ctx->stage;
+        if (!dA) {
+            MSP_CUDA_TRY(ctx, cudaMemcpy2DAsync(c, n * ts, A, lda * ts, n * ts, n,
+                                                cudaMemcpyHostToDevice, ctx->stream));
+            Ad = c;
+            ldd = n;
+            c += round_up(n * n * ts, 256);
+        }
+        if (!db) {
+            MSP_CUDA_TRY(ctx, cudaMemcpyAsync(c, b, n * 8, cudaMemcpyHostToDevice, ctx->stream));
+            bd = (const double*)c;
+            c += round_up(n * 8, 256);
+        }
+        if (!dx) xd = (double*)c;
+    }
+    msp_sketch_t* sk = nullptr;
+    msp_factor_t* f = nullptr;
+    msp_status st = sketch_impl(ctx, Ad, dtype, n, ldd, s, gamma, seed, &sk);
+    if (st == MSP_OK) st = nystrom_impl(ctx, sk, lambda, lambda0, phi, gamma_phi, seed, &f);
+    msp_status st2 = MSP_OK;
+    if (st == MSP_OK) st2 = solve_impl(ctx, f, Ad, dtype, n, ldd, lambda, bd, xd, &o, info);
+    if (st == MSP_OK && (st2 == MSP_OK || st2 == MSP_ENOCONV) && !dx) {
+        cudaError_t e = cudaMemcpyAsync(x, xd, n * 8, cudaMemcpyDeviceToHost, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) st2 = msp_set_error(ctx, MSP_ECUDA, "solve_full: copy-out failed");
+    }
+    cudaStreamSynchronize(ctx->stream);
+    msp_factor_destroy(f);
+    msp_sketch_destroy(sk);
+    return st != MSP_OK ? st : st2;
+}
+
+msp_status msp_matvec_f64(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n, int64_t lda,
+                          double lambda, const double* x, double* y) {
+    if (!ctx) return msp_set_error(nullptr, MSP_EINVAL, "ctx is NULL");
+    if (!A || !x || !y || n < 1 || lda < n)
+        return msp_set_error(ctx, MSP_EINVAL, "matvec: bad argument");
+    DeviceGuard g(ctx->device);
+    return msp_matvec64(ctx, A, dtype, n, lda, lambda, x, nullptr, y, nullptr);
+}
+
+}  // extern "C"

@@ -1,0 +1,857 @@
+// Level-1 and level-2 iterations of MSP on sm_103a (Algorithm 1 step 5 and
+// Algorithm 2).
+//
+// One level-1 (outer) iteration is two launches:
+//   k_gemv      q = (A + lam I) p, one pass over A, with the dot p^T q fused;
+//               the last block to finish forms alpha = (r^T z) / (p^T q).
+//   k_level2    persistent cooperative kernel: x += alpha p, r -= alpha q,
+//               convergence test on |r|, then SolveM1(r) (Algorithm 2):
+//               g = C^T r; level-2 PCG on (C^T C + lam~ W) y = g
+//               preconditioned by M2^{-1} v = B^T (B v); w = (r - C y)/lam~;
+//               finally the flexible (Polak-Ribiere) beta and p = w + beta p.
+// Level-2 vectors (length s) are held redundantly in every block's shared
+// memory; every block computes the same scalars from the same partial sums
+// in the same order, so all blocks take identical branches and the number of
+// grid barriers always matches. Reductions use fixed orders (deterministic).
+#include "msp_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace {
+
+constexpr int kNW = 8;             // warps per block in k_level2
+constexpr int kThreads = kNW * 32;
+
+enum { MODE_INIT = 0, MODE_ITER = 1, MODE_APPLY = 2 };
+
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int W = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int W = 2; };
+
+template <typename T>
+__device__ inline void load16(const T* p, T* out) {
+    typename Vec16<T>::type v = *reinterpret_cast<const typename Vec16<T>::type*>(p);
+    if constexpr (Vec16<T>::W == 4) { out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w; }
+    else { out[0] = v.x; out[1] = v.y; }
+}
+
+// Streaming (evict-first) 16-byte load: A is read once per pass, so it should
+// not displace the sketch C, which the level-2 iteration re-reads from L2.
+template <typename T>
+__device__ inline void load16_stream(const T* p, T* out) {
+    typename Vec16<T>::type v = __ldcs(reinterpret_cast<const typename Vec16<T>::type*>(p));
+    if constexpr (Vec16<T>::W == 4) { out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w; }
+    else { out[0] = v.x; out[1] = v.y; }
+}
+
+// Deterministic block-wide sum of one double per thread (all threads get it).
+__device__ inline double block_sum(double v, double* red) {
+    v = msp::warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    const int nw = blockDim.x >> 5;
+    for (int k = 0; k < nw; ++k) t += red[k];
+    return t;
+}
+
+// Sum of a per-block partial array in fixed order (all threads get it).
+__device__ inline double sum_parts(const double* parts, int stride, int G, double* red) {
+    double v = 0.0;
+    for (int k = threadIdx.x; k < G; k += blockDim.x) v += __ldcg(&parts[(int64_t)k * stride]);
+    return block_sum(v, red);
+}
+
+// ------------------------------------------------------------------ GEMV
+
+// q = (A + lam I) p; warp per row (grid-stride); lane reads 16 B vectors.
+// The block partials of p^T q are combined by the last block, which writes
+// ctl->pq and ctl->alpha = ctl->rz / pq (or flags an error).
+template <typename TA, typename T, bool VEC>
+__global__ void __launch_bounds__(256) k_gemv(const TA* __restrict__ A, int64_t lda, int64_t n,
+                                             double lam, const T* __restrict__ p,
+                                             T* __restrict__ q, double* __restrict__ part,
+                                             CtlBlock* ctl) {
+    if (ctl->done | ctl->error) return;
+    __shared__ double red[32];
+    __shared__ bool am_last;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    double pq = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n;
+         i += warps) {
+        const TA* row = A + i * lda;
+        T acc = T(0);
+        if constexpr (VEC) {
+            constexpr int W = Vec16<TA>::W;
+            int64_t j = (int64_t)lane * W;
+            // 4 independent 16 B loads in flight per lane
+            for (; j + 3 * 32 * W < n; j += 4 * 32 * W) {
+                TA a[4][W];
+                T pv[4][W];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) load16_stream(row + j + u * 32 * W, a[u]);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+#pragma unroll
+                    for (int e = 0; e < W; ++e) pv[u][e] = p[j + u * 32 * W + e];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int e = 0; e < W; ++e) acc += (T)a[u][e] * pv[u][e];
+            }
+            for (; j < n; j += 32 * W) {
+                TA a[W];
+                load16_stream(row + j, a);
+#pragma unroll
+                for (int e = 0; e < W; ++e) acc += (T)a[e] * p[j + e];
+            }
+        } else {
+            for (int64_t j = lane; j < n; j += 32) acc += (T)__ldcs(&row[j]) * p[j];
+        }
+        acc = msp::warp_sum(acc);
+        if (lane == 0) {
+            T qi = acc + (T)lam * p[i];
+            q[i] = qi;
+            pq += (double)p[i] * (double)qi;
+        }
+    }
+    double tot = block_sum(pq, red);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = tot;
+        __threadfence();
+        unsigned int t = atomicAdd(&ctl->last_block_counter, 1u);
+        am_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    double all = sum_parts(part, 1, gridDim.x, red);
+    if (threadIdx.x == 0) {
+        ctl->last_block_counter = 0;
+        ctl->pq = all;
+        if (!isfinite(all)) { ctl->error = MSP_ENONFINITE; }
+        else if (!(all > 0.0)) { ctl->error = MSP_ENOTPD; }
+        else ctl->alpha = ctl->rz / all;
+    }
+}
+
+// out = b - (A + lam I) x  (or (A + lam I) x if b == nullptr), FP64
+// accumulation; |out|^2 into *norm2 (last block, fixed order).
+template <typename TA>
+__global__ void __launch_bounds__(256) k_matvec64(const TA* __restrict__ A, int64_t lda, int64_t n,
+                                                 double lam, const double* __restrict__ x,
+                                                 const double* __restrict__ b,
+                                                 double* __restrict__ out, double* __restrict__ part,
+                                                 unsigned int* counter, double* norm2) {
+    __shared__ double red[32];
+    __shared__ bool am_last;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    double nn = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n;
+         i += warps) {
+        const TA* row = A + i * lda;
+        double acc = 0.0;
+        for (int64_t j = lane; j < n; j += 32) acc = fma((double)__ldcs(&row[j]), x[j], acc);
+        acc = msp::warp_sum(acc);
+        if (lane == 0) {
+            double v = acc + lam * x[i];
+            if (b) v = b[i] - v;
+            out[i] = v;
+            nn += v * v;
+        }
+    }
+    double tot = block_sum(nn, red);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = tot;
+        __threadfence();
+        unsigned int t = atomicAdd(counter, 1u);
+        am_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    double all = sum_parts(part, 1, gridDim.x, red);
+    if (threadIdx.x == 0) {
+        *counter = 0;
+        if (norm2) *norm2 = all;
+    }
+}
+
+// ---------------------------------------------------------- level 2
+
+template <typename T>
+struct L2Args {
+    int64_t n, s_pad;
+    int mode;
+    const T* C;
+    const T* W;
+    const T* B;
+    const T* Bt;
+    T lam_t;
+    double tol_rel2;        // level-1 tolerance^2 (MODE_INIT sets ctl->tol2)
+    double inner_tol2;
+    int max_inner;
+    T* x;
+    T* r;
+    const T* q;
+    T* p;
+    T* z;                   // level-1 preconditioned residual (in/out)
+    CtlBlock* ctl;
+    T* part;                // G x s_pad
+    T* gvec;                // s_pad
+    T* uvec;
+    T* tvec;
+    T* zvec;
+    T* wdvec;
+    double* dpart;          // G x 4
+};
+
+// Per-lane slice of an s_pad row: PL elements as PL/W vectors of W elements,
+// element index of vector v, component e: v*32*W + lane*W + e.
+template <typename T, int PL>
+struct RowSlice {
+    static constexpr int W = Vec16<T>::W;
+    static constexpr int NVEC = PL / W;
+    T v[PL];
+    __device__ inline void load(const T* row, int lane) {
+#pragma unroll
+        for (int k = 0; k < NVEC; ++k) load16(row + k * 32 * W + lane * W, v + k * W);
+    }
+    __device__ inline T dot_smem(const T* s, int lane) const {
+        T a = T(0);
+#pragma unroll
+        for (int k = 0; k < NVEC; ++k)
+#pragma unroll
+            for (int e = 0; e < W; ++e) a += v[k * W + e] * s[k * 32 * W + lane * W + e];
+        return a;
+    }
+};
+
+template <typename T, int PL>
+__device__ inline void store_slice(T* dst, const T* src, int lane) {
+    constexpr int W = Vec16<T>::W;
+#pragma unroll
+    for (int k = 0; k < PL / W; ++k)
+#pragma unroll
+        for (int e = 0; e < W; ++e) dst[k * 32 * W + lane * W + e] = src[k * W + e];
+}
+
+// Row pass over this block's rows of C.
+//   kind 0: acc += r_i c_i                     (g = C^T r)
+//   kind 1: acc += (c_i . d) c_i               (u = C^T C d)
+//   kind 2: w_i = (r_i - c_i . y) / lam~; dots r.w and r.z_old  (no acc)
+// Per-warp accumulators are combined through shared memory into part[b].
+template <typename T, int PL>
+__device__ inline void row_one(const L2Args<T>& a, int kind, int64_t i, const RowSlice<T, PL>& c,
+                               const T* svec, T* acc, double& d_rw, double& d_rzo, int lane) {
+    T coef;
+    if (kind == 0) {
+        coef = a.r[i];
+    } else {
+        T t = msp::warp_sum(c.dot_smem(svec, lane));
+        if (kind == 1) {
+            coef = t;
+        } else {
+            T ri = a.r[i];
+            T wi = (ri - t) / a.lam_t;
+            if (lane == 0) {
+                T zo = a.z[i];
+                d_rw += (double)ri * (double)wi;
+                d_rzo += (double)ri * (double)zo;
+                a.z[i] = wi;
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < PL; ++k) acc[k] += coef * c.v[k];
+}
+
+// Row pass over this block's rows of C, two rows in flight per warp.
+//   kind 0: acc += r_i c_i                     (g = C^T r)
+//   kind 1: acc += (c_i . d) c_i               (u = C^T C d)
+//   kind 2: w_i = (r_i - c_i . y) / lam~; dots r.w and r.z_old  (no acc)
+// Per-warp accumulators are combined through shared memory into part[b].
+template <typename T, int PL>
+__device__ void row_pass(const L2Args<T>& a, int kind, int64_t row0, int64_t row1, const T* svec,
+                         T* swarp, double* rw, double* rzo) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T acc[PL];
+#pragma unroll
+    for (int k = 0; k < PL; ++k) acc[k] = T(0);
+    double d_rw = 0.0, d_rzo = 0.0;
+    int64_t i = row0 + w;
+    for (; i + kNW < row1; i += 2 * kNW) {
+        RowSlice<T, PL> c0, c1;
+        c0.load(a.C + i * a.s_pad, lane);
+        c1.load(a.C + (i + kNW) * a.s_pad, lane);
+        row_one<T, PL>(a, kind, i, c0, svec, acc, d_rw, d_rzo, lane);
+        row_one<T, PL>(a, kind, i + kNW, c1, svec, acc, d_rw, d_rzo, lane);
+    }
+    if (i < row1) {
+        RowSlice<T, PL> c0;
+        c0.load(a.C + i * a.s_pad, lane);
+        row_one<T, PL>(a, kind, i, c0, svec, acc, d_rw, d_rzo, lane);
+    }
+    if (kind == 2) {
+        *rw = d_rw;
+        *rzo = d_rzo;
+        return;
+    }
+    store_slice<T, PL>(swarp + (int64_t)w * a.s_pad, acc, lane);
+}
+
+// part[b][c] = sum over warps of swarp[w][c]
+template <typename T>
+__device__ inline void combine_warps(const L2Args<T>& a, const T* swarp, int b) {
+    __syncthreads();
+    for (int64_t c = threadIdx.x; c < a.s_pad; c += blockDim.x) {
+        T v = T(0);
+#pragma unroll
+        for (int w = 0; w < kNW; ++w) v += swarp[w * a.s_pad + c];
+        a.part[(int64_t)b * a.s_pad + c] = v;
+    }
+}
+
+// out[c] = M[c,:] . svec for c in [c0, c1) (warp per row)
+template <typename T, int PL>
+__device__ inline void rows_dot(const T* M, int64_t s_pad, int64_t c0, int64_t c1, const T* svec,
+                                T* out) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t c = c0 + w; c < c1; c += kNW) {
+        RowSlice<T, PL> m;
+        m.load(M + c * s_pad, lane);
+        T t = msp::warp_sum(m.dot_smem(svec, lane));
+        if (lane == 0) out[c] = t;
+    }
+}
+
+template <typename T>
+__device__ inline void load_full(const T* g, T* s, int64_t m) {
+    for (int64_t c = threadIdx.x; c < m; c += blockDim.x) s[c] = __ldcg(&g[c]);
+}
+
+template <typename T, int PL>
+__global__ void __launch_bounds__(kThreads, 1) k_level2(L2Args<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t sp = a.s_pad;
+    T* sd = reinterpret_cast<T*>(smem_raw);       // d (search direction)
+    T* sres = sd + sp;                            // level-2 residual
+    T* sy = sres + sp;                            // level-2 iterate
+    T* stmp = sy + sp;                            // scratch full vector
+    T* swarp = stmp + sp;                         // kNW x sp
+    __shared__ double red[32];
+    __shared__ double s_rw, s_rzo;
+
+    CtlBlock* ctl = a.ctl;
+    if (ctl->done | ctl->error) return;
+    const int G = gridDim.x, b = blockIdx.x;
+    const int64_t row0 = a.n * b / G, row1 = a.n * (b + 1) / G;
+    const int64_t c0 = sp * b / G, c1 = sp * (b + 1) / G;
+    const double alpha = ctl->alpha;
+    const double rz_outer = ctl->rz;
+    const double tol2 = ctl->tol2;
+    unsigned int* bc = &ctl->bar_count;
+    unsigned int* bg = &ctl->bar_gen;
+    int* err = &ctl->error;
+
+    // ---- level-1 update and g = C^T r partials
+    double rr = 0.0;
+    if (a.mode != MODE_APPLY) {
+        for (int64_t i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
+            T ri = a.r[i];
+            if (a.mode == MODE_ITER) {
+                a.x[i] += (T)alpha * a.p[i];
+                ri -= (T)alpha * a.q[i];
+                a.r[i] = ri;
+            }
+            rr += (double)ri * (double)ri;
+        }
+        rr = block_sum(rr, red);
+        if (threadIdx.x == 0) a.dpart[b * 4 + 0] = rr;
+    }
+    __syncthreads();
+    row_pass<T, PL>(a, 0, row0, row1, nullptr, swarp, nullptr, nullptr);
+    combine_warps(a, swarp, b);
+    if (!msp::grid_barrier(bc, bg, err)) return;
+
+    if (a.mode != MODE_APPLY) {
+        rr = sum_parts(a.dpart + 0, 4, G, red);
+        if (!isfinite(rr)) {
+            if (b == 0 && threadIdx.x == 0) ctl->error = MSP_ENONFINITE;
+            return;
+        }
+        double t2 = tol2;
+        if (a.mode == MODE_INIT) t2 = a.tol_rel2 * rr;
+        if (rr <= t2) {
+            if (b == 0 && threadIdx.x == 0) {
+                ctl->rr = rr;
+                if (a.mode == MODE_INIT) { ctl->bb = rr; ctl->tol2 = t2; }
+                if (a.mode == MODE_ITER) ctl->iters += 1;
+                ctl->done = 1;
+            }
+            return;
+        }
+    }
+    // ---- g reduced over this block's columns
+    double gg = 0.0;
+    for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+        T v = T(0);
+        for (int k = 0; k < G; ++k) v += __ldcg(&a.part[(int64_t)k * sp + c]);
+        a.gvec[c] = v;
+        gg += (double)v * (double)v;
+    }
+    gg = block_sum(gg, red);
+    if (threadIdx.x == 0) a.dpart[b * 4 + 1] = gg;
+    if (!msp::grid_barrier(bc, bg, err)) return;
+    gg = sum_parts(a.dpart + 1, 4, G, red);
+    load_full(a.gvec, sres, sp);
+    for (int64_t c = threadIdx.x; c < sp; c += blockDim.x) sy[c] = T(0);
+    __syncthreads();
+
+    // ---- z = M2^{-1} res = B^T (B res)
+    auto precond = [&](double* rz_out) -> bool {
+        rows_dot<T, PL>(a.B, sp, c0, c1, sres, a.tvec);
+        if (!msp::grid_barrier(bc, bg, err)) return false;
+        load_full(a.tvec, stmp, sp);
+        __syncthreads();
+        rows_dot<T, PL>(a.Bt, sp, c0, c1, stmp, a.zvec);
+        __syncthreads();
+        double part = 0.0;
+        for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x)
+            part += (double)sres[c] * (double)a.zvec[c];
+        part = block_sum(part, red);
+        if (threadIdx.x == 0) a.dpart[b * 4 + 2] = part;
+        if (!msp::grid_barrier(bc, bg, err)) return false;
+        *rz_out = sum_parts(a.dpart + 2, 4, G, red);
+        return true;
+    };
+
+    double rz_in = 0.0;
+    if (!precond(&rz_in)) return;
+    load_full(a.zvec, sd, sp);
+    __syncthreads();
+    double rres = gg;
+    const double tin2 = a.inner_tol2 * gg;
+    int k = 0;
+    while (k < a.max_inner && rres > tin2) {
+        // P1: partial u = C^T (C d) over this block's rows; wd = W d (columns)
+        row_pass<T, PL>(a, 1, row0, row1, sd, swarp, nullptr, nullptr);
+        combine_warps(a, swarp, b);
+        rows_dot<T, PL>(a.W, sp, c0, c1, sd, a.wdvec);
+        if (!msp::grid_barrier(bc, bg, err)) return;
+        // P2: u over this block's columns; d.u partial
+        double du = 0.0;
+        for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+            T v = T(0);
+            for (int kk = 0; kk < G; ++kk) v += __ldcg(&a.part[(int64_t)kk * sp + c]);
+            v += a.lam_t * __ldcg(&a.wdvec[c]);
+            a.uvec[c] = v;
+            du += (double)sd[c] * (double)v;
+        }
+        du = block_sum(du, red);
+        if (threadIdx.x == 0) a.dpart[b * 4 + 3] = du;
+        if (!msp::grid_barrier(bc, bg, err)) return;
+        // P3: step
+        du = sum_parts(a.dpart + 3, 4, G, red);
+        if (!(du > 0.0)) break;   // breakdown (same decision in every block)
+        const T ain = (T)(rz_in / du);
+        double loc = 0.0;
+        for (int64_t c = threadIdx.x; c < sp; c += blockDim.x) {
+            T u = __ldcg(&a.uvec[c]);
+            sy[c] += ain * sd[c];
+            T rv = sres[c] - ain * u;
+            sres[c] = rv;
+            loc += (double)rv * (double)rv;
+        }
+        rres = block_sum(loc, red);
+        ++k;
+        if (rres <= tin2) break;
+        double rz_new = 0.0;
+        if (!precond(&rz_new)) return;
+        const T beta = (T)(rz_new / rz_in);
+        rz_in = rz_new;
+        for (int64_t c = threadIdx.x; c < sp; c += blockDim.x) sd[c] = __ldcg(&a.zvec[c]) + beta * sd[c];
+        __syncthreads();
+    }
+
+    // ---- w = (r - C y) / lam~ into z; dots for the level-1 beta
+    __syncthreads();
+    double rw = 0.0, rzo = 0.0;
+    row_pass<T, PL>(a, 2, row0, row1, sy, swarp, &rw, &rzo);
+    rw = block_sum(rw, red);
+    rzo = block_sum(rzo, red);
+    if (threadIdx.x == 0) {
+        a.dpart[b * 4 + 0] = rw;
+        a.dpart[b * 4 + 1] = rzo;
+    }
+    if (a.mode == MODE_APPLY) {
+        if (b == 0 && threadIdx.x == 0) atomicAdd(&ctl->inner_iters, k);
+        return;
+    }
+    if (!msp::grid_barrier(bc, bg, err)) return;
+    rw = sum_parts(a.dpart + 0, 4, G, red);
+    rzo = sum_parts(a.dpart + 1, 4, G, red);
+    T beta = T(0);
+    if (a.mode == MODE_ITER) beta = (T)((rw - rzo) / rz_outer);
+    for (int64_t i = row0 + threadIdx.x; i < row1; i += blockDim.x)
+        a.p[i] = a.z[i] + beta * (a.mode == MODE_ITER ? a.p[i] : T(0));
+    if (b == 0 && threadIdx.x == 0) {
+        ctl->rz = rw;
+        ctl->beta = (double)beta;
+        ctl->rr = rr;
+        ctl->inner_iters += k;
+        if (a.mode == MODE_ITER) ctl->iters += 1;
+        if (a.mode == MODE_INIT) { ctl->bb = rr; ctl->tol2 = a.tol_rel2 * rr; }
+        if (!(rw > 0.0) && isfinite(rw)) ctl->error = MSP_ENOTPD;
+        if (!isfinite(rw)) ctl->error = MSP_ENONFINITE;
+    }
+    (void)s_rw;
+    (void)s_rzo;
+}
+
+template <typename T, int PL>
+msp_status launch_level2_pl(msp_ctx* ctx, L2Args<T>& a, int G) {
+    auto kern = k_level2<T, PL>;
+    size_t smem = (size_t)(4 + kNW) * a.s_pad * sizeof(T);
+    MSP_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem));
+    // co-residency is required by the grid barrier: never exceed what fits
+    int per_sm = 0;
+    MSP_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
+    if (per_sm < 1)
+        return msp_set_error(ctx, MSP_EINVAL, "level-2 kernel does not fit on an SM");
+    G = std::min(G, per_sm * ctx->num_sms);
+    void* args[] = {&a};
+    ++ctx->launches;
+    MSP_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(kThreads), args,
+                                                  smem, ctx->stream));
+    return MSP_OK;
+}
+
+template <typename T>
+msp_status launch_level2(msp_ctx* ctx, L2Args<T>& a, int G) {
+    switch (a.s_pad) {
+        case 128: return launch_level2_pl<T, 4>(ctx, a, G);
+        case 256: return launch_level2_pl<T, 8>(ctx, a, G);
+        case 512: return launch_level2_pl<T, 16>(ctx, a, G);
+        case 1024: return launch_level2_pl<T, 32>(ctx, a, G);
+        case 2048:
+            if constexpr (sizeof(T) == 4) return launch_level2_pl<T, 64>(ctx, a, G);
+            break;
+        default: break;
+    }
+    return msp_set_error(ctx, MSP_EINVAL, "level-2: unsupported padded sketch size %lld",
+                         (long long)a.s_pad);
+}
+
+struct Workspace {
+    void* part;
+    void* vecs;
+    double* dpart;
+    void* level1;   // x r q p z (n each)
+    double* gpart;  // gemv partials
+};
+
+template <typename T>
+msp_status get_workspace(msp_ctx* ctx, int64_t n, int64_t sp, int G, int Gg, Workspace* ws) {
+    size_t ts = sizeof(T);
+    size_t b_part = round_up((int64_t)G * sp * ts, 256);
+    size_t b_vecs = round_up(5 * sp * ts, 256);
+    size_t b_dpart = round_up((int64_t)G * 4 * 8, 256);
+    size_t b_l1 = round_up(5 * n * ts, 256);
+    size_t b_gp = round_up((int64_t)Gg * 8, 256);
+    void* scr = nullptr;
+    MSP_TRY(msp_scratch(ctx, b_part + b_vecs + b_dpart + b_l1 + b_gp, &scr));
+    char* c = (char*)scr;
+    ws->part = c; c += b_part;
+    ws->vecs = c; c += b_vecs;
+    ws->dpart = (double*)c; c += b_dpart;
+    ws->level1 = c; c += b_l1;
+    ws->gpart = (double*)c;
+    return MSP_OK;
+}
+
+template <typename T>
+void fill_l2(L2Args<T>& a, const msp_factor_s* f, int64_t n, const Workspace& ws, CtlBlock* ctl) {
+    const int64_t sp = f->s_pad;
+    a.n = n;
+    a.s_pad = sp;
+    a.C = (const T*)f->sk->C;
+    a.W = (const T*)f->W;
+    a.B = (const T*)f->B;
+    a.Bt = (const T*)f->Bt;
+    a.lam_t = (T)f->lam_tilde;
+    a.ctl = ctl;
+    a.part = (T*)ws.part;
+    T* v = (T*)ws.vecs;
+    a.gvec = v;
+    a.uvec = v + sp;
+    a.tvec = v + 2 * sp;
+    a.zvec = v + 3 * sp;
+    a.wdvec = v + 4 * sp;
+    a.dpart = ws.dpart;
+}
+
+// Upper bound on the level-2 grid (2 blocks per SM); launch_level2_pl lowers
+// it to what the occupancy calculator guarantees co-resident. The workspace is
+// sized for the upper bound.
+int level2_grid(msp_ctx* ctx) { return 2 * ctx->num_sms; }
+int gemv_grid(msp_ctx* ctx) { return ctx->num_sms * 8; }
+
+template <typename T>
+msp_status krylov_solve_t(msp_ctx* ctx, const msp_factor_s* f, const void* A, msp_dtype dt,
+                          int64_t n, int64_t lda, double lambda, const T* rhs, T* sol,
+                          double tol_rel, int max_outer, const msp_opts* o, int* iters,
+                          int* inner_iters, ProfSlot* prof) {
+    const int G = level2_grid(ctx), Gg = gemv_grid(ctx);
+    Profiler pr;
+    pr.ctx = ctx;
+    pr.on = (prof != nullptr) && o->profile;
+    if (pr.on) MSP_TRY(msp_profiler_reserve(ctx, 4096));
+    Workspace ws;
+    MSP_TRY(get_workspace<T>(ctx, n, f->s_pad, G, Gg, &ws));
+    T* x = (T*)ws.level1;
+    T* r = x + n;
+    T* q = r + n;
+    T* p = q + n;
+    T* z = p + n;
+    CtlBlock* ctl = (CtlBlock*)ctx->ctl;
+    MSP_CUDA_TRY(ctx, cudaMemsetAsync(ctl, 0, sizeof(CtlBlock), ctx->stream));
+    MSP_CUDA_TRY(ctx, cudaMemsetAsync(x, 0, n * sizeof(T), ctx->stream));
+    MSP_CUDA_TRY(ctx, cudaMemsetAsync(z, 0, n * sizeof(T), ctx->stream));
+    MSP_CUDA_TRY(ctx, cudaMemcpyAsync(r, rhs, n * sizeof(T), cudaMemcpyDeviceToDevice, ctx->stream));
+
+    L2Args<T> a{};
+    fill_l2(a, f, n, ws, ctl);
+    a.tol_rel2 = tol_rel * tol_rel;
+    a.inner_tol2 = o->inner_tol * o->inner_tol;
+    a.max_inner = o->max_inner;
+    a.x = x; a.r = r; a.q = q; a.p = p; a.z = z;
+    a.mode = MODE_INIT;
+    MSP_TRY(launch_level2(ctx, a, G));
+    a.mode = MODE_ITER;
+
+    const bool vec = (lda % (16 / dtype_size(dt)) == 0) &&
+                     ((uintptr_t)A % 16 == 0) && (n % (16 / dtype_size(dt)) == 0);
+    int* hf = (int*)ctx->host_flags;
+    const int check = std::max(1, o->check_every);
+    for (int it = 0; it < max_outer; ++it) {
+        MSP_TRY(pr.begin(0));
+        if (dt == MSP_F32) {
+            if (vec) k_gemv<float, T, true><<<Gg, 256, 0, ctx->stream>>>((const float*)A, lda, n, lambda, p, q, ws.gpart, ctl);
+            else k_gemv<float, T, false><<<Gg, 256, 0, ctx->stream>>>((const float*)A, lda, n, lambda, p, q, ws.gpart, ctl);
+        } else {
+            if (vec) k_gemv<double, T, true><<<Gg, 256, 0, ctx->stream>>>((const double*)A, lda, n, lambda, p, q, ws.gpart, ctl);
+            else k_gemv<double, T, false><<<Gg, 256, 0, ctx->stream>>>((const double*)A, lda, n, lambda, p, q, ws.gpart, ctl);
+        }
+        MSP_CHECK_LAUNCH(ctx);
+        MSP_TRY(pr.end());
+        MSP_TRY(pr.begin(1));
+        MSP_TRY(launch_level2(ctx, a, G));
+        MSP_TRY(pr.end());
+        if ((it + 1) % check == 0 || it + 1 == max_outer) {
+            MSP_CUDA_TRY(ctx, cudaMemcpyAsync(hf, &ctl->done, 5 * sizeof(int),
+                                              cudaMemcpyDeviceToHost, ctx->stream));
+            MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+            if (hf[0] || hf[1]) break;
+        }
+    }
+    MSP_CUDA_TRY(ctx, cudaMemcpyAsync(hf, &ctl->done, 5 * sizeof(int), cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+    MSP_CUDA_TRY(ctx, cudaMemcpyAsync(sol, x, n * sizeof(T), cudaMemcpyDeviceToDevice, ctx->stream));
+    MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    if (pr.on) MSP_TRY(pr.finish(prof, 2));
+    // hf: done, error, iters, inner_iters, pad
+    if (iters) *iters = hf[2];
+    if (inner_iters) *inner_iters = hf[3];
+    if (hf[1]) {
+        const int e = hf[1];
+        return msp_set_error(ctx, (msp_status)e, "level-1 iteration stopped with device status %d%s",
+                             e, e == MSP_ETIMEOUT ? " (grid barrier timed out)" : "");
+    }
+    if (!hf[0]) return msp_set_error(ctx, MSP_ENOCONV, "no convergence in %d level-1 iterations",
+                                     hf[2]);
+    return MSP_OK;
+}
+
+}  // namespace
+
+msp_status msp_krylov_solve(msp_ctx* ctx, const msp_factor_s* f, const void* A, msp_dtype dt,
+                            int64_t n, int64_t lda, double lambda, const void* rhs, void* sol,
+                            double tol_rel, int max_outer, const msp_opts* o, int* iters,
+                            int* inner_iters, ProfSlot* prof) {
+    if (f->dtype == MSP_F32)
+        return krylov_solve_t<float>(ctx, f, A, dt, n, lda, lambda, (const float*)rhs, (float*)sol,
+                                     tol_rel, max_outer, o, iters, inner_iters, prof);
+    return krylov_solve_t<double>(ctx, f, A, dt, n, lda, lambda, (const double*)rhs, (double*)sol,
+                                  tol_rel, max_outer, o, iters, inner_iters, prof);
+}
+
+// ---------------------------------------------------------------- profiler
+
+msp_status msp_profiler_reserve(msp_ctx* ctx, int pairs) {
+    if (ctx->n_events >= 2 * pairs) return MSP_OK;
+    for (int i = 0; i < ctx->n_events; ++i) cudaEventDestroy(ctx->events[i]);
+    delete[] ctx->events;
+    ctx->events = new cudaEvent_t[2 * pairs];
+    ctx->n_events = 0;
+    for (int i = 0; i < 2 * pairs; ++i) {
+        MSP_CUDA_TRY(ctx, cudaEventCreate(&ctx->events[i]));
+        ctx->n_events = i + 1;
+    }
+    return MSP_OK;
+}
+
+msp_status Profiler::begin(int slot) {
+    if (!on) return MSP_OK;
+    if (used >= 4096 || 2 * used + 1 >= ctx->n_events) return MSP_OK;
+    slot_of[used] = slot;
+    MSP_CUDA_TRY(ctx, cudaEventRecord(ctx->events[2 * used], ctx->stream));
+    return MSP_OK;
+}
+
+msp_status Profiler::end() {
+    if (!on) return MSP_OK;
+    if (used >= 4096 || 2 * used + 1 >= ctx->n_events) return MSP_OK;
+    MSP_CUDA_TRY(ctx, cudaEventRecord(ctx->events[2 * used + 1], ctx->stream));
+    ++used;
+    return MSP_OK;
+}
+
+msp_status Profiler::finish(ProfSlot* slots, int nslots) {
+    if (!on) return MSP_OK;
+    MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < used; ++i) {
+        float ms = 0.f;
+        MSP_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->events[2 * i], ctx->events[2 * i + 1]));
+        if (slot_of[i] < nslots) {
+            slots[slot_of[i]].ms += ms;
+            slots[slot_of[i]].launches += 1;
+        }
+    }
+    used = 0;
+    return MSP_OK;
+}
+
+msp_status msp_solve_m1_impl(msp_ctx* ctx, const msp_factor_s* f, const void* r, void* w,
+                             const msp_opts* o, int* inner_iters) {
+    const int64_t n = f->sk->n;
+    const int G = level2_grid(ctx), Gg = gemv_grid(ctx);
+    CtlBlock* ctl = (CtlBlock*)ctx->ctl;
+    MSP_CUDA_TRY(ctx, cudaMemsetAsync(ctl, 0, sizeof(CtlBlock), ctx->stream));
+    int* hf = (int*)ctx->host_flags;
+    if (f->dtype == MSP_F32) {
+        Workspace ws;
+        MSP_TRY(get_workspace<float>(ctx, n, f->s_pad, G, Gg, &ws));
+        L2Args<float> a{};
+        fill_l2(a, f, n, ws, ctl);
+        a.inner_tol2 = o->inner_tol * o->inner_tol;
+        a.max_inner = o->max_inner;
+        a.r = (float*)r;
+        a.z = (float*)w;
+        a.mode = MODE_APPLY;
+        MSP_TRY(launch_level2(ctx, a, G));
+    } else {
+        Workspace ws;
+        MSP_TRY(get_workspace<double>(ctx, n, f->s_pad, G, Gg, &ws));
+        L2Args<double> a{};
+        fill_l2(a, f, n, ws, ctl);
+        a.inner_tol2 = o->inner_tol * o->inner_tol;
+        a.max_inner = o->max_inner;
+        a.r = (double*)r;
+        a.z = (double*)w;
+        a.mode = MODE_APPLY;
+        MSP_TRY(launch_level2(ctx, a, G));
+    }
+    MSP_CUDA_TRY(ctx, cudaMemcpyAsync(hf, &ctl->done, 5 * sizeof(int), cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+    MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    if (inner_iters) *inner_iters = hf[3];
+    if (hf[1]) return msp_set_error(ctx, (msp_status)hf[1], "SolveM1: device status %d", hf[1]);
+    return MSP_OK;
+}
+
+msp_status msp_matvec64(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t n, int64_t lda,
+                        double lambda, const double* x, const double* b, double* out,
+                        double* norm2_out_dev) {
+    const int Gg = gemv_grid(ctx);
+    void* scr = nullptr;
+    MSP_TRY(msp_scratch(ctx, (size_t)Gg * 8 + 256, &scr));
+    CtlBlock* ctl = (CtlBlock*)ctx->ctl;
+    if (dt == MSP_F32)
+        k_matvec64<float><<<Gg, 256, 0, ctx->stream>>>((const float*)A, lda, n, lambda, x, b, out,
+                                                       (double*)scr, &ctl->last_block_counter,
+                                                       norm2_out_dev);
+    else
+        k_matvec64<double><<<Gg, 256, 0, ctx->stream>>>((const double*)A, lda, n, lambda, x, b, out,
+                                                        (double*)scr, &ctl->last_block_counter,
+                                                        norm2_out_dev);
+    MSP_CHECK_LAUNCH(ctx);
+    return MSP_OK;
+}
+
+// ------------------------------------------------------------ vector ops
+
+namespace {
+
+// |v|^2 of an FP64 vector, one block, fixed order.
+__global__ void k_norm2(const double* __restrict__ v, int64_t n, double* __restrict__ out) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc += v[i] * v[i];
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) *out = acc;
+}
+
+// dst = (T)(src / sqrt(*nrm2)) (0 if the norm is 0)
+template <typename T>
+__global__ void k_scale_cast(const double* __restrict__ src, const double* __restrict__ nrm2,
+                             int64_t n, T* __restrict__ dst) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = *nrm2 > 0.0 ? 1.0 / sqrt(*nrm2) : 0.0;
+    dst[i] = (T)(src[i] * s);
+}
+
+// x (+)= sqrt(*nrm2) * (double)d
+template <typename T>
+__global__ void k_axpy_back(double* __restrict__ x, const T* __restrict__ d,
+                            const double* __restrict__ nrm2, int64_t n, int accumulate) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v = sqrt(*nrm2) * (double)d[i];
+    x[i] = accumulate ? x[i] + v : v;
+}
+
+}  // namespace
+
+msp_status msp_norm2(msp_ctx* ctx, const double* v, int64_t n, double* out_dev) {
+    k_norm2<<<1, 1024, 0, ctx->stream>>>(v, n, out_dev);
+    MSP_CHECK_LAUNCH(ctx);
+    return MSP_OK;
+}
+
+msp_status msp_scale_cast(msp_ctx* ctx, const double* src, const double* nrm2, int64_t n,
+                          msp_dtype dt, void* dst) {
+    unsigned g = (unsigned)((n + 255) / 256);
+    if (dt == MSP_F32) k_scale_cast<float><<<g, 256, 0, ctx->stream>>>(src, nrm2, n, (float*)dst);
+    else k_scale_cast<double><<<g, 256, 0, ctx->stream>>>(src, nrm2, n, (double*)dst);
+    MSP_CHECK_LAUNCH(ctx);
+    return MSP_OK;
+}
+
+msp_status msp_axpy_back(msp_ctx* ctx, double* x, const void* d, msp_dtype dt, const double* nrm2,
+                         int64_t n, int accumulate) {
+    unsigned g = (unsigned)((n + 255) / 256);
+    if (dt == MSP_F32) k_axpy_back<float><<<g, 256, 0, ctx->stream>>>(x, (const float*)d, nrm2, n, accumulate);
+    else k_axpy_back<double><<<g, 256, 0, ctx->stream>>>(x, (const double*)d, nrm2, n, accumulate);
+    MSP_CHECK_LAUNCH(ctx);
+    return MSP_OK;
+}

@@ -1,0 +1,259 @@
+// Internal declarations shared by the CUDA translation units of libmsp.
+// Nothing here is part of the public ABI (include/msp.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "msp.h"
+
+#define MSP_MAX_GAMMA 64
+#define MSP_MAX_S 2048
+#define MSP_S_ALIGN 128
+
+// ------------------------------------------------------------------ handles
+
+struct msp_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    std::string last_error;
+    // device control block: barrier words, flags, scalars (see CtlBlock)
+    void* ctl = nullptr;
+    // pinned host mirror for flag reads
+    void* host_flags = nullptr;
+    // grow-only scratch for solves and staging of host arguments
+    void* scratch = nullptr;
+    size_t scratch_bytes = 0;
+    void* stage = nullptr;       // device staging for host A / b / x
+    size_t stage_bytes = 0;
+    int64_t launches = 0;        // kernels launched by this context
+    // CUDA-event pool for opts.profile (pairs), created lazily
+    cudaEvent_t* events = nullptr;
+    int n_events = 0;
+};
+
+// Launch accounting / optional event timing of one launch site class.
+struct ProfSlot {
+    double ms = 0.0;
+    int launches = 0;
+};
+
+struct msp_sketch_s {
+    int64_t n = 0, s = 0, s_pad = 0;
+    int gamma = 0;
+    msp_dtype dtype = MSP_F32;
+    uint64_t seed = 0;
+    cudaStream_t stream = nullptr;   // stream of the creating context (frees)
+    int32_t* idx = nullptr;      // n x gamma, columns of Pi per row (sorted)
+    int8_t* sgn = nullptr;       // n x gamma
+    int32_t* csr_ptr = nullptr;  // s_pad + 1, Pi^T rows (= sketch columns)
+    int32_t* csr_ent = nullptr;  // n*gamma entries (j << 1) | negative
+    void* C = nullptr;           // n x s_pad, dtype
+};
+
+struct msp_factor_s {
+    const msp_sketch_s* sk = nullptr;
+    int64_t s = 0, s_pad = 0, phi = 0;
+    double lambda = 0, lambda0 = 0, lam_tilde = 0, shift = 0;
+    int retries = 0;
+    msp_dtype dtype = MSP_F32;
+    cudaStream_t stream = nullptr;
+    void* W = nullptr;          // s_pad x s_pad, dtype (working copy)
+    void* B = nullptr;          // L^{-1}, s_pad x s_pad, dtype (lower)
+    void* Bt = nullptr;         // (L^{-1})^T, dtype (upper)
+    double* W64 = nullptr;      // s_pad x s_pad
+    double* M2 = nullptr;       // s_pad x s_pad, before shift
+    double* Linv64 = nullptr;   // s_pad x s_pad
+};
+
+// Device control block layout (one per context).
+struct CtlBlock {
+    unsigned int bar_count;
+    unsigned int bar_gen;
+    unsigned int last_block_counter;
+    int done;           // level-1 solve converged
+    int error;          // msp_status-like error code set on device
+    int iters;          // level-1 iterations completed
+    int inner_iters;    // level-2 iterations accumulated
+    int pad0;
+    double alpha;       // level-1 step
+    double rz;          // r^T z of the level-1 iteration
+    double rr;          // |r|^2
+    double bb;          // |rhs|^2
+    double tol2;        // tol^2 |rhs|^2
+    double pq;
+    double beta;
+    double scratch[8];
+};
+
+// ------------------------------------------------------------------ errors
+
+msp_status msp_set_error(msp_ctx* ctx, msp_status st, const char* fmt, ...);
+
+#define MSP_CUDA_TRY(ctx, call)                                                  \
+    do {                                                                         \
+        cudaError_t _e = (call);                                                 \
+        if (_e != cudaSuccess) {                                                 \
+            return msp_set_error((ctx), _e == cudaErrorMemoryAllocation          \
+                                            ? MSP_ENOMEM : MSP_ECUDA,            \
+                                 "%s:%d: %s: %s", __FILE__, __LINE__, #call,     \
+                                 cudaGetErrorString(_e));                        \
+        }                                                                        \
+    } while (0)
+
+#define MSP_TRY(expr)                                                            \
+    do {                                                                         \
+        msp_status _s = (expr);                                                  \
+        if (_s != MSP_OK) return _s;                                             \
+    } while (0)
+
+#define MSP_CHECK_LAUNCH(ctx)                                                    \
+    do {                                                                         \
+        ++(ctx)->launches;                                                       \
+        MSP_CUDA_TRY(ctx, cudaGetLastError());                                   \
+    } while (0)
+
+// ------------------------------------------------------------------ memory
+
+msp_status msp_alloc(msp_ctx* ctx, void** p, size_t bytes);
+void msp_free(void* p);
+msp_status msp_scratch(msp_ctx* ctx, size_t bytes, void** out);
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+inline size_t dtype_size(msp_dtype t) { return t == MSP_F64 ? 8 : 4; }
+
+// ------------------------------------------------------ device primitives
+
+namespace msp {
+
+// SplitMix64 finaliser and the counter-based draw described in msp.h.
+__host__ __device__ inline uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__host__ __device__ inline uint64_t draw(uint64_t seed, uint32_t stream, uint64_t row,
+                                         uint32_t q) {
+    uint64_t k = ((uint64_t)stream << 56) | (row << 8) | (uint64_t)q;
+    return mix64(seed + (k + 1ull) * 0x9E3779B97F4A7C15ull);
+}
+
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ inline float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ inline uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wall-clock limit of every device-side wait (ns).
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+// Grid-wide barrier for a cooperative (co-resident) launch. Sense via a
+// generation counter; bounded in wall-clock time: on timeout it records
+// MSP_ETIMEOUT in *err and returns false. All blocks must call it equally
+// often. Uses acquire/release atomics at device scope.
+__device__ inline bool grid_barrier(unsigned int* count, unsigned int* gen, int* err) {
+    __syncthreads();
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        unsigned int g;
+        __threadfence();
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(gen) : "memory");
+        unsigned int arrived;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
+                     : "=r"(arrived) : "l"(count) : "memory");
+        if (arrived == gridDim.x * gridDim.y * gridDim.z - 1) {
+            asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" :: "l"(count) : "memory");
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(gen) : "memory");
+        } else {
+            uint64_t t0 = globaltimer_ns();
+            unsigned int cur;
+            int spins = 0;
+            while (true) {
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(gen) : "memory");
+                if (cur != g) break;
+                if (++spins > 64) {
+                    __nanosleep(40);
+                    if ((spins & 255) == 0 && globaltimer_ns() - t0 > kWaitLimitNs) {
+                        atomicExch(err, (int)MSP_ETIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+}  // namespace msp
+
+// ------------------------------------------------- cross-unit entry points
+
+// sketch.cu
+msp_status msp_pattern_launch(msp_ctx* ctx, int64_t n, int64_t rows, int gamma,
+                              uint64_t seed, int stream, int32_t* idx, int8_t* sgn,
+                              int32_t* counts);
+msp_status msp_build_csr(msp_ctx* ctx, int64_t n, int64_t rows, int gamma,
+                         const int32_t* idx, const int8_t* sgn, int32_t* ptr,
+                         int32_t* ent);
+msp_status msp_sketch_apply(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t n,
+                            int64_t lda, int64_t s_pad, const int32_t* ptr,
+                            const int32_t* ent, int gamma, void* C);
+msp_status msp_gather_rows(msp_ctx* ctx, msp_dtype dt, int64_t rows_out, int64_t width,
+                           const int32_t* ptr, const int32_t* ent, const void* in,
+                           int64_t ld_in, double scale, void* out, int64_t ld_out);
+
+// factor.cu
+msp_status msp_build_factor(msp_ctx* ctx, msp_factor_s* f, const void* Ct, int64_t phi_rows);
+
+// krylov.cu
+// prof: null, or two slots (A-pass GEMV, level-2 kernel) to accumulate
+// event-timed durations into (opts->profile).
+msp_status msp_krylov_solve(msp_ctx* ctx, const msp_factor_s* f, const void* A,
+                            msp_dtype dt, int64_t n, int64_t lda, double lambda,
+                            const void* rhs, void* sol, double tol_rel, int max_outer,
+                            const msp_opts* o, int* iters, int* inner_iters,
+                            ProfSlot* prof);
+msp_status msp_matvec64(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t n,
+                        int64_t lda, double lambda, const double* x, const double* b,
+                        double* out, double* norm2_out_dev);
+
+// Event timing helper: with `on`, records an event pair around each timed
+// launch; finish() sums the elapsed times (after a stream sync).
+struct Profiler {
+    msp_ctx* ctx = nullptr;
+    bool on = false;
+    int used = 0;
+    int slot_of[4096];
+    msp_status begin(int slot);
+    msp_status end();
+    msp_status finish(ProfSlot* slots, int nslots);
+};
+msp_status msp_profiler_reserve(msp_ctx* ctx, int pairs);
+msp_status msp_norm2(msp_ctx* ctx, const double* v, int64_t n, double* out_dev);
+msp_status msp_scale_cast(msp_ctx* ctx, const double* src, const double* nrm2, int64_t n,
+                          msp_dtype dt, void* dst);
+msp_status msp_axpy_back(msp_ctx* ctx, double* x, const void* d, msp_dtype dt, const double* nrm2,
+                         int64_t n, int accumulate);
+msp_status msp_solve_m1_impl(msp_ctx* ctx, const msp_factor_s* f, const void* r, void* w,
+                             const msp_opts* o, int* inner_iters);

@@ -1,0 +1,321 @@
+// Sparse sketches of Algorithm 1 on sm_103a:
+//   * the pattern of a sparse embedding (Definition 2.1),
+//   * its transpose as CSR (the list of (j, sign) per sketch column c),
+//   * C = A Pi (Pi = S^T): one pass over A, gathering each output column's
+//     ~n*gamma/s source columns from a shared-memory tile of A,
+//   * row gathers out[r,:] = scale * sum_{(j,sign) in list(r)} sign * in[j,:],
+//     which give W = Pi^T C = S C and C~ = Phi C.
+#include "msp_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace {
+
+// ---------------------------------------------------------------- pattern
+
+// One thread per column j of the embedding (row j of Pi). Floyd's sampling:
+// for q = 0..gamma-1, t = rows - gamma + q, r = mulhi(u_q, t + 1) in [0, t];
+// keep r unless already chosen, else keep t. Then sort ascending and draw the
+// sign of the q-th smallest from the top bit of draw(stream + 1, j, q).
+__global__ void k_pattern(int64_t n, int rows, int gamma, uint64_t seed, int stream,
+                          int32_t* __restrict__ idx, int8_t* __restrict__ sgn,
+                          int32_t* __restrict__ counts) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    int c[MSP_MAX_GAMMA];
+    for (int q = 0; q < gamma; ++q) {
+        uint64_t t = (uint64_t)(rows - gamma + q);
+        uint64_t u = msp::draw(seed, (uint32_t)stream, (uint64_t)j, (uint32_t)q);
+        int r = (int)__umul64hi(u, t + 1ull);
+        bool seen = false;
+        for (int k = 0; k < q; ++k) seen |= (c[k] == r);
+        c[q] = seen ? (int)t : r;
+    }
+    for (int a = 1; a < gamma; ++a) {          // insertion sort, gamma <= 64
+        int v = c[a], b = a - 1;
+        while (b >= 0 && c[b] > v) { c[b + 1] = c[b]; --b; }
+        c[b + 1] = v;
+    }
+    for (int q = 0; q < gamma; ++q) {
+        uint64_t u = msp::draw(seed, (uint32_t)(stream + 1), (uint64_t)j, (uint32_t)q);
+        idx[j * gamma + q] = c[q];
+        sgn[j * gamma + q] = (u >> 63) ? (int8_t)-1 : (int8_t)1;
+        if (counts) atomicAdd(&counts[c[q]], 1);
+    }
+}
+
+// counts[c] = number of pattern entries equal to c
+__global__ void k_hist(int64_t m, const int32_t* __restrict__ idx, int32_t* __restrict__ counts) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) atomicAdd(&counts[idx[i]], 1);
+}
+
+// Exclusive scan of counts[0..m) into ptr[0..m], single block.
+__global__ void k_scan(const int32_t* __restrict__ counts, int64_t m, int32_t* __restrict__ ptr) {
+    __shared__ int32_t warp_tot[32];
+    __shared__ int32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t base = 0; base < m; base += blockDim.x) {
+        int64_t i = base + threadIdx.x;
+        int32_t v = i < m ? counts[i] : 0;
+        int32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int32_t t = lane < nw ? warp_tot[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int32_t y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            if (lane < nw) warp_tot[lane] = t;   // inclusive over warps
+        }
+        __syncthreads();
+        int32_t before = carry + (wid > 0 ? warp_tot[wid - 1] : 0) + x - v;
+        if (i < m) ptr[i] = before;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = before + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) ptr[m] = carry;
+}
+
+// Scatter (j, sign) into each row's bucket (order made canonical below).
+__global__ void k_fill(int64_t n, int gamma, const int32_t* __restrict__ idx,
+                       const int8_t* __restrict__ sgn, const int32_t* __restrict__ ptr,
+                       int32_t* __restrict__ cursor, int32_t* __restrict__ ent) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    for (int q = 0; q < gamma; ++q) {
+        int c = idx[j * gamma + q];
+        int pos = ptr[c] + atomicAdd(&cursor[c], 1);
+        ent[pos] = (int32_t)((j << 1) | (sgn[j * gamma + q] < 0 ? 1 : 0));
+    }
+}
+
+// Sort every bucket by j (entries in a bucket have distinct j): warp per
+// bucket, each entry placed at its rank. Reads `in`, writes `out`.
+__global__ void k_sort_buckets(int64_t m, const int32_t* __restrict__ ptr,
+                               const int32_t* __restrict__ in, int32_t* __restrict__ out) {
+    int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (b >= m) return;
+    int lo = ptr[b], hi = ptr[b + 1];
+    for (int e = lo + lane; e < hi; e += 32) {
+        int32_t v = in[e];
+        int32_t jv = v >> 1;
+        int rank = 0;
+        for (int k = lo; k < hi; ++k) rank += ((in[k] >> 1) < jv);
+        out[lo + rank] = v;
+    }
+}
+
+// ------------------------------------------------------------ C = A Pi
+
+// Block: R rows of A x all s_pad outputs. Thread t owns output columns
+// c = t + k*blockDim.x (k < NC) for the R rows (NC*R accumulators). A is
+// streamed in chunks of J columns into shared memory transposed to
+// tile[jj][0..R) so that one list entry (j, sign) costs R/4 vector loads.
+// Each thread walks its columns' sorted lists with a cursor per column.
+template <typename T, int R, int NC>
+__global__ void __launch_bounds__(512, 1) k_sketch_apply(
+    const T* __restrict__ A, int64_t lda, int64_t n, int64_t s_pad,
+    const int32_t* __restrict__ ptr, const int32_t* __restrict__ ent, T scale,
+    T* __restrict__ C, int J) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* tile = reinterpret_cast<T*>(smem_raw);    // J x R
+    const int64_t i0 = (int64_t)blockIdx.x * R;
+    const int nthr = blockDim.x;
+    T acc[NC][R];
+    int cur[NC], end[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        int c = threadIdx.x + k * nthr;
+        cur[k] = ptr[c];
+        end[k] = ptr[c + 1];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[k][r] = T(0);
+    }
+    for (int64_t j0 = 0; j0 < n; j0 += J) {
+        const int jlen = (int)min((int64_t)J, n - j0);
+        __syncthreads();
+        // load: thread handles column jj, all R rows (coalesced along jj)
+        for (int jj = threadIdx.x; jj < jlen; jj += nthr) {
+            T v[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                v[r] = (i0 + r < n) ? __ldcs(&A[(i0 + r) * lda + j0 + jj]) : T(0);
+#pragma unroll
+            for (int r = 0; r < R; ++r) tile[(int64_t)jj * R + r] = v[r];
+        }
+        __syncthreads();
+        const int32_t jend = (int32_t)(j0 + jlen);
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            int e = cur[k];
+            const int ee = end[k];
+            while (e < ee) {
+                int32_t v = __ldg(&ent[e]);
+                int32_t j = v >> 1;
+                if (j >= jend) break;
+                const T* src = tile + (int64_t)(j - j0) * R;
+                if (v & 1) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) acc[k][r] -= src[r];
+                } else {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) acc[k][r] += src[r];
+                }
+                ++e;
+            }
+            cur[k] = e;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        int c = threadIdx.x + k * nthr;
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+            if (i0 + r < n) C[(i0 + r) * s_pad + c] = acc[k][r] * scale;
+    }
+}
+
+template <typename T, int R>
+msp_status launch_sketch_apply_r(msp_ctx* ctx, const T* A, int64_t lda, int64_t n,
+                                 int64_t s_pad, const int32_t* ptr, const int32_t* ent,
+                                 T scale, T* C) {
+    // s_pad is a multiple of 128: the smallest NC in {1, 2, 4} with
+    // s_pad / NC <= 512 threads gives a whole number of warps per block.
+    int nc = 1;
+    while (s_pad / nc > 512) nc *= 2;
+    const int threads = (int)(s_pad / nc);
+    if (nc > 4 || threads * nc != s_pad || threads % 32 != 0)
+        return msp_set_error(ctx, MSP_EINVAL, "sketch: unsupported s_pad %lld", (long long)s_pad);
+    const int J = (int)((64 * 1024) / (sizeof(T) * R));
+    size_t smem = (size_t)J * R * sizeof(T);
+    dim3 grid((unsigned)((n + R - 1) / R));
+#define MSP_SK_CASE(NCV)                                                              \
+    case NCV: {                                                                       \
+        auto kern = k_sketch_apply<T, R, NCV>;                                        \
+        MSP_CUDA_TRY(ctx, cudaFuncSetAttribute(kern,                                  \
+                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));        \
+        kern<<<grid, threads, smem, ctx->stream>>>(A, lda, n, s_pad, ptr, ent, scale, \
+                                                  C, J);                              \
+        break;                                                                        \
+    }
+    switch (nc) {
+        MSP_SK_CASE(1)
+        MSP_SK_CASE(2)
+        MSP_SK_CASE(4)
+        default:
+            return msp_set_error(ctx, MSP_EINVAL, "sketch: unsupported s_pad %lld",
+                                 (long long)s_pad);
+    }
+#undef MSP_SK_CASE
+    MSP_CHECK_LAUNCH(ctx);
+    return MSP_OK;
+}
+
+// ------------------------------------------------------------ row gathers
+
+// out[r, c] = scale * sum_{(j,neg) in list(r)} (+-) in[j, c]; block per output
+// row, threads over columns.
+template <typename T>
+__global__ void k_gather_rows(int64_t rows_out, int64_t width, const int32_t* __restrict__ ptr,
+                              const int32_t* __restrict__ ent, const T* __restrict__ in,
+                              int64_t ld_in, T scale, T* __restrict__ out, int64_t ld_out) {
+    int64_t r = blockIdx.x;
+    if (r >= rows_out) return;
+    const int lo = ptr[r], hi = ptr[r + 1];
+    for (int64_t c = threadIdx.x; c < width; c += blockDim.x) {
+        T acc = T(0);
+        for (int e = lo; e < hi; ++e) {
+            int32_t v = __ldg(&ent[e]);
+            T a = in[(int64_t)(v >> 1) * ld_in + c];
+            acc += (v & 1) ? -a : a;
+        }
+        out[r * ld_out + c] = acc * scale;
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- host side
+
+msp_status msp_pattern_launch(msp_ctx* ctx, int64_t n, int64_t rows, int gamma,
+                              uint64_t seed, int stream, int32_t* idx, int8_t* sgn,
+                              int32_t* counts) {
+    if (n <= 0 || rows <= 0 || gamma < 1 || gamma > MSP_MAX_GAMMA || gamma > rows ||
+        n >= (1ll << 30) || rows >= (1ll << 30) || stream < 0 || stream > 254)
+        return msp_set_error(ctx, MSP_EINVAL,
+                             "pattern: need 1 <= gamma <= min(rows, %d), n, rows < 2^30",
+                             MSP_MAX_GAMMA);
+    int threads = 256;
+    k_pattern<<<(unsigned)((n + threads - 1) / threads), threads, 0, ctx->stream>>>(
+        n, (int)rows, gamma, seed, stream, idx, sgn, counts);
+    MSP_CHECK_LAUNCH(ctx);
+    return MSP_OK;
+}
+
+msp_status msp_build_csr(msp_ctx* ctx, int64_t n, int64_t rows, int gamma,
+                         const int32_t* idx, const int8_t* sgn, int32_t* ptr,
+                         int32_t* ent) {
+    // counts, cursor and an unsorted copy of the entries live in scratch
+    size_t need = (size_t)rows * 4 * 2 + (size_t)n * gamma * 4;
+    void* scr = nullptr;
+    MSP_TRY(msp_scratch(ctx, need, &scr));
+    int32_t* counts = (int32_t*)scr;
+    int32_t* cursor = counts + rows;
+    int32_t* tmp = cursor + rows;
+    MSP_CUDA_TRY(ctx, cudaMemsetAsync(counts, 0, (size_t)rows * 8, ctx->stream));
+    {
+        const int threads = 256;
+        int64_t m = n * gamma;
+        k_hist<<<(unsigned)((m + threads - 1) / threads), threads, 0, ctx->stream>>>(m, idx, counts);
+        MSP_CHECK_LAUNCH(ctx);
+    }
+    k_scan<<<1, 1024, 0, ctx->stream>>>(counts, rows, ptr);
+    MSP_CHECK_LAUNCH(ctx);
+    k_fill<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, gamma, idx, sgn, ptr,
+                                                                  cursor, tmp);
+    MSP_CHECK_LAUNCH(ctx);
+    int64_t warps = rows;
+    k_sort_buckets<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, ctx->stream>>>(rows, ptr,
+                                                                                  tmp, ent);
+    MSP_CHECK_LAUNCH(ctx);
+    return MSP_OK;
+}
+
+msp_status msp_sketch_apply(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t n,
+                            int64_t lda, int64_t s_pad, const int32_t* ptr,
+                            const int32_t* ent, int gamma, void* C) {
+    // accumulators per thread: R rows x NC (<= 4) columns, kept <= 64 registers
+    double scale = 1.0 / sqrt((double)gamma);
+    if (dt == MSP_F32)
+        return launch_sketch_apply_r<float, 16>(ctx, (const float*)A, lda, n, s_pad, ptr, ent,
+                                                (float)scale, (float*)C);
+    return launch_sketch_apply_r<double, 8>(ctx, (const double*)A, lda, n, s_pad, ptr, ent,
+                                            scale, (double*)C);
+}
+
+msp_status msp_gather_rows(msp_ctx* ctx, msp_dtype dt, int64_t rows_out, int64_t width,
+                           const int32_t* ptr, const int32_t* ent, const void* in,
+                           int64_t ld_in, double scale, void* out, int64_t ld_out) {
+    int threads = (int)std::min<int64_t>(1024, round_up(width, 32));
+    if (dt == MSP_F32)
+        k_gather_rows<float><<<(unsigned)rows_out, threads, 0, ctx->stream>>>(
+            rows_out, width, ptr, ent, (const float*)in, ld_in, (float)scale, (float*)out, ld_out);
+    else
+        k_gather_rows<double><<<(unsigned)rows_out, threads, 0, ctx->stream>>>(
+            rows_out, width, ptr, ent, (const double*)in, ld_in, scale, (double*)out, ld_out);
+    MSP_CHECK_LAUNCH(ctx);
+    return MSP_OK;
+}
