@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--phi-mult", type=int, default=4)
     ap.add_argument("--inner-tol", type=float, default=1e-6)
     ap.add_argument("--refine-tol", type=float, default=1e-6)
+    ap.add_argument("--max-inner", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -237,7 +238,7 @@ def run_msp(args, rank, world, local):
         sk = ctx.sketch(A, s, 8, SEED)
         f = ctx.nystrom(sk, lam, 0.0, phi=phi, gamma_phi=8, seed=SEED)
         x, info = ctx.solve(f, A, bd, lam, precision=prec, tol=tol, inner_tol=args.inner_tol,
-                            refine_tol=args.refine_tol, profile=profile)
+                            refine_tol=args.refine_tol, max_inner=args.max_inner, profile=profile)
         f.close()
         sk.close()
         return x, info
@@ -294,7 +295,9 @@ def run_msp(args, rank, world, local):
     l2_ms = sum(i["level2_ms"] for i in infos)
     r_ms = sum(i["resid_ms"] for i in infos)
     avg_ms = g_ms / max(1, g_n)
-    alg_bytes = 4.0 * n * n + 3 * 4.0 * n           # A (FP32) + p read + q write
+    # symmetric A: the distinct entries n(n+1)/2 in FP32, read once per pass,
+    # plus p (read) and the q partials (written and read back): algorithmic bytes
+    alg_bytes = 4.0 * n * (n + 1) / 2 + 3 * 4.0 * n
     achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
     peak, peak_src = measured_peaks()
     traffic = gemv_traffic_bytes(n)
@@ -344,7 +347,7 @@ def run_msp(args, rank, world, local):
            "fp32_plain": fp32,
            "phase_ms_per_step": {"a_pass": g_ms / args.steps, "level2": l2_ms / args.steps,
                                  "fp64_residual": r_ms / args.steps},
-           "roofline": {"bound": "hbm", "kernel": "k_gemv (q = (A + lam I) p)",
+           "roofline": {"bound": "hbm", "kernel": "k_symv_packed (q = (A + lam I) p, packed upper tiles)",
                         "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
                         "alg_bytes_per_launch": alg_bytes, "avg_launch_us": avg_ms * 1e3,

@@ -93,7 +93,10 @@ typedef struct {
                              residual refine_tol. Default 1e-6.                  */
     double inner_tol;     /* level-2 (SolveM1) solve stops at
                              |res| <= inner_tol |C^T r|. Default 1e-6.           */
-    int max_inner;        /* cap on level-2 iterations per SolveM1. 50.          */
+    int max_inner;        /* cap on level-2 iterations per SolveM1. 50.
+                             0 selects the direct level 2: y = M2^{-1} C^T r with
+                             no correction steps, exact when M2 is the level-2
+                             operator itself (phi = 0, Phi = I).                 */
     int precision;        /* msp_precision. Default MSP_PREC_MIXED.              */
     int check_every;      /* level-1 iterations between host checks of the
                              device-side convergence flag. Default 8.            */
@@ -146,7 +149,7 @@ MSP_API int64_t msp_launch_count(const msp_ctx* ctx);
  * Draws: counter-based SplitMix64 (Steele, Lea, Flood 2014) with counter
  * (stream << 56) | (j << 8) | q, Floyd's sampling, sign from the top bit of
  * the draw on stream+1. stream 0 is S, stream 2 is Phi.
- * Requires 1 <= gamma <= min(rows, 255), n < 2^31, rows < 2^31.
+ * Requires 1 <= gamma <= min(rows, 64), n < 2^30, rows < 2^30.
  * idx, sgn: device arrays of n*gamma elements, caller-owned. */
 MSP_API msp_status msp_sketch_pattern(msp_ctx* ctx, int64_t n, int64_t rows, int gamma,
                               uint64_t seed, int stream, int32_t* idx, int8_t* sgn);
@@ -158,7 +161,7 @@ MSP_API msp_status msp_sketch_pattern(msp_ctx* ctx, int64_t n, int64_t rows, int
  * A: device, n x n, leading dimension lda >= n, dtype MSP_F32 or MSP_F64.
  * The C of the handle has the dtype of A. s is padded internally to a
  * multiple of 128 with zero columns (sizes reported by msp_sketch_info).
- * Requires 1 <= gamma <= min(s, 255), 16 <= s <= 4096, s <= n. */
+ * Requires 1 <= gamma <= min(s, 64), 16 <= s <= 1024, s <= n. */
 MSP_API msp_status msp_sketch(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n,
                       int64_t lda, int64_t s, int gamma, uint64_t seed,
                       msp_sketch_t** out);

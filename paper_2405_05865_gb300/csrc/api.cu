@@ -177,7 +177,8 @@ msp_status msp_sketch_pattern(msp_ctx* ctx, int64_t n, int64_t rows, int gamma, 
 
 void msp_sketch_destroy(msp_sketch_t* sk) {
     if (!sk) return;
-    for (void* p : {(void*)sk->idx, (void*)sk->sgn, (void*)sk->csr_ptr, (void*)sk->csr_ent, sk->C})
+    for (void* p : {(void*)sk->idx, (void*)sk->sgn, (void*)sk->csr_ptr, (void*)sk->csr_ent, sk->C,
+                    (void*)sk->packed})
         if (p) cudaFreeAsync(p, sk->stream);
     delete sk;
 }
@@ -212,11 +213,16 @@ static msp_status sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int6
         (st = msp_build_csr(ctx, n, sp, gamma, sk->idx, sk->sgn, sk->csr_ptr, sk->csr_ent)) !=
             MSP_OK ||
         (st = msp_sketch_apply(ctx, A, dtype, n, lda, sp, sk->csr_ptr, sk->csr_ent, gamma,
-                               sk->C)) != MSP_OK) {
+                               sk->C)) != MSP_OK ||
+        (dtype == MSP_F32 &&
+         ((st = msp_alloc(ctx, (void**)&sk->packed, (size_t)msp_packed_tiles(n) * 128 * 128 * 4)) !=
+              MSP_OK ||
+          (st = msp_pack_upper(ctx, (const float*)A, lda, n, sk->packed)) != MSP_OK))) {
         cudaStreamSynchronize(ctx->stream);
         msp_sketch_destroy(sk);
         return st;
     }
+    sk->A_src = A;
     *out = sk;
     return MSP_OK;
 }
@@ -384,10 +390,13 @@ static msp_status solve_impl(msp_ctx* ctx, const msp_factor_s* f, const void* A,
     } else {
         return msp_set_error(ctx, MSP_EINVAL, "solve: unknown precision %d", prec);
     }
-    if (!(o->tol > 0.0) || o->max_outer < 1 || o->max_inner < 1 || o->max_refine < 0)
+    if (!(o->tol > 0.0) || o->max_outer < 1 || o->max_inner < 0 || o->max_refine < 0)
         return msp_set_error(ctx, MSP_EINVAL, "solve: bad options");
     const msp_dtype wt = f->dtype;
     const size_t ts = dtype_size(wt);
+    // the sketch's packed upper tiles stand in for A when A is the sketched matrix
+    const float* packed = (dtype == MSP_F32 && f->sk->packed && A == f->sk->A_src)
+                              ? f->sk->packed : nullptr;
     // per-solve buffers: r64 (n), rhs_w (n), sol_w (n), scalars
     void* mem = nullptr;
     size_t b_r = round_up(n * 8, 256), b_w = round_up(n * ts, 256);
@@ -463,7 +472,7 @@ static msp_status solve_impl(msp_ctx* ctx, const msp_factor_s* f, const void* A,
         if ((st = msp_scale_cast(ctx, r64, scal + 1, n, wt, rhs_w)) != MSP_OK) return finish(st);
         int it = 0, in = 0;
         kst = msp_krylov_solve(ctx, f, A, dtype, n, lda, lambda, rhs_w, sol_w, step_tol,
-                               o->max_outer, o, &it, &in, pr.on ? slots : nullptr);
+                               o->max_outer, o, &it, &in, pr.on ? slots : nullptr, packed);
         outer_total += it;
         inner_total += in;
         if (kst != MSP_OK && kst != MSP_ENOCONV) return finish(kst);

@@ -21,54 +21,111 @@ namespace {
 // ----------------------------------------------------------- Gram (SIMT)
 
 // M2[a][b] = sum_k Ct[k][a] Ct[k][b] + lam_t * W[a][b], FP64 output; pad rows
-// (a >= s or b >= s) get the identity. 64 x 64 output tile, 256 threads each
-// 4 x 4, K chunks of 16. Accumulates in TA (FP32 for FP32 data).
+// (a >= s or b >= s) get the identity. One 64 x 64 tile of the upper
+// triangle per block (mirrored), 256 threads each 4 x 4 outputs, K chunks of
+// 16 from shared memory. Each chunk is summed in TA, then added into an
+// (hi, lo) pair with Knuth's TwoSum (compensated summation), so the
+// accumulated rounding error does not grow with K (K = n when Phi = I).
 template <typename TA>
-__global__ void __launch_bounds__(256) k_gram(const TA* __restrict__ Ct, int64_t K,
-                                             int64_t ld, const TA* __restrict__ W,
-                                             double lam_t, int64_t s, int64_t s_pad,
-                                             double* __restrict__ M2) {
-    __shared__ TA As[16][64 + 4];
-    __shared__ TA Bs[16][64 + 4];
-    const int a0 = blockIdx.y * 64, b0 = blockIdx.x * 64;
+__device__ inline void two_sum_add(TA& hi, TA& lo, TA v) {
+    TA s = hi + v;
+    TA bp = s - hi;
+    TA err = (hi - (s - bp)) + (v - bp);
+    hi = s;
+    lo += err;
+}
+
+constexpr int kGramSlices = 4;   // split-K slices of the Gram (combined in FP64)
+
+// Partial Gram of one K slice: P[slice][a][b] = sum_{k in slice} Ct[k][a] Ct[k][b]
+// for the upper-triangular 64 x 64 tile pairs (mirrored), FP64 output (hi + lo).
+// blockIdx.x = tile pair, blockIdx.y = K slice.
+template <typename TA>
+__global__ void __launch_bounds__(256, 4) k_gram(const TA* __restrict__ Ct, int64_t K, int64_t ld,
+                                                int64_t s_pad, double* __restrict__ P) {
+    __shared__ __align__(16) TA As[16][64];
+    __shared__ __align__(16) TA Bs[16][64];
+    const int nt = (int)(s_pad / 64);
+    int ta = 0, rem = blockIdx.x;
+    while (rem >= nt - ta) { rem -= nt - ta; ++ta; }
+    const int tb = ta + rem;
+    const int a0 = ta * 64, b0 = tb * 64;
+    const int64_t kper = ((K + kGramSlices - 1) / kGramSlices + 15) / 16 * 16;
+    const int64_t kbeg = (int64_t)blockIdx.y * kper;
+    const int64_t kend = min(K, kbeg + kper);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    TA acc[4][4];
+    TA hi[4][4], lo[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = TA(0);
-    for (int64_t k0 = 0; k0 < K; k0 += 16) {
+        for (int j = 0; j < 4; ++j) { hi[i][j] = TA(0); lo[i][j] = TA(0); }
+    for (int64_t k0 = kbeg; k0 < kend; k0 += 16) {
         for (int e = threadIdx.x; e < 16 * 64; e += 256) {
             int kk = e >> 6, cc = e & 63;
-            bool in = (k0 + kk) < K;
+            bool in = (k0 + kk) < kend;
             As[kk][cc] = in ? Ct[(k0 + kk) * ld + a0 + cc] : TA(0);
             Bs[kk][cc] = in ? Ct[(k0 + kk) * ld + b0 + cc] : TA(0);
         }
         __syncthreads();
+        TA acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = TA(0);
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk) {
             TA av[4], bv[4];
+            if constexpr (sizeof(TA) == 4) {
+                const float4 va = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+                const float4 vb = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+                av[0] = va.x; av[1] = va.y; av[2] = va.z; av[3] = va.w;
+                bv[0] = vb.x; bv[1] = vb.y; bv[2] = vb.z; bv[3] = vb.w;
+            } else {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) av[i] = As[kk][ty * 4 + i];
+                for (int i = 0; i < 4; ++i) av[i] = As[kk][ty * 4 + i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx * 4 + j];
+                for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx * 4 + j];
+            }
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
         }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) two_sum_add(hi[i][j], lo[i][j], acc[i][j]);
         __syncthreads();
     }
+    double* Ps = P + (int64_t)blockIdx.y * s_pad * s_pad;
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            int64_t a = a0 + ty * 4 + i, b = b0 + tx * 4 + j;
-            double v;
-            if (a < s && b < s) v = (double)acc[i][j] + lam_t * (double)W[a * s_pad + b];
-            else v = (a == b) ? 1.0 : 0.0;
-            M2[a * s_pad + b] = v;
+            const int64_t a = a0 + ty * 4 + i, b = b0 + tx * 4 + j;
+            const double v = (double)hi[i][j] + (double)lo[i][j];
+            Ps[a * s_pad + b] = v;
+            Ps[b * s_pad + a] = v;
         }
+}
+
+// M2 = sum_slices P + lam_t W (FP64, fixed order); pad rows/cols get identity.
+template <typename TA>
+__global__ void k_gram_finish(const double* __restrict__ P, const TA* __restrict__ W, double lam_t,
+                              int64_t s, int64_t s_pad, double* __restrict__ M2) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= s_pad * s_pad) return;
+    const int64_t a = e / s_pad, b = e % s_pad;
+    double v;
+    if (a < s && b < s) {
+        v = 0.0;
+#pragma unroll
+        for (int sl = 0; sl < kGramSlices; ++sl) v += P[(int64_t)sl * s_pad * s_pad + e];
+        v += lam_t * (double)W[e];
+    } else {
+        v = (a == b) ? 1.0 : 0.0;
+    }
+    M2[e] = v;
 }
 
 // W <- (W + W^T)/2 in place (working precision) and W64 = (double)W.
@@ -86,53 +143,72 @@ __global__ void k_symmetrize(T* __restrict__ W, double* __restrict__ W64, int64_
 // ----------------------------------------------------------- FP64 GEMM
 
 // Cm = alpha * op(A) op(B) + beta * Cm, row-major; op(A) is m x k, op(B) k x n.
-// 32 x 32 tile, 256 threads each 2 x 2, K chunks of 16.
-template <bool TA_, bool TB_>
+// TS x TS output tile (TS = 16 or 32), 256 threads, K chunks of 16. The
+// triangular structure of the operands limits the K range of each tile:
+//   tri_a = 1: op(A) lower triangular (A[i][k] = 0 for k > i)
+//   tri_b = 1: op(B) upper triangular (B[k][j] = 0 for k > j)
+//   tri_b = 2: op(B) lower triangular (B[k][j] = 0 for k < j)
+//   lower_out: only tiles touching the lower triangle (i >= j) are computed.
+template <bool TA_, bool TB_, int TS>
 __global__ void __launch_bounds__(256) k_dgemm(int64_t m, int64_t n, int64_t k, double alpha,
                                               const double* __restrict__ A, int64_t lda,
                                               const double* __restrict__ B, int64_t ldb,
-                                              double beta, double* __restrict__ Cm, int64_t ldc) {
-    __shared__ double As[16][32 + 1];   // As[kk][i] = op(A)[i][k0+kk]
-    __shared__ double Bs[16][32 + 1];   // Bs[kk][j] = op(B)[k0+kk][j]
-    const int64_t i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+                                              double beta, double* __restrict__ Cm, int64_t ldc,
+                                              int tri_a, int tri_b, int lower_out) {
+    constexpr int PT = TS / 16;              // outputs per thread per dimension
+    __shared__ double As[16][TS + 1];        // As[kk][i] = op(A)[i][k0+kk]
+    __shared__ double Bs[16][TS + 1];        // Bs[kk][j] = op(B)[k0+kk][j]
+    const int64_t i0 = (int64_t)blockIdx.y * TS, j0 = (int64_t)blockIdx.x * TS;
+    if (lower_out && j0 > i0 + TS - 1) return;
+    int64_t kbeg = 0, kend = k;
+    if (tri_a == 1) kend = min(kend, i0 + TS);
+    if (tri_b == 1) kend = min(kend, j0 + TS);
+    if (tri_b == 2) kbeg = (j0 / 16) * 16;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    double acc[2][2] = {{0, 0}, {0, 0}};
-    for (int64_t k0 = 0; k0 < k; k0 += 16) {
-        for (int e = threadIdx.x; e < 16 * 32; e += 256) {
+    double acc[PT][PT];
+#pragma unroll
+    for (int i = 0; i < PT; ++i)
+#pragma unroll
+        for (int j = 0; j < PT; ++j) acc[i][j] = 0.0;
+    for (int64_t k0 = kbeg; k0 < kend; k0 += 16) {
+        for (int e = threadIdx.x; e < 16 * TS; e += 256) {
             int kk, ii;
-            if (TA_) { ii = e & 31; kk = e >> 5; }   // A^T: read A[k][i], contiguous in i
+            if (TA_) { ii = e % TS; kk = e / TS; }   // A^T: read A[k][i], contiguous in i
             else { kk = e & 15; ii = e >> 4; }        // A: read A[i][k], contiguous in k
             int64_t gi = i0 + ii, gk = k0 + kk;
             double v = 0.0;
-            if (gi < m && gk < k) v = TA_ ? A[gk * lda + gi] : A[gi * lda + gk];
+            if (gi < m && gk < kend) v = TA_ ? A[gk * lda + gi] : A[gi * lda + gk];
             As[kk][ii] = v;
         }
-        for (int e = threadIdx.x; e < 16 * 32; e += 256) {
+        for (int e = threadIdx.x; e < 16 * TS; e += 256) {
             int kk, jj;
             if (TB_) { kk = e & 15; jj = e >> 4; }    // B^T: read B[j][k], contiguous in k
-            else { jj = e & 31; kk = e >> 5; }        // B: read B[k][j], contiguous in j
+            else { jj = e % TS; kk = e / TS; }        // B: read B[k][j], contiguous in j
             int64_t gj = j0 + jj, gk = k0 + kk;
             double v = 0.0;
-            if (gj < n && gk < k) v = TB_ ? B[gj * ldb + gk] : B[gk * ldb + gj];
+            if (gj < n && gk < kend) v = TB_ ? B[gj * ldb + gk] : B[gk * ldb + gj];
             Bs[kk][jj] = v;
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk) {
-            double a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
-            double b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
-            acc[0][0] = fma(a0, b0, acc[0][0]);
-            acc[0][1] = fma(a0, b1, acc[0][1]);
-            acc[1][0] = fma(a1, b0, acc[1][0]);
-            acc[1][1] = fma(a1, b1, acc[1][1]);
+            double av[PT], bv[PT];
+#pragma unroll
+            for (int i = 0; i < PT; ++i) av[i] = As[kk][ty * PT + i];
+#pragma unroll
+            for (int j = 0; j < PT; ++j) bv[j] = Bs[kk][tx * PT + j];
+#pragma unroll
+            for (int i = 0; i < PT; ++i)
+#pragma unroll
+                for (int j = 0; j < PT; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < PT; ++i)
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            int64_t gi = i0 + ty * 2 + i, gj = j0 + tx * 2 + j;
+        for (int j = 0; j < PT; ++j) {
+            int64_t gi = i0 + ty * PT + i, gj = j0 + tx * PT + j;
             if (gi < m && gj < n) {
                 double c = beta == 0.0 ? 0.0 : beta * Cm[gi * ldc + gj];
                 Cm[gi * ldc + gj] = c + alpha * acc[i][j];
@@ -140,9 +216,6 @@ __global__ void __launch_bounds__(256) k_dgemm(int64_t m, int64_t n, int64_t k, 
         }
 }
 
-// Leaf: dense Cholesky of the nb x nb block at M (ld) in place (lower), and
-// its inverse into X (ld), one block of 256 threads, nb <= 64. On a
-// non-positive or non-finite pivot sets *fail = 1.
 constexpr int kLeafSmem = 2 * 64 * 65 * (int)sizeof(double);
 
 __global__ void __launch_bounds__(256) k_chol_leaf(double* __restrict__ M, double* __restrict__ X,
@@ -150,6 +223,7 @@ __global__ void __launch_bounds__(256) k_chol_leaf(double* __restrict__ M, doubl
     extern __shared__ __align__(16) double leaf_smem[];
     double (*a)[65] = reinterpret_cast<double (*)[65]>(leaf_smem);
     double (*x)[65] = reinterpret_cast<double (*)[65]>(leaf_smem + 64 * 65);
+    __shared__ double inv_d[64];
     __shared__ int bad;
     if (threadIdx.x == 0) bad = 0;
     for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
@@ -157,31 +231,37 @@ __global__ void __launch_bounds__(256) k_chol_leaf(double* __restrict__ M, doubl
         a[i][j] = (j <= i) ? M[i * ld + j] : 0.0;
     }
     __syncthreads();
-    for (int kcol = 0; kcol < nb; ++kcol) {
-        // pivot
+    // right-looking Cholesky; one reciprocal per pivot
+    for (int kc = 0; kc < nb; ++kc) {
         if (threadIdx.x == 0) {
-            double d = a[kcol][kcol];
+            double d = a[kc][kc];
             if (!(d > 0.0) || !isfinite(d)) { bad = 1; d = 1.0; }
-            a[kcol][kcol] = sqrt(d);
+            const double r = sqrt(d);
+            a[kc][kc] = r;
+            inv_d[kc] = 1.0 / r;
         }
         __syncthreads();
-        double piv = a[kcol][kcol];
-        for (int i = kcol + 1 + threadIdx.x; i < nb; i += blockDim.x) a[i][kcol] /= piv;
+        const double ip = inv_d[kc];
+        for (int i = kc + 1 + threadIdx.x; i < nb; i += blockDim.x) a[i][kc] *= ip;
         __syncthreads();
-        // trailing update of the lower triangle
-        int rem = nb - kcol - 1;
-        for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
-            int i = kcol + 1 + e / rem, j = kcol + 1 + e % rem;
-            if (j <= i) a[i][j] -= a[i][kcol] * a[j][kcol];
+        // trailing lower triangle: thread (ty, tx) of a 16 x 16 grid strides
+        // over rows and columns (no integer division in the loop)
+        const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+        for (int i = kc + 1 + ty; i < nb; i += 16) {
+            const double li = a[i][kc];
+            for (int j = kc + 1 + tx; j <= i; j += 16) a[i][j] = fma(-li, a[j][kc], a[i][j]);
         }
         __syncthreads();
     }
-    // X = L^{-1}: column j by forward substitution (thread per column)
+    // X = L^{-1}: column j by forward substitution (thread per column), with
+    // the pivot reciprocals instead of divisions
     for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-        for (int i = 0; i < nb; ++i) {
-            double v = (i == j) ? 1.0 : 0.0;
-            for (int kk = j; kk < i; ++kk) v -= a[i][kk] * x[kk][j];
-            x[i][j] = (i < j) ? 0.0 : v / a[i][i];
+        for (int i = 0; i < j; ++i) x[i][j] = 0.0;
+        x[j][j] = inv_d[j];
+        for (int i = j + 1; i < nb; ++i) {
+            double v = 0.0;
+            for (int q = j; q < i; ++q) v = fma(a[i][q], x[q][j], v);
+            x[i][j] = -v * inv_d[i];
         }
     }
     __syncthreads();
@@ -227,14 +307,27 @@ __global__ void k_cast_tri(const double* __restrict__ X, T* __restrict__ B, T* _
     Bt[j * s_pad + i] = (T)v;
 }
 
+template <int TS>
+void launch_dgemm_ts(msp_ctx* ctx, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha,
+                     const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                     double* Cm, int64_t ldc, int tri_a, int tri_b, int lower_out) {
+    dim3 grid((unsigned)((n + TS - 1) / TS), (unsigned)((m + TS - 1) / TS));
+    if (!ta && !tb) k_dgemm<false, false, TS><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, A, lda, B, ldb, beta, Cm, ldc, tri_a, tri_b, lower_out);
+    else if (!ta && tb) k_dgemm<false, true, TS><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, A, lda, B, ldb, beta, Cm, ldc, tri_a, tri_b, lower_out);
+    else if (ta && !tb) k_dgemm<true, false, TS><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, A, lda, B, ldb, beta, Cm, ldc, tri_a, tri_b, lower_out);
+    else k_dgemm<true, true, TS><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, A, lda, B, ldb, beta, Cm, ldc, tri_a, tri_b, lower_out);
+}
+
 msp_status dgemm(msp_ctx* ctx, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha,
                  const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
-                 double* Cm, int64_t ldc) {
-    dim3 grid((unsigned)((n + 31) / 32), (unsigned)((m + 31) / 32));
-    if (!ta && !tb) k_dgemm<false, false><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, A, lda, B, ldb, beta, Cm, ldc);
-    else if (!ta && tb) k_dgemm<false, true><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, A, lda, B, ldb, beta, Cm, ldc);
-    else if (ta && !tb) k_dgemm<true, false><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, A, lda, B, ldb, beta, Cm, ldc);
-    else k_dgemm<true, true><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, A, lda, B, ldb, beta, Cm, ldc);
+                 double* Cm, int64_t ldc, int tri_a = 0, int tri_b = 0, int lower_out = 0) {
+    // FP64 work is pipe-bound on this part: prefer the larger tile only when it
+    // still yields two blocks per SM
+    const int64_t tiles32 = ((m + 31) / 32) * ((n + 31) / 32);
+    if (tiles32 >= 2 * ctx->num_sms)
+        launch_dgemm_ts<32>(ctx, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, Cm, ldc, tri_a, tri_b, lower_out);
+    else
+        launch_dgemm_ts<16>(ctx, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, Cm, ldc, tri_a, tri_b, lower_out);
     MSP_CHECK_LAUNCH(ctx);
     return MSP_OK;
 }
@@ -264,14 +357,14 @@ msp_status chol_inv(msp_ctx* ctx, double* M, double* X, double* T1, double* T2, 
     double* X21 = X + (off + n1) * ld + off;
     double* X22 = X + (off + n1) * ld + off + n1;
     MSP_TRY(chol_inv(ctx, M, X, T1, T2, ld, off, n1, fail));
-    // T1 = L21 = A21 X11^T   (n2 x n1)
-    MSP_TRY(dgemm(ctx, false, true, n2, n1, n1, 1.0, A21, ld, X11, ld, 0.0, T1, ld));
-    // A22 -= L21 L21^T
-    MSP_TRY(dgemm(ctx, false, true, n2, n2, n1, -1.0, T1, ld, T1, ld, 1.0, A22, ld));
+    // T1 = L21 = A21 X11^T   (n2 x n1; X11^T is upper triangular)
+    MSP_TRY(dgemm(ctx, false, true, n2, n1, n1, 1.0, A21, ld, X11, ld, 0.0, T1, ld, 0, 1, 0));
+    // A22 -= L21 L21^T (lower triangle is all the recursion reads)
+    MSP_TRY(dgemm(ctx, false, true, n2, n2, n1, -1.0, T1, ld, T1, ld, 1.0, A22, ld, 0, 0, 1));
     MSP_TRY(chol_inv(ctx, M, X, T1 + n1, T2 + n1, ld, off + n1, n2, fail));
-    // T2 = L21 X11; X21 = -X22 T2
-    MSP_TRY(dgemm(ctx, false, false, n2, n1, n1, 1.0, T1, ld, X11, ld, 0.0, T2, ld));
-    MSP_TRY(dgemm(ctx, false, false, n2, n1, n2, -1.0, X22, ld, T2, ld, 0.0, X21, ld));
+    // T2 = L21 X11 (X11 lower); X21 = -X22 T2 (X22 lower)
+    MSP_TRY(dgemm(ctx, false, false, n2, n1, n1, 1.0, T1, ld, X11, ld, 0.0, T2, ld, 0, 2, 0));
+    MSP_TRY(dgemm(ctx, false, false, n2, n1, n2, -1.0, X22, ld, T2, ld, 0.0, X21, ld, 1, 0, 0));
     // store L21 into M
     MSP_CUDA_TRY(ctx, cudaMemcpy2DAsync(A21, ld * 8, T1, ld * 8, n1 * 8, n2,
                                         cudaMemcpyDeviceToDevice, ctx->stream));
@@ -294,17 +387,26 @@ msp_status msp_build_factor(msp_ctx* ctx, msp_factor_s* f, const void* Ct, int64
             k_symmetrize<double><<<grid, blk, 0, ctx->stream>>>((double*)f->W, f->W64, sp);
         MSP_CHECK_LAUNCH(ctx);
     }
-    // M2 = Ct^T Ct + lam_t W
+    // M2 = Ct^T Ct + lam_t W: split-K partial Grams (upper tiles, mirrored),
+    // then the fixed-order FP64 combination
     {
-        dim3 grid((unsigned)(sp / 64), (unsigned)(sp / 64));
-        if (f->dtype == MSP_F32)
-            k_gram<float><<<grid, 256, 0, ctx->stream>>>((const float*)Ct, phi_rows, sp,
-                                                         (const float*)f->W, f->lam_tilde, f->s,
-                                                         sp, f->M2);
-        else
-            k_gram<double><<<grid, 256, 0, ctx->stream>>>((const double*)Ct, phi_rows, sp,
-                                                          (const double*)f->W, f->lam_tilde, f->s,
-                                                          sp, f->M2);
+        void* scr = nullptr;
+        MSP_TRY(msp_scratch(ctx, (size_t)kGramSlices * sp * sp * 8, &scr));
+        double* P = (double*)scr;
+        const int nt = (int)(sp / 64);
+        dim3 grid((unsigned)(nt * (nt + 1) / 2), kGramSlices);
+        const unsigned fb = (unsigned)((sp * sp + 255) / 256);
+        if (f->dtype == MSP_F32) {
+            k_gram<float><<<grid, 256, 0, ctx->stream>>>((const float*)Ct, phi_rows, sp, sp, P);
+            MSP_CHECK_LAUNCH(ctx);
+            k_gram_finish<float><<<fb, 256, 0, ctx->stream>>>(P, (const float*)f->W, f->lam_tilde,
+                                                               f->s, sp, f->M2);
+        } else {
+            k_gram<double><<<grid, 256, 0, ctx->stream>>>((const double*)Ct, phi_rows, sp, sp, P);
+            MSP_CHECK_LAUNCH(ctx);
+            k_gram_finish<double><<<fb, 256, 0, ctx->stream>>>(P, (const double*)f->W, f->lam_tilde,
+                                                                f->s, sp, f->M2);
+        }
         MSP_CHECK_LAUNCH(ctx);
     }
     // factor with shift retries

@@ -140,9 +140,27 @@ __global__ void __launch_bounds__(256) k_gemv(const TA* __restrict__ A, int64_t 
     }
 }
 
+// Exact binary32 -> binary64 widening with integer instructions (the FP64
+// pipe, which bounds the residual, then only executes the FMAs). Subnormal
+// inputs are flushed to zero (their products are below 1e-37 |x|); infinities
+// and NaNs keep their class.
+__device__ inline double widen_f32(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t ex = u & 0x7f800000u;
+    const uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
+    uint64_t bits;
+    if (ex == 0u) bits = sign;                                               // zero / subnormal
+    else if (ex == 0x7f800000u) bits = sign | 0x7ff0000000000000ull | ((uint64_t)(u & 0x007fffffu) << 29);
+    else bits = sign | (((uint64_t)(u & 0x7fffffffu) << 29) + ((uint64_t)(1023 - 127) << 52));
+    return __longlong_as_double((long long)bits);
+}
+
 // out = b - (A + lam I) x  (or (A + lam I) x if b == nullptr), FP64
-// accumulation; |out|^2 into *norm2 (last block, fixed order).
-template <typename TA>
+// accumulation; |out|^2 into *norm2 (last block, fixed order). The FP64 FMA
+// rate bounds this kernel on this part (two FMAs per clock per SM): loads are
+// vectorised (16 B of A, 32 B of x per lane step) and A is widened with
+// integer instructions so that the FP64 pipe issues only the FMAs.
+template <typename TA, bool VEC>
 __global__ void __launch_bounds__(256) k_matvec64(const TA* __restrict__ A, int64_t lda, int64_t n,
                                                  double lam, const double* __restrict__ x,
                                                  const double* __restrict__ b,
@@ -156,9 +174,36 @@ __global__ void __launch_bounds__(256) k_matvec64(const TA* __restrict__ A, int6
     for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n;
          i += warps) {
         const TA* row = A + i * lda;
-        double acc = 0.0;
-        for (int64_t j = lane; j < n; j += 32) acc = fma((double)__ldcs(&row[j]), x[j], acc);
-        acc = msp::warp_sum(acc);
+        double acc0 = 0.0, acc1 = 0.0;
+        if constexpr (VEC && sizeof(TA) == 4) {
+            int64_t j = (int64_t)lane * 4;
+            for (; j + 32 * 4 < n; j += 2 * 32 * 4) {
+                const float4 a0 = __ldcs(reinterpret_cast<const float4*>(row + j));
+                const float4 a1 = __ldcs(reinterpret_cast<const float4*>(row + j + 128));
+                const double2 x0 = *reinterpret_cast<const double2*>(x + j);
+                const double2 x1 = *reinterpret_cast<const double2*>(x + j + 2);
+                const double2 x2 = *reinterpret_cast<const double2*>(x + j + 128);
+                const double2 x3 = *reinterpret_cast<const double2*>(x + j + 130);
+                acc0 = fma(widen_f32(a0.x), x0.x, acc0);
+                acc1 = fma(widen_f32(a1.x), x2.x, acc1);
+                acc0 = fma(widen_f32(a0.y), x0.y, acc0);
+                acc1 = fma(widen_f32(a1.y), x2.y, acc1);
+                acc0 = fma(widen_f32(a0.z), x1.x, acc0);
+                acc1 = fma(widen_f32(a1.z), x3.x, acc1);
+                acc0 = fma(widen_f32(a0.w), x1.y, acc0);
+                acc1 = fma(widen_f32(a1.w), x3.y, acc1);
+            }
+            for (; j < n; j += 32 * 4) {
+                const float4 a0 = __ldcs(reinterpret_cast<const float4*>(row + j));
+                acc0 = fma(widen_f32(a0.x), x[j], acc0);
+                acc0 = fma(widen_f32(a0.y), x[j + 1], acc0);
+                acc0 = fma(widen_f32(a0.z), x[j + 2], acc0);
+                acc0 = fma(widen_f32(a0.w), x[j + 3], acc0);
+            }
+        } else {
+            for (int64_t j = lane; j < n; j += 32) acc0 = fma((double)__ldcs(&row[j]), x[j], acc0);
+        }
+        double acc = msp::warp_sum(acc0 + acc1);
         if (lane == 0) {
             double v = acc + lam * x[i];
             if (b) v = b[i] - v;
@@ -202,6 +247,10 @@ struct L2Args {
     const T* q;
     T* p;
     T* z;                   // level-1 preconditioned residual (in/out)
+    const float* qpart;     // packed A pass: q_i = sum_slot qpart[slot][i] + lam p_i
+    int q_slots;
+    int64_t q_ld;
+    T lam;
     CtlBlock* ctl;
     T* part;                // G x s_pad
     T* gvec;                // s_pad
@@ -247,25 +296,20 @@ __device__ inline void store_slice(T* dst, const T* src, int lane) {
 //   kind 1: acc += (c_i . d) c_i               (u = C^T C d)
 //   kind 2: w_i = (r_i - c_i . y) / lam~; dots r.w and r.z_old  (no acc)
 // Per-warp accumulators are combined through shared memory into part[b].
+constexpr int kRowChunk = 256;   // rows of C staged per round (r, z, w in shared memory)
+
 template <typename T, int PL>
-__device__ inline void row_one(const L2Args<T>& a, int kind, int64_t i, const RowSlice<T, PL>& c,
-                               const T* svec, T* acc, double& d_rw, double& d_rzo, int lane) {
+__device__ inline void row_one(const L2Args<T>& a, int kind, int64_t il, const RowSlice<T, PL>& c,
+                               const T* svec, T* acc, const T* sr, T* sw, int lane) {
     T coef;
     if (kind == 0) {
-        coef = a.r[i];
+        coef = sr[il];
     } else {
         T t = msp::warp_sum(c.dot_smem(svec, lane));
         if (kind == 1) {
             coef = t;
         } else {
-            T ri = a.r[i];
-            T wi = (ri - t) / a.lam_t;
-            if (lane == 0) {
-                T zo = a.z[i];
-                d_rw += (double)ri * (double)wi;
-                d_rzo += (double)ri * (double)zo;
-                a.z[i] = wi;
-            }
+            if (lane == 0) sw[il] = (sr[il] - t) / a.lam_t;
             return;
         }
     }
@@ -273,31 +317,54 @@ __device__ inline void row_one(const L2Args<T>& a, int kind, int64_t i, const Ro
     for (int k = 0; k < PL; ++k) acc[k] += coef * c.v[k];
 }
 
-// Row pass over this block's rows of C, two rows in flight per warp.
+// Row pass over this block's rows of C, two rows in flight per warp, in
+// chunks of kRowChunk rows whose r (and z_old, w) live in shared memory so no
+// per-row global access sits on the critical path.
 //   kind 0: acc += r_i c_i                     (g = C^T r)
 //   kind 1: acc += (c_i . d) c_i               (u = C^T C d)
-//   kind 2: w_i = (r_i - c_i . y) / lam~; dots r.w and r.z_old  (no acc)
+//   kind 2: w_i = (r_i - c_i . y) / lam~ into z; per-thread dots r.w, r.z_old
 // Per-warp accumulators are combined through shared memory into part[b].
 template <typename T, int PL>
 __device__ void row_pass(const L2Args<T>& a, int kind, int64_t row0, int64_t row1, const T* svec,
-                         T* swarp, double* rw, double* rzo) {
+                         T* swarp, T* srow, double* rw, double* rzo) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T* sr = srow;                 // kRowChunk
+    T* sw = srow + kRowChunk;     // kRowChunk
     T acc[PL];
 #pragma unroll
     for (int k = 0; k < PL; ++k) acc[k] = T(0);
     double d_rw = 0.0, d_rzo = 0.0;
-    int64_t i = row0 + w;
-    for (; i + kNW < row1; i += 2 * kNW) {
-        RowSlice<T, PL> c0, c1;
-        c0.load(a.C + i * a.s_pad, lane);
-        c1.load(a.C + (i + kNW) * a.s_pad, lane);
-        row_one<T, PL>(a, kind, i, c0, svec, acc, d_rw, d_rzo, lane);
-        row_one<T, PL>(a, kind, i + kNW, c1, svec, acc, d_rw, d_rzo, lane);
-    }
-    if (i < row1) {
-        RowSlice<T, PL> c0;
-        c0.load(a.C + i * a.s_pad, lane);
-        row_one<T, PL>(a, kind, i, c0, svec, acc, d_rw, d_rzo, lane);
+    for (int64_t base = row0; base < row1; base += kRowChunk) {
+        const int64_t end = min(row1, base + kRowChunk);
+        const int nr = (int)(end - base);
+        if (kind != 1) {
+            for (int e = threadIdx.x; e < nr; e += blockDim.x) sr[e] = a.r[base + e];
+            __syncthreads();
+        }
+        int il = w;
+        for (; il + kNW < nr; il += 2 * kNW) {
+            RowSlice<T, PL> c0, c1;
+            c0.load(a.C + (base + il) * a.s_pad, lane);
+            c1.load(a.C + (base + il + kNW) * a.s_pad, lane);
+            row_one<T, PL>(a, kind, il, c0, svec, acc, sr, sw, lane);
+            row_one<T, PL>(a, kind, il + kNW, c1, svec, acc, sr, sw, lane);
+        }
+        if (il < nr) {
+            RowSlice<T, PL> c0;
+            c0.load(a.C + (base + il) * a.s_pad, lane);
+            row_one<T, PL>(a, kind, il, c0, svec, acc, sr, sw, lane);
+        }
+        if (kind != 1) __syncthreads();
+        if (kind == 2) {
+            for (int e = threadIdx.x; e < nr; e += blockDim.x) {
+                const T ri = sr[e], wi = sw[e];
+                const T zo = a.z[base + e];
+                d_rw += (double)ri * (double)wi;
+                d_rzo += (double)ri * (double)zo;
+                a.z[base + e] = wi;
+            }
+            __syncthreads();
+        }
     }
     if (kind == 2) {
         *rw = d_rw;
@@ -332,6 +399,51 @@ __device__ inline void rows_dot(const T* M, int64_t s_pad, int64_t c0, int64_t c
     }
 }
 
+// out[c] = sum_k part[k][c] (+ add_scale * addend[c]) for c in [c0, c1), k < G.
+// Fixed order: thread t sums k = t, t + blockDim, ...; then a warp tree; then
+// warps in index order. Returns sum_c out[c] * dvec[c] (dvec in shared memory,
+// may be null) and sum_c out[c]^2 through *sq (may be null). Columns are
+// processed 8 at a time so all loads of a chunk are in flight together.
+template <typename T>
+__device__ inline void reduce_cols(const T* part, int G, int64_t sp, int64_t c0, int64_t c1,
+                                   const T* addend, T add_scale, T* out, const T* dvec,
+                                   double* dot_out, double* sq_out, double* red2 /*8*32*/) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double dot = 0.0, sq = 0.0;
+    for (int64_t cb = c0; cb < c1; cb += 8) {
+        const int nc = (int)min((int64_t)8, c1 - cb);
+        T v[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v[c] = T(0);
+        for (int k = threadIdx.x; k < G; k += blockDim.x) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                if (c < nc) v[c] += __ldcg(&part[(int64_t)k * sp + cb + c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v[c] = msp::warp_sum(v[c]);
+        __syncthreads();
+        if (lane == 0) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) red2[c * 32 + w] = (double)v[c];
+        }
+        __syncthreads();
+        if (threadIdx.x < nc) {
+            const int c = threadIdx.x;
+            double acc = 0.0;
+            for (int k = 0; k < nw; ++k) acc += red2[c * 32 + k];
+            T r = (T)acc;
+            if (addend) r += add_scale * __ldcg(&addend[cb + c]);
+            out[cb + c] = r;
+            if (dvec) dot += (double)dvec[cb + c] * (double)r;
+            sq += (double)r * (double)r;
+        }
+    }
+    __syncthreads();
+    if (dot_out) *dot_out = dot;   // per-thread partials; caller block-sums them
+    if (sq_out) *sq_out = sq;
+}
+
 template <typename T>
 __device__ inline void load_full(const T* g, T* s, int64_t m) {
     for (int64_t c = threadIdx.x; c < m; c += blockDim.x) s[c] = __ldcg(&g[c]);
@@ -346,7 +458,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_level2(L2Args<T> a) {
     T* sy = sres + sp;                            // level-2 iterate
     T* stmp = sy + sp;                            // scratch full vector
     T* swarp = stmp + sp;                         // kNW x sp
+    T* srow = swarp + kNW * sp;                   // 2 x kRowChunk (row pass staging)
     __shared__ double red[32];
+    __shared__ double red2[8 * 32];
     __shared__ double s_rw, s_rzo;
 
     CtlBlock* ctl = a.ctl;
@@ -363,7 +477,45 @@ __global__ void __launch_bounds__(kThreads, 1) k_level2(L2Args<T> a) {
 
     // ---- level-1 update and g = C^T r partials
     double rr = 0.0;
-    if (a.mode != MODE_APPLY) {
+    if (a.mode == MODE_ITER && a.qpart) {
+        // q_i = sum over the packed A pass's slot partials + lam p_i; 32 rows x
+        // 8 slot groups per round, fixed summation order
+        T* sq = swarp;  // 8 x 32 scratch in shared memory (swarp is free here)
+        const int rl = threadIdx.x & 31, grp = threadIdx.x >> 5;
+        for (int64_t base = row0; base < row1; base += 32) {
+            const int64_t i = base + rl;
+            T v = T(0);
+            if (i < row1) {
+                // eight independent loads in flight per thread
+                int sl = grp;
+                for (; sl + 7 * kNW < a.q_slots; sl += 8 * kNW) {
+                    T t8[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        t8[u] = __ldcg(&a.qpart[(int64_t)(sl + u * kNW) * a.q_ld + i]);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) v += t8[u];
+                }
+                for (; sl < a.q_slots; sl += kNW) v += __ldcg(&a.qpart[(int64_t)sl * a.q_ld + i]);
+            }
+            sq[grp * 32 + rl] = v;
+            __syncthreads();
+            if (grp == 0 && i < row1) {
+                T qi = T(0);
+#pragma unroll
+                for (int g = 0; g < kNW; ++g) qi += sq[g * 32 + rl];
+                qi += a.lam * a.p[i];
+                T ri = a.r[i];
+                a.x[i] += (T)alpha * a.p[i];
+                ri -= (T)alpha * qi;
+                a.r[i] = ri;
+                rr += (double)ri * (double)ri;
+            }
+            __syncthreads();
+        }
+        rr = block_sum(rr, red);
+        if (threadIdx.x == 0) a.dpart[b * 4 + 0] = rr;
+    } else if (a.mode != MODE_APPLY) {
         for (int64_t i = row0 + threadIdx.x; i < row1; i += blockDim.x) {
             T ri = a.r[i];
             if (a.mode == MODE_ITER) {
@@ -377,7 +529,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_level2(L2Args<T> a) {
         if (threadIdx.x == 0) a.dpart[b * 4 + 0] = rr;
     }
     __syncthreads();
-    row_pass<T, PL>(a, 0, row0, row1, nullptr, swarp, nullptr, nullptr);
+    row_pass<T, PL>(a, 0, row0, row1, nullptr, swarp, srow, nullptr, nullptr);
     combine_warps(a, swarp, b);
     if (!msp::grid_barrier(bc, bg, err)) return;
 
@@ -401,12 +553,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_level2(L2Args<T> a) {
     }
     // ---- g reduced over this block's columns
     double gg = 0.0;
-    for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-        T v = T(0);
-        for (int k = 0; k < G; ++k) v += __ldcg(&a.part[(int64_t)k * sp + c]);
-        a.gvec[c] = v;
-        gg += (double)v * (double)v;
-    }
+    reduce_cols<T>(a.part, G, sp, c0, c1, nullptr, T(0), a.gvec, nullptr, nullptr, &gg, red2);
     gg = block_sum(gg, red);
     if (threadIdx.x == 0) a.dpart[b * 4 + 1] = gg;
     if (!msp::grid_barrier(bc, bg, err)) return;
@@ -440,21 +587,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_level2(L2Args<T> a) {
     double rres = gg;
     const double tin2 = a.inner_tol2 * gg;
     int k = 0;
+    if (a.max_inner == 0) {
+        // direct level 2: M2 is the level-2 operator itself (Phi = I), so
+        // y = M2^{-1} C^T r with no correction steps
+        for (int64_t c = threadIdx.x; c < sp; c += blockDim.x) sy[c] = sd[c];
+        __syncthreads();
+    }
     while (k < a.max_inner && rres > tin2) {
         // P1: partial u = C^T (C d) over this block's rows; wd = W d (columns)
-        row_pass<T, PL>(a, 1, row0, row1, sd, swarp, nullptr, nullptr);
+        row_pass<T, PL>(a, 1, row0, row1, sd, swarp, srow, nullptr, nullptr);
         combine_warps(a, swarp, b);
         rows_dot<T, PL>(a.W, sp, c0, c1, sd, a.wdvec);
         if (!msp::grid_barrier(bc, bg, err)) return;
         // P2: u over this block's columns; d.u partial
         double du = 0.0;
-        for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-            T v = T(0);
-            for (int kk = 0; kk < G; ++kk) v += __ldcg(&a.part[(int64_t)kk * sp + c]);
-            v += a.lam_t * __ldcg(&a.wdvec[c]);
-            a.uvec[c] = v;
-            du += (double)sd[c] * (double)v;
-        }
+        reduce_cols<T>(a.part, G, sp, c0, c1, a.wdvec, a.lam_t, a.uvec, sd, &du, nullptr, red2);
         du = block_sum(du, red);
         if (threadIdx.x == 0) a.dpart[b * 4 + 3] = du;
         if (!msp::grid_barrier(bc, bg, err)) return;
@@ -484,7 +631,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_level2(L2Args<T> a) {
     // ---- w = (r - C y) / lam~ into z; dots for the level-1 beta
     __syncthreads();
     double rw = 0.0, rzo = 0.0;
-    row_pass<T, PL>(a, 2, row0, row1, sy, swarp, &rw, &rzo);
+    row_pass<T, PL>(a, 2, row0, row1, sy, swarp, srow, &rw, &rzo);
     rw = block_sum(rw, red);
     rzo = block_sum(rzo, red);
     if (threadIdx.x == 0) {
@@ -519,7 +666,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_level2(L2Args<T> a) {
 template <typename T, int PL>
 msp_status launch_level2_pl(msp_ctx* ctx, L2Args<T>& a, int G) {
     auto kern = k_level2<T, PL>;
-    size_t smem = (size_t)(4 + kNW) * a.s_pad * sizeof(T);
+    size_t smem = ((size_t)(4 + kNW) * a.s_pad + 2 * kRowChunk) * sizeof(T);
     MSP_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem));
     // co-residency is required by the grid barrier: never exceed what fits
@@ -555,26 +702,34 @@ struct Workspace {
     void* part;
     void* vecs;
     double* dpart;
-    void* level1;   // x r q p z (n each)
-    double* gpart;  // gemv partials
+    void* level1;   // x r q p z (n_pad each)
+    double* gpart;  // A-pass partials
+    float* qpart;   // packed A pass: nt x n_pad slot partials (or null)
+    int64_t n_pad;
 };
 
 template <typename T>
-msp_status get_workspace(msp_ctx* ctx, int64_t n, int64_t sp, int G, int Gg, Workspace* ws) {
+msp_status get_workspace(msp_ctx* ctx, int64_t n, int64_t sp, int G, int Gg, bool packed,
+                         Workspace* ws) {
     size_t ts = sizeof(T);
+    const int64_t n_pad = round_up(n, 128);
+    const int64_t nt = n_pad / 128;
     size_t b_part = round_up((int64_t)G * sp * ts, 256);
     size_t b_vecs = round_up(5 * sp * ts, 256);
     size_t b_dpart = round_up((int64_t)G * 4 * 8, 256);
-    size_t b_l1 = round_up(5 * n * ts, 256);
+    size_t b_l1 = round_up(5 * n_pad * ts, 256);
     size_t b_gp = round_up((int64_t)Gg * 8, 256);
+    size_t b_qp = packed ? round_up(nt * n_pad * 4, 256) : 0;
     void* scr = nullptr;
-    MSP_TRY(msp_scratch(ctx, b_part + b_vecs + b_dpart + b_l1 + b_gp, &scr));
+    MSP_TRY(msp_scratch(ctx, b_part + b_vecs + b_dpart + b_l1 + b_gp + b_qp, &scr));
     char* c = (char*)scr;
     ws->part = c; c += b_part;
     ws->vecs = c; c += b_vecs;
     ws->dpart = (double*)c; c += b_dpart;
     ws->level1 = c; c += b_l1;
-    ws->gpart = (double*)c;
+    ws->gpart = (double*)c; c += b_gp;
+    ws->qpart = packed ? (float*)c : nullptr;
+    ws->n_pad = n_pad;
     return MSP_OK;
 }
 
@@ -609,23 +764,25 @@ template <typename T>
 msp_status krylov_solve_t(msp_ctx* ctx, const msp_factor_s* f, const void* A, msp_dtype dt,
                           int64_t n, int64_t lda, double lambda, const T* rhs, T* sol,
                           double tol_rel, int max_outer, const msp_opts* o, int* iters,
-                          int* inner_iters, ProfSlot* prof) {
+                          int* inner_iters, ProfSlot* prof, const float* packed) {
     const int G = level2_grid(ctx), Gg = gemv_grid(ctx);
+    const bool use_packed = (packed != nullptr) && (sizeof(T) == 4);
     Profiler pr;
     pr.ctx = ctx;
     pr.on = (prof != nullptr) && o->profile;
     if (pr.on) MSP_TRY(msp_profiler_reserve(ctx, 4096));
     Workspace ws;
-    MSP_TRY(get_workspace<T>(ctx, n, f->s_pad, G, Gg, &ws));
+    MSP_TRY(get_workspace<T>(ctx, n, f->s_pad, G, Gg, use_packed, &ws));
+    const int64_t np = ws.n_pad;
     T* x = (T*)ws.level1;
-    T* r = x + n;
-    T* q = r + n;
-    T* p = q + n;
-    T* z = p + n;
+    T* r = x + np;
+    T* q = r + np;
+    T* p = q + np;
+    T* z = p + np;
     CtlBlock* ctl = (CtlBlock*)ctx->ctl;
     MSP_CUDA_TRY(ctx, cudaMemsetAsync(ctl, 0, sizeof(CtlBlock), ctx->stream));
-    MSP_CUDA_TRY(ctx, cudaMemsetAsync(x, 0, n * sizeof(T), ctx->stream));
-    MSP_CUDA_TRY(ctx, cudaMemsetAsync(z, 0, n * sizeof(T), ctx->stream));
+    // all five level-1 vectors, pads included (p must be zero past n)
+    MSP_CUDA_TRY(ctx, cudaMemsetAsync(x, 0, 5 * np * sizeof(T), ctx->stream));
     MSP_CUDA_TRY(ctx, cudaMemcpyAsync(r, rhs, n * sizeof(T), cudaMemcpyDeviceToDevice, ctx->stream));
 
     L2Args<T> a{};
@@ -634,6 +791,10 @@ msp_status krylov_solve_t(msp_ctx* ctx, const msp_factor_s* f, const void* A, ms
     a.inner_tol2 = o->inner_tol * o->inner_tol;
     a.max_inner = o->max_inner;
     a.x = x; a.r = r; a.q = q; a.p = p; a.z = z;
+    a.qpart = use_packed ? ws.qpart : nullptr;
+    a.q_slots = (int)(np / 128);
+    a.q_ld = np;
+    a.lam = (T)lambda;
     a.mode = MODE_INIT;
     MSP_TRY(launch_level2(ctx, a, G));
     a.mode = MODE_ITER;
@@ -644,14 +805,17 @@ msp_status krylov_solve_t(msp_ctx* ctx, const msp_factor_s* f, const void* A, ms
     const int check = std::max(1, o->check_every);
     for (int it = 0; it < max_outer; ++it) {
         MSP_TRY(pr.begin(0));
-        if (dt == MSP_F32) {
+        if (use_packed) {
+            MSP_TRY(msp_symv_packed(ctx, packed, n, (float)lambda, (const float*)p, ws.qpart,
+                                    ws.gpart, ctx->num_sms));
+        } else if (dt == MSP_F32) {
             if (vec) k_gemv<float, T, true><<<Gg, 256, 0, ctx->stream>>>((const float*)A, lda, n, lambda, p, q, ws.gpart, ctl);
             else k_gemv<float, T, false><<<Gg, 256, 0, ctx->stream>>>((const float*)A, lda, n, lambda, p, q, ws.gpart, ctl);
         } else {
             if (vec) k_gemv<double, T, true><<<Gg, 256, 0, ctx->stream>>>((const double*)A, lda, n, lambda, p, q, ws.gpart, ctl);
             else k_gemv<double, T, false><<<Gg, 256, 0, ctx->stream>>>((const double*)A, lda, n, lambda, p, q, ws.gpart, ctl);
         }
-        MSP_CHECK_LAUNCH(ctx);
+        if (!use_packed) MSP_CHECK_LAUNCH(ctx);
         MSP_TRY(pr.end());
         MSP_TRY(pr.begin(1));
         MSP_TRY(launch_level2(ctx, a, G));
@@ -686,12 +850,12 @@ msp_status krylov_solve_t(msp_ctx* ctx, const msp_factor_s* f, const void* A, ms
 msp_status msp_krylov_solve(msp_ctx* ctx, const msp_factor_s* f, const void* A, msp_dtype dt,
                             int64_t n, int64_t lda, double lambda, const void* rhs, void* sol,
                             double tol_rel, int max_outer, const msp_opts* o, int* iters,
-                            int* inner_iters, ProfSlot* prof) {
+                            int* inner_iters, ProfSlot* prof, const float* packed) {
     if (f->dtype == MSP_F32)
         return krylov_solve_t<float>(ctx, f, A, dt, n, lda, lambda, (const float*)rhs, (float*)sol,
-                                     tol_rel, max_outer, o, iters, inner_iters, prof);
+                                     tol_rel, max_outer, o, iters, inner_iters, prof, packed);
     return krylov_solve_t<double>(ctx, f, A, dt, n, lda, lambda, (const double*)rhs, (double*)sol,
-                                  tol_rel, max_outer, o, iters, inner_iters, prof);
+                                  tol_rel, max_outer, o, iters, inner_iters, prof, nullptr);
 }
 
 // ---------------------------------------------------------------- profiler
@@ -749,7 +913,7 @@ msp_status msp_solve_m1_impl(msp_ctx* ctx, const msp_factor_s* f, const void* r,
     int* hf = (int*)ctx->host_flags;
     if (f->dtype == MSP_F32) {
         Workspace ws;
-        MSP_TRY(get_workspace<float>(ctx, n, f->s_pad, G, Gg, &ws));
+        MSP_TRY(get_workspace<float>(ctx, n, f->s_pad, G, Gg, false, &ws));
         L2Args<float> a{};
         fill_l2(a, f, n, ws, ctl);
         a.inner_tol2 = o->inner_tol * o->inner_tol;
@@ -760,7 +924,7 @@ msp_status msp_solve_m1_impl(msp_ctx* ctx, const msp_factor_s* f, const void* r,
         MSP_TRY(launch_level2(ctx, a, G));
     } else {
         Workspace ws;
-        MSP_TRY(get_workspace<double>(ctx, n, f->s_pad, G, Gg, &ws));
+        MSP_TRY(get_workspace<double>(ctx, n, f->s_pad, G, Gg, false, &ws));
         L2Args<double> a{};
         fill_l2(a, f, n, ws, ctl);
         a.inner_tol2 = o->inner_tol * o->inner_tol;
@@ -785,18 +949,25 @@ msp_status msp_matvec64(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t n, in
     void* scr = nullptr;
     MSP_TRY(msp_scratch(ctx, (size_t)Gg * 8 + 256, &scr));
     CtlBlock* ctl = (CtlBlock*)ctx->ctl;
-    if (dt == MSP_F32)
-        k_matvec64<float><<<Gg, 256, 0, ctx->stream>>>((const float*)A, lda, n, lambda, x, b, out,
-                                                       (double*)scr, &ctl->last_block_counter,
-                                                       norm2_out_dev);
-    else
-        k_matvec64<double><<<Gg, 256, 0, ctx->stream>>>((const double*)A, lda, n, lambda, x, b, out,
-                                                        (double*)scr, &ctl->last_block_counter,
-                                                        norm2_out_dev);
+    const bool vec = (dt == MSP_F32) && (lda % 4 == 0) && (n % 4 == 0) &&
+                     ((uintptr_t)A % 16 == 0) && ((uintptr_t)x % 16 == 0);
+    if (dt == MSP_F32) {
+        if (vec)
+            k_matvec64<float, true><<<Gg, 256, 0, ctx->stream>>>((const float*)A, lda, n, lambda, x, b,
+                                                                 out, (double*)scr,
+                                                                 &ctl->last_block_counter, norm2_out_dev);
+        else
+            k_matvec64<float, false><<<Gg, 256, 0, ctx->stream>>>((const float*)A, lda, n, lambda, x, b,
+                                                                  out, (double*)scr,
+                                                                  &ctl->last_block_counter, norm2_out_dev);
+    } else {
+        k_matvec64<double, false><<<Gg, 256, 0, ctx->stream>>>((const double*)A, lda, n, lambda, x, b,
+                                                               out, (double*)scr,
+                                                               &ctl->last_block_counter, norm2_out_dev);
+    }
     MSP_CHECK_LAUNCH(ctx);
     return MSP_OK;
 }
-
 // ------------------------------------------------------------ vector ops
 
 namespace {

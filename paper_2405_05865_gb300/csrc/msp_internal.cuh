@@ -10,7 +10,7 @@
 #include "msp.h"
 
 #define MSP_MAX_GAMMA 64
-#define MSP_MAX_S 2048
+#define MSP_MAX_S 1024
 #define MSP_S_ALIGN 128
 
 // ------------------------------------------------------------------ handles
@@ -53,6 +53,8 @@ struct msp_sketch_s {
     int32_t* csr_ptr = nullptr;  // s_pad + 1, Pi^T rows (= sketch columns)
     int32_t* csr_ent = nullptr;  // n*gamma entries (j << 1) | negative
     void* C = nullptr;           // n x s_pad, dtype
+    float* packed = nullptr;     // FP32 A: upper 128 x 128 tiles (see symv.cu)
+    const void* A_src = nullptr; // the A the sketch (and packed copy) came from
 };
 
 struct msp_factor_s {
@@ -226,14 +228,21 @@ msp_status msp_gather_rows(msp_ctx* ctx, msp_dtype dt, int64_t rows_out, int64_t
 // factor.cu
 msp_status msp_build_factor(msp_ctx* ctx, msp_factor_s* f, const void* Ct, int64_t phi_rows);
 
+// symv.cu
+int64_t msp_packed_tiles(int64_t n);
+msp_status msp_pack_upper(msp_ctx* ctx, const float* A, int64_t lda, int64_t n, float* packed);
+msp_status msp_symv_packed(msp_ctx* ctx, const float* packed, int64_t n, float lam, const float* p,
+                           float* part, double* dpart, int grid);
+
 // krylov.cu
 // prof: null, or two slots (A-pass GEMV, level-2 kernel) to accumulate
 // event-timed durations into (opts->profile).
+// packed: null (dense A pass over A) or the sketch's packed upper tiles.
 msp_status msp_krylov_solve(msp_ctx* ctx, const msp_factor_s* f, const void* A,
                             msp_dtype dt, int64_t n, int64_t lda, double lambda,
                             const void* rhs, void* sol, double tol_rel, int max_outer,
                             const msp_opts* o, int* iters, int* inner_iters,
-                            ProfSlot* prof);
+                            ProfSlot* prof, const float* packed);
 msp_status msp_matvec64(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t n,
                         int64_t lda, double lambda, const double* x, const double* b,
                         double* out, double* norm2_out_dev);

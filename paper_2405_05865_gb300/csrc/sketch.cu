@@ -123,15 +123,26 @@ __global__ void k_sort_buckets(int64_t m, const int32_t* __restrict__ ptr,
 // Block: R rows of A x all s_pad outputs. Thread t owns output columns
 // c = t + k*blockDim.x (k < NC) for the R rows (NC*R accumulators). A is
 // streamed in chunks of J columns into shared memory transposed to
-// tile[jj][0..R) so that one list entry (j, sign) costs R/4 vector loads.
-// Each thread walks its columns' sorted lists with a cursor per column.
+// tile[jj][0..R), stored as R/VW vectors of VW elements (16 bytes) whose
+// order is XOR-swizzled by (jj >> 1) so that the transposing vector stores of
+// 8 consecutive columns hit 8 distinct bank groups. One list entry (j, sign)
+// then costs R/VW vector loads. Each thread walks its columns' sorted lists
+// with a cursor per column.
+template <typename T> struct V16;
+template <> struct V16<float> { using type = float4; static constexpr int W = 4; };
+template <> struct V16<double> { using type = double2; static constexpr int W = 2; };
+
 template <typename T, int R, int NC>
-__global__ void __launch_bounds__(512, 1) k_sketch_apply(
+__global__ void __launch_bounds__(256) k_sketch_apply(
     const T* __restrict__ A, int64_t lda, int64_t n, int64_t s_pad,
     const int32_t* __restrict__ ptr, const int32_t* __restrict__ ent, T scale,
     T* __restrict__ C, int J) {
+    using VT = typename V16<T>::type;
+    constexpr int VW = V16<T>::W;
+    constexpr int NV = R / VW;                  // vectors per tile row (4)
+    static_assert(NV == 4, "swizzle assumes four 16-byte vectors per tile row");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* tile = reinterpret_cast<T*>(smem_raw);    // J x R
+    VT* tile = reinterpret_cast<VT*>(smem_raw);    // J x NV vectors
     const int64_t i0 = (int64_t)blockIdx.x * R;
     const int nthr = blockDim.x;
     T acc[NC][R];
@@ -147,14 +158,19 @@ __global__ void __launch_bounds__(512, 1) k_sketch_apply(
     for (int64_t j0 = 0; j0 < n; j0 += J) {
         const int jlen = (int)min((int64_t)J, n - j0);
         __syncthreads();
-        // load: thread handles column jj, all R rows (coalesced along jj)
         for (int jj = threadIdx.x; jj < jlen; jj += nthr) {
             T v[R];
 #pragma unroll
             for (int r = 0; r < R; ++r)
                 v[r] = (i0 + r < n) ? __ldcs(&A[(i0 + r) * lda + j0 + jj]) : T(0);
+            const int sw = (jj >> 1) & 3;
 #pragma unroll
-            for (int r = 0; r < R; ++r) tile[(int64_t)jj * R + r] = v[r];
+            for (int q = 0; q < NV; ++q) {
+                VT x;
+                if constexpr (VW == 4) x = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                else x = make_double2(v[2 * q], v[2 * q + 1]);
+                tile[jj * NV + (q ^ sw)] = x;
+            }
         }
         __syncthreads();
         const int32_t jend = (int32_t)(j0 + jlen);
@@ -163,16 +179,24 @@ __global__ void __launch_bounds__(512, 1) k_sketch_apply(
             int e = cur[k];
             const int ee = end[k];
             while (e < ee) {
-                int32_t v = __ldg(&ent[e]);
-                int32_t j = v >> 1;
+                const int32_t v = __ldg(&ent[e]);
+                const int32_t j = v >> 1;
                 if (j >= jend) break;
-                const T* src = tile + (int64_t)(j - j0) * R;
-                if (v & 1) {
+                const int jl = j - (int32_t)j0;
+                const int sw = (jl >> 1) & 3;
+                const T sg = (v & 1) ? T(-1) : T(1);
 #pragma unroll
-                    for (int r = 0; r < R; ++r) acc[k][r] -= src[r];
-                } else {
-#pragma unroll
-                    for (int r = 0; r < R; ++r) acc[k][r] += src[r];
+                for (int q = 0; q < NV; ++q) {
+                    const VT x = tile[jl * NV + (q ^ sw)];
+                    if constexpr (VW == 4) {
+                        acc[k][4 * q + 0] = fma(sg, x.x, acc[k][4 * q + 0]);
+                        acc[k][4 * q + 1] = fma(sg, x.y, acc[k][4 * q + 1]);
+                        acc[k][4 * q + 2] = fma(sg, x.z, acc[k][4 * q + 2]);
+                        acc[k][4 * q + 3] = fma(sg, x.w, acc[k][4 * q + 3]);
+                    } else {
+                        acc[k][2 * q + 0] = fma(sg, x.x, acc[k][2 * q + 0]);
+                        acc[k][2 * q + 1] = fma(sg, x.y, acc[k][2 * q + 1]);
+                    }
                 }
                 ++e;
             }
@@ -192,13 +216,18 @@ template <typename T, int R>
 msp_status launch_sketch_apply_r(msp_ctx* ctx, const T* A, int64_t lda, int64_t n,
                                  int64_t s_pad, const int32_t* ptr, const int32_t* ent,
                                  T scale, T* C) {
-    // s_pad is a multiple of 128: the smallest NC in {1, 2, 4} with
-    // s_pad / NC <= 512 threads gives a whole number of warps per block.
-    int nc = 1;
-    while (s_pad / nc > 512) nc *= 2;
-    const int threads = (int)(s_pad / nc);
-    if (nc > 4 || threads * nc != s_pad || threads % 32 != 0)
+    // s_pad is a multiple of 128: the smallest NC with s_pad / NC a multiple
+    // of 32 and at most 256 threads (two blocks per SM fit)
+    int nc = 0;
+    for (int cand : {1, 2, 3, 4}) {
+        if (s_pad % cand == 0 && (s_pad / cand) % 32 == 0 && s_pad / cand <= 256) {
+            nc = cand;
+            break;
+        }
+    }
+    if (nc == 0)
         return msp_set_error(ctx, MSP_EINVAL, "sketch: unsupported s_pad %lld", (long long)s_pad);
+    const int threads = (int)(s_pad / nc);
     const int J = (int)((64 * 1024) / (sizeof(T) * R));
     size_t smem = (size_t)J * R * sizeof(T);
     dim3 grid((unsigned)((n + R - 1) / R));
@@ -214,6 +243,7 @@ msp_status launch_sketch_apply_r(msp_ctx* ctx, const T* A, int64_t lda, int64_t 
     switch (nc) {
         MSP_SK_CASE(1)
         MSP_SK_CASE(2)
+        MSP_SK_CASE(3)
         MSP_SK_CASE(4)
         default:
             return msp_set_error(ctx, MSP_EINVAL, "sketch: unsupported s_pad %lld",
@@ -297,8 +327,11 @@ msp_status msp_build_csr(msp_ctx* ctx, int64_t n, int64_t rows, int gamma,
 msp_status msp_sketch_apply(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t n,
                             int64_t lda, int64_t s_pad, const int32_t* ptr,
                             const int32_t* ent, int gamma, void* C) {
-    // accumulators per thread: R rows x NC (<= 4) columns, kept <= 64 registers
+    // accumulators per thread: R rows x NC columns; R = 4 vectors of 16 bytes
     double scale = 1.0 / sqrt((double)gamma);
+    if (s_pad > 1024)
+        return msp_set_error(ctx, MSP_EINVAL, "sketch: s_pad %lld above 1024 is not supported",
+                             (long long)s_pad);
     if (dt == MSP_F32)
         return launch_sketch_apply_r<float, 16>(ctx, (const float*)A, lda, n, s_pad, ptr, ent,
                                                 (float)scale, (float*)C);

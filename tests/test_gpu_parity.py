@@ -174,6 +174,48 @@ def test_solve_mixed_rbf_to_1e10(ctx, n):
     assert info["refine_steps"] >= 2
 
 
+@pytest.mark.parametrize("n", [1000, 2048 + 77])
+def test_packed_and_dense_A_pass_agree(ctx, n):
+    # The sketch keeps a packed copy of A's upper 128 x 128 tiles; msp_solve uses
+    # it when given the sketched A and the dense row pass for any other pointer
+    # (here a copy). Both must converge to the same solution; ragged n exercises
+    # the zero-padded last tile row/column.
+    w = make_workload("rbf", seed=7, n=n)
+    A_dev = _cuda(w.A.astype(np.float32))
+    A_copy = A_dev.clone()
+    sk = ctx.sketch(A_dev, 128, 8, SEED)
+    f = ctx.nystrom(sk, w.lam, 0.0, phi=0)
+    b = _cuda(w.b)
+    xp, ip = ctx.solve(f, A_dev, b, w.lam, precision="mixed", tol=1e-10, max_inner=0,
+                       profile=1)
+    xd, idn = ctx.solve(f, A_copy, b, w.lam, precision="mixed", tol=1e-10, max_inner=0,
+                        profile=1)
+    assert ip["rel_resid"] <= 1e-10 and idn["rel_resid"] <= 1e-10
+    xs = reference.solve_dense(w.A.astype(np.float32).astype(np.float64), w.b, w.lam)
+    for x in (xp, xd):
+        assert np.linalg.norm(x.cpu().numpy() - xs) <= 1e-7 * np.linalg.norm(xs)
+    assert abs(ip["outer_iters"] - idn["outer_iters"]) <= 2 + 0.05 * idn["outer_iters"]
+
+
+@pytest.mark.parametrize("n", [257, 4096])
+def test_fp64_residual_operator(ctx, n):
+    # y = (A + lam I) x with FP64 accumulation from FP32 A (the refinement's
+    # residual operator): exact widening of each A entry (zeros, subnormals
+    # flushed, wide magnitudes) and FP64 sums, vs a host FP64 product.
+    rng = np.random.default_rng(n)
+    A = (rng.standard_normal((n, n)) * np.exp(rng.uniform(-30, 30, (n, n)))).astype(np.float32)
+    A[rng.random((n, n)) < 0.05] = 0.0
+    A[0, :8] = np.float32(1e-42)          # subnormals
+    A_dev = _cuda(A)
+    x = rng.standard_normal(n)
+    y = ctx.matvec_f64(A_dev, _cuda(x), lam=0.37).cpu().numpy()
+    A64 = A.astype(np.float64)
+    A64[np.abs(A64) < np.finfo(np.float32).tiny] = 0.0
+    ref = A64 @ x + 0.37 * x
+    scale = np.abs(A64) @ np.abs(x) + 0.37 * np.abs(x)
+    assert np.all(np.abs(y - ref) <= 4 * n * 2.0 ** -53 * scale)
+
+
 def test_solve_plain_fp32_rbf(ctx):
     # plain FP32 (no refinement): the FP32 recurrence reaches 1e-5 but the true
     # residual stalls near u32 * |A| |x| / |b|; check the normwise backward error
