@@ -235,6 +235,25 @@ MSP_API msp_status msp_solve_full(msp_ctx* ctx, const void* A, msp_dtype dtype, 
                           int gamma_phi, uint64_t seed, const msp_opts* opts,
                           msp_info* info);
 
+/* ------------------------------------------------- a11: RBF and adjoint */
+
+/* The Gaussian (RBF) kernel matrix of kernel ridge regression (Section 3,
+ * the system (K + lambda I) x = y): K_ij = exp(-|p_i - p_j|^2 / (2 ell^2))
+ * for n points in R^dim (1 <= dim <= 4), points: device FP64 row-major n x dim.
+ * Computed in FP32 from the points rounded to FP32; K: device FP32 row-major,
+ * ldk >= n (K_ii = 1 exactly). */
+MSP_API msp_status msp_rbf_kernel(msp_ctx* ctx, const double* points, int64_t n, int dim,
+                                  double ell, float* K, int64_t ldk);
+
+/* Adjoint of the RBF length scale for x = (K + lambda I)^{-1} b: with the
+ * adjoint solution a = (K + lambda I)^{-1} g of a loss L with dL/dx = g,
+ * dL/d ell = -a^T (dK/d ell) x, dK_ij/d ell = K_ij d_ij^2 / ell^3. Each
+ * pair's term is recomputed from the points (dK is never formed); FP32
+ * pair terms with compensated sums, FP64 row totals. a, x: device FP64
+ * vectors of n; out: device FP64 scalar (written when the work completes). */
+MSP_API msp_status msp_rbf_grad_ell(msp_ctx* ctx, const double* points, int64_t n, int dim,
+                                    double ell, const double* a, const double* x, double* out);
+
 /* ----------------------------------------------------- helpers (tests) */
 
 /* y = (A + lambda I) x, FP64 accumulation, FP64 x and y; A FP32 or FP64.

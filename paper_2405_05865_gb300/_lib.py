@@ -72,6 +72,8 @@ _SIGS = {
                                  C.c_double, I64, C.c_int, C.c_uint64, C.POINTER(MspOpts),
                                  C.POINTER(MspInfo)]),
     "msp_matvec_f64": (C.c_int, [P, P, C.c_int, I64, I64, C.c_double, P, P]),
+    "msp_rbf_kernel": (C.c_int, [P, P, I64, C.c_int, C.c_double, P, I64]),
+    "msp_rbf_grad_ell": (C.c_int, [P, P, I64, C.c_int, C.c_double, P, P, P]),
 }
 
 _lib = None

@@ -196,6 +196,24 @@ class Context:
                                                   C.byref(o), C.byref(info)))
         return x, info.as_dict()
 
+    # -- a11: RBF kernels and the adjoint of the length scale
+    def rbf_kernel(self, points: torch.Tensor, ell: float) -> torch.Tensor:
+        if not points.is_cuda or points.dtype != torch.float64 or points.dim() != 2:
+            raise ValueError("points must be a CUDA float64 (n, dim) tensor")
+        points = points.contiguous()
+        n, dim = points.shape
+        K = torch.empty((n, n), dtype=torch.float32, device=self.device)
+        L.check(self.ptr, self.lib.msp_rbf_kernel(self.ptr, _ptr(points), n, dim, float(ell), _ptr(K), n))
+        return K
+
+    def rbf_grad_ell(self, points: torch.Tensor, ell: float, a: torch.Tensor, x: torch.Tensor) -> torch.Tensor:
+        points = points.contiguous()
+        n, dim = points.shape
+        out = torch.empty((), dtype=torch.float64, device=self.device)
+        L.check(self.ptr, self.lib.msp_rbf_grad_ell(self.ptr, _ptr(points), n, dim, float(ell),
+                                                    _ptr(a.contiguous()), _ptr(x.contiguous()), _ptr(out)))
+        return out
+
     def matvec_f64(self, A: torch.Tensor, x: torch.Tensor, lam: float = 0.0) -> torch.Tensor:
         n, lda, dt = _check_matrix(A)
         y = torch.empty_like(x)
