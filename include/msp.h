@@ -254,6 +254,32 @@ MSP_API msp_status msp_rbf_kernel(msp_ctx* ctx, const double* points, int64_t n,
 MSP_API msp_status msp_rbf_grad_ell(msp_ctx* ctx, const double* points, int64_t n, int dim,
                                     double ell, const double* a, const double* x, double* out);
 
+/* No-allocation variant of msp_rbf_grad_ell (the paper has no counterpart:
+ * this is an interface for callers, not a step of the method). Some callers
+ * cannot allocate device memory at the point where they need the gradient:
+ * a framework whose allocator owns the whole device, a time-critical loop
+ * that forbids allocation after start-up, or code that must not disturb the
+ * memory state of a pool it does not own. This entry point takes no context
+ * and allocates nothing: the block partials and the reduction counter live in
+ * a fixed array inside the library, and the result is identical to
+ * msp_rbf_grad_ell's (same kernel, same fixed-order reduction).
+ *   - points, a, x, out: device memory owned by the caller, as for
+ *     msp_rbf_grad_ell; stream: the cudaStream_t to run on (NULL = legacy
+ *     default stream); the current device is used.
+ *   - n <= 524288 (one scratch slot per 8 points); larger n returns
+ *     MSP_EINVAL with a message from msp_last_error(NULL).
+ *   - The first call on each device resolves the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture
+ *     on that device.
+ *   - Every call on a device shares the one array, which keeps the last
+ *     call's contents; each call clears the counter it needs on its stream.
+ *     Calls whose work overlaps on the GPU (different streams, or several
+ *     host threads) race on the array: serialise them.
+ *   - It calls no cudaMalloc, cudaFree or allocating library routine. */
+MSP_API msp_status msp_rbf_grad_ell_static(const double* points, int64_t n, int dim, double ell,
+                                           const double* a, const double* x, double* out,
+                                           void* stream);
+
 /* ----------------------------------------------------- helpers (tests) */
 
 /* y = (A + lambda I) x, FP64 accumulation, FP64 x and y; A FP32 or FP64.

@@ -74,6 +74,7 @@ _SIGS = {
     "msp_matvec_f64": (C.c_int, [P, P, C.c_int, I64, I64, C.c_double, P, P]),
     "msp_rbf_kernel": (C.c_int, [P, P, I64, C.c_int, C.c_double, P, I64]),
     "msp_rbf_grad_ell": (C.c_int, [P, P, I64, C.c_int, C.c_double, P, P, P]),
+    "msp_rbf_grad_ell_static": (C.c_int, [P, I64, C.c_int, C.c_double, P, P, P, P]),
 }
 
 _lib = None

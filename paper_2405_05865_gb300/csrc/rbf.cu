@@ -19,6 +19,7 @@
 #include "msp_internal.cuh"
 
 #include <cmath>
+#include <mutex>
 
 namespace {
 
@@ -137,9 +138,70 @@ __global__ void __launch_bounds__(256) k_rbf_grad_ell(const double* __restrict__
     *out = -all * scale;
 }
 
+// ---------------------------------------------------- no-allocation variant
+//
+// Scratch of msp_rbf_grad_ell_static: word 0 holds the last-block counter,
+// the FP64 block partials start at element 32 (256 bytes in). The grid has
+// one block per 8 points, so n is limited to 8 * kStaticMaxBlocks. Every GPU
+// that loads the library holds this array (about 512 KiB) until exit.
+constexpr int64_t kStaticMaxBlocks = 65536;
+constexpr int64_t kStaticMaxN = 8 * kStaticMaxBlocks;
+static __device__ __align__(256) double g_rbf_grad_static[32 + kStaticMaxBlocks];
+
+std::mutex g_static_mu;
+double* g_static_ptr[64] = {};   // device address of the array, per device
+
 }  // namespace
 
 extern "C" {
+
+msp_status msp_rbf_grad_ell_static(const double* points, int64_t n, int dim, double ell,
+                                   const double* a, const double* x, double* out, void* stream) {
+    if (!points || !a || !x || !out || n < 1 || dim < 1 || dim > 4 || !(ell > 0.0))
+        return msp_set_error(nullptr, MSP_EINVAL,
+                             "rbf_grad_ell_static: need n >= 1, 1 <= dim <= 4, ell > 0, non-NULL arrays");
+    if (n > kStaticMaxN)
+        return msp_set_error(nullptr, MSP_EINVAL,
+                             "rbf_grad_ell_static: n = %lld exceeds the static scratch limit n <= %lld",
+                             (long long)n, (long long)kStaticMaxN);
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return msp_set_error(nullptr, MSP_ECUDA, "rbf_grad_ell_static: no current CUDA device");
+    }
+    double* scratch = nullptr;
+    {
+        // set-up, once per device, with that device current: the host-side
+        // name of the array is not a device address
+        std::lock_guard<std::mutex> lock(g_static_mu);
+        if (!g_static_ptr[dev]) {
+            void* p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_rbf_grad_static);
+            if (e != cudaSuccess || !p) {
+                cudaGetLastError();
+                return msp_set_error(nullptr, MSP_ECUDA, "rbf_grad_ell_static: cudaGetSymbolAddress: %s",
+                                     cudaGetErrorString(e));
+            }
+            g_static_ptr[dev] = (double*)p;
+        }
+        scratch = g_static_ptr[dev];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned int* counter = reinterpret_cast<unsigned int*>(scratch);
+    // the counter must start at zero (the array keeps the last call's contents)
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return msp_set_error(nullptr, MSP_ECUDA, "rbf_grad_ell_static: %s", cudaGetErrorString(e));
+    }
+    const unsigned blocks = (unsigned)((n + 7) / 8);
+    k_rbf_grad_ell<<<blocks, 256, 0, st>>>(points, n, dim, (float)(1.0 / (2.0 * ell * ell)), a, x,
+                                           scratch + 32, counter, out, 1.0 / (ell * ell * ell));
+    e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return msp_set_error(nullptr, MSP_ECUDA, "rbf_grad_ell_static: launch: %s", cudaGetErrorString(e));
+    return MSP_OK;
+}
 
 msp_status msp_rbf_kernel(msp_ctx* ctx, const double* points, int64_t n, int dim, double ell,
                           float* K, int64_t ldk) {
