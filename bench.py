@@ -9,7 +9,9 @@ bounds the normwise backward error by 1e-10).
 Workload (default): RBF kernel K_ij = exp(-|p_i - p_j|^2 / (2 l^2)) on n=16384
 seeded uniform points in [0,1]^3, l = 0.1, lam = 1e-2, K stored FP32 (1.07 GB,
 larger than L2, so no flush is needed between steps), sketch s = 1024 with 8
-nonzeros per row of Pi, level-2 sketch phi = 4 s, b ~ N(0, I).
+nonzeros per row of Pi, level-2 embedding Phi = I (M2 = C^T C + lam W exactly,
+direct level-2 solve), FP32 correction solves to 1e-4 per refinement step,
+b ~ N(0, I).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl msp|reference]
 
@@ -52,13 +54,14 @@ def parse():
     ap.add_argument("--impl", default="msp", choices=["msp", "reference"])
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--s", type=int, default=1024)
-    ap.add_argument("--phi-mult", type=int, default=4)
+    ap.add_argument("--phi-mult", type=int, default=0, help="phi = mult * s; 0 selects Phi = I")
     ap.add_argument("--inner-tol", type=float, default=1e-6)
-    ap.add_argument("--refine-tol", type=float, default=1e-6)
-    ap.add_argument("--max-inner", type=int, default=50)
+    ap.add_argument("--refine-tol", type=float, default=1e-4)
+    ap.add_argument("--max-inner", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-schatten", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=5, help="level-1 iterations in the CPU sample")
     return ap.parse_args()
 
@@ -289,6 +292,28 @@ def run_msp(args, rank, world, local):
                 "rel_resid_max": max(i["rel_resid"] for i in inf32),
                 "outer_iters": inf32[-1]["outer_iters"], "ms_per_step": ms32 / args.steps}
 
+    # Schatten-1 norm of the same PSD kernel matrix (tr K = n exactly) by
+    # Hutchinson with 256 Rademacher probes
+    sch = None
+    if not args.no_schatten:
+        ctx.schatten(A, p=1.0, probes=256)
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        est = se = 0.0
+        for _ in range(args.steps):
+            est, se = ctx.schatten(A, p=1.0, probes=256)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        sms = e0.elapsed_time(e1) / args.steps
+        flops = 2.0 * n * n * 256 / 2          # packed symmetric tiles: half of 2 n^2 m
+        sch = {"estimate": est, "exact": float(n), "std_err": se,
+               "rel_err": abs(est - n) / n, "ms_per_estimate": sms,
+               "estimates_per_s": 1000.0 / sms, "tflops_fp32": flops / (sms * 1e-3) / 1e12,
+               "probes": 256}
+
     # roofline of the dominant kernel: the A pass q = (A + lam I) p
     g_ms = sum(i["gemv_ms"] for i in infos)
     g_n = sum(i["gemv_launches"] for i in infos)
@@ -345,6 +370,7 @@ def run_msp(args, rank, world, local):
                         "outer_iters": last["outer_iters"], "inner_iters": last["inner_iters"],
                         "refine_steps": last["refine_steps"]},
            "fp32_plain": fp32,
+           "schatten1": sch,
            "phase_ms_per_step": {"a_pass": g_ms / args.steps, "level2": l2_ms / args.steps,
                                  "fp64_residual": r_ms / args.steps},
            "roofline": {"bound": "hbm", "kernel": "k_symv_packed (q = (A + lam I) p, packed upper tiles)",

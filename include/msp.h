@@ -235,6 +235,29 @@ MSP_API msp_status msp_solve_full(msp_ctx* ctx, const void* A, msp_dtype dtype, 
                           int gamma_phi, uint64_t seed, const msp_opts* opts,
                           msp_info* info);
 
+/* ------------------------------------------------ a10: Schatten-1 norm */
+
+/* Schatten-p norm |A|_p = (sum_i sigma_i^p)^{1/p} of a PSD matrix A
+ * (Section 3.2, the norm estimators built on stochastic trace estimation).
+ * Only p = 1 is implemented: for PSD A, |A|_1 = tr(A), estimated by
+ * Hutchinson's estimator (1/m) sum_j g_j^T A g_j with m = `probes` Rademacher
+ * probes (row i of probe j negative iff the top bit of
+ * draw(seed, 7 + 2 (j / 256), i, j mod 256) is set). A: device FP32,
+ * row-major n x n, lda >= n, symmetric; read once as packed upper tiles.
+ * probes: a multiple of 64 in [64, 4096]. Outputs (host scalars, any may be
+ * NULL): norm = the estimate of |A|_1, norm_pow = |A|_1^p (the same for
+ * p = 1), std_err = sample standard deviation of the q_j / sqrt(m).
+ * Other p return MSP_EINVAL (they need shifted MSP solves). */
+MSP_API msp_status msp_schatten(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n,
+                                int64_t lda, double p, int64_t probes, uint64_t seed,
+                                double* norm, double* norm_pow, double* std_err);
+
+/* The per-probe quadratic forms q_j = g_j^T A g_j of msp_schatten (device
+ * FP64 array of `probes`), each a sum over the packed tiles of 128-term FP32
+ * tile products combined in FP64. */
+MSP_API msp_status msp_hutchinson(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n,
+                                  int64_t lda, int64_t probes, uint64_t seed, double* q);
+
 /* ------------------------------------------------- a11: RBF and adjoint */
 
 /* The Gaussian (RBF) kernel matrix of kernel ridge regression (Section 3,

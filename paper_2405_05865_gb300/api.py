@@ -196,6 +196,22 @@ class Context:
                                                   C.byref(o), C.byref(info)))
         return x, info.as_dict()
 
+    # -- a10: Schatten-1 norm (PSD A) by Hutchinson
+    def schatten(self, A: torch.Tensor, p: float = 1.0, probes: int = 256,
+                 seed: int = DEFAULT_SEED) -> tuple[float, float]:
+        """(estimate of |A|_p, standard error); p = 1 only."""
+        n, lda, dt = _check_matrix(A)
+        v, vp, se = C.c_double(), C.c_double(), C.c_double()
+        L.check(self.ptr, self.lib.msp_schatten(self.ptr, _ptr(A), dt, n, lda, p, probes, seed,
+                                                C.byref(v), C.byref(vp), C.byref(se)))
+        return v.value, se.value
+
+    def hutchinson(self, A: torch.Tensor, probes: int = 256, seed: int = DEFAULT_SEED) -> torch.Tensor:
+        n, lda, dt = _check_matrix(A)
+        q = torch.empty(probes, dtype=torch.float64, device=self.device)
+        L.check(self.ptr, self.lib.msp_hutchinson(self.ptr, _ptr(A), dt, n, lda, probes, seed, _ptr(q)))
+        return q
+
     # -- a11: RBF kernels and the adjoint of the length scale
     def rbf_kernel(self, points: torch.Tensor, ell: float) -> torch.Tensor:
         if not points.is_cuda or points.dtype != torch.float64 or points.dim() != 2:

@@ -1,0 +1,64 @@
+"""Schatten-1 norm of a PSD matrix by Hutchinson (row a10): per-probe parity
+of q_j = g_j^T A g_j with the FP64 oracle on the same probes, and the estimate
+against the exact sum of singular values."""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import hutchinson, reference
+from workloads import make_workload, outlier_spectrum, spectrum_matrix
+
+pytestmark = pytest.mark.gpu
+SEED = 0x4D5350
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2405_05865_gb300 import Context
+    c = Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("n,m", [(200, 64), (1000 + 37, 128), (2048, 320)])
+def test_quadratic_forms_match_oracle(ctx, n, m):
+    sig = outlier_spectrum(n, max(4, n // 64))
+    A = spectrum_matrix(sig, seed=n).astype(np.float32)
+    q = ctx.hutchinson(torch.from_numpy(A).cuda(), probes=m, seed=SEED).cpu().numpy()
+    G = hutchinson.probes(n, m, SEED)
+    A64 = A.astype(np.float64)
+    qo = hutchinson.quadratic_forms(A64, G)
+    # FP32 128-term tile sums + 128-term contraction, FP64 across tiles:
+    # |dq_j| <= c u32 sum_ik |A_ik| (|g_i| = |g_k| = 1)
+    bound = 512 * 2.0 ** -24 * np.abs(A64).sum()
+    assert np.all(np.abs(q - qo) <= bound)
+
+
+def test_schatten1_estimate_outlier_spectrum(ctx):
+    # 2048 x 2048 PSD, 32 outliers 1e4 -> 1e2, tail i^-1.5: |A|_1 = sum sigma
+    n = 2048
+    sig = outlier_spectrum(n, 32)
+    A = spectrum_matrix(sig, seed=7)
+    est, se = ctx.schatten(torch.from_numpy(A.astype(np.float32)).cuda(), p=1.0, probes=256)
+    exact = reference.schatten(sig, 1.0)
+    sd = np.sqrt(hutchinson.rademacher_variance(A) / 256)
+    assert abs(est - exact) <= 4 * sd
+    assert se == pytest.approx(sd, rel=0.3)
+
+
+def test_schatten1_rbf_trace_is_n(ctx):
+    # RBF kernel: K_ii = 1, so |K|_1 = tr K = n exactly
+    w = make_workload("rbf", seed=3, n=4096)
+    K = torch.from_numpy(w.A.astype(np.float32)).cuda()
+    est, se = ctx.schatten(K, p=1.0, probes=256)
+    assert abs(est - 4096) <= 4 * se + 1e-9 * 4096
+
+
+def test_schatten_rejects_other_p(ctx):
+    from paper_2405_05865_gb300 import MspError
+    A = torch.eye(128, dtype=torch.float32, device="cuda")
+    with pytest.raises(MspError) as e:
+        ctx.schatten(A, p=0.5)
+    assert e.value.status == 1

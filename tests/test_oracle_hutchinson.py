@@ -1,0 +1,46 @@
+"""Pins for the oracle's Hutchinson estimator: exact identities of Rademacher
+probes and the estimator's mean and variance."""
+
+import numpy as np
+import pytest
+
+from oracle import hutchinson, prng, reference
+from workloads import outlier_spectrum, spectrum_matrix
+
+
+def test_probes_are_rademacher_and_deterministic():
+    G = hutchinson.probes(200, 300, seed=9)
+    assert set(np.unique(G)) == {-1.0, 1.0}
+    assert np.array_equal(G, hutchinson.probes(200, 300, seed=9))
+    assert abs(G.mean()) < 4 / np.sqrt(G.size)
+    # probe 256 uses the next stream pair
+    assert G[5, 256] == (-1 if prng.draw(9, 9, 5, 0) >> 63 else 1)
+
+
+def test_diagonal_matrix_is_exact_for_every_probe():
+    d = np.random.default_rng(1).random(150)
+    G = hutchinson.probes(150, 40, seed=2)
+    q = hutchinson.quadratic_forms(np.diag(d), G)
+    assert np.allclose(q, d.sum(), rtol=1e-14)
+
+
+def test_quadratic_forms_match_loops():
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((30, 30))
+    A = A + A.T
+    G = hutchinson.probes(30, 5, seed=4)
+    for j in range(5):
+        ref = sum(G[i, j] * A[i, k] * G[k, j] for i in range(30) for k in range(30))
+        assert hutchinson.quadratic_forms(A, G)[j] == pytest.approx(ref, rel=1e-12)
+
+
+def test_unbiased_with_closed_form_variance():
+    # many independent probes: mean within 4 sigma of tr(A), sample variance
+    # close to 2(|A|_F^2 - sum A_ii^2)
+    sig = outlier_spectrum(120, 6)
+    A = spectrum_matrix(sig, seed=5)
+    G = hutchinson.probes(120, 4000, seed=6)
+    q = hutchinson.quadratic_forms(A, G)
+    var = hutchinson.rademacher_variance(A)
+    assert abs(q.mean() - reference.schatten(sig, 1.0)) <= 4 * np.sqrt(var / q.size)
+    assert q.var(ddof=1) == pytest.approx(var, rel=0.1)
