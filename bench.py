@@ -145,16 +145,17 @@ def measured_peaks() -> tuple[float, str]:
         return 6800.0, "fallback"
 
 
-def gemv_traffic_bytes(n: int) -> float | None:
-    """DRAM bytes per A-pass launch from the committed ncu summary, if it was taken
-    on the current kernel source (sha256 of csrc/krylov.cu matches)."""
+def symv_traffic_bytes(n: int) -> float | None:
+    """DRAM bytes per packed A-pass launch from the committed ncu summary
+    (profiles/traffic.json), if it was taken on the current kernel source
+    (sha256 of csrc/symv.cu matches); scaled from the captured n by n^2."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
-    src = os.path.join(ROOT, "paper_2405_05865_gb300", "csrc", "krylov.cu")
+    src = os.path.join(ROOT, "paper_2405_05865_gb300", "csrc", "symv.cu")
     try:
         with open(p) as fh:
-            d = json.load(fh)["gemv"]
+            d = json.load(fh)["k_symv_packed"]
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if d.get("krylov_cu_sha256") != sha:
+        if d.get("symv_cu_sha256") != sha:
             return None
         # scale the captured case to this n (traffic grows with n^2)
         return float(d["bytes_per_launch"]) * (n / d["n"]) ** 2
@@ -325,7 +326,7 @@ def run_msp(args, rank, world, local):
     alg_bytes = 4.0 * n * (n + 1) / 2 + 3 * 4.0 * n
     achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
     peak, peak_src = measured_peaks()
-    traffic = gemv_traffic_bytes(n)
+    traffic = symv_traffic_bytes(n)
 
     # end to end through the C ABI with host (pinned) buffers
     e2e = None

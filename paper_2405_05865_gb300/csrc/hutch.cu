@@ -40,8 +40,10 @@ __global__ void k_probes(int64_t n, int64_t n_pad, int m, uint64_t seed, float* 
 }
 
 __device__ inline void tile_coords_h(int t, int nt, int& I, int& J) {
-    double a = 2.0 * nt + 1.0;
-    int i = (int)((a - sqrt(a * a - 8.0 * t)) * 0.5);
+    // FP32 estimate (the FP64 pipe is scarce on this part), then exact
+    // integer correction
+    const float a = 2.0f * nt + 1.0f;
+    int i = (int)((a - sqrtf(fmaxf(a * a - 8.0f * t, 0.0f))) * 0.5f);
     if (i < 0) i = 0;
     if (i > nt - 1) i = nt - 1;
     while (i > 0 && (long long)i * nt - (long long)i * (i - 1) / 2 > t) --i;

@@ -684,14 +684,16 @@ msp_status launch_level2_pl(msp_ctx* ctx, L2Args<T>& a, int G) {
 
 template <typename T>
 msp_status launch_level2(msp_ctx* ctx, L2Args<T>& a, int G) {
+    // one instantiation per padded sketch size (multiples of 128 up to 1024)
     switch (a.s_pad) {
         case 128: return launch_level2_pl<T, 4>(ctx, a, G);
         case 256: return launch_level2_pl<T, 8>(ctx, a, G);
+        case 384: return launch_level2_pl<T, 12>(ctx, a, G);
         case 512: return launch_level2_pl<T, 16>(ctx, a, G);
+        case 640: return launch_level2_pl<T, 20>(ctx, a, G);
+        case 768: return launch_level2_pl<T, 24>(ctx, a, G);
+        case 896: return launch_level2_pl<T, 28>(ctx, a, G);
         case 1024: return launch_level2_pl<T, 32>(ctx, a, G);
-        case 2048:
-            if constexpr (sizeof(T) == 4) return launch_level2_pl<T, 64>(ctx, a, G);
-            break;
         default: break;
     }
     return msp_set_error(ctx, MSP_EINVAL, "level-2: unsupported padded sketch size %lld",

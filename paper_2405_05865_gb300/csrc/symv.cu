@@ -106,8 +106,10 @@ __device__ inline uint64_t policy_evict_first() {
 // tile index -> (I, J), I <= J, row-major over the upper triangle
 __device__ inline void tile_coords(int t, int nt, int& I, int& J) {
     // I = largest i with start(i) <= t, start(i) = i*nt - i*(i-1)/2
-    double a = 2.0 * nt + 1.0;
-    int i = (int)((a - sqrt(a * a - 8.0 * t)) * 0.5);
+    // FP32 estimate (the FP64 pipe is scarce on this part), then exact
+    // integer correction
+    const float a = 2.0f * nt + 1.0f;
+    int i = (int)((a - sqrtf(fmaxf(a * a - 8.0f * t, 0.0f))) * 0.5f);
     if (i < 0) i = 0;
     if (i > nt - 1) i = nt - 1;
     while (i > 0 && (long long)i * nt - (long long)i * (i - 1) / 2 > t) --i;
@@ -301,11 +303,16 @@ __global__ void __launch_bounds__(kSymvThreads, 1) k_symv_packed(SymvArgs a) {
             }
             rv[0] += __shfl_xor_sync(0xffffffffu, rv[0], 1);
             const float w_tile = (I == J) ? 1.f : 2.f;
+            float tdot = 0.f;
             if ((lane & 1) == 0) {
                 const int r = warp + kConsumerWarps * (lane >> 1);
                 a.part[(int64_t)J * a.n_pad + (int64_t)I * kTile + r] = rv[0];
-                acc_dot += (double)w_tile * (double)pI[r] * (double)rv[0];
+                tdot = pI[r] * rv[0];
             }
+            // this warp's 16 rows of p_I^T A_IJ p_J: FP32 within the tile, one
+            // FP64 add per warp and tile
+            tdot = msp::warp_sum(tdot);
+            if (lane == 0) acc_dot += (double)(w_tile * tdot);
             // stage (tile and column buffer) consumed: release it to the producer
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);

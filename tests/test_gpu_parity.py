@@ -174,6 +174,18 @@ def test_solve_mixed_rbf_to_1e10(ctx, n):
     assert info["refine_steps"] >= 2
 
 
+@pytest.mark.parametrize("s", [300, 640])
+def test_solve_ragged_sketch_sizes(ctx, s):
+    # padded sketch sizes that are not powers of two (s_pad = 384, 640)
+    w = make_workload("rbf", seed=8, n=2500)
+    A_dev = _cuda(w.A.astype(np.float32))
+    sk = ctx.sketch(A_dev, s, 8, SEED)
+    f = ctx.nystrom(sk, w.lam, 0.0, phi=0)
+    x, info = ctx.solve(f, A_dev, _cuda(w.b), w.lam, precision="mixed", tol=1e-10, max_inner=0)
+    rr = reference.rel_residual(w.A.astype(np.float32).astype(np.float64), x.cpu().numpy(), w.b, w.lam)
+    assert info["rel_resid"] <= 1e-10 and rr <= 1.2e-10
+
+
 @pytest.mark.parametrize("n", [1000, 2048 + 77])
 def test_packed_and_dense_A_pass_agree(ctx, n):
     # The sketch keeps a packed copy of A's upper 128 x 128 tiles; msp_solve uses
