@@ -22,4 +22,6 @@ Modules
               backward error, effective dimension, Schatten-p closed forms
 ``hutchinson`` Hutchinson trace estimate of tr(A) = |A|_1 for PSD A
 ``adjoint``   gradients of L = g^T x, x = (K_theta + lam I)^{-1} b
+``batch``     batches of instances with several right-hand sides each: the
+              definition (independent per-column solves) as a loop
 """

@@ -17,4 +17,7 @@ from .generators import (  # noqa: F401
     Workload,
     make_workload,
     WORKLOADS,
+    BatchSpec,
+    batch_specs,
+    batch_instance,
 )

@@ -176,4 +176,43 @@ def make_workload(name: str, seed: int = 0, n: int | None = None,
     raise ValueError(f"unknown workload {name!r}")
 
 
+@dataclasses.dataclass
+class BatchSpec:
+    """One instance of the batched workload: the RBF kernel of ``rbf_kernel`` on
+    n uniform points in [0,1]^3 with length scale ell, (K + lam I) X = B with
+    B ~ N(0, I) of shape (n, m), sketch size s."""
+    n: int
+    ell: float
+    lam: float
+    s: int
+    m: int
+    seed: int
+
+
+def batch_specs(seed: int, count: int = 64, n_lo: int = 512, n_hi: int = 8192, m: int = 16,
+                lam: float = 1e-2, ell_lo: float = 0.05, ell_hi: float = 0.2,
+                s_max: int = 1024) -> list[BatchSpec]:
+    """``count`` instances with n ~ U{n_lo..n_hi} and ell ~ U(ell_lo, ell_hi), drawn
+    in instance order; s = min(s_max, n / 4) rounded down to a multiple of 64
+    (at least 64, at most n). Instance k draws its points and right-hand sides
+    with seed ``seed * 4096 + k + 1``."""
+    g = _rng(seed, _TAG_INSTANCE)
+    ns = g.integers(n_lo, n_hi + 1, size=count)
+    ells = g.uniform(ell_lo, ell_hi, size=count)
+    out = []
+    for k in range(count):
+        n = int(ns[k])
+        s = min(s_max, max(64, (n // 4) // 64 * 64), n)
+        out.append(BatchSpec(n, float(ells[k]), lam, s, m, seed * 4096 + k + 1))
+    return out
+
+
+def batch_instance(spec: BatchSpec, out_dtype=np.float32) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """(points, K rounded once to ``out_dtype``, B (n, m) FP64) of one instance."""
+    P = rbf_points(spec.n, spec.seed)
+    K = rbf_kernel(P, spec.ell, out_dtype=out_dtype)
+    B = _rng(spec.seed, _TAG_RHS).standard_normal((spec.n, spec.m))
+    return P, K, B
+
+
 WORKLOADS = ("outlier", "rbf", "outlier256", "householder")
