@@ -235,6 +235,73 @@ MSP_API msp_status msp_solve_full(msp_ctx* ctx, const void* A, msp_dtype dtype, 
                           int gamma_phi, uint64_t seed, const msp_opts* opts,
                           msp_info* info);
 
+/* ------------------------------------------------------ a9: batching */
+
+/* One instance of a batch: (A + lambda I) X = B with m right-hand sides,
+ * each column an independent solve of Algorithm 1 (Section 4) sharing the
+ * instance's sketch and Nystrom factor. Columns are not coupled (no block
+ * Krylov method): each has its own level-1 scalars, so a column's result
+ * equals that of a single-RHS solve up to rounding. */
+typedef struct {
+    const float* A;      /* device FP32 n x n row-major, lda >= n, symmetric   */
+    int64_t n;           /* 16 <= n <= 65536                                   */
+    int64_t lda;
+    double lambda;       /* > 0                                                */
+    double lambda0;      /* >= 0 (lambda~ = lambda + lambda0)                  */
+    const double* B;     /* device FP64 n x m column-major, ldb >= n           */
+    int64_t ldb;
+    double* X;           /* device FP64 n x m column-major, ldx >= n (output)  */
+    int64_t ldx;
+    int m;               /* 1 <= m <= 16                                       */
+    int gamma;           /* nonzeros per column of S (msp_sketch)              */
+    int64_t s;           /* sketch size, 16 <= s <= min(n, 1024)               */
+    int64_t phi;         /* level-2 embedding rows; 0 = Phi = I (msp_nystrom)  */
+    int gamma_phi;
+    int pad_;
+    uint64_t seed;
+} msp_instance;
+
+typedef struct msp_batch_s msp_batch_t;
+
+/* Set up a batch (Algorithm 1 steps 1-4 for every instance): sketch, W, M2
+ * and its factor per instance, built concurrently on worker streams owned by
+ * the context, and a copy of each A re-laid out as the tiles the batched A
+ * pass streams. The preconditioner is applied directly at level 2
+ * (y = M2^{-1} C^T r, as with opts.max_inner = 0). The A, B and X buffers
+ * named by `inst` must stay valid and unchanged in size for the life of the
+ * batch; B and X are read and written by msp_batch_solve, and A's contents
+ * are copied here (later changes to A are not seen). Requires count >= 1 and
+ * every instance valid; the whole batch fails on the first bad instance.
+ * Destroy every batch before its context. */
+MSP_API msp_status msp_batch_create(msp_ctx* ctx, int count, const msp_instance* inst,
+                                    msp_batch_t** out);
+MSP_API void msp_batch_destroy(msp_batch_t* batch);
+
+/* Solve every column of every instance (Algorithm 1 step 5 with FP64
+ * refinement in MSP_PREC_MIXED) in ONE persistent cooperative kernel launch
+ * on the context's stream: the level-1 iteration, the direct level 2, the
+ * FP64-accurate residual and every convergence decision run on the device,
+ * with no host synchronisation. X is overwritten (no initial guess).
+ * opts: tol, max_outer (per correction solve), max_refine, refine_tol,
+ * precision (MSP_PREC_MIXED or MSP_PREC_FP32); other fields are ignored.
+ * infos: NULL makes the call asynchronous (and capturable in a CUDA graph on
+ * the context's stream); otherwise `count` entries are filled after a
+ * stream synchronisation, as msp_batch_info does. The returned status is the
+ * first non-OK instance status (MSP_ENOCONV when only caps were hit). */
+MSP_API msp_status msp_batch_solve(msp_ctx* ctx, msp_batch_t* batch, const msp_opts* opts,
+                                   msp_info* infos);
+
+/* Per-instance results of the last msp_batch_solve (synchronises the
+ * context's stream): outer_iters = level-1 iterations in which the instance
+ * had an unconverged column, refine_steps, rel_resid = the largest
+ * |b_j - (A + lambda I) x_j| / |b_j| over its columns (FP64-accurate
+ * residual), lambda_tilde, shift, shift_retries, status. */
+MSP_API msp_status msp_batch_info(msp_ctx* ctx, const msp_batch_t* batch, msp_info* infos);
+
+/* msp_batch_create + msp_batch_solve + msp_batch_destroy. */
+MSP_API msp_status msp_solve_batched(msp_ctx* ctx, int count, const msp_instance* inst,
+                                     const msp_opts* opts, msp_info* infos);
+
 /* ------------------------------------------------ a10: Schatten-1 norm */
 
 /* Schatten-p norm |A|_p = (sum_i sigma_i^p)^{1/p} of a PSD matrix A

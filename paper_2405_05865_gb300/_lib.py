@@ -39,6 +39,14 @@ class MspInfo(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class MspInstance(C.Structure):
+    """One instance of a batch (msp_instance)."""
+    _fields_ = [("A", C.c_void_p), ("n", C.c_int64), ("lda", C.c_int64), ("lam", C.c_double),
+                ("lam0", C.c_double), ("B", C.c_void_p), ("ldb", C.c_int64), ("X", C.c_void_p),
+                ("ldx", C.c_int64), ("m", C.c_int), ("gamma", C.c_int), ("s", C.c_int64),
+                ("phi", C.c_int64), ("gamma_phi", C.c_int), ("pad_", C.c_int), ("seed", C.c_uint64)]
+
+
 class MspError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -72,6 +80,12 @@ _SIGS = {
                                  C.c_double, I64, C.c_int, C.c_uint64, C.POINTER(MspOpts),
                                  C.POINTER(MspInfo)]),
     "msp_matvec_f64": (C.c_int, [P, P, C.c_int, I64, I64, C.c_double, P, P]),
+    "msp_batch_create": (C.c_int, [P, C.c_int, C.POINTER(MspInstance), C.POINTER(P)]),
+    "msp_batch_destroy": (None, [P]),
+    "msp_batch_solve": (C.c_int, [P, P, C.POINTER(MspOpts), C.POINTER(MspInfo)]),
+    "msp_batch_info": (C.c_int, [P, P, C.POINTER(MspInfo)]),
+    "msp_solve_batched": (C.c_int, [P, C.c_int, C.POINTER(MspInstance), C.POINTER(MspOpts),
+                                    C.POINTER(MspInfo)]),
     "msp_schatten": (C.c_int, [P, P, C.c_int, I64, I64, C.c_double, I64, C.c_uint64,
                                C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "msp_hutchinson": (C.c_int, [P, P, C.c_int, I64, I64, I64, C.c_uint64, P]),

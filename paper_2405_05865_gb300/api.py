@@ -100,6 +100,51 @@ class Factor:
             pass
 
 
+class Batch:
+    """A set-up batch (msp_batch_create). Holds the caller tensors whose
+    pointers the library keeps: A, and the column-major copies of B and the
+    solution X (``X(k)`` returns instance k's solution as an (n, m) view)."""
+
+    def __init__(self, ctx: "Context", handle: C.c_void_p, keep: list):
+        self.ctx, self.handle, self.keep = ctx, handle, keep
+        self.count = len(keep)
+
+    def X(self, k: int) -> torch.Tensor:
+        return self.keep[k][2].t()
+
+    def solve(self, sync: bool = True, raise_on_noconv: bool = True, **opts) -> list[dict] | None:
+        """One persistent launch over every instance; sync=False returns at
+        once (no host synchronisation; the call can be captured in a CUDA
+        graph on the context's stream)."""
+        o = make_opts(self.ctx.lib, **opts)
+        if not sync:
+            L.check(self.ctx.ptr, self.ctx.lib.msp_batch_solve(self.ctx.ptr, self.handle, C.byref(o), None))
+            return None
+        infos = (L.MspInfo * self.count)()
+        st = self.ctx.lib.msp_batch_solve(self.ctx.ptr, self.handle, C.byref(o), infos)
+        if st != 0 and not (st == 5 and not raise_on_noconv):
+            L.check(self.ctx.ptr, st)
+        return [i.as_dict() for i in infos]
+
+    def info(self) -> list[dict]:
+        infos = (L.MspInfo * self.count)()
+        st = self.ctx.lib.msp_batch_info(self.ctx.ptr, self.handle, infos)
+        if st not in (0, 5):
+            L.check(self.ctx.ptr, st)
+        return [i.as_dict() for i in infos]
+
+    def close(self) -> None:
+        if self.handle:
+            self.ctx.lib.msp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Context:
     """An MSP context bound to one CUDA device and one stream."""
 
@@ -195,6 +240,37 @@ class Context:
                                                   _ptr(x), s, gamma, lam0, phi, gamma_phi, seed,
                                                   C.byref(o), C.byref(info)))
         return x, info.as_dict()
+
+    # -- a9: batches of instances, up to 16 right-hand sides each
+    def batch(self, instances: list[dict], gamma: int = 8, lam0: float = 0.0, phi: int = 0,
+              gamma_phi: int = 8, seed: int = DEFAULT_SEED) -> Batch:
+        """instances: dicts with A (CUDA FP32 (n, n)), B (CUDA FP64 (n, m) or
+        (n,)), lam, s, and optionally gamma, lam0, phi, gamma_phi, seed."""
+        arr = (L.MspInstance * len(instances))()
+        keep = []
+        for k, d in enumerate(instances):
+            A = d["A"]
+            n, lda, dt = _check_matrix(A)
+            if dt != L.MSP_F32:
+                raise TypeError("batched instances need an FP32 A")
+            B = d["B"]
+            if not B.is_cuda or B.dtype != torch.float64 or B.shape[0] != n:
+                raise ValueError("B must be a CUDA float64 (n, m) tensor")
+            if B.dim() == 1:
+                B = B[:, None]
+            Bc = B.t().contiguous()          # column-major n x m
+            Xc = torch.empty_like(Bc)
+            e = arr[k]
+            e.A, e.n, e.lda = A.data_ptr(), n, lda
+            e.lam, e.lam0 = float(d["lam"]), float(d.get("lam0", lam0))
+            e.B, e.ldb, e.X, e.ldx, e.m = Bc.data_ptr(), n, Xc.data_ptr(), n, Bc.shape[0]
+            e.gamma, e.s = int(d.get("gamma", gamma)), int(d["s"])
+            e.phi, e.gamma_phi = int(d.get("phi", phi)), int(d.get("gamma_phi", gamma_phi))
+            e.seed = int(d.get("seed", seed))
+            keep.append((A, Bc, Xc))
+        h = C.c_void_p()
+        L.check(self.ptr, self.lib.msp_batch_create(self.ptr, len(instances), arr, C.byref(h)))
+        return Batch(self, h, keep)
 
     # -- a10: Schatten-1 norm (PSD A) by Hutchinson
     def schatten(self, A: torch.Tensor, p: float = 1.0, probes: int = 256,

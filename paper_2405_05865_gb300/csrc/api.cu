@@ -12,19 +12,7 @@ namespace {
 
 thread_local std::string g_noctx_error;
 
-// Switch to the context's device for the duration of a call.
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = true;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) ok = (cudaSetDevice(dev) == cudaSuccess);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
+using msp::DeviceGuard;
 
 bool is_device_ptr(const void* p) {
     cudaPointerAttributes at;
@@ -160,6 +148,12 @@ void msp_destroy(msp_ctx* ctx) {
     if (ctx->host_flags) cudaFreeHost(ctx->host_flags);
     for (int i = 0; i < ctx->n_events; ++i) cudaEventDestroy(ctx->events[i]);
     delete[] ctx->events;
+    for (int i = 0; i < ctx->n_lanes; ++i) {
+        msp_destroy(ctx->lanes[i]);
+        cudaStreamDestroy(ctx->lane_streams[i]);
+    }
+    delete[] ctx->lanes;
+    delete[] ctx->lane_streams;
     delete ctx;
 }
 
@@ -183,9 +177,11 @@ void msp_sketch_destroy(msp_sketch_t* sk) {
     delete sk;
 }
 
-static msp_status sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n,
-                              int64_t lda, int64_t s, int gamma, uint64_t seed,
-                              msp_sketch_t** out) {
+}  // extern "C"
+
+msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n,
+                           int64_t lda, int64_t s, int gamma, uint64_t seed, bool pack,
+                           msp_sketch_t** out) {
     if (dtype != MSP_F32 && dtype != MSP_F64)
         return msp_set_error(ctx, MSP_EINVAL, "sketch: dtype must be MSP_F32 or MSP_F64");
     if (n < 1 || lda < n || s < 16 || s > MSP_MAX_S || s > n || gamma < 1 ||
@@ -214,7 +210,7 @@ static msp_status sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int6
             MSP_OK ||
         (st = msp_sketch_apply(ctx, A, dtype, n, lda, sp, sk->csr_ptr, sk->csr_ent, gamma,
                                sk->C)) != MSP_OK ||
-        (dtype == MSP_F32 &&
+        (dtype == MSP_F32 && pack &&
          ((st = msp_alloc(ctx, (void**)&sk->packed, (size_t)msp_packed_tiles(n) * 128 * 128 * 4)) !=
               MSP_OK ||
           (st = msp_pack_upper(ctx, (const float*)A, lda, n, sk->packed)) != MSP_OK))) {
@@ -222,10 +218,12 @@ static msp_status sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int6
         msp_sketch_destroy(sk);
         return st;
     }
-    sk->A_src = A;
+    sk->A_src = pack ? A : nullptr;
     *out = sk;
     return MSP_OK;
 }
+
+extern "C" {
 
 msp_status msp_sketch(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n, int64_t lda,
                       int64_t s, int gamma, uint64_t seed, msp_sketch_t** out) {
@@ -233,7 +231,7 @@ msp_status msp_sketch(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n, i
     if (!A || !out) return msp_set_error(ctx, MSP_EINVAL, "sketch: NULL argument");
     DeviceGuard g(ctx->device);
     *out = nullptr;
-    return sketch_impl(ctx, A, dtype, n, lda, s, gamma, seed, out);
+    return msp_sketch_impl(ctx, A, dtype, n, lda, s, gamma, seed, true, out);
 }
 
 msp_status msp_sketch_info(const msp_sketch_t* sk, int64_t* n, int64_t* s, int64_t* s_pad,
@@ -265,8 +263,10 @@ void msp_factor_destroy(msp_factor_t* f) {
     delete f;
 }
 
-static msp_status nystrom_impl(msp_ctx* ctx, const msp_sketch_s* sk, double lambda, double lambda0,
-                               int64_t phi, int gamma_phi, uint64_t seed, msp_factor_t** out) {
+}  // extern "C"
+
+msp_status msp_nystrom_impl(msp_ctx* ctx, const msp_sketch_s* sk, double lambda, double lambda0,
+                            int64_t phi, int gamma_phi, uint64_t seed, msp_factor_t** out) {
     if (!(lambda > 0.0) || !(lambda0 >= 0.0) || !std::isfinite(lambda) || !std::isfinite(lambda0))
         return msp_set_error(ctx, MSP_EINVAL, "nystrom: need lambda > 0 and lambda0 >= 0");
     if (phi < 0 || (phi > 0 && (gamma_phi < 1 || gamma_phi > MSP_MAX_GAMMA || gamma_phi > phi ||
@@ -331,13 +331,15 @@ static msp_status nystrom_impl(msp_ctx* ctx, const msp_sketch_s* sk, double lamb
     return MSP_OK;
 }
 
+extern "C" {
+
 msp_status msp_nystrom(msp_ctx* ctx, const msp_sketch_t* sk, double lambda, double lambda0,
                        int64_t phi, int gamma_phi, uint64_t seed, msp_factor_t** out) {
     if (!ctx) return msp_set_error(nullptr, MSP_EINVAL, "ctx is NULL");
     if (!sk || !out) return msp_set_error(ctx, MSP_EINVAL, "nystrom: NULL argument");
     DeviceGuard g(ctx->device);
     *out = nullptr;
-    return nystrom_impl(ctx, sk, lambda, lambda0, phi, gamma_phi, seed, out);
+    return msp_nystrom_impl(ctx, sk, lambda, lambda0, phi, gamma_phi, seed, out);
 }
 
 msp_status msp_factor_get(msp_ctx* ctx, const msp_factor_t* f, double* W, double* M2, double* Linv,
@@ -546,8 +548,8 @@ msp_status msp_solve_full(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t 
     }
     msp_sketch_t* sk = nullptr;
     msp_factor_t* f = nullptr;
-    msp_status st = sketch_impl(ctx, Ad, dtype, n, ldd, s, gamma, seed, &sk);
-    if (st == MSP_OK) st = nystrom_impl(ctx, sk, lambda, lambda0, phi, gamma_phi, seed, &f);
+    msp_status st = msp_sketch_impl(ctx, Ad, dtype, n, ldd, s, gamma, seed, true, &sk);
+    if (st == MSP_OK) st = msp_nystrom_impl(ctx, sk, lambda, lambda0, phi, gamma_phi, seed, &f);
     msp_status st2 = MSP_OK;
     if (st == MSP_OK) st2 = solve_impl(ctx, f, Ad, dtype, n, ldd, lambda, bd, xd, &o, info);
     if (st == MSP_OK && (st2 == MSP_OK || st2 == MSP_ENOCONV) && !dx) {

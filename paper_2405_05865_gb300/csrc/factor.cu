@@ -12,6 +12,8 @@
 // and an FP64 GEMM kernel for the rest.
 #include "msp_internal.cuh"
 
+#include <atomic>
+
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -337,12 +339,14 @@ msp_status dgemm(msp_ctx* ctx, bool ta, bool tb, int64_t m, int64_t n, int64_t k
 msp_status chol_inv(msp_ctx* ctx, double* M, double* X, double* T1, double* T2, int64_t ld,
                     int64_t off, int64_t n, int* fail) {
     if (n <= 64) {
-        static bool attr_set = false;
-        if (!attr_set) {
+        // set once per device; batch set-up calls this from several threads
+        static std::atomic<bool> attr_set[64];
+        const int d = ctx->device;
+        if (d < 0 || d >= 64 || !attr_set[d].load()) {
             MSP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_chol_leaf,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    kLeafSmem));
-            attr_set = true;
+            if (d >= 0 && d < 64) attr_set[d] = true;
         }
         k_chol_leaf<<<1, 256, kLeafSmem, ctx->stream>>>(M + off * ld + off, X + off * ld + off, ld,
                                                          (int)n, fail);

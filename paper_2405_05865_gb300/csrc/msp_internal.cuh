@@ -34,6 +34,10 @@ struct msp_ctx {
     // CUDA-event pool for opts.profile (pairs), created lazily
     cudaEvent_t* events = nullptr;
     int n_events = 0;
+    // worker contexts (own streams) for concurrent batch set-up, created lazily
+    msp_ctx** lanes = nullptr;
+    cudaStream_t* lane_streams = nullptr;
+    int n_lanes = 0;
 };
 
 // Launch accounting / optional event timing of one launch site class.
@@ -132,6 +136,19 @@ inline size_t dtype_size(msp_dtype t) { return t == MSP_F64 ? 8 : 4; }
 
 namespace msp {
 
+// Switch to a device for the duration of a call (restores the caller's).
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
 // SplitMix64 finaliser and the counter-based draw described in msp.h.
 __host__ __device__ inline uint64_t mix64(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -224,6 +241,14 @@ msp_status msp_sketch_apply(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t n
 msp_status msp_gather_rows(msp_ctx* ctx, msp_dtype dt, int64_t rows_out, int64_t width,
                            const int32_t* ptr, const int32_t* ent, const void* in,
                            int64_t ld_in, double scale, void* out, int64_t ld_out);
+
+// api.cu: sketch (pack = also build the packed upper tiles of an FP32 A for
+// the single-RHS A pass) and Nystrom factor, without argument re-checks of
+// the handles
+msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n, int64_t lda,
+                           int64_t s, int gamma, uint64_t seed, bool pack, msp_sketch_s** out);
+msp_status msp_nystrom_impl(msp_ctx* ctx, const msp_sketch_s* sk, double lambda, double lambda0,
+                            int64_t phi, int gamma_phi, uint64_t seed, msp_factor_s** out);
 
 // factor.cu
 msp_status msp_build_factor(msp_ctx* ctx, msp_factor_s* f, const void* Ct, int64_t phi_rows);
