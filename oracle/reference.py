@@ -52,6 +52,24 @@ def backward_error(A, x, b, lam, norm_A: float | None = None) -> float:
     return float(np.linalg.norm(r) / ((norm_A + lam) * np.linalg.norm(x) + np.linalg.norm(b)))
 
 
+def norm_lower_bound(A) -> float:
+    """A certified lower bound L <= |A|_2 for symmetric PSD A: the larger of the
+    largest column 2-norm (|A e_i| <= |A|_2) and the Rayleigh quotient of the
+    all-ones vector (1^T A 1 / n <= lambda_max(A) = |A|_2)."""
+    A = np.asarray(A, dtype=np.float64)
+    col = float(np.sqrt((A * A).sum(axis=0)).max())
+    return max(col, float(A.sum()) / A.shape[0])
+
+
+def backward_error_bound(A, x, b, lam) -> float:
+    """|r| / ((L + lam) |x| + |b|) with L = norm_lower_bound(A). Since
+    L + lam <= |A + lam I|_2, this is an upper bound on the normwise backward
+    error |r| / (|A + lam I|_2 |x| + |b|) (Rigal and Gaches) of x."""
+    r = residual(A, x, b, lam)
+    L = norm_lower_bound(A)
+    return float(np.linalg.norm(r) / ((L + lam) * np.linalg.norm(x) + np.linalg.norm(b)))
+
+
 def energy_error(A, x, xs, lam) -> float:
     """|x - x*|_{A + lam I} / |x*|_{A + lam I}."""
     A = np.asarray(A, dtype=np.float64)

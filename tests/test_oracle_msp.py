@@ -286,3 +286,44 @@ def test_effective_dimension_and_schatten_closed_forms():
     assert reference.schatten(sig, 1.0) == pytest.approx(np.trace(A), rel=1e-12)
     ev = np.linalg.eigvalsh(A)
     assert reference.schatten(sig, 0.5) == pytest.approx(np.sum(np.abs(ev) ** 0.5) ** 2, rel=1e-8)
+
+
+# ---- certified lower bound of |A|_2 and the backward-error bound
+
+def test_norm_lower_bound_closed_forms():
+    from oracle import reference as ref
+    n = 37
+    # A = 1 1^T: |A|_2 = n, the all-ones Rayleigh quotient attains it
+    assert ref.norm_lower_bound(np.ones((n, n))) == pytest.approx(n, rel=1e-15)
+    # A = I: every column has norm 1 = |A|_2
+    assert ref.norm_lower_bound(np.eye(n)) == pytest.approx(1.0, rel=1e-15)
+    # A = v v^T with one spike: the column norm |v_k| |v| attains |v|^2 when v = e_k
+    v = np.zeros(n)
+    v[5] = 3.0
+    assert ref.norm_lower_bound(np.outer(v, v)) == pytest.approx(9.0, rel=1e-15)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_norm_lower_bound_below_the_norm(seed):
+    from oracle import reference as ref
+    from workloads import make_workload
+    for name in ("outlier", "rbf"):
+        w = make_workload(name, seed=seed, n=256, rbf_dtype=np.float64)
+        A = np.asarray(w.A, dtype=np.float64)
+        L = ref.norm_lower_bound(A)
+        top = float(np.linalg.eigvalsh(A)[-1])
+        assert 0.0 < L <= top * (1 + 1e-12)
+        if name == "rbf":
+            # positive kernel: the ones quotient is within a small factor
+            assert L >= 0.25 * top
+
+
+def test_backward_error_bound_dominates():
+    from oracle import reference as ref
+    from workloads import make_workload
+    w = make_workload("rbf", seed=3, n=200, rbf_dtype=np.float64)
+    A = np.asarray(w.A, dtype=np.float64)
+    xs = ref.solve_dense(A, w.b, w.lam)
+    x = xs + 1e-6 * np.random.default_rng(0).standard_normal(xs.shape)
+    exact = ref.backward_error(A, x, w.b, w.lam, norm_A=float(np.linalg.eigvalsh(A)[-1]))
+    assert ref.backward_error_bound(A, x, w.b, w.lam) >= exact * (1 - 1e-12)
