@@ -103,7 +103,22 @@ typedef struct {
     int profile;          /* 1: time every A-pass and level-2 launch with CUDA
                              events on the context stream (msp_info *_ms).
                              Default 0.                                          */
+    int criterion;        /* stopping rule of the solve (the last refinement
+                             step in MSP_PREC_MIXED), msp_criterion. Default
+                             MSP_STOP_RESIDUAL.                                  */
 } msp_opts;
+
+/* Stopping rules.
+ *   MSP_STOP_RESIDUAL : |b - (A + lam I) x| <= tol |b| (relative residual).
+ *   MSP_STOP_BACKWARD : |b - (A + lam I) x| <= tol ((L + lam) |x| + |b|)
+ *                       with L <= |A|_2 the certified lower bound of
+ *                       msp_norm_lower_bound, so the normwise backward error
+ *                       |r| / (|A + lam I|_2 |x| + |b|) (Rigal-Gaches) is at
+ *                       most tol. Always satisfied when the residual rule is. */
+typedef enum {
+    MSP_STOP_RESIDUAL = 0,
+    MSP_STOP_BACKWARD = 1
+} msp_criterion;
 
 typedef struct {
     int outer_iters;      /* total level-1 iterations (all refinement steps)     */
@@ -122,6 +137,9 @@ typedef struct {
     double gemv_ms;
     double level2_ms;
     double resid_ms;
+    double backward_err;  /* |r| / ((L + lam) |x| + |b|) at the end: an upper
+                             bound on the normwise backward error            */
+    double norm_lb;       /* L, the lower bound of |A|_2 used (0 if not formed) */
 } msp_info;
 
 /* ---------------------------------------------------------------- context */
@@ -282,8 +300,14 @@ MSP_API void msp_batch_destroy(msp_batch_t* batch);
  * on the context's stream: the level-1 iteration, the direct level 2, the
  * FP64-accurate residual and every convergence decision run on the device,
  * with no host synchronisation. X is overwritten (no initial guess).
- * opts: tol, max_outer (per correction solve), max_refine, refine_tol,
- * precision (MSP_PREC_MIXED or MSP_PREC_FP32); other fields are ignored.
+ * opts: tol, criterion (per column), max_outer (per correction solve),
+ * max_refine, refine_tol, precision (MSP_PREC_MIXED or MSP_PREC_FP32); other
+ * fields are ignored. The residual of the refinement is float-float: x is
+ * split into an FP32 pair (48 bits), products are exact (FMA) and sums are
+ * kept as FP32 pairs (TwoSum), so it carries an error of a few
+ * 2^-48 |(|A| |x|)|; with MSP_STOP_RESIDUAL and a tol below that level
+ * relative to |b| a column ends with MSP_ENOCONV. MSP_STOP_BACKWARD, whose
+ * threshold scales with |A| |x|, is not limited by it.
  * infos: NULL makes the call asynchronous (and capturable in a CUDA graph on
  * the context's stream); otherwise `count` entries are filled after a
  * stream synchronisation, as msp_batch_info does. The returned status is the
@@ -294,9 +318,23 @@ MSP_API msp_status msp_batch_solve(msp_ctx* ctx, msp_batch_t* batch, const msp_o
 /* Per-instance results of the last msp_batch_solve (synchronises the
  * context's stream): outer_iters = level-1 iterations in which the instance
  * had an unconverged column, refine_steps, rel_resid = the largest
- * |b_j - (A + lambda I) x_j| / |b_j| over its columns (FP64-accurate
- * residual), lambda_tilde, shift, shift_retries, status. */
+ * |b_j - (A + lambda I) x_j| / |b_j| over its columns, backward_err = the
+ * largest |r_j| / ((L + lambda) |x_j| + |b_j|), norm_lb = L, lambda_tilde,
+ * shift, shift_retries, status. gemv_launches / resid_launches count the
+ * batch's A passes and residual passes and gemv_ms / level2_ms / resid_ms
+ * split the launch's device time (the same in every entry). */
 MSP_API msp_status msp_batch_info(msp_ctx* ctx, const msp_batch_t* batch, msp_info* infos);
+
+/* Counters of the last msp_batch_solve (synchronises the context's stream),
+ * written to stats[0..9]: [0] level-1 A passes, [1] residual passes,
+ * [2] bytes of A streamed by the level-1 passes, [3] by the residual passes
+ * (instances whose columns had all converged are skipped), [4..7] device-
+ * timer milliseconds spent in the A passes, the level-2 and vector steps,
+ * the residual passes with the X update, and the convergence checks,
+ * [8] bytes of one full pass over every tiled A (sum of n_pad^2 * 4),
+ * [9] sum of n^2 * 4. The times are read by one block between grid
+ * barriers, so each class includes its barrier. */
+MSP_API msp_status msp_batch_stats(msp_ctx* ctx, const msp_batch_t* batch, double* stats);
 
 /* msp_batch_create + msp_batch_solve + msp_batch_destroy. */
 MSP_API msp_status msp_solve_batched(msp_ctx* ctx, int count, const msp_instance* inst,
@@ -371,6 +409,12 @@ MSP_API msp_status msp_rbf_grad_ell_static(const double* points, int64_t n, int 
                                            void* stream);
 
 /* ----------------------------------------------------- helpers (tests) */
+
+/* L = max(max_i |A e_i|_2, 1^T A 1 / n) <= |A|_2 for symmetric PSD A (a
+ * column norm and the Rayleigh quotient of the all-ones vector), FP64 sums
+ * over one pass of A (device, FP32 or FP64, lda >= n). *out: host scalar. */
+MSP_API msp_status msp_norm_lower_bound(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n,
+                                        int64_t lda, double* out);
 
 /* y = (A + lambda I) x, FP64 accumulation, FP64 x and y; A FP32 or FP64.
  * The residual operator of the refinement step (one pass over A). */

@@ -17,6 +17,7 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "msp.h")
 
 MSP_F64, MSP_F32 = 0, 1
 MSP_PREC_FP64, MSP_PREC_FP32, MSP_PREC_MIXED = 0, 1, 2
+MSP_STOP_RESIDUAL, MSP_STOP_BACKWARD = 0, 1
 STATUS = {0: "MSP_OK", 1: "MSP_EINVAL", 2: "MSP_ENOMEM", 3: "MSP_ECUDA", 4: "MSP_ENOTPD",
           5: "MSP_ENOCONV", 6: "MSP_ENONFINITE", 7: "MSP_ETIMEOUT"}
 
@@ -24,7 +25,8 @@ STATUS = {0: "MSP_OK", 1: "MSP_EINVAL", 2: "MSP_ENOMEM", 3: "MSP_ECUDA", 4: "MSP
 class MspOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_outer", C.c_int), ("max_refine", C.c_int),
                 ("refine_tol", C.c_double), ("inner_tol", C.c_double), ("max_inner", C.c_int),
-                ("precision", C.c_int), ("check_every", C.c_int), ("profile", C.c_int)]
+                ("precision", C.c_int), ("check_every", C.c_int), ("profile", C.c_int),
+                ("criterion", C.c_int)]
 
 
 class MspInfo(C.Structure):
@@ -33,7 +35,7 @@ class MspInfo(C.Structure):
                 ("lambda_tilde", C.c_double), ("shift", C.c_double), ("status", C.c_int),
                 ("gemv_launches", C.c_int), ("level2_launches", C.c_int), ("resid_launches", C.c_int),
                 ("pad_", C.c_int), ("gemv_ms", C.c_double), ("level2_ms", C.c_double),
-                ("resid_ms", C.c_double)]
+                ("resid_ms", C.c_double), ("backward_err", C.c_double), ("norm_lb", C.c_double)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -80,10 +82,12 @@ _SIGS = {
                                  C.c_double, I64, C.c_int, C.c_uint64, C.POINTER(MspOpts),
                                  C.POINTER(MspInfo)]),
     "msp_matvec_f64": (C.c_int, [P, P, C.c_int, I64, I64, C.c_double, P, P]),
+    "msp_norm_lower_bound": (C.c_int, [P, P, C.c_int, I64, I64, C.POINTER(C.c_double)]),
     "msp_batch_create": (C.c_int, [P, C.c_int, C.POINTER(MspInstance), C.POINTER(P)]),
     "msp_batch_destroy": (None, [P]),
     "msp_batch_solve": (C.c_int, [P, P, C.POINTER(MspOpts), C.POINTER(MspInfo)]),
     "msp_batch_info": (C.c_int, [P, P, C.POINTER(MspInfo)]),
+    "msp_batch_stats": (C.c_int, [P, P, P]),
     "msp_solve_batched": (C.c_int, [P, C.c_int, C.POINTER(MspInstance), C.POINTER(MspOpts),
                                     C.POINTER(MspInfo)]),
     "msp_schatten": (C.c_int, [P, P, C.c_int, I64, I64, C.c_double, I64, C.c_uint64,

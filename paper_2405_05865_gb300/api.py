@@ -19,6 +19,7 @@ DEFAULT_SEED = 0x4D5350      # "MSP"
 
 _DT = {torch.float32: L.MSP_F32, torch.float64: L.MSP_F64}
 _PREC = {"fp64": L.MSP_PREC_FP64, "fp32": L.MSP_PREC_FP32, "mixed": L.MSP_PREC_MIXED}
+_STOP = {"residual": L.MSP_STOP_RESIDUAL, "backward": L.MSP_STOP_BACKWARD}
 
 
 def _ptr(t: torch.Tensor) -> C.c_void_p:
@@ -33,6 +34,8 @@ def make_opts(lib, **kw) -> L.MspOpts:
             continue
         if k == "precision" and isinstance(v, str):
             v = _PREC[v]
+        if k == "criterion" and isinstance(v, str):
+            v = _STOP[v]
         if not hasattr(o, k):
             raise TypeError(f"unknown option {k!r}")
         setattr(o, k, v)
@@ -132,6 +135,14 @@ class Batch:
         if st not in (0, 5):
             L.check(self.ctx.ptr, st)
         return [i.as_dict() for i in infos]
+
+    def stats(self) -> dict:
+        """Counters and device-timer split of the last solve (msp_batch_stats)."""
+        v = (C.c_double * 10)()
+        L.check(self.ctx.ptr, self.ctx.lib.msp_batch_stats(self.ctx.ptr, self.handle, v))
+        keys = ("a_passes", "resid_passes", "a_bytes", "resid_bytes", "a_ms", "level2_ms",
+                "resid_ms", "check_ms", "dense_pass_bytes", "nn_bytes")
+        return dict(zip(keys, list(v)))
 
     def close(self) -> None:
         if self.handle:
@@ -305,6 +316,13 @@ class Context:
         L.check(self.ptr, self.lib.msp_rbf_grad_ell(self.ptr, _ptr(points), n, dim, float(ell),
                                                     _ptr(a.contiguous()), _ptr(x.contiguous()), _ptr(out)))
         return out
+
+    def norm_lower_bound(self, A: torch.Tensor) -> float:
+        """L <= |A|_2 (largest column norm, all-ones Rayleigh quotient)."""
+        n, lda, dt = _check_matrix(A)
+        v = C.c_double()
+        L.check(self.ptr, self.lib.msp_norm_lower_bound(self.ptr, _ptr(A), dt, n, lda, C.byref(v)))
+        return v.value
 
     def matvec_f64(self, A: torch.Tensor, x: torch.Tensor, lam: float = 0.0) -> torch.Tensor:
         n, lda, dt = _check_matrix(A)

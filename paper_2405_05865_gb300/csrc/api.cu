@@ -399,15 +399,20 @@ static msp_status solve_impl(msp_ctx* ctx, const msp_factor_s* f, const void* A,
     // the sketch's packed upper tiles stand in for A when A is the sketched matrix
     const float* packed = (dtype == MSP_F32 && f->sk->packed && A == f->sk->A_src)
                               ? f->sk->packed : nullptr;
-    // per-solve buffers: r64 (n), rhs_w (n), sol_w (n), scalars
+    if (o->criterion != MSP_STOP_RESIDUAL && o->criterion != MSP_STOP_BACKWARD)
+        return msp_set_error(ctx, MSP_EINVAL, "solve: unknown criterion %d", o->criterion);
+    const bool crit_bw = o->criterion == MSP_STOP_BACKWARD;
+    // per-solve buffers: r64 (n), rhs_w (n), sol_w (n), scalars, |A| bound work
     void* mem = nullptr;
     size_t b_r = round_up(n * 8, 256), b_w = round_up(n * ts, 256);
-    MSP_TRY(msp_alloc(ctx, &mem, b_r + 2 * b_w + 256));
+    const size_t b_nw = crit_bw ? (size_t)round_up(2 * n * 8, 256) : 0;
+    MSP_TRY(msp_alloc(ctx, &mem, b_r + 2 * b_w + 256 + b_nw));
     char* c = (char*)mem;
     double* r64 = (double*)c; c += b_r;
     void* rhs_w = c; c += b_w;
     void* sol_w = c; c += b_w;
-    double* scal = (double*)c;    // [0] |b|^2, [1] |r|^2
+    double* scal = (double*)c;    // [0] |b|^2, [1] |r|^2, [2] L <= |A|_2, [3] |x|^2
+    double* nwork = (double*)(c + 256);
     double* hs = (double*)ctx->host_flags + 8;
     msp_status st = MSP_OK;
     int outer_total = 0, inner_total = 0, steps = 0;
@@ -435,17 +440,29 @@ static msp_status solve_impl(msp_ctx* ctx, const msp_factor_s* f, const void* A,
         if (info) *info = inf;
         return s2;
     };
+    double Lb = 0.0, xx = 0.0;
     auto read2 = [&](double* a0, double* a1) -> msp_status {
-        MSP_CUDA_TRY(ctx, cudaMemcpyAsync(hs, scal, 16, cudaMemcpyDeviceToHost, ctx->stream));
+        MSP_CUDA_TRY(ctx, cudaMemcpyAsync(hs, scal, 32, cudaMemcpyDeviceToHost, ctx->stream));
         MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
         *a0 = hs[0];
         *a1 = hs[1];
+        Lb = hs[2];
+        xx = hs[3];
         return MSP_OK;
     };
+    // the stopping rule of the solve
+    auto met = [&]() {
+        if (crit_bw) return std::sqrt(rr) <= o->tol * ((Lb + lambda) * std::sqrt(xx) + std::sqrt(bb));
+        return rr <= o->tol * o->tol * bb;
+    };
+    MSP_CUDA_TRY(ctx, cudaMemsetAsync(scal, 0, 32, ctx->stream));
+    if (crit_bw && (st = msp_norm_lb_launch(ctx, A, dtype, n, lda, nwork, scal + 2)) != MSP_OK)
+        return finish(st);
     if ((st = msp_norm2(ctx, b, n, scal + 0)) != MSP_OK) return finish(st);
     MSP_CUDA_TRY(ctx, cudaMemcpyAsync(r64, b, n * 8, cudaMemcpyDeviceToDevice, ctx->stream));
     MSP_CUDA_TRY(ctx, cudaMemcpyAsync(scal + 1, scal + 0, 8, cudaMemcpyDeviceToDevice, ctx->stream));
     if ((st = read2(&bb, &rr)) != MSP_OK) return finish(st);
+    inf.norm_lb = Lb;
     if (!std::isfinite(bb)) return finish(msp_set_error(ctx, MSP_ENONFINITE, "solve: b is not finite"));
     MSP_CUDA_TRY(ctx, cudaMemsetAsync(x, 0, n * 8, ctx->stream));
     if (bb == 0.0) {
@@ -464,12 +481,13 @@ static msp_status solve_impl(msp_ctx* ctx, const msp_factor_s* f, const void* A,
                 return finish(st);
             if ((st = pr.end()) != MSP_OK) return finish(st);
             if ((st = pr.finish(&slots[2], 1)) != MSP_OK) return finish(st);
+            if (crit_bw && (st = msp_norm2(ctx, x, n, scal + 3)) != MSP_OK) return finish(st);
             if ((st = read2(&bb, &rr)) != MSP_OK) return finish(st);
             if (!std::isfinite(rr))
                 return finish(msp_set_error(ctx, MSP_ENONFINITE, "solve: residual is not finite"));
             have_resid = true;
         }
-        if (rr <= o->tol * o->tol * bb) break;
+        if (met()) break;
         // correction solve on the normalised residual: (A + lam I) d = r / |r|
         if ((st = msp_scale_cast(ctx, r64, scal + 1, n, wt, rhs_w)) != MSP_OK) return finish(st);
         int it = 0, in = 0;
@@ -489,13 +507,16 @@ static msp_status solve_impl(msp_ctx* ctx, const msp_factor_s* f, const void* A,
             return finish(st);
         if ((st = pr.end()) != MSP_OK) return finish(st);
         if ((st = pr.finish(&slots[2], 1)) != MSP_OK) return finish(st);
+        if (crit_bw && (st = msp_norm2(ctx, x, n, scal + 3)) != MSP_OK) return finish(st);
         if ((st = read2(&bb, &rr)) != MSP_OK) return finish(st);
     }
     inf.rel_resid = std::sqrt(rr / bb);
-    if (!(inf.rel_resid <= o->tol) && prec != MSP_PREC_FP32)
+    if (crit_bw) inf.backward_err = std::sqrt(rr) / ((Lb + lambda) * std::sqrt(xx) + std::sqrt(bb));
+    if (!met() && prec != MSP_PREC_FP32)
         return finish(msp_set_error(ctx, MSP_ENOCONV,
-                                    "solve: relative residual %.3e above tol %.3e after %d steps",
-                                    inf.rel_resid, o->tol, steps));
+                                    "solve: relative residual %.3e (backward error bound %.3e) "
+                                    "above tol %.3e after %d steps",
+                                    inf.rel_resid, inf.backward_err, o->tol, steps));
     if (kst == MSP_ENOCONV) return finish(kst);
     return finish(MSP_OK);
 }

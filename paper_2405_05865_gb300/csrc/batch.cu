@@ -93,7 +93,14 @@ struct BCtl {
     int ctrA, ctrR;
     int active[2];
     int unfinished[2];
-    int pad[7];
+    int sweepsA, sweepsR;     // A passes and residual passes run
+    int pad0;
+    unsigned long long tilesA;   // A tiles streamed by the level-1 passes
+    unsigned long long tilesR;   // A tiles streamed by the residual passes
+    // device-timer nanoseconds per step class, taken by block 0 between grid
+    // barriers: 0 A pass, 1 level-2 and vector steps, 2 residual and X
+    // update, 3 convergence checks and set-up of a correction solve
+    unsigned long long t_ns[4];
 };
 
 struct BArgs {
@@ -105,15 +112,17 @@ struct BArgs {
     float *P, *Q, *R, *Z, *XW, *XH, *XL;
     double* R64;
     float *G, *Y1, *Y2;
-    double *p_pq, *p_rr, *p_zr, *p_zq, *p_r64;
+    double *p_pq, *p_rr, *p_zr, *p_zq, *p_r64, *p_xx;
     double *bb, *scale, *alpha, *rz;    // per column; rz holds two generations
     int *act, *fin;                     // per column
     int *iact;                          // two generations x count
     int *istep, *iters, *ierr, *isteps; // per instance
-    double* rel;                        // per instance
+    double* rel;                        // per instance: largest |r| / |b|
+    double* berr;                       // per instance: largest backward-error bound
+    const double* anorm;                // per instance: L <= |A|_2
     BCtl* ctl;
-    double tol2, rtol2;
-    int max_outer, max_steps;
+    double tol, tol2, rtol2;
+    int max_outer, max_steps, crit;
 };
 
 __device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
@@ -279,7 +288,7 @@ __device__ __forceinline__ double colsum_rv(const float (&v)[8], float* wsum, in
 // --------------------------------------------------- the streamed A passes
 
 template <bool kResid>
-__device__ __forceinline__ void producer(const BArgs& a, unsigned char* ring, uint64_t* full, uint64_t* empty,
+__device__ __noinline__ void producer(const BArgs& a, unsigned char* ring, uint64_t* full, uint64_t* empty,
                          int2* hdr, uint32_t& kring, int* counter,
                          const int* flag) {
     const uint64_t pol = msp::policy_evict_first();
@@ -311,6 +320,7 @@ __device__ __forceinline__ void producer(const BArgs& a, unsigned char* ring, ui
                 break;
             }
             hdr[s] = make_int2(it, kt);
+            if (kt == 0) atomicAdd(kResid ? &a.ctl->tilesR : &a.ctl->tilesA, (unsigned long long)nk);
             const BInst& I = a.inst[inst];
             const float* At = I.At + ((int64_t)rb * nk + kt) * kTileFloats;
             const int64_t vrow = (int64_t)I.voff + (int64_t)kt * kKT;
@@ -333,7 +343,7 @@ __device__ __forceinline__ void producer(const BArgs& a, unsigned char* ring, ui
 }
 
 // SA consumers: Q = (A + lam I) P and the block partials of p^T q.
-__device__ __forceinline__ void consume_A(const BArgs& a, unsigned char* ring, uint64_t* full, uint64_t* empty,
+__device__ __noinline__ void consume_A(const BArgs& a, unsigned char* ring, uint64_t* full, uint64_t* empty,
                           const int2* hdr, uint32_t& kring, float* red,
                           float* wsum, int w, int lane) {
     float acc[4][16];
@@ -385,7 +395,7 @@ __device__ __forceinline__ void consume_A(const BArgs& a, unsigned char* ring, u
 
 // Refinement residual consumers: R64 = B - lam X - A X with A X from
 // compensated FP32 tiles, and the block partials of |r|^2 (FP64).
-__device__ __forceinline__ void consume_R(const BArgs& a, unsigned char* ring, uint64_t* full, uint64_t* empty,
+__device__ __noinline__ void consume_R(const BArgs& a, unsigned char* ring, uint64_t* full, uint64_t* empty,
                           const int2* hdr, uint32_t& kring, double* redd,
                           double* wsumd, int w, int lane) {
     float s[2][16], c[2][16];
@@ -540,6 +550,7 @@ __device__ __forceinline__ void step_init(const BArgs& a, double* wsumd, int tid
             double t = 0.0;
             for (int ww = 0; ww < kWorkWarps; ++ww) t += wsumd[ww * 16 + lane];
             a.p_r64[((int64_t)I.boff + item.y) * kM + lane] = t;
+            a.p_xx[((int64_t)I.boff + item.y) * kM + lane] = 0.0;
         }
         msp::bar_workers<kWorkers>();
     }
@@ -552,26 +563,37 @@ __device__ __forceinline__ void step_check(const BArgs& a, int step, int w, int 
     for (int i = blockIdx.x; i < a.count; i += gridDim.x) {
         const BInst& I = a.inst[i];
         const int c = lane & 15;
-        double rr = 0.0;
-        for (int b = 0; b < I.nb; ++b) rr += a.p_r64[((int64_t)I.boff + b) * kM + c];
+        double rr = 0.0, xx = 0.0;
+        for (int b = 0; b < I.nb; ++b) {
+            rr += a.p_r64[((int64_t)I.boff + b) * kM + c];
+            xx += a.p_xx[((int64_t)I.boff + b) * kM + c];
+        }
         const int gi = i * kM + c;
         if (step == 0 && lane < 16) a.bb[gi] = rr;
         const double bb = (step == 0) ? rr : a.bb[gi];
         if (lane < 16 && c < I.m && !isfinite(rr)) atomicCAS(&a.ierr[i], 0, (int)MSP_ENONFINITE);
         __syncwarp();
         const int e = ld_volatile(&a.ierr[i]);
-        const bool f = (c >= I.m) || e != 0 || !(bb > 0.0) || rr <= a.tol2 * bb;
+        // backward-error bound |r| / ((L + lam) |x| + |b|), L <= |A|_2
+        const double den = (a.anorm[i] + I.lam64) * sqrt(xx) + sqrt(bb);
+        const double be = (c < I.m && den > 0.0 && isfinite(rr)) ? sqrt(rr) / den : 0.0;
+        const bool met = a.crit ? sqrt(rr) <= a.tol * den : rr <= a.tol2 * bb;
+        const bool f = (c >= I.m) || e != 0 || !(bb > 0.0) || met;
         const double rel = (c < I.m && bb > 0.0 && isfinite(rr)) ? sqrt(rr / bb) : 0.0;
         if (lane < 16) {
             a.fin[gi] = f ? 1 : 0;
             a.scale[gi] = sqrt(rr);
         }
         const unsigned unf = __ballot_sync(0xffffffffu, lane < 16 && !f);
-        double mr = (lane < 16) ? rel : 0.0;
+        double mr = (lane < 16) ? rel : 0.0, mb = (lane < 16) ? be : 0.0;
 #pragma unroll
-        for (int o = 8; o > 0; o >>= 1) mr = fmax(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+        for (int o = 8; o > 0; o >>= 1) {
+            mr = fmax(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+            mb = fmax(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+        }
         if (lane == 0) {
             a.rel[i] = mr;
+            a.berr[i] = mb;
             if (unf) atomicAdd(&a.ctl->unfinished[step & 1], __popc(unf));
         }
     }
@@ -627,7 +649,7 @@ __device__ __forceinline__ void step_scale(const BArgs& a, int step, float* wsum
 }
 
 // S2: convergence flags (one block per instance), then G = C^T R by strips.
-__device__ __forceinline__ void step_G(const BArgs& a, int t, unsigned char* smem, float* red, int tid, int w, int lane) {
+__device__ __noinline__ void step_G(const BArgs& a, int t, unsigned char* smem, float* red, int tid, int w, int lane) {
     const int cur = t & 1, prev = cur ^ 1;
     float* ring = reinterpret_cast<float*>(smem);
     for (int it = blockIdx.x; it < a.nstrips; it += gridDim.x) {
@@ -736,7 +758,7 @@ __device__ __forceinline__ void step_G(const BArgs& a, int t, unsigned char* sme
 
 // S3 / S4: Y_out[chunk] = L^{-1} G or L^{-T} Y1 (triangular k range).
 template <bool kUpper>
-__device__ __forceinline__ void step_tri(const BArgs& a, int t, unsigned char* smem, float* red, int tid, int w, int lane) {
+__device__ __noinline__ void step_tri(const BArgs& a, int t, unsigned char* smem, float* red, int tid, int w, int lane) {
     const int cur = t & 1;
     float* tiles = reinterpret_cast<float*>(smem);
     float* Vs = reinterpret_cast<float*>(smem + kVsOffset);
@@ -766,7 +788,7 @@ __device__ __forceinline__ void step_tri(const BArgs& a, int t, unsigned char* s
 }
 
 // S5: Z = (R - C Y2) / lam~ by row blocks, partials of z.r and z.q.
-__device__ __forceinline__ void step_Z(const BArgs& a, int t, unsigned char* smem, float* red, float* wsum, int tid,
+__device__ __noinline__ void step_Z(const BArgs& a, int t, unsigned char* smem, float* red, float* wsum, int tid,
                        int w, int lane) {
     const int cur = t & 1;
     float* tiles = reinterpret_cast<float*>(smem);
@@ -910,7 +932,7 @@ __device__ __forceinline__ void step_X(const BArgs& a, int t, float* wsum, float
 
 // End of a correction solve: X += |R64| X_w, then X = x_hi + x_lo for the
 // residual pass.
-__device__ __forceinline__ void step_back(const BArgs& a, int tid) {
+__device__ __forceinline__ void step_back(const BArgs& a, double* wsumd, int tid, int w, int lane) {
     int i0, i1;
     my_range(a.nrows, i0, i1);
     for (int it = i0; it < i1; ++it) {
@@ -920,6 +942,7 @@ __device__ __forceinline__ void step_back(const BArgs& a, int tid) {
         const int row = item.y * kRB + (tid >> 1), ch = tid & 1;
         const int64_t vrow = (int64_t)I.voff + row;
         float xh[8], xl[8];
+        double d[8];
 #pragma unroll
         for (int c8 = 0; c8 < 8; ++c8) {
             const int col = 8 * ch + c8;
@@ -931,7 +954,22 @@ __device__ __forceinline__ void step_back(const BArgs& a, int tid) {
             }
             xh[c8] = (float)x;
             xl[c8] = (float)(x - (double)xh[c8]);
+            d[c8] = x * x;
         }
+#pragma unroll
+        for (int c8 = 0; c8 < 8; ++c8)
+#pragma unroll
+            for (int o = 2; o < 32; o <<= 1) d[c8] += __shfl_xor_sync(0xffffffffu, d[c8], o);
+        if (lane < 2)
+#pragma unroll
+            for (int c8 = 0; c8 < 8; ++c8) wsumd[w * 16 + 8 * lane + c8] = d[c8];
+        msp::bar_workers<kWorkers>();
+        if (w == 0 && lane < 16) {
+            double t = 0.0;
+            for (int ww = 0; ww < kWorkWarps; ++ww) t += wsumd[ww * 16 + lane];
+            a.p_xx[((int64_t)I.boff + item.y) * kM + lane] = t;
+        }
+        msp::bar_workers<kWorkers>();
         st4(a.XH + vrow * kM + 8 * ch, make_float4(xh[0], xh[1], xh[2], xh[3]));
         st4(a.XH + vrow * kM + 8 * ch + 4, make_float4(xh[4], xh[5], xh[6], xh[7]));
         st4(a.XL + vrow * kM + 8 * ch, make_float4(xl[0], xl[1], xl[2], xl[3]));
@@ -964,48 +1002,59 @@ __global__ void __launch_bounds__(kThreads, 1) k_batch_solve(BArgs a) {
     __syncthreads();
     BCtl* ctl = a.ctl;
     uint32_t kring = 0;
-#define MSP_GBAR()                                                                     \
+    uint64_t t_last = msp::globaltimer_ns();
+    const bool timer = blockIdx.x == 0 && tid == 0;
+#define MSP_GBAR(cls)                                                                  \
     do {                                                                               \
         if (!msp::grid_barrier(&ctl->bar_count, &ctl->bar_gen, &ctl->error)) return;   \
         if (ld_volatile(&ctl->error)) return;                                          \
+        if (timer) {                                                                   \
+            const uint64_t now = msp::globaltimer_ns();                                \
+            ctl->t_ns[cls] += now - t_last;                                            \
+            t_last = now;                                                              \
+        }                                                                              \
     } while (0)
 
     if (worker) step_init(a, wsumd, tid, w, lane);
-    MSP_GBAR();
+    MSP_GBAR(3);
     for (int step = 0;; ++step) {
         step_check(a, step, w, lane);
-        MSP_GBAR();
+        MSP_GBAR(3);
         const int unf = ld_volatile(&ctl->unfinished[step & 1]);
         if (unf == 0 || step >= a.max_steps) break;
         if (worker) step_scale(a, step, wsum, sd, tid, w, lane);
-        MSP_GBAR();
+        MSP_GBAR(3);
         for (int t = 0;; ++t) {
             if (worker) step_G(a, t, smem, red, tid, w, lane);
-            MSP_GBAR();
+            MSP_GBAR(1);
             if (ld_volatile(&ctl->active[t & 1]) == 0) break;
-            if (blockIdx.x == 0 && tid == 0) ctl->active[(t + 1) & 1] = 0;
+            if (blockIdx.x == 0 && tid == 0) {
+                ctl->active[(t + 1) & 1] = 0;
+                ctl->sweepsA += 1;
+            }
             if (worker) step_tri<false>(a, t, smem, red, tid, w, lane);
-            MSP_GBAR();
+            MSP_GBAR(1);
             if (worker) step_tri<true>(a, t, smem, red, tid, w, lane);
-            MSP_GBAR();
+            MSP_GBAR(1);
             if (worker) step_Z(a, t, smem, red, wsum, tid, w, lane);
-            MSP_GBAR();
+            MSP_GBAR(1);
             if (worker) step_P(a, t, sv, tid, w, lane);
-            MSP_GBAR();
+            MSP_GBAR(1);
             if (worker) consume_A(a, ring, full, empty, hdr, kring, red, wsum, w, lane);
             else if (lane == 0)
                 producer<false>(a, ring, full, empty, hdr, kring, &ctl->ctrA, a.iact + (t & 1) * a.count);
-            MSP_GBAR();
+            MSP_GBAR(0);
             if (worker) step_X(a, t, wsum, sv, tid, w, lane);
-            MSP_GBAR();
+            MSP_GBAR(1);
         }
-        if (worker) step_back(a, tid);
-        MSP_GBAR();
+        if (worker) step_back(a, wsumd, tid, w, lane);
+        MSP_GBAR(2);
+        if (blockIdx.x == 0 && tid == 0) ctl->sweepsR += 1;
         if (worker)
             consume_R(a, ring, full, empty, hdr, kring, reinterpret_cast<double*>(red), wsumd, w, lane);
         else if (lane == 0)
             producer<true>(a, ring, full, empty, hdr, kring, &ctl->ctrR, a.istep);
-        MSP_GBAR();
+        MSP_GBAR(2);
     }
 #undef MSP_GBAR
 }
@@ -1054,6 +1103,7 @@ struct msp_batch_s {
     int last_max_steps = 0;
     int last_mixed = 1;
     double last_tol = 0.0;
+    int last_crit = 0;
 };
 
 namespace {
@@ -1290,15 +1340,19 @@ msp_status msp_batch_create(msp_ctx* ctx, int count, const msp_instance* inst, m
     const size_t sbytes = (size_t)ns * kM * 4;
     const size_t o_g = take(sbytes), o_y1 = take(sbytes), o_y2 = take(sbytes);
     const size_t pbytes = (size_t)nbt * kM * 8;
-    size_t o_p[5];
-    for (int q = 0; q < 5; ++q) o_p[q] = take(pbytes);
+    size_t o_p[6];
+    for (int q = 0; q < 6; ++q) o_p[q] = take(pbytes);
     const size_t cbytes = (size_t)cnt * kM * 8;
     const size_t o_bb = take(cbytes), o_sc = take(cbytes), o_al = take(cbytes), o_rz = take(2 * cbytes);
     const size_t o_act = take((size_t)cnt * kM * 4), o_fin = take((size_t)cnt * kM * 4);
     const size_t o_iact = take((size_t)cnt * 8);
     const size_t o_istep = take((size_t)cnt * 4), o_iters = take((size_t)cnt * 4);
     const size_t o_ierr = take((size_t)cnt * 4), o_isteps = take((size_t)cnt * 4);
-    const size_t o_rel = take((size_t)cnt * 8);
+    const size_t o_rel = take((size_t)cnt * 8), o_berr = take((size_t)cnt * 8);
+    const size_t o_anorm = take((size_t)cnt * 8);
+    int64_t nmax = 0;
+    for (int k = 0; k < count; ++k) nmax = std::max<int64_t>(nmax, inst[k].n);
+    const size_t o_nwork = take((size_t)nmax * 16);
     const size_t o_ctl = take(sizeof(BCtl));
     const size_t total = off;
     if (cudaMallocAsync(&b->mem, total, ctx->stream) != cudaSuccess) {
@@ -1351,8 +1405,8 @@ msp_status msp_batch_create(msp_ctx* ctx, int count, const msp_instance* inst, m
     A.G = (float*)(base + o_g);
     A.Y1 = (float*)(base + o_y1);
     A.Y2 = (float*)(base + o_y2);
-    double** pp[5] = {&A.p_pq, &A.p_rr, &A.p_zr, &A.p_zq, &A.p_r64};
-    for (int q = 0; q < 5; ++q) *pp[q] = (double*)(base + o_p[q]);
+    double** pp[6] = {&A.p_pq, &A.p_rr, &A.p_zr, &A.p_zq, &A.p_r64, &A.p_xx};
+    for (int q = 0; q < 6; ++q) *pp[q] = (double*)(base + o_p[q]);
     A.bb = (double*)(base + o_bb);
     A.scale = (double*)(base + o_sc);
     A.alpha = (double*)(base + o_al);
@@ -1365,7 +1419,15 @@ msp_status msp_batch_create(msp_ctx* ctx, int count, const msp_instance* inst, m
     A.ierr = (int*)(base + o_ierr);
     A.isteps = (int*)(base + o_isteps);
     A.rel = (double*)(base + o_rel);
+    A.berr = (double*)(base + o_berr);
+    A.anorm = (const double*)(base + o_anorm);
     A.ctl = (BCtl*)(base + o_ctl);
+    // L <= |A_k|_2 for the backward-error rule (one pass over each A)
+    for (int k = 0; k < count; ++k) {
+        const msp_status st = msp_norm_lb_launch(ctx, inst[k].A, MSP_F32, inst[k].n, inst[k].lda,
+                                                 (double*)(base + o_nwork), (double*)(base + o_anorm) + k);
+        if (st != MSP_OK) return fail(st);
+    }
     // the host copies above are from pageable memory: complete before return
     MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     *out = b;
@@ -1384,7 +1446,11 @@ msp_status msp_batch_solve(msp_ctx* ctx, msp_batch_t* b, const msp_opts* opts, m
         return msp_set_error(ctx, MSP_EINVAL, "batch_solve: precision must be MSP_PREC_MIXED or MSP_PREC_FP32");
     msp::DeviceGuard guard(ctx->device);
     const bool mixed = o.precision == MSP_PREC_MIXED;
+    if (o.criterion != MSP_STOP_RESIDUAL && o.criterion != MSP_STOP_BACKWARD)
+        return msp_set_error(ctx, MSP_EINVAL, "batch_solve: unknown criterion %d", o.criterion);
     BArgs a = b->args;
+    a.crit = o.criterion;
+    a.tol = o.tol;
     a.tol2 = o.tol * o.tol;
     const double rt = mixed ? std::max(o.refine_tol, o.tol) : o.tol;
     a.rtol2 = rt * rt;
@@ -1393,6 +1459,7 @@ msp_status msp_batch_solve(msp_ctx* ctx, msp_batch_t* b, const msp_opts* opts, m
     b->last_max_steps = a.max_steps;
     b->last_mixed = mixed ? 1 : 0;
     b->last_tol = o.tol;
+    b->last_crit = o.criterion;
     // per-solve state: control block and per-instance counters
     MSP_CUDA_TRY(ctx, cudaMemsetAsync(a.ctl, 0, sizeof(BCtl), ctx->stream));
     MSP_CUDA_TRY(ctx, cudaMemsetAsync(a.iters, 0, (size_t)a.count * 4, ctx->stream));
@@ -1422,9 +1489,11 @@ msp_status msp_batch_info(msp_ctx* ctx, const msp_batch_t* b, msp_info* infos) {
     msp::DeviceGuard guard(ctx->device);
     const int cnt = b->count;
     std::vector<int> iters(cnt), ierr(cnt), steps(cnt);
-    std::vector<double> rel(cnt);
+    std::vector<double> rel(cnt), berr(cnt), anorm(cnt);
     BCtl ctl;
     const BArgs& a = b->args;
+    MSP_CUDA_TRY(ctx, cudaMemcpyAsync(berr.data(), a.berr, cnt * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    MSP_CUDA_TRY(ctx, cudaMemcpyAsync(anorm.data(), a.anorm, cnt * 8, cudaMemcpyDeviceToHost, ctx->stream));
     MSP_CUDA_TRY(ctx, cudaMemcpyAsync(iters.data(), a.iters, cnt * 4, cudaMemcpyDeviceToHost, ctx->stream));
     MSP_CUDA_TRY(ctx, cudaMemcpyAsync(ierr.data(), a.ierr, cnt * 4, cudaMemcpyDeviceToHost, ctx->stream));
     MSP_CUDA_TRY(ctx, cudaMemcpyAsync(steps.data(), a.isteps, cnt * 4, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1435,15 +1504,24 @@ msp_status msp_batch_info(msp_ctx* ctx, const msp_batch_t* b, msp_info* infos) {
     for (int k = 0; k < cnt; ++k) {
         msp_info& I = infos[k];
         std::memset(&I, 0, sizeof I);
+        // batch-wide device-timer split of the one launch (same in every entry)
+        I.gemv_launches = ctl.sweepsA;
+        I.resid_launches = ctl.sweepsR;
+        I.gemv_ms = 1e-6 * (double)ctl.t_ns[0];
+        I.level2_ms = 1e-6 * (double)ctl.t_ns[1];
+        I.resid_ms = 1e-6 * (double)ctl.t_ns[2];
         I.outer_iters = iters[k];
         I.refine_steps = steps[k];
         I.rel_resid = rel[k];
+        I.backward_err = berr[k];
+        I.norm_lb = anorm[k];
         I.lambda_tilde = b->f[k]->lam_tilde;
         I.shift = b->f[k]->shift;
         I.shift_retries = b->f[k]->retries;
         msp_status st = (msp_status)ierr[k];
         if (st == MSP_OK && ctl.error) st = (msp_status)ctl.error;
-        if (st == MSP_OK && b->last_mixed && !(rel[k] <= b->last_tol)) st = MSP_ENOCONV;
+        const double achieved = b->last_crit == MSP_STOP_BACKWARD ? berr[k] : rel[k];
+        if (st == MSP_OK && b->last_mixed && !(achieved <= b->last_tol)) st = MSP_ENOCONV;
         I.status = st;
         if (first == MSP_OK && st != MSP_OK) first = st;
     }
@@ -1452,6 +1530,27 @@ msp_status msp_batch_info(msp_ctx* ctx, const msp_batch_t* b, msp_info* infos) {
                              ctl.error);
     if (first != MSP_OK)
         return msp_set_error(ctx, first, "batch_solve: at least one instance ended with status %d", (int)first);
+    return MSP_OK;
+}
+
+msp_status msp_batch_stats(msp_ctx* ctx, const msp_batch_t* b, double* stats) {
+    if (!ctx) return msp_set_error(nullptr, MSP_EINVAL, "ctx is NULL");
+    if (!b || !stats) return msp_set_error(ctx, MSP_EINVAL, "batch_stats: NULL argument");
+    msp::DeviceGuard guard(ctx->device);
+    BCtl ctl;
+    MSP_CUDA_TRY(ctx, cudaMemcpyAsync(&ctl, b->args.ctl, sizeof ctl, cudaMemcpyDeviceToHost, ctx->stream));
+    MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    int64_t dense = 0;
+    for (const BInst& H : b->hinst) dense += (int64_t)H.n_pad * H.n_pad;
+    stats[0] = (double)ctl.sweepsA;
+    stats[1] = (double)ctl.sweepsR;
+    stats[2] = (double)ctl.tilesA * kTileBytes;
+    stats[3] = (double)ctl.tilesR * kTileBytes;
+    for (int c = 0; c < 4; ++c) stats[4 + c] = 1e-6 * (double)ctl.t_ns[c];
+    stats[8] = (double)dense * 4.0;
+    int64_t nn = 0;
+    for (const BInst& H : b->hinst) nn += (int64_t)H.n * H.n;
+    stats[9] = (double)nn * 4.0;
     return MSP_OK;
 }
 

@@ -195,3 +195,25 @@ def test_batch_bad_arguments(ctx):
     with pytest.raises(MspError):
         B17 = torch.zeros((100, 17), dtype=torch.float64, device="cuda")
         ctx.batch([dict(A=A, B=B17, lam=LAM, s=32)])            # m > 16
+
+
+def test_batch_backward_error_rule(ctx):
+    """Smooth and rough kernels under the backward-error rule: every column's
+    normwise backward error, recomputed here with the exact |A|_2, is at most
+    tol, and the library's L matches the oracle's bound."""
+    cases = [(1500, 0.2, 16, 71, 320), (800, 0.05, 7, 72, 192)]
+    insts = [_instance(*c) for c in cases]
+    dev = [dict(A=torch.from_numpy(K).cuda(), B=torch.from_numpy(B).cuda(), lam=LAM, s=c[4])
+           for (K, B), c in zip(insts, cases)]
+    bt = ctx.batch(dev)
+    infos = bt.solve(tol=1e-10, refine_tol=1e-4, criterion="backward")
+    for k, ((K, B), info) in enumerate(zip(insts, infos)):
+        K64 = K.astype(np.float64)
+        X = bt.X(k).cpu().numpy()
+        assert info["status"] == 0 and info["backward_err"] <= 1e-10
+        assert info["norm_lb"] == pytest.approx(reference.norm_lower_bound(K64), rel=1e-12)
+        top = float(np.linalg.eigvalsh(K64)[-1])
+        for j in range(B.shape[1]):
+            eta = reference.backward_error(K64, X[:, j], B[:, j], LAM, norm_A=top)
+            assert eta <= 1e-10
+    bt.close()

@@ -282,3 +282,32 @@ def test_negative_definite_reports_not_pd(ctx):
     with pytest.raises(MspError) as e:
         ctx.solve(f, A_dev, b, 1e-2, precision="fp64")
     assert e.value.status == 4
+
+
+# ---- certified |A|_2 lower bound and the backward-error stopping rule
+
+@pytest.mark.parametrize("name,n,seed", [("rbf", 1500, 2), ("outlier", 700, 1)])
+def test_norm_lower_bound_matches_oracle(ctx, name, n, seed):
+    w = make_workload(name, seed=seed, n=n)
+    A = np.asarray(w.A)
+    dt = torch.float32 if A.dtype == np.float32 else torch.float64
+    L = ctx.norm_lower_bound(_cuda(A, dt))
+    Lo = reference.norm_lower_bound(A.astype(np.float64))
+    assert abs(L - Lo) <= 1e-12 * Lo
+
+
+def test_solve_backward_error_rule(ctx):
+    w = make_workload("rbf", seed=4, n=2048)
+    A = _cuda(w.A)
+    sk = ctx.sketch(A, s=128)
+    f = ctx.nystrom(sk, lam=w.lam, phi=0)
+    x, info = ctx.solve(f, A, _cuda(w.b), lam=w.lam, max_inner=0, criterion="backward", tol=1e-10,
+                        refine_tol=1e-4)
+    x = x.cpu().numpy()
+    A64 = np.asarray(w.A, dtype=np.float64)
+    assert info["norm_lb"] == pytest.approx(reference.norm_lower_bound(A64), rel=1e-12)
+    assert info["backward_err"] <= 1e-10
+    top = float(np.linalg.eigvalsh(A64)[-1])
+    eta = reference.backward_error(A64, x, w.b, w.lam, norm_A=top)
+    assert eta <= info["backward_err"] * (1 + 1e-6) + 1e-16
+    assert eta <= 1e-10
