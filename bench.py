@@ -289,7 +289,8 @@ def run_batched(args, ctx, dev, rank, peak):
             "outer_iters_max": max(i["outer_iters"] for i in infos),
             "refine_steps_max": max(i["refine_steps"] for i in infos),
             "a_passes": st["a_passes"], "resid_passes": st["resid_passes"],
-            "phase_ms": {"a_pass": st["a_ms"], "level2": st["level2_ms"], "residual": st["resid_ms"],
+            "phase_ms": {"a_pass": st["a_ms"], "g_CtR": st["g_ms"], "tri_Linv": st["tri_ms"],
+                         "z_R_minus_CY": st["z_ms"], "vector": st["vec_ms"], "residual": st["resid_ms"],
                          "checks": st["check_ms"]},
             "a_pass_roofline": {"bound": "hbm", "achieved": a_gbs, "peak": peak, "unit": "GB/s",
                                 "frac": (a_gbs / peak) if a_gbs else None,

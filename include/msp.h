@@ -326,13 +326,14 @@ MSP_API msp_status msp_batch_solve(msp_ctx* ctx, msp_batch_t* batch, const msp_o
 MSP_API msp_status msp_batch_info(msp_ctx* ctx, const msp_batch_t* batch, msp_info* infos);
 
 /* Counters of the last msp_batch_solve (synchronises the context's stream),
- * written to stats[0..9]: [0] level-1 A passes, [1] residual passes,
+ * written to stats[0..12]: [0] level-1 A passes, [1] residual passes,
  * [2] bytes of A streamed by the level-1 passes, [3] by the residual passes
- * (instances whose columns had all converged are skipped), [4..7] device-
- * timer milliseconds spent in the A passes, the level-2 and vector steps,
- * the residual passes with the X update, and the convergence checks,
- * [8] bytes of one full pass over every tiled A (sum of n_pad^2 * 4),
- * [9] sum of n^2 * 4. The times are read by one block between grid
+ * (instances whose columns had all converged are skipped), [4..10] device-
+ * timer milliseconds of the A passes, G = C^T R, the two triangular
+ * applications of L^{-1}, Z = (R - C Y) / lambda~, the vector updates (P,
+ * X, R), the residual passes with the X update, and the convergence checks,
+ * [11] bytes of one full pass over every tiled A (sum of n_pad^2 * 4),
+ * [12] sum of n^2 * 4. The times are read by one block between grid
  * barriers, so each class includes its barrier. */
 MSP_API msp_status msp_batch_stats(msp_ctx* ctx, const msp_batch_t* batch, double* stats);
 

@@ -138,10 +138,10 @@ class Batch:
 
     def stats(self) -> dict:
         """Counters and device-timer split of the last solve (msp_batch_stats)."""
-        v = (C.c_double * 10)()
+        v = (C.c_double * 13)()
         L.check(self.ctx.ptr, self.ctx.lib.msp_batch_stats(self.ctx.ptr, self.handle, v))
-        keys = ("a_passes", "resid_passes", "a_bytes", "resid_bytes", "a_ms", "level2_ms",
-                "resid_ms", "check_ms", "dense_pass_bytes", "nn_bytes")
+        keys = ("a_passes", "resid_passes", "a_bytes", "resid_bytes", "a_ms", "g_ms", "tri_ms",
+                "z_ms", "vec_ms", "resid_ms", "check_ms", "dense_pass_bytes", "nn_bytes")
         return dict(zip(keys, list(v)))
 
     def close(self) -> None:

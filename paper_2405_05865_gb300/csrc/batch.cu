@@ -70,6 +70,9 @@ constexpr int kVsOffset = kMvTiles * kTileBytes;          // 96 KB
 // S2 ring: C tile + R tile per stage
 constexpr int kS2Stage = kTileBytes + kRB * kM * 4;       // 40 KB
 
+// device-timer classes of BCtl::t_ns
+enum { kTA = 0, kTG, kTTri, kTZ, kTVec, kTResid, kTCheck, kTimerClasses };
+
 struct BInst {
     const float* At;      // tile-major A
     const float* C;       // n x s_pad
@@ -94,13 +97,13 @@ struct BCtl {
     int active[2];
     int unfinished[2];
     int sweepsA, sweepsR;     // A passes and residual passes run
+    int ctrG, ctrT1, ctrT2, ctrZ;   // dynamic item counters of S2, S3, S4, S5
     int pad0;
     unsigned long long tilesA;   // A tiles streamed by the level-1 passes
     unsigned long long tilesR;   // A tiles streamed by the residual passes
     // device-timer nanoseconds per step class, taken by block 0 between grid
-    // barriers: 0 A pass, 1 level-2 and vector steps, 2 residual and X
-    // update, 3 convergence checks and set-up of a correction solve
-    unsigned long long t_ns[4];
+    // barriers (each includes its barrier)
+    unsigned long long t_ns[kTimerClasses];
 };
 
 struct BArgs {
@@ -319,7 +322,7 @@ __device__ __noinline__ void producer(const BArgs& a, unsigned char* ring, uint6
                 stop = true;
                 break;
             }
-            hdr[s] = make_int2(it, kt);
+            hdr[s] = make_int2(it, 2 * kt + (kt == nk - 1 ? 1 : 0));
             if (kt == 0) atomicAdd(kResid ? &a.ctl->tilesR : &a.ctl->tilesA, (unsigned long long)nk);
             const BInst& I = a.inst[inst];
             const float* At = I.At + ((int64_t)rb * nk + kt) * kTileFloats;
@@ -366,9 +369,9 @@ __device__ __noinline__ void consume_A(const BArgs& a, unsigned char* ring, uint
         fma_tile(acc, T, T + kTileFloats, w, lane);
         __syncwarp();
         if (lane == 0) msp::mbar_arrive(&empty[s]);
+        if (!(h.y & 1)) continue;
         const int2 item = a.rows[h.x];
         const BInst& I = a.inst[item.x];
-        if (h.y != I.n_pad / kKT - 1) continue;
         // ---- row block complete
         float out[8];
         reduce_scatter(acc, red, out, w, lane);
@@ -419,9 +422,9 @@ __device__ __noinline__ void consume_R(const BArgs& a, unsigned char* ring, uint
         comp_tile(s, c, T, T + kTileFloats, T + kTileFloats + kSliceFloats, h, kg, lane);
         __syncwarp();
         if (lane == 0) msp::mbar_arrive(&empty[st]);
+        if (!(hd.y & 1)) continue;
         const int2 item = a.rows[hd.x];
         const BInst& I = a.inst[item.x];
-        if (hd.y != I.n_pad / kKT - 1) continue;
         // ---- row block complete: combine the 4 column groups in FP64
 #pragma unroll
         for (int i = 0; i < 2; ++i)
@@ -517,6 +520,16 @@ __device__ __forceinline__ void my_range(int n, int& i0, int& i1) {
     i1 = (int)((int64_t)n * (blockIdx.x + 1) / gridDim.x);
 }
 
+// Dynamic item claim for the worker threads: thread 0 takes the next index
+// of the step's counter and shares it through `slot`.
+__device__ __forceinline__ int claim(int* ctr, int* slot, int tid) {
+    if (tid == 0) *slot = atomicAdd(ctr, 1);
+    msp::bar_workers<kWorkers>();
+    const int it = *(volatile int*)slot;
+    msp::bar_workers<kWorkers>();
+    return it;
+}
+
 // R64 = B (X = 0), partials of |b|^2.
 __device__ __forceinline__ void step_init(const BArgs& a, double* wsumd, int tid, int w, int lane) {
     int i0, i1;
@@ -608,6 +621,7 @@ __device__ __forceinline__ void step_scale(const BArgs& a, int step, float* wsum
         a.ctl->active[1] = 0;
         a.ctl->unfinished[(step + 1) & 1] = 0;
         a.ctl->ctrA = 0;
+        a.ctl->ctrG = a.ctl->ctrT1 = a.ctl->ctrT2 = a.ctl->ctrZ = 0;
     }
     int i0, i1;
     my_range(a.nrows, i0, i1);
@@ -649,10 +663,13 @@ __device__ __forceinline__ void step_scale(const BArgs& a, int step, float* wsum
 }
 
 // S2: convergence flags (one block per instance), then G = C^T R by strips.
-__device__ __noinline__ void step_G(const BArgs& a, int t, unsigned char* smem, float* red, int tid, int w, int lane) {
+__device__ __noinline__ void step_G(const BArgs& a, int t, unsigned char* smem, float* red, int* slot,
+                                    int tid, int w, int lane) {
     const int cur = t & 1, prev = cur ^ 1;
     float* ring = reinterpret_cast<float*>(smem);
-    for (int it = blockIdx.x; it < a.nstrips; it += gridDim.x) {
+    for (;;) {
+        const int it = claim(&a.ctl->ctrG, slot, tid);
+        if (it >= a.nstrips) break;
         const int2 item = a.strips[it];
         const int i = item.x;
         const BInst& I = a.inst[i];
@@ -758,11 +775,14 @@ __device__ __noinline__ void step_G(const BArgs& a, int t, unsigned char* smem, 
 
 // S3 / S4: Y_out[chunk] = L^{-1} G or L^{-T} Y1 (triangular k range).
 template <bool kUpper>
-__device__ __noinline__ void step_tri(const BArgs& a, int t, unsigned char* smem, float* red, int tid, int w, int lane) {
+__device__ __noinline__ void step_tri(const BArgs& a, int t, unsigned char* smem, float* red, int* slot,
+                                      int tid, int w, int lane) {
     const int cur = t & 1;
     float* tiles = reinterpret_cast<float*>(smem);
     float* Vs = reinterpret_cast<float*>(smem + kVsOffset);
-    for (int it = blockIdx.x; it < a.nchunks; it += gridDim.x) {
+    for (;;) {
+        const int it = claim(kUpper ? &a.ctl->ctrT2 : &a.ctl->ctrT1, slot, tid);
+        if (it >= a.nchunks) break;
         const int2 item = a.chunks[it];
         const BInst& I = a.inst[item.x];
         if (!ld_volatile(&a.iact[cur * a.count + item.x])) continue;
@@ -788,15 +808,15 @@ __device__ __noinline__ void step_tri(const BArgs& a, int t, unsigned char* smem
 }
 
 // S5: Z = (R - C Y2) / lam~ by row blocks, partials of z.r and z.q.
-__device__ __noinline__ void step_Z(const BArgs& a, int t, unsigned char* smem, float* red, float* wsum, int tid,
-                       int w, int lane) {
+__device__ __noinline__ void step_Z(const BArgs& a, int t, unsigned char* smem, float* red, float* wsum,
+                                    int* slot, int tid, int w, int lane) {
     const int cur = t & 1;
     float* tiles = reinterpret_cast<float*>(smem);
     float* Vs = reinterpret_cast<float*>(smem + kVsOffset);
-    int i0, i1;
-    my_range(a.nrows, i0, i1);
     int staged = -1;
-    for (int it = i0; it < i1; ++it) {
+    for (;;) {
+        const int it = claim(&a.ctl->ctrZ, slot, tid);
+        if (it >= a.nrows) break;
         const int2 item = a.rows[it];
         const BInst& I = a.inst[item.x];
         if (!ld_volatile(&a.iact[cur * a.count + item.x])) continue;
@@ -844,27 +864,33 @@ __device__ __forceinline__ void step_P(const BArgs& a, int t, float* sv, int tid
     const int cur = t & 1, prev = cur ^ 1;
     int i0, i1;
     my_range(a.nrows, i0, i1);
+    int cached = -1;
     for (int it = i0; it < i1; ++it) {
         const int2 item = a.rows[it];
         const BInst& I = a.inst[item.x];
         if (!ld_volatile(&a.iact[cur * a.count + item.x])) continue;
-        if (w == 0 && lane < 16) {
-            const int c = lane, gi = item.x * kM + c;
-            double rzn = 0.0, zq = 0.0;
-            for (int b = 0; b < I.nb; ++b) {
-                rzn += a.p_zr[((int64_t)I.boff + b) * kM + c];
-                zq += a.p_zq[((int64_t)I.boff + b) * kM + c];
+        // beta of the instance: once per instance met by this block
+        if (item.x != cached || item.y == 0) {
+            msp::bar_workers<kWorkers>();     // the previous item's readers of sv are done
+            if (w == 0 && lane < 16) {
+                const int c = lane, gi = item.x * kM + c;
+                double rzn = 0.0, zq = 0.0;
+                for (int b = 0; b < I.nb; ++b) {
+                    rzn += a.p_zr[((int64_t)I.boff + b) * kM + c];
+                    zq += a.p_zq[((int64_t)I.boff + b) * kM + c];
+                }
+                const double rzo = a.rz[(int64_t)prev * a.count * kM + gi];
+                double beta = 0.0;
+                if (t > 0 && a.act[gi] && rzo > 0.0 && isfinite(rzo)) beta = -a.alpha[gi] * zq / rzo;
+                sv[c] = (float)beta;
+                if (item.y == 0) {
+                    a.rz[(int64_t)cur * a.count * kM + gi] = rzn;
+                    if (a.act[gi] && !(rzn > 0.0)) atomicCAS(&a.ierr[item.x], 0, (int)MSP_ENOTPD);
+                }
             }
-            const double rzo = a.rz[(int64_t)prev * a.count * kM + gi];
-            double beta = 0.0;
-            if (t > 0 && a.act[gi] && rzo > 0.0 && isfinite(rzo)) beta = -a.alpha[gi] * zq / rzo;
-            sv[c] = (float)beta;
-            if (item.y == 0) {
-                a.rz[(int64_t)cur * a.count * kM + gi] = rzn;
-                if (a.act[gi] && !(rzn > 0.0)) atomicCAS(&a.ierr[item.x], 0, (int)MSP_ENOTPD);
-            }
+            cached = item.x;
+            msp::bar_workers<kWorkers>();
         }
-        msp::bar_workers<kWorkers>();
         const int row = item.y * kRB + (tid >> 1), ch = tid & 1;
         const int64_t vrow = (int64_t)I.voff + row;
 #pragma unroll
@@ -876,34 +902,42 @@ __device__ __forceinline__ void step_P(const BArgs& a, int t, float* sv, int tid
                 make_float4(fmaf(sv[off + 0], p.x, z.x), fmaf(sv[off + 1], p.y, z.y),
                             fmaf(sv[off + 2], p.z, z.z), fmaf(sv[off + 3], p.w, z.w)));
         }
-        msp::bar_workers<kWorkers>();
     }
+    msp::bar_workers<kWorkers>();
 }
 
 // S1: alpha = rz / p^T q, X_w += alpha P, R -= alpha Q, partials of |r|^2.
 __device__ __forceinline__ void step_X(const BArgs& a, int t, float* wsum, float* sv, int tid, int w, int lane) {
     const int cur = t & 1;
-    if (blockIdx.x == 0 && tid == 0) a.ctl->ctrA = 0;
+    if (blockIdx.x == 0 && tid == 0) {
+        a.ctl->ctrA = 0;
+        a.ctl->ctrG = a.ctl->ctrT1 = a.ctl->ctrT2 = a.ctl->ctrZ = 0;
+    }
     int i0, i1;
     my_range(a.nrows, i0, i1);
+    int cached = -1;
     for (int it = i0; it < i1; ++it) {
         const int2 item = a.rows[it];
         const BInst& I = a.inst[item.x];
         if (!ld_volatile(&a.iact[cur * a.count + item.x])) continue;
-        if (w == 0 && lane < 16) {
-            const int c = lane, gi = item.x * kM + c;
-            double al = 0.0;
-            if (a.act[gi]) {
-                double pq = 0.0;
-                for (int b = 0; b < I.nb; ++b) pq += a.p_pq[((int64_t)I.boff + b) * kM + c];
-                const double rz = a.rz[(int64_t)cur * a.count * kM + gi];
-                if (pq > 0.0 && isfinite(pq)) al = rz / pq;
-                else atomicCAS(&a.ierr[item.x], 0, isfinite(pq) ? (int)MSP_ENOTPD : (int)MSP_ENONFINITE);
+        // alpha of the instance: once per instance met by this block
+        if (item.x != cached || item.y == 0) {
+            if (w == 0 && lane < 16) {
+                const int c = lane, gi = item.x * kM + c;
+                double al = 0.0;
+                if (a.act[gi]) {
+                    double pq = 0.0;
+                    for (int b = 0; b < I.nb; ++b) pq += a.p_pq[((int64_t)I.boff + b) * kM + c];
+                    const double rz = a.rz[(int64_t)cur * a.count * kM + gi];
+                    if (pq > 0.0 && isfinite(pq)) al = rz / pq;
+                    else atomicCAS(&a.ierr[item.x], 0, isfinite(pq) ? (int)MSP_ENOTPD : (int)MSP_ENONFINITE);
+                }
+                sv[c] = (float)al;
+                if (item.y == 0) a.alpha[gi] = al;
             }
-            sv[c] = (float)al;
-            if (item.y == 0) a.alpha[gi] = al;
+            cached = item.x;
+            msp::bar_workers<kWorkers>();
         }
-        msp::bar_workers<kWorkers>();
         const int row = item.y * kRB + (tid >> 1), ch = tid & 1;
         const int64_t vrow = (int64_t)I.voff + row;
         float d[8];
@@ -989,6 +1023,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_batch_solve(BArgs a) {
     double* wsumd = reinterpret_cast<double*>(misc + 128);
     float* sv = reinterpret_cast<float*>(misc + 1152);        // 16 per-column scalars
     double* sd = reinterpret_cast<double*>(misc + 1280);      // 16 per-column scalars
+    int* slot = reinterpret_cast<int*>(misc + 1408);          // claimed item index
 
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const bool worker = w < kWorkWarps;
@@ -1016,45 +1051,45 @@ __global__ void __launch_bounds__(kThreads, 1) k_batch_solve(BArgs a) {
     } while (0)
 
     if (worker) step_init(a, wsumd, tid, w, lane);
-    MSP_GBAR(3);
+    MSP_GBAR(kTCheck);
     for (int step = 0;; ++step) {
         step_check(a, step, w, lane);
-        MSP_GBAR(3);
+        MSP_GBAR(kTCheck);
         const int unf = ld_volatile(&ctl->unfinished[step & 1]);
         if (unf == 0 || step >= a.max_steps) break;
         if (worker) step_scale(a, step, wsum, sd, tid, w, lane);
-        MSP_GBAR(3);
+        MSP_GBAR(kTCheck);
         for (int t = 0;; ++t) {
-            if (worker) step_G(a, t, smem, red, tid, w, lane);
-            MSP_GBAR(1);
+            if (worker) step_G(a, t, smem, red, slot, tid, w, lane);
+            MSP_GBAR(kTG);
             if (ld_volatile(&ctl->active[t & 1]) == 0) break;
             if (blockIdx.x == 0 && tid == 0) {
                 ctl->active[(t + 1) & 1] = 0;
                 ctl->sweepsA += 1;
             }
-            if (worker) step_tri<false>(a, t, smem, red, tid, w, lane);
-            MSP_GBAR(1);
-            if (worker) step_tri<true>(a, t, smem, red, tid, w, lane);
-            MSP_GBAR(1);
-            if (worker) step_Z(a, t, smem, red, wsum, tid, w, lane);
-            MSP_GBAR(1);
+            if (worker) step_tri<false>(a, t, smem, red, slot, tid, w, lane);
+            MSP_GBAR(kTTri);
+            if (worker) step_tri<true>(a, t, smem, red, slot, tid, w, lane);
+            MSP_GBAR(kTTri);
+            if (worker) step_Z(a, t, smem, red, wsum, slot, tid, w, lane);
+            MSP_GBAR(kTZ);
             if (worker) step_P(a, t, sv, tid, w, lane);
-            MSP_GBAR(1);
+            MSP_GBAR(kTVec);
             if (worker) consume_A(a, ring, full, empty, hdr, kring, red, wsum, w, lane);
             else if (lane == 0)
                 producer<false>(a, ring, full, empty, hdr, kring, &ctl->ctrA, a.iact + (t & 1) * a.count);
-            MSP_GBAR(0);
+            MSP_GBAR(kTA);
             if (worker) step_X(a, t, wsum, sv, tid, w, lane);
-            MSP_GBAR(1);
+            MSP_GBAR(kTVec);
         }
         if (worker) step_back(a, wsumd, tid, w, lane);
-        MSP_GBAR(2);
+        MSP_GBAR(kTResid);
         if (blockIdx.x == 0 && tid == 0) ctl->sweepsR += 1;
         if (worker)
             consume_R(a, ring, full, empty, hdr, kring, reinterpret_cast<double*>(red), wsumd, w, lane);
         else if (lane == 0)
             producer<true>(a, ring, full, empty, hdr, kring, &ctl->ctrR, a.istep);
-        MSP_GBAR(2);
+        MSP_GBAR(kTResid);
     }
 #undef MSP_GBAR
 }
@@ -1507,9 +1542,9 @@ msp_status msp_batch_info(msp_ctx* ctx, const msp_batch_t* b, msp_info* infos) {
         // batch-wide device-timer split of the one launch (same in every entry)
         I.gemv_launches = ctl.sweepsA;
         I.resid_launches = ctl.sweepsR;
-        I.gemv_ms = 1e-6 * (double)ctl.t_ns[0];
-        I.level2_ms = 1e-6 * (double)ctl.t_ns[1];
-        I.resid_ms = 1e-6 * (double)ctl.t_ns[2];
+        I.gemv_ms = 1e-6 * (double)ctl.t_ns[kTA];
+        I.level2_ms = 1e-6 * (double)(ctl.t_ns[kTG] + ctl.t_ns[kTTri] + ctl.t_ns[kTZ] + ctl.t_ns[kTVec]);
+        I.resid_ms = 1e-6 * (double)ctl.t_ns[kTResid];
         I.outer_iters = iters[k];
         I.refine_steps = steps[k];
         I.rel_resid = rel[k];
@@ -1546,11 +1581,11 @@ msp_status msp_batch_stats(msp_ctx* ctx, const msp_batch_t* b, double* stats) {
     stats[1] = (double)ctl.sweepsR;
     stats[2] = (double)ctl.tilesA * kTileBytes;
     stats[3] = (double)ctl.tilesR * kTileBytes;
-    for (int c = 0; c < 4; ++c) stats[4 + c] = 1e-6 * (double)ctl.t_ns[c];
-    stats[8] = (double)dense * 4.0;
+    for (int c = 0; c < kTimerClasses; ++c) stats[4 + c] = 1e-6 * (double)ctl.t_ns[c];
+    stats[11] = (double)dense * 4.0;
     int64_t nn = 0;
     for (const BInst& H : b->hinst) nn += (int64_t)H.n * H.n;
-    stats[9] = (double)nn * 4.0;
+    stats[12] = (double)nn * 4.0;
     return MSP_OK;
 }
 
