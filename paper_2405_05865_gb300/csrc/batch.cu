@@ -24,10 +24,12 @@
 //   S6  beta, P = Z + beta P
 //   SA  Q = (A + lam I) P    dynamic items over the row blocks: a producer
 //                            warp streams A tiles + P slices by bulk copy
-//                            into a 4-stage mbarrier ring, 8 warps each own
-//                            8 of the 64 columns of a tile and 4 rows x 16
-//                            right-hand sides per lane (FP32 FMA: 16 flops
-//                            per loaded element keep this pass HBM-bound)
+//                            into a 4-stage mbarrier ring; each of 8 warps
+//                            takes 8 of the 64 columns of a tile for all 128
+//                            rows on the tensor cores (mma.sync m16n8k8 TF32,
+//                            split 3xTF32 for FP32 accuracy): FP32 FMA at 16
+//                            products per loaded element could not keep up
+//                            with HBM
 //   S1  alpha, X_w += alpha P, R -= alpha Q
 // with a grid barrier between steps. Around it, the FP64 refinement
 // (MSP_PREC_MIXED): R64 = B - (A + lam I) X is formed by the same tile
@@ -139,34 +141,57 @@ __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volati
 
 // ------------------------------------------------------------ tile math
 
-// acc[i][c] += sum over the warp's 8 columns k of the tile of T[lane+32i][k] V[k][c].
-// T: 128 x 64 swizzled tile; V: 64 rows of 16.
-__device__ __forceinline__ void fma_tile(float (&acc)[4][16], const float* __restrict__ T,
+// x = hi + lo with hi the TF32 value nearest x and lo the TF32 value
+// nearest the exact FP32 remainder x - hi ("3xTF32": the products
+// hi*hi + hi*lo + lo*hi keep about FP32 accuracy).
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
+    const float r = x - __uint_as_float(hi);
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
+}
+
+// d += a b on the tensor cores: one 16 x 8 x 8 TF32 product, FP32 accumulate.
+__device__ __forceinline__ void mma_tf32(float& d0, float& d1, float& d2, float& d3, const uint32_t (&a)[4],
+                                         uint32_t b0, uint32_t b1) {
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d0), "+f"(d1), "+f"(d2), "+f"(d3)
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// acc += T[:, 8w..8w+7] V[8w..8w+7, :] for the 128 x 64 swizzled tile T and
+// the 64 x 16 block V: warp w takes one 8-column step of the tile for all
+// 128 rows (eight 16 x 8 x 8 products per 8 right-hand sides) in 3xTF32.
+// Lane (g, t) = (lane / 4, lane % 4) holds rows g, g + 8 and columns t, t + 4
+// of each 16-row A fragment; the tile's granule swizzle (granule j of row r
+// at j ^ (r % 8)) makes those loads hit 32 distinct banks. Accumulator
+// layout: acc[mt / 2][(mt % 2) * 8 + nt * 4 + e] is row 16 mt + g + 8 (e / 2),
+// column 8 nt + 2 t + e % 2.
+__device__ __forceinline__ void mma_tile(float (&acc)[4][16], const float* __restrict__ T,
                                          const float* __restrict__ V, int w, int lane) {
-    const float4* T4 = reinterpret_cast<const float4*>(T);
-    const float4* V4 = reinterpret_cast<const float4*>(V);
-    const int sw = lane & 7;
+    const int g = lane >> 2, t = lane & 3;
+    const int k0 = 8 * w;
+    uint32_t bh[2][2], bl[2][2];
 #pragma unroll
-    for (int gi = 0; gi < 2; ++gi) {
-        const int g = 2 * w + gi;
-        float4 a[4];
+    for (int nt = 0; nt < 2; ++nt) {
+        split_tf32(V[(k0 + t) * kM + 8 * nt + g], bh[nt][0], bl[nt][0]);
+        split_tf32(V[(k0 + t + 4) * kM + 8 * nt + g], bh[nt][1], bl[nt][1]);
+    }
+    const int c0 = ((2 * w) ^ g) * 4 + t, c1 = ((2 * w + 1) ^ g) * 4 + t;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] = T4[(lane + 32 * i) * 16 + (g ^ sw)];
+    for (int mt = 0; mt < 8; ++mt) {
+        const int r0 = 16 * mt + g;
+        uint32_t ah[4], al[4];
+        split_tf32(T[r0 * kKT + c0], ah[0], al[0]);
+        split_tf32(T[(r0 + 8) * kKT + c0], ah[1], al[1]);
+        split_tf32(T[r0 * kKT + c1], ah[2], al[2]);
+        split_tf32(T[(r0 + 8) * kKT + c1], ah[3], al[3]);
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-            const int k = 4 * g + kk;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const float4 v = V4[k * 4 + j];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float av = comp(a[i], kk);
-                    acc[i][4 * j + 0] = fmaf(av, v.x, acc[i][4 * j + 0]);
-                    acc[i][4 * j + 1] = fmaf(av, v.y, acc[i][4 * j + 1]);
-                    acc[i][4 * j + 2] = fmaf(av, v.z, acc[i][4 * j + 2]);
-                    acc[i][4 * j + 3] = fmaf(av, v.w, acc[i][4 * j + 3]);
-                }
-            }
+        for (int nt = 0; nt < 2; ++nt) {
+            float* d = &acc[mt >> 1][(mt & 1) * 8 + nt * 4];
+            mma_tf32(d[0], d[1], d[2], d[3], al, bh[nt][0], bh[nt][1]);
+            mma_tf32(d[0], d[1], d[2], d[3], ah, bl[nt][0], bl[nt][1]);
+            mma_tf32(d[0], d[1], d[2], d[3], ah, bh[nt][0], bh[nt][1]);
         }
     }
 }
@@ -220,24 +245,33 @@ __device__ __forceinline__ void comp_tile(float (&s)[2][16], float (&c)[2][16],
     }
 }
 
-// After fma_tile accumulation over a whole row block: warps exchange through
-// `red` so that warp w ends with rows 16w + (lane & 15), columns
-// 8 (lane >> 4) + 0..7, summed over the 8 column groups in warp order.
+// After mma_tile accumulation over a row block: warps exchange through `red`
+// (8 warps x 128 rows x 16 columns) so that warp w ends with rows
+// 16w + (lane & 15), columns 8 (lane >> 4) + 0..7, summed over the 8 column
+// steps in warp order.
 __device__ __forceinline__ void reduce_scatter(const float (&acc)[4][16], float* red, float (&out)[8],
                                                int w, int lane) {
+    const int g = lane >> 2, t = lane & 3;
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int mt = 0; mt < 8; ++mt)
 #pragma unroll
-        for (int c = 0; c < 16; ++c) red[((w * 4 + i) * 16 + c) * 32 + lane] = acc[i][c];
+        for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int row = 16 * mt + g + 8 * h, col = 8 * nt + 2 * t;
+                const float* d = &acc[mt >> 1][(mt & 1) * 8 + nt * 4 + 2 * h];
+                *reinterpret_cast<float2*>(red + (w * kRB + row) * kM + col) = make_float2(d[0], d[1]);
+            }
     msp::bar_workers<kWorkers>();
-    const int i = w >> 1, srcl = 16 * (w & 1) + (lane & 15), ch = lane >> 4;
+    const int row = 16 * w + (lane & 15), ch = lane >> 4;
 #pragma unroll
-    for (int c8 = 0; c8 < 8; ++c8) {
-        const int c = 8 * ch + c8;
-        float v = 0.f;
+    for (int c8 = 0; c8 < 8; ++c8) out[c8] = 0.f;
 #pragma unroll
-        for (int ww = 0; ww < kWorkWarps; ++ww) v += red[((ww * 4 + i) * 16 + c) * 32 + srcl];
-        out[c8] = v;
+    for (int ww = 0; ww < kWorkWarps; ++ww) {
+        const float4 u0 = ld4(red + (ww * kRB + row) * kM + 8 * ch);
+        const float4 u1 = ld4(red + (ww * kRB + row) * kM + 8 * ch + 4);
+        out[0] += u0.x; out[1] += u0.y; out[2] += u0.z; out[3] += u0.w;
+        out[4] += u1.x; out[5] += u1.y; out[6] += u1.z; out[7] += u1.w;
     }
 }
 
@@ -366,7 +400,7 @@ __device__ __noinline__ void consume_A(const BArgs& a, unsigned char* ring, uint
             return;
         }
         const float* T = reinterpret_cast<const float*>(ring + (size_t)s * kStageBytes);
-        fma_tile(acc, T, T + kTileFloats, w, lane);
+        mma_tile(acc, T, T + kTileFloats, w, lane);
         __syncwarp();
         if (lane == 0) msp::mbar_arrive(&empty[s]);
         if (!(h.y & 1)) continue;
@@ -499,7 +533,7 @@ __device__ __forceinline__ void mv_stream(float (&acc)[4][16], const float* __re
         msp::cp_async_commit();
         msp::cp_async_wait<2>();
         msp::bar_workers<kWorkers>();
-        fma_tile(acc, tiles + (i % kMvTiles) * kTileFloats, Vs + (int64_t)(kt0 + i) * kKT * kM, w, lane);
+        mma_tile(acc, tiles + (i % kMvTiles) * kTileFloats, Vs + (int64_t)(kt0 + i) * kKT * kM, w, lane);
         msp::bar_workers<kWorkers>();
     }
 }
