@@ -29,7 +29,8 @@
 //                            rows on the tensor cores (mma.sync m16n8k8 TF32,
 //                            split 3xTF32 for FP32 accuracy): FP32 FMA at 16
 //                            products per loaded element could not keep up
-//                            with HBM
+//                            with HBM. The level-2 mat-vecs stay on FP32 FMA
+//                            (see fma_tile).
 //   S1  alpha, X_w += alpha P, R -= alpha Q
 // with a grid barrier between steps. Around it, the FP64 refinement
 // (MSP_PREC_MIXED): R64 = B - (A + lam I) X is formed by the same tile
@@ -140,6 +141,61 @@ __device__ __forceinline__ float comp(const float4& v, int k) {
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
 
 // ------------------------------------------------------------ tile math
+
+// acc[i][c] += sum over the warp's 8 columns k of the tile of T[lane+32i][k] V[k][c]
+// in FP32 FMA (the level-2 mat-vecs: the Woodbury form (r - C M2^{-1} C^T r)
+// cancels up to lambda_max / lambda~, so these keep FP32 rounding).
+// T: 128 x 64 swizzled tile; V: 64 rows of 16.
+__device__ __forceinline__ void fma_tile(float (&acc)[4][16], const float* __restrict__ T,
+                                         const float* __restrict__ V, int w, int lane) {
+    const float4* T4 = reinterpret_cast<const float4*>(T);
+    const float4* V4 = reinterpret_cast<const float4*>(V);
+    const int sw = lane & 7;
+#pragma unroll
+    for (int gi = 0; gi < 2; ++gi) {
+        const int g = 2 * w + gi;
+        float4 a[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = T4[(lane + 32 * i) * 16 + (g ^ sw)];
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const int k = 4 * g + kk;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float4 v = V4[k * 4 + j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float av = comp(a[i], kk);
+                    acc[i][4 * j + 0] = fmaf(av, v.x, acc[i][4 * j + 0]);
+                    acc[i][4 * j + 1] = fmaf(av, v.y, acc[i][4 * j + 1]);
+                    acc[i][4 * j + 2] = fmaf(av, v.z, acc[i][4 * j + 2]);
+                    acc[i][4 * j + 3] = fmaf(av, v.w, acc[i][4 * j + 3]);
+                }
+            }
+        }
+    }
+}
+
+// After fma_tile accumulation: warps exchange through `red` so that warp w
+// ends with rows 16w + (lane & 15), columns 8 (lane >> 4) + 0..7, summed
+// over the 8 column groups in warp order.
+__device__ __forceinline__ void reduce_scatter_fma(const float (&acc)[4][16], float* red, float (&out)[8],
+                                                   int w, int lane) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int c = 0; c < 16; ++c) red[((w * 4 + i) * 16 + c) * 32 + lane] = acc[i][c];
+    msp::bar_workers<kWorkers>();
+    const int i = w >> 1, srcl = 16 * (w & 1) + (lane & 15), ch = lane >> 4;
+#pragma unroll
+    for (int c8 = 0; c8 < 8; ++c8) {
+        const int c = 8 * ch + c8;
+        float v = 0.f;
+#pragma unroll
+        for (int ww = 0; ww < kWorkWarps; ++ww) v += red[((ww * 4 + i) * 16 + c) * 32 + srcl];
+        out[c8] = v;
+    }
+}
 
 // x = hi + lo with hi the TF32 value nearest x and lo the TF32 value
 // nearest the exact FP32 remainder x - hi ("3xTF32": the products
@@ -533,7 +589,7 @@ __device__ __forceinline__ void mv_stream(float (&acc)[4][16], const float* __re
         msp::cp_async_commit();
         msp::cp_async_wait<2>();
         msp::bar_workers<kWorkers>();
-        mma_tile(acc, tiles + (i % kMvTiles) * kTileFloats, Vs + (int64_t)(kt0 + i) * kKT * kM, w, lane);
+        fma_tile(acc, tiles + (i % kMvTiles) * kTileFloats, Vs + (int64_t)(kt0 + i) * kKT * kM, w, lane);
         msp::bar_workers<kWorkers>();
     }
 }
@@ -832,7 +888,7 @@ __device__ __noinline__ void step_tri(const BArgs& a, int t, unsigned char* smem
         const float* M = (kUpper ? I.Bu : I.Bl) + (int64_t)item.y * kRB * I.s_pad;
         mv_stream(acc, M, I.s_pad, kRB, kt0, kt1, Vs, tiles, tid, w, lane);
         float out[8];
-        reduce_scatter(acc, red, out, w, lane);
+        reduce_scatter_fma(acc, red, out, w, lane);
         const int ch = lane >> 4;
         float* Y = (kUpper ? a.Y2 : a.Y1) + ((int64_t)I.soff + item.y * kRB + 16 * w + (lane & 15)) * kM + 8 * ch;
         st4(Y, make_float4(out[0], out[1], out[2], out[3]));
@@ -867,7 +923,7 @@ __device__ __noinline__ void step_Z(const BArgs& a, int t, unsigned char* smem, 
         mv_stream(acc, I.C + (int64_t)item.y * kRB * I.s_pad, I.s_pad, rows_valid, 0, I.s_pad / kKT, Vs,
                   tiles, tid, w, lane);
         float out[8];
-        reduce_scatter(acc, red, out, w, lane);
+        reduce_scatter_fma(acc, red, out, w, lane);
         const int ch = lane >> 4;
         const int64_t vrow = (int64_t)I.voff + item.y * kRB + 16 * w + (lane & 15);
         const float4 r0 = ld4(a.R + vrow * kM + 8 * ch), r1 = ld4(a.R + vrow * kM + 8 * ch + 4);
