@@ -243,15 +243,19 @@ def run_batched(args, ctx, dev, rank, peak):
         insts.append(dict(A=K, B=B, lam=sp.lam, s=sp.s))
     rhs_total = sum(sp.m for sp in specs)
     opts = dict(tol=1e-10, refine_tol=args.refine_tol, criterion="backward")
-    # warm-up (also builds the worker contexts)
+    # warm-up (also builds the worker contexts) and the unit-width search
     bt = ctx.batch(insts)
     bt.solve(raise_on_noconv=False, **opts)
+    t0 = time.perf_counter()
+    ut = bt.autotune(0)
+    tune_s = time.perf_counter() - t0
     bt.close()
     torch.cuda.synchronize(dev)
     full = []
     for _ in range(args.batch_steps):
         t0 = time.perf_counter()
         bt = ctx.batch(insts)
+        bt.autotune(ut)
         t1 = time.perf_counter()
         infos = bt.solve(raise_on_noconv=False, **opts)
         t2 = time.perf_counter()
@@ -279,6 +283,7 @@ def run_batched(args, ctx, dev, rank, peak):
                         f"{sum(sp.n * sp.n for sp in specs)}), ell~U(0.05,0.2), lam=1e-2, 16 RHS each, "
                         f"s=min(1024,n/4) rounded to 64, gamma=8, Phi=I, mixed precision to backward error 1e-10 per column",
             "rhs_total": rhs_total,
+            "unit_tiles": ut, "autotune_ms": tune_s * 1e3,
             "value_full": rhs_total / full_s, "value_solve": rhs_total / (solve_ms * 1e-3),
             "unit": "rhs-solves/s", "ms_full": full_s * 1e3, "ms_setup": setup_s * 1e3,
             "ms_solve": solve_ms, "launches_per_solve": launches / args.batch_steps,
@@ -289,6 +294,8 @@ def run_batched(args, ctx, dev, rank, peak):
             "outer_iters_max": max(i["outer_iters"] for i in infos),
             "refine_steps_max": max(i["refine_steps"] for i in infos),
             "a_passes": st["a_passes"], "resid_passes": st["resid_passes"],
+            "c_pass_gbs": {"g_CtR": st["g_bytes"] / (st["g_ms"] * 1e-3) / 1e9 if st["g_ms"] else None,
+                           "z_R_minus_CY": st["z_bytes"] / (st["z_ms"] * 1e-3) / 1e9 if st["z_ms"] else None},
             "phase_ms": {"a_pass": st["a_ms"], "g_CtR": st["g_ms"], "tri_Linv": st["tri_ms"],
                          "z_R_minus_CY": st["z_ms"], "vector": st["vec_ms"], "residual": st["resid_ms"],
                          "checks": st["check_ms"]},

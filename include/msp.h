@@ -326,16 +326,26 @@ MSP_API msp_status msp_batch_solve(msp_ctx* ctx, msp_batch_t* batch, const msp_o
 MSP_API msp_status msp_batch_info(msp_ctx* ctx, const msp_batch_t* batch, msp_info* infos);
 
 /* Counters of the last msp_batch_solve (synchronises the context's stream),
- * written to stats[0..12]: [0] level-1 A passes, [1] residual passes,
+ * written to stats[0..15]: [0] level-1 A passes, [1] residual passes,
  * [2] bytes of A streamed by the level-1 passes, [3] by the residual passes
  * (instances whose columns had all converged are skipped), [4..10] device-
  * timer milliseconds of the A passes, G = C^T R, the two triangular
  * applications of L^{-1}, Z = (R - C Y) / lambda~, the vector updates (P,
  * X, R), the residual passes with the X update, and the convergence checks,
  * [11] bytes of one full pass over every tiled A (sum of n_pad^2 * 4),
- * [12] sum of n^2 * 4. The times are read by one block between grid
- * barriers, so each class includes its barrier. */
+ * [12] sum of n^2 * 4, [13] bytes of C read by G, [14] by Z, [15] the unit
+ * width in tiles. The times are read by one block between grid barriers, so
+ * each class includes its barrier. */
 MSP_API msp_status msp_batch_stats(msp_ctx* ctx, const msp_batch_t* batch, double* stats);
+
+/* Width of the work units of the batched A passes, the tile shape choice of
+ * the batched kernel: a unit is one 128-row block of an A times at most
+ * `*unit_tiles` x 64 columns. *unit_tiles > 0 (a power of two >= 16) sets
+ * it; *unit_tiles == 0 times the A passes of 12 level-1 iterations at every
+ * width from 16 tiles to a whole row and keeps the fastest, returned in
+ * *unit_tiles. The timing runs overwrite the X buffers of the batch. A new
+ * batch starts with the widest unit that still gives 8 units per SM. */
+MSP_API msp_status msp_batch_autotune(msp_ctx* ctx, msp_batch_t* batch, int* unit_tiles);
 
 /* msp_batch_create + msp_batch_solve + msp_batch_destroy. */
 MSP_API msp_status msp_solve_batched(msp_ctx* ctx, int count, const msp_instance* inst,

@@ -88,6 +88,7 @@ _SIGS = {
     "msp_batch_solve": (C.c_int, [P, P, C.POINTER(MspOpts), C.POINTER(MspInfo)]),
     "msp_batch_info": (C.c_int, [P, P, C.POINTER(MspInfo)]),
     "msp_batch_stats": (C.c_int, [P, P, P]),
+    "msp_batch_autotune": (C.c_int, [P, P, C.POINTER(C.c_int)]),
     "msp_solve_batched": (C.c_int, [P, C.c_int, C.POINTER(MspInstance), C.POINTER(MspOpts),
                                     C.POINTER(MspInfo)]),
     "msp_schatten": (C.c_int, [P, P, C.c_int, I64, I64, C.c_double, I64, C.c_uint64,

@@ -136,12 +136,20 @@ class Batch:
             L.check(self.ctx.ptr, st)
         return [i.as_dict() for i in infos]
 
+    def autotune(self, unit_tiles: int = 0) -> int:
+        """Set (unit_tiles > 0) or search (0) the unit width of the batched A
+        passes; returns the width in use. A search overwrites the X buffers."""
+        v = C.c_int(unit_tiles)
+        L.check(self.ctx.ptr, self.ctx.lib.msp_batch_autotune(self.ctx.ptr, self.handle, C.byref(v)))
+        return v.value
+
     def stats(self) -> dict:
         """Counters and device-timer split of the last solve (msp_batch_stats)."""
-        v = (C.c_double * 13)()
+        v = (C.c_double * 16)()
         L.check(self.ctx.ptr, self.ctx.lib.msp_batch_stats(self.ctx.ptr, self.handle, v))
         keys = ("a_passes", "resid_passes", "a_bytes", "resid_bytes", "a_ms", "g_ms", "tri_ms",
-                "z_ms", "vec_ms", "resid_ms", "check_ms", "dense_pass_bytes", "nn_bytes")
+                "z_ms", "vec_ms", "resid_ms", "check_ms", "dense_pass_bytes", "nn_bytes", "g_bytes",
+                "z_bytes", "unit_tiles")
         return dict(zip(keys, list(v)))
 
     def close(self) -> None:

@@ -63,6 +63,12 @@ constexpr int kTileBytes = kTileFloats * 4;     // 32 KB
 constexpr int kSliceFloats = kKT * kM;          // 1024
 constexpr int kSliceBytes = kSliceFloats * 4;   // 4 KB
 constexpr int kStageBytes = kTileBytes + 2 * kSliceBytes;
+// A unit of the streamed A passes is one 128-row block times at most
+// BArgs::ut tiles (ut x 64 columns); smaller units balance a pass across the
+// SMs better, larger ones pay the per-unit reduction less often. The width
+// is a run-time choice (msp_batch_autotune); kUtMin bounds the partial
+// buffers.
+constexpr int kUtMin = 16;
 constexpr int kRingBytes = kStages * kStageBytes;   // 160 KB
 constexpr int kRedBytes = 65536;
 constexpr int kMiscBytes = 2048;
@@ -86,6 +92,8 @@ struct BInst {
     int64_t ldb, ldx;
     int n, n_pad, s_pad, m;
     int nb;               // row blocks n_pad / 128
+    int nkc;              // units per row block: ceil(n_pad / 64 / ut)
+    int qoff;             // first row of the instance in the unit-partial arrays
     int voff;             // first row in the [.][16] vector arrays
     int soff;             // first row in the s-length arrays
     int boff;             // first row block in the partial arrays
@@ -104,6 +112,8 @@ struct BCtl {
     int pad0;
     unsigned long long tilesA;   // A tiles streamed by the level-1 passes
     unsigned long long tilesR;   // A tiles streamed by the residual passes
+    unsigned long long bytesG;   // C bytes read by G = C^T R
+    unsigned long long bytesZ;   // C bytes read by Z = (R - C Y) / lambda~
     // device-timer nanoseconds per step class, taken by block 0 between grid
     // barriers (each includes its barrier)
     unsigned long long t_ns[kTimerClasses];
@@ -115,6 +125,12 @@ struct BArgs {
     const int2* rows;     // (instance, row block), largest n first
     const int2* strips;   // (instance, 64-column strip of C)
     const int2* chunks;   // (instance, 128-row chunk of s)
+    int nunits;
+    int ut;               // tiles per unit
+    const int2* units;    // (instance, row block | unit << 16), largest first
+    float* Qp;            // [nkc][n_pad][16] partial A P per unit
+    double* Rp;           // [nkc][n_pad][16] partial A X per unit (residual)
+    int* rbcnt;           // per row block: units finished in the current pass
     float *P, *Q, *R, *Z, *XW, *XH, *XL;
     double* R64;
     float *G, *Y1, *Y2;
@@ -389,15 +405,17 @@ __device__ __noinline__ void producer(const BArgs& a, unsigned char* ring, uint6
     bool stop = false;
     while (!stop) {
         const int it = atomicAdd(counter, 1);
-        int inst = -1, rb = 0, nk = 1;
-        if (it < a.nrows) {
-            const int2 w = a.rows[it];
+        int inst = -1, rb = 0, nk = 1, k0 = 0, k1 = 1;
+        if (it < a.nunits) {
+            const int2 w = a.units[it];
             inst = w.x;
-            rb = w.y;
+            rb = w.y & 0xffff;
             if (!ld_volatile(flag + inst)) continue;
             nk = a.inst[inst].n_pad / kKT;
+            k0 = (w.y >> 16) * a.ut;
+            k1 = min(nk, k0 + a.ut);
         }
-        for (int kt = 0; kt < nk; ++kt) {
+        for (int kt = k0; kt < k1; ++kt) {
             const int s = (int)(kring % kStages);
             if (kring >= kStages &&
                 !msp::mbar_wait_timed(&empty[s], ((kring / kStages) & 1u) ^ 1u, err)) {
@@ -405,15 +423,15 @@ __device__ __noinline__ void producer(const BArgs& a, unsigned char* ring, uint6
                 break;
             }
             unsigned char* st = ring + (size_t)s * kStageBytes;
-            if (it >= a.nrows) {
+            if (it >= a.nunits) {
                 hdr[s] = make_int2(-1, 0);
                 msp::mbar_arrive(&full[s]);
                 ++kring;
                 stop = true;
                 break;
             }
-            hdr[s] = make_int2(it, 2 * kt + (kt == nk - 1 ? 1 : 0));
-            if (kt == 0) atomicAdd(kResid ? &a.ctl->tilesR : &a.ctl->tilesA, (unsigned long long)nk);
+            hdr[s] = make_int2(it, 2 * kt + (kt == k1 - 1 ? 1 : 0));
+            if (kt == k0) atomicAdd(kResid ? &a.ctl->tilesR : &a.ctl->tilesA, (unsigned long long)(k1 - k0));
             const BInst& I = a.inst[inst];
             const float* At = I.At + ((int64_t)rb * nk + kt) * kTileFloats;
             const int64_t vrow = (int64_t)I.voff + (int64_t)kt * kKT;
@@ -435,10 +453,29 @@ __device__ __noinline__ void producer(const BArgs& a, unsigned char* ring, uint6
         if (!msp::mbar_wait_timed(&full[k % kStages], (k / kStages) & 1u, err)) break;
 }
 
+// Unit partials of a row block that spans several units: every unit writes
+// its part; the block that finishes the row block's last unit (counter, with
+// fences between the parts and the count) sums the parts in unit order, so
+// the result does not depend on which block finished last. Returns whether
+// this block is that one (uniform over the worker threads).
+__device__ __forceinline__ bool last_unit(int* cnt, int nkc, int* sflag, int tid) {
+    __threadfence();
+    msp::bar_workers<kWorkers>();
+    if (tid == 0) {
+        const int k = atomicAdd(cnt, 1);
+        *sflag = (k == nkc - 1);
+        if (k == nkc - 1) *cnt = 0;
+    }
+    msp::bar_workers<kWorkers>();
+    const bool last = *(volatile int*)sflag != 0;
+    if (last) __threadfence();
+    return last;
+}
+
 // SA consumers: Q = (A + lam I) P and the block partials of p^T q.
 __device__ __noinline__ void consume_A(const BArgs& a, unsigned char* ring, uint64_t* full, uint64_t* empty,
                           const int2* hdr, uint32_t& kring, float* red,
-                          float* wsum, int w, int lane) {
+                          float* wsum, int* sflag, int w, int lane) {
     float acc[4][16];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -460,13 +497,35 @@ __device__ __noinline__ void consume_A(const BArgs& a, unsigned char* ring, uint
         __syncwarp();
         if (lane == 0) msp::mbar_arrive(&empty[s]);
         if (!(h.y & 1)) continue;
-        const int2 item = a.rows[h.x];
+        const int2 u = a.units[h.x];
+        const int2 item = make_int2(u.x, u.y & 0xffff);
+        const int kc = u.y >> 16;
         const BInst& I = a.inst[item.x];
-        // ---- row block complete
+        // ---- unit complete
         float out[8];
         reduce_scatter(acc, red, out, w, lane);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[i][c] = 0.f;
         const int ch = lane >> 4;
-        const int64_t vrow = (int64_t)I.voff + (int64_t)item.y * kRB + 16 * w + (lane & 15);
+        const int row = item.y * kRB + 16 * w + (lane & 15);
+        const int64_t vrow = (int64_t)I.voff + row;
+        if (I.nkc > 1) {
+            float* qp = a.Qp + ((int64_t)I.qoff + (int64_t)kc * I.n_pad + row) * kM + 8 * ch;
+            st4(qp, make_float4(out[0], out[1], out[2], out[3]));
+            st4(qp + 4, make_float4(out[4], out[5], out[6], out[7]));
+            if (!last_unit(a.rbcnt + I.boff + item.y, I.nkc, sflag, w * 32 + lane)) continue;
+#pragma unroll
+            for (int c8 = 0; c8 < 8; ++c8) out[c8] = 0.f;
+            for (int k = 0; k < I.nkc; ++k) {
+                const float* q2 = a.Qp + ((int64_t)I.qoff + (int64_t)k * I.n_pad + row) * kM + 8 * ch;
+                const float4 u0 = __ldcg(reinterpret_cast<const float4*>(q2));
+                const float4 u1 = __ldcg(reinterpret_cast<const float4*>(q2 + 4));
+                out[0] += u0.x; out[1] += u0.y; out[2] += u0.z; out[3] += u0.w;
+                out[4] += u1.x; out[5] += u1.y; out[6] += u1.z; out[7] += u1.w;
+            }
+        }
         const float4 p0 = ld4(a.P + vrow * kM + 8 * ch), p1 = ld4(a.P + vrow * kM + 8 * ch + 4);
         const float pv[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
         float q[8], d[8];
@@ -479,10 +538,6 @@ __device__ __noinline__ void consume_A(const BArgs& a, unsigned char* ring, uint
         st4(a.Q + vrow * kM + 8 * ch + 4, make_float4(q[4], q[5], q[6], q[7]));
         const double t = colsum_rs(d, wsum, w, lane);
         if (w == 0 && lane < 16) a.p_pq[((int64_t)I.boff + item.y) * kM + lane] = t;
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int c = 0; c < 16; ++c) acc[i][c] = 0.f;
     }
 }
 
@@ -490,7 +545,7 @@ __device__ __noinline__ void consume_A(const BArgs& a, unsigned char* ring, uint
 // compensated FP32 tiles, and the block partials of |r|^2 (FP64).
 __device__ __noinline__ void consume_R(const BArgs& a, unsigned char* ring, uint64_t* full, uint64_t* empty,
                           const int2* hdr, uint32_t& kring, double* redd,
-                          double* wsumd, int w, int lane) {
+                          double* wsumd, int* sflag, int w, int lane) {
     float s[2][16], c[2][16];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -513,9 +568,11 @@ __device__ __noinline__ void consume_R(const BArgs& a, unsigned char* ring, uint
         __syncwarp();
         if (lane == 0) msp::mbar_arrive(&empty[st]);
         if (!(hd.y & 1)) continue;
-        const int2 item = a.rows[hd.x];
+        const int2 u = a.units[hd.x];
+        const int2 item = make_int2(u.x, u.y & 0xffff);
+        const int kc = u.y >> 16;
         const BInst& I = a.inst[item.x];
-        // ---- row block complete: combine the 4 column groups in FP64
+        // ---- unit complete: combine the 4 column groups in FP64
 #pragma unroll
         for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -528,13 +585,33 @@ __device__ __noinline__ void consume_R(const BArgs& a, unsigned char* ring, uint
         const int hh = r >> 6, i = (r & 63) >> 5, srcl = r & 31, ch = lane >> 4;
         const int row = item.y * kRB + r;
         const int64_t vrow = (int64_t)I.voff + row;
-        double d2[8];
+        double v8[8];
 #pragma unroll
         for (int c8 = 0; c8 < 8; ++c8) {
             const int col = 8 * ch + c8;
             double v = 0.0;
 #pragma unroll
             for (int g = 0; g < 4; ++g) v += redd[(((4 * hh + g) * 2 + i) * 16 + col) * 32 + srcl];
+            v8[c8] = v;
+        }
+        if (I.nkc > 1) {
+            double* rp = a.Rp + ((int64_t)I.qoff + (int64_t)kc * I.n_pad + row) * kM + 8 * ch;
+#pragma unroll
+            for (int c8 = 0; c8 < 8; ++c8) rp[c8] = v8[c8];
+            if (!last_unit(a.rbcnt + I.boff + item.y, I.nkc, sflag, w * 32 + lane)) continue;
+#pragma unroll
+            for (int c8 = 0; c8 < 8; ++c8) v8[c8] = 0.0;
+            for (int k = 0; k < I.nkc; ++k) {
+                const double* r2 = a.Rp + ((int64_t)I.qoff + (int64_t)k * I.n_pad + row) * kM + 8 * ch;
+#pragma unroll
+                for (int c8 = 0; c8 < 8; ++c8) v8[c8] += __ldcg(r2 + c8);
+            }
+        }
+        double d2[8];
+#pragma unroll
+        for (int c8 = 0; c8 < 8; ++c8) {
+            const int col = 8 * ch + c8;
+            const double v = v8[c8];
             double rv = 0.0;
             if (row < I.n && col < I.m) {
                 const double b = I.B[(int64_t)col * I.ldb + row];
@@ -782,6 +859,7 @@ __device__ __noinline__ void step_G(const BArgs& a, int t, unsigned char* smem, 
             }
         }
         if (!ld_volatile(&a.iact[prev * a.count + i])) continue;
+        if (tid == 0) atomicAdd(&a.ctl->bytesG, (unsigned long long)I.n * kKT * 4);
         // G[strip] = sum over row tiles of C[tile rows][strip]^T R[tile rows]
         float acc[2][16];
 #pragma unroll
@@ -920,6 +998,7 @@ __device__ __noinline__ void step_Z(const BArgs& a, int t, unsigned char* smem, 
 #pragma unroll
             for (int c = 0; c < 16; ++c) acc[i][c] = 0.f;
         const int rows_valid = min(kRB, I.n - item.y * kRB);
+        if (tid == 0) atomicAdd(&a.ctl->bytesZ, (unsigned long long)rows_valid * I.s_pad * 4);
         mv_stream(acc, I.C + (int64_t)item.y * kRB * I.s_pad, I.s_pad, rows_valid, 0, I.s_pad / kKT, Vs,
                   tiles, tid, w, lane);
         float out[8];
@@ -1114,6 +1193,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_batch_solve(BArgs a) {
     float* sv = reinterpret_cast<float*>(misc + 1152);        // 16 per-column scalars
     double* sd = reinterpret_cast<double*>(misc + 1280);      // 16 per-column scalars
     int* slot = reinterpret_cast<int*>(misc + 1408);          // claimed item index
+    int* sflag = reinterpret_cast<int*>(misc + 1412);         // last-unit flag
 
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
     const bool worker = w < kWorkWarps;
@@ -1165,7 +1245,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_batch_solve(BArgs a) {
             MSP_GBAR(kTZ);
             if (worker) step_P(a, t, sv, tid, w, lane);
             MSP_GBAR(kTVec);
-            if (worker) consume_A(a, ring, full, empty, hdr, kring, red, wsum, w, lane);
+            if (worker) consume_A(a, ring, full, empty, hdr, kring, red, wsum, sflag, w, lane);
             else if (lane == 0)
                 producer<false>(a, ring, full, empty, hdr, kring, &ctl->ctrA, a.iact + (t & 1) * a.count);
             MSP_GBAR(kTA);
@@ -1176,7 +1256,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_batch_solve(BArgs a) {
         MSP_GBAR(kTResid);
         if (blockIdx.x == 0 && tid == 0) ctl->sweepsR += 1;
         if (worker)
-            consume_R(a, ring, full, empty, hdr, kring, reinterpret_cast<double*>(red), wsumd, w, lane);
+            consume_R(a, ring, full, empty, hdr, kring, reinterpret_cast<double*>(red), wsumd, sflag, w, lane);
         else if (lane == 0)
             producer<true>(a, ring, full, empty, hdr, kring, &ctl->ctrR, a.istep);
         MSP_GBAR(kTResid);
@@ -1220,7 +1300,7 @@ struct msp_batch_s {
     std::vector<msp_sketch_t*> sk;
     std::vector<msp_factor_t*> f;
     std::vector<BInst> hinst;
-    std::vector<int2> rows, strips, chunks;
+    std::vector<int2> rows, strips, chunks, units;
     void* mem = nullptr;
     cudaStream_t stream = nullptr;
     BArgs args{};
@@ -1229,6 +1309,8 @@ struct msp_batch_s {
     int last_mixed = 1;
     double last_tol = 0.0;
     int last_crit = 0;
+    std::vector<int> by_n;      // instances, largest n first
+    BInst* d_inst = nullptr;    // device copy of hinst
 };
 
 namespace {
@@ -1290,6 +1372,41 @@ msp_status check_instance(msp_ctx* ctx, int k, const msp_instance& I) {
         return msp_set_error(ctx, MSP_EINVAL,
                              "batch: instance %d needs 16 <= s <= min(n, %d), 1 <= gamma <= min(s, %d)", k,
                              MSP_MAX_S, MSP_MAX_GAMMA);
+    return MSP_OK;
+}
+
+// Units of width ut (tiles): per-instance unit counts, partial-buffer
+// offsets and the unit list (largest first; the last unit of a row block may
+// be shorter), uploaded with the instance table.
+msp_status set_units(msp_ctx* ctx, msp_batch_s* b, int ut) {
+    std::vector<std::pair<int, int2>> us;
+    int64_t nq = 0;
+    for (BInst& H : b->hinst) {
+        const int nk = H.n_pad / kKT;
+        H.nkc = (nk + ut - 1) / ut;
+        H.qoff = (int)nq;
+        if (H.nkc > 1) nq += (int64_t)H.nkc * H.n_pad;
+    }
+    for (int k : b->by_n) {
+        const BInst& H = b->hinst[k];
+        const int nk = H.n_pad / kKT;
+        for (int r = 0; r < H.nb; ++r)
+            for (int c = 0; c < H.nkc; ++c)
+                us.push_back({std::min(nk, (c + 1) * ut) - c * ut, make_int2(k, r | (c << 16))});
+    }
+    std::stable_sort(us.begin(), us.end(), [](const std::pair<int, int2>& x, const std::pair<int, int2>& y) {
+        return x.first > y.first;
+    });
+    b->units.clear();
+    for (const auto& u : us) b->units.push_back(u.second);
+    b->args.ut = ut;
+    b->args.nunits = (int)b->units.size();
+    MSP_CUDA_TRY(ctx, cudaMemcpyAsync((void*)b->args.units, b->units.data(), sizeof(int2) * b->units.size(),
+                                      cudaMemcpyHostToDevice, ctx->stream));
+    MSP_CUDA_TRY(ctx, cudaMemcpyAsync(b->d_inst, b->hinst.data(), sizeof(BInst) * b->hinst.size(),
+                                      cudaMemcpyHostToDevice, ctx->stream));
+    // pageable sources: the copies complete before the host vectors change
+    MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     return MSP_OK;
 }
 
@@ -1407,7 +1524,7 @@ msp_status msp_batch_create(msp_ctx* ctx, int count, const msp_instance* inst, m
     }
 
     // ---- layout
-    int64_t nv = 0, ns = 0, nbt = 0, at = 0;
+    int64_t nv = 0, ns = 0, nbt = 0, at = 0, nq = 0;
     b->hinst.resize(count);
     for (int k = 0; k < count; ++k) {
         const msp_instance& I = inst[k];
@@ -1420,6 +1537,8 @@ msp_status msp_batch_create(msp_ctx* ctx, int count, const msp_instance* inst, m
         H.voff = (int)nv;
         H.soff = (int)ns;
         H.boff = (int)nbt;
+        H.nkc = (H.n_pad / kKT + kUtMin - 1) / kUtMin;   // the most units (smallest width)
+        H.qoff = (int)nq;
         H.lam = (float)I.lambda;
         H.lam64 = I.lambda;
         H.inv_lt = (float)(1.0 / b->f[k]->lam_tilde);
@@ -1430,9 +1549,10 @@ msp_status msp_batch_create(msp_ctx* ctx, int count, const msp_instance* inst, m
         nv += H.n_pad;
         ns += H.s_pad;
         nbt += H.nb;
+        if (H.nkc > 1) nq += (int64_t)H.nkc * H.n_pad;
         at += (int64_t)H.n_pad * H.n_pad;
     }
-    if (nv * kM >= (1ll << 31) || nbt >= (1 << 30))
+    if (nv * kM >= (1ll << 31) || nq * kM >= (1ll << 31) || nbt >= (1 << 30))
         return fail(msp_set_error(ctx, MSP_EINVAL, "batch: total size too large"));
     // row items: largest instance first (dynamic scheduling then balances)
     std::vector<int> by_n(count);
@@ -1444,6 +1564,10 @@ msp_status msp_batch_create(msp_ctx* ctx, int count, const msp_instance* inst, m
         for (int s = 0; s < b->hinst[k].s_pad / kKT; ++s) b->strips.push_back(make_int2(k, s));
     for (int k : by_n)
         for (int s = 0; s < b->hinst[k].s_pad / kRB; ++s) b->chunks.push_back(make_int2(k, s));
+    b->by_n = by_n;
+    // room for the units list at the smallest width
+    size_t max_units = 0;
+    for (const BInst& H : b->hinst) max_units += (size_t)H.nb * H.nkc;
 
     const int cnt = count;
     size_t off = 0;
@@ -1457,6 +1581,7 @@ msp_status msp_batch_create(msp_ctx* ctx, int count, const msp_instance* inst, m
     const size_t o_rows = take(sizeof(int2) * b->rows.size());
     const size_t o_strips = take(sizeof(int2) * b->strips.size());
     const size_t o_chunks = take(sizeof(int2) * b->chunks.size());
+    const size_t o_units = take(sizeof(int2) * max_units);
     const size_t o_vec = off;
     const size_t vbytes = (size_t)nv * kM * 4;
     size_t o_v[7];
@@ -1478,6 +1603,9 @@ msp_status msp_batch_create(msp_ctx* ctx, int count, const msp_instance* inst, m
     int64_t nmax = 0;
     for (int k = 0; k < count; ++k) nmax = std::max<int64_t>(nmax, inst[k].n);
     const size_t o_nwork = take((size_t)nmax * 16);
+    const size_t o_qp = take((size_t)std::max<int64_t>(nq, 1) * kM * 4);
+    const size_t o_rp = take((size_t)std::max<int64_t>(nq, 1) * kM * 8);
+    const size_t o_rbcnt = take((size_t)nbt * 4);
     const size_t o_ctl = take(sizeof(BCtl));
     const size_t total = off;
     if (cudaMallocAsync(&b->mem, total, ctx->stream) != cudaSuccess) {
@@ -1524,6 +1652,11 @@ msp_status msp_batch_create(msp_ctx* ctx, int count, const msp_instance* inst, m
     A.rows = (const int2*)(base + o_rows);
     A.strips = (const int2*)(base + o_strips);
     A.chunks = (const int2*)(base + o_chunks);
+    A.units = (const int2*)(base + o_units);
+    A.Qp = (float*)(base + o_qp);
+    A.Rp = (double*)(base + o_rp);
+    A.rbcnt = (int*)(base + o_rbcnt);
+    b->d_inst = (BInst*)(base + o_inst);
     float** vp[7] = {&A.P, &A.Q, &A.R, &A.Z, &A.XW, &A.XH, &A.XL};
     for (int q = 0; q < 7; ++q) *vp[q] = (float*)(base + o_v[q]);
     A.R64 = (double*)(base + o_r64);
@@ -1551,6 +1684,20 @@ msp_status msp_batch_create(msp_ctx* ctx, int count, const msp_instance* inst, m
     for (int k = 0; k < count; ++k) {
         const msp_status st = msp_norm_lb_launch(ctx, inst[k].A, MSP_F32, inst[k].n, inst[k].lda,
                                                  (double*)(base + o_nwork), (double*)(base + o_anorm) + k);
+        if (st != MSP_OK) return fail(st);
+    }
+    {
+        // default width: the widest whose units still number 8 per SM
+        int ut = kUtMin;
+        for (int cand : {256, 128, 64, 32, 16}) {
+            size_t nu = 0;
+            for (const BInst& H : b->hinst) nu += (size_t)H.nb * ((H.n_pad / kKT + cand - 1) / cand);
+            if (nu >= (size_t)8 * ctx->num_sms) {
+                ut = cand;
+                break;
+            }
+        }
+        const msp_status st = set_units(ctx, b, ut);
         if (st != MSP_OK) return fail(st);
     }
     // the host copies above are from pageable memory: complete before return
@@ -1590,6 +1737,10 @@ msp_status msp_batch_solve(msp_ctx* ctx, msp_batch_t* b, const msp_opts* opts, m
     MSP_CUDA_TRY(ctx, cudaMemsetAsync(a.iters, 0, (size_t)a.count * 4, ctx->stream));
     MSP_CUDA_TRY(ctx, cudaMemsetAsync(a.ierr, 0, (size_t)a.count * 4, ctx->stream));
     MSP_CUDA_TRY(ctx, cudaMemsetAsync(a.isteps, 0, (size_t)a.count * 4, ctx->stream));
+    // unit counters (left at zero by a completed pass; cleared in case the
+    // last solve stopped inside one)
+    MSP_CUDA_TRY(ctx, cudaMemsetAsync(a.rbcnt, 0, (size_t)(b->hinst.back().boff + b->hinst.back().nb) * 4,
+                                      ctx->stream));
     const int d = ctx->device;
     if (d >= 0 && d < 64 && !g_attr_set[d].load()) {
         MSP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_batch_solve, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1673,9 +1824,53 @@ msp_status msp_batch_stats(msp_ctx* ctx, const msp_batch_t* b, double* stats) {
     stats[3] = (double)ctl.tilesR * kTileBytes;
     for (int c = 0; c < kTimerClasses; ++c) stats[4 + c] = 1e-6 * (double)ctl.t_ns[c];
     stats[11] = (double)dense * 4.0;
+    stats[13] = (double)ctl.bytesG;
+    stats[14] = (double)ctl.bytesZ;
+    stats[15] = (double)b->args.ut;
     int64_t nn = 0;
     for (const BInst& H : b->hinst) nn += (int64_t)H.n * H.n;
     stats[12] = (double)nn * 4.0;
+    return MSP_OK;
+}
+
+msp_status msp_batch_autotune(msp_ctx* ctx, msp_batch_t* b, int* unit_tiles) {
+    if (!ctx) return msp_set_error(nullptr, MSP_EINVAL, "ctx is NULL");
+    if (!b || !unit_tiles) return msp_set_error(ctx, MSP_EINVAL, "batch_autotune: NULL argument");
+    msp::DeviceGuard guard(ctx->device);
+    const int want = *unit_tiles;
+    if (want > 0) {
+        if (want < kUtMin || (want & (want - 1)))
+            return msp_set_error(ctx, MSP_EINVAL, "batch_autotune: unit width must be a power of two >= %d",
+                                 kUtMin);
+        return set_units(ctx, b, want);
+    }
+    // time the A passes of a fixed number of level-1 iterations at each width
+    msp_opts o;
+    msp_default_opts(&o);
+    o.max_refine = 0;
+    o.refine_tol = 1e-300;
+    o.tol = 1e-300;
+    o.max_outer = 12;
+    int nk_max = 1;
+    for (const BInst& H : b->hinst) nk_max = std::max(nk_max, H.n_pad / kKT);
+    double best = 0.0;
+    int best_ut = b->args.ut;
+    for (int ut = kUtMin; ut < 2 * nk_max && ut <= 1024; ut *= 2) {
+        MSP_TRY(set_units(ctx, b, ut));
+        double st[16];
+        for (int rep = 0; rep < 2; ++rep) {     // the first run warms caches and clocks
+            const msp_status s = msp_batch_solve(ctx, b, &o, nullptr);
+            if (s != MSP_OK) return s;
+        }
+        MSP_TRY(msp_batch_stats(ctx, b, st));
+        const double rate = st[4] > 0.0 ? st[2] / st[4] : 0.0;     // bytes per ms of A pass
+        if (rate > best) {
+            best = rate;
+            best_ut = ut;
+        }
+    }
+    MSP_TRY(set_units(ctx, b, best_ut));
+    *unit_tiles = best_ut;
     return MSP_OK;
 }
 

@@ -217,3 +217,60 @@ def test_batch_backward_error_rule(ctx):
             eta = reference.backward_error(K64, X[:, j], B[:, j], LAM, norm_A=top)
             assert eta <= 1e-10
     bt.close()
+
+
+def test_batch_multi_unit_rows(ctx):
+    """Instances wide enough that each 128-row block of A is streamed as
+    several units whose partial products are summed by the block that
+    finishes last (at 32 tiles per unit, n = 2500: 2 units, n = 4200: 3
+    units per row block), next to a one-unit instance; backward error checked
+    with the exact |A|_2, and repeated solves identical bit for bit."""
+    cases = [(2500, 0.1, 4, 81, 320), (4200, 0.15, 3, 82, 512), (700, 0.08, 2, 83, 128)]
+    insts = [_instance(*c) for c in cases]
+    dev = [dict(A=torch.from_numpy(K).cuda(), B=torch.from_numpy(B).cuda(), lam=LAM, s=c[4])
+           for (K, B), c in zip(insts, cases)]
+    bt = ctx.batch(dev)
+    assert bt.autotune(32) == 32
+    infos = bt.solve(tol=1e-10, refine_tol=1e-4, criterion="backward")
+    X1 = [bt.X(k).cpu().numpy() for k in range(len(cases))]
+    bt.solve(tol=1e-10, refine_tol=1e-4, criterion="backward")
+    for k, ((K, B), info) in enumerate(zip(insts, infos)):
+        assert np.array_equal(bt.X(k).cpu().numpy(), X1[k])      # fixed-order unit sums
+        K64 = K.astype(np.float64)
+        assert info["status"] == 0 and info["backward_err"] <= 1e-10
+        top = float(np.linalg.eigvalsh(K64)[-1])
+        for j in range(B.shape[1]):
+            x = X1[k][:, j]
+            assert reference.backward_error(K64, x, B[:, j], LAM, norm_A=top) <= 1e-10
+            r = B[:, j] - (K64 @ x + LAM * x)
+            xs = reference.solve_dense(K64, B[:, j], LAM)
+            assert np.linalg.norm(x - xs) <= 1.01 * np.linalg.norm(r) / LAM + 1e-12 * np.linalg.norm(xs)
+    bt.close()
+
+
+def test_batch_unit_width(ctx):
+    """Every unit width gives a certified solution; the search returns a
+    width it tried; bad widths are refused."""
+    from paper_2405_05865_gb300 import MspError
+    cases = [(2600, 0.12, 3, 91, 320), (900, 0.07, 2, 92, 128)]
+    insts = [_instance(*c) for c in cases]
+    dev = [dict(A=torch.from_numpy(K).cuda(), B=torch.from_numpy(B).cuda(), lam=LAM, s=c[4])
+           for (K, B), c in zip(insts, cases)]
+    bt = ctx.batch(dev)
+    for ut in (16, 32, 64):
+        assert bt.autotune(ut) == ut
+        infos = bt.solve(tol=1e-10, refine_tol=1e-4, criterion="backward")
+        for k, ((K, B), info) in enumerate(zip(insts, infos)):
+            assert info["status"] == 0 and info["backward_err"] <= 1e-10
+            X = bt.X(k).cpu().numpy()
+            K64 = K.astype(np.float64)
+            for j in range(B.shape[1]):
+                r = B[:, j] - (K64 @ X[:, j] + LAM * X[:, j])
+                assert np.linalg.norm(r) <= 1.01e-10 * ((info["norm_lb"] + LAM) * np.linalg.norm(X[:, j])
+                                                        + np.linalg.norm(B[:, j]))
+    found = bt.autotune(0)
+    assert found in (16, 32, 64)
+    for bad in (8, 48):
+        with pytest.raises(MspError):
+            bt.autotune(bad)
+    bt.close()
