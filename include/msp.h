@@ -196,9 +196,10 @@ MSP_API msp_status msp_sketch_get_C(msp_ctx* ctx, const msp_sketch_t* sk, void* 
 /* Algorithm 1, steps 3-4: W = S C (s x s, symmetrised), lambda~ = lambda +
  * lambda0, C~ = Phi C with Phi a phi x n sparse embedding (gamma_phi
  * nonzeros per column, stream 2), M2 = C~^T C~ + lambda~ W, and the FP64
- * Cholesky factor M2 + nu I = L L^T (nu = 0 first; on failure
- * nu = s 2^-52 |M2|_F for FP64 data or 2^-24 |M2|_F for FP32 data, times 100
- * per retry, at most 4 retries, else MSP_ENOTPD). The level-2 preconditioner is applied as
+ * Cholesky factor M2 + nu I = L L^T (FP64 data: nu = 0 first, on failure
+ * nu = s 2^-52 |M2|_F; FP32 data: nu = 2^-24 |M2|_F from the start, the
+ * rounding level of the data; then times 100 per retry, at most 4 retries,
+ * else MSP_ENOTPD). The level-2 preconditioner is applied as
  * M2^{-1} v = L^{-T} (L^{-1} v) with L^{-1} stored explicitly
  * ("pre-compute M2^{-1} exactly", Section 4, Part 3).
  * phi == 0 selects Phi = I_n (C~ = C, M2 = C^T C + lambda~ W exactly: the
@@ -421,9 +422,13 @@ MSP_API msp_status msp_rbf_grad_ell_static(const double* points, int64_t n, int 
 
 /* ----------------------------------------------------- helpers (tests) */
 
-/* L = max(max_i |A e_i|_2, 1^T A 1 / n) <= |A|_2 for symmetric PSD A (a
- * column norm and the Rayleigh quotient of the all-ones vector), FP64 sums
- * over one pass of A (device, FP32 or FP64, lda >= n). *out: host scalar. */
+/* L <= |A|_2 for symmetric PSD A from max(max_i |A e_i|_2, 1^T A 1 / n) (a
+ * column norm and the Rayleigh quotient of the all-ones vector), one pass
+ * over A (device, FP32 or FP64, lda >= n). Entries are summed in FP32 chunks
+ * of 16 combined in FP64, and each term is lowered by the rounding bound of
+ * those chunks, so the result is a certified lower bound, within about 1e-6
+ * (relative to the sums of |a_ij|) of the exact expression. *out: host
+ * scalar. */
 MSP_API msp_status msp_norm_lower_bound(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n,
                                         int64_t lda, double* out);
 

@@ -405,7 +405,7 @@ static msp_status solve_impl(msp_ctx* ctx, const msp_factor_s* f, const void* A,
     // per-solve buffers: r64 (n), rhs_w (n), sol_w (n), scalars, |A| bound work
     void* mem = nullptr;
     size_t b_r = round_up(n * 8, 256), b_w = round_up(n * ts, 256);
-    const size_t b_nw = crit_bw ? (size_t)round_up(2 * n * 8, 256) : 0;
+    const size_t b_nw = crit_bw ? (size_t)round_up(3 * n * 8, 256) : 0;
     MSP_TRY(msp_alloc(ctx, &mem, b_r + 2 * b_w + 256 + b_nw));
     char* c = (char*)mem;
     double* r64 = (double*)c; c += b_r;

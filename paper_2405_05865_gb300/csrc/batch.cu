@@ -1602,7 +1602,7 @@ msp_status msp_batch_create(msp_ctx* ctx, int count, const msp_instance* inst, m
     const size_t o_anorm = take((size_t)cnt * 8);
     int64_t nmax = 0;
     for (int k = 0; k < count; ++k) nmax = std::max<int64_t>(nmax, inst[k].n);
-    const size_t o_nwork = take((size_t)nmax * 16);
+    const size_t o_nwork = take((size_t)nmax * 24);
     const size_t o_qp = take((size_t)std::max<int64_t>(nq, 1) * kM * 4);
     const size_t o_rp = take((size_t)std::max<int64_t>(nq, 1) * kM * 8);
     const size_t o_rbcnt = take((size_t)nbt * 4);

@@ -284,17 +284,31 @@ __global__ void k_copy_add_diag(const double* __restrict__ src, double* __restri
 }
 
 // Frobenius norm^2 partials (single block, deterministic order).
-__global__ void k_fro2(const double* __restrict__ M, int64_t m, double* __restrict__ out) {
-    __shared__ double part[32];
+// |M|_F^2 in two fixed-order stages: kFroBlocks block partials, then one
+// block sums them.
+constexpr int kFroBlocks = 128;
+
+__global__ void __launch_bounds__(256) k_fro2_part(const double* __restrict__ M, int64_t m,
+                                                  double* __restrict__ part) {
+    __shared__ double red[8];
     double acc = 0.0;
-    for (int64_t e = threadIdx.x; e < m; e += blockDim.x) acc += M[e] * M[e];
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+        acc += M[e] * M[e];
     acc = msp::warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
-    if (threadIdx.x < 32) {
-        double v = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
-        v = msp::warp_sum(v);
-        if (threadIdx.x == 0) *out = v;
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int w = 0; w < 8; ++w) v += red[w];
+        part[blockIdx.x] = v;
+    }
+}
+
+__global__ void k_fro2_final(const double* __restrict__ part, double* __restrict__ out) {
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int b = 0; b < kFroBlocks; ++b) v += part[b];
+        *out = v;
     }
 }
 
@@ -416,14 +430,35 @@ msp_status msp_build_factor(msp_ctx* ctx, msp_factor_s* f, const void* Ct, int64
     // factor with shift retries
     void* scr = nullptr;
     size_t mat = (size_t)sp * sp * 8;
-    MSP_TRY(msp_scratch(ctx, 3 * mat + 256, &scr));
+    MSP_TRY(msp_scratch(ctx, 3 * mat + 2048, &scr));
     double* Mw = (double*)scr;
     double* T1 = Mw + sp * sp;
     double* T2 = T1 + sp * sp;
     int* fail = (int*)(T2 + sp * sp);
     double* fro = (double*)(fail + 16);
-    double nu = 0.0;
+    double* fro_part = fro + 2;
     int* hflag = (int*)ctx->host_flags;
+    auto fro_norm = [&](double* out) -> msp_status {
+        k_fro2_part<<<kFroBlocks, 256, 0, ctx->stream>>>(f->M2, sp * sp, fro_part);
+        MSP_CHECK_LAUNCH(ctx);
+        k_fro2_final<<<1, 32, 0, ctx->stream>>>(fro_part, fro);
+        MSP_CHECK_LAUNCH(ctx);
+        double h = 0.0;
+        MSP_CUDA_TRY(ctx, cudaMemcpyAsync(&h, fro, 8, cudaMemcpyDeviceToHost, ctx->stream));
+        MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        *out = std::sqrt(h);
+        return MSP_OK;
+    };
+    // FP32 data: M2 carries rounding errors of about 2^-24 |M2|_F (C and W are
+    // FP32), which leave it indefinite by that much where C^T C + lam~ W has
+    // tiny eigenvalues; shifting by that amount from the start saves a
+    // second factorisation. FP64 data: unshifted first.
+    double nu = 0.0;
+    if (f->dtype == MSP_F32) {
+        double fn = 0.0;
+        MSP_TRY(fro_norm(&fn));
+        nu = std::ldexp(1.0, -24) * fn;
+    }
     for (int attempt = 0; attempt <= 4; ++attempt) {
         unsigned blocks = (unsigned)((sp * sp + 255) / 256);
         k_copy_add_diag<<<blocks, 256, 0, ctx->stream>>>(f->M2, Mw, sp, nu);
@@ -448,15 +483,12 @@ msp_status msp_build_factor(msp_ctx* ctx, msp_factor_s* f, const void* Ct, int64
             (void)ts;
             return MSP_OK;
         }
-        if (attempt == 0) {
-            k_fro2<<<1, 1024, 0, ctx->stream>>>(f->M2, sp * sp, fro);
-            MSP_CHECK_LAUNCH(ctx);
-            double h = 0.0;
-            MSP_CUDA_TRY(ctx, cudaMemcpyAsync(&h, fro, 8, cudaMemcpyDeviceToHost, ctx->stream));
-            MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        if (nu == 0.0) {
             // first shift at the rounding level of the data M2 was assembled from
-            nu = (f->dtype == MSP_F64 ? (double)f->s * std::ldexp(1.0, -52)
-                                      : std::ldexp(1.0, -24)) * std::sqrt(h);
+            double fn = 0.0;
+            MSP_TRY(fro_norm(&fn));
+            nu = (f->dtype == MSP_F64 ? (double)f->s * std::ldexp(1.0, -52) : std::ldexp(1.0, -24)) * fn;
+            if (nu == 0.0) break;
         } else {
             nu *= 100.0;
         }

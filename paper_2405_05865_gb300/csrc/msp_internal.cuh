@@ -250,7 +250,7 @@ msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t
 msp_status msp_nystrom_impl(msp_ctx* ctx, const msp_sketch_s* sk, double lambda, double lambda0,
                             int64_t phi, int gamma_phi, uint64_t seed, msp_factor_s** out);
 
-// norms.cu: L <= |A|_2 into *out_dev; work holds 2n doubles
+// norms.cu: L <= |A|_2 into *out_dev; work holds 3n doubles
 msp_status msp_norm_lb_launch(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t n, int64_t lda,
                               double* work, double* out_dev);
 

@@ -4,61 +4,95 @@
 // both terms at most |A|_2 (a column of A is A e_i; the second is the Rayleigh
 // quotient of the all-ones vector). One pass over A.
 //
-// k_row_stats  one warp per row: FP64 sums of a_ij and a_ij^2 over the row
-//              (= column, A symmetric), lanes striding the row, fixed-order
-//              warp reduction.
-// k_norm_lb    one block: the maximum of the row squares and the FP64 sum of
-//              the row sums in a fixed order.
+// k_row_stats  one warp per row: the row is summed in chunks of 16 entries
+//              per lane in FP32 (sum, sum of |.|, sum of squares), chunk
+//              results combined in FP64, with the rounding bound of every
+//              FP32 chunk kept beside it (the FP64 pipe of this part is 1/64
+//              of the FP32 rate, so a per-entry FP64 sum would set the pass's
+//              speed).
+// k_norm_lb    one block: max of the row squares and the FP64 sum of the row
+//              sums in a fixed order, each lowered by its rounding bound, so
+//              the result stays at most |A|_2.
 #include "msp_internal.cuh"
 
 namespace {
 
+// FP32 chunk of 16 terms: |fl(sum) - sum| <= 15 u sum|t| (recursive
+// summation, u = 2^-24); the exact sum of squares (positive terms) is at
+// least (1 - 19 u) of the computed one, FP32 rounding of FP64 entries
+// included.
+constexpr int kChunk = 16;
+constexpr double kU32 = 5.9604644775390625e-8;
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_row_stats(const T* __restrict__ A, int64_t n, int64_t lda,
-                                                  double* __restrict__ rowsum, double* __restrict__ rowsq) {
+                                                  double* __restrict__ rowsum, double* __restrict__ rowerr,
+                                                  double* __restrict__ rowsq) {
     const int lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (i >= n) return;
     const T* row = A + i * lda;
-    double s = 0.0, q = 0.0;
-    for (int64_t j = lane; j < n; j += 32) {
-        const double v = (double)__ldcs(row + j);
-        s += v;
-        q += v * v;
+    double s = 0.0, e = 0.0, q = 0.0;
+    int64_t j = lane;
+    while (j < n) {
+        float cs = 0.f, ca = 0.f, cq = 0.f;
+#pragma unroll 4
+        for (int k = 0; k < kChunk && j < n; ++k, j += 32) {
+            const float v = (float)__ldcs(row + j);
+            cs += v;
+            ca += fabsf(v);
+            cq = fmaf(v, v, cq);
+        }
+        s += (double)cs;
+        e += (double)ca;
+        q += (double)cq;
     }
     s = msp::warp_sum(s);
+    e = msp::warp_sum(e);
     q = msp::warp_sum(q);
     if (lane == 0) {
         rowsum[i] = s;
+        // chunk summation (15 u) plus, for FP64 input, the rounding of each
+        // entry to FP32 (u)
+        rowerr[i] = (kChunk + 1) * kU32 * e * (1.0 + 1e-6);
         rowsq[i] = q;
     }
 }
 
 __global__ void __launch_bounds__(1024) k_norm_lb(const double* __restrict__ rowsum,
+                                                 const double* __restrict__ rowerr,
                                                  const double* __restrict__ rowsq, int64_t n,
                                                  double* out) {
-    __shared__ double ssum[32], smax[32];
-    double s = 0.0, m = 0.0;
+    __shared__ double ssum[32], serr[32], smax[32];
+    double s = 0.0, e = 0.0, m = 0.0;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
         s += rowsum[i];
+        e += rowerr[i];
         m = fmax(m, rowsq[i]);
     }
     s = msp::warp_sum(s);
+    e = msp::warp_sum(e);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) {
         ssum[w] = s;
+        serr[w] = e;
         smax[w] = m;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double ts = 0.0, tm = 0.0;
+        double ts = 0.0, te = 0.0, tm = 0.0;
         for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
             ts += ssum[k];
+            te += serr[k];
             tm = fmax(tm, smax[k]);
         }
-        *out = fmax(sqrt(tm), ts / (double)n);
+        // FP64 combination error (n^2 / 16 chunk terms) is far below the
+        // FP32 chunk bound; 2e-6 covers it with room
+        const double col = sqrt(tm * (1.0 - (kChunk + 3) * kU32) * (1.0 - 2e-6));
+        const double ones = (ts - te * (1.0 + 2e-6) - 2e-6 * fabs(ts)) / (double)n;
+        *out = fmax(col, ones);
     }
 }
 
@@ -68,11 +102,13 @@ msp_status msp_norm_lb_launch(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t
                               double* work, double* out_dev) {
     const unsigned blocks = (unsigned)((n + 7) / 8);
     if (dt == MSP_F32)
-        k_row_stats<float><<<blocks, 256, 0, ctx->stream>>>((const float*)A, n, lda, work, work + n);
+        k_row_stats<float><<<blocks, 256, 0, ctx->stream>>>((const float*)A, n, lda, work, work + n,
+                                                           work + 2 * n);
     else
-        k_row_stats<double><<<blocks, 256, 0, ctx->stream>>>((const double*)A, n, lda, work, work + n);
+        k_row_stats<double><<<blocks, 256, 0, ctx->stream>>>((const double*)A, n, lda, work, work + n,
+                                                            work + 2 * n);
     MSP_CHECK_LAUNCH(ctx);
-    k_norm_lb<<<1, 1024, 0, ctx->stream>>>(work, work + n, n, out_dev);
+    k_norm_lb<<<1, 1024, 0, ctx->stream>>>(work, work + n, work + 2 * n, n, out_dev);
     MSP_CHECK_LAUNCH(ctx);
     return MSP_OK;
 }
@@ -84,11 +120,11 @@ extern "C" msp_status msp_norm_lower_bound(msp_ctx* ctx, const void* A, msp_dtyp
         return msp_set_error(ctx, MSP_EINVAL, "norm_lower_bound: bad argument");
     msp::DeviceGuard g(ctx->device);
     void* mem = nullptr;
-    MSP_TRY(msp_alloc(ctx, &mem, (size_t)(2 * n + 1) * 8));
+    MSP_TRY(msp_alloc(ctx, &mem, (size_t)(3 * n + 1) * 8));
     double* work = (double*)mem;
-    msp_status st = msp_norm_lb_launch(ctx, A, dtype, n, lda, work, work + 2 * n);
+    msp_status st = msp_norm_lb_launch(ctx, A, dtype, n, lda, work, work + 3 * n);
     if (st == MSP_OK) {
-        cudaError_t e = cudaMemcpyAsync(out, work + 2 * n, 8, cudaMemcpyDeviceToHost, ctx->stream);
+        cudaError_t e = cudaMemcpyAsync(out, work + 3 * n, 8, cudaMemcpyDeviceToHost, ctx->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) st = msp_set_error(ctx, MSP_ECUDA, "norm_lower_bound: %s", cudaGetErrorString(e));
     }

@@ -211,7 +211,8 @@ def test_batch_backward_error_rule(ctx):
         K64 = K.astype(np.float64)
         X = bt.X(k).cpu().numpy()
         assert info["status"] == 0 and info["backward_err"] <= 1e-10
-        assert info["norm_lb"] == pytest.approx(reference.norm_lower_bound(K64), rel=1e-12)
+        Lo = reference.norm_lower_bound(K64)
+        assert Lo * (1 - 1e-5) <= info["norm_lb"] <= Lo * (1 + 1e-12)
         top = float(np.linalg.eigvalsh(K64)[-1])
         for j in range(B.shape[1]):
             eta = reference.backward_error(K64, X[:, j], B[:, j], LAM, norm_A=top)

@@ -293,7 +293,8 @@ def test_norm_lower_bound_matches_oracle(ctx, name, n, seed):
     dt = torch.float32 if A.dtype == np.float32 else torch.float64
     L = ctx.norm_lower_bound(_cuda(A, dt))
     Lo = reference.norm_lower_bound(A.astype(np.float64))
-    assert abs(L - Lo) <= 1e-12 * Lo
+    # certified: at most the exact expression, within the FP32 chunk bound
+    assert Lo * (1 - 1e-5) <= L <= Lo * (1 + 1e-12)
 
 
 def test_solve_backward_error_rule(ctx):
@@ -305,7 +306,8 @@ def test_solve_backward_error_rule(ctx):
                         refine_tol=1e-4)
     x = x.cpu().numpy()
     A64 = np.asarray(w.A, dtype=np.float64)
-    assert info["norm_lb"] == pytest.approx(reference.norm_lower_bound(A64), rel=1e-12)
+    Lo = reference.norm_lower_bound(A64)
+    assert Lo * (1 - 1e-5) <= info["norm_lb"] <= Lo * (1 + 1e-12)
     assert info["backward_err"] <= 1e-10
     top = float(np.linalg.eigvalsh(A64)[-1])
     eta = reference.backward_error(A64, x, w.b, w.lam, norm_A=top)
