@@ -36,16 +36,6 @@ __device__ inline void load16(const T* p, T* out) {
     else { out[0] = v.x; out[1] = v.y; }
 }
 
-// 16-byte load with an L2 eviction policy (createpolicy) attached.
-__device__ inline void load16_keep(const float* p, float* out, uint64_t pol) {
-    asm("ld.global.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
-        : "=f"(out[0]), "=f"(out[1]), "=f"(out[2]), "=f"(out[3])
-        : "l"(p), "l"(pol));
-}
-__device__ inline void load16_keep(const double* p, double* out, uint64_t pol) {
-    asm("ld.global.L2::cache_hint.v2.f64 {%0,%1}, [%2], %3;" : "=d"(out[0]), "=d"(out[1]) : "l"(p), "l"(pol));
-}
-
 // Streaming (evict-first) 16-byte load: A is read once per pass, so it should
 // not displace the sketch C, which the level-2 iteration re-reads from L2.
 template <typename T>
@@ -278,13 +268,9 @@ struct RowSlice {
     static constexpr int W = Vec16<T>::W;
     static constexpr int NVEC = PL / W;
     T v[PL];
-    // C rows: kept in L2 across level-1 iterations (67 MB at n = 16384,
-    // s = 1024, next to the evict-first stream of A)
     __device__ inline void load(const T* row, int lane) {
-        uint64_t pol;
-        asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
 #pragma unroll
-        for (int k = 0; k < NVEC; ++k) load16_keep(row + k * 32 * W + lane * W, v + k * W, pol);
+        for (int k = 0; k < NVEC; ++k) load16(row + k * 32 * W + lane * W, v + k * W);
     }
     __device__ inline T dot_smem(const T* s, int lane) const {
         T a = T(0);
