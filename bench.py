@@ -80,6 +80,24 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, device="cpu") -> float:
+    """The largest x over the ranks of the default process group (x itself
+    when there is none): the slowest rank's time is the job's time."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time
+    (weak scaling: each rank solves its own instances)."""
+    return units_per_rank * world / seconds
+
+
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
@@ -356,12 +374,8 @@ def run_msp(args, rank, world, local):
         ev1.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
-        ms = ev0.elapsed_time(ev1)
+        ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
         launches = ctx.lib.msp_launch_count(ctx.ptr) - l0
-        if dist:
-            t = torch.tensor([ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
         return ms, infos, launches
 
     for _ in range(args.warmup):
@@ -371,14 +385,14 @@ def run_msp(args, rank, world, local):
     ms, infos, launches = timed(args.steps, profile=1)
     clk = clocks.stop()
     total = args.steps * world
-    value = total / (ms / 1000.0)
+    value = job_rate(args.steps, world, ms / 1000.0)
     ok = all(i["backward_err"] <= 1e-10 and i["status"] == 0 for i in infos)
 
     # the stricter rule: relative residual |r| / |b| <= 1e-10
     for _ in range(1):
         step(criterion="residual", refine_tol=args.strict_refine_tol)
     ms_r, inf_r, _ = timed(args.steps, criterion="residual", refine_tol=args.strict_refine_tol)
-    strict = {"value": total / (ms_r / 1000.0), "unit": "solves/s", "ms_per_step": ms_r / args.steps,
+    strict = {"value": job_rate(args.steps, world, ms_r / 1000.0), "unit": "solves/s", "ms_per_step": ms_r / args.steps,
               "rel_resid_max": max(i["rel_resid"] for i in inf_r),
               "outer_iters": inf_r[-1]["outer_iters"], "refine_steps": inf_r[-1]["refine_steps"]}
 
@@ -388,7 +402,7 @@ def run_msp(args, rank, world, local):
         for _ in range(max(1, args.warmup // 2)):
             step(prec="fp32", tol=1e-5, criterion="backward")
         ms32, inf32, _ = timed(args.steps, prec="fp32", tol=1e-5, criterion="backward")
-        fp32 = {"value": total / (ms32 / 1000.0), "unit": "solves/s",
+        fp32 = {"value": job_rate(args.steps, world, ms32 / 1000.0), "unit": "solves/s",
                 "rel_resid_max": max(i["rel_resid"] for i in inf32),
                 "backward_err_max": max(i["backward_err"] for i in inf32),
                 "outer_iters": inf32[-1]["outer_iters"], "ms_per_step": ms32 / args.steps,
@@ -446,12 +460,8 @@ def run_msp(args, rank, world, local):
             _, e2e_info = ctx.solve_full(Ah, bh, lam, s, 8, 0.0, phi, 8, SEED, out=xh, **e2e_opts)
         torch.cuda.synchronize(dev)
         t1 = time.perf_counter()
-        et = t1 - t0
-        if dist:
-            t = torch.tensor([et], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            et = float(t.item())
-        e2e = {"value": total / et, "unit": "solves/s", "h2d_bytes_per_step": 4 * n * n + 8 * n,
+        et = max_over_ranks(t1 - t0, dev)
+        e2e = {"value": job_rate(args.steps, world, et), "unit": "solves/s", "h2d_bytes_per_step": 4 * n * n + 8 * n,
                "d2h_bytes_per_step": 8 * n, "backward_err": e2e_info["backward_err"]}
 
     batched = None
