@@ -219,60 +219,99 @@ __global__ void __launch_bounds__(256) k_dgemm(int64_t m, int64_t n, int64_t k, 
 }
 
 constexpr int kLeafSmem = 2 * 64 * 65 * (int)sizeof(double);
+constexpr int kLeafThreads = 128;   // 4 warps: one per SM sub-partition's FP64 unit
 
-__global__ void __launch_bounds__(256) k_chol_leaf(double* __restrict__ M, double* __restrict__ X,
-                                                  int64_t ld, int nb, int* __restrict__ fail) {
+// 1/sqrt(d) for a positive normal FP64 d: FP32 reciprocal square root as the
+// seed, then two Newton-Raphson steps y <- y (3 - d y^2) / 2 for f(y) =
+// 1/y^2 - d (quadratic convergence: ~2^-22 -> 2^-44 -> FP64 rounding). The
+// FP64 square root and division cost tens of FP64 instructions each on this
+// part, whose FP64 unit takes ~64 cycles per warp instruction.
+__device__ inline double rsqrt_newton(double d) {
+    if (!(d >= 1e-30 && d <= 1e30)) return 1.0 / sqrt(d);
+    double y = (double)rsqrtf((float)d);
+    const double hd = 0.5 * d;
+    y = y * fma(-hd * y, y, 1.5);
+    y = y * fma(-hd * y, y, 1.5);
+    return y;
+}
+
+// Cholesky and inverse of an nb x nb (nb <= 64) FP64 block on one SM:
+// M = L L^T (lower triangle of M overwritten with L), X = L^{-1}.
+// Right-looking factorisation, two block barriers per pivot: every warp
+// computes the pivot's 1/sqrt itself (no barrier to publish it), scales the
+// column, then the trailing lower triangle is updated. The inverse is a
+// blocked forward substitution over 16-row blocks: the block's right-hand
+// side from the rows already inverted (independent dot products), then a
+// 16-step substitution per column, so the longest dependent chain is ~16 +
+// 48 instead of ~nb^2 / 2.
+__global__ void __launch_bounds__(kLeafThreads) k_chol_leaf(double* __restrict__ M, double* __restrict__ X,
+                                                           int64_t ld, int nb, int* __restrict__ fail) {
     extern __shared__ __align__(16) double leaf_smem[];
     double (*a)[65] = reinterpret_cast<double (*)[65]>(leaf_smem);
     double (*x)[65] = reinterpret_cast<double (*)[65]>(leaf_smem + 64 * 65);
-    __shared__ double inv_d[64];
+    __shared__ double inv_d[64], rdiag[64];
     __shared__ int bad;
-    if (threadIdx.x == 0) bad = 0;
-    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-        int i = e / nb, j = e % nb;
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid == 0) bad = 0;
+    for (int e = tid; e < nb * nb; e += kLeafThreads) {
+        const int i = e / nb, j = e % nb;
         a[i][j] = (j <= i) ? M[i * ld + j] : 0.0;
+        x[i][j] = 0.0;
     }
     __syncthreads();
-    // right-looking Cholesky; one reciprocal per pivot
+    const int tx = tid & 7, ty = tid >> 3;      // 16 x 8 thread grid for the trailing update
     for (int kc = 0; kc < nb; ++kc) {
-        if (threadIdx.x == 0) {
+        double y = 0.0;
+        if (lane == 0) {
             double d = a[kc][kc];
-            if (!(d > 0.0) || !isfinite(d)) { bad = 1; d = 1.0; }
-            const double r = sqrt(d);
-            a[kc][kc] = r;
-            inv_d[kc] = 1.0 / r;
+            if (!(d > 0.0) || !isfinite(d)) {
+                if (tid == 0) bad = 1;
+                d = 1.0;
+            }
+            y = rsqrt_newton(d);
+            if (tid == 0) {
+                inv_d[kc] = y;
+                rdiag[kc] = d * y;
+            }
         }
+        y = __shfl_sync(0xffffffffu, y, 0);
+        for (int i = kc + 1 + tid; i < nb; i += kLeafThreads) a[i][kc] *= y;
         __syncthreads();
-        const double ip = inv_d[kc];
-        for (int i = kc + 1 + threadIdx.x; i < nb; i += blockDim.x) a[i][kc] *= ip;
-        __syncthreads();
-        // trailing lower triangle: thread (ty, tx) of a 16 x 16 grid strides
-        // over rows and columns (no integer division in the loop)
-        const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
         for (int i = kc + 1 + ty; i < nb; i += 16) {
             const double li = a[i][kc];
-            for (int j = kc + 1 + tx; j <= i; j += 16) a[i][j] = fma(-li, a[j][kc], a[i][j]);
+            for (int j = kc + 1 + tx; j <= i; j += 8) a[i][j] = fma(-li, a[j][kc], a[i][j]);
         }
         __syncthreads();
     }
-    // X = L^{-1}: column j by forward substitution (thread per column), with
-    // the pivot reciprocals instead of divisions
-    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
-        for (int i = 0; i < j; ++i) x[i][j] = 0.0;
-        x[j][j] = inv_d[j];
-        for (int i = j + 1; i < nb; ++i) {
+    // X = L^{-1}, row blocks of 16
+    for (int r0 = 0; r0 < nb; r0 += 16) {
+        const int r1 = min(nb, r0 + 16);
+        // right-hand side of the block's rows for the columns left of it:
+        // x[i][j] = -sum_{q=j}^{r0-1} l_iq x_qj  (scaled by 1/l_ii below)
+        for (int e = tid; e < (r1 - r0) * r0; e += kLeafThreads) {
+            const int i = r0 + e / r0, j = e % r0;
             double v = 0.0;
-            for (int q = j; q < i; ++q) v = fma(a[i][q], x[q][j], v);
-            x[i][j] = -v * inv_d[i];
+            for (int q = j; q < r0; ++q) v = fma(a[i][q], x[q][j], v);
+            x[i][j] = -v;
         }
+        __syncthreads();
+        // substitution inside the block, one thread per column j < r1
+        for (int j = tid; j < r1; j += kLeafThreads) {
+            for (int i = max(r0, j); i < r1; ++i) {
+                double v = (i == j) ? 1.0 : x[i][j];
+                for (int q = max(r0, j); q < i; ++q) v = fma(-a[i][q], x[q][j], v);
+                x[i][j] = v * inv_d[i];
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-        int i = e / nb, j = e % nb;
-        if (j <= i) M[i * ld + j] = a[i][j];
+    for (int e = tid; e < nb * nb; e += kLeafThreads) {
+        const int i = e / nb, j = e % nb;
+        if (j < i) M[i * ld + j] = a[i][j];
+        else if (j == i) M[i * ld + j] = rdiag[i];
         X[i * ld + j] = (j <= i) ? x[i][j] : 0.0;
     }
-    if (threadIdx.x == 0 && bad) atomicExch(fail, 1);
+    if (tid == 0 && bad) atomicExch(fail, 1);
 }
 
 __global__ void k_copy_add_diag(const double* __restrict__ src, double* __restrict__ dst,
@@ -362,7 +401,7 @@ msp_status chol_inv(msp_ctx* ctx, double* M, double* X, double* T1, double* T2, 
                                                    kLeafSmem));
             if (d >= 0 && d < 64) attr_set[d] = true;
         }
-        k_chol_leaf<<<1, 256, kLeafSmem, ctx->stream>>>(M + off * ld + off, X + off * ld + off, ld,
+        k_chol_leaf<<<1, kLeafThreads, kLeafSmem, ctx->stream>>>(M + off * ld + off, X + off * ld + off, ld,
                                                          (int)n, fail);
         MSP_CHECK_LAUNCH(ctx);
         return MSP_OK;

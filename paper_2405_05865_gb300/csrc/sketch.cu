@@ -132,10 +132,29 @@ template <typename T> struct V16;
 template <> struct V16<float> { using type = float4; static constexpr int W = 4; };
 template <> struct V16<double> { using type = double2; static constexpr int W = 2; };
 
+// Start of every J-row chunk in each column's entry list (entries sorted by
+// row): tab[c * (nch + 1) + t] = first entry of column c with row >= t J,
+// t = 0..nch. One thread per (column, chunk), binary search.
+__global__ void k_chunk_starts(const int32_t* __restrict__ ptr, const int32_t* __restrict__ ent,
+                               int64_t s_pad, int J, int nch, int32_t* __restrict__ tab) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= s_pad * (nch + 1)) return;
+    const int64_t c = e / (nch + 1);
+    const int tch = (int)(e % (nch + 1));
+    int lo = ptr[c], hi = ptr[c + 1];
+    const int64_t jt = (int64_t)tch * J;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((int64_t)(ent[mid] >> 1) < jt) lo = mid + 1;
+        else hi = mid;
+    }
+    tab[e] = lo;
+}
+
 template <typename T, int R, int NC>
 __global__ void __launch_bounds__(256) k_sketch_apply(
     const T* __restrict__ A, int64_t lda, int64_t n, int64_t s_pad,
-    const int32_t* __restrict__ ptr, const int32_t* __restrict__ ent, T scale,
+    const int32_t* __restrict__ tab, int nch, const int32_t* __restrict__ ent, T scale,
     T* __restrict__ C, int J) {
     using VT = typename V16<T>::type;
     constexpr int VW = V16<T>::W;
@@ -146,16 +165,12 @@ __global__ void __launch_bounds__(256) k_sketch_apply(
     const int64_t i0 = (int64_t)blockIdx.x * R;
     const int nthr = blockDim.x;
     T acc[NC][R];
-    int cur[NC], end[NC];
 #pragma unroll
-    for (int k = 0; k < NC; ++k) {
-        int c = threadIdx.x + k * nthr;
-        cur[k] = ptr[c];
-        end[k] = ptr[c + 1];
+    for (int k = 0; k < NC; ++k)
 #pragma unroll
         for (int r = 0; r < R; ++r) acc[k][r] = T(0);
-    }
-    for (int64_t j0 = 0; j0 < n; j0 += J) {
+    int chunk = 0;
+    for (int64_t j0 = 0; j0 < n; j0 += J, ++chunk) {
         const int jlen = (int)min((int64_t)J, n - j0);
         __syncthreads();
         for (int jj = threadIdx.x; jj < jlen; jj += nthr) {
@@ -173,16 +188,16 @@ __global__ void __launch_bounds__(256) k_sketch_apply(
             }
         }
         __syncthreads();
-        const int32_t jend = (int32_t)(j0 + jlen);
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
-            int e = cur[k];
-            const int ee = end[k];
-            while (e < ee) {
+            const int c = threadIdx.x + k * nthr;
+            const int e0 = __ldg(&tab[(int64_t)c * (nch + 1) + chunk]);
+            const int e1 = __ldg(&tab[(int64_t)c * (nch + 1) + chunk + 1]);
+            // fixed bounds: the entry loads of a chunk are independent
+#pragma unroll 4
+            for (int e = e0; e < e1; ++e) {
                 const int32_t v = __ldg(&ent[e]);
-                const int32_t j = v >> 1;
-                if (j >= jend) break;
-                const int jl = j - (int32_t)j0;
+                const int jl = (v >> 1) - (int32_t)j0;
                 const int sw = (jl >> 1) & 3;
                 const T sg = (v & 1) ? T(-1) : T(1);
 #pragma unroll
@@ -198,9 +213,7 @@ __global__ void __launch_bounds__(256) k_sketch_apply(
                         acc[k][2 * q + 1] = fma(sg, x.y, acc[k][2 * q + 1]);
                     }
                 }
-                ++e;
             }
-            cur[k] = e;
         }
     }
 #pragma unroll
@@ -231,13 +244,22 @@ msp_status launch_sketch_apply_r(msp_ctx* ctx, const T* A, int64_t lda, int64_t 
     const int J = (int)((64 * 1024) / (sizeof(T) * R));
     size_t smem = (size_t)J * R * sizeof(T);
     dim3 grid((unsigned)((n + R - 1) / R));
+    const int nch = (int)((n + J - 1) / J);
+    void* scr = nullptr;
+    MSP_TRY(msp_scratch(ctx, (size_t)s_pad * (nch + 1) * 4, &scr));
+    int32_t* tab = (int32_t*)scr;
+    {
+        const int64_t cnt = s_pad * (nch + 1);
+        k_chunk_starts<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(ptr, ent, s_pad, J, nch, tab);
+        MSP_CHECK_LAUNCH(ctx);
+    }
 #define MSP_SK_CASE(NCV)                                                              \
     case NCV: {                                                                       \
         auto kern = k_sketch_apply<T, R, NCV>;                                        \
         MSP_CUDA_TRY(ctx, cudaFuncSetAttribute(kern,                                  \
                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));        \
-        kern<<<grid, threads, smem, ctx->stream>>>(A, lda, n, s_pad, ptr, ent, scale, \
-                                                  C, J);                              \
+        kern<<<grid, threads, smem, ctx->stream>>>(A, lda, n, s_pad, tab, nch, ent,   \
+                                                  scale, C, J);                       \
         break;                                                                        \
     }
     switch (nc) {
