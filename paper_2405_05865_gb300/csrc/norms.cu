@@ -33,7 +33,36 @@ __global__ void __launch_bounds__(256) k_row_stats(const T* __restrict__ A, int6
     if (i >= n) return;
     const T* row = A + i * lda;
     double s = 0.0, e = 0.0, q = 0.0;
-    int64_t j = lane;
+    int64_t j = 0;
+    if constexpr (sizeof(T) == 4) {
+        // 16-byte loads, four per lane in flight per chunk of 16 entries
+        if ((((uintptr_t)row) & 15) == 0) {
+            const int64_t n4 = n & ~(int64_t)127;
+            for (; j < n4; j += 4 * 128) {
+                float4 v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    v[u] = (j + u * 128 < n4) ? __ldcs(reinterpret_cast<const float4*>(row + j + u * 128) + lane)
+                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+                float cs = 0.f, ca = 0.f, cq = 0.f;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float w4[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        cs += w4[c];
+                        ca += fabsf(w4[c]);
+                        cq = fmaf(w4[c], w4[c], cq);
+                    }
+                }
+                s += (double)cs;
+                e += (double)ca;
+                q += (double)cq;
+            }
+            j = n4;
+        }
+    }
+    j += lane;
     while (j < n) {
         float cs = 0.f, ca = 0.f, cq = 0.f;
 #pragma unroll 4
