@@ -84,6 +84,7 @@ enum { kTA = 0, kTG, kTTri, kTZ, kTVec, kTResid, kTCheck, kTimerClasses };
 
 struct BInst {
     const float* At;      // tile-major A
+    const float* Ct;      // tile-major C (n_pad x s_pad)
     const float* C;       // n x s_pad
     const float* Bl;      // L^{-1}, s_pad x s_pad (lower)
     const float* Bu;      // L^{-T} (upper)
@@ -396,7 +397,11 @@ __device__ __forceinline__ double colsum_rv(const float (&v)[8], float* wsum, in
 
 // --------------------------------------------------- the streamed A passes
 
-template <bool kResid>
+// What a streamed pass reads: A tiles with P slices (level-1 A pass), A
+// tiles with x_hi / x_lo slices (residual), C tiles with Y2 slices (Z step).
+enum { kModeA = 0, kModeR = 1, kModeZ = 2 };
+
+template <int Mode>
 __device__ __noinline__ void producer(const BArgs& a, unsigned char* ring, uint64_t* full, uint64_t* empty,
                          int2* hdr, uint32_t& kring, int* counter,
                          const int* flag) {
@@ -405,15 +410,22 @@ __device__ __noinline__ void producer(const BArgs& a, unsigned char* ring, uint6
     bool stop = false;
     while (!stop) {
         const int it = atomicAdd(counter, 1);
+        const int nitems = (Mode == kModeZ) ? a.nrows : a.nunits;
         int inst = -1, rb = 0, nk = 1, k0 = 0, k1 = 1;
-        if (it < a.nunits) {
-            const int2 w = a.units[it];
+        if (it < nitems) {
+            const int2 w = (Mode == kModeZ) ? a.rows[it] : a.units[it];
             inst = w.x;
             rb = w.y & 0xffff;
             if (!ld_volatile(flag + inst)) continue;
-            nk = a.inst[inst].n_pad / kKT;
-            k0 = (w.y >> 16) * a.ut;
-            k1 = min(nk, k0 + a.ut);
+            if (Mode == kModeZ) {
+                nk = a.inst[inst].s_pad / kKT;
+                k0 = 0;
+                k1 = nk;
+            } else {
+                nk = a.inst[inst].n_pad / kKT;
+                k0 = (w.y >> 16) * a.ut;
+                k1 = min(nk, k0 + a.ut);
+            }
         }
         for (int kt = k0; kt < k1; ++kt) {
             const int s = (int)(kring % kStages);
@@ -423,7 +435,7 @@ __device__ __noinline__ void producer(const BArgs& a, unsigned char* ring, uint6
                 break;
             }
             unsigned char* st = ring + (size_t)s * kStageBytes;
-            if (it >= a.nunits) {
+            if (it >= nitems) {
                 hdr[s] = make_int2(-1, 0);
                 msp::mbar_arrive(&full[s]);
                 ++kring;
@@ -431,18 +443,25 @@ __device__ __noinline__ void producer(const BArgs& a, unsigned char* ring, uint6
                 break;
             }
             hdr[s] = make_int2(it, 2 * kt + (kt == k1 - 1 ? 1 : 0));
-            if (kt == k0) atomicAdd(kResid ? &a.ctl->tilesR : &a.ctl->tilesA, (unsigned long long)(k1 - k0));
+            if (kt == k0) {
+                if (Mode == kModeZ) atomicAdd(&a.ctl->bytesZ, (unsigned long long)(k1 - k0) * kTileBytes);
+                else atomicAdd(Mode == kModeR ? &a.ctl->tilesR : &a.ctl->tilesA, (unsigned long long)(k1 - k0));
+            }
             const BInst& I = a.inst[inst];
-            const float* At = I.At + ((int64_t)rb * nk + kt) * kTileFloats;
-            const int64_t vrow = (int64_t)I.voff + (int64_t)kt * kKT;
-            msp::mbar_arrive_expect_tx(&full[s], kTileBytes + (kResid ? 2 : 1) * kSliceBytes);
+            const float* At = (Mode == kModeZ ? I.Ct : I.At) + ((int64_t)rb * nk + kt) * kTileFloats;
+            msp::mbar_arrive_expect_tx(&full[s], kTileBytes + (Mode == kModeR ? 2 : 1) * kSliceBytes);
             msp::bulk_g2s_hint(st, At, kTileBytes / 2, &full[s], pol);
             msp::bulk_g2s_hint(st + kTileBytes / 2, At + kTileFloats / 2, kTileBytes / 2, &full[s], pol);
-            if (!kResid) {
+            if (Mode == kModeA) {
+                const int64_t vrow = (int64_t)I.voff + (int64_t)kt * kKT;
                 msp::bulk_g2s(st + kTileBytes, a.P + vrow * kM, kSliceBytes, &full[s]);
-            } else {
+            } else if (Mode == kModeR) {
+                const int64_t vrow = (int64_t)I.voff + (int64_t)kt * kKT;
                 msp::bulk_g2s(st + kTileBytes, a.XH + vrow * kM, kSliceBytes, &full[s]);
                 msp::bulk_g2s(st + kTileBytes + kSliceBytes, a.XL + vrow * kM, kSliceBytes, &full[s]);
+            } else {
+                const int64_t srow = (int64_t)I.soff + (int64_t)kt * kKT;
+                msp::bulk_g2s(st + kTileBytes, a.Y2 + srow * kM, kSliceBytes, &full[s]);
             }
             ++kring;
         }
@@ -975,34 +994,41 @@ __device__ __noinline__ void step_tri(const BArgs& a, int t, unsigned char* smem
     }
 }
 
-// S5: Z = (R - C Y2) / lam~ by row blocks, partials of z.r and z.q.
-__device__ __noinline__ void step_Z(const BArgs& a, int t, unsigned char* smem, float* red, float* wsum,
-                                    int* slot, int tid, int w, int lane) {
-    const int cur = t & 1;
-    float* tiles = reinterpret_cast<float*>(smem);
-    float* Vs = reinterpret_cast<float*>(smem + kVsOffset);
-    int staged = -1;
-    for (;;) {
-        const int it = claim(&a.ctl->ctrZ, slot, tid);
-        if (it >= a.nrows) break;
-        const int2 item = a.rows[it];
-        const BInst& I = a.inst[item.x];
-        if (!ld_volatile(&a.iact[cur * a.count + item.x])) continue;
-        if (staged != item.x) {
-            stage_vec(Vs, a.Y2 + (int64_t)I.soff * kM, 0, I.s_pad, tid);
-            staged = item.x;
+// S5: Z = (R - C Y2) / lam~ by row blocks, partials of z.r and z.q: the
+// producer warp streams the instance's C tiles with Y2 slices through the
+// ring; the consumers keep FP32 FMA (the Woodbury form cancels).
+__device__ __noinline__ void consume_Z(const BArgs& a, unsigned char* ring, uint64_t* full, uint64_t* empty,
+                                       const int2* hdr, uint32_t& kring, float* red, float* wsum, int w,
+                                       int lane) {
+    float acc[4][16];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc[i][c] = 0.f;
+    int* err = &a.ctl->error;
+    while (true) {
+        const int s = (int)(kring % kStages);
+        if (!msp::mbar_wait_timed(&full[s], (kring / kStages) & 1u, err)) return;
+        const int2 h = hdr[s];
+        ++kring;
+        if (h.x < 0) {
+            __syncwarp();
+            if (lane == 0) msp::mbar_arrive(&empty[s]);
+            return;
         }
-        float acc[4][16];
+        const float* T = reinterpret_cast<const float*>(ring + (size_t)s * kStageBytes);
+        fma_tile(acc, T, T + kTileFloats, w, lane);
+        __syncwarp();
+        if (lane == 0) msp::mbar_arrive(&empty[s]);
+        if (!(h.y & 1)) continue;
+        const int2 item = a.rows[h.x];
+        const BInst& I = a.inst[item.x];
+        float out[8];
+        reduce_scatter_fma(acc, red, out, w, lane);
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int c = 0; c < 16; ++c) acc[i][c] = 0.f;
-        const int rows_valid = min(kRB, I.n - item.y * kRB);
-        if (tid == 0) atomicAdd(&a.ctl->bytesZ, (unsigned long long)rows_valid * I.s_pad * 4);
-        mv_stream(acc, I.C + (int64_t)item.y * kRB * I.s_pad, I.s_pad, rows_valid, 0, I.s_pad / kKT, Vs,
-                  tiles, tid, w, lane);
-        float out[8];
-        reduce_scatter_fma(acc, red, out, w, lane);
         const int ch = lane >> 4;
         const int64_t vrow = (int64_t)I.voff + item.y * kRB + 16 * w + (lane & 15);
         const float4 r0 = ld4(a.R + vrow * kM + 8 * ch), r1 = ld4(a.R + vrow * kM + 8 * ch + 4);
@@ -1241,13 +1267,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_batch_solve(BArgs a) {
             MSP_GBAR(kTTri);
             if (worker) step_tri<true>(a, t, smem, red, slot, tid, w, lane);
             MSP_GBAR(kTTri);
-            if (worker) step_Z(a, t, smem, red, wsum, slot, tid, w, lane);
+            if (worker) consume_Z(a, ring, full, empty, hdr, kring, red, wsum, w, lane);
+            else if (lane == 0)
+                producer<kModeZ>(a, ring, full, empty, hdr, kring, &ctl->ctrZ, a.iact + (t & 1) * a.count);
             MSP_GBAR(kTZ);
             if (worker) step_P(a, t, sv, tid, w, lane);
             MSP_GBAR(kTVec);
             if (worker) consume_A(a, ring, full, empty, hdr, kring, red, wsum, sflag, w, lane);
             else if (lane == 0)
-                producer<false>(a, ring, full, empty, hdr, kring, &ctl->ctrA, a.iact + (t & 1) * a.count);
+                producer<kModeA>(a, ring, full, empty, hdr, kring, &ctl->ctrA, a.iact + (t & 1) * a.count);
             MSP_GBAR(kTA);
             if (worker) step_X(a, t, wsum, sv, tid, w, lane);
             MSP_GBAR(kTVec);
@@ -1258,15 +1286,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_batch_solve(BArgs a) {
         if (worker)
             consume_R(a, ring, full, empty, hdr, kring, reinterpret_cast<double*>(red), wsumd, sflag, w, lane);
         else if (lane == 0)
-            producer<true>(a, ring, full, empty, hdr, kring, &ctl->ctrR, a.istep);
+            producer<kModeR>(a, ring, full, empty, hdr, kring, &ctl->ctrR, a.istep);
         MSP_GBAR(kTResid);
     }
 #undef MSP_GBAR
 }
 
-// Copy A (row-major, lda) into the swizzled tile layout, zero-padded.
+// Copy a rows x cols row-major matrix (lda) into the swizzled tile layout,
+// zero-padded: A itself, and the sketch C for the Z step.
 __global__ void __launch_bounds__(256) k_pack_tiles(const float* __restrict__ A, int64_t lda, int n,
-                                                   int nk, float* __restrict__ At) {
+                                                   int ncols, int nk, float* __restrict__ At) {
     const int tile = blockIdx.x, I = tile / nk, K = tile % nk;
     float* dst = At + (int64_t)tile * kTileFloats;
     const bool vec = (lda % 4 == 0) && (((uintptr_t)A & 15) == 0);
@@ -1275,13 +1304,13 @@ __global__ void __launch_bounds__(256) k_pack_tiles(const float* __restrict__ A,
         const int64_t gr = (int64_t)I * kRB + r, gc = (int64_t)K * kKT + 4 * g;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (gr < n) {
-            if (vec && gc + 4 <= n) {
+            if (vec && gc + 4 <= ncols) {
                 v = __ldcs(reinterpret_cast<const float4*>(A + gr * lda + gc));
             } else {
-                if (gc + 0 < n) v.x = A[gr * lda + gc + 0];
-                if (gc + 1 < n) v.y = A[gr * lda + gc + 1];
-                if (gc + 2 < n) v.z = A[gr * lda + gc + 2];
-                if (gc + 3 < n) v.w = A[gr * lda + gc + 3];
+                if (gc + 0 < ncols) v.x = A[gr * lda + gc + 0];
+                if (gc + 1 < ncols) v.y = A[gr * lda + gc + 1];
+                if (gc + 2 < ncols) v.z = A[gr * lda + gc + 2];
+                if (gc + 3 < ncols) v.w = A[gr * lda + gc + 3];
             }
         }
         reinterpret_cast<float4*>(dst)[r * 16 + (g ^ (r & 7))] = v;
@@ -1577,6 +1606,9 @@ msp_status msp_batch_create(msp_ctx* ctx, int count, const msp_instance* inst, m
         return o;
     };
     const size_t o_at = take((size_t)at * 4);
+    int64_t ct_total = 0;
+    for (const BInst& H : b->hinst) ct_total += (int64_t)H.n_pad * H.s_pad;
+    const size_t o_ct = take((size_t)ct_total * 4);
     const size_t o_inst = take(sizeof(BInst) * cnt);
     const size_t o_rows = take(sizeof(int2) * b->rows.size());
     const size_t o_strips = take(sizeof(int2) * b->strips.size());
@@ -1614,10 +1646,12 @@ msp_status msp_batch_create(msp_ctx* ctx, int count, const msp_instance* inst, m
         return fail(msp_set_error(ctx, MSP_ENOMEM, "batch: device allocation of %zu bytes failed", total));
     }
     char* base = (char*)b->mem;
-    int64_t ta = 0;
+    int64_t ta = 0, tc = 0;
     for (int k = 0; k < count; ++k) {
         BInst& H = b->hinst[k];
         H.At = (const float*)(base + o_at) + ta;
+        H.Ct = (const float*)(base + o_ct) + tc;
+        tc += (int64_t)H.n_pad * H.s_pad;
         ta += (int64_t)H.n_pad * H.n_pad;
         H.C = (const float*)b->sk[k]->C;
         H.Bl = (const float*)b->f[k]->B;
@@ -1628,7 +1662,11 @@ msp_status msp_batch_create(msp_ctx* ctx, int count, const msp_instance* inst, m
         const BInst& H = b->hinst[k];
         const int nk = H.n_pad / kKT;
         const int tiles = H.nb * nk;
-        k_pack_tiles<<<tiles, 256, 0, ctx->stream>>>(inst[k].A, inst[k].lda, H.n, nk, (float*)H.At);
+        k_pack_tiles<<<tiles, 256, 0, ctx->stream>>>(inst[k].A, inst[k].lda, H.n, H.n, nk, (float*)H.At);
+        if (cudaGetLastError() != cudaSuccess) return fail(msp_set_error(ctx, MSP_ECUDA, "batch: pack launch failed"));
+        ++ctx->launches;
+        const int nkc = H.s_pad / kKT;
+        k_pack_tiles<<<H.nb * nkc, 256, 0, ctx->stream>>>(H.C, H.s_pad, H.n, H.s_pad, nkc, (float*)H.Ct);
         if (cudaGetLastError() != cudaSuccess) return fail(msp_set_error(ctx, MSP_ECUDA, "batch: pack launch failed"));
         ++ctx->launches;
     }
