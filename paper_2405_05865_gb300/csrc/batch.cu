@@ -76,8 +76,6 @@ constexpr size_t kSmem = (size_t)kRingBytes + kRedBytes + kMiscBytes;
 // smem map of the mat-vec steps (S3-S5): 3 tiles, the staged vector block
 constexpr int kMvTiles = 3;
 constexpr int kVsOffset = kMvTiles * kTileBytes;          // 96 KB
-// S2 ring: C tile + R tile per stage
-constexpr int kS2Stage = kTileBytes + kRB * kM * 4;       // 40 KB
 
 // device-timer classes of BCtl::t_ns
 enum { kTA = 0, kTG, kTTri, kTZ, kTVec, kTResid, kTCheck, kTimerClasses };
@@ -398,8 +396,9 @@ __device__ __forceinline__ double colsum_rv(const float (&v)[8], float* wsum, in
 // --------------------------------------------------- the streamed A passes
 
 // What a streamed pass reads: A tiles with P slices (level-1 A pass), A
-// tiles with x_hi / x_lo slices (residual), C tiles with Y2 slices (Z step).
-enum { kModeA = 0, kModeR = 1, kModeZ = 2 };
+// tiles with x_hi / x_lo slices (residual), C tiles with Y2 slices (Z step),
+// a 64-column strip of C tiles down the row blocks with R rows (G step).
+enum { kModeA = 0, kModeR = 1, kModeZ = 2, kModeG = 3 };
 
 template <int Mode>
 __device__ __noinline__ void producer(const BArgs& a, unsigned char* ring, uint64_t* full, uint64_t* empty,
@@ -410,14 +409,19 @@ __device__ __noinline__ void producer(const BArgs& a, unsigned char* ring, uint6
     bool stop = false;
     while (!stop) {
         const int it = atomicAdd(counter, 1);
-        const int nitems = (Mode == kModeZ) ? a.nrows : a.nunits;
+        const int nitems = (Mode == kModeZ) ? a.nrows : (Mode == kModeG) ? a.nstrips : a.nunits;
         int inst = -1, rb = 0, nk = 1, k0 = 0, k1 = 1;
         if (it < nitems) {
-            const int2 w = (Mode == kModeZ) ? a.rows[it] : a.units[it];
+            const int2 w = (Mode == kModeZ) ? a.rows[it] : (Mode == kModeG) ? a.strips[it] : a.units[it];
             inst = w.x;
             rb = w.y & 0xffff;
             if (!ld_volatile(flag + inst)) continue;
-            if (Mode == kModeZ) {
+            if (Mode == kModeG) {
+                // rb holds the strip; the loop runs over the row blocks
+                nk = a.inst[inst].s_pad / kKT;
+                k0 = 0;
+                k1 = a.inst[inst].nb;
+            } else if (Mode == kModeZ) {
                 nk = a.inst[inst].s_pad / kKT;
                 k0 = 0;
                 k1 = nk;
@@ -445,11 +449,13 @@ __device__ __noinline__ void producer(const BArgs& a, unsigned char* ring, uint6
             hdr[s] = make_int2(it, 2 * kt + (kt == k1 - 1 ? 1 : 0));
             if (kt == k0) {
                 if (Mode == kModeZ) atomicAdd(&a.ctl->bytesZ, (unsigned long long)(k1 - k0) * kTileBytes);
+                else if (Mode == kModeG) atomicAdd(&a.ctl->bytesG, (unsigned long long)(k1 - k0) * kTileBytes);
                 else atomicAdd(Mode == kModeR ? &a.ctl->tilesR : &a.ctl->tilesA, (unsigned long long)(k1 - k0));
             }
             const BInst& I = a.inst[inst];
-            const float* At = (Mode == kModeZ ? I.Ct : I.At) + ((int64_t)rb * nk + kt) * kTileFloats;
-            msp::mbar_arrive_expect_tx(&full[s], kTileBytes + (Mode == kModeR ? 2 : 1) * kSliceBytes);
+            const int64_t tile = (Mode == kModeG) ? ((int64_t)kt * nk + rb) : ((int64_t)rb * nk + kt);
+            const float* At = (Mode == kModeZ || Mode == kModeG ? I.Ct : I.At) + tile * kTileFloats;
+            msp::mbar_arrive_expect_tx(&full[s], kTileBytes + (Mode == kModeR || Mode == kModeG ? 2 : 1) * kSliceBytes);
             msp::bulk_g2s_hint(st, At, kTileBytes / 2, &full[s], pol);
             msp::bulk_g2s_hint(st + kTileBytes / 2, At + kTileFloats / 2, kTileBytes / 2, &full[s], pol);
             if (Mode == kModeA) {
@@ -459,9 +465,12 @@ __device__ __noinline__ void producer(const BArgs& a, unsigned char* ring, uint6
                 const int64_t vrow = (int64_t)I.voff + (int64_t)kt * kKT;
                 msp::bulk_g2s(st + kTileBytes, a.XH + vrow * kM, kSliceBytes, &full[s]);
                 msp::bulk_g2s(st + kTileBytes + kSliceBytes, a.XL + vrow * kM, kSliceBytes, &full[s]);
-            } else {
+            } else if (Mode == kModeZ) {
                 const int64_t srow = (int64_t)I.soff + (int64_t)kt * kKT;
                 msp::bulk_g2s(st + kTileBytes, a.Y2 + srow * kM, kSliceBytes, &full[s]);
+            } else {
+                const int64_t vrow = (int64_t)I.voff + (int64_t)kt * kRB;
+                msp::bulk_g2s(st + kTileBytes, a.R + vrow * kM, 2 * kSliceBytes, &full[s]);
             }
             ++kring;
         }
@@ -848,97 +857,82 @@ __device__ __forceinline__ void step_scale(const BArgs& a, int step, float* wsum
     }
 }
 
-// S2: convergence flags (one block per instance), then G = C^T R by strips.
-__device__ __noinline__ void step_G(const BArgs& a, int t, unsigned char* smem, float* red, int* slot,
-                                    int tid, int w, int lane) {
-    const int cur = t & 1, prev = cur ^ 1;
-    float* ring = reinterpret_cast<float*>(smem);
-    for (;;) {
-        const int it = claim(&a.ctl->ctrG, slot, tid);
-        if (it >= a.nstrips) break;
-        const int2 item = a.strips[it];
-        const int i = item.x;
+// S2 part 1: per instance (one block each, warp 0), the convergence flags of
+// its columns from the |r|^2 partials, and the active-column count.
+__device__ __forceinline__ void step_flags(const BArgs& a, int t, int lane) {
+    const int cur = t & 1;
+    for (int i = blockIdx.x; i < a.count; i += gridDim.x) {
         const BInst& I = a.inst[i];
-        if (item.y == 0 && w == 0) {
-            const int c = lane & 15, gi = i * kM + c;
-            double rr = 0.0;
-            for (int b = 0; b < I.nb; ++b) rr += a.p_rr[((int64_t)I.boff + b) * kM + c];
-            const bool live = lane < 16 && c < I.m && !a.fin[gi];
-            if (live && !isfinite(rr)) atomicCAS(&a.ierr[i], 0, (int)MSP_ENONFINITE);
+        const int c = lane & 15, gi = i * kM + c;
+        double rr = 0.0;
+        for (int b = 0; b < I.nb; ++b) rr += a.p_rr[((int64_t)I.boff + b) * kM + c];
+        const bool live = lane < 16 && c < I.m && !a.fin[gi];
+        if (live && !isfinite(rr)) atomicCAS(&a.ierr[i], 0, (int)MSP_ENONFINITE);
+        __syncwarp();
+        const bool act = live && ld_volatile(&a.ierr[i]) == 0 && rr > a.rtol2 && t < a.max_outer;
+        if (lane < 16) a.act[gi] = act ? 1 : 0;
+        const unsigned m = __ballot_sync(0xffffffffu, act);
+        if (lane == 0) {
+            a.iact[cur * a.count + i] = m ? 1 : 0;
+            if (m) {
+                a.iters[i] += 1;
+                atomicAdd(&a.ctl->active[cur], __popc(m));
+            }
+        }
+    }
+}
+
+// S2 part 2: G = C^T R by 64-column strips of C: the producer streams the
+// strip's tiles down all row blocks with the R rows of each; warp w takes
+// rows 16w..16w+15 of a tile, a lane two columns x 16 right-hand sides
+// (FP32 FMA), and the 8 warps' sums are combined in warp order at the end of
+// the strip.
+__device__ __noinline__ void consume_G(const BArgs& a, unsigned char* ring, uint64_t* full, uint64_t* empty,
+                                       const int2* hdr, uint32_t& kring, float* red, int w, int lane) {
+    float acc[2][16];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc[q][c] = 0.f;
+    int* err = &a.ctl->error;
+    const int tid = w * 32 + lane;
+    while (true) {
+        const int s = (int)(kring % kStages);
+        if (!msp::mbar_wait_timed(&full[s], (kring / kStages) & 1u, err)) return;
+        const int2 h = hdr[s];
+        ++kring;
+        if (h.x < 0) {
             __syncwarp();
-            const bool act = live && ld_volatile(&a.ierr[i]) == 0 && rr > a.rtol2 && t < a.max_outer;
-            if (lane < 16) a.act[gi] = act ? 1 : 0;
-            const unsigned m = __ballot_sync(0xffffffffu, act);
-            if (lane == 0) {
-                a.iact[cur * a.count + i] = m ? 1 : 0;
-                if (m) {
-                    a.iters[i] += 1;
-                    atomicAdd(&a.ctl->active[cur], __popc(m));
-                }
-            }
+            if (lane == 0) msp::mbar_arrive(&empty[s]);
+            return;
         }
-        if (!ld_volatile(&a.iact[prev * a.count + i])) continue;
-        if (tid == 0) atomicAdd(&a.ctl->bytesG, (unsigned long long)I.n * kKT * 4);
-        // G[strip] = sum over row tiles of C[tile rows][strip]^T R[tile rows]
-        float acc[2][16];
-#pragma unroll
-        for (int q = 0; q < 2; ++q)
-#pragma unroll
-            for (int c = 0; c < 16; ++c) acc[q][c] = 0.f;
-        const int nrt = I.nb;
-        const float* Cs = I.C + item.y * kKT;
-        auto issue = [&](int rt, int buf) {
-            float* T = ring + buf * (kS2Stage / 4);
-            float* Rt = T + kTileFloats;
-            const int rows_valid = min(kRB, I.n - rt * kRB);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int e = tid + kWorkers * j;
-                const int row = e >> 4, g = e & 15;
-                const bool ok = row < rows_valid;
-                const float* src = ok ? Cs + (int64_t)(rt * kRB + row) * I.s_pad + 4 * g : I.C;
-                msp::cp_async16(T + row * kKT + ((g ^ (row & 7)) << 2), src, ok);
-            }
-            const float* rsrc = a.R + ((int64_t)I.voff + rt * kRB) * kM;
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const int e = tid + kWorkers * j;
-                msp::cp_async16(Rt + 4 * e, rsrc + 4 * e, true);
-            }
-        };
-        for (int j = 0; j < 2; ++j) {
-            if (j < nrt) issue(j, j);
-            msp::cp_async_commit();
-        }
-        for (int rt = 0; rt < nrt; ++rt) {
-            if (rt + 2 < nrt) issue(rt + 2, (rt + 2) % 3);
-            msp::cp_async_commit();
-            msp::cp_async_wait<2>();
-            msp::bar_workers<kWorkers>();
-            const float* T = ring + (rt % 3) * (kS2Stage / 4);
-            const float4* R4 = reinterpret_cast<const float4*>(T + kTileFloats);
+        const float* T = reinterpret_cast<const float*>(ring + (size_t)s * kStageBytes);
+        const float4* R4 = reinterpret_cast<const float4*>(T + kTileFloats);
 #pragma unroll 4
-            for (int rr = 0; rr < 16; ++rr) {
-                const int r = 16 * w + rr, sw = r & 7;
-                const float* Tr = T + r * kKT;
-                const float c0 = Tr[(((lane >> 2) ^ sw) << 2) + (lane & 3)];
-                const float c1 = Tr[((((lane >> 2) + 8) ^ sw) << 2) + (lane & 3)];
+        for (int rr = 0; rr < 16; ++rr) {
+            const int r = 16 * w + rr, sw = r & 7;
+            const float* Tr = T + r * kKT;
+            const float c0 = Tr[(((lane >> 2) ^ sw) << 2) + (lane & 3)];
+            const float c1 = Tr[((((lane >> 2) + 8) ^ sw) << 2) + (lane & 3)];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float4 v = R4[r * 4 + j];
-                    acc[0][4 * j + 0] = fmaf(c0, v.x, acc[0][4 * j + 0]);
-                    acc[0][4 * j + 1] = fmaf(c0, v.y, acc[0][4 * j + 1]);
-                    acc[0][4 * j + 2] = fmaf(c0, v.z, acc[0][4 * j + 2]);
-                    acc[0][4 * j + 3] = fmaf(c0, v.w, acc[0][4 * j + 3]);
-                    acc[1][4 * j + 0] = fmaf(c1, v.x, acc[1][4 * j + 0]);
-                    acc[1][4 * j + 1] = fmaf(c1, v.y, acc[1][4 * j + 1]);
-                    acc[1][4 * j + 2] = fmaf(c1, v.z, acc[1][4 * j + 2]);
-                    acc[1][4 * j + 3] = fmaf(c1, v.w, acc[1][4 * j + 3]);
-                }
+            for (int j = 0; j < 4; ++j) {
+                const float4 v = R4[r * 4 + j];
+                acc[0][4 * j + 0] = fmaf(c0, v.x, acc[0][4 * j + 0]);
+                acc[0][4 * j + 1] = fmaf(c0, v.y, acc[0][4 * j + 1]);
+                acc[0][4 * j + 2] = fmaf(c0, v.z, acc[0][4 * j + 2]);
+                acc[0][4 * j + 3] = fmaf(c0, v.w, acc[0][4 * j + 3]);
+                acc[1][4 * j + 0] = fmaf(c1, v.x, acc[1][4 * j + 0]);
+                acc[1][4 * j + 1] = fmaf(c1, v.y, acc[1][4 * j + 1]);
+                acc[1][4 * j + 2] = fmaf(c1, v.z, acc[1][4 * j + 2]);
+                acc[1][4 * j + 3] = fmaf(c1, v.w, acc[1][4 * j + 3]);
             }
-            msp::bar_workers<kWorkers>();
         }
-        // sum the 8 warps' partials in order
+        __syncwarp();
+        if (lane == 0) msp::mbar_arrive(&empty[s]);
+        if (!(h.y & 1)) continue;
+        // ---- strip complete: sum the 8 warps' partials in order
+        const int2 item = a.strips[h.x];
+        const BInst& I = a.inst[item.x];
         float4* red4 = reinterpret_cast<float4*>(red);
 #pragma unroll
         for (int q = 0; q < 2; ++q)
@@ -946,6 +940,10 @@ __device__ __noinline__ void step_G(const BArgs& a, int t, unsigned char* smem, 
             for (int j = 0; j < 4; ++j)
                 red4[(w * 64 + lane + 32 * q) * 4 + j] =
                     make_float4(acc[q][4 * j], acc[q][4 * j + 1], acc[q][4 * j + 2], acc[q][4 * j + 3]);
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[q][c] = 0.f;
         msp::bar_workers<kWorkers>();
         {
             const int j = tid >> 2, qd = tid & 3;
@@ -1256,7 +1254,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_batch_solve(BArgs a) {
         if (worker) step_scale(a, step, wsum, sd, tid, w, lane);
         MSP_GBAR(kTCheck);
         for (int t = 0;; ++t) {
-            if (worker) step_G(a, t, smem, red, slot, tid, w, lane);
+            if (worker) {
+                if (w == 0) step_flags(a, t, lane);
+                consume_G(a, ring, full, empty, hdr, kring, red, w, lane);
+            } else if (lane == 0) {
+                producer<kModeG>(a, ring, full, empty, hdr, kring, &ctl->ctrG, a.iact + ((t + 1) & 1) * a.count);
+            }
             MSP_GBAR(kTG);
             if (ld_volatile(&ctl->active[t & 1]) == 0) break;
             if (blockIdx.x == 0 && tid == 0) {
