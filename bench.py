@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-schatten", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=5, help="level-1 iterations in the CPU sample")
     ap.add_argument("--batch-count", type=int, default=64, help="instances of the batched workload")
     ap.add_argument("--batch-steps", type=int, default=3)
@@ -431,6 +432,58 @@ def run_msp(args, rank, world, local):
                "estimates_per_s": 1000.0 / sms, "tflops_fp32": flops / (sms * 1e-3) / 1e12,
                "probes": 256}
 
+    # adjoint (the backward of x = (K_ell + lam I)^{-1} b for L = c^T x): the
+    # forward solve, then a second solve with the cached factor, dL/dlam and
+    # the fused dL/dell pair kernel; and that kernel alone
+    adj = None
+    if not args.no_adjoint:
+        from workloads import make_workload
+        from paper_2405_05865_gb300.autograd import rbf_solve
+        w = make_workload("rbf", seed=rank, n=n, rbf_dtype=np.float32)
+        pts = torch.from_numpy(w.points).to(dev)
+        cvec = torch.from_numpy(np.random.default_rng([rank, 9]).standard_normal(n)).to(dev)
+        ell = torch.tensor(0.1, dtype=torch.float64, requires_grad=True)
+        lam_t = torch.tensor(lam, dtype=torch.float64, requires_grad=True)
+        b_t = bd.clone().requires_grad_(True)
+        sopts = dict(tol=1e-10, refine_tol=args.refine_tol, criterion="backward")
+
+        def fwd_bwd():
+            x = rbf_solve(pts, ell, lam_t, b_t, ctx, s, **sopts)
+            (cvec @ x).backward()
+            return ell.grad, lam_t.grad
+
+        fwd_bwd()
+        barrier()
+        torch.cuda.synchronize(dev)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.steps):
+            ell.grad = None
+            lam_t.grad = None
+            b_t.grad = None
+            fwd_bwd()
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        ams = max_over_ranks(a0.elapsed_time(a1) / args.steps, dev)
+        # the fused dL/dell kernel alone
+        av = torch.randn(n, dtype=torch.float64, device=dev)
+        xv = torch.randn(n, dtype=torch.float64, device=dev)
+        ctx.rbf_grad_ell(pts, 0.1, av, xv)
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(args.steps):
+            ctx.rbf_grad_ell(pts, 0.1, av, xv)
+        g1.record(stream)
+        torch.cuda.synchronize(dev)
+        gms = g0.elapsed_time(g1) / args.steps
+        adj = {"workload": f"RBF n={n} l=0.1 lam=1e-2, L = c^T x: forward solve + backward (adjoint "
+                           f"solve with the cached factor, dL/db, dL/dlam, dL/dell), backward error 1e-10",
+               "value": job_rate(args.steps, world, ams * args.steps / 1000.0), "unit": "gradients/s",
+               "ms_per_gradient": ams, "dL_dell": float(ell.grad), "dL_dlam": float(lam_t.grad),
+               "grad_ell_kernel_ms": gms, "grad_ell_pairs_per_s": n * n / (gms * 1e-3)}
+
     # roofline of the dominant kernel: the A pass q = (A + lam I) p
     g_ms = sum(i["gemv_ms"] for i in infos)
     g_n = sum(i["gemv_launches"] for i in infos)
@@ -494,6 +547,7 @@ def run_msp(args, rank, world, local):
            "rel_resid_1e-10": strict,
            "fp32_plain": fp32,
            "schatten1": sch,
+           "adjoint": adj,
            "batched": batched,
            "phase_ms_per_step": {"a_pass": g_ms / args.steps, "level2": l2_ms / args.steps,
                                  "fp64_residual": r_ms / args.steps},

@@ -394,6 +394,12 @@ MSP_API msp_status msp_rbf_kernel(msp_ctx* ctx, const double* points, int64_t n,
 MSP_API msp_status msp_rbf_grad_ell(msp_ctx* ctx, const double* points, int64_t n, int dim,
                                     double ell, const double* a, const double* x, double* out);
 
+/* out = scale * x^T y for device FP64 vectors of n (FP64, fixed-order block
+ * reduction), written to the device scalar out when the work completes. The
+ * adjoint's dL/dlambda = -a^T x is msp_dot(a, x, scale = -1). */
+MSP_API msp_status msp_dot(msp_ctx* ctx, const double* x, const double* y, int64_t n, double scale,
+                           double* out);
+
 /* No-allocation variant of msp_rbf_grad_ell (the paper has no counterpart:
  * this is an interface for callers, not a step of the method). Some callers
  * cannot allocate device memory at the point where they need the gradient:

@@ -325,6 +325,15 @@ class Context:
                                                     _ptr(a.contiguous()), _ptr(x.contiguous()), _ptr(out)))
         return out
 
+    def dot(self, x: torch.Tensor, y: torch.Tensor, scale: float = 1.0) -> torch.Tensor:
+        """scale * x^T y as a 0-d CUDA float64 tensor (msp_dot)."""
+        if not (x.is_cuda and y.is_cuda and x.dtype == y.dtype == torch.float64 and x.numel() == y.numel()):
+            raise ValueError("x, y must be CUDA float64 vectors of one length")
+        out = torch.empty((), dtype=torch.float64, device=self.device)
+        L.check(self.ptr, self.lib.msp_dot(self.ptr, _ptr(x.contiguous()), _ptr(y.contiguous()), x.numel(),
+                                           float(scale), _ptr(out)))
+        return out
+
     def norm_lower_bound(self, A: torch.Tensor) -> float:
         """L <= |A|_2 (largest column norm, all-ones Rayleigh quotient)."""
         n, lda, dt = _check_matrix(A)

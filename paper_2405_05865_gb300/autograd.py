@@ -35,7 +35,7 @@ class RbfSolve(torch.autograd.Function):
         (x,) = fctx.saved_tensors
         ctx, K, sk, f, points, ell_v, lam_v, opts = fctx.state
         a, _ = ctx.solve(f, K, gx.contiguous().to(torch.float64), lam_v, **opts)
-        g_lam = -(a @ x)
+        g_lam = ctx.dot(a, x, -1.0)
         g_ell = ctx.rbf_grad_ell(points, ell_v, a, x)
         fctx.state = None
         return None, g_ell, g_lam, a, None, None, None, None

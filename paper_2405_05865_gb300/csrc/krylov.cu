@@ -983,6 +983,15 @@ __global__ void k_norm2(const double* __restrict__ v, int64_t n, double* __restr
     if (threadIdx.x == 0) *out = acc;
 }
 
+__global__ void k_dot(const double* __restrict__ x, const double* __restrict__ y, int64_t n, double scale,
+                      double* __restrict__ out) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) acc += x[i] * y[i];
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) *out = scale * acc;
+}
+
 // dst = (T)(src / sqrt(*nrm2)) (0 if the norm is 0)
 template <typename T>
 __global__ void k_scale_cast(const double* __restrict__ src, const double* __restrict__ nrm2,
@@ -1007,6 +1016,16 @@ __global__ void k_axpy_back(double* __restrict__ x, const T* __restrict__ d,
 
 msp_status msp_norm2(msp_ctx* ctx, const double* v, int64_t n, double* out_dev) {
     k_norm2<<<1, 1024, 0, ctx->stream>>>(v, n, out_dev);
+    MSP_CHECK_LAUNCH(ctx);
+    return MSP_OK;
+}
+
+extern "C" msp_status msp_dot(msp_ctx* ctx, const double* x, const double* y, int64_t n, double scale,
+                              double* out) {
+    if (!ctx) return msp_set_error(nullptr, MSP_EINVAL, "ctx is NULL");
+    if (!x || !y || !out || n < 1) return msp_set_error(ctx, MSP_EINVAL, "dot: bad argument");
+    msp::DeviceGuard g(ctx->device);
+    k_dot<<<1, 1024, 0, ctx->stream>>>(x, y, n, scale, out);
     MSP_CHECK_LAUNCH(ctx);
     return MSP_OK;
 }
