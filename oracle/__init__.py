@@ -24,4 +24,5 @@ Modules
 ``adjoint``   gradients of L = g^T x, x = (K_theta + lam I)^{-1} b
 ``batch``     batches of instances with several right-hand sides each: the
               definition (independent per-column solves) as a loop
+``effdim``    effective dimension d_lambda by Hutchinson over regularised solves
 """

@@ -1,0 +1,41 @@
+"""Effective dimension by Hutchinson over regularised solves (oracle, FP64).
+
+d_lambda = tr(A (A + lambda I)^{-1}) = sum_i sigma_i / (sigma_i + lambda)
+(Section 2, Lemma 2.1's quantity; the KRR analysis of Section 3 sets the
+sketch size from it). With A (A + lambda I)^{-1} = I - lambda (A + lambda I)^{-1},
+
+    d_lambda = n - lambda tr((A + lambda I)^{-1}),
+
+and the trace is estimated as in the Schatten-1 estimator: the mean over
+Rademacher probes g_j of g_j^T (A + lambda I)^{-1} g_j, the solves being the
+regularised systems the method solves. Probes are those of ``hutchinson``.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+from . import reference
+
+
+def quadratic_forms(A: np.ndarray, lam: float, G: np.ndarray, solve=None) -> np.ndarray:
+    """q_j = g_j^T (A + lam I)^{-1} g_j; ``solve(A, G, lam)`` defaults to the
+    dense Cholesky solve."""
+    X = (solve or reference.solve_dense)(A, G, lam)
+    return np.einsum("ij,ij->j", G, X)
+
+
+def estimate(A: np.ndarray, lam: float, G: np.ndarray, solve=None) -> tuple[float, float]:
+    """(estimate of d_lambda, standard error of the mean over probes)."""
+    n, m = G.shape
+    vals = n - lam * quadratic_forms(A, lam, G, solve)
+    se = float(vals.std(ddof=1) / np.sqrt(m)) if m > 1 else float("nan")
+    return float(vals.mean()), se
+
+
+def variance_one_probe(A: np.ndarray, lam: float) -> float:
+    """Var(n - lam g^T (A + lam I)^{-1} g) for Rademacher g: with
+    B = lam (A + lam I)^{-1} symmetric, Var(g^T B g) = 2 (|B|_F^2 - sum_i B_ii^2)."""
+    A = np.asarray(A, dtype=np.float64)
+    B = lam * np.linalg.inv(A + lam * np.eye(A.shape[0]))
+    return float(2.0 * (np.sum(B * B) - np.sum(np.diag(B) ** 2)))
