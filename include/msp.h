@@ -291,7 +291,11 @@ typedef struct msp_batch_s msp_batch_t;
  * batch; B and X are read and written by msp_batch_solve, and A's contents
  * are copied here (later changes to A are not seen). Requires count >= 1 and
  * every instance valid; the whole batch fails on the first bad instance.
- * Destroy every batch before its context. */
+ * Instances that name the same A pointer, n, lda, lambda, lambda0, s,
+ * gamma, phi, gamma_phi and seed are one system with more right-hand sides:
+ * they share one sketch, factor and tiled copy of A (set up once), so a
+ * system with more than 16 right-hand sides is solved as several such
+ * instances in one launch. Destroy every batch before its context. */
 MSP_API msp_status msp_batch_create(msp_ctx* ctx, int count, const msp_instance* inst,
                                     msp_batch_t** out);
 MSP_API void msp_batch_destroy(msp_batch_t* batch);
@@ -374,6 +378,27 @@ MSP_API msp_status msp_schatten(msp_ctx* ctx, const void* A, msp_dtype dtype, in
  * tile products combined in FP64. */
 MSP_API msp_status msp_hutchinson(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n,
                                   int64_t lda, int64_t probes, uint64_t seed, double* q);
+
+/* ------------------------------------------ effective dimension d_lambda */
+
+/* d_lambda = tr(A (A + lambda I)^{-1}) = sum_i sigma_i / (sigma_i + lambda)
+ * (Section 2, the quantity of Lemma 2.1 that sets the sketch size in the
+ * kernel ridge regression analysis), estimated as
+ * n - lambda (1/m) sum_j g_j^T (A + lambda I)^{-1} g_j over m = `probes`
+ * Rademacher probes (the probes of msp_schatten with `seed`), the solves run
+ * as one batch (msp_batch_create with every instance naming A, so the
+ * sketch of size s and gamma, seed `seed`, the factor and the tiled copy of
+ * A are built once; Phi = I; opts as for msp_batch_solve).
+ * A: device FP32 n x n, lda >= n, symmetric PSD; 2 <= probes <= 4096.
+ * estimate, std_err: host scalars (the mean and the standard error of the
+ * per-probe values n - lambda g_j^T x_j), either may be NULL; q: NULL or a
+ * device FP64 array of `probes` receiving those values. Returns the solve's
+ * status (MSP_ENOCONV when a solve hit its caps; the estimate is still
+ * written). */
+MSP_API msp_status msp_effective_dimension(msp_ctx* ctx, const float* A, int64_t n, int64_t lda,
+                                           double lambda, int64_t probes, uint64_t seed, int64_t s,
+                                           int gamma, const msp_opts* opts, double* estimate,
+                                           double* std_err, double* q);
 
 /* ------------------------------------------------- a11: RBF and adjoint */
 

@@ -83,6 +83,8 @@ _SIGS = {
                                  C.POINTER(MspInfo)]),
     "msp_matvec_f64": (C.c_int, [P, P, C.c_int, I64, I64, C.c_double, P, P]),
     "msp_dot": (C.c_int, [P, P, P, I64, C.c_double, P]),
+    "msp_effective_dimension": (C.c_int, [P, P, I64, I64, C.c_double, I64, C.c_uint64, I64, C.c_int,
+                                          C.POINTER(MspOpts), C.POINTER(C.c_double), C.POINTER(C.c_double), P]),
     "msp_norm_lower_bound": (C.c_int, [P, P, C.c_int, I64, I64, C.POINTER(C.c_double)]),
     "msp_batch_create": (C.c_int, [P, C.c_int, C.POINTER(MspInstance), C.POINTER(P)]),
     "msp_batch_destroy": (None, [P]),

@@ -291,6 +291,23 @@ class Context:
         L.check(self.ptr, self.lib.msp_batch_create(self.ptr, len(instances), arr, C.byref(h)))
         return Batch(self, h, keep)
 
+    # -- effective dimension d_lambda by Hutchinson over batched solves
+    def effective_dimension(self, A: torch.Tensor, lam: float, s: int, probes: int = 64, gamma: int = 8,
+                            seed: int = DEFAULT_SEED, raise_on_noconv: bool = True,
+                            **opts) -> tuple[float, float, torch.Tensor]:
+        """(estimate of tr(A (A + lam I)^{-1}), standard error, per-probe values)."""
+        n, lda, dt = _check_matrix(A)
+        if dt != L.MSP_F32:
+            raise TypeError("effective_dimension needs an FP32 A")
+        o = make_opts(self.lib, **opts)
+        est, se = C.c_double(), C.c_double()
+        q = torch.empty(probes, dtype=torch.float64, device=self.device)
+        st = self.lib.msp_effective_dimension(self.ptr, _ptr(A), n, lda, float(lam), probes, seed, s, gamma,
+                                              C.byref(o), C.byref(est), C.byref(se), _ptr(q))
+        if st != 0 and not (st == 5 and not raise_on_noconv):
+            L.check(self.ptr, st)
+        return est.value, se.value, q
+
     # -- a10: Schatten-1 norm (PSD A) by Hutchinson
     def schatten(self, A: torch.Tensor, p: float = 1.0, probes: int = 256,
                  seed: int = DEFAULT_SEED) -> tuple[float, float]:

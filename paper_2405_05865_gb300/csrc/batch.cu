@@ -42,6 +42,8 @@
 #include "bulk.cuh"
 
 #include <algorithm>
+#include <map>
+#include <tuple>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -1342,6 +1344,7 @@ struct msp_batch_s {
     double last_tol = 0.0;
     int last_crit = 0;
     std::vector<int> by_n;      // instances, largest n first
+    std::vector<int> dup;       // first identical instance (shared set-up), or -1
     BInst* d_inst = nullptr;    // device copy of hinst
 };
 
@@ -1443,8 +1446,10 @@ msp_status set_units(msp_ctx* ctx, msp_batch_s* b, int ut) {
 }
 
 void destroy_parts(msp_batch_s* b) {
-    for (auto* f : b->f) msp_factor_destroy(f);
-    for (auto* s : b->sk) msp_sketch_destroy(s);
+    for (size_t k = 0; k < b->f.size(); ++k)
+        if (b->dup.empty() || b->dup[k] < 0) msp_factor_destroy(b->f[k]);
+    for (size_t k = 0; k < b->sk.size(); ++k)
+        if (b->dup.empty() || b->dup[k] < 0) msp_sketch_destroy(b->sk[k]);
     b->f.clear();
     b->sk.clear();
     if (b->mem) cudaFreeAsync(b->mem, b->stream);
@@ -1497,10 +1502,28 @@ msp_status msp_batch_create(msp_ctx* ctx, int count, const msp_instance* inst, m
         cudaEventDestroy(ev);
         return fail(msp_set_error(ctx, MSP_ECUDA, "batch: cudaEventRecord failed"));
     }
-    std::vector<int> order(count);
-    for (int k = 0; k < count; ++k) order[k] = k;
+    // instances that differ only in B / X / m share the sketch, the factor
+    // and the tiled copies of A and C (the same system with more right-hand
+    // sides than one instance holds)
+    b->dup.assign(count, -1);
+    {
+        std::map<std::tuple<const float*, int64_t, int64_t, double, double, int64_t, int, int64_t, int, uint64_t>,
+                 int> first;
+        for (int k = 0; k < count; ++k) {
+            const msp_instance& I = inst[k];
+            const auto key = std::make_tuple(I.A, I.n, I.lda, I.lambda, I.lambda0, I.s, I.gamma, I.phi,
+                                             I.gamma_phi, I.seed);
+            const auto it = first.find(key);
+            if (it == first.end()) first.emplace(key, k);
+            else b->dup[k] = it->second;
+        }
+    }
+    std::vector<int> order;
+    for (int k = 0; k < count; ++k)
+        if (b->dup[k] < 0) order.push_back(k);
     std::stable_sort(order.begin(), order.end(),
                      [&](int x, int y) { return inst[x].n * inst[x].s > inst[y].n * inst[y].s; });
+    const int nuniq = (int)order.size();
     std::atomic<int> next{0};
     std::atomic<int> bad{-1};
     std::vector<msp_status> lst(nl, MSP_OK);
@@ -1515,7 +1538,7 @@ msp_status msp_batch_create(msp_ctx* ctx, int count, const msp_instance* inst, m
         }
         while (bad.load() < 0) {
             const int j = next.fetch_add(1);
-            if (j >= count) break;
+            if (j >= nuniq) break;
             const int k = order[j];
             const msp_instance& I = inst[k];
             msp_sketch_t* sk = nullptr;
@@ -1551,6 +1574,11 @@ msp_status msp_batch_create(msp_ctx* ctx, int count, const msp_instance* inst, m
     }
     // handles are freed on the main stream from now on (worker work is complete)
     for (int k = 0; k < count; ++k) {
+        if (b->dup[k] >= 0) {
+            b->sk[k] = b->sk[b->dup[k]];
+            b->f[k] = b->f[b->dup[k]];
+            continue;
+        }
         b->sk[k]->stream = ctx->stream;
         b->f[k]->stream = ctx->stream;
     }
@@ -1582,7 +1610,7 @@ msp_status msp_batch_create(msp_ctx* ctx, int count, const msp_instance* inst, m
         ns += H.s_pad;
         nbt += H.nb;
         if (H.nkc > 1) nq += (int64_t)H.nkc * H.n_pad;
-        at += (int64_t)H.n_pad * H.n_pad;
+        if (b->dup[k] < 0) at += (int64_t)H.n_pad * H.n_pad;
     }
     if (nv * kM >= (1ll << 31) || nq * kM >= (1ll << 31) || nbt >= (1 << 30))
         return fail(msp_set_error(ctx, MSP_EINVAL, "batch: total size too large"));
@@ -1610,7 +1638,8 @@ msp_status msp_batch_create(msp_ctx* ctx, int count, const msp_instance* inst, m
     };
     const size_t o_at = take((size_t)at * 4);
     int64_t ct_total = 0;
-    for (const BInst& H : b->hinst) ct_total += (int64_t)H.n_pad * H.s_pad;
+    for (int k = 0; k < count; ++k)
+        if (b->dup[k] < 0) ct_total += (int64_t)b->hinst[k].n_pad * b->hinst[k].s_pad;
     const size_t o_ct = take((size_t)ct_total * 4);
     const size_t o_inst = take(sizeof(BInst) * cnt);
     const size_t o_rows = take(sizeof(int2) * b->rows.size());
@@ -1652,16 +1681,22 @@ msp_status msp_batch_create(msp_ctx* ctx, int count, const msp_instance* inst, m
     int64_t ta = 0, tc = 0;
     for (int k = 0; k < count; ++k) {
         BInst& H = b->hinst[k];
-        H.At = (const float*)(base + o_at) + ta;
-        H.Ct = (const float*)(base + o_ct) + tc;
-        tc += (int64_t)H.n_pad * H.s_pad;
-        ta += (int64_t)H.n_pad * H.n_pad;
+        if (b->dup[k] >= 0) {
+            H.At = b->hinst[b->dup[k]].At;
+            H.Ct = b->hinst[b->dup[k]].Ct;
+        } else {
+            H.At = (const float*)(base + o_at) + ta;
+            H.Ct = (const float*)(base + o_ct) + tc;
+            tc += (int64_t)H.n_pad * H.s_pad;
+            ta += (int64_t)H.n_pad * H.n_pad;
+        }
         H.C = (const float*)b->sk[k]->C;
         H.Bl = (const float*)b->f[k]->B;
         H.Bu = (const float*)b->f[k]->Bt;
     }
     // A -> tiles
     for (int k = 0; k < count; ++k) {
+        if (b->dup[k] >= 0) continue;
         const BInst& H = b->hinst[k];
         const int nk = H.n_pad / kKT;
         const int tiles = H.nb * nk;
@@ -1723,8 +1758,14 @@ msp_status msp_batch_create(msp_ctx* ctx, int count, const msp_instance* inst, m
     A.ctl = (BCtl*)(base + o_ctl);
     // L <= |A_k|_2 for the backward-error rule (one pass over each A)
     for (int k = 0; k < count; ++k) {
+        double* dst = (double*)(base + o_anorm) + k;
+        if (b->dup[k] >= 0) {
+            MSP_CUDA_TRY(ctx, cudaMemcpyAsync(dst, (double*)(base + o_anorm) + b->dup[k], 8,
+                                              cudaMemcpyDeviceToDevice, ctx->stream));
+            continue;
+        }
         const msp_status st = msp_norm_lb_launch(ctx, inst[k].A, MSP_F32, inst[k].n, inst[k].lda,
-                                                 (double*)(base + o_nwork), (double*)(base + o_anorm) + k);
+                                                 (double*)(base + o_nwork), dst);
         if (st != MSP_OK) return fail(st);
     }
     {

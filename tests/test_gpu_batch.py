@@ -275,3 +275,29 @@ def test_batch_unit_width(ctx):
         with pytest.raises(MspError):
             bt.autotune(bad)
     bt.close()
+
+
+def test_batch_shared_setup_matches_separate_copies(ctx):
+    """Instances naming one A (same sizes, lam, sketch parameters) share one
+    set-up; the result equals that of a batch given separate copies of A."""
+    K, B = _instance(777, 0.08, 16, 41, 128)
+    K2, B2 = _instance(450, 0.2, 7, 42, 64)
+    A = torch.from_numpy(K).cuda()
+    cols = [B[:, :16], B[:, 3:13], B[:, :5][:, ::-1]]
+    shared = [dict(A=A, B=torch.from_numpy(np.ascontiguousarray(c)).cuda(), lam=LAM, s=128) for c in cols]
+    shared.insert(1, dict(A=torch.from_numpy(K2).cuda(), B=torch.from_numpy(B2).cuda(), lam=LAM, s=64))
+    copies = [dict(d, A=d["A"].clone()) for d in shared]
+    bt_s, bt_c = ctx.batch(shared), ctx.batch(copies)
+    info_s = bt_s.solve(tol=1e-10, refine_tol=1e-6)
+    info_c = bt_c.solve(tol=1e-10, refine_tol=1e-6)
+    for k in range(len(shared)):
+        assert info_s[k]["status"] == 0
+        assert np.array_equal(bt_s.X(k).cpu().numpy(), bt_c.X(k).cpu().numpy())
+        assert info_s[k]["shift"] == info_c[k]["shift"]
+    for k in (0, 2, 3):
+        X = bt_s.X(k).cpu().numpy()
+        Bk = shared[k]["B"].cpu().numpy()
+        for j in range(X.shape[1]):
+            _check_column(K, Bk[:, j], X[:, j], LAM, 1e-10)
+    bt_s.close()
+    bt_c.close()

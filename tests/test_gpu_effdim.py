@@ -1,0 +1,70 @@
+"""Effective dimension d_lambda = tr(A (A + lam I)^{-1}) through
+msp_effective_dimension against the FP64 oracle.
+
+* per probe, the device value n - lam g^T x against the oracle's value on the
+  same Rademacher probes and the same (FP32-rounded) matrix, within the bound
+  the solve's backward error gives: with r = g - (A + lam I) x,
+  |lam g^T (x - x*)| <= |g| |r| and |r| <= tol ((L + lam) |x| + |g|);
+* the estimate within 5 standard errors of the closed form
+  sum_i sigma_i / (sigma_i + lam) over the eigenvalues of that matrix;
+* a probe count that is not a multiple of 16 (a ragged last instance).
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import effdim, hutchinson, reference
+from workloads import outlier_spectrum, spectrum_matrix
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2405_05865_gb300 import Context
+    c = Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def system():
+    n = 2048
+    A32 = spectrum_matrix(outlier_spectrum(n, 8), 7).astype(np.float32)
+    A64 = A32.astype(np.float64)
+    return A32, A64, np.linalg.eigvalsh(A64), reference.norm_lower_bound(A64)
+
+
+@pytest.mark.parametrize("m,seed", [(64, 11), (40, 12)])
+def test_effective_dimension(ctx, system, m, seed):
+    A32, A64, eig, L = system
+    n, lam = A32.shape[0], 1e-2
+    A = torch.from_numpy(A32).cuda()
+    est, se, q = ctx.effective_dimension(A, lam, s=256, probes=m, seed=seed, tol=TOL, refine_tol=1e-6,
+                                         criterion="backward")
+    q = q.cpu().numpy()
+    G = hutchinson.probes(n, m, seed)
+    X = reference.solve_dense(A64, G, lam)
+    ref = n - lam * np.einsum("ij,ij->j", G, X)
+    for j in range(m):
+        bound = np.sqrt(n) * TOL * ((L + lam) * np.linalg.norm(X[:, j]) + np.sqrt(n))
+        assert abs(q[j] - ref[j]) <= 1.01 * bound, (j, q[j], ref[j], bound)
+    o_est, o_se = effdim.estimate(A64, lam, G)
+    assert est == pytest.approx(float(q.mean()), rel=1e-14)
+    assert se == pytest.approx(float(q.std(ddof=1) / np.sqrt(m)), rel=1e-10)
+    assert abs(est - o_est) <= 1e-6 * o_est
+    assert se == pytest.approx(o_se, rel=1e-3)
+    exact = reference.effective_dimension(eig, lam)
+    assert abs(est - exact) <= 5 * se
+
+
+def test_effective_dimension_bad_arguments(ctx, system):
+    A = torch.from_numpy(system[0]).cuda()
+    with pytest.raises(Exception):
+        ctx.effective_dimension(A, 0.0, s=256, probes=16)
+    with pytest.raises(Exception):
+        ctx.effective_dimension(A, 1e-2, s=256, probes=1)
