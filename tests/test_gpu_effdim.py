@@ -8,6 +8,10 @@ msp_effective_dimension against the FP64 oracle.
 * the estimate within 5 standard errors of the closed form
   sum_i sigma_i / (sigma_i + lam) over the eigenvalues of that matrix;
 * a probe count that is not a multiple of 16 (a ragged last instance).
+
+The system is the kernel ridge regression one d_lambda is defined for
+(Section 3): an RBF kernel matrix, n = 2048, length scale 0.2, lam = 1e-2
+(d_lambda ~ 323), sketch size s = 768.
 """
 
 import numpy as np
@@ -15,8 +19,8 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+import workloads
 from oracle import effdim, hutchinson, reference
-from workloads import outlier_spectrum, spectrum_matrix
 
 pytestmark = pytest.mark.gpu
 
@@ -33,8 +37,7 @@ def ctx():
 
 @pytest.fixture(scope="module")
 def system():
-    n = 2048
-    A32 = spectrum_matrix(outlier_spectrum(n, 8), 7).astype(np.float32)
+    _, A32, _ = workloads.batch_instance(workloads.BatchSpec(2048, 0.2, 1e-2, 768, 1, 7))
     A64 = A32.astype(np.float64)
     return A32, A64, np.linalg.eigvalsh(A64), reference.norm_lower_bound(A64)
 
@@ -44,7 +47,7 @@ def test_effective_dimension(ctx, system, m, seed):
     A32, A64, eig, L = system
     n, lam = A32.shape[0], 1e-2
     A = torch.from_numpy(A32).cuda()
-    est, se, q = ctx.effective_dimension(A, lam, s=256, probes=m, seed=seed, tol=TOL, refine_tol=1e-6,
+    est, se, q = ctx.effective_dimension(A, lam, s=768, probes=m, seed=seed, tol=TOL, refine_tol=1e-6,
                                          criterion="backward")
     q = q.cpu().numpy()
     G = hutchinson.probes(n, m, seed)
