@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-schatten", action="store_true")
+    ap.add_argument("--no-effdim", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=5, help="level-1 iterations in the CPU sample")
     ap.add_argument("--batch-count", type=int, default=64, help="instances of the batched workload")
@@ -432,6 +433,30 @@ def run_msp(args, rank, world, local):
                "estimates_per_s": 1000.0 / sms, "tflops_fp32": flops / (sms * 1e-3) / 1e12,
                "probes": 256}
 
+    # effective dimension d_lambda = tr(K (K + lam I)^{-1}) of the same system
+    # by Hutchinson: 64 probes solved as one batch of 4 instances sharing one
+    # set-up (sketch, factor, tiled K); each estimate includes that set-up
+    edim = None
+    if not args.no_effdim:
+        eargs = dict(probes=64, tol=1e-10, refine_tol=args.batch_refine_tol, criterion="backward")
+        ctx.effective_dimension(A, lam, s, **eargs)
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        est = se = 0.0
+        nst = max(1, args.steps // 4)
+        for _ in range(nst):
+            est, se, _ = ctx.effective_dimension(A, lam, s, **eargs)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ems = e0.elapsed_time(e1) / nst
+        edim = {"estimate": est, "std_err": se, "probes": 64, "ms_per_estimate": ems,
+                "estimates_per_s": 1000.0 / ems, "probe_solves_per_s": 64e3 / ems,
+                "note": "each probe solved to normwise backward error 1e-10; the time includes "
+                        "the shared set-up (sketch, factor, tiled K) of every estimate"}
+
     # adjoint (the backward of x = (K_ell + lam I)^{-1} b for L = c^T x): the
     # forward solve, then a second solve with the cached factor, dL/dlam and
     # the fused dL/dell pair kernel; and that kernel alone
@@ -547,6 +572,7 @@ def run_msp(args, rank, world, local):
            "rel_resid_1e-10": strict,
            "fp32_plain": fp32,
            "schatten1": sch,
+           "effective_dimension": edim,
            "adjoint": adj,
            "batched": batched,
            "phase_ms_per_step": {"a_pass": g_ms / args.steps, "level2": l2_ms / args.steps,
