@@ -400,6 +400,40 @@ MSP_API msp_status msp_effective_dimension(msp_ctx* ctx, const float* A, int64_t
                                            int gamma, const msp_opts* opts, double* estimate,
                                            double* std_err, double* q);
 
+/* Sketch size and shift chosen from d_lambda (Section 3: l = 2 d_lambda in
+ * the kernel ridge regression corollary; Lemma 2.1):
+ *   l = ceil(2 d), so lambda_l <= lambda (Lemma 2.1(1), gamma = 1);
+ *   s = l rounded up to 16, capped at min(n, 1024) rounded down to 16
+ *       (`capped` = 1 when s < l);
+ *   lambda0 = 2 lambda d / s when s >= d: Lemma 2.1(2) bounds
+ *       sum_{i > s} lambda_i by lambda d, so this is an upper bound of the
+ *       paper's (2/s) sum_{i > s} lambda_i and lambda0 <= lambda;
+ *       lambda0 = 0 when s < d (the lemma gives nothing there);
+ *   direct = 1 when d >= n/4 (the paper then inverts A + lambda I directly).
+ * d_std_err is the estimate's standard error (0 from msp_params_from_effdim). */
+typedef struct {
+    double d_lambda;
+    double d_std_err;
+    int64_t l;
+    int64_t s;
+    double lambda0;
+    int capped;
+    int direct;
+} msp_param_choice;
+
+/* The rule above for a given d (host only, no GPU work). MSP_EINVAL unless
+ * d >= 0 finite, n >= 16, lambda > 0, out != NULL. */
+MSP_API msp_status msp_params_from_effdim(double d, int64_t n, double lambda, msp_param_choice* out);
+
+/* Estimate d_lambda (msp_effective_dimension with the largest sketch,
+ * s = min(n, 1024) rounded down to 16, lambda0 = 0) and apply the rule to the
+ * estimate clamped to [0, n]. Arguments as for msp_effective_dimension;
+ * errors: those of msp_effective_dimension (a solve that hit its caps is an
+ * error here: MSP_ENOCONV). */
+MSP_API msp_status msp_auto_params(msp_ctx* ctx, const float* A, int64_t n, int64_t lda, double lambda,
+                                   int64_t probes, uint64_t seed, int gamma, const msp_opts* opts,
+                                   msp_param_choice* out);
+
 /* ------------------------------------------------- a11: RBF and adjoint */
 
 /* The Gaussian (RBF) kernel matrix of kernel ridge regression (Section 3,

@@ -39,3 +39,28 @@ def variance_one_probe(A: np.ndarray, lam: float) -> float:
     A = np.asarray(A, dtype=np.float64)
     B = lam * np.linalg.inv(A + lam * np.eye(A.shape[0]))
     return float(2.0 * (np.sum(B * B) - np.sum(np.diag(B) ** 2)))
+
+
+def params_from_effdim(d: float, n: int, lam: float, s_cap: int = 1024) -> dict:
+    """Sketch size and shift from d_lambda, as Section 3 and Lemma 2.1 give them.
+
+    * l = 2 d_lambda (the KRR corollary's choice), taken as the integer
+      ceiling; Lemma 2.1(1) with gamma = 1 then gives lambda_l <= lambda.
+    * s = l, rounded up to a multiple of 16 (the library's tile), but no
+      larger than min(n, s_cap) rounded down to a multiple of 16, and no
+      smaller than 16. ``capped`` records s < l.
+    * lambda0: the paper's shift is (2/s) sum_{i>s} lambda_i. For s >= d,
+      Lemma 2.1(2) bounds the tail sum by lambda d, so 2 lambda d / s is an
+      upper bound of that shift computable from d alone; below d the lemma
+      gives no bound and the shift is 0.
+    * direct: d >= n/4, where the paper inverts A + lambda I directly.
+    """
+    if not (d >= 0.0 and np.isfinite(d)) or n < 16 or not lam > 0.0:
+        raise ValueError("need d >= 0 finite, n >= 16, lam > 0")
+    l = max(1, int(np.ceil(2.0 * d)))
+    top = (min(n, s_cap) // 16) * 16
+    s = min(top, -(-l // 16) * 16)
+    s = max(16, s)
+    lam0 = 2.0 * lam * d / s if s >= d else 0.0
+    return {"d_lambda": float(d), "l": l, "s": s, "lambda0": lam0, "capped": int(s < l),
+            "direct": int(4.0 * d >= n)}

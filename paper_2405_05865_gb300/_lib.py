@@ -49,6 +49,15 @@ class MspInstance(C.Structure):
                 ("phi", C.c_int64), ("gamma_phi", C.c_int), ("pad_", C.c_int), ("seed", C.c_uint64)]
 
 
+class MspAutoParams(C.Structure):
+    """Sketch size and shift chosen from d_lambda (msp_auto_params)."""
+    _fields_ = [("d_lambda", C.c_double), ("d_std_err", C.c_double), ("l", C.c_int64), ("s", C.c_int64),
+                ("lambda0", C.c_double), ("capped", C.c_int), ("direct", C.c_int)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class MspError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -83,6 +92,9 @@ _SIGS = {
                                  C.POINTER(MspInfo)]),
     "msp_matvec_f64": (C.c_int, [P, P, C.c_int, I64, I64, C.c_double, P, P]),
     "msp_dot": (C.c_int, [P, P, P, I64, C.c_double, P]),
+    "msp_params_from_effdim": (C.c_int, [C.c_double, I64, C.c_double, C.POINTER(MspAutoParams)]),
+    "msp_auto_params": (C.c_int, [P, P, I64, I64, C.c_double, I64, C.c_uint64, C.c_int, C.POINTER(MspOpts),
+                                  C.POINTER(MspAutoParams)]),
     "msp_effective_dimension": (C.c_int, [P, P, I64, I64, C.c_double, I64, C.c_uint64, I64, C.c_int,
                                           C.POINTER(MspOpts), C.POINTER(C.c_double), C.POINTER(C.c_double), P]),
     "msp_norm_lower_bound": (C.c_int, [P, P, C.c_int, I64, I64, C.POINTER(C.c_double)]),

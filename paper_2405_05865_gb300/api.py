@@ -54,6 +54,17 @@ def _check_matrix(A: torch.Tensor, need_cuda: bool = True) -> tuple[int, int, in
     return A.shape[0], A.stride(0), _DT[A.dtype]
 
 
+def params_from_effdim(d: float, n: int, lam: float) -> dict:
+    """The library's rule from d_lambda to (l, s, lambda0, capped, direct);
+    host only (msp_params_from_effdim)."""
+    lib = L.load()
+    out = L.MspAutoParams()
+    st = lib.msp_params_from_effdim(float(d), int(n), float(lam), C.byref(out))
+    if st != 0:
+        raise L.MspError(st, "params_from_effdim: invalid arguments")
+    return out.as_dict()
+
+
 class Sketch:
     def __init__(self, ctx: "Context", handle: C.c_void_p, n: int, s: int, dtype: torch.dtype):
         self.ctx, self.handle, self.n, self.s, self.dtype = ctx, handle, n, s, dtype
@@ -307,6 +318,18 @@ class Context:
         if st != 0 and not (st == 5 and not raise_on_noconv):
             L.check(self.ptr, st)
         return est.value, se.value, q
+
+    def auto_params(self, A: torch.Tensor, lam: float, probes: int = 64, gamma: int = 8,
+                    seed: int = DEFAULT_SEED, **opts) -> dict:
+        """Sketch size s ~ 2 d_lambda and shift lambda0 from a d_lambda estimate."""
+        n, lda, dt = _check_matrix(A)
+        if dt != L.MSP_F32:
+            raise TypeError("auto_params needs an FP32 A")
+        o = make_opts(self.lib, **opts)
+        out = L.MspAutoParams()
+        L.check(self.ptr, self.lib.msp_auto_params(self.ptr, _ptr(A), n, lda, float(lam), probes, seed, gamma,
+                                                    C.byref(o), C.byref(out)))
+        return out.as_dict()
 
     # -- a10: Schatten-1 norm (PSD A) by Hutchinson
     def schatten(self, A: torch.Tensor, p: float = 1.0, probes: int = 256,

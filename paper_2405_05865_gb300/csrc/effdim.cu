@@ -116,3 +116,46 @@ extern "C" msp_status msp_effective_dimension(msp_ctx* ctx, const float* A, int6
     if (std_err) *std_err = std::sqrt(var / (double)m);
     return done(sst);
 }
+
+// Parameters from d_lambda (Section 3, the proof of the KRR corollary, and
+// Lemma 2.1): l = ceil(2 d), for which lambda_l <= lambda (Lemma 2.1(1) with
+// gamma = 1); s = l rounded up to 16 and capped at the largest sketch the
+// library builds; lambda0 = 2 lambda d / s, which bounds the paper's
+// (2/s) sum_{i > s} lambda_i from above when s >= d (Lemma 2.1(2)); with the
+// cap below that (s < d) the lemma says nothing and lambda0 = 0 (plain
+// Nystrom preconditioner M = A_nys + lambda I). d >= n/4 marks the regime
+// where the paper solves directly.
+extern "C" msp_status msp_params_from_effdim(double d, int64_t n, double lambda, msp_param_choice* out) {
+    if (!out || !(d >= 0.0) || !std::isfinite(d) || n < 16 || !(lambda > 0.0)) return MSP_EINVAL;
+    const int64_t s_max = std::min<int64_t>(n, 1024) / 16 * 16;
+    const int64_t l = std::max<int64_t>(1, (int64_t)std::ceil(2.0 * d));
+    const int64_t s = std::max<int64_t>(16, std::min<int64_t>(s_max, (l + 15) / 16 * 16));
+    out->d_lambda = d;
+    out->l = l;
+    out->s = s;
+    out->capped = s < l ? 1 : 0;
+    out->lambda0 = ((double)s >= d) ? 2.0 * lambda * d / (double)s : 0.0;
+    out->direct = (4.0 * d >= (double)n) ? 1 : 0;
+    return MSP_OK;
+}
+
+extern "C" msp_status msp_auto_params(msp_ctx* ctx, const float* A, int64_t n, int64_t lda, double lambda,
+                                      int64_t probes, uint64_t seed, int gamma, const msp_opts* opts,
+                                      msp_param_choice* out) {
+    if (!ctx) return msp_set_error(nullptr, MSP_EINVAL, "ctx is NULL");
+    if (!out) return msp_set_error(ctx, MSP_EINVAL, "auto_params: out is NULL");
+    if (n < 16) return msp_set_error(ctx, MSP_EINVAL, "auto_params: need n >= 16");
+    // pilot: the largest sketch, no shift
+    const int64_t s_pilot = std::min<int64_t>(n, 1024) / 16 * 16;
+    double d = 0.0, se = 0.0;
+    const msp_status st = msp_effective_dimension(ctx, A, n, lda, lambda, probes, seed, s_pilot, gamma, opts, &d,
+                                                  &se, nullptr);
+    if (st != MSP_OK) return st;
+    // the estimate can leave [0, n] by its spread: clamp to the range of tr
+    const double dc = std::min<double>((double)n, std::max(0.0, d));
+    if (msp_params_from_effdim(dc, n, lambda, out) != MSP_OK)
+        return msp_set_error(ctx, MSP_EINVAL, "auto_params: bad estimate %g", d);
+    out->d_lambda = d;
+    out->d_std_err = se;
+    return MSP_OK;
+}

@@ -71,3 +71,30 @@ def test_effective_dimension_bad_arguments(ctx, system):
         ctx.effective_dimension(A, 0.0, s=256, probes=16)
     with pytest.raises(Exception):
         ctx.effective_dimension(A, 1e-2, s=256, probes=1)
+
+
+def test_auto_params_then_solve(ctx, system):
+    """msp_auto_params: the estimate is within 5 standard errors of the
+    closed form, the chosen (l, s, lambda0) are the oracle's rule applied to
+    that estimate, and the system solves with them to backward error 1e-10."""
+    A32, A64, eig, L = system
+    n, lam = A32.shape[0], 1e-2
+    A = torch.from_numpy(A32).cuda()
+    p = ctx.auto_params(A, lam, probes=64, seed=5, tol=TOL, refine_tol=1e-6, criterion="backward")
+    exact = reference.effective_dimension(eig, lam)
+    assert abs(p["d_lambda"] - exact) <= 5 * p["d_std_err"]
+    want = effdim.params_from_effdim(min(float(n), max(0.0, p["d_lambda"])), n, lam)
+    for key in ("l", "s", "capped", "direct"):
+        assert p[key] == want[key], key
+    assert p["lambda0"] == want["lambda0"]
+    assert 0.0 < p["lambda0"] <= lam and not p["capped"]
+    b = np.random.default_rng(9).standard_normal(n)
+    sk = ctx.sketch(A, s=p["s"])
+    f = ctx.nystrom(sk, lam=lam, lam0=p["lambda0"], phi=0)
+    x, info = ctx.solve(f, A, torch.from_numpy(b).cuda(), lam=lam, max_inner=0, criterion="backward", tol=TOL)
+    f.close()
+    sk.close()
+    x = x.cpu().numpy()
+    r = b - (A64 @ x + lam * x)
+    assert info["status"] == 0
+    assert np.linalg.norm(r) <= TOL * ((L + lam) * np.linalg.norm(x) + np.linalg.norm(b))
