@@ -24,5 +24,8 @@ Modules
 ``adjoint``   gradients of L = g^T x, x = (K_theta + lam I)^{-1} b
 ``batch``     batches of instances with several right-hand sides each: the
               definition (independent per-column solves) as a loop
-``effdim``    effective dimension d_lambda by Hutchinson over regularised solves
+``effdim``    effective dimension d_lambda by Hutchinson over regularised solves,
+              and the sketch size / shift rule built on it (Lemma 2.1)
+``general``   three-level MSP for (A^T A + lam I) x = c, A rectangular:
+              Algorithm 3 with SolveM1 (Algorithm 4) and SolveM2 (Algorithm 5)
 """

@@ -20,4 +20,6 @@ from .generators import (  # noqa: F401
     BatchSpec,
     batch_specs,
     batch_instance,
+    svd_matrix,
+    tall_matrix,
 )

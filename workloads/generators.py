@@ -12,6 +12,9 @@ its two workload shapes:
   shape of Problem 1.1.
 * ``rbf_kernel``: a Gaussian (RBF) kernel matrix on uniform points in [0,1]^3 --
   the kernel ridge regression shape (K + lambda I) x = y.
+* ``svd_matrix`` / ``tall_matrix``: rectangular m x n matrices with a few
+  large singular values over a flat tail -- the general
+  (A^T A + lambda I) x = c shape of the main technical result (Section 3).
 
 Rounding to the storage precision (FP32 or BF16) is the caller's business; the
 generated FP64 values are the definition of the problem.
@@ -83,6 +86,35 @@ def householder_matrix(sigma: np.ndarray, seed: int, reflectors: int = 64) -> np
         vA = v @ A
         A = A - beta * np.outer(vA, v)          # (H A) H
     return 0.5 * (A + A.T)
+
+
+def svd_matrix(m: int, n: int, sigma: np.ndarray, seed: int) -> np.ndarray:
+    """A = U diag(sigma) V^T (m x n, m >= n) with U, V the orthogonal factors
+    (numpy.linalg.qr) of seeded N(0,1) m x n and n x n matrices: exactly the
+    singular values sigma. For the general (A^T A + lambda I) systems."""
+    if m < n or sigma.shape[0] != n:
+        raise ValueError("need m >= n and n singular values")
+    r = _rng(seed, _TAG_MATRIX)
+    U, _ = np.linalg.qr(r.standard_normal((m, n)))
+    V, _ = np.linalg.qr(r.standard_normal((n, n)))
+    return (U * sigma[None, :]) @ V.T
+
+
+def tall_matrix(m: int, n: int, d: np.ndarray, seed: int, out_dtype=np.float32,
+                chunk: int = 8192) -> np.ndarray:
+    """A = G diag(d) / sqrt(m) with G seeded N(0,1) (m x n), drawn row chunk by
+    row chunk in FP64 and rounded once to ``out_dtype``. For m >> n the
+    singular values are d_i (1 + O(sqrt(n/m))): the large-size stand-in for
+    ``svd_matrix`` (no QR of an m x n matrix)."""
+    if d.shape[0] != n:
+        raise ValueError("need n column scales")
+    r = _rng(seed, _TAG_MATRIX)
+    A = np.empty((m, n), dtype=out_dtype)
+    scale = d[None, :] / math.sqrt(m)
+    for i in range(0, m, chunk):
+        rows = min(chunk, m - i)
+        A[i:i + rows] = (r.standard_normal((rows, n)) * scale).astype(out_dtype)
+    return A
 
 
 def rbf_points(n: int, seed: int, dim: int = 3) -> np.ndarray:
