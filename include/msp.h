@@ -106,6 +106,11 @@ typedef struct {
     int criterion;        /* stopping rule of the solve (the last refinement
                              step in MSP_PREC_MIXED), msp_criterion. Default
                              MSP_STOP_RESIDUAL.                                  */
+    int level2_iters;     /* msp_general_solve only: PCG steps of the level-2
+                             solve in each SolveM1 (Algorithm 4). Default 8.     */
+    int level3_iters;     /* msp_general_solve only: PCG steps of each of the
+                             two level-3 solves in SolveM2 (Algorithm 5).
+                             Default 8.                                          */
 } msp_opts;
 
 /* Stopping rules.
@@ -433,6 +438,62 @@ MSP_API msp_status msp_params_from_effdim(double d, int64_t n, double lambda, ms
 MSP_API msp_status msp_auto_params(msp_ctx* ctx, const float* A, int64_t n, int64_t lda, double lambda,
                                    int64_t probes, uint64_t seed, int gamma, const msp_opts* opts,
                                    msp_param_choice* out);
+
+/* -------------------------- three-level MSP for (A^T A + lambda I) x = c */
+
+/* Section 5 (the main technical result, Theorem 3.1): A is m x n, m >= n,
+ * full column rank, FP32 row-major on the device (lda >= n; rows whose start
+ * is not 16-byte aligned, or odd n, are copied once into a padded layout).
+ * msp_general_create runs Algorithm 3 steps 2-6: lambda~ = lambda + lambda0,
+ * S (s x n, gamma nonzeros per column, the streams of msp_sketch with `seed`),
+ * A~ = A S^T (m x s), A^ = Phi A~ with Phi a phi x m sparse embedding
+ * (gamma_phi nonzeros per column, the level-2 streams), M3a = A^^T A^ and
+ * M3b = M3a + lambda~ I factored in FP64 (the FP32-data shift of msp_nystrom)
+ * and kept as dense FP32 inverses. A is read again by every solve and must
+ * stay valid and unchanged for the life of the handle (unless it was copied).
+ * Requires 16 <= n <= 8192, n <= m < 2^31, lambda >= 0, lambda0 >= 0 with
+ * lambda + lambda0 > 0 (SolveM1 divides by lambda~), 16 <= s <= min(n, 1024),
+ * s <= phi <= m. Errors: MSP_EINVAL, MSP_ENOMEM, MSP_ENOTPD (a level-3 Gram
+ * not positive definite after the shift retries), MSP_ECUDA. */
+typedef struct msp_general_s msp_general_t;
+MSP_API msp_status msp_general_create(msp_ctx* ctx, const float* A, int64_t m, int64_t n, int64_t lda,
+                                      double lambda, double lambda0, int64_t s, int gamma, int64_t phi,
+                                      int gamma_phi, uint64_t seed, msp_general_t** out);
+MSP_API void msp_general_destroy(msp_general_t* g);
+/* s_pad (the padded sketch width), lambda~, and the stabilising shifts added
+ * to M3a and M3b (host scalars, each may be NULL). */
+MSP_API msp_status msp_general_info(const msp_general_t* g, int64_t* s_pad, double* lambda_tilde,
+                                    double* shift_a, double* shift_b);
+/* Copies of the set-up for tests (device buffers, each may be NULL): A~ as
+ * FP32 m x s row-major with leading dimension ld_at; M3a and M3b as FP64
+ * s x s row-major (before the shift). */
+MSP_API msp_status msp_general_get(msp_ctx* ctx, const msp_general_t* g, float* At, int64_t ld_at,
+                                   double* M3a, double* M3b);
+/* Solve (A^T A + lambda I) x = c by Algorithm 3 step 7: flexible PCG at
+ * level 1 with SolveM1 (Algorithm 4: opts.level2_iters flexible PCG steps on
+ * (A~^T A A^T A~ + lambda~ A~^T A~) y = A~^T A r, preconditioned by SolveM2,
+ * then w = (r - A^T A~ y) / lambda~), SolveM2 (Algorithm 5: opts.level3_iters
+ * PCG steps on A~^T A~ u = r and on (A~^T A~ + lambda~ I) v = r,
+ * preconditioned by M3a^{-1} and M3b^{-1}, then z = (u - v) / lambda~).
+ * Levels run in FP32 with FP64 dot products; MSP_PREC_MIXED wraps the solve
+ * in FP64 refinement (r = c - (A^T A + lambda I) x accumulated in FP64, each
+ * correction solved to opts.refine_tol). Stops at
+ * |c - (A^T A + lambda I) x| <= opts.tol |c| (MSP_STOP_RESIDUAL only).
+ * c, x: device FP64 vectors of length n. info (host, may be NULL): level-1
+ * iterations, level-2 iterations, refinement steps, final relative residual
+ * in FP64, lambda~. Errors: MSP_EINVAL (bad options), MSP_ENOCONV (x and info
+ * hold the last iterate), MSP_ENOTPD / MSP_ENONFINITE (a breakdown), MSP_ECUDA. */
+MSP_API msp_status msp_general_solve(msp_ctx* ctx, msp_general_t* g, const double* c, double* x,
+                                     const msp_opts* opts, msp_info* info);
+/* One application of SolveM1 (w ~ M^{-1} r, M = C W^{-1} C^T + lambda~ I,
+ * C = A^T A~, W = A~^T A~) with t2 level-2 and t3 level-3 steps, and one of
+ * SolveM2 (z ~ (W^2 + lambda~ W)^{-1} r) with t3 level-3 steps: device FP32
+ * vectors (r, w of length n; r, z of length s); for tests. */
+MSP_API msp_status msp_general_solve_m1(msp_ctx* ctx, msp_general_t* g, const float* r, float* w, int t2,
+                                        int t3);
+MSP_API msp_status msp_general_solve_m2(msp_ctx* ctx, msp_general_t* g, const float* r, float* z, int t3);
+/* y = (A^T A + lambda I) x with FP64 accumulation (device FP64, length n). */
+MSP_API msp_status msp_general_matvec64(msp_ctx* ctx, msp_general_t* g, const double* x, double* y);
 
 /* ------------------------------------------------- a11: RBF and adjoint */
 

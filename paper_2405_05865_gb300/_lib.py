@@ -26,7 +26,7 @@ class MspOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_outer", C.c_int), ("max_refine", C.c_int),
                 ("refine_tol", C.c_double), ("inner_tol", C.c_double), ("max_inner", C.c_int),
                 ("precision", C.c_int), ("check_every", C.c_int), ("profile", C.c_int),
-                ("criterion", C.c_int)]
+                ("criterion", C.c_int), ("level2_iters", C.c_int), ("level3_iters", C.c_int)]
 
 
 class MspInfo(C.Structure):
@@ -98,6 +98,16 @@ _SIGS = {
     "msp_effective_dimension": (C.c_int, [P, P, I64, I64, C.c_double, I64, C.c_uint64, I64, C.c_int,
                                           C.POINTER(MspOpts), C.POINTER(C.c_double), C.POINTER(C.c_double), P]),
     "msp_norm_lower_bound": (C.c_int, [P, P, C.c_int, I64, I64, C.POINTER(C.c_double)]),
+    "msp_general_create": (C.c_int, [P, P, I64, I64, I64, C.c_double, C.c_double, I64, C.c_int, I64, C.c_int,
+                                     C.c_uint64, C.POINTER(P)]),
+    "msp_general_destroy": (None, [P]),
+    "msp_general_info": (C.c_int, [P, C.POINTER(I64), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                   C.POINTER(C.c_double)]),
+    "msp_general_get": (C.c_int, [P, P, P, I64, P, P]),
+    "msp_general_solve": (C.c_int, [P, P, P, P, C.POINTER(MspOpts), C.POINTER(MspInfo)]),
+    "msp_general_solve_m1": (C.c_int, [P, P, P, P, C.c_int, C.c_int]),
+    "msp_general_solve_m2": (C.c_int, [P, P, P, P, C.c_int]),
+    "msp_general_matvec64": (C.c_int, [P, P, P, P]),
     "msp_batch_create": (C.c_int, [P, C.c_int, C.POINTER(MspInstance), C.POINTER(P)]),
     "msp_batch_destroy": (None, [P]),
     "msp_batch_solve": (C.c_int, [P, P, C.POINTER(MspOpts), C.POINTER(MspInfo)]),

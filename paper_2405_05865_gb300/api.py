@@ -175,6 +175,69 @@ class Batch:
             pass
 
 
+class General:
+    """Three-level MSP for (A^T A + lam I) x = c (msp_general_create). Keeps
+    the caller's A alive: the library reads it on every solve."""
+
+    def __init__(self, ctx: "Context", handle: C.c_void_p, A: torch.Tensor):
+        self.ctx, self.handle, self.A = ctx, handle, A
+        self.m, self.n = A.shape
+        sp, lt, sa, sb = L.I64(), C.c_double(), C.c_double(), C.c_double()
+        L.check(ctx.ptr, ctx.lib.msp_general_info(handle, C.byref(sp), C.byref(lt), C.byref(sa), C.byref(sb)))
+        self.s_pad, self.lambda_tilde, self.shift_a, self.shift_b = sp.value, lt.value, sa.value, sb.value
+
+    def solve(self, c: torch.Tensor, raise_on_noconv: bool = True, **opts) -> tuple[torch.Tensor, dict]:
+        if not c.is_cuda or c.dtype != torch.float64 or c.shape != (self.n,):
+            raise ValueError("c must be a CUDA float64 vector of length n")
+        c = c.contiguous()
+        x = torch.empty_like(c)
+        o = make_opts(self.ctx.lib, **opts)
+        info = L.MspInfo()
+        st = self.ctx.lib.msp_general_solve(self.ctx.ptr, self.handle, _ptr(c), _ptr(x), C.byref(o), C.byref(info))
+        if st != 0 and not (st == 5 and not raise_on_noconv):
+            L.check(self.ctx.ptr, st)
+        return x, info.as_dict()
+
+    def solve_m1(self, r: torch.Tensor, t2: int, t3: int) -> torch.Tensor:
+        r = r.to(torch.float32).contiguous()
+        w = torch.empty(self.n, dtype=torch.float32, device=r.device)
+        L.check(self.ctx.ptr, self.ctx.lib.msp_general_solve_m1(self.ctx.ptr, self.handle, _ptr(r), _ptr(w), t2, t3))
+        return w
+
+    def solve_m2(self, r: torch.Tensor, t3: int) -> torch.Tensor:
+        r = r.to(torch.float32).contiguous()
+        z = torch.empty(r.shape[0], dtype=torch.float32, device=r.device)
+        L.check(self.ctx.ptr, self.ctx.lib.msp_general_solve_m2(self.ctx.ptr, self.handle, _ptr(r), _ptr(z), t3))
+        return z
+
+    def matvec(self, x: torch.Tensor) -> torch.Tensor:
+        x = x.to(torch.float64).contiguous()
+        y = torch.empty_like(x)
+        L.check(self.ctx.ptr, self.ctx.lib.msp_general_matvec64(self.ctx.ptr, self.handle, _ptr(x), _ptr(y)))
+        return y
+
+    def setup(self, s: int) -> dict:
+        """A~ (m x s FP32) and the FP64 Grams M3a, M3b (s x s) as device tensors."""
+        dev = self.A.device
+        At = torch.empty((self.m, s), dtype=torch.float32, device=dev)
+        M3a = torch.empty((s, s), dtype=torch.float64, device=dev)
+        M3b = torch.empty_like(M3a)
+        L.check(self.ctx.ptr, self.ctx.lib.msp_general_get(self.ctx.ptr, self.handle, _ptr(At), s, _ptr(M3a),
+                                                           _ptr(M3b)))
+        return {"At": At, "M3a": M3a, "M3b": M3b}
+
+    def close(self) -> None:
+        if self.handle:
+            self.ctx.lib.msp_general_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Context:
     """An MSP context bound to one CUDA device and one stream."""
 
@@ -301,6 +364,18 @@ class Context:
         h = C.c_void_p()
         L.check(self.ptr, self.lib.msp_batch_create(self.ptr, len(instances), arr, C.byref(h)))
         return Batch(self, h, keep)
+
+    # -- three-level MSP for (A^T A + lam I) x = c
+    def general(self, A: torch.Tensor, lam: float, s: int, lam0: float = 0.0, phi: int | None = None,
+                gamma: int = 8, gamma_phi: int = 8, seed: int = DEFAULT_SEED) -> General:
+        if not A.is_cuda or A.dtype != torch.float32 or A.dim() != 2 or A.stride(1) != 1:
+            raise ValueError("A must be a CUDA float32 (m, n) tensor with unit column stride")
+        m, n = A.shape
+        h = C.c_void_p()
+        L.check(self.ptr, self.lib.msp_general_create(self.ptr, _ptr(A), m, n, A.stride(0), float(lam), float(lam0),
+                                                      s, gamma, phi if phi is not None else 4 * s, gamma_phi, seed,
+                                                      C.byref(h)))
+        return General(self, h, A)
 
     # -- effective dimension d_lambda by Hutchinson over batched solves
     def effective_dimension(self, A: torch.Tensor, lam: float, s: int, probes: int = 64, gamma: int = 8,

@@ -93,6 +93,8 @@ void msp_default_opts(msp_opts* o) {
     o->max_inner = 50;
     o->precision = MSP_PREC_MIXED;
     o->check_every = 8;
+    o->level2_iters = 8;
+    o->level3_iters = 8;
 }
 
 const char* msp_last_error(const msp_ctx* ctx) {

@@ -111,7 +111,8 @@ __global__ void __launch_bounds__(256, 4) k_gram(const TA* __restrict__ Ct, int6
         }
 }
 
-// M2 = sum_slices P + lam_t W (FP64, fixed order); pad rows/cols get identity.
+// M2 = sum_slices P + lam_t W (FP64, fixed order), or + lam_t I when W is
+// NULL; pad rows/cols get identity.
 template <typename TA>
 __global__ void k_gram_finish(const double* __restrict__ P, const TA* __restrict__ W, double lam_t,
                               int64_t s, int64_t s_pad, double* __restrict__ M2) {
@@ -123,7 +124,7 @@ __global__ void k_gram_finish(const double* __restrict__ P, const TA* __restrict
         v = 0.0;
 #pragma unroll
         for (int sl = 0; sl < kGramSlices; ++sl) v += P[(int64_t)sl * s_pad * s_pad + e];
-        v += lam_t * (double)W[e];
+        v += W ? lam_t * (double)W[e] : (a == b ? lam_t : 0.0);
     } else {
         v = (a == b) ? 1.0 : 0.0;
     }
@@ -362,6 +363,11 @@ __global__ void k_cast_tri(const double* __restrict__ X, T* __restrict__ B, T* _
     Bt[j * s_pad + i] = (T)v;
 }
 
+__global__ void k_cast_f32(const double* __restrict__ X, float* __restrict__ Y, int64_t len) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < len) Y[e] = (float)X[e];
+}
+
 template <int TS>
 void launch_dgemm_ts(msp_ctx* ctx, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha,
                      const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
@@ -428,6 +434,70 @@ msp_status chol_inv(msp_ctx* ctx, double* M, double* X, double* T1, double* T2, 
     return MSP_OK;
 }
 
+// Cholesky inverse of M + nu I (lower L^{-1} into Linv64), s_pad x s_pad
+// FP64 M with identity padding. FP32 data: M carries rounding errors of
+// about 2^-24 |M|_F (its operands are FP32), which leave it indefinite by
+// that much where it has tiny eigenvalues; nu starts there, which saves a
+// second factorisation. FP64 data: unshifted first, then s 2^-52 |M|_F.
+// Then nu x 100 per retry, at most 4 retries, else MSP_ENOTPD.
+msp_status factor_shifted(msp_ctx* ctx, const double* M, int64_t s, int64_t sp, bool fp32_data,
+                          double* Linv64, double* shift_out, int* retries_out) {
+    void* scr = nullptr;
+    size_t mat = (size_t)sp * sp * 8;
+    MSP_TRY(msp_scratch(ctx, 3 * mat + 2048, &scr));
+    double* Mw = (double*)scr;
+    double* T1 = Mw + sp * sp;
+    double* T2 = T1 + sp * sp;
+    int* fail = (int*)(T2 + sp * sp);
+    double* fro = (double*)(fail + 16);
+    double* fro_part = fro + 2;
+    int* hflag = (int*)ctx->host_flags;
+    auto fro_norm = [&](double* out) -> msp_status {
+        k_fro2_part<<<kFroBlocks, 256, 0, ctx->stream>>>(M, sp * sp, fro_part);
+        MSP_CHECK_LAUNCH(ctx);
+        k_fro2_final<<<1, 32, 0, ctx->stream>>>(fro_part, fro);
+        MSP_CHECK_LAUNCH(ctx);
+        double h = 0.0;
+        MSP_CUDA_TRY(ctx, cudaMemcpyAsync(&h, fro, 8, cudaMemcpyDeviceToHost, ctx->stream));
+        MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        *out = std::sqrt(h);
+        return MSP_OK;
+    };
+    double nu = 0.0;
+    if (fp32_data) {
+        double fn = 0.0;
+        MSP_TRY(fro_norm(&fn));
+        nu = std::ldexp(1.0, -24) * fn;
+    }
+    for (int attempt = 0; attempt <= 4; ++attempt) {
+        unsigned blocks = (unsigned)((sp * sp + 255) / 256);
+        k_copy_add_diag<<<blocks, 256, 0, ctx->stream>>>(M, Mw, sp, nu);
+        MSP_CHECK_LAUNCH(ctx);
+        MSP_CUDA_TRY(ctx, cudaMemsetAsync(Linv64, 0, mat, ctx->stream));
+        MSP_CUDA_TRY(ctx, cudaMemsetAsync(fail, 0, sizeof(int), ctx->stream));
+        MSP_TRY(chol_inv(ctx, Mw, Linv64, T1, T2, sp, 0, sp, fail));
+        MSP_CUDA_TRY(ctx, cudaMemcpyAsync(hflag, fail, sizeof(int), cudaMemcpyDeviceToHost,
+                                          ctx->stream));
+        MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        if (hflag[0] == 0) {
+            *shift_out = nu;
+            *retries_out = attempt;
+            return MSP_OK;
+        }
+        if (nu == 0.0) {
+            double fn = 0.0;
+            MSP_TRY(fro_norm(&fn));
+            nu = (fp32_data ? std::ldexp(1.0, -24) : (double)s * std::ldexp(1.0, -52)) * fn;
+            if (nu == 0.0) break;
+        } else {
+            nu *= 100.0;
+        }
+    }
+    return msp_set_error(ctx, MSP_ENOTPD,
+                         "matrix + shift is not positive definite after 4 retries (last shift %g)",
+                         nu / 100.0);
+}
+
 }  // namespace
 
 // Build W (symmetrised), M2, its shifted Cholesky inverse, and the working
@@ -466,73 +536,45 @@ msp_status msp_build_factor(msp_ctx* ctx, msp_factor_s* f, const void* Ct, int64
         }
         MSP_CHECK_LAUNCH(ctx);
     }
-    // factor with shift retries
-    void* scr = nullptr;
-    size_t mat = (size_t)sp * sp * 8;
-    MSP_TRY(msp_scratch(ctx, 3 * mat + 2048, &scr));
-    double* Mw = (double*)scr;
-    double* T1 = Mw + sp * sp;
-    double* T2 = T1 + sp * sp;
-    int* fail = (int*)(T2 + sp * sp);
-    double* fro = (double*)(fail + 16);
-    double* fro_part = fro + 2;
-    int* hflag = (int*)ctx->host_flags;
-    auto fro_norm = [&](double* out) -> msp_status {
-        k_fro2_part<<<kFroBlocks, 256, 0, ctx->stream>>>(f->M2, sp * sp, fro_part);
-        MSP_CHECK_LAUNCH(ctx);
-        k_fro2_final<<<1, 32, 0, ctx->stream>>>(fro_part, fro);
-        MSP_CHECK_LAUNCH(ctx);
-        double h = 0.0;
-        MSP_CUDA_TRY(ctx, cudaMemcpyAsync(&h, fro, 8, cudaMemcpyDeviceToHost, ctx->stream));
-        MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-        *out = std::sqrt(h);
-        return MSP_OK;
-    };
-    // FP32 data: M2 carries rounding errors of about 2^-24 |M2|_F (C and W are
-    // FP32), which leave it indefinite by that much where C^T C + lam~ W has
-    // tiny eigenvalues; shifting by that amount from the start saves a
-    // second factorisation. FP64 data: unshifted first.
-    double nu = 0.0;
-    if (f->dtype == MSP_F32) {
-        double fn = 0.0;
-        MSP_TRY(fro_norm(&fn));
-        nu = std::ldexp(1.0, -24) * fn;
-    }
-    for (int attempt = 0; attempt <= 4; ++attempt) {
-        unsigned blocks = (unsigned)((sp * sp + 255) / 256);
-        k_copy_add_diag<<<blocks, 256, 0, ctx->stream>>>(f->M2, Mw, sp, nu);
-        MSP_CHECK_LAUNCH(ctx);
-        MSP_CUDA_TRY(ctx, cudaMemsetAsync(f->Linv64, 0, mat, ctx->stream));
-        MSP_CUDA_TRY(ctx, cudaMemsetAsync(fail, 0, sizeof(int), ctx->stream));
-        MSP_TRY(chol_inv(ctx, Mw, f->Linv64, T1, T2, sp, 0, sp, fail));
-        MSP_CUDA_TRY(ctx, cudaMemcpyAsync(hflag, fail, sizeof(int), cudaMemcpyDeviceToHost,
-                                          ctx->stream));
-        MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-        if (hflag[0] == 0) {
-            f->shift = nu;
-            f->retries = attempt;
-            unsigned b2 = (unsigned)((sp * sp + 255) / 256);
-            if (f->dtype == MSP_F32)
-                k_cast_tri<float><<<b2, 256, 0, ctx->stream>>>(f->Linv64, (float*)f->B,
-                                                               (float*)f->Bt, sp);
-            else
-                k_cast_tri<double><<<b2, 256, 0, ctx->stream>>>(f->Linv64, (double*)f->B,
-                                                                (double*)f->Bt, sp);
-            MSP_CHECK_LAUNCH(ctx);
-            (void)ts;
-            return MSP_OK;
-        }
-        if (nu == 0.0) {
-            // first shift at the rounding level of the data M2 was assembled from
-            double fn = 0.0;
-            MSP_TRY(fro_norm(&fn));
-            nu = (f->dtype == MSP_F64 ? (double)f->s * std::ldexp(1.0, -52) : std::ldexp(1.0, -24)) * fn;
-            if (nu == 0.0) break;
-        } else {
-            nu *= 100.0;
-        }
-    }
-    return msp_set_error(ctx, MSP_ENOTPD,
-                         "M2 + shift is not positive definite after 4 retries (last shift %g)",
-                         nu / 100.0);
+    MSP_TRY(factor_shifted(ctx, f->M2, f->s, sp, f->dtype == MSP_F32, f->Linv64, &f->shift, &f->retries));
+    unsigned b2 = (unsigned)((sp * sp + 255) / 256);
+    if (f->dtype == MSP_F32)
+        k_cast_tri<float><<<b2, 256, 0, ctx->stream>>>(f->Linv64, (float*)f->B, (float*)f->Bt, sp);
+    else
+        k_cast_tri<double><<<b2, 256, 0, ctx->stream>>>(f->Linv64, (double*)f->B, (double*)f->Bt, sp);
+    MSP_CHECK_LAUNCH(ctx);
+    (void)ts;
+    return MSP_OK;
 }
+
+// Dense inverse of G + diag I with G = X^T X (X: rows x s_pad FP32 row-major,
+// pad columns zero): FP64 Gram (split-K, compensated), Cholesky with the
+// FP32-data shift rule, then G^{-1} = L^{-T} L^{-1} in FP64, cast to FP32
+// (full symmetric, pad block identity). G64 (optional) receives G + diag I
+// before the shift.
+msp_status msp_gram_inverse(msp_ctx* ctx, const float* X, int64_t rows, int64_t s, int64_t sp,
+                            double diag, double* G64, double* Linv64, float* Minv,
+                            double* shift, int* retries) {
+    {
+        void* scr = nullptr;
+        MSP_TRY(msp_scratch(ctx, (size_t)kGramSlices * sp * sp * 8, &scr));
+        double* P = (double*)scr;
+        const int nt = (int)(sp / 64);
+        dim3 grid((unsigned)(nt * (nt + 1) / 2), kGramSlices);
+        k_gram<float><<<grid, 256, 0, ctx->stream>>>(X, rows, sp, sp, P);
+        MSP_CHECK_LAUNCH(ctx);
+        k_gram_finish<float><<<(unsigned)((sp * sp + 255) / 256), 256, 0, ctx->stream>>>(
+            P, nullptr, diag, s, sp, G64);
+        MSP_CHECK_LAUNCH(ctx);
+    }
+    MSP_TRY(factor_shifted(ctx, G64, s, sp, true, Linv64, shift, retries));
+    // G^{-1} = X^T X with X = L^{-1} (lower); FP64 product into scratch
+    void* scr = nullptr;
+    MSP_TRY(msp_scratch(ctx, (size_t)sp * sp * 8, &scr));
+    double* Gi = (double*)scr;
+    MSP_TRY(dgemm(ctx, true, false, sp, sp, sp, 1.0, Linv64, sp, Linv64, sp, 0.0, Gi, sp));
+    k_cast_f32<<<(unsigned)((sp * sp + 255) / 256), 256, 0, ctx->stream>>>(Gi, Minv, sp * sp);
+    MSP_CHECK_LAUNCH(ctx);
+    return MSP_OK;
+}
+

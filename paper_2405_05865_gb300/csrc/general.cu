@@ -1,0 +1,993 @@
+// Three-level MSP for (A^T A + lambda I) x = c with A in R^{m x n} of full
+// column rank (Section 5): Algorithm 3 (set-up and the level-1 iteration),
+// Algorithm 4 (SolveM1, level 2) and Algorithm 5 (SolveM2, level 3).
+//
+// Every operator of every level is a pass over the rows of one or two
+// row-major FP32 matrices that share the row index (A, m x n, and
+// A~ = A S^T, m x s):
+//     t_r = X_r . a + beta z_r        (a row dot)
+//     out = sum_r t_r Y_r             (a row combination)
+// k_rowpass does both in one sweep: each CTA owns a contiguous range of rows,
+// its 8 warps take one row each for the dots, then all threads fold those 8
+// rows into per-CTA partial sums of Y^T t (the rows come back from L2); a
+// column sum finishes the partials in a fixed order. So:
+//     level 1  (A^T A + lam I) p            X = Y = A
+//     SolveM1  g = A~^T (A r)               X = A,  Y = A~
+//              v = A^T (A~ y), u = A~ y     X = A~, Y = A   (u kept)
+//              A~^T (A v + lam~ u)          X = A,  Y = A~  (z = u)
+//              w = (r - A^T (A~ y)) / lam~  X = A~, Y = A
+//     SolveM2  A~^T A~ p (+ lam~ p)         X = Y = A~
+// The inner levels run a fixed number of PCG steps (t2, t3) with all scalars
+// on the device, so one application of SolveM1 is a fixed launch sequence;
+// it is captured once into a CUDA graph and replayed per level-1 iteration.
+// The level-3 preconditioners M3a^{-1}, M3b^{-1} are dense s x s inverses of
+// the sketched Grams (FP64 Cholesky), applied by a dense mat-vec.
+#include "msp_internal.cuh"
+
+#include <cmath>
+#include <cstring>
+#include <new>
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kRows = 8;          // rows per CTA step: one per warp
+constexpr int kVecThreads = 1024; // single-block vector kernels
+constexpr int kMaxN = 8192;       // columns of A (register partials, vector kernels)
+
+struct Pcg {
+    double rz, pq, alpha, rr, beta, rzn, rzo, bb;
+};
+
+template <typename Acc>
+__device__ __forceinline__ Acc fma_acc(float x, Acc a, Acc t) {
+    return fma((Acc)x, a, t);
+}
+
+template <typename Acc>
+__device__ __forceinline__ Acc warp_sum_t(Acc v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename Acc, int NV, bool kSame>
+__global__ void __launch_bounds__(kThreads, 2) k_rowpass(
+    const float* __restrict__ X, int64_t ldx, int nx4, const float* __restrict__ Y, int64_t ldy,
+    int ny4, int64_t m, int64_t rows_per_cta, const Acc* __restrict__ a, const Acc* __restrict__ z,
+    Acc beta, Acc* __restrict__ tout, Acc* __restrict__ part, int64_t ldp) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Acc* sa = reinterpret_cast<Acc*>(smem_raw);
+    __shared__ Acc st[kRows];
+    for (int i = threadIdx.x; i < nx4 * 4; i += kThreads) sa[i] = a[i];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Acc acc[NV][4];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = Acc(0);
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
+    const int64_t r1 = min(m, r0 + rows_per_cta);
+    const float* Ys = kSame ? X : Y;
+    const int64_t ldys = kSame ? ldx : ldy;
+    __syncthreads();
+    for (int64_t g = r0; g < r1; g += kRows) {
+        const int64_t r = g + warp;
+        Acc t = Acc(0);
+        if (r < r1) {
+            const float4* xr = reinterpret_cast<const float4*>(X + r * ldx);
+#pragma unroll 8
+            for (int c = lane; c < nx4; c += 32) {
+                const float4 v = xr[c];
+                const Acc* ap = sa + 4 * c;
+                t = fma_acc(v.x, ap[0], t);
+                t = fma_acc(v.y, ap[1], t);
+                t = fma_acc(v.z, ap[2], t);
+                t = fma_acc(v.w, ap[3], t);
+            }
+        }
+        t = warp_sum_t(t);
+        if (lane == 0) {
+            Acc tv = Acc(0);
+            if (r < r1) {
+                tv = t + (z ? beta * z[r] : Acc(0));
+                if (tout) tout[r] = tv;
+            }
+            st[warp] = tv;
+        }
+        __syncthreads();
+        const int nr = (int)min((int64_t)kRows, r1 - g);
+#pragma unroll
+        for (int rr = 0; rr < kRows; ++rr) {
+            if (rr < nr) {
+                const Acc tr = st[rr];
+                const float4* yr = reinterpret_cast<const float4*>(Ys + (g + rr) * ldys);
+#pragma unroll
+                for (int k = 0; k < NV; ++k) {
+                    const int c = threadIdx.x + k * kThreads;
+                    if (c < ny4) {
+                        const float4 v = yr[c];
+                        acc[k][0] = fma_acc(v.x, tr, acc[k][0]);
+                        acc[k][1] = fma_acc(v.y, tr, acc[k][1]);
+                        acc[k][2] = fma_acc(v.z, tr, acc[k][2]);
+                        acc[k][3] = fma_acc(v.w, tr, acc[k][3]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    Acc* pp = part + (int64_t)blockIdx.x * ldp;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const int c = threadIdx.x + k * kThreads;
+        if (c < ny4) {
+            pp[4 * c + 0] = acc[k][0];
+            pp[4 * c + 1] = acc[k][1];
+            pp[4 * c + 2] = acc[k][2];
+            pp[4 * c + 3] = acc[k][3];
+        }
+    }
+}
+
+// out[j] = alpha sum_g part[g][j] + beta w[j] + v[j] (w, v optional), the
+// partials summed in FP64 in a fixed order. Block 32 x 8: 32 columns, the
+// G partial rows split over 8 thread rows, combined in a fixed order.
+template <typename Acc>
+__global__ void k_colsum(const Acc* __restrict__ part, int64_t ldp, int G, int ny, double alpha,
+                         const Acc* __restrict__ w, double beta, const Acc* __restrict__ v,
+                         Acc* __restrict__ out) {
+    __shared__ double red[8][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int j = blockIdx.x * 32 + tx;
+    double s = 0.0;
+    if (j < ny)
+        for (int g = ty; g < G; g += 8) s += (double)part[(int64_t)g * ldp + j];
+    red[ty][tx] = s;
+    __syncthreads();
+    if (ty == 0 && j < ny) {
+        double tot = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) tot += red[q][tx];
+        double o = alpha * tot;
+        if (w) o += beta * (double)w[j];
+        if (v) o += (double)v[j];
+        out[j] = (Acc)o;
+    }
+}
+
+// ------------------------------------------------- single-block vector steps
+
+__device__ double block_sum(double v, double* red) {
+    v = warp_sum_t(v);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+        red[32] = t;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+// x = 0, r = b, bb = b.b
+__global__ void k_pcg_init(int len, const float* __restrict__ b, float* __restrict__ x,
+                           float* __restrict__ r, Pcg* sc) {
+    __shared__ double red[33];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        const float v = b[i];
+        x[i] = 0.f;
+        r[i] = v;
+        s += (double)v * v;
+    }
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) {
+        sc->bb = s;
+        sc->rr = s;
+    }
+}
+
+// rz = r.z, p = z, zo = z
+__global__ void k_pcg_start(int len, const float* __restrict__ r, const float* __restrict__ z,
+                            float* __restrict__ p, float* __restrict__ zo, Pcg* sc) {
+    __shared__ double red[33];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        const float v = z[i];
+        p[i] = v;
+        zo[i] = v;
+        s += (double)r[i] * v;
+    }
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) sc->rz = s;
+}
+
+// pq = p.q; alpha = rz / pq (0 when the step is undefined); x += alpha p;
+// r -= alpha q; rr = r.r
+__global__ void k_pcg_step(int len, const float* __restrict__ p, const float* __restrict__ q,
+                           float* __restrict__ x, float* __restrict__ r, Pcg* sc, int* err) {
+    __shared__ double red[33];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) s += (double)p[i] * q[i];
+    const double pq = block_sum(s, red);
+    const double rz = sc->rz;
+    double alpha = 0.0;
+    if (pq > 0.0 && isfinite(pq) && isfinite(rz)) alpha = rz / pq;
+    else if (err && threadIdx.x == 0 && rz != 0.0) atomicCAS(err, 0, isfinite(pq) ? (int)MSP_ENOTPD : (int)MSP_ENONFINITE);
+    const float af = (float)alpha;
+    double s2 = 0.0;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        x[i] = fmaf(af, p[i], x[i]);
+        const float rv = fmaf(-af, q[i], r[i]);
+        r[i] = rv;
+        s2 += (double)rv * rv;
+    }
+    const double rr = block_sum(s2, red);
+    if (threadIdx.x == 0) {
+        sc->pq = pq;
+        sc->alpha = alpha;
+        sc->rr = rr;
+    }
+}
+
+// rzn = r.z; flexible: beta = (rzn - r.zo) / rz, else rzn / rz; p = z + beta p;
+// zo = z; rz = rzn
+__global__ void k_pcg_dir(int len, const float* __restrict__ r, const float* __restrict__ z,
+                          float* __restrict__ zo, float* __restrict__ p, Pcg* sc, int flexible) {
+    __shared__ double red[33];
+    double s1 = 0.0, s2 = 0.0;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        const double rv = r[i];
+        s1 += rv * z[i];
+        s2 += rv * zo[i];
+    }
+    const double rzn = block_sum(s1, red);
+    const double rzo = flexible ? block_sum(s2, red) : 0.0;
+    const double rz = sc->rz;
+    double beta = 0.0;
+    if (rz != 0.0 && isfinite(rz)) beta = (rzn - rzo) / rz;
+    if (!isfinite(beta)) beta = 0.0;
+    const float bf = (float)beta;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        const float zv = z[i];
+        p[i] = fmaf(bf, p[i], zv);
+        zo[i] = zv;
+    }
+    if (threadIdx.x == 0) {
+        sc->rzn = rzn;
+        sc->rzo = rzo;
+        sc->beta = beta;
+        sc->rz = rzn;
+    }
+}
+
+// out = M v for a dense s_pad x s_pad FP32 M (row-major), one warp per row,
+// FP64 accumulation
+__global__ void k_dense_mv(const float* __restrict__ M, const float* __restrict__ v, int sp,
+                           float* __restrict__ out) {
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= sp) return;
+    const float4* mr = reinterpret_cast<const float4*>(M + (int64_t)row * sp);
+    const float4* vv = reinterpret_cast<const float4*>(v);
+    double s = 0.0;
+    for (int c = lane; c < sp / 4; c += 32) {
+        const float4 a = mr[c], b = vv[c];
+        s += (double)a.x * b.x + (double)a.y * b.y + (double)a.z * b.z + (double)a.w * b.w;
+    }
+    s = warp_sum_t(s);
+    if (lane == 0) out[row] = (float)s;
+}
+
+// out = a x + b y
+__global__ void k_axpby(int len, float a, const float* __restrict__ x, float b,
+                        const float* __restrict__ y, float* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < len) out[i] = a * x[i] + b * y[i];
+}
+
+// ------------------------------------------------------ FP64 refinement
+
+__global__ void k_norm2_64(int len, const double* __restrict__ v, double* out) {
+    __shared__ double red[33];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < len; i += blockDim.x) s += v[i] * v[i];
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) *out = s;
+}
+
+__global__ void k_scale_to_f32(int len, const double* __restrict__ r, double inv, float* __restrict__ b) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < len) b[i] = (float)(r[i] * inv);
+}
+
+__global__ void k_axpy_64(int len, double a, const float* __restrict__ d, double* __restrict__ x) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < len) x[i] += a * (double)d[i];
+}
+
+__global__ void k_pad_copy_64(int len, int n, const double* __restrict__ src, double* __restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < len) dst[i] = (i < n) ? src[i] : 0.0;
+}
+
+__global__ void k_pad_copy_32(int len, int n, const float* __restrict__ src, float* __restrict__ dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < len) dst[i] = (i < n) ? src[i] : 0.f;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ the handle
+
+struct msp_general_s {
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int64_t m = 0, n = 0, n_pad = 0, lda = 0, s = 0, s_pad = 0, phi = 0;
+    int gamma = 0, gamma_phi = 0;
+    uint64_t seed = 0;
+    double lambda = 0, lambda0 = 0, lam_tilde = 0;
+    double shift_a = 0, shift_b = 0;
+    int retries_a = 0, retries_b = 0;
+    const float* A = nullptr;       // user's A, or A_copy
+    float* A_copy = nullptr;        // padded copy when the user's rows are not 16-byte aligned
+    float* At = nullptr;            // A~ = A S^T, m x s_pad
+    float* M3a = nullptr;           // (A^^T A^)^{-1}, s_pad x s_pad
+    float* M3b = nullptr;           // (A^^T A^ + lam~ I)^{-1}
+    double* G3a = nullptr;          // A^^T A^ (FP64, before the shift), for tests
+    double* G3b = nullptr;
+    double* Linv = nullptr;         // FP64 scratch for the factorisations
+    void* work = nullptr;
+    float *x1, *r1, *z1, *zo1, *p1, *q1, *b1;
+    float *g2, *y2, *r2, *z2, *zo2, *p2, *q2;
+    float *u3, *v3, *r3, *z3, *zo3, *p3, *q3;
+    float *tm, *vn, *part;
+    double *part64, *x64, *r64, *c64, *d64;
+    Pcg* sc = nullptr;              // [0] level 1, [1] level 2, [2] level 3
+    int* err = nullptr;
+    double* host = nullptr;         // pinned: 16 doubles
+    int G = 0;
+    int64_t rows_per_cta = 0;
+    cudaGraphExec_t m1_exec = nullptr;
+    int m1_t2 = -1, m1_t3 = -1;
+    int m1_kernels = 0;
+};
+
+namespace {
+
+using G_t = msp_general_s;
+
+template <typename Acc, bool kSame>
+msp_status launch_rowpass_nv(msp_ctx* ctx, G_t* g, const float* X, int64_t ldx, int nx4, const float* Y,
+                             int64_t ldy, int ny4, const Acc* a, const Acc* z, Acc beta, Acc* tout,
+                             Acc* part, int64_t ldp, int* count) {
+    const size_t smem = (size_t)nx4 * 4 * sizeof(Acc);
+    const int nv = (ny4 + kThreads - 1) / kThreads;
+#define MSP_RP(NVV)                                                                                     \
+    case NVV: {                                                                                         \
+        auto kern = k_rowpass<Acc, NVV, kSame>;                                                         \
+        kern<<<g->G, kThreads, smem, ctx->stream>>>(X, ldx, nx4, Y, ldy, ny4, g->m, g->rows_per_cta, a, \
+                                                    z, beta, tout, part, ldp);                          \
+        break;                                                                                          \
+    }
+    switch (nv <= 1 ? 1 : nv <= 2 ? 2 : nv <= 4 ? 4 : 8) {
+        MSP_RP(1)
+        MSP_RP(2)
+        MSP_RP(4)
+        MSP_RP(8)
+    }
+#undef MSP_RP
+    MSP_CHECK_LAUNCH(ctx);
+    if (count) ++*count;
+    return MSP_OK;
+}
+
+template <typename Acc>
+msp_status set_rowpass_attrs(msp_ctx* ctx, size_t smem) {
+#define MSP_RA(NVV)                                                                                        \
+    MSP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_rowpass<Acc, NVV, true>,                                     \
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));      \
+    MSP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_rowpass<Acc, NVV, false>,                                    \
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    MSP_RA(1)
+    MSP_RA(2)
+    MSP_RA(4)
+    MSP_RA(8)
+#undef MSP_RA
+    return MSP_OK;
+}
+
+// out = alpha (sum of the pass over the rows) + beta w + v
+template <typename Acc>
+msp_status colsum(msp_ctx* ctx, G_t* g, const Acc* part, int64_t ldp, int ny, double alpha, const Acc* w,
+                  double beta, const Acc* v, Acc* out, int* count) {
+    k_colsum<Acc><<<(unsigned)((ny + 31) / 32), 256, 0, ctx->stream>>>(part, ldp, g->G, ny, alpha, w, beta, v,
+                                                                      out);
+    MSP_CHECK_LAUNCH(ctx);
+    if (count) ++*count;
+    return MSP_OK;
+}
+
+// The levels' operators. `ld` of the partials is the widest vector (n_pad).
+struct Ops {
+    msp_ctx* ctx;
+    G_t* g;
+    int* count;
+    int64_t ldp() const { return g->n_pad; }
+    int na4() const { return (int)(g->n_pad / 4); }
+    int ns4() const { return (int)(g->s_pad / 4); }
+
+    // q = (A^T A + lam I) p  (level 1)
+    msp_status op1(const float* p, float* q) {
+        MSP_TRY((launch_rowpass_nv<float, true>(ctx, g, g->A, g->lda, na4(), g->A, g->lda, na4(), p, nullptr, 0.f,
+                                                nullptr, g->part, ldp(), count)));
+        return colsum<float>(ctx, g, g->part, ldp(), (int)g->n_pad, 1.0, p, g->lambda, nullptr, q, count);
+    }
+    // out = A~^T (A r)
+    msp_status sketch_rhs(const float* r, float* out) {
+        MSP_TRY((launch_rowpass_nv<float, false>(ctx, g, g->A, g->lda, na4(), g->At, g->s_pad, ns4(), r, nullptr,
+                                                 0.f, nullptr, g->part, ldp(), count)));
+        return colsum<float>(ctx, g, g->part, ldp(), (int)g->s_pad, 1.0, nullptr, 0.0, nullptr, out, count);
+    }
+    // q = (A~^T A A^T A~ + lam~ A~^T A~) y  (level 2)
+    msp_status op2(const float* y, float* q) {
+        MSP_TRY((launch_rowpass_nv<float, false>(ctx, g, g->At, g->s_pad, ns4(), g->A, g->lda, na4(), y, nullptr,
+                                                 0.f, g->tm, g->part, ldp(), count)));
+        MSP_TRY(colsum<float>(ctx, g, g->part, ldp(), (int)g->n_pad, 1.0, nullptr, 0.0, nullptr, g->vn, count));
+        MSP_TRY((launch_rowpass_nv<float, false>(ctx, g, g->A, g->lda, na4(), g->At, g->s_pad, ns4(), g->vn, g->tm,
+                                                 (float)g->lam_tilde, nullptr, g->part, ldp(), count)));
+        return colsum<float>(ctx, g, g->part, ldp(), (int)g->s_pad, 1.0, nullptr, 0.0, nullptr, q, count);
+    }
+    // w = (r - A^T (A~ y)) / lam~  (Algorithm 4 step 3)
+    msp_status finish_m1(const float* y, const float* r, float* w) {
+        MSP_TRY((launch_rowpass_nv<float, false>(ctx, g, g->At, g->s_pad, ns4(), g->A, g->lda, na4(), y, nullptr,
+                                                 0.f, nullptr, g->part, ldp(), count)));
+        const double il = 1.0 / g->lam_tilde;
+        return colsum<float>(ctx, g, g->part, ldp(), (int)g->n_pad, -il, r, il, nullptr, w, count);
+    }
+    // q = A~^T A~ p + shift p  (level 3)
+    msp_status op3(const float* p, float* q, double shift) {
+        MSP_TRY((launch_rowpass_nv<float, true>(ctx, g, g->At, g->s_pad, ns4(), g->At, g->s_pad, ns4(), p, nullptr,
+                                                0.f, nullptr, g->part, ldp(), count)));
+        return colsum<float>(ctx, g, g->part, ldp(), (int)g->s_pad, 1.0, p, shift, nullptr, q, count);
+    }
+    msp_status dense(const float* M, const float* v, float* out) {
+        const int sp = (int)g->s_pad;
+        k_dense_mv<<<(unsigned)((sp + 7) / 8), 256, 0, ctx->stream>>>(M, v, sp, out);
+        MSP_CHECK_LAUNCH(ctx);
+        if (count) ++*count;
+        return MSP_OK;
+    }
+    msp_status vec(int which, int len, const float* a0, const float* a1, float* a2, float* a3, Pcg* sc,
+                   int flexible = 0) {
+        switch (which) {
+            case 0: k_pcg_init<<<1, kVecThreads, 0, ctx->stream>>>(len, a0, a2, a3, sc); break;
+            case 1: k_pcg_start<<<1, kVecThreads, 0, ctx->stream>>>(len, a0, a1, a2, a3, sc); break;
+            case 2: k_pcg_step<<<1, kVecThreads, 0, ctx->stream>>>(len, a0, a1, a2, a3, sc, g->err); break;
+            default: k_pcg_dir<<<1, kVecThreads, 0, ctx->stream>>>(len, a0, a1, a2, a3, sc, flexible); break;
+        }
+        MSP_CHECK_LAUNCH(ctx);
+        if (count) ++*count;
+        return MSP_OK;
+    }
+
+    // t3 PCG steps on (A~^T A~ + shift I) x = b preconditioned by the dense Minv
+    msp_status level3(const float* b, float* x, const float* Minv, double shift, int t3) {
+        const int sp = (int)g->s_pad;
+        Pcg* sc = g->sc + 2;
+        MSP_TRY(vec(0, sp, b, nullptr, x, g->r3, sc));
+        MSP_TRY(dense(Minv, g->r3, g->z3));
+        MSP_TRY(vec(1, sp, g->r3, g->z3, g->p3, g->zo3, sc));
+        for (int k = 0; k < t3; ++k) {
+            MSP_TRY(op3(g->p3, g->q3, shift));
+            MSP_TRY(vec(2, sp, g->p3, g->q3, x, g->r3, sc));
+            if (k + 1 < t3) {
+                MSP_TRY(dense(Minv, g->r3, g->z3));
+                MSP_TRY(vec(3, sp, g->r3, g->z3, g->zo3, g->p3, sc, 0));
+            }
+        }
+        return MSP_OK;
+    }
+    // Algorithm 5: z = (u - v) / lam~
+    msp_status solve_m2(const float* r, float* z, int t3) {
+        MSP_TRY(level3(r, g->u3, g->M3a, 0.0, t3));
+        MSP_TRY(level3(r, g->v3, g->M3b, g->lam_tilde, t3));
+        const int sp = (int)g->s_pad;
+        const float il = (float)(1.0 / g->lam_tilde);
+        k_axpby<<<(unsigned)((sp + 255) / 256), 256, 0, ctx->stream>>>(sp, il, g->u3, -il, g->v3, z);
+        MSP_CHECK_LAUNCH(ctx);
+        if (count) ++*count;
+        return MSP_OK;
+    }
+    // Algorithm 4: t2 flexible PCG steps on the level-2 system, SolveM2 as
+    // the preconditioner, then w = (r - A^T A~ y) / lam~
+    msp_status solve_m1(const float* r, float* w, int t2, int t3) {
+        const int sp = (int)g->s_pad;
+        Pcg* sc = g->sc + 1;
+        MSP_TRY(sketch_rhs(r, g->g2));
+        MSP_TRY(vec(0, sp, g->g2, nullptr, g->y2, g->r2, sc));
+        MSP_TRY(solve_m2(g->r2, g->z2, t3));
+        MSP_TRY(vec(1, sp, g->r2, g->z2, g->p2, g->zo2, sc));
+        for (int k = 0; k < t2; ++k) {
+            MSP_TRY(op2(g->p2, g->q2));
+            MSP_TRY(vec(2, sp, g->p2, g->q2, g->y2, g->r2, sc));
+            if (k + 1 < t2) {
+                MSP_TRY(solve_m2(g->r2, g->z2, t3));
+                MSP_TRY(vec(3, sp, g->r2, g->z2, g->zo2, g->p2, sc, 1));
+            }
+        }
+        return finish_m1(g->y2, r, w);
+    }
+};
+
+void destroy_general(G_t* g) {
+    if (!g) return;
+    if (g->m1_exec) cudaGraphExecDestroy(g->m1_exec);
+    cudaStream_t s = g->stream;
+    for (void* p : {(void*)g->A_copy, (void*)g->At, (void*)g->M3a, (void*)g->M3b, (void*)g->G3a, (void*)g->G3b,
+                    (void*)g->Linv, g->work})
+        if (p) cudaFreeAsync(p, s);
+    if (g->host) cudaFreeHost(g->host);
+    delete g;
+}
+
+// SolveM1 for the handle's (t2, t3) as a CUDA graph, rebuilt when they change
+msp_status ensure_m1_graph(msp_ctx* ctx, G_t* g, int t2, int t3) {
+    if (g->m1_exec && g->m1_t2 == t2 && g->m1_t3 == t3) return MSP_OK;
+    if (g->m1_exec) {
+        cudaGraphExecDestroy(g->m1_exec);
+        g->m1_exec = nullptr;
+    }
+    int count = 0;
+    Ops ops{ctx, g, &count};
+    MSP_CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    const int64_t l0 = ctx->launches;
+    msp_status st = ops.solve_m1(g->r1, g->z1, t2, t3);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+    ctx->launches = l0;   // counted per replay instead
+    if (st != MSP_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (ce != cudaSuccess || !graph) {
+        cudaGetLastError();
+        return msp_set_error(ctx, MSP_ECUDA, "general: SolveM1 capture failed: %s", cudaGetErrorString(ce));
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&g->m1_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+        cudaGetLastError();
+        g->m1_exec = nullptr;
+        return msp_set_error(ctx, MSP_ECUDA, "general: graph instantiation failed");
+    }
+    g->m1_t2 = t2;
+    g->m1_t3 = t3;
+    g->m1_kernels = count;
+    return MSP_OK;
+}
+
+msp_status run_m1(msp_ctx* ctx, G_t* g, int t2, int t3) {
+    MSP_TRY(ensure_m1_graph(ctx, g, t2, t3));
+    MSP_CUDA_TRY(ctx, cudaGraphLaunch(g->m1_exec, ctx->stream));
+    ctx->launches += g->m1_kernels;
+    return MSP_OK;
+}
+
+msp_status read_scalars(msp_ctx* ctx, G_t* g, const Pcg* sc, double* rr, double* bb) {
+    MSP_CUDA_TRY(ctx, cudaMemcpyAsync(g->host, sc, sizeof(Pcg), cudaMemcpyDeviceToHost, ctx->stream));
+    MSP_CUDA_TRY(ctx, cudaMemcpyAsync(g->host + 8, g->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    const Pcg* h = reinterpret_cast<const Pcg*>(g->host);
+    *rr = h->rr;
+    *bb = h->bb;
+    int e = 0;
+    std::memcpy(&e, g->host + 8, sizeof(int));
+    if (e != 0) return msp_set_error(ctx, (msp_status)e, "general: breakdown in an inner iteration (status %d)", e);
+    return MSP_OK;
+}
+
+// Level 1 (Algorithm 3 step 7): flexible PCG on (A^T A + lam I) x1 = b1 with
+// SolveM1, FP32 vectors; stops at |r| <= tol |b1| or after maxit steps.
+msp_status level1(msp_ctx* ctx, G_t* g, double tol, int maxit, int t2, int t3, int* iters, bool* conv,
+                  int* inner) {
+    Ops ops{ctx, g, nullptr};
+    const int len = (int)g->n_pad;
+    Pcg* sc = g->sc;
+    MSP_TRY(ops.vec(0, len, g->b1, nullptr, g->x1, g->r1, sc));
+    double rr = 0, bb = 0;
+    MSP_TRY(read_scalars(ctx, g, sc, &rr, &bb));
+    *iters = 0;
+    *conv = false;
+    if (bb == 0.0) {
+        *conv = true;
+        return MSP_OK;
+    }
+    MSP_TRY(run_m1(ctx, g, t2, t3));
+    *inner += t2;
+    MSP_TRY(ops.vec(1, len, g->r1, g->z1, g->p1, g->zo1, sc));
+    for (int k = 1; k <= maxit; ++k) {
+        MSP_TRY(ops.op1(g->p1, g->q1));
+        MSP_TRY(ops.vec(2, len, g->p1, g->q1, g->x1, g->r1, sc));
+        MSP_TRY(read_scalars(ctx, g, sc, &rr, &bb));
+        *iters = k;
+        if (!std::isfinite(rr)) return msp_set_error(ctx, MSP_ENONFINITE, "general: non-finite residual");
+        if (rr <= tol * tol * bb) {
+            *conv = true;
+            return MSP_OK;
+        }
+        if (k == maxit) break;
+        MSP_TRY(run_m1(ctx, g, t2, t3));
+        *inner += t2;
+        MSP_TRY(ops.vec(3, len, g->r1, g->z1, g->zo1, g->p1, sc, 1));
+    }
+    return MSP_OK;
+}
+
+// out = sgn (A^T A + lam I) x64 + v, FP64 accumulation
+msp_status apply64(msp_ctx* ctx, G_t* g, double sgn, const double* v, double* out) {
+    const int na4 = (int)(g->n_pad / 4);
+    MSP_TRY((launch_rowpass_nv<double, true>(ctx, g, g->A, g->lda, na4, g->A, g->lda, na4, g->x64, nullptr, 0.0,
+                                             nullptr, g->part64, g->n_pad, nullptr)));
+    return colsum<double>(ctx, g, g->part64, g->n_pad, (int)g->n_pad, sgn, g->x64, sgn * g->lambda, v, out,
+                          nullptr);
+}
+
+// r64 = c64 - (A^T A + lam I) x64
+msp_status residual64(msp_ctx* ctx, G_t* g) { return apply64(ctx, g, -1.0, g->c64, g->r64); }
+
+msp_status norm64(msp_ctx* ctx, G_t* g, const double* v, double* out) {
+    k_norm2_64<<<1, kVecThreads, 0, ctx->stream>>>((int)g->n_pad, v, g->d64);
+    MSP_CHECK_LAUNCH(ctx);
+    MSP_CUDA_TRY(ctx, cudaMemcpyAsync(g->host + 10, g->d64, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    *out = std::sqrt(g->host[10]);
+    return MSP_OK;
+}
+
+msp_status check_vec_args(msp_ctx* ctx, const void* p) {
+    if (!p) return msp_set_error(ctx, MSP_EINVAL, "general: NULL vector");
+    return MSP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+msp_status msp_general_create(msp_ctx* ctx, const float* A, int64_t m, int64_t n, int64_t lda, double lambda,
+                              double lambda0, int64_t s, int gamma, int64_t phi, int gamma_phi, uint64_t seed,
+                              msp_general_t** out) {
+    if (!ctx) return msp_set_error(nullptr, MSP_EINVAL, "ctx is NULL");
+    if (!A || !out) return msp_set_error(ctx, MSP_EINVAL, "general: NULL argument");
+    *out = nullptr;
+    if (n < 16 || n > kMaxN || m < n || m >= (1ll << 31) || lda < n || !(lambda >= 0.0) || !(lambda0 >= 0.0) ||
+        !(lambda + lambda0 > 0.0) || s < 16 || s > MSP_MAX_S || s > n || gamma < 1 || gamma > MSP_MAX_GAMMA ||
+        gamma > s || phi < s || phi > m || gamma_phi < 1 || gamma_phi > MSP_MAX_GAMMA || gamma_phi > phi)
+        return msp_set_error(ctx, MSP_EINVAL,
+                             "general: need 16 <= n <= %d, n <= m < 2^31, lda >= n, lambda, lambda0 >= 0 with "
+                             "lambda + lambda0 > 0, 16 <= s <= min(n, %d), 1 <= gamma <= min(s, %d), "
+                             "s <= phi <= m, 1 <= gamma_phi <= min(phi, %d)",
+                             kMaxN, MSP_MAX_S, MSP_MAX_GAMMA, MSP_MAX_GAMMA);
+    msp::DeviceGuard guard(ctx->device);
+    G_t* g = new (std::nothrow) G_t();
+    if (!g) return msp_set_error(ctx, MSP_ENOMEM, "general: host allocation failed");
+    g->stream = ctx->stream;
+    g->device = ctx->device;
+    g->m = m;
+    g->n = n;
+    g->n_pad = round_up(n, 4);
+    g->s = s;
+    g->s_pad = round_up(s, MSP_S_ALIGN);
+    g->phi = phi;
+    g->gamma = gamma;
+    g->gamma_phi = gamma_phi;
+    g->seed = seed;
+    g->lambda = lambda;
+    g->lambda0 = lambda0;
+    g->lam_tilde = lambda + lambda0;
+    auto fail = [&](msp_status st) {
+        cudaStreamSynchronize(ctx->stream);
+        destroy_general(g);
+        return st;
+    };
+    if (cudaMallocHost((void**)&g->host, 16 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        g->host = nullptr;
+        return fail(msp_set_error(ctx, MSP_ENOMEM, "general: pinned allocation failed"));
+    }
+    const int64_t np = g->n_pad, sp = g->s_pad;
+    // rows must start on 16-byte boundaries for the float4 row passes
+    const bool aligned = (lda % 4 == 0) && (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+    msp_status st = MSP_OK;
+    if (aligned) {
+        g->A = A;
+        g->lda = lda;
+    } else {
+        if ((st = msp_alloc(ctx, (void**)&g->A_copy, (size_t)m * np * 4)) != MSP_OK) return fail(st);
+        if (np != n && cudaMemsetAsync(g->A_copy, 0, (size_t)m * np * 4, ctx->stream) != cudaSuccess)
+            return fail(msp_set_error(ctx, MSP_ECUDA, "general: memset failed"));
+        if (cudaMemcpy2DAsync(g->A_copy, np * 4, A, lda * 4, n * 4, m, cudaMemcpyDeviceToDevice, ctx->stream) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return fail(msp_set_error(ctx, MSP_ECUDA, "general: copy of A failed"));
+        }
+        g->A = g->A_copy;
+        g->lda = np;
+    }
+    // rows per CTA step: 2 CTAs per SM
+    g->G = (int)std::min<int64_t>(2 * ctx->num_sms, (m + kRows - 1) / kRows);
+    g->rows_per_cta = round_up((m + g->G - 1) / g->G, kRows);
+    g->G = (int)((m + g->rows_per_cta - 1) / g->rows_per_cta);
+
+    // ---- Algorithm 3 steps 3-4: S, A~ = A S^T, A^ = Phi A~
+    {
+        int32_t *idx = nullptr, *ptr = nullptr, *ent = nullptr, *pptr = nullptr, *pent = nullptr;
+        int8_t *sgn = nullptr;
+        float* Ah = nullptr;
+        void* tmp = nullptr;
+        const size_t b_idx = (size_t)std::max<int64_t>(n * gamma, m * gamma_phi) * 4;
+        const size_t b_sgn = (size_t)std::max<int64_t>(n * gamma, m * gamma_phi);
+        const size_t b_ptr = (size_t)(std::max<int64_t>(sp, phi) + 1) * 4;
+        size_t off = 0;
+        auto take = [&](size_t b) { const size_t o = off; off += (size_t)round_up((int64_t)b, 256); return o; };
+        const size_t o_idx = take(b_idx), o_sgn = take(b_sgn), o_ptr = take(b_ptr), o_ent = take(b_idx);
+        const size_t o_ah = take((size_t)phi * sp * 4);
+        if ((st = msp_alloc(ctx, &tmp, off)) != MSP_OK) return fail(st);
+        char* tb = (char*)tmp;
+        idx = (int32_t*)(tb + o_idx);
+        sgn = (int8_t*)(tb + o_sgn);
+        ptr = (int32_t*)(tb + o_ptr);
+        ent = (int32_t*)(tb + o_ent);
+        pptr = ptr;
+        pent = ent;
+        Ah = (float*)(tb + o_ah);
+        auto tfail = [&](msp_status e) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFreeAsync(tmp, ctx->stream);
+            return fail(e);
+        };
+        if ((st = msp_alloc(ctx, (void**)&g->At, (size_t)m * sp * 4)) != MSP_OK) return tfail(st);
+        if ((st = msp_pattern_launch(ctx, n, s, gamma, seed, 0, idx, sgn, nullptr)) != MSP_OK ||
+            (st = msp_build_csr(ctx, n, sp, gamma, idx, sgn, ptr, ent)) != MSP_OK ||
+            (st = msp_sketch_apply_rows(ctx, g->A, MSP_F32, m, n, g->lda, sp, ptr, ent, gamma, g->At)) != MSP_OK)
+            return tfail(st);
+        // Phi (phi x m) on the level-2 streams; its rows gather rows of A~
+        if ((st = msp_pattern_launch(ctx, m, phi, gamma_phi, seed, 2, idx, sgn, nullptr)) != MSP_OK ||
+            (st = msp_build_csr(ctx, m, phi, gamma_phi, idx, sgn, pptr, pent)) != MSP_OK ||
+            (st = msp_gather_rows(ctx, MSP_F32, phi, sp, pptr, pent, g->At, sp, 1.0 / std::sqrt((double)gamma_phi),
+                                  Ah, sp)) != MSP_OK)
+            return tfail(st);
+        // ---- steps 5-6: M3a = A^^T A^, M3b = M3a + lam~ I and their inverses
+        const size_t mat = (size_t)sp * sp;
+        if ((st = msp_alloc(ctx, (void**)&g->M3a, mat * 4)) != MSP_OK ||
+            (st = msp_alloc(ctx, (void**)&g->M3b, mat * 4)) != MSP_OK ||
+            (st = msp_alloc(ctx, (void**)&g->G3a, mat * 8)) != MSP_OK ||
+            (st = msp_alloc(ctx, (void**)&g->G3b, mat * 8)) != MSP_OK ||
+            (st = msp_alloc(ctx, (void**)&g->Linv, mat * 8)) != MSP_OK)
+            return tfail(st);
+        if ((st = msp_gram_inverse(ctx, Ah, phi, s, sp, 0.0, g->G3a, g->Linv, g->M3a, &g->shift_a,
+                                   &g->retries_a)) != MSP_OK ||
+            (st = msp_gram_inverse(ctx, Ah, phi, s, sp, g->lam_tilde, g->G3b, g->Linv, g->M3b, &g->shift_b,
+                                   &g->retries_b)) != MSP_OK)
+            return tfail(st);
+        cudaFreeAsync(tmp, ctx->stream);
+    }
+    // ---- work vectors
+    {
+        size_t off = 0;
+        auto take = [&](size_t b) { const size_t o = off; off += (size_t)round_up((int64_t)b, 256); return o; };
+        size_t o1[7], o2[7], o3[7];
+        for (auto& o : o1) o = take((size_t)np * 4);
+        for (auto& o : o2) o = take((size_t)sp * 4);
+        for (auto& o : o3) o = take((size_t)sp * 4);
+        const size_t o_tm = take((size_t)m * 4), o_vn = take((size_t)np * 4);
+        const size_t o_part = take((size_t)g->G * np * 4);
+        const size_t o_p64 = take((size_t)g->G * np * 8);
+        const size_t o_x64 = take((size_t)np * 8), o_r64 = take((size_t)np * 8), o_c64 = take((size_t)np * 8);
+        const size_t o_d64 = take(64);
+        const size_t o_sc = take(sizeof(Pcg) * 3), o_err = take(16);
+        if ((st = msp_alloc(ctx, &g->work, off)) != MSP_OK) return fail(st);
+        if (cudaMemsetAsync(g->work, 0, off, ctx->stream) != cudaSuccess)
+            return fail(msp_set_error(ctx, MSP_ECUDA, "general: memset failed"));
+        char* w = (char*)g->work;
+        float** v1[7] = {&g->x1, &g->r1, &g->z1, &g->zo1, &g->p1, &g->q1, &g->b1};
+        float** v2[7] = {&g->g2, &g->y2, &g->r2, &g->z2, &g->zo2, &g->p2, &g->q2};
+        float** v3[7] = {&g->u3, &g->v3, &g->r3, &g->z3, &g->zo3, &g->p3, &g->q3};
+        for (int q = 0; q < 7; ++q) {
+            *v1[q] = (float*)(w + o1[q]);
+            *v2[q] = (float*)(w + o2[q]);
+            *v3[q] = (float*)(w + o3[q]);
+        }
+        g->tm = (float*)(w + o_tm);
+        g->vn = (float*)(w + o_vn);
+        g->part = (float*)(w + o_part);
+        g->part64 = (double*)(w + o_p64);
+        g->x64 = (double*)(w + o_x64);
+        g->r64 = (double*)(w + o_r64);
+        g->c64 = (double*)(w + o_c64);
+        g->d64 = (double*)(w + o_d64);
+        g->sc = (Pcg*)(w + o_sc);
+        g->err = (int*)(w + o_err);
+    }
+    if ((st = set_rowpass_attrs<float>(ctx, (size_t)np * 4)) != MSP_OK ||
+        (st = set_rowpass_attrs<double>(ctx, (size_t)np * 8)) != MSP_OK)
+        return fail(st);
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(msp_set_error(ctx, MSP_ECUDA, "general: set-up failed"));
+    }
+    *out = g;
+    return MSP_OK;
+}
+
+void msp_general_destroy(msp_general_t* g) {
+    if (!g) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(g->device);
+    cudaStreamSynchronize(g->stream);
+    destroy_general(g);
+    cudaSetDevice(prev);
+}
+
+msp_status msp_general_info(const msp_general_t* g, int64_t* s_pad, double* lambda_tilde, double* shift_a,
+                            double* shift_b) {
+    if (!g) return msp_set_error(nullptr, MSP_EINVAL, "general: handle is NULL");
+    if (s_pad) *s_pad = g->s_pad;
+    if (lambda_tilde) *lambda_tilde = g->lam_tilde;
+    if (shift_a) *shift_a = g->shift_a;
+    if (shift_b) *shift_b = g->shift_b;
+    return MSP_OK;
+}
+
+msp_status msp_general_get(msp_ctx* ctx, const msp_general_t* g, float* At, int64_t ld_at, double* M3a,
+                           double* M3b) {
+    if (!ctx || !g) return msp_set_error(ctx, MSP_EINVAL, "general: NULL argument");
+    msp::DeviceGuard guard(ctx->device);
+    const int64_t sp = g->s_pad;
+    if (At) {
+        if (ld_at < g->s) return msp_set_error(ctx, MSP_EINVAL, "general_get: ld_at < s");
+        MSP_CUDA_TRY(ctx, cudaMemcpy2DAsync(At, ld_at * 4, g->At, sp * 4, g->s * 4, g->m, cudaMemcpyDeviceToDevice,
+                                            ctx->stream));
+    }
+    if (M3a)
+        MSP_CUDA_TRY(ctx, cudaMemcpy2DAsync(M3a, g->s * 8, g->G3a, sp * 8, g->s * 8, g->s, cudaMemcpyDeviceToDevice,
+                                            ctx->stream));
+    if (M3b)
+        MSP_CUDA_TRY(ctx, cudaMemcpy2DAsync(M3b, g->s * 8, g->G3b, sp * 8, g->s * 8, g->s, cudaMemcpyDeviceToDevice,
+                                            ctx->stream));
+    return MSP_OK;
+}
+
+msp_status msp_general_solve_m2(msp_ctx* ctx, msp_general_t* g, const float* r, float* z, int t3) {
+    if (!ctx || !g) return msp_set_error(ctx, MSP_EINVAL, "general: NULL argument");
+    MSP_TRY(check_vec_args(ctx, r));
+    MSP_TRY(check_vec_args(ctx, z));
+    if (t3 < 1 || t3 > 1000) return msp_set_error(ctx, MSP_EINVAL, "general: need 1 <= t3 <= 1000");
+    msp::DeviceGuard guard(ctx->device);
+    const int sp = (int)g->s_pad;
+    k_pad_copy_32<<<(unsigned)((sp + 255) / 256), 256, 0, ctx->stream>>>(sp, (int)g->s, r, g->r2);
+    MSP_CHECK_LAUNCH(ctx);
+    Ops ops{ctx, g, nullptr};
+    MSP_TRY(ops.solve_m2(g->r2, g->z2, t3));
+    MSP_CUDA_TRY(ctx, cudaMemcpyAsync(z, g->z2, (size_t)g->s * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+    return MSP_OK;
+}
+
+msp_status msp_general_solve_m1(msp_ctx* ctx, msp_general_t* g, const float* r, float* w, int t2, int t3) {
+    if (!ctx || !g) return msp_set_error(ctx, MSP_EINVAL, "general: NULL argument");
+    MSP_TRY(check_vec_args(ctx, r));
+    MSP_TRY(check_vec_args(ctx, w));
+    if (t2 < 1 || t2 > 1000 || t3 < 1 || t3 > 1000)
+        return msp_set_error(ctx, MSP_EINVAL, "general: need 1 <= t2, t3 <= 1000");
+    msp::DeviceGuard guard(ctx->device);
+    const int np = (int)g->n_pad;
+    k_pad_copy_32<<<(unsigned)((np + 255) / 256), 256, 0, ctx->stream>>>(np, (int)g->n, r, g->r1);
+    MSP_CHECK_LAUNCH(ctx);
+    MSP_TRY(run_m1(ctx, g, t2, t3));
+    MSP_CUDA_TRY(ctx, cudaMemcpyAsync(w, g->z1, (size_t)g->n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+    return MSP_OK;
+}
+
+msp_status msp_general_matvec64(msp_ctx* ctx, msp_general_t* g, const double* x, double* y) {
+    if (!ctx || !g) return msp_set_error(ctx, MSP_EINVAL, "general: NULL argument");
+    MSP_TRY(check_vec_args(ctx, x));
+    MSP_TRY(check_vec_args(ctx, y));
+    msp::DeviceGuard guard(ctx->device);
+    const int np = (int)g->n_pad;
+    k_pad_copy_64<<<(unsigned)((np + 255) / 256), 256, 0, ctx->stream>>>(np, (int)g->n, x, g->x64);
+    MSP_CHECK_LAUNCH(ctx);
+    MSP_TRY(apply64(ctx, g, 1.0, nullptr, g->r64));
+    MSP_CUDA_TRY(ctx, cudaMemcpyAsync(y, g->r64, (size_t)g->n * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    return MSP_OK;
+}
+
+msp_status msp_general_solve(msp_ctx* ctx, msp_general_t* g, const double* c, double* x, const msp_opts* opts,
+                             msp_info* info) {
+    if (!ctx || !g) return msp_set_error(ctx, MSP_EINVAL, "general: NULL argument");
+    MSP_TRY(check_vec_args(ctx, c));
+    MSP_TRY(check_vec_args(ctx, x));
+    msp_opts o;
+    if (opts) o = *opts;
+    else msp_default_opts(&o);
+    if (!(o.tol > 0.0) || o.max_outer < 1 || o.level2_iters < 1 || o.level2_iters > 1000 || o.level3_iters < 1 ||
+        o.level3_iters > 1000 || (o.precision != MSP_PREC_MIXED && o.precision != MSP_PREC_FP32) ||
+        o.criterion != MSP_STOP_RESIDUAL || (o.precision == MSP_PREC_MIXED && !(o.refine_tol > 0.0)))
+        return msp_set_error(ctx, MSP_EINVAL,
+                             "general: need tol > 0, max_outer >= 1, 1 <= level2_iters, level3_iters <= 1000, "
+                             "precision MIXED or FP32, the residual criterion");
+    msp::DeviceGuard guard(ctx->device);
+    msp_info inf;
+    std::memset(&inf, 0, sizeof inf);
+    inf.lambda_tilde = g->lam_tilde;
+    inf.shift = g->shift_a;
+    inf.shift_retries = g->retries_a + g->retries_b;
+    const int np = (int)g->n_pad;
+    const unsigned nb = (unsigned)((np + 255) / 256);
+    MSP_CUDA_TRY(ctx, cudaMemsetAsync(g->err, 0, sizeof(int), ctx->stream));
+    k_pad_copy_64<<<nb, 256, 0, ctx->stream>>>(np, (int)g->n, c, g->c64);
+    MSP_CHECK_LAUNCH(ctx);
+    double cn = 0.0;
+    MSP_TRY(norm64(ctx, g, g->c64, &cn));
+    msp_status result = MSP_OK;
+    const int t2 = o.level2_iters, t3 = o.level3_iters;
+    if (cn == 0.0) {
+        MSP_CUDA_TRY(ctx, cudaMemsetAsync(x, 0, (size_t)g->n * 8, ctx->stream));
+    } else if (o.precision == MSP_PREC_FP32) {
+        k_scale_to_f32<<<nb, 256, 0, ctx->stream>>>(np, g->c64, 1.0 / cn, g->b1);
+        MSP_CHECK_LAUNCH(ctx);
+        int it = 0;
+        bool conv = false;
+        MSP_TRY(level1(ctx, g, o.tol, o.max_outer, t2, t3, &it, &conv, &inf.inner_iters));
+        inf.outer_iters = it;
+        MSP_CUDA_TRY(ctx, cudaMemsetAsync(g->x64, 0, (size_t)np * 8, ctx->stream));
+        k_axpy_64<<<nb, 256, 0, ctx->stream>>>(np, cn, g->x1, g->x64);
+        MSP_CHECK_LAUNCH(ctx);
+        MSP_TRY(residual64(ctx, g));
+        double rn = 0.0;
+        MSP_TRY(norm64(ctx, g, g->r64, &rn));
+        inf.rel_resid = rn / cn;
+        if (!conv) result = MSP_ENOCONV;
+    } else {
+        MSP_CUDA_TRY(ctx, cudaMemsetAsync(g->x64, 0, (size_t)np * 8, ctx->stream));
+        MSP_CUDA_TRY(ctx, cudaMemcpyAsync(g->r64, g->c64, (size_t)np * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+        double rn = cn;
+        bool done = false;
+        for (int step = 0; step < o.max_refine; ++step) {
+            if (rn <= o.tol * cn) {
+                done = true;
+                break;
+            }
+            k_scale_to_f32<<<nb, 256, 0, ctx->stream>>>(np, g->r64, 1.0 / rn, g->b1);
+            MSP_CHECK_LAUNCH(ctx);
+            int it = 0;
+            bool conv = false;
+            MSP_TRY(level1(ctx, g, o.refine_tol, o.max_outer, t2, t3, &it, &conv, &inf.inner_iters));
+            inf.outer_iters += it;
+            ++inf.refine_steps;
+            k_axpy_64<<<nb, 256, 0, ctx->stream>>>(np, rn, g->x1, g->x64);
+            MSP_CHECK_LAUNCH(ctx);
+            MSP_TRY(residual64(ctx, g));
+            const double prev = rn;
+            MSP_TRY(norm64(ctx, g, g->r64, &rn));
+            if (!std::isfinite(rn)) return msp_set_error(ctx, MSP_ENONFINITE, "general: non-finite residual");
+            if (rn >= prev && !(rn <= o.tol * cn)) break;   // refinement stalled
+        }
+        if (!done && rn <= o.tol * cn) done = true;
+        inf.rel_resid = rn / cn;
+        if (!done) result = MSP_ENOCONV;
+    }
+    if (cn != 0.0)
+        MSP_CUDA_TRY(ctx, cudaMemcpyAsync(x, g->x64, (size_t)g->n * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    inf.status = result;
+    if (info) *info = inf;
+    if (result == MSP_ENOCONV)
+        return msp_set_error(ctx, MSP_ENOCONV, "general: relative residual %.3g above tol %.3g", inf.rel_resid,
+                             o.tol);
+    return result;
+}
+
+}  // extern "C"

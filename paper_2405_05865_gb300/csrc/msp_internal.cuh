@@ -238,6 +238,10 @@ msp_status msp_build_csr(msp_ctx* ctx, int64_t n, int64_t rows, int gamma,
 msp_status msp_sketch_apply(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t n,
                             int64_t lda, int64_t s_pad, const int32_t* ptr,
                             const int32_t* ent, int gamma, void* C);
+// C = A Pi for an m x n A (rows of C follow the rows of A).
+msp_status msp_sketch_apply_rows(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t m, int64_t n,
+                                 int64_t lda, int64_t s_pad, const int32_t* ptr,
+                                 const int32_t* ent, int gamma, void* C);
 msp_status msp_gather_rows(msp_ctx* ctx, msp_dtype dt, int64_t rows_out, int64_t width,
                            const int32_t* ptr, const int32_t* ent, const void* in,
                            int64_t ld_in, double scale, void* out, int64_t ld_out);
@@ -256,6 +260,10 @@ msp_status msp_norm_lb_launch(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t
 
 // factor.cu
 msp_status msp_build_factor(msp_ctx* ctx, msp_factor_s* f, const void* Ct, int64_t phi_rows);
+// (X^T X + diag I)^{-1} as a dense FP32 s_pad x s_pad matrix (see factor.cu)
+msp_status msp_gram_inverse(msp_ctx* ctx, const float* X, int64_t rows, int64_t s, int64_t sp,
+                            double diag, double* G64, double* Linv64, float* Minv,
+                            double* shift, int* retries);
 
 // symv.cu
 int64_t msp_packed_tiles(int64_t n);

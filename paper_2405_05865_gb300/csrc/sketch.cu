@@ -153,7 +153,7 @@ __global__ void k_chunk_starts(const int32_t* __restrict__ ptr, const int32_t* _
 
 template <typename T, int R, int NC>
 __global__ void __launch_bounds__(256) k_sketch_apply(
-    const T* __restrict__ A, int64_t lda, int64_t n, int64_t s_pad,
+    const T* __restrict__ A, int64_t lda, int64_t m, int64_t n, int64_t s_pad,
     const int32_t* __restrict__ tab, int nch, const int32_t* __restrict__ ent, T scale,
     T* __restrict__ C, int J) {
     using VT = typename V16<T>::type;
@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(256) k_sketch_apply(
             T v[R];
 #pragma unroll
             for (int r = 0; r < R; ++r)
-                v[r] = (i0 + r < n) ? __ldcs(&A[(i0 + r) * lda + j0 + jj]) : T(0);
+                v[r] = (i0 + r < m) ? __ldcs(&A[(i0 + r) * lda + j0 + jj]) : T(0);
             const int sw = (jj >> 1) & 3;
 #pragma unroll
             for (int q = 0; q < NV; ++q) {
@@ -221,12 +221,12 @@ __global__ void __launch_bounds__(256) k_sketch_apply(
         int c = threadIdx.x + k * nthr;
 #pragma unroll
         for (int r = 0; r < R; ++r)
-            if (i0 + r < n) C[(i0 + r) * s_pad + c] = acc[k][r] * scale;
+            if (i0 + r < m) C[(i0 + r) * s_pad + c] = acc[k][r] * scale;
     }
 }
 
 template <typename T, int R>
-msp_status launch_sketch_apply_r(msp_ctx* ctx, const T* A, int64_t lda, int64_t n,
+msp_status launch_sketch_apply_r(msp_ctx* ctx, const T* A, int64_t lda, int64_t m, int64_t n,
                                  int64_t s_pad, const int32_t* ptr, const int32_t* ent,
                                  T scale, T* C) {
     // s_pad is a multiple of 128: the smallest NC with s_pad / NC a multiple
@@ -243,7 +243,7 @@ msp_status launch_sketch_apply_r(msp_ctx* ctx, const T* A, int64_t lda, int64_t 
     const int threads = (int)(s_pad / nc);
     const int J = (int)((64 * 1024) / (sizeof(T) * R));
     size_t smem = (size_t)J * R * sizeof(T);
-    dim3 grid((unsigned)((n + R - 1) / R));
+    dim3 grid((unsigned)((m + R - 1) / R));
     const int nch = (int)((n + J - 1) / J);
     void* scr = nullptr;
     MSP_TRY(msp_scratch(ctx, (size_t)s_pad * (nch + 1) * 4, &scr));
@@ -258,7 +258,7 @@ msp_status launch_sketch_apply_r(msp_ctx* ctx, const T* A, int64_t lda, int64_t 
         auto kern = k_sketch_apply<T, R, NCV>;                                        \
         MSP_CUDA_TRY(ctx, cudaFuncSetAttribute(kern,                                  \
                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));        \
-        kern<<<grid, threads, smem, ctx->stream>>>(A, lda, n, s_pad, tab, nch, ent,   \
+        kern<<<grid, threads, smem, ctx->stream>>>(A, lda, m, n, s_pad, tab, nch, ent, \
                                                   scale, C, J);                       \
         break;                                                                        \
     }
@@ -349,15 +349,21 @@ msp_status msp_build_csr(msp_ctx* ctx, int64_t n, int64_t rows, int gamma,
 msp_status msp_sketch_apply(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t n,
                             int64_t lda, int64_t s_pad, const int32_t* ptr,
                             const int32_t* ent, int gamma, void* C) {
+    return msp_sketch_apply_rows(ctx, A, dt, n, n, lda, s_pad, ptr, ent, gamma, C);
+}
+
+msp_status msp_sketch_apply_rows(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t m, int64_t n,
+                                 int64_t lda, int64_t s_pad, const int32_t* ptr,
+                                 const int32_t* ent, int gamma, void* C) {
     // accumulators per thread: R rows x NC columns; R = 4 vectors of 16 bytes
     double scale = 1.0 / sqrt((double)gamma);
     if (s_pad > 1024)
         return msp_set_error(ctx, MSP_EINVAL, "sketch: s_pad %lld above 1024 is not supported",
                              (long long)s_pad);
     if (dt == MSP_F32)
-        return launch_sketch_apply_r<float, 16>(ctx, (const float*)A, lda, n, s_pad, ptr, ent,
+        return launch_sketch_apply_r<float, 16>(ctx, (const float*)A, lda, m, n, s_pad, ptr, ent,
                                                 (float)scale, (float*)C);
-    return launch_sketch_apply_r<double, 8>(ctx, (const double*)A, lda, n, s_pad, ptr, ent,
+    return launch_sketch_apply_r<double, 8>(ctx, (const double*)A, lda, m, n, s_pad, ptr, ent,
                                             scale, (double*)C);
 }
 
