@@ -350,6 +350,8 @@ struct msp_general_s {
     double* host = nullptr;         // pinned: 16 doubles
     int G = 0;
     int64_t rows_per_cta = 0;
+    int64_t ldp = 0;                // row stride of the partials: max(n_pad, s_pad)
+    cudaStream_t cap = nullptr;     // private stream the SolveM1 graph is captured on
     cudaGraphExec_t m1_exec = nullptr;
     int m1_t2 = -1, m1_t3 = -1;
     int m1_kernels = 0;
@@ -360,7 +362,7 @@ namespace {
 using G_t = msp_general_s;
 
 template <typename Acc, bool kSame>
-msp_status launch_rowpass_nv(msp_ctx* ctx, G_t* g, const float* X, int64_t ldx, int nx4, const float* Y,
+msp_status launch_rowpass_nv(msp_ctx* ctx, cudaStream_t strm, G_t* g, const float* X, int64_t ldx, int nx4, const float* Y,
                              int64_t ldy, int ny4, const Acc* a, const Acc* z, Acc beta, Acc* tout,
                              Acc* part, int64_t ldp, int* count) {
     const size_t smem = (size_t)nx4 * 4 * sizeof(Acc);
@@ -368,7 +370,7 @@ msp_status launch_rowpass_nv(msp_ctx* ctx, G_t* g, const float* X, int64_t ldx, 
 #define MSP_RP(NVV)                                                                                     \
     case NVV: {                                                                                         \
         auto kern = k_rowpass<Acc, NVV, kSame>;                                                         \
-        kern<<<g->G, kThreads, smem, ctx->stream>>>(X, ldx, nx4, Y, ldy, ny4, g->m, g->rows_per_cta, a, \
+        kern<<<g->G, kThreads, smem, strm>>>(X, ldx, nx4, Y, ldy, ny4, g->m, g->rows_per_cta, a,        \
                                                     z, beta, tout, part, ldp);                          \
         break;                                                                                          \
     }
@@ -401,10 +403,9 @@ msp_status set_rowpass_attrs(msp_ctx* ctx, size_t smem) {
 
 // out = alpha (sum of the pass over the rows) + beta w + v
 template <typename Acc>
-msp_status colsum(msp_ctx* ctx, G_t* g, const Acc* part, int64_t ldp, int ny, double alpha, const Acc* w,
+msp_status colsum(msp_ctx* ctx, cudaStream_t strm, G_t* g, const Acc* part, int64_t ldp, int ny, double alpha, const Acc* w,
                   double beta, const Acc* v, Acc* out, int* count) {
-    k_colsum<Acc><<<(unsigned)((ny + 31) / 32), 256, 0, ctx->stream>>>(part, ldp, g->G, ny, alpha, w, beta, v,
-                                                                      out);
+    k_colsum<Acc><<<(unsigned)((ny + 31) / 32), 256, 0, strm>>>(part, ldp, g->G, ny, alpha, w, beta, v, out);
     MSP_CHECK_LAUNCH(ctx);
     if (count) ++*count;
     return MSP_OK;
@@ -415,47 +416,48 @@ struct Ops {
     msp_ctx* ctx;
     G_t* g;
     int* count;
-    int64_t ldp() const { return g->n_pad; }
+    cudaStream_t strm;
+    int64_t ldp() const { return g->ldp; }
     int na4() const { return (int)(g->n_pad / 4); }
     int ns4() const { return (int)(g->s_pad / 4); }
 
     // q = (A^T A + lam I) p  (level 1)
     msp_status op1(const float* p, float* q) {
-        MSP_TRY((launch_rowpass_nv<float, true>(ctx, g, g->A, g->lda, na4(), g->A, g->lda, na4(), p, nullptr, 0.f,
+        MSP_TRY((launch_rowpass_nv<float, true>(ctx, strm, g, g->A, g->lda, na4(), g->A, g->lda, na4(), p, nullptr, 0.f,
                                                 nullptr, g->part, ldp(), count)));
-        return colsum<float>(ctx, g, g->part, ldp(), (int)g->n_pad, 1.0, p, g->lambda, nullptr, q, count);
+        return colsum<float>(ctx, strm, g, g->part, ldp(), (int)g->n_pad, 1.0, p, g->lambda, nullptr, q, count);
     }
     // out = A~^T (A r)
     msp_status sketch_rhs(const float* r, float* out) {
-        MSP_TRY((launch_rowpass_nv<float, false>(ctx, g, g->A, g->lda, na4(), g->At, g->s_pad, ns4(), r, nullptr,
+        MSP_TRY((launch_rowpass_nv<float, false>(ctx, strm, g, g->A, g->lda, na4(), g->At, g->s_pad, ns4(), r, nullptr,
                                                  0.f, nullptr, g->part, ldp(), count)));
-        return colsum<float>(ctx, g, g->part, ldp(), (int)g->s_pad, 1.0, nullptr, 0.0, nullptr, out, count);
+        return colsum<float>(ctx, strm, g, g->part, ldp(), (int)g->s_pad, 1.0, nullptr, 0.0, nullptr, out, count);
     }
     // q = (A~^T A A^T A~ + lam~ A~^T A~) y  (level 2)
     msp_status op2(const float* y, float* q) {
-        MSP_TRY((launch_rowpass_nv<float, false>(ctx, g, g->At, g->s_pad, ns4(), g->A, g->lda, na4(), y, nullptr,
+        MSP_TRY((launch_rowpass_nv<float, false>(ctx, strm, g, g->At, g->s_pad, ns4(), g->A, g->lda, na4(), y, nullptr,
                                                  0.f, g->tm, g->part, ldp(), count)));
-        MSP_TRY(colsum<float>(ctx, g, g->part, ldp(), (int)g->n_pad, 1.0, nullptr, 0.0, nullptr, g->vn, count));
-        MSP_TRY((launch_rowpass_nv<float, false>(ctx, g, g->A, g->lda, na4(), g->At, g->s_pad, ns4(), g->vn, g->tm,
+        MSP_TRY(colsum<float>(ctx, strm, g, g->part, ldp(), (int)g->n_pad, 1.0, nullptr, 0.0, nullptr, g->vn, count));
+        MSP_TRY((launch_rowpass_nv<float, false>(ctx, strm, g, g->A, g->lda, na4(), g->At, g->s_pad, ns4(), g->vn, g->tm,
                                                  (float)g->lam_tilde, nullptr, g->part, ldp(), count)));
-        return colsum<float>(ctx, g, g->part, ldp(), (int)g->s_pad, 1.0, nullptr, 0.0, nullptr, q, count);
+        return colsum<float>(ctx, strm, g, g->part, ldp(), (int)g->s_pad, 1.0, nullptr, 0.0, nullptr, q, count);
     }
     // w = (r - A^T (A~ y)) / lam~  (Algorithm 4 step 3)
     msp_status finish_m1(const float* y, const float* r, float* w) {
-        MSP_TRY((launch_rowpass_nv<float, false>(ctx, g, g->At, g->s_pad, ns4(), g->A, g->lda, na4(), y, nullptr,
+        MSP_TRY((launch_rowpass_nv<float, false>(ctx, strm, g, g->At, g->s_pad, ns4(), g->A, g->lda, na4(), y, nullptr,
                                                  0.f, nullptr, g->part, ldp(), count)));
         const double il = 1.0 / g->lam_tilde;
-        return colsum<float>(ctx, g, g->part, ldp(), (int)g->n_pad, -il, r, il, nullptr, w, count);
+        return colsum<float>(ctx, strm, g, g->part, ldp(), (int)g->n_pad, -il, r, il, nullptr, w, count);
     }
     // q = A~^T A~ p + shift p  (level 3)
     msp_status op3(const float* p, float* q, double shift) {
-        MSP_TRY((launch_rowpass_nv<float, true>(ctx, g, g->At, g->s_pad, ns4(), g->At, g->s_pad, ns4(), p, nullptr,
+        MSP_TRY((launch_rowpass_nv<float, true>(ctx, strm, g, g->At, g->s_pad, ns4(), g->At, g->s_pad, ns4(), p, nullptr,
                                                 0.f, nullptr, g->part, ldp(), count)));
-        return colsum<float>(ctx, g, g->part, ldp(), (int)g->s_pad, 1.0, p, shift, nullptr, q, count);
+        return colsum<float>(ctx, strm, g, g->part, ldp(), (int)g->s_pad, 1.0, p, shift, nullptr, q, count);
     }
     msp_status dense(const float* M, const float* v, float* out) {
         const int sp = (int)g->s_pad;
-        k_dense_mv<<<(unsigned)((sp + 7) / 8), 256, 0, ctx->stream>>>(M, v, sp, out);
+        k_dense_mv<<<(unsigned)((sp + 7) / 8), 256, 0, strm>>>(M, v, sp, out);
         MSP_CHECK_LAUNCH(ctx);
         if (count) ++*count;
         return MSP_OK;
@@ -463,10 +465,10 @@ struct Ops {
     msp_status vec(int which, int len, const float* a0, const float* a1, float* a2, float* a3, Pcg* sc,
                    int flexible = 0) {
         switch (which) {
-            case 0: k_pcg_init<<<1, kVecThreads, 0, ctx->stream>>>(len, a0, a2, a3, sc); break;
-            case 1: k_pcg_start<<<1, kVecThreads, 0, ctx->stream>>>(len, a0, a1, a2, a3, sc); break;
-            case 2: k_pcg_step<<<1, kVecThreads, 0, ctx->stream>>>(len, a0, a1, a2, a3, sc, g->err); break;
-            default: k_pcg_dir<<<1, kVecThreads, 0, ctx->stream>>>(len, a0, a1, a2, a3, sc, flexible); break;
+            case 0: k_pcg_init<<<1, kVecThreads, 0, strm>>>(len, a0, a2, a3, sc); break;
+            case 1: k_pcg_start<<<1, kVecThreads, 0, strm>>>(len, a0, a1, a2, a3, sc); break;
+            case 2: k_pcg_step<<<1, kVecThreads, 0, strm>>>(len, a0, a1, a2, a3, sc, g->err); break;
+            default: k_pcg_dir<<<1, kVecThreads, 0, strm>>>(len, a0, a1, a2, a3, sc, flexible); break;
         }
         MSP_CHECK_LAUNCH(ctx);
         if (count) ++*count;
@@ -496,7 +498,7 @@ struct Ops {
         MSP_TRY(level3(r, g->v3, g->M3b, g->lam_tilde, t3));
         const int sp = (int)g->s_pad;
         const float il = (float)(1.0 / g->lam_tilde);
-        k_axpby<<<(unsigned)((sp + 255) / 256), 256, 0, ctx->stream>>>(sp, il, g->u3, -il, g->v3, z);
+        k_axpby<<<(unsigned)((sp + 255) / 256), 256, 0, strm>>>(sp, il, g->u3, -il, g->v3, z);
         MSP_CHECK_LAUNCH(ctx);
         if (count) ++*count;
         return MSP_OK;
@@ -530,6 +532,7 @@ void destroy_general(G_t* g) {
                     (void*)g->Linv, g->work})
         if (p) cudaFreeAsync(p, s);
     if (g->host) cudaFreeHost(g->host);
+    if (g->cap) cudaStreamDestroy(g->cap);
     delete g;
 }
 
@@ -541,12 +544,12 @@ msp_status ensure_m1_graph(msp_ctx* ctx, G_t* g, int t2, int t3) {
         g->m1_exec = nullptr;
     }
     int count = 0;
-    Ops ops{ctx, g, &count};
-    MSP_CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    Ops ops{ctx, g, &count, g->cap};
+    MSP_CUDA_TRY(ctx, cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal));
     const int64_t l0 = ctx->launches;
     msp_status st = ops.solve_m1(g->r1, g->z1, t2, t3);
     cudaGraph_t graph = nullptr;
-    const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+    const cudaError_t ce = cudaStreamEndCapture(g->cap, &graph);
     ctx->launches = l0;   // counted per replay instead
     if (st != MSP_OK) {
         if (graph) cudaGraphDestroy(graph);
@@ -593,7 +596,7 @@ msp_status read_scalars(msp_ctx* ctx, G_t* g, const Pcg* sc, double* rr, double*
 // SolveM1, FP32 vectors; stops at |r| <= tol |b1| or after maxit steps.
 msp_status level1(msp_ctx* ctx, G_t* g, double tol, int maxit, int t2, int t3, int* iters, bool* conv,
                   int* inner) {
-    Ops ops{ctx, g, nullptr};
+    Ops ops{ctx, g, nullptr, ctx->stream};
     const int len = (int)g->n_pad;
     Pcg* sc = g->sc;
     MSP_TRY(ops.vec(0, len, g->b1, nullptr, g->x1, g->r1, sc));
@@ -629,9 +632,9 @@ msp_status level1(msp_ctx* ctx, G_t* g, double tol, int maxit, int t2, int t3, i
 // out = sgn (A^T A + lam I) x64 + v, FP64 accumulation
 msp_status apply64(msp_ctx* ctx, G_t* g, double sgn, const double* v, double* out) {
     const int na4 = (int)(g->n_pad / 4);
-    MSP_TRY((launch_rowpass_nv<double, true>(ctx, g, g->A, g->lda, na4, g->A, g->lda, na4, g->x64, nullptr, 0.0,
+    MSP_TRY((launch_rowpass_nv<double, true>(ctx, ctx->stream, g, g->A, g->lda, na4, g->A, g->lda, na4, g->x64, nullptr, 0.0,
                                              nullptr, g->part64, g->n_pad, nullptr)));
-    return colsum<double>(ctx, g, g->part64, g->n_pad, (int)g->n_pad, sgn, g->x64, sgn * g->lambda, v, out,
+    return colsum<double>(ctx, ctx->stream, g, g->part64, g->n_pad, (int)g->n_pad, sgn, g->x64, sgn * g->lambda, v, out,
                           nullptr);
 }
 
@@ -662,11 +665,11 @@ msp_status msp_general_create(msp_ctx* ctx, const float* A, int64_t m, int64_t n
     if (!ctx) return msp_set_error(nullptr, MSP_EINVAL, "ctx is NULL");
     if (!A || !out) return msp_set_error(ctx, MSP_EINVAL, "general: NULL argument");
     *out = nullptr;
-    if (n < 16 || n > kMaxN || m < n || m >= (1ll << 31) || lda < n || !(lambda >= 0.0) || !(lambda0 >= 0.0) ||
+    if (n < 16 || n > kMaxN || m < n || m >= (1ll << 30) || lda < n || !(lambda >= 0.0) || !(lambda0 >= 0.0) ||
         !(lambda + lambda0 > 0.0) || s < 16 || s > MSP_MAX_S || s > n || gamma < 1 || gamma > MSP_MAX_GAMMA ||
         gamma > s || phi < s || phi > m || gamma_phi < 1 || gamma_phi > MSP_MAX_GAMMA || gamma_phi > phi)
         return msp_set_error(ctx, MSP_EINVAL,
-                             "general: need 16 <= n <= %d, n <= m < 2^31, lda >= n, lambda, lambda0 >= 0 with "
+                             "general: need 16 <= n <= %d, n <= m < 2^30, lda >= n, lambda, lambda0 >= 0 with "
                              "lambda + lambda0 > 0, 16 <= s <= min(n, %d), 1 <= gamma <= min(s, %d), "
                              "s <= phi <= m, 1 <= gamma_phi <= min(phi, %d)",
                              kMaxN, MSP_MAX_S, MSP_MAX_GAMMA, MSP_MAX_GAMMA);
@@ -720,6 +723,12 @@ msp_status msp_general_create(msp_ctx* ctx, const float* A, int64_t m, int64_t n
     g->G = (int)std::min<int64_t>(2 * ctx->num_sms, (m + kRows - 1) / kRows);
     g->rows_per_cta = round_up((m + g->G - 1) / g->G, kRows);
     g->G = (int)((m + g->rows_per_cta - 1) / g->rows_per_cta);
+    g->ldp = std::max<int64_t>(g->n_pad, g->s_pad);
+    if (cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        g->cap = nullptr;
+        return fail(msp_set_error(ctx, MSP_ECUDA, "general: stream creation failed"));
+    }
 
     // ---- Algorithm 3 steps 3-4: S, A~ = A S^T, A^ = Phi A~
     {
@@ -783,7 +792,7 @@ msp_status msp_general_create(msp_ctx* ctx, const float* A, int64_t m, int64_t n
         for (auto& o : o2) o = take((size_t)sp * 4);
         for (auto& o : o3) o = take((size_t)sp * 4);
         const size_t o_tm = take((size_t)m * 4), o_vn = take((size_t)np * 4);
-        const size_t o_part = take((size_t)g->G * np * 4);
+        const size_t o_part = take((size_t)g->G * g->ldp * 4);
         const size_t o_p64 = take((size_t)g->G * np * 8);
         const size_t o_x64 = take((size_t)np * 8), o_r64 = take((size_t)np * 8), o_c64 = take((size_t)np * 8);
         const size_t o_d64 = take(64);
@@ -811,7 +820,7 @@ msp_status msp_general_create(msp_ctx* ctx, const float* A, int64_t m, int64_t n
         g->sc = (Pcg*)(w + o_sc);
         g->err = (int*)(w + o_err);
     }
-    if ((st = set_rowpass_attrs<float>(ctx, (size_t)np * 4)) != MSP_OK ||
+    if ((st = set_rowpass_attrs<float>(ctx, (size_t)std::max(np, sp) * 4)) != MSP_OK ||
         (st = set_rowpass_attrs<double>(ctx, (size_t)np * 8)) != MSP_OK)
         return fail(st);
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
@@ -870,7 +879,7 @@ msp_status msp_general_solve_m2(msp_ctx* ctx, msp_general_t* g, const float* r, 
     const int sp = (int)g->s_pad;
     k_pad_copy_32<<<(unsigned)((sp + 255) / 256), 256, 0, ctx->stream>>>(sp, (int)g->s, r, g->r2);
     MSP_CHECK_LAUNCH(ctx);
-    Ops ops{ctx, g, nullptr};
+    Ops ops{ctx, g, nullptr, ctx->stream};
     MSP_TRY(ops.solve_m2(g->r2, g->z2, t3));
     MSP_CUDA_TRY(ctx, cudaMemcpyAsync(z, g->z2, (size_t)g->s * 4, cudaMemcpyDeviceToDevice, ctx->stream));
     return MSP_OK;
