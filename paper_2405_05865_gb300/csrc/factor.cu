@@ -363,11 +363,6 @@ __global__ void k_cast_tri(const double* __restrict__ X, T* __restrict__ B, T* _
     Bt[j * s_pad + i] = (T)v;
 }
 
-__global__ void k_cast_f32(const double* __restrict__ X, float* __restrict__ Y, int64_t len) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < len) Y[e] = (float)X[e];
-}
-
 template <int TS>
 void launch_dgemm_ts(msp_ctx* ctx, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha,
                      const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
@@ -549,11 +544,11 @@ msp_status msp_build_factor(msp_ctx* ctx, msp_factor_s* f, const void* Ct, int64
 
 // Dense inverse of G + diag I with G = X^T X (X: rows x s_pad FP32 row-major,
 // pad columns zero): FP64 Gram (split-K, compensated), Cholesky with the
-// FP32-data shift rule, then G^{-1} = L^{-T} L^{-1} in FP64, cast to FP32
-// (full symmetric, pad block identity). G64 (optional) receives G + diag I
-// before the shift.
+// FP32-data shift rule, then G^{-1} = L^{-T} L^{-1} in FP64 (full symmetric,
+// pad block identity). G64 receives G + diag I before the shift. An FP32
+// copy of the inverse would perturb its products by about 2^-24 kappa(G).
 msp_status msp_gram_inverse(msp_ctx* ctx, const float* X, int64_t rows, int64_t s, int64_t sp,
-                            double diag, double* G64, double* Linv64, float* Minv,
+                            double diag, double* G64, double* Linv64, double* Minv,
                             double* shift, int* retries) {
     {
         void* scr = nullptr;
@@ -568,13 +563,7 @@ msp_status msp_gram_inverse(msp_ctx* ctx, const float* X, int64_t rows, int64_t 
         MSP_CHECK_LAUNCH(ctx);
     }
     MSP_TRY(factor_shifted(ctx, G64, s, sp, true, Linv64, shift, retries));
-    // G^{-1} = X^T X with X = L^{-1} (lower); FP64 product into scratch
-    void* scr = nullptr;
-    MSP_TRY(msp_scratch(ctx, (size_t)sp * sp * 8, &scr));
-    double* Gi = (double*)scr;
-    MSP_TRY(dgemm(ctx, true, false, sp, sp, sp, 1.0, Linv64, sp, Linv64, sp, 0.0, Gi, sp));
-    k_cast_f32<<<(unsigned)((sp * sp + 255) / 256), 256, 0, ctx->stream>>>(Gi, Minv, sp * sp);
-    MSP_CHECK_LAUNCH(ctx);
-    return MSP_OK;
+    // G^{-1} = X^T X with X = L^{-1} (lower), FP64
+    return dgemm(ctx, true, false, sp, sp, sp, 1.0, Linv64, sp, Linv64, sp, 0.0, Minv, sp);
 }
 

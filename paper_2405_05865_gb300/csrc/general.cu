@@ -20,8 +20,8 @@
 // The inner levels run a fixed number of PCG steps (t2, t3) with all scalars
 // on the device, so one application of SolveM1 is a fixed launch sequence;
 // it is captured once into a CUDA graph and replayed per level-1 iteration.
-// The level-3 preconditioners M3a^{-1}, M3b^{-1} are dense s x s inverses of
-// the sketched Grams (FP64 Cholesky), applied by a dense mat-vec.
+// The level-3 preconditioners M3a^{-1}, M3b^{-1} are dense FP64 s x s
+// inverses of the sketched Grams (FP64 Cholesky), applied by a dense mat-vec.
 #include "msp_internal.cuh"
 
 #include <cmath>
@@ -263,19 +263,20 @@ __global__ void k_pcg_dir(int len, const float* __restrict__ r, const float* __r
     }
 }
 
-// out = M v for a dense s_pad x s_pad FP32 M (row-major), one warp per row,
-// FP64 accumulation
-__global__ void k_dense_mv(const float* __restrict__ M, const float* __restrict__ v, int sp,
+// out = M v for a dense s_pad x s_pad FP64 M (row-major), one warp per row
+__global__ void k_dense_mv(const double* __restrict__ M, const float* __restrict__ v, int sp,
                            float* __restrict__ out) {
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= sp) return;
-    const float4* mr = reinterpret_cast<const float4*>(M + (int64_t)row * sp);
-    const float4* vv = reinterpret_cast<const float4*>(v);
+    const double2* mr = reinterpret_cast<const double2*>(M + (int64_t)row * sp);
+    const float2* vv = reinterpret_cast<const float2*>(v);
     double s = 0.0;
-    for (int c = lane; c < sp / 4; c += 32) {
-        const float4 a = mr[c], b = vv[c];
-        s += (double)a.x * b.x + (double)a.y * b.y + (double)a.z * b.z + (double)a.w * b.w;
+    for (int c = lane; c < sp / 2; c += 32) {
+        const double2 a = mr[c];
+        const float2 b = vv[c];
+        s = fma(a.x, (double)b.x, s);
+        s = fma(a.y, (double)b.y, s);
     }
     s = warp_sum_t(s);
     if (lane == 0) out[row] = (float)s;
@@ -334,8 +335,8 @@ struct msp_general_s {
     const float* A = nullptr;       // user's A, or A_copy
     float* A_copy = nullptr;        // padded copy when the user's rows are not 16-byte aligned
     float* At = nullptr;            // A~ = A S^T, m x s_pad
-    float* M3a = nullptr;           // (A^^T A^)^{-1}, s_pad x s_pad
-    float* M3b = nullptr;           // (A^^T A^ + lam~ I)^{-1}
+    double* M3a = nullptr;          // (A^^T A^)^{-1}, s_pad x s_pad FP64
+    double* M3b = nullptr;          // (A^^T A^ + lam~ I)^{-1}
     double* G3a = nullptr;          // A^^T A^ (FP64, before the shift), for tests
     double* G3b = nullptr;
     double* Linv = nullptr;         // FP64 scratch for the factorisations
@@ -455,7 +456,7 @@ struct Ops {
                                                 0.f, nullptr, g->part, ldp(), count)));
         return colsum<float>(ctx, strm, g, g->part, ldp(), (int)g->s_pad, 1.0, p, shift, nullptr, q, count);
     }
-    msp_status dense(const float* M, const float* v, float* out) {
+    msp_status dense(const double* M, const float* v, float* out) {
         const int sp = (int)g->s_pad;
         k_dense_mv<<<(unsigned)((sp + 7) / 8), 256, 0, strm>>>(M, v, sp, out);
         MSP_CHECK_LAUNCH(ctx);
@@ -476,7 +477,7 @@ struct Ops {
     }
 
     // t3 PCG steps on (A~^T A~ + shift I) x = b preconditioned by the dense Minv
-    msp_status level3(const float* b, float* x, const float* Minv, double shift, int t3) {
+    msp_status level3(const float* b, float* x, const double* Minv, double shift, int t3) {
         const int sp = (int)g->s_pad;
         Pcg* sc = g->sc + 2;
         MSP_TRY(vec(0, sp, b, nullptr, x, g->r3, sc));
@@ -770,8 +771,8 @@ msp_status msp_general_create(msp_ctx* ctx, const float* A, int64_t m, int64_t n
             return tfail(st);
         // ---- steps 5-6: M3a = A^^T A^, M3b = M3a + lam~ I and their inverses
         const size_t mat = (size_t)sp * sp;
-        if ((st = msp_alloc(ctx, (void**)&g->M3a, mat * 4)) != MSP_OK ||
-            (st = msp_alloc(ctx, (void**)&g->M3b, mat * 4)) != MSP_OK ||
+        if ((st = msp_alloc(ctx, (void**)&g->M3a, mat * 8)) != MSP_OK ||
+            (st = msp_alloc(ctx, (void**)&g->M3b, mat * 8)) != MSP_OK ||
             (st = msp_alloc(ctx, (void**)&g->G3a, mat * 8)) != MSP_OK ||
             (st = msp_alloc(ctx, (void**)&g->G3b, mat * 8)) != MSP_OK ||
             (st = msp_alloc(ctx, (void**)&g->Linv, mat * 8)) != MSP_OK)

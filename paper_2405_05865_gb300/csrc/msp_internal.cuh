@@ -260,9 +260,9 @@ msp_status msp_norm_lb_launch(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t
 
 // factor.cu
 msp_status msp_build_factor(msp_ctx* ctx, msp_factor_s* f, const void* Ct, int64_t phi_rows);
-// (X^T X + diag I)^{-1} as a dense FP32 s_pad x s_pad matrix (see factor.cu)
+// (X^T X + diag I)^{-1} as a dense FP64 s_pad x s_pad matrix (see factor.cu)
 msp_status msp_gram_inverse(msp_ctx* ctx, const float* X, int64_t rows, int64_t s, int64_t sp,
-                            double diag, double* G64, double* Linv64, float* Minv,
+                            double diag, double* G64, double* Linv64, double* Minv,
                             double* shift, int* retries);
 
 // symv.cu
