@@ -448,7 +448,8 @@ MSP_API msp_status msp_auto_params(msp_ctx* ctx, const float* A, int64_t n, int6
  * S (s x n, gamma nonzeros per column, the streams of msp_sketch with `seed`),
  * A~ = A S^T (m x s), A^ = Phi A~ with Phi a phi x m sparse embedding
  * (gamma_phi nonzeros per column, the level-2 streams), M3a = A^^T A^ and
- * M3b = M3a + lambda~ I factored in FP64 (the FP32-data shift of msp_nystrom)
+ * M3b = M3a + lambda~ I factored in FP64 (unshifted; on failure the FP64-data
+ * shift rule of msp_nystrom)
  * and kept as dense FP64 inverses. A is read again by every solve and must
  * stay valid and unchanged for the life of the handle (unless it was copied).
  * Requires 16 <= n <= 8192, n <= m < 2^30, lambda >= 0, lambda0 >= 0 with

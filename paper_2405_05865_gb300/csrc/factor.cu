@@ -543,8 +543,8 @@ msp_status msp_build_factor(msp_ctx* ctx, msp_factor_s* f, const void* Ct, int64
 }
 
 // Dense inverse of G + diag I with G = X^T X (X: rows x s_pad FP32 row-major,
-// pad columns zero): FP64 Gram (split-K, compensated), Cholesky with the
-// FP32-data shift rule, then G^{-1} = L^{-T} L^{-1} in FP64 (full symmetric,
+// pad columns zero): FP64 Gram (split-K, compensated), Cholesky (shifted
+// only on failure), then G^{-1} = L^{-T} L^{-1} in FP64 (full symmetric,
 // pad block identity). G64 receives G + diag I before the shift. An FP32
 // copy of the inverse would perturb its products by about 2^-24 kappa(G).
 msp_status msp_gram_inverse(msp_ctx* ctx, const float* X, int64_t rows, int64_t s, int64_t sp,
@@ -562,7 +562,10 @@ msp_status msp_gram_inverse(msp_ctx* ctx, const float* X, int64_t rows, int64_t 
             P, nullptr, diag, s, sp, G64);
         MSP_CHECK_LAUNCH(ctx);
     }
-    MSP_TRY(factor_shifted(ctx, G64, s, sp, true, Linv64, shift, retries));
+    // G is the Gram of the stored FP32 X itself, accumulated with compensated
+    // FP32 partial sums combined in FP64: PSD to about 2^-48 relative, so the
+    // FP64-data rule (unshifted first) applies, not the FP32 one
+    MSP_TRY(factor_shifted(ctx, G64, s, sp, false, Linv64, shift, retries));
     // G^{-1} = X^T X with X = L^{-1} (lower), FP64
     return dgemm(ctx, true, false, sp, sp, sp, 1.0, Linv64, sp, Linv64, sp, 0.0, Minv, sp);
 }
