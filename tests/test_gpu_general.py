@@ -144,7 +144,10 @@ def test_fp32_solve_and_zero_rhs(system):
     n = A32.shape[1]
     c = np.random.default_rng(15).standard_normal(n)
     x, info = g.solve(torch.from_numpy(c).cuda(), tol=1e-4, precision="fp32")
-    assert info["status"] == 0 and info["rel_resid"] <= 2e-4
+    # the FP32 recurrence residual meets tol; the true residual can differ by
+    # the FP32 rounding of the operator, about u kappa(A^T A + lam I)
+    kappa = (sig[0] ** 2 + LAM) / (np.min(sig) ** 2 + LAM)
+    assert info["status"] == 0 and info["rel_resid"] <= 1e-4 + 4 * U32 * kappa
     x0, info0 = g.solve(torch.zeros(n, dtype=torch.float64, device="cuda"))
     assert info0["status"] == 0 and not torch.any(x0)
 
