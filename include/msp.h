@@ -493,6 +493,10 @@ MSP_API msp_status msp_general_solve(msp_ctx* ctx, msp_general_t* g, const doubl
 MSP_API msp_status msp_general_solve_m1(msp_ctx* ctx, msp_general_t* g, const float* r, float* w, int t2,
                                         int t3);
 MSP_API msp_status msp_general_solve_m2(msp_ctx* ctx, msp_general_t* g, const float* r, float* z, int t3);
+/* q = (A^T A + lambda I) p in FP32, the level-1 operator: one fused pass
+ * over the rows of A (t = A p and A^T t together) and a column sum (device
+ * FP32, length n). */
+MSP_API msp_status msp_general_op(msp_ctx* ctx, msp_general_t* g, const float* p, float* q);
 /* y = (A^T A + lambda I) x with FP64 accumulation (device FP64, length n). */
 MSP_API msp_status msp_general_matvec64(msp_ctx* ctx, msp_general_t* g, const double* x, double* y);
 

@@ -210,6 +210,13 @@ class General:
         L.check(self.ctx.ptr, self.ctx.lib.msp_general_solve_m2(self.ctx.ptr, self.handle, _ptr(r), _ptr(z), t3))
         return z
 
+    def op(self, p: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """q = (A^T A + lam I) p in FP32 (the level-1 operator, one row pass)."""
+        p = p.to(torch.float32).contiguous()
+        q = out if out is not None else torch.empty_like(p)
+        L.check(self.ctx.ptr, self.ctx.lib.msp_general_op(self.ctx.ptr, self.handle, _ptr(p), _ptr(q)))
+        return q
+
     def matvec(self, x: torch.Tensor) -> torch.Tensor:
         x = x.to(torch.float64).contiguous()
         y = torch.empty_like(x)

@@ -542,31 +542,130 @@ msp_status msp_build_factor(msp_ctx* ctx, msp_factor_s* f, const void* Ct, int64
     return MSP_OK;
 }
 
-// Dense inverse of G + diag I with G = X^T X (X: rows x s_pad FP32 row-major,
-// pad columns zero): FP64 Gram (split-K, compensated), Cholesky (shifted
-// only on failure), then G^{-1} = L^{-T} L^{-1} in FP64 (full symmetric,
-// pad block identity). G64 receives G + diag I before the shift. An FP32
-// copy of the inverse would perturb its products by about 2^-24 kappa(G).
-msp_status msp_gram_inverse(msp_ctx* ctx, const float* X, int64_t rows, int64_t s, int64_t sp,
-                            double diag, double* G64, double* Linv64, double* Minv,
-                            double* shift, int* retries) {
-    {
-        void* scr = nullptr;
-        MSP_TRY(msp_scratch(ctx, (size_t)kGramSlices * sp * sp * 8, &scr));
-        double* P = (double*)scr;
-        const int nt = (int)(sp / 64);
-        dim3 grid((unsigned)(nt * (nt + 1) / 2), kGramSlices);
-        k_gram<float><<<grid, 256, 0, ctx->stream>>>(X, rows, sp, sp, P);
-        MSP_CHECK_LAUNCH(ctx);
-        k_gram_finish<float><<<(unsigned)((sp * sp + 255) / 256), 256, 0, ctx->stream>>>(
-            P, nullptr, diag, s, sp, G64);
-        MSP_CHECK_LAUNCH(ctx);
-    }
-    // G is the Gram of the stored FP32 X itself, accumulated with compensated
-    // FP32 partial sums combined in FP64: PSD to about 2^-48 relative, so the
-    // FP64-data rule (unshifted first) applies, not the FP32 one
-    MSP_TRY(factor_shifted(ctx, G64, s, sp, false, Linv64, shift, retries));
-    // G^{-1} = X^T X with X = L^{-1} (lower), FP64
+// G64 = X^T X + diag I over the leading s columns of X (rows x ld FP32
+// row-major, columns s..s_pad-1 zero): split-K partial Grams with compensated
+// FP32 sums, combined in FP64 in a fixed order; pad block identity.
+msp_status msp_gram64(msp_ctx* ctx, const float* X, int64_t rows, int64_t ld, int64_t s, int64_t sp,
+                      double diag, double* G64) {
+    void* scr = nullptr;
+    MSP_TRY(msp_scratch(ctx, (size_t)kGramSlices * sp * sp * 8, &scr));
+    double* P = (double*)scr;
+    const int nt = (int)(sp / 64);
+    dim3 grid((unsigned)(nt * (nt + 1) / 2), kGramSlices);
+    k_gram<float><<<grid, 256, 0, ctx->stream>>>(X, rows, ld, sp, P);
+    MSP_CHECK_LAUNCH(ctx);
+    k_gram_finish<float><<<(unsigned)((sp * sp + 255) / 256), 256, 0, ctx->stream>>>(P, nullptr, diag, s, sp,
+                                                                                      G64);
+    MSP_CHECK_LAUNCH(ctx);
+    return MSP_OK;
+}
+
+// Minv = M^{-1} (dense FP64) for an SPD s_pad x s_pad M64: FP64 Cholesky,
+// shifted only on failure (the FP64-data rule), then L^{-T} L^{-1}.
+msp_status msp_spd_inverse(msp_ctx* ctx, const double* M64, int64_t s, int64_t sp, double* Linv64,
+                           double* Minv, double* shift, int* retries) {
+    MSP_TRY(factor_shifted(ctx, M64, s, sp, false, Linv64, shift, retries));
     return dgemm(ctx, true, false, sp, sp, sp, 1.0, Linv64, sp, Linv64, sp, 0.0, Minv, sp);
 }
 
+// Dense inverse of G + diag I with G = X^T X. G is the Gram of the stored
+// FP32 X itself, accumulated with compensated FP32 partial sums combined in
+// FP64: PSD to about 2^-48 relative, so the FP64-data shift rule (unshifted
+// first) applies. An FP32 copy of the inverse would perturb its products by
+// about 2^-24 kappa(G), so the inverse stays FP64. G64 receives G + diag I.
+msp_status msp_gram_inverse(msp_ctx* ctx, const float* X, int64_t rows, int64_t s, int64_t sp,
+                            double diag, double* G64, double* Linv64, double* Minv,
+                            double* shift, int* retries) {
+    MSP_TRY(msp_gram64(ctx, X, rows, sp, s, sp, diag, G64));
+    return msp_spd_inverse(ctx, G64, s, sp, Linv64, Minv, shift, retries);
+}
+
+namespace {
+
+// Partial products P[slice][a][b] = sum_{k in slice} X[k][a] Y[k][b] for one
+// 64 x 64 output tile (blockIdx.x over tile pairs, blockIdx.y the K slice),
+// FP32 chunks of 16 accumulated with TwoSum into FP64 outputs. Columns of X
+// at or beyond ncx (of Y: ncy) read as zero.
+__global__ void __launch_bounds__(256, 4) k_gemm_tn(const float* __restrict__ X, int64_t ldx, int64_t ncx,
+                                                   const float* __restrict__ Y, int64_t ldy, int64_t ncy,
+                                                   int64_t K, int64_t ny_pad, int64_t nx_pad,
+                                                   double* __restrict__ P) {
+    __shared__ __align__(16) float As[16][64];
+    __shared__ __align__(16) float Bs[16][64];
+    const int nty = (int)(ny_pad / 64);
+    const int ta = blockIdx.x / nty, tb = blockIdx.x % nty;
+    const int64_t a0 = (int64_t)ta * 64, b0 = (int64_t)tb * 64;
+    const int64_t kper = ((K + kGramSlices - 1) / kGramSlices + 15) / 16 * 16;
+    const int64_t kbeg = (int64_t)blockIdx.y * kper;
+    const int64_t kend = min(K, kbeg + kper);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float hi[4][4], lo[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { hi[i][j] = 0.f; lo[i][j] = 0.f; }
+    for (int64_t k0 = kbeg; k0 < kend; k0 += 16) {
+        for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+            const int kk = e >> 6, cc = e & 63;
+            const bool in = (k0 + kk) < kend;
+            As[kk][cc] = (in && a0 + cc < ncx) ? X[(k0 + kk) * ldx + a0 + cc] : 0.f;
+            Bs[kk][cc] = (in && b0 + cc < ncy) ? Y[(k0 + kk) * ldy + b0 + cc] : 0.f;
+        }
+        __syncthreads();
+        float acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            const float4 va = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+            const float4 vb = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+            const float av[4] = {va.x, va.y, va.z, va.w}, bv[4] = {vb.x, vb.y, vb.z, vb.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) two_sum_add(hi[i][j], lo[i][j], acc[i][j]);
+        __syncthreads();
+    }
+    double* Ps = P + (int64_t)blockIdx.y * nx_pad * ny_pad;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            Ps[(a0 + ty * 4 + i) * ny_pad + b0 + tx * 4 + j] = (double)hi[i][j] + (double)lo[i][j];
+}
+
+__global__ void k_sum_slices_f32(const double* __restrict__ P, int64_t len, float* __restrict__ out) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= len) return;
+    double v = 0.0;
+#pragma unroll
+    for (int sl = 0; sl < kGramSlices; ++sl) v += P[(int64_t)sl * len + e];
+    out[e] = (float)v;
+}
+
+}  // namespace
+
+// C = X^T Y (FP32 nx_pad x ny_pad row-major, nx_pad and ny_pad multiples of
+// 64) for X: K x ncx (ldx) and Y: K x ncy (ldy), FP32 row-major; entries past
+// ncx / ncy are zero. Compensated FP32 chunk sums combined in FP64, rounded
+// once to FP32.
+msp_status msp_gemm_tn(msp_ctx* ctx, const float* X, int64_t ldx, int64_t ncx, const float* Y, int64_t ldy,
+                       int64_t ncy, int64_t K, int64_t nx_pad, int64_t ny_pad, float* C) {
+    void* scr = nullptr;
+    MSP_TRY(msp_scratch(ctx, (size_t)kGramSlices * nx_pad * ny_pad * 8, &scr));
+    double* P = (double*)scr;
+    dim3 grid((unsigned)((nx_pad / 64) * (ny_pad / 64)), kGramSlices);
+    k_gemm_tn<<<grid, 256, 0, ctx->stream>>>(X, ldx, ncx, Y, ldy, ncy, K, ny_pad, nx_pad, P);
+    MSP_CHECK_LAUNCH(ctx);
+    const int64_t len = nx_pad * ny_pad;
+    k_sum_slices_f32<<<(unsigned)((len + 255) / 256), 256, 0, ctx->stream>>>(P, len, C);
+    MSP_CHECK_LAUNCH(ctx);
+    return MSP_OK;
+}

@@ -352,6 +352,14 @@ struct msp_general_s {
     int G = 0;
     int64_t rows_per_cta = 0;
     int64_t ldp = 0;                // row stride of the partials: max(n_pad, s_pad)
+    // direct modes: W = A~^T A~, M2^{-1} = (W^{-1} - (W + lam~ I)^{-1}) / lam~
+    // (level 3 exact); C = A^T A~ and (C^T C + lam~ W)^{-1} (level 2 exact)
+    double* W64 = nullptr;
+    double* M2inv = nullptr;
+    float* Cm = nullptr;            // n64 x s_pad FP32
+    double* Binv = nullptr;
+    float* zeros = nullptr;         // s_pad zeros
+    int64_t n64 = 0;
     cudaStream_t cap = nullptr;     // private stream the SolveM1 graph is captured on
     cudaGraphExec_t m1_exec = nullptr;
     int m1_t2 = -1, m1_t3 = -1;
@@ -362,17 +370,32 @@ namespace {
 
 using G_t = msp_general_s;
 
+// rows [0, rows) split into `ctas` contiguous ranges of rows_per_cta
+struct RowGrid {
+    int64_t rows, rows_per_cta;
+    int ctas;
+};
+
+RowGrid make_grid(int64_t rows, int num_sms) {
+    RowGrid rg;
+    rg.rows = rows;
+    int G = (int)std::min<int64_t>(2 * num_sms, (rows + kRows - 1) / kRows);
+    rg.rows_per_cta = round_up((rows + G - 1) / G, kRows);
+    rg.ctas = (int)((rows + rg.rows_per_cta - 1) / rg.rows_per_cta);
+    return rg;
+}
+
 template <typename Acc, bool kSame>
-msp_status launch_rowpass_nv(msp_ctx* ctx, cudaStream_t strm, G_t* g, const float* X, int64_t ldx, int nx4, const float* Y,
-                             int64_t ldy, int ny4, const Acc* a, const Acc* z, Acc beta, Acc* tout,
-                             Acc* part, int64_t ldp, int* count) {
+msp_status launch_rowpass_rg(msp_ctx* ctx, cudaStream_t strm, const RowGrid& rg, const float* X, int64_t ldx,
+                             int nx4, const float* Y, int64_t ldy, int ny4, const Acc* a, const Acc* z, Acc beta,
+                             Acc* tout, Acc* part, int64_t ldp, int* count) {
     const size_t smem = (size_t)nx4 * 4 * sizeof(Acc);
     const int nv = (ny4 + kThreads - 1) / kThreads;
 #define MSP_RP(NVV)                                                                                     \
     case NVV: {                                                                                         \
         auto kern = k_rowpass<Acc, NVV, kSame>;                                                         \
-        kern<<<g->G, kThreads, smem, strm>>>(X, ldx, nx4, Y, ldy, ny4, g->m, g->rows_per_cta, a,        \
-                                                    z, beta, tout, part, ldp);                          \
+        kern<<<rg.ctas, kThreads, smem, strm>>>(X, ldx, nx4, Y, ldy, ny4, rg.rows, rg.rows_per_cta, a,  \
+                                                z, beta, tout, part, ldp);                              \
         break;                                                                                          \
     }
     switch (nv <= 1 ? 1 : nv <= 2 ? 2 : nv <= 4 ? 4 : 8) {
@@ -385,6 +408,15 @@ msp_status launch_rowpass_nv(msp_ctx* ctx, cudaStream_t strm, G_t* g, const floa
     MSP_CHECK_LAUNCH(ctx);
     if (count) ++*count;
     return MSP_OK;
+}
+
+template <typename Acc, bool kSame>
+msp_status launch_rowpass_nv(msp_ctx* ctx, cudaStream_t strm, G_t* g, const float* X, int64_t ldx, int nx4,
+                             const float* Y, int64_t ldy, int ny4, const Acc* a, const Acc* z, Acc beta, Acc* tout,
+                             Acc* part, int64_t ldp, int* count) {
+    const RowGrid rg{g->m, g->rows_per_cta, g->G};
+    return launch_rowpass_rg<Acc, kSame>(ctx, strm, rg, X, ldx, nx4, Y, ldy, ny4, a, z, beta, tout, part, ldp,
+                                         count);
 }
 
 template <typename Acc>
@@ -405,8 +437,9 @@ msp_status set_rowpass_attrs(msp_ctx* ctx, size_t smem) {
 // out = alpha (sum of the pass over the rows) + beta w + v
 template <typename Acc>
 msp_status colsum(msp_ctx* ctx, cudaStream_t strm, G_t* g, const Acc* part, int64_t ldp, int ny, double alpha, const Acc* w,
-                  double beta, const Acc* v, Acc* out, int* count) {
-    k_colsum<Acc><<<(unsigned)((ny + 31) / 32), 256, 0, strm>>>(part, ldp, g->G, ny, alpha, w, beta, v, out);
+                  double beta, const Acc* v, Acc* out, int* count, int ctas = 0) {
+    k_colsum<Acc><<<(unsigned)((ny + 31) / 32), 256, 0, strm>>>(part, ldp, ctas ? ctas : g->G, ny, alpha, w, beta,
+                                                              v, out);
     MSP_CHECK_LAUNCH(ctx);
     if (count) ++*count;
     return MSP_OK;
@@ -449,6 +482,27 @@ struct Ops {
                                                  0.f, nullptr, g->part, ldp(), count)));
         const double il = 1.0 / g->lam_tilde;
         return colsum<float>(ctx, strm, g, g->part, ldp(), (int)g->n_pad, -il, r, il, nullptr, w, count);
+    }
+    // Algorithm 4 with the level-2 system solved exactly through the formed
+    // C = A^T A~: w = (r - C (C^T C + lam~ W)^{-1} C^T r) / lam~
+    msp_status solve_m1_direct(const float* r, float* w) {
+        const RowGrid rg = make_grid(g->n_pad, ctx->num_sms);
+        const int ns4 = (int)(g->s_pad / 4);
+        // h = C^T r: row combination with t_j = r_j (zero row dots)
+        MSP_TRY((launch_rowpass_rg<float, true>(ctx, strm, rg, g->Cm, g->s_pad, ns4, g->Cm, g->s_pad, ns4, g->zeros,
+                                                r, 1.f, nullptr, g->part, ldp(), count)));
+        MSP_TRY(colsum<float>(ctx, strm, g, g->part, ldp(), (int)g->s_pad, 1.0, nullptr, 0.0, nullptr, g->g2, count,
+                              rg.ctas));
+        MSP_TRY(dense(g->Binv, g->g2, g->y2));
+        // t = C y (row dots only), w = (r - t) / lam~
+        MSP_TRY((launch_rowpass_rg<float, true>(ctx, strm, rg, g->Cm, g->s_pad, ns4, g->Cm, g->s_pad, 0, g->y2,
+                                                nullptr, 0.f, g->vn, g->part, ldp(), count)));
+        const int np = (int)g->n_pad;
+        const float il = (float)(1.0 / g->lam_tilde);
+        k_axpby<<<(unsigned)((np + 255) / 256), 256, 0, strm>>>(np, il, r, -il, g->vn, w);
+        MSP_CHECK_LAUNCH(ctx);
+        if (count) ++*count;
+        return MSP_OK;
     }
     // q = A~^T A~ p + shift p  (level 3)
     msp_status op3(const float* p, float* q, double shift) {
@@ -493,8 +547,9 @@ struct Ops {
         }
         return MSP_OK;
     }
-    // Algorithm 5: z = (u - v) / lam~
+    // Algorithm 5: z = (u - v) / lam~ (t3 = 0: the exact M2^{-1} r)
     msp_status solve_m2(const float* r, float* z, int t3) {
+        if (t3 == 0) return dense(g->M2inv, r, z);
         MSP_TRY(level3(r, g->u3, g->M3a, 0.0, t3));
         MSP_TRY(level3(r, g->v3, g->M3b, g->lam_tilde, t3));
         const int sp = (int)g->s_pad;
@@ -507,6 +562,7 @@ struct Ops {
     // Algorithm 4: t2 flexible PCG steps on the level-2 system, SolveM2 as
     // the preconditioner, then w = (r - A^T A~ y) / lam~
     msp_status solve_m1(const float* r, float* w, int t2, int t3) {
+        if (t2 == 0) return solve_m1_direct(r, w);
         const int sp = (int)g->s_pad;
         Pcg* sc = g->sc + 1;
         MSP_TRY(sketch_rhs(r, g->g2));
@@ -530,11 +586,115 @@ void destroy_general(G_t* g) {
     if (g->m1_exec) cudaGraphExecDestroy(g->m1_exec);
     cudaStream_t s = g->stream;
     for (void* p : {(void*)g->A_copy, (void*)g->At, (void*)g->M3a, (void*)g->M3b, (void*)g->G3a, (void*)g->G3b,
-                    (void*)g->Linv, g->work})
+                    (void*)g->Linv, g->work, (void*)g->W64, (void*)g->M2inv, (void*)g->Cm, (void*)g->Binv,
+                    (void*)g->zeros})
         if (p) cudaFreeAsync(p, s);
     if (g->host) cudaFreeHost(g->host);
     if (g->cap) cudaStreamDestroy(g->cap);
     delete g;
+}
+
+__global__ void k_diag_add64(const double* __restrict__ W, double d, int64_t s, int64_t sp, double* __restrict__ out) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= sp * sp) return;
+    const int64_t a = e / sp, b = e % sp;
+    out[e] = W[e] + ((a == b && a < s) ? d : 0.0);
+}
+
+// out = (X - Y) / d on the leading s x s block, identity on the pad
+__global__ void k_diff_scale64(const double* __restrict__ X, const double* __restrict__ Y, double inv_d, int64_t s,
+                               int64_t sp, double* __restrict__ out) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= sp * sp) return;
+    const int64_t a = e / sp, b = e % sp;
+    out[e] = (a < s && b < s) ? (X[e] - Y[e]) * inv_d : (a == b ? 1.0 : 0.0);
+}
+
+// B = G + lam~ W on the leading block (G's pad is already identity)
+__global__ void k_add_scaled64(double* __restrict__ G, double lt, const double* __restrict__ W, int64_t s, int64_t sp) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= sp * sp) return;
+    const int64_t a = e / sp, b = e % sp;
+    if (a < s && b < s) G[e] += lt * W[e];
+}
+
+msp_status ensure_w64(msp_ctx* ctx, G_t* g) {
+    if (g->W64) return MSP_OK;
+    const int64_t sp = g->s_pad;
+    MSP_TRY(msp_alloc(ctx, (void**)&g->W64, (size_t)sp * sp * 8));
+    return msp_gram64(ctx, g->At, g->m, sp, g->s, sp, 0.0, g->W64);
+}
+
+// level 3 exact: M2^{-1} = (W^{-1} - (W + lam~ I)^{-1}) / lam~ (Section 5)
+msp_status ensure_direct3(msp_ctx* ctx, G_t* g) {
+    if (g->M2inv) return MSP_OK;
+    MSP_TRY(ensure_w64(ctx, g));
+    const int64_t sp = g->s_pad, mat = sp * sp;
+    double* tmp = nullptr;
+    MSP_TRY(msp_alloc(ctx, (void**)&tmp, (size_t)mat * 3 * 8));
+    double *Wi = tmp, *Wb = tmp + mat, *Wbi = tmp + 2 * mat;
+    double sh = 0.0;
+    int rt = 0;
+    const unsigned nb = (unsigned)((mat + 255) / 256);
+    msp_status st = msp_spd_inverse(ctx, g->W64, g->s, sp, g->Linv, Wi, &sh, &rt);
+    if (st == MSP_OK) {
+        k_diag_add64<<<nb, 256, 0, ctx->stream>>>(g->W64, g->lam_tilde, g->s, sp, Wb);
+        st = cudaGetLastError() == cudaSuccess ? MSP_OK : msp_set_error(ctx, MSP_ECUDA, "general: launch failed");
+        ++ctx->launches;
+    }
+    if (st == MSP_OK) st = msp_spd_inverse(ctx, Wb, g->s, sp, g->Linv, Wbi, &sh, &rt);
+    if (st == MSP_OK) st = msp_alloc(ctx, (void**)&g->M2inv, (size_t)mat * 8);
+    if (st == MSP_OK) {
+        k_diff_scale64<<<nb, 256, 0, ctx->stream>>>(Wi, Wbi, 1.0 / g->lam_tilde, g->s, sp, g->M2inv);
+        st = cudaGetLastError() == cudaSuccess ? MSP_OK : msp_set_error(ctx, MSP_ECUDA, "general: launch failed");
+        ++ctx->launches;
+    }
+    cudaFreeAsync(tmp, ctx->stream);
+    if (st != MSP_OK && g->M2inv) {
+        cudaFreeAsync(g->M2inv, ctx->stream);
+        g->M2inv = nullptr;
+    }
+    return st;
+}
+
+// level 2 exact: C = A^T A~ (n64 x s_pad) and (C^T C + lam~ W)^{-1}
+msp_status ensure_direct2(msp_ctx* ctx, G_t* g) {
+    if (g->Binv) return MSP_OK;
+    MSP_TRY(ensure_w64(ctx, g));
+    const int64_t sp = g->s_pad, mat = sp * sp;
+    g->n64 = round_up(g->n, 64);
+    if (!g->Cm) {
+        MSP_TRY(msp_alloc(ctx, (void**)&g->Cm, (size_t)g->n64 * sp * 4));
+        MSP_TRY(msp_gemm_tn(ctx, g->A, g->lda, g->n, g->At, sp, sp, g->m, g->n64, sp, g->Cm));
+    }
+    if (!g->zeros) {
+        MSP_TRY(msp_alloc(ctx, (void**)&g->zeros, (size_t)sp * 4));
+        MSP_CUDA_TRY(ctx, cudaMemsetAsync(g->zeros, 0, (size_t)sp * 4, ctx->stream));
+    }
+    double* B = nullptr;
+    MSP_TRY(msp_alloc(ctx, (void**)&B, (size_t)mat * 8));
+    double sh = 0.0;
+    int rt = 0;
+    msp_status st = msp_gram64(ctx, g->Cm, g->n64, sp, g->s, sp, 0.0, B);
+    if (st == MSP_OK) {
+        k_add_scaled64<<<(unsigned)((mat + 255) / 256), 256, 0, ctx->stream>>>(B, g->lam_tilde, g->W64, g->s, sp);
+        st = cudaGetLastError() == cudaSuccess ? MSP_OK : msp_set_error(ctx, MSP_ECUDA, "general: launch failed");
+        ++ctx->launches;
+    }
+    if (st == MSP_OK) st = msp_alloc(ctx, (void**)&g->Binv, (size_t)mat * 8);
+    if (st == MSP_OK) st = msp_spd_inverse(ctx, B, g->s, sp, g->Linv, g->Binv, &sh, &rt);
+    cudaFreeAsync(B, ctx->stream);
+    if (st != MSP_OK && g->Binv) {
+        cudaFreeAsync(g->Binv, ctx->stream);
+        g->Binv = nullptr;
+    }
+    return st;
+}
+
+msp_status ensure_direct(msp_ctx* ctx, G_t* g, int t2, int t3) {
+    if (t2 == 0) return ensure_direct2(ctx, g);
+    if (t3 == 0) return ensure_direct3(ctx, g);
+    return MSP_OK;
 }
 
 // SolveM1 for the handle's (t2, t3) as a CUDA graph, rebuilt when they change
@@ -574,6 +734,7 @@ msp_status ensure_m1_graph(msp_ctx* ctx, G_t* g, int t2, int t3) {
 }
 
 msp_status run_m1(msp_ctx* ctx, G_t* g, int t2, int t3) {
+    MSP_TRY(ensure_direct(ctx, g, t2, t3));
     MSP_TRY(ensure_m1_graph(ctx, g, t2, t3));
     MSP_CUDA_TRY(ctx, cudaGraphLaunch(g->m1_exec, ctx->stream));
     ctx->launches += g->m1_kernels;
@@ -875,8 +1036,9 @@ msp_status msp_general_solve_m2(msp_ctx* ctx, msp_general_t* g, const float* r, 
     if (!ctx || !g) return msp_set_error(ctx, MSP_EINVAL, "general: NULL argument");
     MSP_TRY(check_vec_args(ctx, r));
     MSP_TRY(check_vec_args(ctx, z));
-    if (t3 < 1 || t3 > 1000) return msp_set_error(ctx, MSP_EINVAL, "general: need 1 <= t3 <= 1000");
+    if (t3 < 0 || t3 > 1000) return msp_set_error(ctx, MSP_EINVAL, "general: need 0 <= t3 <= 1000");
     msp::DeviceGuard guard(ctx->device);
+    if (t3 == 0) MSP_TRY(ensure_direct3(ctx, g));
     const int sp = (int)g->s_pad;
     k_pad_copy_32<<<(unsigned)((sp + 255) / 256), 256, 0, ctx->stream>>>(sp, (int)g->s, r, g->r2);
     MSP_CHECK_LAUNCH(ctx);
@@ -890,14 +1052,31 @@ msp_status msp_general_solve_m1(msp_ctx* ctx, msp_general_t* g, const float* r, 
     if (!ctx || !g) return msp_set_error(ctx, MSP_EINVAL, "general: NULL argument");
     MSP_TRY(check_vec_args(ctx, r));
     MSP_TRY(check_vec_args(ctx, w));
-    if (t2 < 1 || t2 > 1000 || t3 < 1 || t3 > 1000)
-        return msp_set_error(ctx, MSP_EINVAL, "general: need 1 <= t2, t3 <= 1000");
+    if (t2 < 0 || t2 > 1000 || t3 < 0 || t3 > 1000)
+        return msp_set_error(ctx, MSP_EINVAL, "general: need 0 <= t2, t3 <= 1000");
     msp::DeviceGuard guard(ctx->device);
     const int np = (int)g->n_pad;
     k_pad_copy_32<<<(unsigned)((np + 255) / 256), 256, 0, ctx->stream>>>(np, (int)g->n, r, g->r1);
     MSP_CHECK_LAUNCH(ctx);
     MSP_TRY(run_m1(ctx, g, t2, t3));
     MSP_CUDA_TRY(ctx, cudaMemcpyAsync(w, g->z1, (size_t)g->n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+    return MSP_OK;
+}
+
+msp_status msp_general_op(msp_ctx* ctx, msp_general_t* g, const float* p, float* q) {
+    if (!ctx || !g) return msp_set_error(ctx, MSP_EINVAL, "general: NULL argument");
+    MSP_TRY(check_vec_args(ctx, p));
+    MSP_TRY(check_vec_args(ctx, q));
+    msp::DeviceGuard guard(ctx->device);
+    const int np = (int)g->n_pad;
+    if (p != g->p1) {
+        k_pad_copy_32<<<(unsigned)((np + 255) / 256), 256, 0, ctx->stream>>>(np, (int)g->n, p, g->p1);
+        MSP_CHECK_LAUNCH(ctx);
+    }
+    Ops ops{ctx, g, nullptr, ctx->stream};
+    MSP_TRY(ops.op1(g->p1, g->q1));
+    if (q != g->q1)
+        MSP_CUDA_TRY(ctx, cudaMemcpyAsync(q, g->q1, (size_t)g->n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
     return MSP_OK;
 }
 
@@ -922,11 +1101,11 @@ msp_status msp_general_solve(msp_ctx* ctx, msp_general_t* g, const double* c, do
     msp_opts o;
     if (opts) o = *opts;
     else msp_default_opts(&o);
-    if (!(o.tol > 0.0) || o.max_outer < 1 || o.level2_iters < 1 || o.level2_iters > 1000 || o.level3_iters < 1 ||
+    if (!(o.tol > 0.0) || o.max_outer < 1 || o.level2_iters < 0 || o.level2_iters > 1000 || o.level3_iters < 0 ||
         o.level3_iters > 1000 || (o.precision != MSP_PREC_MIXED && o.precision != MSP_PREC_FP32) ||
         o.criterion != MSP_STOP_RESIDUAL || (o.precision == MSP_PREC_MIXED && !(o.refine_tol > 0.0)))
         return msp_set_error(ctx, MSP_EINVAL,
-                             "general: need tol > 0, max_outer >= 1, 1 <= level2_iters, level3_iters <= 1000, "
+                             "general: need tol > 0, max_outer >= 1, 0 <= level2_iters, level3_iters <= 1000, "
                              "precision MIXED or FP32, the residual criterion");
     msp::DeviceGuard guard(ctx->device);
     msp_info inf;

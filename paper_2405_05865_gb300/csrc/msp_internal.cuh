@@ -260,6 +260,14 @@ msp_status msp_norm_lb_launch(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t
 
 // factor.cu
 msp_status msp_build_factor(msp_ctx* ctx, msp_factor_s* f, const void* Ct, int64_t phi_rows);
+// G64 = X^T X + diag I (FP64, pad identity); M^{-1} of an SPD FP64 matrix;
+// C = X^T Y (FP32, compensated) -- see factor.cu
+msp_status msp_gram64(msp_ctx* ctx, const float* X, int64_t rows, int64_t ld, int64_t s, int64_t sp,
+                      double diag, double* G64);
+msp_status msp_spd_inverse(msp_ctx* ctx, const double* M64, int64_t s, int64_t sp, double* Linv64,
+                           double* Minv, double* shift, int* retries);
+msp_status msp_gemm_tn(msp_ctx* ctx, const float* X, int64_t ldx, int64_t ncx, const float* Y, int64_t ldy,
+                       int64_t ncy, int64_t K, int64_t nx_pad, int64_t ny_pad, float* C);
 // (X^T X + diag I)^{-1} as a dense FP64 s_pad x s_pad matrix (see factor.cu)
 msp_status msp_gram_inverse(msp_ctx* ctx, const float* X, int64_t rows, int64_t s, int64_t sp,
                             double diag, double* G64, double* Linv64, double* Minv,

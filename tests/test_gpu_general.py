@@ -111,6 +111,46 @@ def test_solve_m1_matches_oracle(system):
     assert err <= 4 * U32 * amp, (err, 4 * U32 * amp)
 
 
+def test_solve_m2_direct_matches_exact(system):
+    """level3_iters = 0: M2^{-1} = (W^{-1} - (W + lam~ I)^{-1}) / lam~ applied
+    exactly, against the oracle's dense solve with W^2 + lam~ W."""
+    A32, sig, lam0, g, p, st = system
+    r = np.random.default_rng(17).standard_normal(p.s).astype(np.float32)
+    z = g.solve_m2(torch.from_numpy(r).cuda(), 0).cpu().numpy().astype(np.float64)
+    ref = general.solve_m2(st, r.astype(np.float64), general.GenParams(s=p.s, lam0=lam0, level3="exact"))
+    W = st.At.T @ st.At
+    amp = 1.0 + np.linalg.eigvalsh(W)[-1] / st.lam_tilde
+    err = np.linalg.norm(z - ref) / np.linalg.norm(ref)
+    assert err <= 4 * U32 * amp, (err, 4 * U32 * amp)
+
+
+def test_solve_m1_direct_matches_exact(system):
+    """level2_iters = 0: C = A^T A~ formed, M^{-1} r by the Woodbury form with
+    (C^T C + lam~ W)^{-1}, against the oracle's exact level 2."""
+    A32, sig, lam0, g, p, st = system
+    n = A32.shape[1]
+    r = np.random.default_rng(18).standard_normal(n).astype(np.float32)
+    w = g.solve_m1(torch.from_numpy(r).cuda(), 0, 0).cpu().numpy().astype(np.float64)
+    ref = general.solve_m1(st, r.astype(np.float64), general.GenParams(s=p.s, lam0=lam0, level2="exact"))
+    W = st.At.T @ st.At
+    amp = (1.0 + np.linalg.eigvalsh(W)[-1] / st.lam_tilde) * (1.0 + sig[0] ** 2 / st.lam_tilde)
+    err = np.linalg.norm(w - ref) / np.linalg.norm(ref)
+    assert err <= 4 * U32 * amp, (err, 4 * U32 * amp)
+
+
+@pytest.mark.parametrize("t2,t3", [(8, 0), (0, 0)])
+def test_full_solve_direct_modes(system, t2, t3):
+    A32, sig, lam0, g, p, st = system
+    A64 = A32.astype(np.float64)
+    n = A32.shape[1]
+    c = np.random.default_rng(19).standard_normal(n)
+    x, info = g.solve(torch.from_numpy(c).cuda(), tol=1e-10, refine_tol=1e-3, level2_iters=t2, level3_iters=t3)
+    x = x.cpu().numpy()
+    r = c - (A64.T @ (A64 @ x) + LAM * x)
+    assert info["status"] == 0
+    assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(c)
+
+
 def test_matvec64(system):
     A32, sig, lam0, g, p, st = system
     A64 = A32.astype(np.float64)
@@ -120,6 +160,20 @@ def test_matvec64(system):
     # FP64 accumulation of m + n terms per entry
     bound = 4 * (A32.shape[0] + A32.shape[1]) * 2.0 ** -53 * (np.abs(A64).T @ (np.abs(A64) @ np.abs(x)))
     assert np.all(np.abs(y - ref) <= bound + LAM * np.abs(x) * 2.0 ** -52)
+
+
+def test_op_fp32(system):
+    A32, sig, lam0, g, p, st = system
+    A64 = A32.astype(np.float64)
+    x = np.random.default_rng(16).standard_normal(A32.shape[1]).astype(np.float32)
+    y = g.op(torch.from_numpy(x).cuda()).cpu().numpy().astype(np.float64)
+    x64 = x.astype(np.float64)
+    ref = A64.T @ (A64 @ x64) + LAM * x64
+    # FP32: row dots of n terms, then sums of m products (the partials per
+    # CTA in FP32, combined in FP64), each entry within (n + m) u |A|^T (|A| |x|)
+    m, n = A32.shape
+    bound = (n + m) * U32 * (np.abs(A64).T @ (np.abs(A64) @ np.abs(x64))) + 4 * U32 * LAM * np.abs(x64)
+    assert np.all(np.abs(y - ref) <= bound)
 
 
 def test_full_solve_reaches_tolerance(system):
