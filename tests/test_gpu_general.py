@@ -218,7 +218,7 @@ def test_bad_arguments(ctx):
     A2 = torch.randn((200, 40), dtype=torch.float32, device="cuda")
     g = ctx.general(A2, 1e-2, 16)
     with pytest.raises(MspError):
-        g.solve(torch.ones(40, dtype=torch.float64, device="cuda"), level2_iters=0)
+        g.solve(torch.ones(40, dtype=torch.float64, device="cuda"), level2_iters=-1)
     with pytest.raises(MspError):
         g.solve(torch.ones(40, dtype=torch.float64, device="cuda"), criterion="backward")
     g.close()
