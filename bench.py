@@ -68,6 +68,10 @@ def parse():
     ap.add_argument("--no-schatten", action="store_true")
     ap.add_argument("--no-effdim", action="store_true")
     ap.add_argument("--no-general", action="store_true")
+    ap.add_argument("--general-m", type=int, default=65536, help="rows of A in the general section")
+    ap.add_argument("--general-n", type=int, default=4096, help="columns of A in the general section")
+    ap.add_argument("--general-modes", default="three_level,exact_level3,exact_level2",
+                    help="comma-separated subset of three_level, exact_level3, exact_level2")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=5, help="level-1 iterations in the CPU sample")
     ap.add_argument("--batch-count", type=int, default=64, help="instances of the batched workload")
@@ -261,7 +265,7 @@ def run_general(args, ctx, dev, rank, peak):
     import torch
     import workloads
 
-    m, n, k = 65536, 4096, 32
+    m, n, k = args.general_m, args.general_n, 32
     d = workloads.householder_spectrum(n, k, 3 + rank, hi=1e2, lo=1e1)
     A = torch.from_numpy(workloads.tall_matrix(m, n, d, 3 + rank)).to(dev)
     lam, l = 1e-3, 2 * k
@@ -285,7 +289,10 @@ def run_general(args, ctx, dev, rank, peak):
     alg = float(m) * n * 4
     op_gbs = alg / (op_ms * 1e-3) / 1e9
     modes = {}
+    wanted = set(args.general_modes.split(","))
     for name, t2, t3, reps in (("three_level", 8, 8, 1), ("exact_level3", 8, 0, 1), ("exact_level2", 0, 0, 5)):
+        if name not in wanted:
+            continue
         o = dict(tol=1e-10, refine_tol=1e-4 if t2 == 0 else 1e-3, level2_iters=t2, level3_iters=t3)
         x, info = g.solve(c, raise_on_noconv=False, **o)
         e0.record(stream)
