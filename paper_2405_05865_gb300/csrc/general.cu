@@ -51,12 +51,6 @@ __device__ __forceinline__ Acc warp_sum_t(Acc v) {
     return v;
 }
 
-// Bring `bytes` (a multiple of 16, 16-byte aligned source) into L2 with one
-// bulk prefetch: no registers, no scoreboard, the copy engine fetches it.
-__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
 template <typename Acc, int NV, bool kSame>
 __global__ void __launch_bounds__(kThreads, 2) k_rowpass(
     const float* __restrict__ X, int64_t ldx, int nx4, const float* __restrict__ Y, int64_t ldy,
@@ -74,19 +68,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_rowpass(
     const int64_t r1 = min(m, r0 + rows_per_cta);
     const float* Ys = kSame ? X : Y;
     const int64_t ldys = kSame ? ldx : ldy;
-    // rows of the next group are prefetched into L2 while this group is
-    // folded (phase 2 reads L2 only), so HBM keeps streaming
-    auto prefetch_group = [&](int64_t g0) {
-        const int64_t pr = g0 + warp;
-        if (lane == 0 && pr < r1) {
-            prefetch_l2(X + pr * ldx, (unsigned)nx4 * 16u);
-            if (!kSame && ny4 > 0) prefetch_l2(Y + pr * ldy, (unsigned)ny4 * 16u);
-        }
-    };
-    prefetch_group(r0);
     __syncthreads();
     for (int64_t g = r0; g < r1; g += kRows) {
-        prefetch_group(g + kRows);
         const int64_t r = g + warp;
         Acc t = Acc(0);
         if (r < r1) {
