@@ -22,6 +22,7 @@
 // it is captured once into a CUDA graph and replayed per level-1 iteration.
 // The level-3 preconditioners M3a^{-1}, M3b^{-1} are dense FP64 s x s
 // inverses of the sketched Grams (FP64 Cholesky), applied by a dense mat-vec.
+#include "bulk.cuh"
 #include "msp_internal.cuh"
 
 #include <cmath>
@@ -124,6 +125,175 @@ __global__ void __launch_bounds__(kThreads, 2) k_rowpass(
             pp[4 * c + 1] = acc[k][1];
             pp[4 * c + 2] = acc[k][2];
             pp[4 * c + 3] = acc[k][3];
+        }
+    }
+}
+
+// The same pass with X = Y, the rows staged in shared memory: a producer warp
+// streams groups of R contiguous-row copies (cp.async.bulk, one per row) into
+// a ring of kRing stages guarded by mbarriers; the 8 worker warps take the row
+// dots from shared memory (R < 8: 8/R warps per row, column slices combined in
+// a fixed order), then fold the same rows into the per-CTA partial sums. HBM
+// sees each row once and nothing is re-read through L2. One CTA per SM.
+// Every wait is bounded: a timeout sets *err, the workers leave together
+// (a shared flag read after a barrier), and the producer waits for its
+// copies in flight before the block exits.
+constexpr int kRing = 3;
+constexpr int kWorkerThreads = 256;
+constexpr size_t kRingHdr = 128;       // mbarriers and the abort flag
+constexpr size_t kRingSaOff = 768;     // after 64 + 8 t values of up to 8 bytes
+constexpr uint32_t kRingStageMax = 64 * 1024;
+
+__host__ __device__ constexpr size_t ring_a_bytes(int nx4, size_t acc) { return ((size_t)nx4 * 4 * acc + 127) / 128 * 128; }
+
+struct RingShape {
+    int rows;            // R, rows per stage
+    int wpr;             // warps per row in the dots (R < 8), else 1
+    uint32_t row_bytes;  // nx4 * 16
+    uint32_t stage_bytes;
+};
+
+template <typename Acc, int NV>
+__global__ void __launch_bounds__(kWorkerThreads + 32, 1) k_rowpass_ring(
+    const float* __restrict__ X, int64_t ldx, int nx4, int64_t m, int64_t rows_per_cta, RingShape sh,
+    const Acc* __restrict__ a, const Acc* __restrict__ z, Acc beta, Acc* __restrict__ tout,
+    Acc* __restrict__ part, int64_t ldp, int* err) {
+    extern __shared__ __align__(128) unsigned char ring_smem[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(ring_smem);
+    uint64_t* empty = full + kRing;
+    int* abort_flag = reinterpret_cast<int*>(empty + kRing);
+    Acc* st = reinterpret_cast<Acc*>(ring_smem + kRingHdr);             // up to 64 t values
+    Acc* sp = st + 64;                                                 // 8 partial dots
+    Acc* sa = reinterpret_cast<Acc*>(ring_smem + kRingSaOff);
+    unsigned char* ring = ring_smem + kRingSaOff + ring_a_bytes(nx4, sizeof(Acc));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
+    const int64_t r1 = min(m, r0 + rows_per_cta);
+    const int ngroups = (int)((r1 - r0 + sh.rows - 1) / sh.rows);
+    if (tid == 0) {
+        for (int s = 0; s < kRing; ++s) {
+            msp::mbar_init(&full[s], 1);
+            msp::mbar_init(&empty[s], 1);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int i = tid; i < nx4 * 4; i += blockDim.x) sa[i] = a[i];
+    __syncthreads();
+
+    if (warp == 8) {
+        // ---- producer
+        if (lane == 0) {
+            uint32_t k = 0;
+            for (int gi = 0; gi < ngroups; ++gi, ++k) {
+                const int s = (int)(k % kRing);
+                if (k >= (uint32_t)kRing && !msp::mbar_wait_timed(&empty[s], ((k / kRing) & 1u) ^ 1u, err)) break;
+                const int64_t g0 = r0 + (int64_t)gi * sh.rows;
+                const int nr = (int)min((int64_t)sh.rows, r1 - g0);
+                unsigned char* dst = ring + (size_t)s * sh.stage_bytes;
+                msp::mbar_arrive_expect_tx(&full[s], (uint32_t)nr * sh.row_bytes);
+                for (int r = 0; r < nr; ++r)
+                    msp::bulk_g2s(dst + (size_t)r * sh.row_bytes, X + (g0 + r) * ldx, sh.row_bytes, &full[s]);
+            }
+            // every issued copy lands before the block exits
+            const uint32_t kb = k > (uint32_t)kRing ? k - kRing : 0u;
+            for (uint32_t q = kb; q < k; ++q)
+                if (!msp::mbar_wait_timed(&full[q % kRing], (q / kRing) & 1u, err)) break;
+        }
+        return;
+    }
+
+    // ---- workers
+    Acc acc[NV][4];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = Acc(0);
+    for (int gi = 0; gi < ngroups; ++gi) {
+        const int s = gi % kRing;
+        const uint32_t par = (uint32_t)(gi / kRing) & 1u;
+        if (!msp::mbar_wait_timed(&full[s], par, err) && lane == 0) atomicExch(abort_flag, 1);
+        msp::bar_workers<kWorkerThreads>();
+        if (*(volatile int*)abort_flag) break;
+        const int64_t g0 = r0 + (int64_t)gi * sh.rows;
+        const int nr = (int)min((int64_t)sh.rows, r1 - g0);
+        const float4* rows4 = reinterpret_cast<const float4*>(ring + (size_t)s * sh.stage_bytes);
+        // row dots
+        if (sh.wpr > 1) {
+            const int row = warp / sh.wpr, part_i = warp % sh.wpr;
+            const int per = (nx4 + sh.wpr - 1) / sh.wpr;
+            const int c0 = part_i * per, c1 = min(nx4, c0 + per);
+            Acc tp = Acc(0);
+            if (row < nr) {
+                const float4* xr = rows4 + (size_t)row * nx4;
+#pragma unroll 4
+                for (int c = c0 + lane; c < c1; c += 32) {
+                    const float4 v = xr[c];
+                    tp = fma_acc(v.x, sa[4 * c + 0], tp);
+                    tp = fma_acc(v.y, sa[4 * c + 1], tp);
+                    tp = fma_acc(v.z, sa[4 * c + 2], tp);
+                    tp = fma_acc(v.w, sa[4 * c + 3], tp);
+                }
+            }
+            tp = warp_sum_t(tp);
+            if (lane == 0) sp[warp] = tp;
+            msp::bar_workers<kWorkerThreads>();
+            if (tid < nr) {
+                Acc tv = Acc(0);
+                for (int q = 0; q < sh.wpr; ++q) tv += sp[tid * sh.wpr + q];
+                const int64_t r = g0 + tid;
+                tv += z ? beta * z[r] : Acc(0);
+                if (tout) tout[r] = tv;
+                st[tid] = tv;
+            }
+        } else {
+            for (int row = warp; row < nr; row += 8) {
+                const float4* xr = rows4 + (size_t)row * nx4;
+                Acc tp = Acc(0);
+#pragma unroll 4
+                for (int c = lane; c < nx4; c += 32) {
+                    const float4 v = xr[c];
+                    tp = fma_acc(v.x, sa[4 * c + 0], tp);
+                    tp = fma_acc(v.y, sa[4 * c + 1], tp);
+                    tp = fma_acc(v.z, sa[4 * c + 2], tp);
+                    tp = fma_acc(v.w, sa[4 * c + 3], tp);
+                }
+                tp = warp_sum_t(tp);
+                if (lane == 0) {
+                    const int64_t r = g0 + row;
+                    tp += z ? beta * z[r] : Acc(0);
+                    if (tout) tout[r] = tp;
+                    st[row] = tp;
+                }
+            }
+        }
+        msp::bar_workers<kWorkerThreads>();
+        // fold the stage's rows
+        for (int row = 0; row < nr; ++row) {
+            const Acc tr = st[row];
+            const float4* yr = rows4 + (size_t)row * nx4;
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                const int c = tid + q * kWorkerThreads;
+                if (c < nx4) {
+                    const float4 v = yr[c];
+                    acc[q][0] = fma_acc(v.x, tr, acc[q][0]);
+                    acc[q][1] = fma_acc(v.y, tr, acc[q][1]);
+                    acc[q][2] = fma_acc(v.z, tr, acc[q][2]);
+                    acc[q][3] = fma_acc(v.w, tr, acc[q][3]);
+                }
+            }
+        }
+        msp::bar_workers<kWorkerThreads>();
+        if (tid == 0) msp::mbar_arrive(&empty[s]);
+    }
+    Acc* pp = part + (int64_t)blockIdx.x * ldp;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        const int c = tid + q * kWorkerThreads;
+        if (c < nx4) {
+            pp[4 * c + 0] = acc[q][0];
+            pp[4 * c + 1] = acc[q][1];
+            pp[4 * c + 2] = acc[q][2];
+            pp[4 * c + 3] = acc[q][3];
         }
     }
 }
@@ -434,6 +604,75 @@ msp_status set_rowpass_attrs(msp_ctx* ctx, size_t smem) {
     return MSP_OK;
 }
 
+// Ring shape for rows of nx4 float4: R rows per stage within kRingStageMax
+// and the shared-memory budget; R < 8 is a power of two (8/R warps per row).
+// Returns false when not even one row fits (the caller uses k_rowpass).
+bool ring_shape(int nx4, size_t acc, size_t smem_optin, RingShape* sh, size_t* smem) {
+    const uint32_t rb = (uint32_t)nx4 * 16u;
+    const size_t fixed = kRingSaOff + ring_a_bytes(nx4, acc);
+    if (smem_optin <= fixed) return false;
+    const size_t per_stage = std::min<size_t>(kRingStageMax, (smem_optin - fixed) / kRing / 128 * 128);
+    int R = (int)(per_stage / rb);
+    if (R < 1) return false;
+    if (R >= 8) R = std::min(R, 64);
+    else R = R >= 4 ? 4 : R >= 2 ? 2 : 1;
+    sh->rows = R;
+    sh->wpr = R >= 8 ? 1 : 8 / R;
+    sh->row_bytes = rb;
+    sh->stage_bytes = (uint32_t)(((size_t)R * rb + 127) / 128 * 128);
+    *smem = fixed + (size_t)kRing * sh->stage_bytes;
+    return true;
+}
+
+template <typename Acc>
+msp_status set_ring_attrs(msp_ctx* ctx) {
+    const int lim = (int)ctx->smem_optin;
+#define MSP_RG(NVV)                                                                                        \
+    MSP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_rowpass_ring<Acc, NVV>,                                     \
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    MSP_RG(1)
+    MSP_RG(2)
+    MSP_RG(4)
+    MSP_RG(8)
+#undef MSP_RG
+    return MSP_OK;
+}
+
+// The X = Y pass over rows [0, rows) of X: the staged ring when a row fits,
+// else k_rowpass. `max_ctas` bounds the grid (rows of the partials buffer).
+template <typename Acc>
+msp_status launch_same(msp_ctx* ctx, cudaStream_t strm, int max_ctas, int64_t rows, const float* X, int64_t ldx,
+                       int nx4, const Acc* a, const Acc* z, Acc beta, Acc* tout, Acc* part, int64_t ldp, int* err,
+                       int* count, int* ctas_used) {
+    RingShape sh;
+    size_t smem = 0;
+    if (nx4 > 0 && ring_shape(nx4, sizeof(Acc), ctx->smem_optin, &sh, &smem)) {
+        const int ctas = (int)std::max<int64_t>(1, std::min<int64_t>(std::min(ctx->num_sms, max_ctas),
+                                                                      (rows + sh.rows - 1) / sh.rows));
+        const int64_t rpc = (rows + ctas - 1) / ctas;
+        const int nv = (nx4 + kWorkerThreads - 1) / kWorkerThreads;
+#define MSP_RL(NVV)                                                                                     \
+    case NVV:                                                                                           \
+        k_rowpass_ring<Acc, NVV><<<ctas, kWorkerThreads + 32, smem, strm>>>(X, ldx, nx4, rows, rpc, sh, a, z, \
+                                                                             beta, tout, part, ldp, err);  \
+        break;
+        switch (nv <= 1 ? 1 : nv <= 2 ? 2 : nv <= 4 ? 4 : 8) {
+            MSP_RL(1)
+            MSP_RL(2)
+            MSP_RL(4)
+            MSP_RL(8)
+        }
+#undef MSP_RL
+        MSP_CHECK_LAUNCH(ctx);
+        if (count) ++*count;
+        *ctas_used = (int)((rows + rpc - 1) / rpc);
+        return MSP_OK;
+    }
+    const RowGrid rg = make_grid(rows, ctx->num_sms);
+    *ctas_used = rg.ctas;
+    return launch_rowpass_rg<Acc, true>(ctx, strm, rg, X, ldx, nx4, X, ldx, nx4, a, z, beta, tout, part, ldp, count);
+}
+
 // out = alpha (sum of the pass over the rows) + beta w + v
 template <typename Acc>
 msp_status colsum(msp_ctx* ctx, cudaStream_t strm, G_t* g, const Acc* part, int64_t ldp, int ny, double alpha, const Acc* w,
@@ -457,9 +696,11 @@ struct Ops {
 
     // q = (A^T A + lam I) p  (level 1)
     msp_status op1(const float* p, float* q) {
-        MSP_TRY((launch_rowpass_nv<float, true>(ctx, strm, g, g->A, g->lda, na4(), g->A, g->lda, na4(), p, nullptr, 0.f,
-                                                nullptr, g->part, ldp(), count)));
-        return colsum<float>(ctx, strm, g, g->part, ldp(), (int)g->n_pad, 1.0, p, g->lambda, nullptr, q, count);
+        int used = 0;
+        MSP_TRY(launch_same<float>(ctx, strm, g->G, g->m, g->A, g->lda, na4(), p, nullptr, 0.f, nullptr, g->part,
+                                   ldp(), g->err, count, &used));
+        return colsum<float>(ctx, strm, g, g->part, ldp(), (int)g->n_pad, 1.0, p, g->lambda, nullptr, q, count,
+                             used);
     }
     // out = A~^T (A r)
     msp_status sketch_rhs(const float* r, float* out) {
@@ -489,10 +730,11 @@ struct Ops {
         const RowGrid rg = make_grid(g->n_pad, ctx->num_sms);
         const int ns4 = (int)(g->s_pad / 4);
         // h = C^T r: row combination with t_j = r_j (zero row dots)
-        MSP_TRY((launch_rowpass_rg<float, true>(ctx, strm, rg, g->Cm, g->s_pad, ns4, g->Cm, g->s_pad, ns4, g->zeros,
-                                                r, 1.f, nullptr, g->part, ldp(), count)));
+        int used = 0;
+        MSP_TRY(launch_same<float>(ctx, strm, rg.ctas, g->n_pad, g->Cm, g->s_pad, ns4, g->zeros, r, 1.f, nullptr,
+                                   g->part, ldp(), g->err, count, &used));
         MSP_TRY(colsum<float>(ctx, strm, g, g->part, ldp(), (int)g->s_pad, 1.0, nullptr, 0.0, nullptr, g->g2, count,
-                              rg.ctas));
+                              used));
         MSP_TRY(dense(g->Binv, g->g2, g->y2));
         // t = C y (row dots only), w = (r - t) / lam~
         MSP_TRY((launch_rowpass_rg<float, true>(ctx, strm, rg, g->Cm, g->s_pad, ns4, g->Cm, g->s_pad, 0, g->y2,
@@ -506,9 +748,10 @@ struct Ops {
     }
     // q = A~^T A~ p + shift p  (level 3)
     msp_status op3(const float* p, float* q, double shift) {
-        MSP_TRY((launch_rowpass_nv<float, true>(ctx, strm, g, g->At, g->s_pad, ns4(), g->At, g->s_pad, ns4(), p, nullptr,
-                                                0.f, nullptr, g->part, ldp(), count)));
-        return colsum<float>(ctx, strm, g, g->part, ldp(), (int)g->s_pad, 1.0, p, shift, nullptr, q, count);
+        int used = 0;
+        MSP_TRY(launch_same<float>(ctx, strm, g->G, g->m, g->At, g->s_pad, ns4(), p, nullptr, 0.f, nullptr, g->part,
+                                   ldp(), g->err, count, &used));
+        return colsum<float>(ctx, strm, g, g->part, ldp(), (int)g->s_pad, 1.0, p, shift, nullptr, q, count, used);
     }
     msp_status dense(const double* M, const float* v, float* out) {
         const int sp = (int)g->s_pad;
@@ -794,10 +1037,11 @@ msp_status level1(msp_ctx* ctx, G_t* g, double tol, int maxit, int t2, int t3, i
 // out = sgn (A^T A + lam I) x64 + v, FP64 accumulation
 msp_status apply64(msp_ctx* ctx, G_t* g, double sgn, const double* v, double* out) {
     const int na4 = (int)(g->n_pad / 4);
-    MSP_TRY((launch_rowpass_nv<double, true>(ctx, ctx->stream, g, g->A, g->lda, na4, g->A, g->lda, na4, g->x64, nullptr, 0.0,
-                                             nullptr, g->part64, g->n_pad, nullptr)));
-    return colsum<double>(ctx, ctx->stream, g, g->part64, g->n_pad, (int)g->n_pad, sgn, g->x64, sgn * g->lambda, v, out,
-                          nullptr);
+    int used = 0;
+    MSP_TRY(launch_same<double>(ctx, ctx->stream, g->G, g->m, g->A, g->lda, na4, g->x64, nullptr, 0.0, nullptr,
+                                g->part64, g->n_pad, g->err, nullptr, &used));
+    return colsum<double>(ctx, ctx->stream, g, g->part64, g->n_pad, (int)g->n_pad, sgn, g->x64, sgn * g->lambda, v,
+                          out, nullptr, used);
 }
 
 // r64 = c64 - (A^T A + lam I) x64
@@ -807,8 +1051,12 @@ msp_status norm64(msp_ctx* ctx, G_t* g, const double* v, double* out) {
     k_norm2_64<<<1, kVecThreads, 0, ctx->stream>>>((int)g->n_pad, v, g->d64);
     MSP_CHECK_LAUNCH(ctx);
     MSP_CUDA_TRY(ctx, cudaMemcpyAsync(g->host + 10, g->d64, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    MSP_CUDA_TRY(ctx, cudaMemcpyAsync(g->host + 11, g->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     *out = std::sqrt(g->host[10]);
+    int e = 0;
+    std::memcpy(&e, g->host + 11, sizeof(int));
+    if (e != 0) return msp_set_error(ctx, (msp_status)e, "general: device error %d (a bounded wait timed out)", e);
     return MSP_OK;
 }
 
@@ -982,7 +1230,8 @@ msp_status msp_general_create(msp_ctx* ctx, const float* A, int64_t m, int64_t n
         g->sc = (Pcg*)(w + o_sc);
         g->err = (int*)(w + o_err);
     }
-    if ((st = set_rowpass_attrs<float>(ctx, (size_t)std::max(np, sp) * 4)) != MSP_OK ||
+    if ((st = set_ring_attrs<float>(ctx)) != MSP_OK || (st = set_ring_attrs<double>(ctx)) != MSP_OK ||
+        (st = set_rowpass_attrs<float>(ctx, (size_t)std::max(np, sp) * 4)) != MSP_OK ||
         (st = set_rowpass_attrs<double>(ctx, (size_t)np * 8)) != MSP_OK)
         return fail(st);
     if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
