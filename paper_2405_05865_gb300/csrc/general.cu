@@ -153,9 +153,10 @@ struct RingShape {
     uint32_t stage_bytes;
 };
 
-template <typename Acc, int NV>
+template <typename Acc, int NV, bool kSame>
 __global__ void __launch_bounds__(kWorkerThreads + 32, 1) k_rowpass_ring(
-    const float* __restrict__ X, int64_t ldx, int nx4, int64_t m, int64_t rows_per_cta, RingShape sh,
+    const float* __restrict__ X, int64_t ldx, int nx4, const float* __restrict__ Y, int64_t ldy, int ny4,
+    int64_t m, int64_t rows_per_cta, RingShape sh,
     const Acc* __restrict__ a, const Acc* __restrict__ z, Acc beta, Acc* __restrict__ tout,
     Acc* __restrict__ part, int64_t ldp, int* err) {
     extern __shared__ __align__(128) unsigned char ring_smem[];
@@ -191,9 +192,14 @@ __global__ void __launch_bounds__(kWorkerThreads + 32, 1) k_rowpass_ring(
                 const int64_t g0 = r0 + (int64_t)gi * sh.rows;
                 const int nr = (int)min((int64_t)sh.rows, r1 - g0);
                 unsigned char* dst = ring + (size_t)s * sh.stage_bytes;
-                msp::mbar_arrive_expect_tx(&full[s], (uint32_t)nr * sh.row_bytes);
+                const uint32_t yb = kSame ? 0u : (uint32_t)ny4 * 16u;
+                msp::mbar_arrive_expect_tx(&full[s], (uint32_t)nr * (sh.row_bytes + yb));
                 for (int r = 0; r < nr; ++r)
                     msp::bulk_g2s(dst + (size_t)r * sh.row_bytes, X + (g0 + r) * ldx, sh.row_bytes, &full[s]);
+                if (!kSame && yb > 0)
+                    for (int r = 0; r < nr; ++r)
+                        msp::bulk_g2s(dst + (size_t)sh.rows * sh.row_bytes + (size_t)r * yb, Y + (g0 + r) * ldy, yb,
+                                      &full[s]);
             }
             // every issued copy lands before the block exits
             const uint32_t kb = k > (uint32_t)kRing ? k - kRing : 0u;
@@ -266,14 +272,16 @@ __global__ void __launch_bounds__(kWorkerThreads + 32, 1) k_rowpass_ring(
             }
         }
         msp::bar_workers<kWorkerThreads>();
-        // fold the stage's rows
+        // fold the stage's rows (of X itself, or the staged rows of Y)
+        const float4* ybase = kSame ? rows4 : rows4 + (size_t)sh.rows * nx4;
+        const int nf4 = kSame ? nx4 : ny4;
         for (int row = 0; row < nr; ++row) {
             const Acc tr = st[row];
-            const float4* yr = rows4 + (size_t)row * nx4;
+            const float4* yr = ybase + (size_t)row * nf4;
 #pragma unroll
             for (int q = 0; q < NV; ++q) {
                 const int c = tid + q * kWorkerThreads;
-                if (c < nx4) {
+                if (c < nf4) {
                     const float4 v = yr[c];
                     acc[q][0] = fma_acc(v.x, tr, acc[q][0]);
                     acc[q][1] = fma_acc(v.y, tr, acc[q][1]);
@@ -286,10 +294,11 @@ __global__ void __launch_bounds__(kWorkerThreads + 32, 1) k_rowpass_ring(
         if (tid == 0) msp::mbar_arrive(&empty[s]);
     }
     Acc* pp = part + (int64_t)blockIdx.x * ldp;
+    const int nf4 = kSame ? nx4 : ny4;
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
         const int c = tid + q * kWorkerThreads;
-        if (c < nx4) {
+        if (c < nf4) {
             pp[4 * c + 0] = acc[q][0];
             pp[4 * c + 1] = acc[q][1];
             pp[4 * c + 2] = acc[q][2];
@@ -604,22 +613,23 @@ msp_status set_rowpass_attrs(msp_ctx* ctx, size_t smem) {
     return MSP_OK;
 }
 
-// Ring shape for rows of nx4 float4: R rows per stage within kRingStageMax
-// and the shared-memory budget; R < 8 is a power of two (8/R warps per row).
+// Ring shape for rows of nx4 float4 (plus ny4_staged of Y): R rows per stage
+// within kRingStageMax and the shared-memory budget; R < 8 takes 8/R warps
+// per row in the dots.
 // Returns false when not even one row fits (the caller uses k_rowpass).
-bool ring_shape(int nx4, size_t acc, size_t smem_optin, RingShape* sh, size_t* smem) {
+bool ring_shape(int nx4, int ny4_staged, size_t acc, size_t smem_optin, RingShape* sh, size_t* smem) {
     const uint32_t rb = (uint32_t)nx4 * 16u;
+    const uint32_t rby = (uint32_t)ny4_staged * 16u;
     const size_t fixed = kRingSaOff + ring_a_bytes(nx4, acc);
     if (smem_optin <= fixed) return false;
     const size_t per_stage = std::min<size_t>(kRingStageMax, (smem_optin - fixed) / kRing / 128 * 128);
-    int R = (int)(per_stage / rb);
+    int R = (int)(per_stage / (rb + rby));
     if (R < 1) return false;
-    if (R >= 8) R = std::min(R, 64);
-    else R = R >= 4 ? 4 : R >= 2 ? 2 : 1;
+    if (R > 64) R = 64;
     sh->rows = R;
-    sh->wpr = R >= 8 ? 1 : 8 / R;
+    sh->wpr = R >= 8 ? 1 : 8 / R;     // R = 3: 2 warps per row, warps 6 and 7 idle in the dots
     sh->row_bytes = rb;
-    sh->stage_bytes = (uint32_t)(((size_t)R * rb + 127) / 128 * 128);
+    sh->stage_bytes = (uint32_t)(((size_t)R * (rb + rby) + 127) / 128 * 128);
     *smem = fixed + (size_t)kRing * sh->stage_bytes;
     return true;
 }
@@ -628,7 +638,9 @@ template <typename Acc>
 msp_status set_ring_attrs(msp_ctx* ctx) {
     const int lim = (int)ctx->smem_optin;
 #define MSP_RG(NVV)                                                                                        \
-    MSP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_rowpass_ring<Acc, NVV>,                                     \
+    MSP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_rowpass_ring<Acc, NVV, true>,                               \
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, lim));         \
+    MSP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_rowpass_ring<Acc, NVV, false>,                              \
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
     MSP_RG(1)
     MSP_RG(2)
@@ -638,23 +650,30 @@ msp_status set_ring_attrs(msp_ctx* ctx) {
     return MSP_OK;
 }
 
-// The X = Y pass over rows [0, rows) of X: the staged ring when a row fits,
-// else k_rowpass. `max_ctas` bounds the grid (rows of the partials buffer).
+// The pass over rows [0, rows) of X (and Y): the staged ring when a row of
+// each fits, else k_rowpass. Y == X (same ld and width) streams the rows
+// once. ny4 = 0: row dots only (tout), nothing folded. `max_ctas` bounds the
+// grid (rows of the partials buffer); *ctas_used is what the column sum reads.
 template <typename Acc>
-msp_status launch_same(msp_ctx* ctx, cudaStream_t strm, int max_ctas, int64_t rows, const float* X, int64_t ldx,
-                       int nx4, const Acc* a, const Acc* z, Acc beta, Acc* tout, Acc* part, int64_t ldp, int* err,
-                       int* count, int* ctas_used) {
+msp_status launch_pass(msp_ctx* ctx, cudaStream_t strm, int max_ctas, int64_t rows, const float* X, int64_t ldx,
+                       int nx4, const float* Y, int64_t ldy, int ny4, const Acc* a, const Acc* z, Acc beta,
+                       Acc* tout, Acc* part, int64_t ldp, int* err, int* count, int* ctas_used) {
+    const bool same = (Y == X && ldy == ldx && ny4 == nx4);
     RingShape sh;
     size_t smem = 0;
-    if (nx4 > 0 && ring_shape(nx4, sizeof(Acc), ctx->smem_optin, &sh, &smem)) {
+    if (nx4 > 0 && ring_shape(nx4, same ? 0 : ny4, sizeof(Acc), ctx->smem_optin, &sh, &smem)) {
         const int ctas = (int)std::max<int64_t>(1, std::min<int64_t>(std::min(ctx->num_sms, max_ctas),
                                                                       (rows + sh.rows - 1) / sh.rows));
         const int64_t rpc = (rows + ctas - 1) / ctas;
-        const int nv = (nx4 + kWorkerThreads - 1) / kWorkerThreads;
-#define MSP_RL(NVV)                                                                                     \
-    case NVV:                                                                                           \
-        k_rowpass_ring<Acc, NVV><<<ctas, kWorkerThreads + 32, smem, strm>>>(X, ldx, nx4, rows, rpc, sh, a, z, \
-                                                                             beta, tout, part, ldp, err);  \
+        const int nv = (std::max(same ? nx4 : ny4, 1) + kWorkerThreads - 1) / kWorkerThreads;
+#define MSP_RL(NVV)                                                                                         \
+    case NVV:                                                                                               \
+        if (same)                                                                                           \
+            k_rowpass_ring<Acc, NVV, true><<<ctas, kWorkerThreads + 32, smem, strm>>>(                      \
+                X, ldx, nx4, X, ldx, nx4, rows, rpc, sh, a, z, beta, tout, part, ldp, err);                 \
+        else                                                                                                \
+            k_rowpass_ring<Acc, NVV, false><<<ctas, kWorkerThreads + 32, smem, strm>>>(                     \
+                X, ldx, nx4, Y, ldy, ny4, rows, rpc, sh, a, z, beta, tout, part, ldp, err);                 \
         break;
         switch (nv <= 1 ? 1 : nv <= 2 ? 2 : nv <= 4 ? 4 : 8) {
             MSP_RL(1)
@@ -670,7 +689,19 @@ msp_status launch_same(msp_ctx* ctx, cudaStream_t strm, int max_ctas, int64_t ro
     }
     const RowGrid rg = make_grid(rows, ctx->num_sms);
     *ctas_used = rg.ctas;
-    return launch_rowpass_rg<Acc, true>(ctx, strm, rg, X, ldx, nx4, X, ldx, nx4, a, z, beta, tout, part, ldp, count);
+    if (same)
+        return launch_rowpass_rg<Acc, true>(ctx, strm, rg, X, ldx, nx4, X, ldx, nx4, a, z, beta, tout, part, ldp,
+                                            count);
+    return launch_rowpass_rg<Acc, false>(ctx, strm, rg, X, ldx, nx4, Y, ldy, ny4, a, z, beta, tout, part, ldp,
+                                         count);
+}
+
+template <typename Acc>
+msp_status launch_same(msp_ctx* ctx, cudaStream_t strm, int max_ctas, int64_t rows, const float* X, int64_t ldx,
+                       int nx4, const Acc* a, const Acc* z, Acc beta, Acc* tout, Acc* part, int64_t ldp, int* err,
+                       int* count, int* ctas_used) {
+    return launch_pass<Acc>(ctx, strm, max_ctas, rows, X, ldx, nx4, X, ldx, nx4, a, z, beta, tout, part, ldp, err,
+                            count, ctas_used);
 }
 
 // out = alpha (sum of the pass over the rows) + beta w + v
@@ -704,25 +735,30 @@ struct Ops {
     }
     // out = A~^T (A r)
     msp_status sketch_rhs(const float* r, float* out) {
-        MSP_TRY((launch_rowpass_nv<float, false>(ctx, strm, g, g->A, g->lda, na4(), g->At, g->s_pad, ns4(), r, nullptr,
-                                                 0.f, nullptr, g->part, ldp(), count)));
-        return colsum<float>(ctx, strm, g, g->part, ldp(), (int)g->s_pad, 1.0, nullptr, 0.0, nullptr, out, count);
+        int used = 0;
+        MSP_TRY(launch_pass<float>(ctx, strm, g->G, g->m, g->A, g->lda, na4(), g->At, g->s_pad, ns4(), r, nullptr, 0.f,
+                                   nullptr, g->part, ldp(), g->err, count, &used));
+        return colsum<float>(ctx, strm, g, g->part, ldp(), (int)g->s_pad, 1.0, nullptr, 0.0, nullptr, out, count,
+                             used);
     }
     // q = (A~^T A A^T A~ + lam~ A~^T A~) y  (level 2)
     msp_status op2(const float* y, float* q) {
-        MSP_TRY((launch_rowpass_nv<float, false>(ctx, strm, g, g->At, g->s_pad, ns4(), g->A, g->lda, na4(), y, nullptr,
-                                                 0.f, g->tm, g->part, ldp(), count)));
-        MSP_TRY(colsum<float>(ctx, strm, g, g->part, ldp(), (int)g->n_pad, 1.0, nullptr, 0.0, nullptr, g->vn, count));
-        MSP_TRY((launch_rowpass_nv<float, false>(ctx, strm, g, g->A, g->lda, na4(), g->At, g->s_pad, ns4(), g->vn, g->tm,
-                                                 (float)g->lam_tilde, nullptr, g->part, ldp(), count)));
-        return colsum<float>(ctx, strm, g, g->part, ldp(), (int)g->s_pad, 1.0, nullptr, 0.0, nullptr, q, count);
+        int used = 0;
+        MSP_TRY(launch_pass<float>(ctx, strm, g->G, g->m, g->At, g->s_pad, ns4(), g->A, g->lda, na4(), y, nullptr, 0.f,
+                                   g->tm, g->part, ldp(), g->err, count, &used));
+        MSP_TRY(colsum<float>(ctx, strm, g, g->part, ldp(), (int)g->n_pad, 1.0, nullptr, 0.0, nullptr, g->vn, count,
+                              used));
+        MSP_TRY(launch_pass<float>(ctx, strm, g->G, g->m, g->A, g->lda, na4(), g->At, g->s_pad, ns4(), g->vn, g->tm,
+                                   (float)g->lam_tilde, nullptr, g->part, ldp(), g->err, count, &used));
+        return colsum<float>(ctx, strm, g, g->part, ldp(), (int)g->s_pad, 1.0, nullptr, 0.0, nullptr, q, count, used);
     }
     // w = (r - A^T (A~ y)) / lam~  (Algorithm 4 step 3)
     msp_status finish_m1(const float* y, const float* r, float* w) {
-        MSP_TRY((launch_rowpass_nv<float, false>(ctx, strm, g, g->At, g->s_pad, ns4(), g->A, g->lda, na4(), y, nullptr,
-                                                 0.f, nullptr, g->part, ldp(), count)));
+        int used = 0;
+        MSP_TRY(launch_pass<float>(ctx, strm, g->G, g->m, g->At, g->s_pad, ns4(), g->A, g->lda, na4(), y, nullptr, 0.f,
+                                   nullptr, g->part, ldp(), g->err, count, &used));
         const double il = 1.0 / g->lam_tilde;
-        return colsum<float>(ctx, strm, g, g->part, ldp(), (int)g->n_pad, -il, r, il, nullptr, w, count);
+        return colsum<float>(ctx, strm, g, g->part, ldp(), (int)g->n_pad, -il, r, il, nullptr, w, count, used);
     }
     // Algorithm 4 with the level-2 system solved exactly through the formed
     // C = A^T A~: w = (r - C (C^T C + lam~ W)^{-1} C^T r) / lam~
@@ -737,8 +773,8 @@ struct Ops {
                               used));
         MSP_TRY(dense(g->Binv, g->g2, g->y2));
         // t = C y (row dots only), w = (r - t) / lam~
-        MSP_TRY((launch_rowpass_rg<float, true>(ctx, strm, rg, g->Cm, g->s_pad, ns4, g->Cm, g->s_pad, 0, g->y2,
-                                                nullptr, 0.f, g->vn, g->part, ldp(), count)));
+        MSP_TRY(launch_pass<float>(ctx, strm, rg.ctas, g->n_pad, g->Cm, g->s_pad, ns4, g->Cm, g->s_pad, 0, g->y2,
+                                   nullptr, 0.f, g->vn, g->part, ldp(), g->err, count, &used));
         const int np = (int)g->n_pad;
         const float il = (float)(1.0 / g->lam_tilde);
         k_axpby<<<(unsigned)((np + 255) / 256), 256, 0, strm>>>(np, il, r, -il, g->vn, w);
