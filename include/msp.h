@@ -475,7 +475,8 @@ MSP_API msp_status msp_general_get(msp_ctx* ctx, const msp_general_t* g, float* 
  * (A~^T A A^T A~ + lambda~ A~^T A~) y = A~^T A r, preconditioned by SolveM2,
  * then w = (r - A^T A~ y) / lambda~), SolveM2 (Algorithm 5: opts.level3_iters
  * PCG steps on A~^T A~ u = r and on (A~^T A~ + lambda~ I) v = r,
- * preconditioned by M3a^{-1} and M3b^{-1}, then z = (u - v) / lambda~).
+ * preconditioned by M3a^{-1} and M3b^{-1}, then z = (u - v) / lambda~; the
+ * level-3 operator W = A~^T A~ is formed once in FP64, s x s).
  * Levels run in FP32 with FP64 dot products; MSP_PREC_MIXED wraps the solve
  * in FP64 refinement (r = c - (A^T A + lambda I) x accumulated in FP64, each
  * correction solved to opts.refine_tol). Stops at

@@ -16,7 +16,9 @@
 //              v = A^T (A~ y), u = A~ y     X = A~, Y = A   (u kept)
 //              A~^T (A v + lam~ u)          X = A,  Y = A~  (z = u)
 //              w = (r - A^T (A~ y)) / lam~  X = A~, Y = A
-//     SolveM2  A~^T A~ p (+ lam~ p)         X = Y = A~
+// SolveM2's two level-3 solves apply W = A~^T A~ as its formed FP64 Gram
+// (s x s, cheaper than a pass over A~ and the same operator), both in one
+// two-block launch (k_level3_pcg).
 // The inner levels run a fixed number of PCG steps (t2, t3) with all scalars
 // on the device, so one application of SolveM1 is a fixed launch sequence;
 // it is captured once into a CUDA graph and replayed per level-1 iteration.
@@ -461,6 +463,58 @@ __global__ void k_dense_mv(const double* __restrict__ M, const float* __restrict
     if (lane == 0) out[row] = (float)s;
 }
 
+// Algorithm 5 steps 2-3 in one launch: block 0 runs t3 PCG steps on
+// W u = r preconditioned by M3a^{-1}, block 1 on (W + lam~ I) v = r with
+// M3b^{-1}; W = A~^T A~ is the formed FP64 Gram (the same operator as
+// A~^T (A~ .), applied as an s x s product). Thread i owns component i
+// (s_pad <= 1024); the dense products read column i of the symmetric
+// matrices (coalesced across threads). FP64 throughout.
+__global__ void __launch_bounds__(1024) k_level3_pcg(const double* __restrict__ W, const double* __restrict__ Ma,
+                                                    const double* __restrict__ Mb, double lam_t, int sp, int t3,
+                                                    const float* __restrict__ b, float* __restrict__ u,
+                                                    float* __restrict__ v) {
+    __shared__ double red[33];
+    __shared__ double sp_[1024], sz[1024];
+    const int i = threadIdx.x;
+    const bool act = i < sp;
+    const double* M = blockIdx.x == 0 ? Ma : Mb;
+    const double shift = blockIdx.x == 0 ? 0.0 : lam_t;
+    float* out = blockIdx.x == 0 ? u : v;
+    auto mv = [&](const double* Mat, const double* vec) {
+        double s = 0.0;
+        if (act)
+            for (int j = 0; j < sp; ++j) s = fma(Mat[(int64_t)j * sp + i], vec[j], s);
+        return s;
+    };
+    double x = 0.0, r = act ? (double)b[i] : 0.0;
+    sz[i] = r;                       // stage r for the preconditioner product
+    __syncthreads();
+    double z = mv(M, sz);
+    double rz = block_sum(r * z, red);
+    double p = z;
+    for (int k = 0; k < t3; ++k) {
+        __syncthreads();
+        sp_[i] = p;
+        __syncthreads();
+        const double q = mv(W, sp_) + shift * p;
+        const double pq = block_sum(p * q, red);
+        const double alpha = (pq > 0.0 && rz != 0.0) ? rz / pq : 0.0;
+        x = fma(alpha, p, x);
+        r = fma(-alpha, q, r);
+        if (k + 1 < t3) {
+            __syncthreads();
+            sz[i] = r;
+            __syncthreads();
+            z = mv(M, sz);
+            const double rzn = block_sum(r * z, red);
+            const double beta = rz != 0.0 ? rzn / rz : 0.0;
+            p = fma(beta, p, z);
+            rz = rzn;
+        }
+    }
+    if (act) out[i] = (float)x;
+}
+
 // out = a x + b y
 __global__ void k_axpby(int len, float a, const float* __restrict__ x, float b,
                         const float* __restrict__ y, float* __restrict__ out) {
@@ -522,10 +576,10 @@ struct msp_general_s {
     void* work = nullptr;
     float *x1, *r1, *z1, *zo1, *p1, *q1, *b1;
     float *g2, *y2, *r2, *z2, *zo2, *p2, *q2;
-    float *u3, *v3, *r3, *z3, *zo3, *p3, *q3;
+    float *u3, *v3;
     float *tm, *vn, *part;
     double *part64, *x64, *r64, *c64, *d64;
-    Pcg* sc = nullptr;              // [0] level 1, [1] level 2, [2] level 3
+    Pcg* sc = nullptr;              // [0] level 1, [1] level 2
     int* err = nullptr;
     double* host = nullptr;         // pinned: 16 doubles
     int G = 0;
@@ -782,13 +836,6 @@ struct Ops {
         if (count) ++*count;
         return MSP_OK;
     }
-    // q = A~^T A~ p + shift p  (level 3)
-    msp_status op3(const float* p, float* q, double shift) {
-        int used = 0;
-        MSP_TRY(launch_same<float>(ctx, strm, g->G, g->m, g->At, g->s_pad, ns4(), p, nullptr, 0.f, nullptr, g->part,
-                                   ldp(), g->err, count, &used));
-        return colsum<float>(ctx, strm, g, g->part, ldp(), (int)g->s_pad, 1.0, p, shift, nullptr, q, count, used);
-    }
     msp_status dense(const double* M, const float* v, float* out) {
         const int sp = (int)g->s_pad;
         k_dense_mv<<<(unsigned)((sp + 7) / 8), 256, 0, strm>>>(M, v, sp, out);
@@ -809,29 +856,14 @@ struct Ops {
         return MSP_OK;
     }
 
-    // t3 PCG steps on (A~^T A~ + shift I) x = b preconditioned by the dense Minv
-    msp_status level3(const float* b, float* x, const double* Minv, double shift, int t3) {
-        const int sp = (int)g->s_pad;
-        Pcg* sc = g->sc + 2;
-        MSP_TRY(vec(0, sp, b, nullptr, x, g->r3, sc));
-        MSP_TRY(dense(Minv, g->r3, g->z3));
-        MSP_TRY(vec(1, sp, g->r3, g->z3, g->p3, g->zo3, sc));
-        for (int k = 0; k < t3; ++k) {
-            MSP_TRY(op3(g->p3, g->q3, shift));
-            MSP_TRY(vec(2, sp, g->p3, g->q3, x, g->r3, sc));
-            if (k + 1 < t3) {
-                MSP_TRY(dense(Minv, g->r3, g->z3));
-                MSP_TRY(vec(3, sp, g->r3, g->z3, g->zo3, g->p3, sc, 0));
-            }
-        }
-        return MSP_OK;
-    }
-    // Algorithm 5: z = (u - v) / lam~ (t3 = 0: the exact M2^{-1} r)
+    // Algorithm 5: z = (u - v) / lam~ (t3 = 0: the exact M2^{-1} r); both
+    // level-3 solves run in one launch on the formed W
     msp_status solve_m2(const float* r, float* z, int t3) {
         if (t3 == 0) return dense(g->M2inv, r, z);
-        MSP_TRY(level3(r, g->u3, g->M3a, 0.0, t3));
-        MSP_TRY(level3(r, g->v3, g->M3b, g->lam_tilde, t3));
         const int sp = (int)g->s_pad;
+        k_level3_pcg<<<2, 1024, 0, strm>>>(g->W64, g->M3a, g->M3b, g->lam_tilde, sp, t3, r, g->u3, g->v3);
+        MSP_CHECK_LAUNCH(ctx);
+        if (count) ++*count;
         const float il = (float)(1.0 / g->lam_tilde);
         k_axpby<<<(unsigned)((sp + 255) / 256), 256, 0, strm>>>(sp, il, g->u3, -il, g->v3, z);
         MSP_CHECK_LAUNCH(ctx);
@@ -973,7 +1005,7 @@ msp_status ensure_direct2(msp_ctx* ctx, G_t* g) {
 msp_status ensure_direct(msp_ctx* ctx, G_t* g, int t2, int t3) {
     if (t2 == 0) return ensure_direct2(ctx, g);
     if (t3 == 0) return ensure_direct3(ctx, g);
-    return MSP_OK;
+    return ensure_w64(ctx, g);
 }
 
 // SolveM1 for the handle's (t2, t3) as a CUDA graph, rebuilt when they change
@@ -1233,7 +1265,7 @@ msp_status msp_general_create(msp_ctx* ctx, const float* A, int64_t m, int64_t n
     {
         size_t off = 0;
         auto take = [&](size_t b) { const size_t o = off; off += (size_t)round_up((int64_t)b, 256); return o; };
-        size_t o1[7], o2[7], o3[7];
+        size_t o1[7], o2[7], o3[2];
         for (auto& o : o1) o = take((size_t)np * 4);
         for (auto& o : o2) o = take((size_t)sp * 4);
         for (auto& o : o3) o = take((size_t)sp * 4);
@@ -1249,12 +1281,12 @@ msp_status msp_general_create(msp_ctx* ctx, const float* A, int64_t m, int64_t n
         char* w = (char*)g->work;
         float** v1[7] = {&g->x1, &g->r1, &g->z1, &g->zo1, &g->p1, &g->q1, &g->b1};
         float** v2[7] = {&g->g2, &g->y2, &g->r2, &g->z2, &g->zo2, &g->p2, &g->q2};
-        float** v3[7] = {&g->u3, &g->v3, &g->r3, &g->z3, &g->zo3, &g->p3, &g->q3};
         for (int q = 0; q < 7; ++q) {
             *v1[q] = (float*)(w + o1[q]);
             *v2[q] = (float*)(w + o2[q]);
-            *v3[q] = (float*)(w + o3[q]);
         }
+        g->u3 = (float*)(w + o3[0]);
+        g->v3 = (float*)(w + o3[1]);
         g->tm = (float*)(w + o_tm);
         g->vn = (float*)(w + o_vn);
         g->part = (float*)(w + o_part);
@@ -1323,7 +1355,7 @@ msp_status msp_general_solve_m2(msp_ctx* ctx, msp_general_t* g, const float* r, 
     MSP_TRY(check_vec_args(ctx, z));
     if (t3 < 0 || t3 > 1000) return msp_set_error(ctx, MSP_EINVAL, "general: need 0 <= t3 <= 1000");
     msp::DeviceGuard guard(ctx->device);
-    if (t3 == 0) MSP_TRY(ensure_direct3(ctx, g));
+    MSP_TRY(t3 == 0 ? ensure_direct3(ctx, g) : ensure_w64(ctx, g));
     const int sp = (int)g->s_pad;
     k_pad_copy_32<<<(unsigned)((sp + 255) / 256), 256, 0, ctx->stream>>>(sp, (int)g->s, r, g->r2);
     MSP_CHECK_LAUNCH(ctx);
