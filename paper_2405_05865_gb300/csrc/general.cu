@@ -466,53 +466,66 @@ __global__ void k_dense_mv(const double* __restrict__ M, const float* __restrict
 // Algorithm 5 steps 2-3 in one launch: block 0 runs t3 PCG steps on
 // W u = r preconditioned by M3a^{-1}, block 1 on (W + lam~ I) v = r with
 // M3b^{-1}; W = A~^T A~ is the formed FP64 Gram (the same operator as
-// A~^T (A~ .), applied as an s x s product). Thread i owns component i
-// (s_pad <= 1024); the dense products read column i of the symmetric
-// matrices (coalesced across threads). FP64 throughout.
+// A~^T (A~ .), applied as an s x s product). Thread i < s_pad owns component
+// i; every dense product is split over 1024 / s_pad threads per component
+// (j ranges, combined in a fixed order) and reads columns of the symmetric
+// matrices (coalesced across threads). FP64 throughout; s_pad <= 1024.
 __global__ void __launch_bounds__(1024) k_level3_pcg(const double* __restrict__ W, const double* __restrict__ Ma,
                                                     const double* __restrict__ Mb, double lam_t, int sp, int t3,
                                                     const float* __restrict__ b, float* __restrict__ u,
                                                     float* __restrict__ v) {
     __shared__ double red[33];
-    __shared__ double sp_[1024], sz[1024];
-    const int i = threadIdx.x;
-    const bool act = i < sp;
+    __shared__ double vec[1024], pbuf[1024];
+    const int tid = threadIdx.x;
+    const int parts = max(1, 1024 / sp);
+    const int per = (sp + parts - 1) / parts;
+    const int ci = tid % sp, part = tid / sp;
+    const bool own = tid < sp;
     const double* M = blockIdx.x == 0 ? Ma : Mb;
     const double shift = blockIdx.x == 0 ? 0.0 : lam_t;
     float* out = blockIdx.x == 0 ? u : v;
-    auto mv = [&](const double* Mat, const double* vec) {
+    // y = Mat vec for the owner threads (vec staged in shared memory by the caller)
+    auto mv = [&](const double* Mat) {
         double s = 0.0;
-        if (act)
-            for (int j = 0; j < sp; ++j) s = fma(Mat[(int64_t)j * sp + i], vec[j], s);
-        return s;
+        if (part < parts) {
+            const int j0 = part * per, j1 = min(sp, j0 + per);
+#pragma unroll 8
+            for (int j = j0; j < j1; ++j) s = fma(Mat[(int64_t)j * sp + ci], vec[j], s);
+        }
+        pbuf[tid] = s;
+        __syncthreads();
+        double y = 0.0;
+        if (own)
+            for (int q = 0; q < parts; ++q) y += pbuf[ci + q * sp];
+        return y;
     };
-    double x = 0.0, r = act ? (double)b[i] : 0.0;
-    sz[i] = r;                       // stage r for the preconditioner product
+    double x = 0.0, r = own ? (double)b[tid] : 0.0;
+    vec[tid] = r;
     __syncthreads();
-    double z = mv(M, sz);
-    double rz = block_sum(r * z, red);
+    double z = mv(M);
+    double rz = block_sum(own ? r * z : 0.0, red);
     double p = z;
     for (int k = 0; k < t3; ++k) {
         __syncthreads();
-        sp_[i] = p;
+        vec[tid] = own ? p : 0.0;
         __syncthreads();
-        const double q = mv(W, sp_) + shift * p;
-        const double pq = block_sum(p * q, red);
+        const double q = mv(W) + shift * p;
+        const double pq = block_sum(own ? p * q : 0.0, red);
         const double alpha = (pq > 0.0 && rz != 0.0) ? rz / pq : 0.0;
         x = fma(alpha, p, x);
         r = fma(-alpha, q, r);
         if (k + 1 < t3) {
             __syncthreads();
-            sz[i] = r;
+            vec[tid] = own ? r : 0.0;
             __syncthreads();
-            z = mv(M, sz);
-            const double rzn = block_sum(r * z, red);
+            z = mv(M);
+            const double rzn = block_sum(own ? r * z : 0.0, red);
             const double beta = rz != 0.0 ? rzn / rz : 0.0;
             p = fma(beta, p, z);
             rz = rzn;
         }
     }
-    if (act) out[i] = (float)x;
+    if (own) out[tid] = (float)x;
 }
 
 // out = a x + b y
