@@ -352,18 +352,65 @@ __device__ double block_sum(double v, double* red) {
     return red[32];
 }
 
+// Compensated FP32 dot products (the FP64 pipe of this part is about 2 DFMA
+// per clock per SM, too slow for per-element FP64 on one SM): each product
+// is split exactly by FMA (TwoProd) and accumulated with TwoSum into a
+// float pair; warps combine pairs the same way and the block adds the 32
+// warp sums in FP64, in a fixed order.
+struct FF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ void ff_add_prod(FF& acc, float a, float b) {
+    const float p = a * b;
+    const float pe = fmaf(a, b, -p);
+    float s, e;
+    two_sum(acc.hi, p, s, e);
+    acc.hi = s;
+    acc.lo += e + pe;
+}
+
+__device__ double block_sum_ff(FF v, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        const float l = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        float s, e;
+        two_sum(v.hi, h, s, e);
+        v.hi = s;
+        v.lo += l + e;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[warp] = (double)v.hi + (double)v.lo;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
+        red[32] = t;
+    }
+    __syncthreads();
+    return red[32];
+}
+
 // x = 0, r = b, bb = b.b
 __global__ void k_pcg_init(int len, const float* __restrict__ b, float* __restrict__ x,
                            float* __restrict__ r, Pcg* sc) {
     __shared__ double red[33];
-    double s = 0.0;
+    FF a{0.f, 0.f};
     for (int i = threadIdx.x; i < len; i += blockDim.x) {
         const float v = b[i];
         x[i] = 0.f;
         r[i] = v;
-        s += (double)v * v;
+        ff_add_prod(a, v, v);
     }
-    s = block_sum(s, red);
+    const double s = block_sum_ff(a, red);
     if (threadIdx.x == 0) {
         sc->bb = s;
         sc->rr = s;
@@ -374,14 +421,14 @@ __global__ void k_pcg_init(int len, const float* __restrict__ b, float* __restri
 __global__ void k_pcg_start(int len, const float* __restrict__ r, const float* __restrict__ z,
                             float* __restrict__ p, float* __restrict__ zo, Pcg* sc) {
     __shared__ double red[33];
-    double s = 0.0;
+    FF a{0.f, 0.f};
     for (int i = threadIdx.x; i < len; i += blockDim.x) {
         const float v = z[i];
         p[i] = v;
         zo[i] = v;
-        s += (double)r[i] * v;
+        ff_add_prod(a, r[i], v);
     }
-    s = block_sum(s, red);
+    const double s = block_sum_ff(a, red);
     if (threadIdx.x == 0) sc->rz = s;
 }
 
@@ -390,22 +437,22 @@ __global__ void k_pcg_start(int len, const float* __restrict__ r, const float* _
 __global__ void k_pcg_step(int len, const float* __restrict__ p, const float* __restrict__ q,
                            float* __restrict__ x, float* __restrict__ r, Pcg* sc, int* err) {
     __shared__ double red[33];
-    double s = 0.0;
-    for (int i = threadIdx.x; i < len; i += blockDim.x) s += (double)p[i] * q[i];
-    const double pq = block_sum(s, red);
+    FF a{0.f, 0.f};
+    for (int i = threadIdx.x; i < len; i += blockDim.x) ff_add_prod(a, p[i], q[i]);
+    const double pq = block_sum_ff(a, red);
     const double rz = sc->rz;
     double alpha = 0.0;
     if (pq > 0.0 && isfinite(pq) && isfinite(rz)) alpha = rz / pq;
     else if (err && threadIdx.x == 0 && rz != 0.0) atomicCAS(err, 0, isfinite(pq) ? (int)MSP_ENOTPD : (int)MSP_ENONFINITE);
     const float af = (float)alpha;
-    double s2 = 0.0;
+    FF a2{0.f, 0.f};
     for (int i = threadIdx.x; i < len; i += blockDim.x) {
         x[i] = fmaf(af, p[i], x[i]);
         const float rv = fmaf(-af, q[i], r[i]);
         r[i] = rv;
-        s2 += (double)rv * rv;
+        ff_add_prod(a2, rv, rv);
     }
-    const double rr = block_sum(s2, red);
+    const double rr = block_sum_ff(a2, red);
     if (threadIdx.x == 0) {
         sc->pq = pq;
         sc->alpha = alpha;
@@ -418,14 +465,14 @@ __global__ void k_pcg_step(int len, const float* __restrict__ p, const float* __
 __global__ void k_pcg_dir(int len, const float* __restrict__ r, const float* __restrict__ z,
                           float* __restrict__ zo, float* __restrict__ p, Pcg* sc, int flexible) {
     __shared__ double red[33];
-    double s1 = 0.0, s2 = 0.0;
+    FF a1{0.f, 0.f}, a2{0.f, 0.f};
     for (int i = threadIdx.x; i < len; i += blockDim.x) {
-        const double rv = r[i];
-        s1 += rv * z[i];
-        s2 += rv * zo[i];
+        const float rv = r[i];
+        ff_add_prod(a1, rv, z[i]);
+        ff_add_prod(a2, rv, zo[i]);
     }
-    const double rzn = block_sum(s1, red);
-    const double rzo = flexible ? block_sum(s2, red) : 0.0;
+    const double rzn = block_sum_ff(a1, red);
+    const double rzo = flexible ? block_sum_ff(a2, red) : 0.0;
     const double rz = sc->rz;
     double beta = 0.0;
     if (rz != 0.0 && isfinite(rz)) beta = (rzn - rzo) / rz;
