@@ -28,4 +28,6 @@ Modules
               and the sketch size / shift rule built on it (Lemma 2.1)
 ``general``   three-level MSP for (A^T A + lam I) x = c, A rectangular:
               Algorithm 3 with SolveM1 (Algorithm 4) and SolveM2 (Algorithm 5)
+``lsq``       least squares by sketch-and-precondition with MSP inner solves
+              (the least-squares corollary of Section 3)
 """
