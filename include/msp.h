@@ -501,6 +501,36 @@ MSP_API msp_status msp_general_op(msp_ctx* ctx, msp_general_t* g, const float* p
 /* y = (A^T A + lambda I) x with FP64 accumulation (device FP64, length n). */
 MSP_API msp_status msp_general_matvec64(msp_ctx* ctx, msp_general_t* g, const double* x, double* y);
 
+/* --------------------------------------------------------- least squares */
+
+/* min_x |A x - b| for a tall A (n_rows x d, FP32 row-major on the device,
+ * lda >= d) by sketch-and-precondition (Section 3, the least-squares
+ * corollary): msp_lsq_create forms A~ = Phi A (s_ls x d, Phi an s_ls x
+ * n_rows sparse embedding with gamma_ls nonzeros per column, streams 4 and 5
+ * of `seed`) and a three-level handle on A~ (msp_general_create with
+ * lambda = 0, lambda0 > 0, s, gamma, phi, gamma_phi, seed). A must stay
+ * valid and unchanged for the life of the handle (unless it was copied).
+ * Requires 16 <= d <= 8192, d <= s_ls <= n_rows < 2^30, lambda0 > 0, and the
+ * msp_general_create conditions on (A~, s, phi). */
+typedef struct msp_general_s msp_lsq_t;
+MSP_API msp_status msp_lsq_create(msp_ctx* ctx, const float* A, int64_t n_rows, int64_t d, int64_t lda,
+                                  int64_t s_ls, int gamma_ls, double lambda0, int64_t s, int gamma, int64_t phi,
+                                  int gamma_phi, uint64_t seed, msp_lsq_t** out);
+MSP_API void msp_lsq_destroy(msp_lsq_t* h);
+/* Flexible PCG on A^T A x = A^T b (FP32, wrapped in FP64 refinement with
+ * MSP_PREC_MIXED) preconditioned by (A~^T A~)^{-1}, each application an
+ * inner solve on A~ (msp_general_solve's level-1 iteration) stopped at
+ * relative residual opts.inner_tol or opts.max_inner iterations (constant
+ * accuracy is enough, 1e-2 typical); opts.level2_iters / level3_iters select
+ * the inner solve's levels as in msp_general_solve. Stops at
+ * |A^T (b - A x)| <= opts.tol |A^T b|. b: device FP64 (n_rows), x: device
+ * FP64 (d). info (host, may be NULL): level-1 iterations, inner iterations,
+ * refinement steps, the final relative normal-equation residual (FP64);
+ * resid_norm (host, may be NULL): |A x - b| in FP64. Errors as
+ * msp_general_solve. */
+MSP_API msp_status msp_lsq_solve(msp_ctx* ctx, msp_lsq_t* h, const double* b, double* x, const msp_opts* opts,
+                                 msp_info* info, double* resid_norm);
+
 /* ------------------------------------------------- a11: RBF and adjoint */
 
 /* The Gaussian (RBF) kernel matrix of kernel ridge regression (Section 3,

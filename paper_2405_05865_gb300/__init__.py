@@ -7,11 +7,11 @@ or PyTorch fallback: without the built library or a CUDA device the API
 raises.
 """
 
-__all__ = ["Context", "Sketch", "Factor", "Batch", "General", "DEFAULT_SEED", "MspError", "params_from_effdim"]
+__all__ = ["Context", "Sketch", "Factor", "Batch", "General", "LeastSquares", "DEFAULT_SEED", "MspError", "params_from_effdim"]
 
 
 def __getattr__(name):
-    if name in ("Context", "Sketch", "Factor", "Batch", "General", "DEFAULT_SEED", "params_from_effdim"):
+    if name in ("Context", "Sketch", "Factor", "Batch", "General", "LeastSquares", "DEFAULT_SEED", "params_from_effdim"):
         from . import api
         return getattr(api, name)
     if name == "MspError":

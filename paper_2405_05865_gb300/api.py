@@ -245,6 +245,43 @@ class General:
             pass
 
 
+class LeastSquares:
+    """min |A x - b| by sketch-and-precondition with three-level inner solves
+    (msp_lsq_create). Keeps the caller's A alive."""
+
+    def __init__(self, ctx: "Context", handle: C.c_void_p, A: torch.Tensor):
+        self.ctx, self.handle, self.A = ctx, handle, A
+        self.n_rows, self.d = A.shape
+
+    def solve(self, b: torch.Tensor, raise_on_noconv: bool = True, **opts) -> tuple[torch.Tensor, dict]:
+        if not b.is_cuda or b.dtype != torch.float64 or b.shape != (self.n_rows,):
+            raise ValueError("b must be a CUDA float64 vector of length n_rows")
+        b = b.contiguous()
+        x = torch.empty(self.d, dtype=torch.float64, device=b.device)
+        opts.setdefault("inner_tol", 1e-2)
+        o = make_opts(self.ctx.lib, **opts)
+        info = L.MspInfo()
+        rn = C.c_double()
+        st = self.ctx.lib.msp_lsq_solve(self.ctx.ptr, self.handle, _ptr(b), _ptr(x), C.byref(o), C.byref(info),
+                                        C.byref(rn))
+        if st != 0 and not (st == 5 and not raise_on_noconv):
+            L.check(self.ctx.ptr, st)
+        d = info.as_dict()
+        d["resid_norm"] = rn.value
+        return x, d
+
+    def close(self) -> None:
+        if self.handle:
+            self.ctx.lib.msp_lsq_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Context:
     """An MSP context bound to one CUDA device and one stream."""
 
@@ -383,6 +420,18 @@ class Context:
                                                       s, gamma, phi if phi is not None else 4 * s, gamma_phi, seed,
                                                       C.byref(h)))
         return General(self, h, A)
+
+    # -- least squares (sketch-and-precondition, three-level inner solves)
+    def lsq(self, A: torch.Tensor, s_ls: int, lam0: float, s: int, gamma_ls: int = 4, phi: int | None = None,
+            gamma: int = 8, gamma_phi: int = 8, seed: int = DEFAULT_SEED) -> LeastSquares:
+        if not A.is_cuda or A.dtype != torch.float32 or A.dim() != 2 or A.stride(1) != 1:
+            raise ValueError("A must be a CUDA float32 (n_rows, d) tensor with unit column stride")
+        n_rows, d = A.shape
+        h = C.c_void_p()
+        L.check(self.ptr, self.lib.msp_lsq_create(self.ptr, _ptr(A), n_rows, d, A.stride(0), s_ls, gamma_ls,
+                                                  float(lam0), s, gamma, phi if phi is not None else 4 * s,
+                                                  gamma_phi, seed, C.byref(h)))
+        return LeastSquares(self, h, A)
 
     # -- effective dimension d_lambda by Hutchinson over batched solves
     def effective_dimension(self, A: torch.Tensor, lam: float, s: int, probes: int = 64, gamma: int = 8,

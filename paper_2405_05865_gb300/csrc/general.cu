@@ -653,6 +653,13 @@ struct msp_general_s {
     double* Binv = nullptr;
     float* zeros = nullptr;         // s_pad zeros
     int64_t n64 = 0;
+    // least squares: the inner handle on A~ = Phi A whose solves precondition
+    // the level-1 iteration of this handle (A^T A x = A^T b)
+    msp_general_s* inner = nullptr;
+    float* As = nullptr;            // A~ (owned), s_ls x n_pad
+    int64_t s_ls = 0;
+    double inner_tol = 1e-2;
+    int inner_maxit = 50;
     cudaStream_t cap = nullptr;     // private stream the SolveM1 graph is captured on
     cudaGraphExec_t m1_exec = nullptr;
     int m1_t2 = -1, m1_t3 = -1;
@@ -962,6 +969,8 @@ void destroy_general(G_t* g) {
         if (p) cudaFreeAsync(p, s);
     if (g->host) cudaFreeHost(g->host);
     if (g->cap) cudaStreamDestroy(g->cap);
+    if (g->inner) destroy_general(g->inner);
+    if (g->As) cudaFreeAsync(g->As, s);
     delete g;
 }
 
@@ -1128,6 +1137,29 @@ msp_status read_scalars(msp_ctx* ctx, G_t* g, const Pcg* sc, double* rr, double*
 // Level 1 (Algorithm 3 step 7): flexible PCG on (A^T A + lam I) x1 = b1 with
 // SolveM1, FP32 vectors; stops at |r| <= tol |b1| or after maxit steps.
 msp_status level1(msp_ctx* ctx, G_t* g, double tol, int maxit, int t2, int t3, int* iters, bool* conv,
+                  int* inner);
+
+// z1 = M^{-1} r1: SolveM1 (the graph), or for a least-squares handle one
+// solve with the inner handle on A~ to relative residual inner_tol (constant
+// accuracy; the level-1 iteration is flexible)
+msp_status precond(msp_ctx* ctx, G_t* g, int t2, int t3, int* inner) {
+    if (!g->inner) {
+        MSP_TRY(run_m1(ctx, g, t2, t3));
+        *inner += t2;
+        return MSP_OK;
+    }
+    G_t* h = g->inner;
+    const size_t bytes = (size_t)g->n_pad * 4;
+    MSP_CUDA_TRY(ctx, cudaMemcpyAsync(h->b1, g->r1, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    int it = 0, in2 = 0;
+    bool conv = false;
+    MSP_TRY(level1(ctx, h, g->inner_tol, g->inner_maxit, t2, t3, &it, &conv, &in2));
+    *inner += it;
+    MSP_CUDA_TRY(ctx, cudaMemcpyAsync(g->z1, h->x1, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    return MSP_OK;
+}
+
+msp_status level1(msp_ctx* ctx, G_t* g, double tol, int maxit, int t2, int t3, int* iters, bool* conv,
                   int* inner) {
     Ops ops{ctx, g, nullptr, ctx->stream};
     const int len = (int)g->n_pad;
@@ -1141,8 +1173,7 @@ msp_status level1(msp_ctx* ctx, G_t* g, double tol, int maxit, int t2, int t3, i
         *conv = true;
         return MSP_OK;
     }
-    MSP_TRY(run_m1(ctx, g, t2, t3));
-    *inner += t2;
+    MSP_TRY(precond(ctx, g, t2, t3, inner));
     MSP_TRY(ops.vec(1, len, g->r1, g->z1, g->p1, g->zo1, sc));
     for (int k = 1; k <= maxit; ++k) {
         MSP_TRY(ops.op1(g->p1, g->q1));
@@ -1155,8 +1186,7 @@ msp_status level1(msp_ctx* ctx, G_t* g, double tol, int maxit, int t2, int t3, i
             return MSP_OK;
         }
         if (k == maxit) break;
-        MSP_TRY(run_m1(ctx, g, t2, t3));
-        *inner += t2;
+        MSP_TRY(precond(ctx, g, t2, t3, inner));
         MSP_TRY(ops.vec(3, len, g->r1, g->z1, g->zo1, g->p1, sc, 1));
     }
     return MSP_OK;
@@ -1188,6 +1218,64 @@ msp_status norm64(msp_ctx* ctx, G_t* g, const double* v, double* out) {
     return MSP_OK;
 }
 
+// The level-1 solve of (A^T A + lam I) x64 = c64 (|c64| = cn > 0): FP32
+// alone (MSP_PREC_FP32), or wrapped in FP64 refinement (MSP_PREC_MIXED);
+// result MSP_ENOCONV when the tolerance was not reached.
+msp_status solve_refined(msp_ctx* ctx, G_t* g, const msp_opts& o, double cn, msp_info* inf_out,
+                         msp_status* result_out) {
+    const int t2 = o.level2_iters, t3 = o.level3_iters;
+    const int np = (int)g->n_pad;
+    const unsigned nb = (unsigned)((np + 255) / 256);
+    msp_status& result = *result_out;
+    msp_info& inf = *inf_out;
+    result = MSP_OK;
+    if (o.precision == MSP_PREC_FP32) {
+        k_scale_to_f32<<<nb, 256, 0, ctx->stream>>>(np, g->c64, 1.0 / cn, g->b1);
+        MSP_CHECK_LAUNCH(ctx);
+        int it = 0;
+        bool conv = false;
+        MSP_TRY(level1(ctx, g, o.tol, o.max_outer, t2, t3, &it, &conv, &inf.inner_iters));
+        inf.outer_iters = it;
+        MSP_CUDA_TRY(ctx, cudaMemsetAsync(g->x64, 0, (size_t)np * 8, ctx->stream));
+        k_axpy_64<<<nb, 256, 0, ctx->stream>>>(np, cn, g->x1, g->x64);
+        MSP_CHECK_LAUNCH(ctx);
+        MSP_TRY(residual64(ctx, g));
+        double rn = 0.0;
+        MSP_TRY(norm64(ctx, g, g->r64, &rn));
+        inf.rel_resid = rn / cn;
+        if (!conv) result = MSP_ENOCONV;
+    } else {
+        MSP_CUDA_TRY(ctx, cudaMemsetAsync(g->x64, 0, (size_t)np * 8, ctx->stream));
+        MSP_CUDA_TRY(ctx, cudaMemcpyAsync(g->r64, g->c64, (size_t)np * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+        double rn = cn;
+        bool done = false;
+        for (int step = 0; step < o.max_refine; ++step) {
+            if (rn <= o.tol * cn) {
+                done = true;
+                break;
+            }
+            k_scale_to_f32<<<nb, 256, 0, ctx->stream>>>(np, g->r64, 1.0 / rn, g->b1);
+            MSP_CHECK_LAUNCH(ctx);
+            int it = 0;
+            bool conv = false;
+            MSP_TRY(level1(ctx, g, o.refine_tol, o.max_outer, t2, t3, &it, &conv, &inf.inner_iters));
+            inf.outer_iters += it;
+            ++inf.refine_steps;
+            k_axpy_64<<<nb, 256, 0, ctx->stream>>>(np, rn, g->x1, g->x64);
+            MSP_CHECK_LAUNCH(ctx);
+            MSP_TRY(residual64(ctx, g));
+            const double prev = rn;
+            MSP_TRY(norm64(ctx, g, g->r64, &rn));
+            if (!std::isfinite(rn)) return msp_set_error(ctx, MSP_ENONFINITE, "general: non-finite residual");
+            if (rn >= prev && !(rn <= o.tol * cn)) break;   // refinement stalled
+        }
+        if (!done && rn <= o.tol * cn) done = true;
+        inf.rel_resid = rn / cn;
+        if (!done) result = MSP_ENOCONV;
+    }
+    return MSP_OK;
+}
+
 msp_status check_vec_args(msp_ctx* ctx, const void* p) {
     if (!p) return msp_set_error(ctx, MSP_EINVAL, "general: NULL vector");
     return MSP_OK;
@@ -1195,23 +1283,13 @@ msp_status check_vec_args(msp_ctx* ctx, const void* p) {
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-msp_status msp_general_create(msp_ctx* ctx, const float* A, int64_t m, int64_t n, int64_t lda, double lambda,
-                              double lambda0, int64_t s, int gamma, int64_t phi, int gamma_phi, uint64_t seed,
-                              msp_general_t** out) {
-    if (!ctx) return msp_set_error(nullptr, MSP_EINVAL, "ctx is NULL");
-    if (!A || !out) return msp_set_error(ctx, MSP_EINVAL, "general: NULL argument");
-    *out = nullptr;
-    if (n < 16 || n > kMaxN || m < n || m >= (1ll << 30) || lda < n || !(lambda >= 0.0) || !(lambda0 >= 0.0) ||
-        !(lambda + lambda0 > 0.0) || s < 16 || s > MSP_MAX_S || s > n || gamma < 1 || gamma > MSP_MAX_GAMMA ||
-        gamma > s || phi < s || phi > m || gamma_phi < 1 || gamma_phi > MSP_MAX_GAMMA || gamma_phi > phi)
-        return msp_set_error(ctx, MSP_EINVAL,
-                             "general: need 16 <= n <= %d, n <= m < 2^30, lda >= n, lambda, lambda0 >= 0 with "
-                             "lambda + lambda0 > 0, 16 <= s <= min(n, %d), 1 <= gamma <= min(s, %d), "
-                             "s <= phi <= m, 1 <= gamma_phi <= min(phi, %d)",
-                             kMaxN, MSP_MAX_S, MSP_MAX_GAMMA, MSP_MAX_GAMMA);
-    msp::DeviceGuard guard(ctx->device);
+// Everything but the sketch: A (or its aligned copy), the row partition, the
+// work vectors for level-1 vectors of n_pad and inner vectors of s_pad
+// (0: none), the capture stream. On failure nothing is left allocated.
+msp_status create_base(msp_ctx* ctx, const float* A, int64_t m, int64_t n, int64_t lda, double lambda,
+                       double lambda0, int64_t s_pad, G_t** out) {
     G_t* g = new (std::nothrow) G_t();
     if (!g) return msp_set_error(ctx, MSP_ENOMEM, "general: host allocation failed");
     g->stream = ctx->stream;
@@ -1219,12 +1297,7 @@ msp_status msp_general_create(msp_ctx* ctx, const float* A, int64_t m, int64_t n
     g->m = m;
     g->n = n;
     g->n_pad = round_up(n, 4);
-    g->s = s;
-    g->s_pad = round_up(s, MSP_S_ALIGN);
-    g->phi = phi;
-    g->gamma = gamma;
-    g->gamma_phi = gamma_phi;
-    g->seed = seed;
+    g->s_pad = s_pad;
     g->lambda = lambda;
     g->lambda0 = lambda0;
     g->lam_tilde = lambda + lambda0;
@@ -1242,6 +1315,7 @@ msp_status msp_general_create(msp_ctx* ctx, const float* A, int64_t m, int64_t n
     // rows must start on 16-byte boundaries for the float4 row passes
     const bool aligned = (lda % 4 == 0) && (n % 4 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
     msp_status st = MSP_OK;
+    (void)st;
     if (aligned) {
         g->A = A;
         g->lda = lda;
@@ -1268,6 +1342,64 @@ msp_status msp_general_create(msp_ctx* ctx, const float* A, int64_t m, int64_t n
         return fail(msp_set_error(ctx, MSP_ECUDA, "general: stream creation failed"));
     }
 
+    // ---- work vectors
+    {
+        size_t off = 0;
+        auto take = [&](size_t b) { const size_t o = off; off += (size_t)round_up((int64_t)b, 256); return o; };
+        size_t o1[7], o2[7], o3[2];
+        for (auto& o : o1) o = take((size_t)np * 4);
+        for (auto& o : o2) o = take((size_t)sp * 4);
+        for (auto& o : o3) o = take((size_t)sp * 4);
+        const size_t o_tm = take((size_t)m * 4), o_vn = take((size_t)np * 4);
+        const size_t o_part = take((size_t)g->G * g->ldp * 4);
+        const size_t o_p64 = take((size_t)g->G * np * 8);
+        const size_t o_x64 = take((size_t)np * 8), o_r64 = take((size_t)np * 8), o_c64 = take((size_t)np * 8);
+        const size_t o_d64 = take(64);
+        const size_t o_sc = take(sizeof(Pcg) * 3), o_err = take(16);
+        if ((st = msp_alloc(ctx, &g->work, off)) != MSP_OK) return fail(st);
+        if (cudaMemsetAsync(g->work, 0, off, ctx->stream) != cudaSuccess)
+            return fail(msp_set_error(ctx, MSP_ECUDA, "general: memset failed"));
+        char* w = (char*)g->work;
+        float** v1[7] = {&g->x1, &g->r1, &g->z1, &g->zo1, &g->p1, &g->q1, &g->b1};
+        float** v2[7] = {&g->g2, &g->y2, &g->r2, &g->z2, &g->zo2, &g->p2, &g->q2};
+        for (int q = 0; q < 7; ++q) {
+            *v1[q] = (float*)(w + o1[q]);
+            *v2[q] = (float*)(w + o2[q]);
+        }
+        g->u3 = (float*)(w + o3[0]);
+        g->v3 = (float*)(w + o3[1]);
+        g->tm = (float*)(w + o_tm);
+        g->vn = (float*)(w + o_vn);
+        g->part = (float*)(w + o_part);
+        g->part64 = (double*)(w + o_p64);
+        g->x64 = (double*)(w + o_x64);
+        g->r64 = (double*)(w + o_r64);
+        g->c64 = (double*)(w + o_c64);
+        g->d64 = (double*)(w + o_d64);
+        g->sc = (Pcg*)(w + o_sc);
+        g->err = (int*)(w + o_err);
+    }
+    if ((st = set_ring_attrs<float>(ctx)) != MSP_OK || (st = set_ring_attrs<double>(ctx)) != MSP_OK ||
+        (st = set_rowpass_attrs<float>(ctx, (size_t)std::max(np, sp) * 4)) != MSP_OK ||
+        (st = set_rowpass_attrs<double>(ctx, (size_t)np * 8)) != MSP_OK)
+        return fail(st);
+    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(msp_set_error(ctx, MSP_ECUDA, "general: set-up failed"));
+    }
+    *out = g;
+    return MSP_OK;
+}
+
+
+// Algorithm 3 steps 3-6 on a base handle: S, A~ = A S^T, A^ = Phi A~,
+// M3a = A^^T A^, M3b = M3a + lam~ I and their FP64 inverses.
+msp_status setup_sketch(msp_ctx* ctx, G_t* g) {
+    const int64_t m = g->m, n = g->n, s = g->s, sp = g->s_pad, phi = g->phi;
+    const int gamma = g->gamma, gamma_phi = g->gamma_phi;
+    const uint64_t seed = g->seed;
+    msp_status st = MSP_OK;
+    auto fail = [&](msp_status e) { return e; };
     // ---- Algorithm 3 steps 3-4: S, A~ = A S^T, A^ = Phi A~
     {
         int32_t *idx = nullptr, *ptr = nullptr, *ent = nullptr, *pptr = nullptr, *pent = nullptr;
@@ -1321,50 +1453,44 @@ msp_status msp_general_create(msp_ctx* ctx, const float* A, int64_t m, int64_t n
             return tfail(st);
         cudaFreeAsync(tmp, ctx->stream);
     }
-    // ---- work vectors
-    {
-        size_t off = 0;
-        auto take = [&](size_t b) { const size_t o = off; off += (size_t)round_up((int64_t)b, 256); return o; };
-        size_t o1[7], o2[7], o3[2];
-        for (auto& o : o1) o = take((size_t)np * 4);
-        for (auto& o : o2) o = take((size_t)sp * 4);
-        for (auto& o : o3) o = take((size_t)sp * 4);
-        const size_t o_tm = take((size_t)m * 4), o_vn = take((size_t)np * 4);
-        const size_t o_part = take((size_t)g->G * g->ldp * 4);
-        const size_t o_p64 = take((size_t)g->G * np * 8);
-        const size_t o_x64 = take((size_t)np * 8), o_r64 = take((size_t)np * 8), o_c64 = take((size_t)np * 8);
-        const size_t o_d64 = take(64);
-        const size_t o_sc = take(sizeof(Pcg) * 3), o_err = take(16);
-        if ((st = msp_alloc(ctx, &g->work, off)) != MSP_OK) return fail(st);
-        if (cudaMemsetAsync(g->work, 0, off, ctx->stream) != cudaSuccess)
-            return fail(msp_set_error(ctx, MSP_ECUDA, "general: memset failed"));
-        char* w = (char*)g->work;
-        float** v1[7] = {&g->x1, &g->r1, &g->z1, &g->zo1, &g->p1, &g->q1, &g->b1};
-        float** v2[7] = {&g->g2, &g->y2, &g->r2, &g->z2, &g->zo2, &g->p2, &g->q2};
-        for (int q = 0; q < 7; ++q) {
-            *v1[q] = (float*)(w + o1[q]);
-            *v2[q] = (float*)(w + o2[q]);
-        }
-        g->u3 = (float*)(w + o3[0]);
-        g->v3 = (float*)(w + o3[1]);
-        g->tm = (float*)(w + o_tm);
-        g->vn = (float*)(w + o_vn);
-        g->part = (float*)(w + o_part);
-        g->part64 = (double*)(w + o_p64);
-        g->x64 = (double*)(w + o_x64);
-        g->r64 = (double*)(w + o_r64);
-        g->c64 = (double*)(w + o_c64);
-        g->d64 = (double*)(w + o_d64);
-        g->sc = (Pcg*)(w + o_sc);
-        g->err = (int*)(w + o_err);
-    }
-    if ((st = set_ring_attrs<float>(ctx)) != MSP_OK || (st = set_ring_attrs<double>(ctx)) != MSP_OK ||
-        (st = set_rowpass_attrs<float>(ctx, (size_t)std::max(np, sp) * 4)) != MSP_OK ||
-        (st = set_rowpass_attrs<double>(ctx, (size_t)np * 8)) != MSP_OK)
-        return fail(st);
-    if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    return MSP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+msp_status msp_general_create(msp_ctx* ctx, const float* A, int64_t m, int64_t n, int64_t lda, double lambda,
+                              double lambda0, int64_t s, int gamma, int64_t phi, int gamma_phi, uint64_t seed,
+                              msp_general_t** out) {
+    if (!ctx) return msp_set_error(nullptr, MSP_EINVAL, "ctx is NULL");
+    if (!A || !out) return msp_set_error(ctx, MSP_EINVAL, "general: NULL argument");
+    *out = nullptr;
+    if (n < 16 || n > kMaxN || m < n || m >= (1ll << 30) || lda < n || !(lambda >= 0.0) || !(lambda0 >= 0.0) ||
+        !(lambda + lambda0 > 0.0) || s < 16 || s > MSP_MAX_S || s > n || gamma < 1 || gamma > MSP_MAX_GAMMA ||
+        gamma > s || phi < s || phi > m || gamma_phi < 1 || gamma_phi > MSP_MAX_GAMMA || gamma_phi > phi)
+        return msp_set_error(ctx, MSP_EINVAL,
+                             "general: need 16 <= n <= %d, n <= m < 2^30, lda >= n, lambda, lambda0 >= 0 with "
+                             "lambda + lambda0 > 0, 16 <= s <= min(n, %d), 1 <= gamma <= min(s, %d), "
+                             "s <= phi <= m, 1 <= gamma_phi <= min(phi, %d)",
+                             kMaxN, MSP_MAX_S, MSP_MAX_GAMMA, MSP_MAX_GAMMA);
+    msp::DeviceGuard guard(ctx->device);
+    G_t* g = nullptr;
+    MSP_TRY(create_base(ctx, A, m, n, lda, lambda, lambda0, round_up(s, MSP_S_ALIGN), &g));
+    g->s = s;
+    g->phi = phi;
+    g->gamma = gamma;
+    g->gamma_phi = gamma_phi;
+    g->seed = seed;
+    msp_status st = setup_sketch(ctx, g);
+    if (st == MSP_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
         cudaGetLastError();
-        return fail(msp_set_error(ctx, MSP_ECUDA, "general: set-up failed"));
+        st = msp_set_error(ctx, MSP_ECUDA, "general: set-up failed");
+    }
+    if (st != MSP_OK) {
+        cudaStreamSynchronize(ctx->stream);
+        destroy_general(g);
+        return st;
     }
     *out = g;
     return MSP_OK;
@@ -1498,53 +1624,8 @@ msp_status msp_general_solve(msp_ctx* ctx, msp_general_t* g, const double* c, do
     double cn = 0.0;
     MSP_TRY(norm64(ctx, g, g->c64, &cn));
     msp_status result = MSP_OK;
-    const int t2 = o.level2_iters, t3 = o.level3_iters;
-    if (cn == 0.0) {
-        MSP_CUDA_TRY(ctx, cudaMemsetAsync(x, 0, (size_t)g->n * 8, ctx->stream));
-    } else if (o.precision == MSP_PREC_FP32) {
-        k_scale_to_f32<<<nb, 256, 0, ctx->stream>>>(np, g->c64, 1.0 / cn, g->b1);
-        MSP_CHECK_LAUNCH(ctx);
-        int it = 0;
-        bool conv = false;
-        MSP_TRY(level1(ctx, g, o.tol, o.max_outer, t2, t3, &it, &conv, &inf.inner_iters));
-        inf.outer_iters = it;
-        MSP_CUDA_TRY(ctx, cudaMemsetAsync(g->x64, 0, (size_t)np * 8, ctx->stream));
-        k_axpy_64<<<nb, 256, 0, ctx->stream>>>(np, cn, g->x1, g->x64);
-        MSP_CHECK_LAUNCH(ctx);
-        MSP_TRY(residual64(ctx, g));
-        double rn = 0.0;
-        MSP_TRY(norm64(ctx, g, g->r64, &rn));
-        inf.rel_resid = rn / cn;
-        if (!conv) result = MSP_ENOCONV;
-    } else {
-        MSP_CUDA_TRY(ctx, cudaMemsetAsync(g->x64, 0, (size_t)np * 8, ctx->stream));
-        MSP_CUDA_TRY(ctx, cudaMemcpyAsync(g->r64, g->c64, (size_t)np * 8, cudaMemcpyDeviceToDevice, ctx->stream));
-        double rn = cn;
-        bool done = false;
-        for (int step = 0; step < o.max_refine; ++step) {
-            if (rn <= o.tol * cn) {
-                done = true;
-                break;
-            }
-            k_scale_to_f32<<<nb, 256, 0, ctx->stream>>>(np, g->r64, 1.0 / rn, g->b1);
-            MSP_CHECK_LAUNCH(ctx);
-            int it = 0;
-            bool conv = false;
-            MSP_TRY(level1(ctx, g, o.refine_tol, o.max_outer, t2, t3, &it, &conv, &inf.inner_iters));
-            inf.outer_iters += it;
-            ++inf.refine_steps;
-            k_axpy_64<<<nb, 256, 0, ctx->stream>>>(np, rn, g->x1, g->x64);
-            MSP_CHECK_LAUNCH(ctx);
-            MSP_TRY(residual64(ctx, g));
-            const double prev = rn;
-            MSP_TRY(norm64(ctx, g, g->r64, &rn));
-            if (!std::isfinite(rn)) return msp_set_error(ctx, MSP_ENONFINITE, "general: non-finite residual");
-            if (rn >= prev && !(rn <= o.tol * cn)) break;   // refinement stalled
-        }
-        if (!done && rn <= o.tol * cn) done = true;
-        inf.rel_resid = rn / cn;
-        if (!done) result = MSP_ENOCONV;
-    }
+    if (cn == 0.0) MSP_CUDA_TRY(ctx, cudaMemsetAsync(x, 0, (size_t)g->n * 8, ctx->stream));
+    else MSP_TRY(solve_refined(ctx, g, o, cn, &inf, &result));
     if (cn != 0.0)
         MSP_CUDA_TRY(ctx, cudaMemcpyAsync(x, g->x64, (size_t)g->n * 8, cudaMemcpyDeviceToDevice, ctx->stream));
     MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
@@ -1552,6 +1633,126 @@ msp_status msp_general_solve(msp_ctx* ctx, msp_general_t* g, const double* c, do
     if (info) *info = inf;
     if (result == MSP_ENOCONV)
         return msp_set_error(ctx, MSP_ENOCONV, "general: relative residual %.3g above tol %.3g", inf.rel_resid,
+                             o.tol);
+    return result;
+}
+
+// ------------------------------------------------------- least squares
+
+msp_status msp_lsq_create(msp_ctx* ctx, const float* A, int64_t n_rows, int64_t d, int64_t lda, int64_t s_ls,
+                          int gamma_ls, double lambda0, int64_t s, int gamma, int64_t phi, int gamma_phi,
+                          uint64_t seed, msp_lsq_t** out) {
+    if (!ctx) return msp_set_error(nullptr, MSP_EINVAL, "ctx is NULL");
+    if (!A || !out) return msp_set_error(ctx, MSP_EINVAL, "lsq: NULL argument");
+    *out = nullptr;
+    if (d < 16 || d > kMaxN || s_ls < d || n_rows < s_ls || n_rows >= (1ll << 30) || lda < d || gamma_ls < 1 ||
+        gamma_ls > MSP_MAX_GAMMA || gamma_ls > s_ls || !(lambda0 > 0.0))
+        return msp_set_error(ctx, MSP_EINVAL,
+                             "lsq: need 16 <= d <= %d, d <= s_ls <= n_rows < 2^30, lda >= d, "
+                             "1 <= gamma_ls <= min(s_ls, %d), lambda0 > 0",
+                             kMaxN, MSP_MAX_GAMMA);
+    msp::DeviceGuard guard(ctx->device);
+    G_t* g = nullptr;
+    MSP_TRY(create_base(ctx, A, n_rows, d, lda, 0.0, 0.0, 0, &g));
+    auto fail = [&](msp_status st) {
+        cudaStreamSynchronize(ctx->stream);
+        destroy_general(g);
+        return st;
+    };
+    const int64_t np = g->n_pad;
+    msp_status st = MSP_OK;
+    if ((st = msp_alloc(ctx, (void**)&g->As, (size_t)s_ls * np * 4)) != MSP_OK) return fail(st);
+    if (cudaMemsetAsync(g->As, 0, (size_t)s_ls * np * 4, ctx->stream) != cudaSuccess)
+        return fail(msp_set_error(ctx, MSP_ECUDA, "lsq: memset failed"));
+    // A~ = Phi A: Phi a sparse embedding of the n_rows rows (streams 4, 5)
+    {
+        void* tmp = nullptr;
+        size_t off = 0;
+        auto take = [&](size_t b) { const size_t o = off; off += (size_t)round_up((int64_t)b, 256); return o; };
+        const size_t o_idx = take((size_t)n_rows * gamma_ls * 4), o_sgn = take((size_t)n_rows * gamma_ls);
+        const size_t o_ptr = take((size_t)(s_ls + 1) * 4), o_ent = take((size_t)n_rows * gamma_ls * 4);
+        if ((st = msp_alloc(ctx, &tmp, off)) != MSP_OK) return fail(st);
+        char* tb = (char*)tmp;
+        int32_t* idx = (int32_t*)(tb + o_idx);
+        int8_t* sgn = (int8_t*)(tb + o_sgn);
+        int32_t* ptr = (int32_t*)(tb + o_ptr);
+        int32_t* ent = (int32_t*)(tb + o_ent);
+        if ((st = msp_pattern_launch(ctx, n_rows, s_ls, gamma_ls, seed, 4, idx, sgn, nullptr)) != MSP_OK ||
+            (st = msp_build_csr(ctx, n_rows, s_ls, gamma_ls, idx, sgn, ptr, ent)) != MSP_OK ||
+            (st = msp_gather_rows(ctx, MSP_F32, s_ls, d, ptr, ent, g->A, g->lda, 1.0 / std::sqrt((double)gamma_ls),
+                                  g->As, np)) != MSP_OK) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFreeAsync(tmp, ctx->stream);
+            return fail(st);
+        }
+        cudaFreeAsync(tmp, ctx->stream);
+    }
+    // Theorem 3.1's solver on A~ (lambda = 0, lambda~ = lambda0)
+    msp_general_t* inner = nullptr;
+    if ((st = msp_general_create(ctx, g->As, s_ls, d, np, 0.0, lambda0, s, gamma, phi, gamma_phi, seed, &inner)) !=
+        MSP_OK)
+        return fail(st);
+    g->inner = inner;
+    g->s_ls = s_ls;
+    *out = g;
+    return MSP_OK;
+}
+
+void msp_lsq_destroy(msp_lsq_t* h) { msp_general_destroy(h); }
+
+msp_status msp_lsq_solve(msp_ctx* ctx, msp_lsq_t* g, const double* b, double* x, const msp_opts* opts,
+                         msp_info* info, double* resid_norm) {
+    if (!ctx || !g || !g->inner) return msp_set_error(ctx, MSP_EINVAL, "lsq: NULL argument or not a lsq handle");
+    MSP_TRY(check_vec_args(ctx, b));
+    MSP_TRY(check_vec_args(ctx, x));
+    msp_opts o;
+    if (opts) o = *opts;
+    else msp_default_opts(&o);
+    if (!(o.tol > 0.0) || o.max_outer < 1 || o.level2_iters < 0 || o.level2_iters > 1000 || o.level3_iters < 0 ||
+        o.level3_iters > 1000 || (o.precision != MSP_PREC_MIXED && o.precision != MSP_PREC_FP32) ||
+        o.criterion != MSP_STOP_RESIDUAL || (o.precision == MSP_PREC_MIXED && !(o.refine_tol > 0.0)) ||
+        !(o.inner_tol > 0.0) || o.max_inner < 1)
+        return msp_set_error(ctx, MSP_EINVAL,
+                             "lsq: need tol, refine_tol, inner_tol > 0, max_outer, max_inner >= 1, "
+                             "0 <= level2_iters, level3_iters <= 1000, precision MIXED or FP32, the residual "
+                             "criterion");
+    msp::DeviceGuard guard(ctx->device);
+    g->inner_tol = o.inner_tol;
+    g->inner_maxit = o.max_inner;
+    msp_info inf;
+    std::memset(&inf, 0, sizeof inf);
+    inf.lambda_tilde = g->inner->lam_tilde;
+    const int np = (int)g->n_pad, na4 = np / 4;
+    MSP_CUDA_TRY(ctx, cudaMemsetAsync(g->err, 0, sizeof(int), ctx->stream));
+    MSP_CUDA_TRY(ctx, cudaMemsetAsync(g->inner->err, 0, sizeof(int), ctx->stream));
+    // c64 = A^T b in FP64 (row dots with a = 0 give t = b)
+    MSP_CUDA_TRY(ctx, cudaMemsetAsync(g->x64, 0, (size_t)np * 8, ctx->stream));
+    int used = 0;
+    MSP_TRY(launch_same<double>(ctx, ctx->stream, g->G, g->m, g->A, g->lda, na4, g->x64, b, 1.0, nullptr, g->part64,
+                                g->n_pad, g->err, nullptr, &used));
+    MSP_TRY(colsum<double>(ctx, ctx->stream, g, g->part64, g->n_pad, np, 1.0, nullptr, 0.0, nullptr, g->c64,
+                           nullptr, used));
+    double cn = 0.0;
+    MSP_TRY(norm64(ctx, g, g->c64, &cn));
+    msp_status result = MSP_OK;
+    if (cn == 0.0) {
+        MSP_CUDA_TRY(ctx, cudaMemsetAsync(g->x64, 0, (size_t)np * 8, ctx->stream));
+    } else {
+        MSP_TRY(solve_refined(ctx, g, o, cn, &inf, &result));
+    }
+    // |A x - b| in FP64: row dots t = A x - b only
+    MSP_TRY(launch_pass<double>(ctx, ctx->stream, g->G, g->m, g->A, g->lda, na4, g->A, g->lda, 0, g->x64, b, -1.0,
+                                g->part64, g->part64, g->n_pad, g->err, nullptr, &used));
+    k_norm2_64<<<1, kVecThreads, 0, ctx->stream>>>((int)g->m, g->part64, g->d64);
+    MSP_CHECK_LAUNCH(ctx);
+    MSP_CUDA_TRY(ctx, cudaMemcpyAsync(g->host + 12, g->d64, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    MSP_CUDA_TRY(ctx, cudaMemcpyAsync(x, g->x64, (size_t)g->n * 8, cudaMemcpyDeviceToDevice, ctx->stream));
+    MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    if (resid_norm) *resid_norm = std::sqrt(g->host[12]);
+    inf.status = result;
+    if (info) *info = inf;
+    if (result == MSP_ENOCONV)
+        return msp_set_error(ctx, MSP_ENOCONV, "lsq: normal-equation residual %.3g above tol %.3g", inf.rel_resid,
                              o.tol);
     return result;
 }
