@@ -321,9 +321,9 @@ def run_lsq(args, ctx, dev, rank):
     """Least squares min |A x - b| (Section 3, the least-squares corollary)
     on the general section's matrix (m = 65536, n = 4096, 1.07 GB FP32),
     b ~ N(0, I): A~ = Phi A with 4n rows (gamma 4), flexible PCG on the
-    normal equations preconditioned by inner solves on A~ to relative
-    residual 1e-2 (Theorem 3.1's solver: exact levels, and the paper's three
-    levels), to |A^T (b - A x)| <= 1e-10 |A^T b|. The time includes forming
+    normal equations preconditioned by inner solves on A~ to a constant
+    relative residual (Theorem 3.1's solver: exact levels, and the paper's
+    three levels), to |A^T (b - A x)| <= 1e-10 |A^T b|. The time includes forming
     A^T b and |A x - b| but not the sketch set-up (reported apart)."""
     import torch
     import workloads
@@ -337,14 +337,20 @@ def run_lsq(args, ctx, dev, rank):
     stream = ctx.stream
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    h = ctx.lsq(A, 4 * n, lam0, 256, phi=1024)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    setup_ms = e0.elapsed_time(e1)
+    handles = {}
+    setup_ms = {}
+    for key, l0 in (("paper", lam0), ("tenth", lam0 / 10)):
+        e0.record(stream)
+        handles[key] = ctx.lsq(A, 4 * n, l0, 256, phi=1024)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        setup_ms[key] = e0.elapsed_time(e1)
     modes = {}
-    for name, t2, t3, reps in (("inner_exact_levels", 0, 0, 3), ("inner_three_level", 8, 8, 1)):
-        o = dict(tol=1e-10, refine_tol=1e-4, inner_tol=1e-2, level2_iters=t2, level3_iters=t3)
+    for name, key, itol, t2, t3, reps in (("inner_exact_levels", "tenth", 0.3, 0, 0, 3),
+                                          ("inner_exact_levels_paper_lambda0", "paper", 1e-1, 0, 0, 3),
+                                          ("inner_three_level", "tenth", 0.3, 8, 8, 1)):
+        h = handles[key]
+        o = dict(tol=1e-10, refine_tol=1e-4, inner_tol=itol, level2_iters=t2, level3_iters=t3)
         x, info = h.solve(b, raise_on_noconv=False, **o)
         e0.record(stream)
         for _ in range(reps):
@@ -355,11 +361,13 @@ def run_lsq(args, ctx, dev, rank):
         modes[name] = {"ms_per_solve": ms, "solves_per_s": 1000.0 / ms, "status": info["status"],
                        "normal_eq_rel_resid": info["rel_resid"], "resid_norm_rel": info["resid_norm"] / float(
                            torch.linalg.vector_norm(b)), "outer_iters": info["outer_iters"],
-                       "inner_iters": info["inner_iters"], "refine_steps": info["refine_steps"]}
-    h.close()
+                       "inner_iters": info["inner_iters"], "refine_steps": info["refine_steps"],
+                       "lambda0": lam0 if key == "paper" else lam0 / 10, "inner_tol": itol}
+    for h in handles.values():
+        h.close()
     return {"workload": f"min |A x - b|, A m={m} n={n} FP32 (the general section's matrix), b ~ N(0, I); "
                         f"A~ = Phi A with {4 * n} rows (gamma 4); inner solves on A~: s=256, phi=1024, "
-                        f"lambda0={lam0:.4g}, to relative residual 1e-2; normal-equation residual 1e-10",
+                        f"lambda0 = Theorem 3.1's {lam0:.4g} or a tenth of it; normal-equation residual 1e-10",
             "setup_ms": setup_ms, "modes": modes}
 
 
