@@ -30,4 +30,6 @@ Modules
               Algorithm 3 with SolveM1 (Algorithm 4) and SolveM2 (Algorithm 5)
 ``lsq``       least squares by sketch-and-precondition with MSP inner solves
               (the least-squares corollary of Section 3)
+``schatten``  Schatten-p, p in (0, 2), from ridge solves through Balakrishnan's
+              integral representation (Section 3.2's black-box requirement)
 """
