@@ -498,8 +498,33 @@ MSP_API msp_status msp_general_solve_m2(msp_ctx* ctx, msp_general_t* g, const fl
  * over the rows of A (t = A p and A^T t together) and a column sum (device
  * FP32, length n). */
 MSP_API msp_status msp_general_op(msp_ctx* ctx, msp_general_t* g, const float* p, float* q);
+/* Change lambda and lambda0 of a general handle (lambda~ = lambda + lambda0
+ * > 0): M3b is refactored and the exact-level inverses are rebuilt when next
+ * used; A~, M3a and C = A^T A~ are kept. Errors: MSP_EINVAL, MSP_ENOTPD. */
+MSP_API msp_status msp_general_set_lambda(msp_ctx* ctx, msp_general_t* g, double lambda, double lambda0);
 /* y = (A^T A + lambda I) x with FP64 accumulation (device FP64, length n). */
 MSP_API msp_status msp_general_matvec64(msp_ctx* ctx, msp_general_t* g, const double* x, double* y);
+
+/* ------------------------------------------ Schatten-p for p in (0, 2) */
+
+/* |A + zI|_p^p (z = 0: |A|_p^p) for a general A (m x n, m >= n, FP32
+ * row-major on the device) from ridge solves (Section 3.2: eq.
+ * schatten-ridge and the random shift A + zI, z a caller-drawn scalar,
+ * square A only). With q = p/2, |A|_p^p = (sin(pi q)/pi) int_0^inf t^(q-1)
+ * d_t dt (Balakrishnan's integral for fractional powers), d_t = n - t
+ * tr((A^T A + t I)^{-1}); the trapezoidal rule in ln t on `nodes` points over
+ * [t_min, t_max] with geometric tails from d_t ~ n (t -> 0) and
+ * d_t ~ |A|_F^2 / t (t -> inf). Each d_t is a Hutchinson mean over `probes`
+ * Rademacher probes (those of msp_schatten with `seed`), each term one
+ * msp_general_solve (opts; s the sketch size, phi = min(4s, m)) with
+ * lambda = t and lambda~ = max(t, lambda_floor_rel * max_j |A e_j|^2).
+ * Cost: nodes x probes solves. estimate, std_err (host, may be NULL): the
+ * mean and standard error over probes; X (host, may be NULL, `probes`
+ * doubles): the per-probe estimates. */
+MSP_API msp_status msp_schatten_p(msp_ctx* ctx, const float* A, int64_t m, int64_t n, int64_t lda, double p,
+                                  double z, double t_min, double t_max, int nodes, int64_t probes, uint64_t seed,
+                                  int64_t s, double lambda_floor_rel, const msp_opts* opts, double* estimate,
+                                  double* std_err, double* X);
 
 /* --------------------------------------------------------- least squares */
 

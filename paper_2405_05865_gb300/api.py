@@ -223,6 +223,10 @@ class General:
         L.check(self.ctx.ptr, self.ctx.lib.msp_general_matvec64(self.ctx.ptr, self.handle, _ptr(x), _ptr(y)))
         return y
 
+    def set_lambda(self, lam: float, lam0: float = 0.0) -> None:
+        L.check(self.ctx.ptr, self.ctx.lib.msp_general_set_lambda(self.ctx.ptr, self.handle, float(lam), float(lam0)))
+        self.lambda_tilde = lam + lam0
+
     def setup(self, s: int) -> dict:
         """A~ (m x s FP32) and the FP64 Grams M3a, M3b (s x s) as device tensors."""
         dev = self.A.device
@@ -420,6 +424,23 @@ class Context:
                                                       s, gamma, phi if phi is not None else 4 * s, gamma_phi, seed,
                                                       C.byref(h)))
         return General(self, h, A)
+
+    # -- Schatten-p, p in (0, 2), from ridge solves (integral representation)
+    def schatten_p(self, A: torch.Tensor, p: float, t_min: float, t_max: float, nodes: int = 32, probes: int = 16,
+                   s: int = 64, z: float = 0.0, lambda_floor_rel: float = 1e-4, seed: int = DEFAULT_SEED,
+                   **opts) -> tuple[float, float, list[float]]:
+        """(estimate of |A + zI|_p^p, standard error, per-probe estimates)."""
+        if not A.is_cuda or A.dtype != torch.float32 or A.dim() != 2 or A.stride(1) != 1:
+            raise ValueError("A must be a CUDA float32 (m, n) tensor with unit column stride")
+        m, n = A.shape
+        o = make_opts(self.lib, **opts)
+        est, se = C.c_double(), C.c_double()
+        X = (C.c_double * probes)()
+        L.check(self.ptr, self.lib.msp_schatten_p(self.ptr, _ptr(A), m, n, A.stride(0), float(p), float(z),
+                                                  float(t_min), float(t_max), nodes, probes, seed, s,
+                                                  float(lambda_floor_rel), C.byref(o), C.byref(est), C.byref(se),
+                                                  C.cast(X, C.c_void_p)))
+        return est.value, se.value, list(X)
 
     # -- least squares (sketch-and-precondition, three-level inner solves)
     def lsq(self, A: torch.Tensor, s_ls: int, lam0: float, s: int, gamma_ls: int = 4, phi: int | None = None,

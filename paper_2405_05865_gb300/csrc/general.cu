@@ -1637,6 +1637,40 @@ msp_status msp_general_solve(msp_ctx* ctx, msp_general_t* g, const double* c, do
     return result;
 }
 
+msp_status msp_general_set_lambda(msp_ctx* ctx, msp_general_t* g, double lambda, double lambda0) {
+    if (!ctx || !g) return msp_set_error(ctx, MSP_EINVAL, "general: NULL argument");
+    if (g->inner || g->s_pad == 0 || !(lambda >= 0.0) || !(lambda0 >= 0.0) || !(lambda + lambda0 > 0.0))
+        return msp_set_error(ctx, MSP_EINVAL,
+                             "general_set_lambda: need a general handle, lambda, lambda0 >= 0, lambda + lambda0 > 0");
+    msp::DeviceGuard guard(ctx->device);
+    g->lambda = lambda;
+    g->lambda0 = lambda0;
+    const double lt = lambda + lambda0;
+    if (lt == g->lam_tilde) return MSP_OK;
+    g->lam_tilde = lt;
+    // lam~-dependent state: M3b (level 3), the exact-level inverses (rebuilt
+    // when next used) and the captured SolveM1 (its kernels take lam~)
+    const int64_t sp = g->s_pad, mat = sp * sp;
+    k_diag_add64<<<(unsigned)((mat + 255) / 256), 256, 0, ctx->stream>>>(g->G3a, lt, g->s, sp, g->G3b);
+    MSP_CHECK_LAUNCH(ctx);
+    MSP_TRY(msp_spd_inverse(ctx, g->G3b, g->s, sp, g->Linv, g->M3b, &g->shift_b, &g->retries_b));
+    if (g->M2inv) {
+        cudaFreeAsync(g->M2inv, ctx->stream);
+        g->M2inv = nullptr;
+    }
+    if (g->Binv) {
+        cudaFreeAsync(g->Binv, ctx->stream);
+        g->Binv = nullptr;
+    }
+    if (g->m1_exec) {
+        MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        cudaGraphExecDestroy(g->m1_exec);
+        g->m1_exec = nullptr;
+        g->m1_t2 = g->m1_t3 = -1;
+    }
+    return MSP_OK;
+}
+
 // ------------------------------------------------------- least squares
 
 msp_status msp_lsq_create(msp_ctx* ctx, const float* A, int64_t n_rows, int64_t d, int64_t lda, int64_t s_ls,
