@@ -517,7 +517,8 @@ MSP_API msp_status msp_general_matvec64(msp_ctx* ctx, msp_general_t* g, const do
  * d_t ~ |A|_F^2 / t (t -> inf). Each d_t is a Hutchinson mean over `probes`
  * Rademacher probes (those of msp_schatten with `seed`), each term one
  * msp_general_solve (opts; s the sketch size, phi = min(4s, m)) with
- * lambda = t and lambda~ = max(t, lambda_floor_rel * max_j |A e_j|^2).
+ * lambda = t and lambda~ = max(t, lambda_floor_rel * |A|_2^2), |A|_2^2
+ * estimated by 30 power iterations (1e-3 keeps the FP32 levels stable).
  * Cost: nodes x probes solves. estimate, std_err (host, may be NULL): the
  * mean and standard error over probes; X (host, may be NULL, `probes`
  * doubles): the per-probe estimates. */

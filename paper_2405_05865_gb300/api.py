@@ -427,7 +427,7 @@ class Context:
 
     # -- Schatten-p, p in (0, 2), from ridge solves (integral representation)
     def schatten_p(self, A: torch.Tensor, p: float, t_min: float, t_max: float, nodes: int = 32, probes: int = 16,
-                   s: int = 64, z: float = 0.0, lambda_floor_rel: float = 1e-4, seed: int = DEFAULT_SEED,
+                   s: int = 64, z: float = 0.0, lambda_floor_rel: float = 1e-3, seed: int = DEFAULT_SEED,
                    **opts) -> tuple[float, float, list[float]]:
         """(estimate of |A + zI|_p^p, standard error, per-probe estimates)."""
         if not A.is_cuda or A.dtype != torch.float32 or A.dim() != 2 or A.stride(1) != 1:

@@ -117,15 +117,46 @@ extern "C" msp_status msp_schatten_p(msp_ctx* ctx, const float* A, int64_t m, in
         fro2 += v;
         cmax = std::max(cmax, v);
     }
-    // lam~ >= lambda_floor_rel * max column norm^2 (<= |A|_2^2) keeps the
-    // FP32 levels' cancellation |A|^2 / lam~ bounded
-    const double floor = lambda_floor_rel * cmax;
     const double step = (std::log(t_max) - std::log(t_min)) / (nodes - 1);
     auto tnode = [&](int j) { return std::exp(std::log(t_min) + step * j); };
     const double t0 = tnode(0);
-    if ((st = msp_general_create(ctx, Ause, m, n, ld, t0, std::max(0.0, floor - t0), s, 8, std::min<int64_t>(4 * s, m),
-                                 8, seed, &g)) != MSP_OK)
+    // the handle starts with lam~ = |A|_F^2 >= |A|_2^2 (safe for any A)
+    if ((st = msp_general_create(ctx, Ause, m, n, ld, t0, std::max(0.0, fro2 - t0), s, 8,
+                                 std::min<int64_t>(4 * s, m), 8, seed, &g)) != MSP_OK)
         return done(st);
+    // |A|_2^2 by the power method on (A^T A + t0 I) (the estimate the shift
+    // argument of Section 3.2 also uses); lam~ >= lambda_floor_rel |A|_2^2
+    // keeps the FP32 levels' cancellation |A|^2 / lam~ bounded
+    double smax2 = cmax;
+    {
+        float* pv = nullptr;
+        if ((st = msp_alloc(ctx, (void**)&pv, (size_t)2 * n * 4)) != MSP_OK) return done(st);
+        float* qv = pv + n;
+        std::vector<float> hv(n), hq(n);
+        for (int64_t i = 0; i < n; ++i) hv[i] = (i % 3 == 0 ? 1.f : -0.5f) + 1e-3f * (float)(i % 7);
+        double lam_est = 0.0;
+        for (int it = 0; it < 30 && st == MSP_OK; ++it) {
+            double nn = 0.0;
+            for (float v : hv) nn += (double)v * v;
+            const float inv = (float)(1.0 / std::sqrt(nn));
+            for (float& v : hv) v *= inv;
+            if (cudaMemcpyAsync(pv, hv.data(), (size_t)n * 4, cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess)
+                st = msp_set_error(ctx, MSP_ECUDA, "schatten_p: copy failed");
+            if (st == MSP_OK) st = msp_general_op(ctx, g, pv, qv);
+            if (st == MSP_OK && (cudaMemcpyAsync(hq.data(), qv, (size_t)n * 4, cudaMemcpyDeviceToHost,
+                                                 ctx->stream) != cudaSuccess ||
+                                 cudaStreamSynchronize(ctx->stream) != cudaSuccess))
+                st = msp_set_error(ctx, MSP_ECUDA, "schatten_p: copy failed");
+            double r = 0.0;
+            for (int64_t i = 0; i < n; ++i) r += (double)hv[i] * hq[i];
+            lam_est = r - t0;
+            hv.swap(hq);
+        }
+        cudaFreeAsync(pv, ctx->stream);
+        if (st != MSP_OK) return done(st);
+        smax2 = std::max(smax2, lam_est);
+    }
+    const double floor = lambda_floor_rel * smax2;
     msp_opts o;
     if (opts) o = *opts;
     else msp_default_opts(&o);
