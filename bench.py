@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--no-effdim", action="store_true")
     ap.add_argument("--no-general", action="store_true")
     ap.add_argument("--no-lsq", action="store_true")
+    ap.add_argument("--no-schatten-p", action="store_true")
     ap.add_argument("--general-m", type=int, default=65536, help="rows of A in the general section")
     ap.add_argument("--general-n", type=int, default=4096, help="columns of A in the general section")
     ap.add_argument("--general-modes", default="three_level,exact_level3,exact_level2",
@@ -369,6 +370,35 @@ def run_lsq(args, ctx, dev, rank):
                         f"A~ = Phi A with {4 * n} rows (gamma 4); inner solves on A~: s=256, phi=1024, "
                         f"lambda0 = Theorem 3.1's {lam0:.4g} or a tenth of it; normal-equation residual 1e-10",
             "setup_ms": setup_ms, "modes": modes}
+
+
+def run_schatten_p(args, ctx, dev, rank):
+    """Schatten-1 of a general A (m = 16384, n = 2048, 134 MB FP32, the
+    general section's spectrum shape) from ridge solves (Section 3.2):
+    24 quadrature nodes over t in [2.5e-5, 1e8], 16 Rademacher probes, one
+    exact-level-2 solve to relative residual 1e-8 per (node, probe)."""
+    import torch
+    import workloads
+
+    m, n, k = 16384, 2048, 32
+    d = workloads.householder_spectrum(n, k, 5 + rank, hi=1e2, lo=1e1)
+    A = torch.from_numpy(workloads.tall_matrix(m, n, d, 5 + rank)).to(dev)
+    nodes, probes = 24, 16
+    stream = ctx.stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    est, se, _ = ctx.schatten_p(A, 1.0, 2.5e-5, 1e8, nodes=nodes, probes=probes, s=128, tol=1e-8,
+                                refine_tol=1e-3, level2_iters=0, level3_iters=0)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    return {"workload": f"|A|_1 of A m={m} n={n} FP32 (G diag(d)/sqrt(m), 32 outliers 1e2->1e1, flat tail "
+                        f"[0.5,1]); {nodes} nodes x {probes} probes = {nodes * probes} ridge solves (exact "
+                        "level 2, s=128, relative residual 1e-8)",
+            "estimate": est, "std_err": se, "sum_of_column_scales": float(np.sum(d)),
+            "ms_per_estimate": ms, "ridge_solves_per_s": nodes * probes * 1000.0 / ms,
+            "note": "the singular values of A lie within 1 +- sqrt(n/m) of the column scales d"}
 
 
 def run_batched(args, ctx, dev, rank, peak):
@@ -678,6 +708,10 @@ def run_msp(args, rank, world, local):
     if not args.no_lsq:
         lsq_res = run_lsq(args, ctx, dev, rank)
 
+    sp_res = None
+    if not args.no_schatten_p:
+        sp_res = run_schatten_p(args, ctx, dev, rank)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         per_solve_iters = infos[-1]["outer_iters"]
@@ -709,6 +743,7 @@ def run_msp(args, rank, world, local):
            "batched": batched,
            "general": gen,
            "least_squares": lsq_res,
+           "schatten_p": sp_res,
            "phase_ms_per_step": {"a_pass": g_ms / args.steps, "level2": l2_ms / args.steps,
                                  "fp64_residual": r_ms / args.steps},
            "roofline": {"bound": "hbm", "kernel": "k_symv_packed (q = (A + lam I) p, packed upper tiles)",
