@@ -1185,6 +1185,9 @@ msp_status level1(msp_ctx* ctx, G_t* g, double tol, int maxit, int t2, int t3, i
             *conv = true;
             return MSP_OK;
         }
+        // a residual 1e4 times the right-hand side: the (inexact) preconditioner
+        // has broken the iteration; stop instead of running to the cap
+        if (rr > 1e8 * bb) return MSP_OK;
         if (k == maxit) break;
         MSP_TRY(precond(ctx, g, t2, t3, inner));
         MSP_TRY(ops.vec(3, len, g->r1, g->z1, g->zo1, g->p1, sc, 1));
