@@ -27,6 +27,8 @@
 #include "bulk.cuh"
 #include "msp_internal.cuh"
 
+#include <cooperative_groups.h>
+
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -575,6 +577,102 @@ __global__ void __launch_bounds__(1024) k_level3_pcg(const double* __restrict__ 
     if (own) out[tid] = (float)x;
 }
 
+// The same two level-3 solves on two thread-block clusters of kCl CTAs
+// (cluster 0: W u = r with M3a^{-1}; cluster 1: (W + lam~ I) v = r with
+// M3b^{-1}). CTA `rank` owns components [rank s_pad / kCl, (rank + 1) s_pad /
+// kCl); each warp forms whole rows of the symmetric matrices (lanes over
+// columns, coalesced), so the FP64 products run on 2 kCl SMs instead of two.
+// Vector slices and dot partials are broadcast to every CTA of the cluster
+// through distributed shared memory; cluster barriers order the steps (no
+// spin-waits). The dot partials are summed in rank order, so every CTA takes
+// the same scalars. s_pad <= 1024, s_pad divisible by kCl.
+constexpr int kCl = 8;
+
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(1024)
+    k_level3_cluster(const double* __restrict__ W, const double* __restrict__ Ma, const double* __restrict__ Mb,
+                     double lam_t, int sp, int t3, const float* __restrict__ b, float* __restrict__ u,
+                     float* __restrict__ v) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    __shared__ double vec[1024];          // the full vector of the next product
+    __shared__ double part[2][kCl];       // dot partials, one slot per rank
+    __shared__ double loc[32];
+    const int rank = (int)cl.block_rank();
+    const int sys = blockIdx.x / kCl;
+    const double* M = sys == 0 ? Ma : Mb;
+    const double shift = sys == 0 ? 0.0 : lam_t;
+    float* out = sys == 0 ? u : v;
+    const int own = sp / kCl, i0 = rank * own;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // owner state: thread c < own keeps component i0 + c
+    double x = 0.0, r = 0.0, z = 0.0, p = 0.0;
+    // y_c = (Mat vec)_(i0 + c) for the owned rows, into ys (shared)
+    __shared__ double ys[1024];
+    auto mv = [&](const double* Mat) {
+        for (int c = warp; c < own; c += 32) {
+            const double* row = Mat + (int64_t)(i0 + c) * sp;
+            double s = 0.0;
+            for (int j = lane; j < sp; j += 32) s = fma(row[j], vec[j], s);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0) ys[c] = s;
+        }
+        __syncthreads();
+    };
+    // every CTA's vec <- the owners' values (slices from all ranks)
+    auto broadcast = [&](double val) {
+        if (tid < own)
+            for (int q = 0; q < kCl; ++q) {
+                double* dst = cl.map_shared_rank(vec, q);
+                dst[i0 + tid] = val;
+            }
+        cl.sync();
+    };
+    // cluster-wide sum of one value per owner thread, fixed order
+    auto csum = [&](double val, int slot) {
+        double s = tid < own ? val : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) loc[warp] = s;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < 32; ++w) t += loc[w];
+            for (int q = 0; q < kCl; ++q) cl.map_shared_rank(&part[slot][0], q)[rank] = t;
+        }
+        cl.sync();
+        double tot = 0.0;
+        for (int q = 0; q < kCl; ++q) tot += part[slot][q];
+        return tot;
+    };
+    if (tid < own) r = (double)b[i0 + tid];
+    broadcast(r);
+    mv(M);
+    if (tid < own) z = ys[tid];
+    double rz = csum(r * z, 0);
+    p = z;
+    for (int k = 0; k < t3; ++k) {
+        broadcast(p);
+        mv(W);
+        const double q = tid < own ? ys[tid] + shift * p : 0.0;
+        const double pq = csum(p * q, 1);
+        const double alpha = (pq > 0.0 && rz != 0.0) ? rz / pq : 0.0;
+        x = fma(alpha, p, x);
+        r = fma(-alpha, q, r);
+        if (k + 1 < t3) {
+            broadcast(r);
+            mv(M);
+            if (tid < own) z = ys[tid];
+            const double rzn = csum(r * z, 0);
+            const double beta = rz != 0.0 ? rzn / rz : 0.0;
+            p = fma(beta, p, z);
+            rz = rzn;
+        }
+    }
+    if (tid < own) out[i0 + tid] = (float)x;
+    cl.sync();   // no CTA leaves while others may still write its shared memory
+}
+
 // out = a x + b y
 __global__ void k_axpby(int len, float a, const float* __restrict__ x, float b,
                         const float* __restrict__ y, float* __restrict__ out) {
@@ -928,7 +1026,11 @@ struct Ops {
     msp_status solve_m2(const float* r, float* z, int t3) {
         if (t3 == 0) return dense(g->M2inv, r, z);
         const int sp = (int)g->s_pad;
-        k_level3_pcg<<<2, 1024, 0, strm>>>(g->W64, g->M3a, g->M3b, g->lam_tilde, sp, t3, r, g->u3, g->v3);
+        if (sp % kCl == 0)
+            k_level3_cluster<<<2 * kCl, 1024, 0, strm>>>(g->W64, g->M3a, g->M3b, g->lam_tilde, sp, t3, r, g->u3,
+                                                         g->v3);
+        else
+            k_level3_pcg<<<2, 1024, 0, strm>>>(g->W64, g->M3a, g->M3b, g->lam_tilde, sp, t3, r, g->u3, g->v3);
         MSP_CHECK_LAUNCH(ctx);
         if (count) ++*count;
         const float il = (float)(1.0 / g->lam_tilde);
