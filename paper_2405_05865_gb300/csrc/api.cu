@@ -2,6 +2,8 @@
 // staging of host buffers and the FP64 refinement driver.
 #include "msp_internal.cuh"
 
+#include <vector>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -156,6 +158,7 @@ void msp_destroy(msp_ctx* ctx) {
     }
     delete[] ctx->lanes;
     delete[] ctx->lane_streams;
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     delete ctx;
 }
 
@@ -183,7 +186,7 @@ void msp_sketch_destroy(msp_sketch_t* sk) {
 
 msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n,
                            int64_t lda, int64_t s, int gamma, uint64_t seed, bool pack,
-                           msp_sketch_t** out) {
+                           msp_sketch_t** out, const void* host_chunks) {
     if (dtype != MSP_F32 && dtype != MSP_F64)
         return msp_set_error(ctx, MSP_EINVAL, "sketch: dtype must be MSP_F32 or MSP_F64");
     if (n < 1 || lda < n || s < 16 || s > MSP_MAX_S || s > n || gamma < 1 ||
@@ -210,12 +213,64 @@ msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t
         (st = msp_pattern_launch(ctx, n, s, gamma, seed, 0, sk->idx, sk->sgn, nullptr)) != MSP_OK ||
         (st = msp_build_csr(ctx, n, sp, gamma, sk->idx, sk->sgn, sk->csr_ptr, sk->csr_ent)) !=
             MSP_OK ||
-        (st = msp_sketch_apply(ctx, A, dtype, n, lda, sp, sk->csr_ptr, sk->csr_ent, gamma,
-                               sk->C)) != MSP_OK ||
         (dtype == MSP_F32 && pack &&
-         ((st = msp_alloc(ctx, (void**)&sk->packed, (size_t)msp_packed_tiles(n) * 128 * 128 * 4)) !=
-              MSP_OK ||
-          (st = msp_pack_upper(ctx, (const float*)A, lda, n, sk->packed)) != MSP_OK))) {
+         (st = msp_alloc(ctx, (void**)&sk->packed, (size_t)msp_packed_tiles(n) * 128 * 128 * 4)) != MSP_OK)) {
+        cudaStreamSynchronize(ctx->stream);
+        msp_sketch_destroy(sk);
+        return st;
+    }
+    if (host_chunks) {
+        // A arrives from the host in row chunks on the copy stream (staged at
+        // A_dev, ld n); each chunk's rows of C and its tile rows of the packed
+        // copy are formed as soon as it lands
+        if (!ctx->copy_stream && cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->copy_stream = nullptr;
+            msp_sketch_destroy(sk);
+            return msp_set_error(ctx, MSP_ECUDA, "sketch: copy stream creation failed");
+        }
+        const int64_t rows = std::max<int64_t>(128, round_up((n + 7) / 8, 128));
+        const int nchunk = (int)((n + rows - 1) / rows);
+        std::vector<cudaEvent_t> ev(nchunk, nullptr);
+        cudaEvent_t ready = nullptr;
+        bool ok = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) == cudaSuccess &&
+                  cudaEventRecord(ready, ctx->stream) == cudaSuccess &&
+                  cudaStreamWaitEvent(ctx->copy_stream, ready, 0) == cudaSuccess;
+        for (int k = 0; ok && k < nchunk; ++k) {
+            const int64_t r0 = k * rows, nr = std::min(rows, n - r0);
+            ok = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaMemcpy2DAsync((char*)A + (size_t)r0 * n * ts, n * ts, (const char*)host_chunks + (size_t)r0 * lda * ts,
+                                   lda * ts, n * ts, nr, cudaMemcpyHostToDevice, ctx->copy_stream) == cudaSuccess &&
+                 cudaEventRecord(ev[k], ctx->copy_stream) == cudaSuccess;
+        }
+        for (int k = 0; ok && k < nchunk; ++k) {
+            const int64_t r0 = k * rows, nr = std::min(rows, n - r0);
+            ok = cudaStreamWaitEvent(ctx->stream, ev[k], 0) == cudaSuccess;
+            if (!ok) break;
+            if ((st = msp_sketch_apply_rows(ctx, (const char*)A + (size_t)r0 * n * ts, dtype, nr, n, n, sp,
+                                            sk->csr_ptr, sk->csr_ent, gamma, (char*)sk->C + (size_t)r0 * sp * ts)) !=
+                    MSP_OK ||
+                (sk->packed && (st = msp_pack_upper_rows(ctx, (const float*)A, n, n, r0 / 128, (r0 + nr + 127) / 128,
+                                                         sk->packed)) != MSP_OK))
+                ok = false;
+        }
+        if (!ok && st == MSP_OK) {
+            cudaGetLastError();
+            st = msp_set_error(ctx, MSP_ECUDA, "sketch: chunked copy failed");
+        }
+        // (destroying a pending event is safe: its resources go once it completes)
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        if (ready) cudaEventDestroy(ready);
+        if (st != MSP_OK) {
+            cudaStreamSynchronize(ctx->copy_stream);
+            cudaStreamSynchronize(ctx->stream);
+            msp_sketch_destroy(sk);
+            return st;
+        }
+    } else if ((st = msp_sketch_apply(ctx, A, dtype, n, lda, sp, sk->csr_ptr, sk->csr_ent, gamma, sk->C)) !=
+                   MSP_OK ||
+               (sk->packed && (st = msp_pack_upper(ctx, (const float*)A, lda, n, sk->packed)) != MSP_OK)) {
         cudaStreamSynchronize(ctx->stream);
         msp_sketch_destroy(sk);
         return st;
@@ -233,7 +288,7 @@ msp_status msp_sketch(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n, i
     if (!A || !out) return msp_set_error(ctx, MSP_EINVAL, "sketch: NULL argument");
     DeviceGuard g(ctx->device);
     *out = nullptr;
-    return msp_sketch_impl(ctx, A, dtype, n, lda, s, gamma, seed, true, out);
+    return msp_sketch_impl(ctx, A, dtype, n, lda, s, gamma, seed, true, out, nullptr);
 }
 
 msp_status msp_sketch_info(const msp_sketch_t* sk, int64_t* n, int64_t* s, int64_t* s_pad,
@@ -552,12 +607,13 @@ msp_status msp_solve_full(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t 
     const double* bd = b;
     double* xd = x;
     int64_t ldd = lda;
+    // a host A is copied in row chunks overlapped with the sketch and the
+    // packing (which read only the chunk's rows)
+    const bool chunked = !dA;
     if (need) {
         MSP_TRY(stage_alloc(ctx, need));
         char* c = (char*)ctx->stage;
         if (!dA) {
-            MSP_CUDA_TRY(ctx, cudaMemcpy2DAsync(c, n * ts, A, lda * ts, n * ts, n,
-                                                cudaMemcpyHostToDevice, ctx->stream));
             Ad = c;
             ldd = n;
             c += round_up(n * n * ts, 256);
@@ -571,7 +627,8 @@ msp_status msp_solve_full(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t 
     }
     msp_sketch_t* sk = nullptr;
     msp_factor_t* f = nullptr;
-    msp_status st = msp_sketch_impl(ctx, Ad, dtype, n, ldd, s, gamma, seed, true, &sk);
+    msp_status st = msp_sketch_impl(ctx, Ad, dtype, n, chunked ? lda : ldd, s, gamma, seed, true, &sk,
+                                    chunked ? A : nullptr);
     if (st == MSP_OK) st = msp_nystrom_impl(ctx, sk, lambda, lambda0, phi, gamma_phi, seed, &f);
     msp_status st2 = MSP_OK;
     if (st == MSP_OK) st2 = solve_impl(ctx, f, Ad, dtype, n, ldd, lambda, bd, xd, &o, info);

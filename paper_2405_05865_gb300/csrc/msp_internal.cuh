@@ -35,6 +35,7 @@ struct msp_ctx {
     cudaEvent_t* events = nullptr;
     int n_events = 0;
     // worker contexts (own streams) for concurrent batch set-up, created lazily
+    cudaStream_t copy_stream = nullptr;   // host-to-device copies overlapped with compute
     msp_ctx** lanes = nullptr;
     cudaStream_t* lane_streams = nullptr;
     int n_lanes = 0;
@@ -249,8 +250,12 @@ msp_status msp_gather_rows(msp_ctx* ctx, msp_dtype dt, int64_t rows_out, int64_t
 // api.cu: sketch (pack = also build the packed upper tiles of an FP32 A for
 // the single-RHS A pass) and Nystrom factor, without argument re-checks of
 // the handles
+// host_chunks != NULL: A is the device staging buffer (ld n) and host_chunks
+// the host matrix (ld lda); the copy runs in row chunks overlapped with the
+// sketch and the packing
 msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n, int64_t lda,
-                           int64_t s, int gamma, uint64_t seed, bool pack, msp_sketch_s** out);
+                           int64_t s, int gamma, uint64_t seed, bool pack, msp_sketch_s** out,
+                           const void* host_chunks = nullptr);
 msp_status msp_nystrom_impl(msp_ctx* ctx, const msp_sketch_s* sk, double lambda, double lambda0,
                             int64_t phi, int gamma_phi, uint64_t seed, msp_factor_s** out);
 
@@ -276,6 +281,8 @@ msp_status msp_gram_inverse(msp_ctx* ctx, const float* X, int64_t rows, int64_t 
 // symv.cu
 int64_t msp_packed_tiles(int64_t n);
 msp_status msp_pack_upper(msp_ctx* ctx, const float* A, int64_t lda, int64_t n, float* packed);
+msp_status msp_pack_upper_rows(msp_ctx* ctx, const float* A, int64_t lda, int64_t n, int64_t I0, int64_t I1,
+                               float* packed);
 msp_status msp_symv_packed(msp_ctx* ctx, const float* packed, int64_t n, float lam, const float* p,
                            float* part, double* dpart, int grid);
 

@@ -120,10 +120,11 @@ __device__ inline void tile_coords(int t, int nt, int& I, int& J) {
 
 // Pack the upper tiles of dense row-major A (n x n, lda) into `packed`.
 __global__ void __launch_bounds__(256) k_pack_upper(const float* __restrict__ A, int64_t lda,
-                                                   int64_t n, int nt, float* __restrict__ packed) {
+                                                   int64_t n, int nt, int tile0, float* __restrict__ packed) {
     int I, J;
-    tile_coords(blockIdx.x, nt, I, J);
-    float* dst = packed + (int64_t)blockIdx.x * kTile * kTile;
+    const int tix = tile0 + (int)blockIdx.x;
+    tile_coords(tix, nt, I, J);
+    float* dst = packed + (int64_t)tix * kTile * kTile;
     const int64_t r0 = (int64_t)I * kTile, c0 = (int64_t)J * kTile;
     const bool vec = (lda % 4 == 0) && (((uintptr_t)A & 15) == 0) && (c0 + kTile <= n);
     for (int e = threadIdx.x; e < kTile * kTile / 4; e += blockDim.x) {
@@ -363,7 +364,20 @@ msp_status msp_pack_upper(msp_ctx* ctx, const float* A, int64_t lda, int64_t n, 
     const int64_t nt = (n + kTile - 1) / kTile;
     const int64_t ntiles = nt * (nt + 1) / 2;
     if (ntiles >= (1ll << 31)) return msp_set_error(ctx, MSP_EINVAL, "pack: n too large");
-    k_pack_upper<<<(unsigned)ntiles, 256, 0, ctx->stream>>>(A, lda, n, (int)nt, packed);
+    k_pack_upper<<<(unsigned)ntiles, 256, 0, ctx->stream>>>(A, lda, n, (int)nt, 0, packed);
+    MSP_CHECK_LAUNCH(ctx);
+    return MSP_OK;
+}
+
+// The tiles whose tile row lies in [I0, I1): contiguous in the packed order
+// (tile rows one after another), and they read only rows [I0, I1) * 128 of A.
+msp_status msp_pack_upper_rows(msp_ctx* ctx, const float* A, int64_t lda, int64_t n, int64_t I0, int64_t I1,
+                               float* packed) {
+    const int64_t nt = (n + kTile - 1) / kTile;
+    if (I0 < 0 || I1 > nt || I0 >= I1) return MSP_OK;
+    auto start = [&](int64_t i) { return i * nt - i * (i - 1) / 2; };
+    const int64_t t0 = start(I0), t1 = start(I1);
+    k_pack_upper<<<(unsigned)(t1 - t0), 256, 0, ctx->stream>>>(A, lda, n, (int)nt, (int)t0, packed);
     MSP_CHECK_LAUNCH(ctx);
     return MSP_OK;
 }

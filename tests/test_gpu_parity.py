@@ -313,3 +313,29 @@ def test_solve_backward_error_rule(ctx):
     eta = reference.backward_error(A64, x, w.b, w.lam, norm_A=top)
     assert eta <= info["backward_err"] * (1 + 1e-6) + 1e-16
     assert eta <= 1e-10
+
+
+@pytest.mark.parametrize("n,pad", [(3000, 0), (2176, 5)])
+def test_solve_full_host_buffers_match_device(ctx, n, pad):
+    """msp_solve_full with host A, b, x (A copied in row chunks overlapped with
+    the sketch and the packing; ragged last chunk; a strided host A when
+    pad > 0) gives bit for bit the result of the device-resident call, and
+    meets the backward-error rule on the host's FP64 residual."""
+    w = make_workload("rbf", seed=4, n=n)
+    A32 = np.ascontiguousarray(w.A.astype(np.float32))
+    big = np.zeros((n, n + pad), dtype=np.float32)
+    big[:, :n] = A32
+    Ah = torch.from_numpy(big).pin_memory()[:, :n]
+    bh = torch.from_numpy(w.b).pin_memory()
+    opts = dict(tol=1e-10, refine_tol=1e-3, max_inner=0, criterion="backward")
+    s = 256
+    xh, info_h = ctx.solve_full(Ah, bh, w.lam, s, 8, 0.0, 0, 8, 0x4D5350, **opts)
+    xd, info_d = ctx.solve_full(torch.from_numpy(A32).cuda(), bh.cuda(), w.lam, s, 8, 0.0, 0, 8, 0x4D5350, **opts)
+    assert not xh.is_cuda
+    assert np.array_equal(xh.numpy(), xd.cpu().numpy())
+    assert info_h["outer_iters"] == info_d["outer_iters"]
+    K = A32.astype(np.float64)
+    x = xh.numpy()
+    r = w.b - (K @ x + w.lam * x)
+    L = reference.norm_lower_bound(K)
+    assert np.linalg.norm(r) <= 1e-10 * ((L + w.lam) * np.linalg.norm(x) + np.linalg.norm(w.b))
