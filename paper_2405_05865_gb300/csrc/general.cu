@@ -758,10 +758,15 @@ struct msp_general_s {
     int64_t s_ls = 0;
     double inner_tol = 1e-2;
     int inner_maxit = 50;
+    int check_every = 4;            // level-1 iterations between host checks
     cudaStream_t cap = nullptr;     // private stream the SolveM1 graph is captured on
     cudaGraphExec_t m1_exec = nullptr;
     int m1_t2 = -1, m1_t3 = -1;
     int m1_kernels = 0;
+    // one whole level-1 iteration (operator, step, SolveM1, direction)
+    cudaGraphExec_t it_exec = nullptr;
+    int it_t2 = -1, it_t3 = -1;
+    int it_kernels = 0;
 };
 
 namespace {
@@ -1064,6 +1069,7 @@ struct Ops {
 void destroy_general(G_t* g) {
     if (!g) return;
     if (g->m1_exec) cudaGraphExecDestroy(g->m1_exec);
+    if (g->it_exec) cudaGraphExecDestroy(g->it_exec);
     cudaStream_t s = g->stream;
     for (void* p : {(void*)g->A_copy, (void*)g->At, (void*)g->M3a, (void*)g->M3b, (void*)g->G3a, (void*)g->G3b,
                     (void*)g->Linv, g->work, (void*)g->W64, (void*)g->M2inv, (void*)g->Cm, (void*)g->Binv,
@@ -1223,6 +1229,49 @@ msp_status run_m1(msp_ctx* ctx, G_t* g, int t2, int t3) {
     return MSP_OK;
 }
 
+// One level-1 iteration (q = (A^T A + lam I) p, the step, z = SolveM1(r),
+// the new direction) as a CUDA graph for the handle's (t2, t3); the lambda
+// values are baked in, so msp_general_set_lambda drops it.
+msp_status ensure_iter_graph(msp_ctx* ctx, G_t* g, int t2, int t3) {
+    if (g->it_exec && g->it_t2 == t2 && g->it_t3 == t3) return MSP_OK;
+    if (g->it_exec) {
+        cudaGraphExecDestroy(g->it_exec);
+        g->it_exec = nullptr;
+    }
+    MSP_TRY(ensure_direct(ctx, g, t2, t3));
+    int count = 0;
+    Ops ops{ctx, g, &count, g->cap};
+    const int len = (int)g->n_pad;
+    MSP_CUDA_TRY(ctx, cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal));
+    const int64_t l0 = ctx->launches;
+    msp_status st = ops.op1(g->p1, g->q1);
+    if (st == MSP_OK) st = ops.vec(2, len, g->p1, g->q1, g->x1, g->r1, g->sc);
+    if (st == MSP_OK) st = ops.solve_m1(g->r1, g->z1, t2, t3);
+    if (st == MSP_OK) st = ops.vec(3, len, g->r1, g->z1, g->zo1, g->p1, g->sc, 1);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(g->cap, &graph);
+    ctx->launches = l0;
+    if (st != MSP_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (ce != cudaSuccess || !graph) {
+        cudaGetLastError();
+        return msp_set_error(ctx, MSP_ECUDA, "general: iteration capture failed: %s", cudaGetErrorString(ce));
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&g->it_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+        cudaGetLastError();
+        g->it_exec = nullptr;
+        return msp_set_error(ctx, MSP_ECUDA, "general: graph instantiation failed");
+    }
+    g->it_t2 = t2;
+    g->it_t3 = t3;
+    g->it_kernels = count;
+    return MSP_OK;
+}
+
 msp_status read_scalars(msp_ctx* ctx, G_t* g, const Pcg* sc, double* rr, double* bb) {
     MSP_CUDA_TRY(ctx, cudaMemcpyAsync(g->host, sc, sizeof(Pcg), cudaMemcpyDeviceToHost, ctx->stream));
     MSP_CUDA_TRY(ctx, cudaMemcpyAsync(g->host + 8, g->err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -1251,6 +1300,7 @@ msp_status precond(msp_ctx* ctx, G_t* g, int t2, int t3, int* inner) {
         return MSP_OK;
     }
     G_t* h = g->inner;
+    h->check_every = 1;     // constant-accuracy inner solves stop at the first chance
     const size_t bytes = (size_t)g->n_pad * 4;
     MSP_CUDA_TRY(ctx, cudaMemcpyAsync(h->b1, g->r1, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
     int it = 0, in2 = 0;
@@ -1277,6 +1327,29 @@ msp_status level1(msp_ctx* ctx, G_t* g, double tol, int maxit, int t2, int t3, i
     }
     MSP_TRY(precond(ctx, g, t2, t3, inner));
     MSP_TRY(ops.vec(1, len, g->r1, g->z1, g->p1, g->zo1, sc));
+    if (!g->inner) {
+        // whole iterations replayed as one graph, the host check every
+        // `check` iterations (a converged PCG only keeps improving)
+        MSP_TRY(ensure_iter_graph(ctx, g, t2, t3));
+        const int check = std::max(1, g->check_every);
+        int k = 0;
+        while (k < maxit) {
+            const int nrun = std::min(check, maxit - k);
+            for (int i = 0; i < nrun; ++i) MSP_CUDA_TRY(ctx, cudaGraphLaunch(g->it_exec, ctx->stream));
+            ctx->launches += (int64_t)nrun * g->it_kernels;
+            k += nrun;
+            *inner += nrun * t2;
+            MSP_TRY(read_scalars(ctx, g, sc, &rr, &bb));
+            *iters = k;
+            if (!std::isfinite(rr)) return msp_set_error(ctx, MSP_ENONFINITE, "general: non-finite residual");
+            if (rr <= tol * tol * bb) {
+                *conv = true;
+                return MSP_OK;
+            }
+            if (rr > 1e8 * bb) return MSP_OK;
+        }
+        return MSP_OK;
+    }
     for (int k = 1; k <= maxit; ++k) {
         MSP_TRY(ops.op1(g->p1, g->q1));
         MSP_TRY(ops.vec(2, len, g->p1, g->q1, g->x1, g->r1, sc));
@@ -1331,6 +1404,7 @@ msp_status solve_refined(msp_ctx* ctx, G_t* g, const msp_opts& o, double cn, msp
     const int t2 = o.level2_iters, t3 = o.level3_iters;
     const int np = (int)g->n_pad;
     const unsigned nb = (unsigned)((np + 255) / 256);
+    g->check_every = std::max(1, std::min(o.check_every, 64));
     msp_status& result = *result_out;
     msp_info& inf = *inf_out;
     result = MSP_OK;
@@ -1767,11 +1841,12 @@ msp_status msp_general_set_lambda(msp_ctx* ctx, msp_general_t* g, double lambda,
         cudaFreeAsync(g->Binv, ctx->stream);
         g->Binv = nullptr;
     }
-    if (g->m1_exec) {
+    if (g->m1_exec || g->it_exec) {
         MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-        cudaGraphExecDestroy(g->m1_exec);
-        g->m1_exec = nullptr;
-        g->m1_t2 = g->m1_t3 = -1;
+        if (g->m1_exec) cudaGraphExecDestroy(g->m1_exec);
+        if (g->it_exec) cudaGraphExecDestroy(g->it_exec);
+        g->m1_exec = g->it_exec = nullptr;
+        g->m1_t2 = g->m1_t3 = g->it_t2 = g->it_t3 = -1;
     }
     return MSP_OK;
 }
