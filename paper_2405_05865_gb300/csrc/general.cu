@@ -1822,6 +1822,13 @@ msp_status msp_general_set_lambda(msp_ctx* ctx, msp_general_t* g, double lambda,
         return msp_set_error(ctx, MSP_EINVAL,
                              "general_set_lambda: need a general handle, lambda, lambda0 >= 0, lambda + lambda0 > 0");
     msp::DeviceGuard guard(ctx->device);
+    if (lambda != g->lambda && g->it_exec) {
+        // the captured level-1 iteration has lambda in its operator
+        MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        cudaGraphExecDestroy(g->it_exec);
+        g->it_exec = nullptr;
+        g->it_t2 = g->it_t3 = -1;
+    }
     g->lambda = lambda;
     g->lambda0 = lambda0;
     const double lt = lambda + lambda0;
