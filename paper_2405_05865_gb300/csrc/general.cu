@@ -42,6 +42,7 @@ constexpr int kMaxN = 8192;       // columns of A (register partials, vector ker
 
 struct Pcg {
     double rz, pq, alpha, rr, beta, rzn, rzo, bb;
+    double tol2;    // level 1: tol^2 |b|^2 (a breakdown counts only above it)
 };
 
 template <typename Acc>
@@ -445,7 +446,8 @@ __global__ void k_pcg_step(int len, const float* __restrict__ p, const float* __
     const double rz = sc->rz;
     double alpha = 0.0;
     if (pq > 0.0 && isfinite(pq) && isfinite(rz)) alpha = rz / pq;
-    else if (err && threadIdx.x == 0 && rz != 0.0) atomicCAS(err, 0, isfinite(pq) ? (int)MSP_ENOTPD : (int)MSP_ENONFINITE);
+    else if (err && threadIdx.x == 0 && rz != 0.0 && sc->rr > sc->tol2)
+        atomicCAS(err, 0, isfinite(pq) ? (int)MSP_ENOTPD : (int)MSP_ENONFINITE);
     const float af = (float)alpha;
     FF a2{0.f, 0.f};
     for (int i = threadIdx.x; i < len; i += blockDim.x) {
@@ -1018,7 +1020,8 @@ struct Ops {
         switch (which) {
             case 0: k_pcg_init<<<1, kVecThreads, 0, strm>>>(len, a0, a2, a3, sc); break;
             case 1: k_pcg_start<<<1, kVecThreads, 0, strm>>>(len, a0, a1, a2, a3, sc); break;
-            case 2: k_pcg_step<<<1, kVecThreads, 0, strm>>>(len, a0, a1, a2, a3, sc, g->err); break;
+            // the fixed-step inner levels only freeze a step with p.q <= 0
+            case 2: k_pcg_step<<<1, kVecThreads, 0, strm>>>(len, a0, a1, a2, a3, sc, sc == g->sc ? g->err : nullptr); break;
             default: k_pcg_dir<<<1, kVecThreads, 0, strm>>>(len, a0, a1, a2, a3, sc, flexible); break;
         }
         MSP_CHECK_LAUNCH(ctx);
@@ -1325,6 +1328,8 @@ msp_status level1(msp_ctx* ctx, G_t* g, double tol, int maxit, int t2, int t3, i
         *conv = true;
         return MSP_OK;
     }
+    g->host[13] = tol * tol * bb;
+    MSP_CUDA_TRY(ctx, cudaMemcpyAsync(&sc->tol2, g->host + 13, 8, cudaMemcpyHostToDevice, ctx->stream));
     MSP_TRY(precond(ctx, g, t2, t3, inner));
     MSP_TRY(ops.vec(1, len, g->r1, g->z1, g->p1, g->zo1, sc));
     if (!g->inner) {
