@@ -1337,9 +1337,12 @@ msp_status level1(msp_ctx* ctx, G_t* g, double tol, int maxit, int t2, int t3, i
         // `check` iterations (a converged PCG only keeps improving)
         MSP_TRY(ensure_iter_graph(ctx, g, t2, t3));
         const int check = std::max(1, g->check_every);
-        int k = 0;
+        // replay as many iterations as the observed rate says are still
+        // needed (at most `check`), so the check rarely overshoots
+        int k = 0, nrun = 1;
+        double rr_prev = bb;
         while (k < maxit) {
-            const int nrun = std::min(check, maxit - k);
+            nrun = std::max(1, std::min(nrun, maxit - k));
             for (int i = 0; i < nrun; ++i) MSP_CUDA_TRY(ctx, cudaGraphLaunch(g->it_exec, ctx->stream));
             ctx->launches += (int64_t)nrun * g->it_kernels;
             k += nrun;
@@ -1352,6 +1355,10 @@ msp_status level1(msp_ctx* ctx, G_t* g, double tol, int maxit, int t2, int t3, i
                 return MSP_OK;
             }
             if (rr > 1e8 * bb) return MSP_OK;
+            const double rate = std::pow(rr / rr_prev, 1.0 / nrun);
+            const double need = (rate > 0.0 && rate < 1.0) ? std::log(tol * tol * bb / rr) / std::log(rate) : 1.0;
+            nrun = (int)std::min<double>(check, std::max(1.0, std::floor(need)));
+            rr_prev = rr;
         }
         return MSP_OK;
     }
