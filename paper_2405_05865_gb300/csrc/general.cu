@@ -145,8 +145,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_rowpass(
 // copies in flight before the block exits.
 constexpr int kRing = 3;
 constexpr int kWorkerThreads = 256;
+constexpr int kWW = kWorkerThreads / 32;   // worker warps
 constexpr size_t kRingHdr = 128;       // mbarriers and the abort flag
-constexpr size_t kRingSaOff = 768;     // after 64 + 8 t values of up to 8 bytes
+constexpr size_t kRingSaOff = 1024;    // after 64 t values and up to 32 partial dots of 8 bytes
 constexpr uint32_t kRingStageMax = 64 * 1024;
 
 __host__ __device__ constexpr size_t ring_a_bytes(int nx4, size_t acc) { return ((size_t)nx4 * 4 * acc + 127) / 128 * 128; }
@@ -169,7 +170,7 @@ __global__ void __launch_bounds__(kWorkerThreads + 32, 1) k_rowpass_ring(
     uint64_t* empty = full + kRing;
     int* abort_flag = reinterpret_cast<int*>(empty + kRing);
     Acc* st = reinterpret_cast<Acc*>(ring_smem + kRingHdr);             // up to 64 t values
-    Acc* sp = st + 64;                                                 // 8 partial dots
+    Acc* sp = st + 64;                                                 // kWW partial dots
     Acc* sa = reinterpret_cast<Acc*>(ring_smem + kRingSaOff);
     unsigned char* ring = ring_smem + kRingSaOff + ring_a_bytes(nx4, sizeof(Acc));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(kWorkerThreads + 32, 1) k_rowpass_ring(
     for (int i = tid; i < nx4 * 4; i += blockDim.x) sa[i] = a[i];
     __syncthreads();
 
-    if (warp == 8) {
+    if (warp == kWW) {
         // ---- producer
         if (lane == 0) {
             uint32_t k = 0;
@@ -256,7 +257,7 @@ __global__ void __launch_bounds__(kWorkerThreads + 32, 1) k_rowpass_ring(
                 st[tid] = tv;
             }
         } else {
-            for (int row = warp; row < nr; row += 8) {
+            for (int row = warp; row < nr; row += kWW) {
                 const float4* xr = rows4 + (size_t)row * nx4;
                 Acc tp = Acc(0);
 #pragma unroll 4
@@ -853,7 +854,7 @@ bool ring_shape(int nx4, int ny4_staged, size_t acc, size_t smem_optin, RingShap
     if (R < 1) return false;
     if (R > 64) R = 64;
     sh->rows = R;
-    sh->wpr = R >= 8 ? 1 : 8 / R;     // R = 3: 2 warps per row, warps 6 and 7 idle in the dots
+    sh->wpr = R >= kWW ? 1 : kWW / R;     // e.g. R = 3, 8 warps: 2 warps per row, 2 warps idle in the dots
     sh->row_bytes = rb;
     sh->stage_bytes = (uint32_t)(((size_t)R * (rb + rby) + 127) / 128 * 128);
     *smem = fixed + (size_t)kRing * sh->stage_bytes;
