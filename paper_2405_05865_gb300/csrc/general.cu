@@ -222,13 +222,13 @@ __global__ void __launch_bounds__(kWorkerThreads + 32, 1) k_rowpass_ring(
     for (int gi = 0; gi < ngroups; ++gi) {
         const int s = gi % kRing;
         const uint32_t par = (uint32_t)(gi / kRing) & 1u;
-        // a timed-out wait is seen by every worker at the barrier after the
-        // dots (that warp's dots read stale shared memory, in bounds)
         if (!msp::mbar_wait_timed(&full[s], par, err) && lane == 0) atomicExch(abort_flag, 1);
+        msp::bar_workers<kWorkerThreads>();
+        if (*(volatile int*)abort_flag) break;
         const int64_t g0 = r0 + (int64_t)gi * sh.rows;
         const int nr = (int)min((int64_t)sh.rows, r1 - g0);
         const float4* rows4 = reinterpret_cast<const float4*>(ring + (size_t)s * sh.stage_bytes);
-        // row dots: 8/R warps per row (partials in sp) or whole rows per warp (st)
+        // row dots
         if (sh.wpr > 1) {
             const int row = warp / sh.wpr, part_i = warp % sh.wpr;
             const int per = (nx4 + sh.wpr - 1) / sh.wpr;
@@ -247,6 +247,15 @@ __global__ void __launch_bounds__(kWorkerThreads + 32, 1) k_rowpass_ring(
             }
             tp = warp_sum_t(tp);
             if (lane == 0) sp[warp] = tp;
+            msp::bar_workers<kWorkerThreads>();
+            if (tid < nr) {
+                Acc tv = Acc(0);
+                for (int q = 0; q < sh.wpr; ++q) tv += sp[tid * sh.wpr + q];
+                const int64_t r = g0 + tid;
+                tv += z ? beta * z[r] : Acc(0);
+                if (tout) tout[r] = tv;
+                st[tid] = tv;
+            }
         } else {
             for (int row = warp; row < nr; row += kWW) {
                 const float4* xr = rows4 + (size_t)row * nx4;
@@ -269,22 +278,11 @@ __global__ void __launch_bounds__(kWorkerThreads + 32, 1) k_rowpass_ring(
             }
         }
         msp::bar_workers<kWorkerThreads>();
-        if (*(volatile int*)abort_flag) break;
-        // fold the stage's rows (of X itself, or the staged rows of Y); with
-        // split dots every thread combines the row's partials in warp order
+        // fold the stage's rows (of X itself, or the staged rows of Y)
         const float4* ybase = kSame ? rows4 : rows4 + (size_t)sh.rows * nx4;
         const int nf4 = kSame ? nx4 : ny4;
         for (int row = 0; row < nr; ++row) {
-            Acc tr;
-            if (sh.wpr > 1) {
-                tr = Acc(0);
-                for (int q = 0; q < sh.wpr; ++q) tr += sp[row * sh.wpr + q];
-                const int64_t r = g0 + row;
-                tr += z ? beta * z[r] : Acc(0);
-                if (tout && tid == row) tout[r] = tr;
-            } else {
-                tr = st[row];
-            }
+            const Acc tr = st[row];
             const float4* yr = ybase + (size_t)row * nf4;
 #pragma unroll
             for (int q = 0; q < NV; ++q) {
