@@ -222,9 +222,9 @@ __global__ void __launch_bounds__(kWorkerThreads + 32, 1) k_rowpass_ring(
     for (int gi = 0; gi < ngroups; ++gi) {
         const int s = gi % kRing;
         const uint32_t par = (uint32_t)(gi / kRing) & 1u;
+        // a timed-out wait is seen by every worker at the barrier after the
+        // dots (that warp's dots read stale shared memory, in bounds)
         if (!msp::mbar_wait_timed(&full[s], par, err) && lane == 0) atomicExch(abort_flag, 1);
-        msp::bar_workers<kWorkerThreads>();
-        if (*(volatile int*)abort_flag) break;
         const int64_t g0 = r0 + (int64_t)gi * sh.rows;
         const int nr = (int)min((int64_t)sh.rows, r1 - g0);
         const float4* rows4 = reinterpret_cast<const float4*>(ring + (size_t)s * sh.stage_bytes);
@@ -278,6 +278,7 @@ __global__ void __launch_bounds__(kWorkerThreads + 32, 1) k_rowpass_ring(
             }
         }
         msp::bar_workers<kWorkerThreads>();
+        if (*(volatile int*)abort_flag) break;
         // fold the stage's rows (of X itself, or the staged rows of Y)
         const float4* ybase = kSame ? rows4 : rows4 + (size_t)sh.rows * nx4;
         const int nf4 = kSame ? nx4 : ny4;
