@@ -146,9 +146,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_rowpass(
 constexpr int kRing = 3;
 constexpr int kWorkerThreads = 256;
 constexpr int kWW = kWorkerThreads / 32;   // worker warps
-constexpr int kMaxA4 = 8;                  // float4 of a per lane in a column slice (nx4 <= 32 kMaxA4 kWW)
 constexpr size_t kRingHdr = 128;       // mbarriers and the abort flag
-constexpr size_t kRingSaOff = 1280;    // after 64 t values and up to 8 x 8 partial dots of 8 bytes
+constexpr size_t kRingSaOff = 1024;    // after 64 t values and up to 32 partial dots of 8 bytes
 constexpr uint32_t kRingStageMax = 64 * 1024;
 
 __host__ __device__ constexpr size_t ring_a_bytes(int nx4, size_t acc) { return ((size_t)nx4 * 4 * acc + 127) / 128 * 128; }
@@ -171,7 +170,7 @@ __global__ void __launch_bounds__(kWorkerThreads + 32, 1) k_rowpass_ring(
     uint64_t* empty = full + kRing;
     int* abort_flag = reinterpret_cast<int*>(empty + kRing);
     Acc* st = reinterpret_cast<Acc*>(ring_smem + kRingHdr);             // up to 64 t values
-    Acc* sp = st + 64;                                                 // R x kWW partial dots (R < kWW)
+    Acc* sp = st + 64;                                                 // kWW partial dots
     Acc* sa = reinterpret_cast<Acc*>(ring_smem + kRingSaOff);
     unsigned char* ring = ring_smem + kRingSaOff + ring_a_bytes(nx4, sizeof(Acc));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -231,47 +230,27 @@ __global__ void __launch_bounds__(kWorkerThreads + 32, 1) k_rowpass_ring(
         const float4* rows4 = reinterpret_cast<const float4*>(ring + (size_t)s * sh.stage_bytes);
         // row dots
         if (sh.wpr > 1) {
-            // long rows (R < 8): warp w takes column slice w of every row of
-            // the stage, with its slice of a held in registers (read once per
-            // stage, not once per row); partials combined in warp order
-            const int per = (nx4 + kWW - 1) / kWW;
-            const int c0 = warp * per, c1 = min(nx4, c0 + per);
-            float4 av[kMaxA4];
-#pragma unroll
-            for (int k = 0; k < kMaxA4; ++k) {
-                const int c = c0 + lane + 32 * k;
-                av[k] = (c < c1) ? make_float4((float)sa[4 * c], (float)sa[4 * c + 1], (float)sa[4 * c + 2],
-                                               (float)sa[4 * c + 3])
-                                 : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-            for (int row = 0; row < nr; ++row) {
+            const int row = warp / sh.wpr, part_i = warp % sh.wpr;
+            const int per = (nx4 + sh.wpr - 1) / sh.wpr;
+            const int c0 = part_i * per, c1 = min(nx4, c0 + per);
+            Acc tp = Acc(0);
+            if (row < nr) {
                 const float4* xr = rows4 + (size_t)row * nx4;
-                Acc tp = Acc(0);
-#pragma unroll
-                for (int k = 0; k < kMaxA4; ++k) {
-                    const int c = c0 + lane + 32 * k;
-                    if (c < c1) {
-                        const float4 v = xr[c];
-                        if constexpr (sizeof(Acc) == 4) {
-                            tp = fmaf(v.x, av[k].x, tp);
-                            tp = fmaf(v.y, av[k].y, tp);
-                            tp = fmaf(v.z, av[k].z, tp);
-                            tp = fmaf(v.w, av[k].w, tp);
-                        } else {
-                            tp = fma((Acc)v.x, sa[4 * c + 0], tp);
-                            tp = fma((Acc)v.y, sa[4 * c + 1], tp);
-                            tp = fma((Acc)v.z, sa[4 * c + 2], tp);
-                            tp = fma((Acc)v.w, sa[4 * c + 3], tp);
-                        }
-                    }
+#pragma unroll 4
+                for (int c = c0 + lane; c < c1; c += 32) {
+                    const float4 v = xr[c];
+                    tp = fma_acc(v.x, sa[4 * c + 0], tp);
+                    tp = fma_acc(v.y, sa[4 * c + 1], tp);
+                    tp = fma_acc(v.z, sa[4 * c + 2], tp);
+                    tp = fma_acc(v.w, sa[4 * c + 3], tp);
                 }
-                tp = warp_sum_t(tp);
-                if (lane == 0) sp[row * kWW + warp] = tp;
             }
+            tp = warp_sum_t(tp);
+            if (lane == 0) sp[warp] = tp;
             msp::bar_workers<kWorkerThreads>();
             if (tid < nr) {
                 Acc tv = Acc(0);
-                for (int q = 0; q < kWW; ++q) tv += sp[tid * kWW + q];
+                for (int q = 0; q < sh.wpr; ++q) tv += sp[tid * sh.wpr + q];
                 const int64_t r = g0 + tid;
                 tv += z ? beta * z[r] : Acc(0);
                 if (tout) tout[r] = tv;
@@ -875,9 +854,8 @@ bool ring_shape(int nx4, int ny4_staged, size_t acc, size_t smem_optin, RingShap
     int R = (int)(per_stage / (rb + rby));
     if (R < 1) return false;
     if (R > 64) R = 64;
-    if (R < kWW && nx4 > 32 * kMaxA4 * kWW) return false;   // column slices too wide for the registers
     sh->rows = R;
-    sh->wpr = R >= kWW ? 1 : kWW;         // R < 8: every warp takes a column slice of every row
+    sh->wpr = R >= kWW ? 1 : kWW / R;     // e.g. R = 3, 8 warps: 2 warps per row, 2 warps idle in the dots
     sh->row_bytes = rb;
     sh->stage_bytes = (uint32_t)(((size_t)R * (rb + rby) + 127) / 128 * 128);
     *smem = fixed + (size_t)kRing * sh->stage_bytes;
