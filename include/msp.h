@@ -248,6 +248,15 @@ MSP_API msp_status msp_solve(msp_ctx* ctx, const msp_factor_t* f, const void* A,
                      msp_dtype dtype, int64_t n, int64_t lda, double lambda,
                      const double* b, double* x, const msp_opts* opts,
                      msp_info* info);
+/* Several right-hand sides with one factor: column j of B (device FP64,
+ * column-major n x m, ldb >= n) is solved exactly as msp_solve would into
+ * column j of X (ldx >= n), one after another; infos (host, may be NULL)
+ * receives m msp_info. Returns MSP_ENOCONV if any column hit its caps (all
+ * columns are still solved), another error at the first failing column. */
+MSP_API msp_status msp_solve_many(msp_ctx* ctx, const msp_factor_t* f, const void* A, msp_dtype dtype,
+                                  int64_t n, int64_t lda, double lambda, const double* B, int64_t ldb,
+                                  double* X, int64_t ldx, int64_t m, const msp_opts* opts,
+                                  msp_info* infos);
 
 /* The whole of Algorithm 1 in one call: sketch, Nystrom factor, solve.
  * A, b and x may each be device or host memory (host buffers are staged

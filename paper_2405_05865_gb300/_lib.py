@@ -109,6 +109,8 @@ _SIGS = {
     "msp_general_solve_m2": (C.c_int, [P, P, P, P, C.c_int]),
     "msp_general_matvec64": (C.c_int, [P, P, P, P]),
     "msp_general_op": (C.c_int, [P, P, P, P]),
+    "msp_solve_many": (C.c_int, [P, P, P, C.c_int, I64, I64, C.c_double, P, I64, P, I64, I64, C.POINTER(MspOpts),
+                                 C.POINTER(MspInfo)]),
     "msp_general_set_lambda": (C.c_int, [P, P, C.c_double, C.c_double]),
     "msp_schatten_p": (C.c_int, [P, P, I64, I64, I64, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int,
                                  I64, C.c_uint64, I64, C.c_double, C.POINTER(MspOpts), C.POINTER(C.c_double),

@@ -361,6 +361,23 @@ class Context:
             L.check(self.ptr, st)
         return x, info.as_dict()
 
+    def solve_many(self, f: Factor, A: torch.Tensor, B: torch.Tensor, lam: float,
+                   raise_on_noconv: bool = True, **opts) -> tuple[torch.Tensor, list[dict]]:
+        """Columns of B (CUDA float64 (n, m)) solved one by one with the factor f."""
+        n, lda, dt = _check_matrix(A)
+        if not B.is_cuda or B.dtype != torch.float64 or B.dim() != 2 or B.shape[0] != n:
+            raise ValueError("B must be a CUDA float64 (n, m) tensor")
+        m = B.shape[1]
+        Bc = B.t().contiguous()              # column-major n x m
+        Xc = torch.empty_like(Bc)
+        o = make_opts(self.lib, **opts)
+        infos = (L.MspInfo * max(m, 1))()
+        st = self.lib.msp_solve_many(self.ptr, f.handle, _ptr(A), dt, n, lda, lam, _ptr(Bc), n, _ptr(Xc), n, m,
+                                     C.byref(o), infos)
+        if st != 0 and not (st == 5 and not raise_on_noconv):
+            L.check(self.ptr, st)
+        return Xc.t(), [infos[j].as_dict() for j in range(m)]
+
     def solve_full(self, A: torch.Tensor, b: torch.Tensor, lam: float, s: int, gamma: int = 8,
                    lam0: float = 0.0, phi: int | None = None, gamma_phi: int = 8,
                    seed: int = DEFAULT_SEED, out: torch.Tensor | None = None,

@@ -589,6 +589,28 @@ msp_status msp_solve(msp_ctx* ctx, const msp_factor_t* f, const void* A, msp_dty
     return solve_impl(ctx, f, A, dtype, n, lda, lambda, b, x, &o, info);
 }
 
+msp_status msp_solve_many(msp_ctx* ctx, const msp_factor_t* f, const void* A, msp_dtype dtype, int64_t n,
+                          int64_t lda, double lambda, const double* B, int64_t ldb, double* X, int64_t ldx,
+                          int64_t m, const msp_opts* opts, msp_info* infos) {
+    if (!ctx) return msp_set_error(nullptr, MSP_EINVAL, "ctx is NULL");
+    if (!f || !A || !B || !X || m < 0 || ldb < n || ldx < n)
+        return msp_set_error(ctx, MSP_EINVAL, "solve_many: NULL argument, m < 0, or ldb / ldx < n");
+    DeviceGuard g(ctx->device);
+    msp_opts o;
+    if (opts) o = *opts; else msp_default_opts(&o);
+    // every column is its own run of Algorithm 1 step 5 with the shared factor
+    msp_status worst = MSP_OK;
+    for (int64_t j = 0; j < m; ++j) {
+        msp_info inf;
+        const msp_status st = solve_impl(ctx, f, A, dtype, n, lda, lambda, B + j * ldb, X + j * ldx, &o, &inf);
+        if (infos) infos[j] = inf;
+        if (st != MSP_OK && st != MSP_ENOCONV) return st;
+        if (st == MSP_ENOCONV) worst = MSP_ENOCONV;
+    }
+    if (worst == MSP_ENOCONV) return msp_set_error(ctx, MSP_ENOCONV, "solve_many: a column did not converge");
+    return MSP_OK;
+}
+
 msp_status msp_solve_full(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n, int64_t lda,
                           double lambda, const double* b, double* x, int64_t s, int gamma,
                           double lambda0, int64_t phi, int gamma_phi, uint64_t seed,

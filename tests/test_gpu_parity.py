@@ -339,3 +339,23 @@ def test_solve_full_host_buffers_match_device(ctx, n, pad):
     r = w.b - (K @ x + w.lam * x)
     L = reference.norm_lower_bound(K)
     assert np.linalg.norm(r) <= 1e-10 * ((L + w.lam) * np.linalg.norm(x) + np.linalg.norm(w.b))
+
+
+def test_solve_many_matches_single_solves(ctx):
+    """msp_solve_many: every column equals the single-RHS msp_solve of it with
+    the same factor, bit for bit (columns are independent runs)."""
+    w = make_workload("rbf", seed=6, n=1500)
+    A = torch.from_numpy(np.ascontiguousarray(w.A.astype(np.float32))).cuda()
+    sk = ctx.sketch(A, s=128)
+    f = ctx.nystrom(sk, lam=w.lam, phi=0)
+    B = torch.from_numpy(np.random.default_rng(3).standard_normal((1500, 5))).cuda()
+    opts = dict(tol=1e-10, refine_tol=1e-3, max_inner=0, criterion="backward")
+    X, infos = ctx.solve_many(f, A, B, w.lam, **opts)
+    for j in range(5):
+        x, info = ctx.solve(f, A, B[:, j].contiguous(), w.lam, **opts)
+        assert torch.equal(X[:, j], x)
+        assert infos[j]["outer_iters"] == info["outer_iters"] and infos[j]["status"] == 0
+    X0, infos0 = ctx.solve_many(f, A, B[:, :0], w.lam, **opts)
+    assert X0.shape == (1500, 0) and infos0 == []
+    f.close()
+    sk.close()
