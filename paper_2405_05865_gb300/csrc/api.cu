@@ -593,7 +593,7 @@ msp_status msp_solve_many(msp_ctx* ctx, const msp_factor_t* f, const void* A, ms
                           int64_t lda, double lambda, const double* B, int64_t ldb, double* X, int64_t ldx,
                           int64_t m, const msp_opts* opts, msp_info* infos) {
     if (!ctx) return msp_set_error(nullptr, MSP_EINVAL, "ctx is NULL");
-    if (!f || !A || !B || !X || m < 0 || ldb < n || ldx < n)
+    if (!f || !A || (m > 0 && (!B || !X)) || m < 0 || ldb < n || ldx < n)
         return msp_set_error(ctx, MSP_EINVAL, "solve_many: NULL argument, m < 0, or ldb / ldx < n");
     DeviceGuard g(ctx->device);
     msp_opts o;
