@@ -261,7 +261,11 @@ MSP_API msp_status msp_solve_many(msp_ctx* ctx, const msp_factor_t* f, const voi
 /* The whole of Algorithm 1 in one call: sketch, Nystrom factor, solve.
  * A, b and x may each be device or host memory (host buffers are staged
  * through device buffers owned by the context; pinned host memory is
- * fastest). Parameters as for msp_sketch / msp_nystrom / msp_solve. */
+ * fastest). A host A is copied in row chunks on a copy stream of the
+ * context, overlapped with the sketch and the packing; of a host FP32 A only
+ * the upper triangle (with the diagonal) is read -- A is symmetric, as the
+ * packed A pass already assumes -- and the lower triangle is mirrored on the
+ * device. Parameters as for msp_sketch / msp_nystrom / msp_solve. */
 MSP_API msp_status msp_solve_full(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n,
                           int64_t lda, double lambda, const double* b, double* x,
                           int64_t s, int gamma, double lambda0, int64_t phi,

@@ -236,17 +236,36 @@ msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t
         bool ok = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) == cudaSuccess &&
                   cudaEventRecord(ready, ctx->stream) == cudaSuccess &&
                   cudaStreamWaitEvent(ctx->copy_stream, ready, 0) == cudaSuccess;
+        // FP32 (the symmetric A the packed A pass assumes): only the upper
+        // trapezoid of each 128-row block crosses the host link (about half of
+        // A); the lower tiles are mirrored on the device once their source
+        // rows have landed. FP64: whole rows.
+        const bool half = (dtype == MSP_F32);
         for (int k = 0; ok && k < nchunk; ++k) {
             const int64_t r0 = k * rows, nr = std::min(rows, n - r0);
-            ok = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming) == cudaSuccess &&
-                 cudaMemcpy2DAsync((char*)A + (size_t)r0 * n * ts, n * ts, (const char*)host_chunks + (size_t)r0 * lda * ts,
-                                   lda * ts, n * ts, nr, cudaMemcpyHostToDevice, ctx->copy_stream) == cudaSuccess &&
-                 cudaEventRecord(ev[k], ctx->copy_stream) == cudaSuccess;
+            ok = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming) == cudaSuccess;
+            if (half) {
+                for (int64_t b0 = r0; ok && b0 < r0 + nr; b0 += 128) {
+                    const int64_t bn = std::min<int64_t>(128, n - b0);
+                    ok = cudaMemcpy2DAsync((char*)A + ((size_t)b0 * n + b0) * ts, n * ts,
+                                           (const char*)host_chunks + ((size_t)b0 * lda + b0) * ts, lda * ts,
+                                           (n - b0) * ts, bn, cudaMemcpyHostToDevice, ctx->copy_stream) == cudaSuccess;
+                }
+            } else {
+                ok = ok && cudaMemcpy2DAsync((char*)A + (size_t)r0 * n * ts, n * ts,
+                                             (const char*)host_chunks + (size_t)r0 * lda * ts, lda * ts, n * ts, nr,
+                                             cudaMemcpyHostToDevice, ctx->copy_stream) == cudaSuccess;
+            }
+            ok = ok && cudaEventRecord(ev[k], ctx->copy_stream) == cudaSuccess;
         }
         for (int k = 0; ok && k < nchunk; ++k) {
             const int64_t r0 = k * rows, nr = std::min(rows, n - r0);
             ok = cudaStreamWaitEvent(ctx->stream, ev[k], 0) == cudaSuccess;
             if (!ok) break;
+            if (half && (st = msp_mirror_lower_rows(ctx, (float*)A, n, n, r0 / 128, (r0 + nr + 127) / 128)) != MSP_OK) {
+                ok = false;
+                break;
+            }
             if ((st = msp_sketch_apply_rows(ctx, (const char*)A + (size_t)r0 * n * ts, dtype, nr, n, n, sp,
                                             sk->csr_ptr, sk->csr_ent, gamma, (char*)sk->C + (size_t)r0 * sp * ts)) !=
                     MSP_OK ||

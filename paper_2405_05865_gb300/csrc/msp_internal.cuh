@@ -283,6 +283,8 @@ int64_t msp_packed_tiles(int64_t n);
 msp_status msp_pack_upper(msp_ctx* ctx, const float* A, int64_t lda, int64_t n, float* packed);
 msp_status msp_pack_upper_rows(msp_ctx* ctx, const float* A, int64_t lda, int64_t n, int64_t I0, int64_t I1,
                                float* packed);
+// fill the strictly lower 128-tiles of tile rows [I0, I1) from the upper ones
+msp_status msp_mirror_lower_rows(msp_ctx* ctx, float* A, int64_t lda, int64_t n, int64_t I0, int64_t I1);
 msp_status msp_symv_packed(msp_ctx* ctx, const float* packed, int64_t n, float lam, const float* p,
                            float* part, double* dpart, int grid);
 

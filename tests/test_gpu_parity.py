@@ -333,6 +333,14 @@ def test_solve_full_host_buffers_match_device(ctx, n, pad):
     xd, info_d = ctx.solve_full(torch.from_numpy(A32).cuda(), bh.cuda(), w.lam, s, 8, 0.0, 0, 8, 0x4D5350, **opts)
     assert not xh.is_cuda
     assert np.array_equal(xh.numpy(), xd.cpu().numpy())
+    # only the upper triangle of a host FP32 A is read: garbage below the
+    # diagonal changes nothing
+    junk = big.copy()
+    low = np.tril_indices(n, -1)
+    junk[low] = 7.0
+    Aj = torch.from_numpy(junk).pin_memory()[:, :n]
+    xj, _ = ctx.solve_full(Aj, bh, w.lam, s, 8, 0.0, 0, 8, 0x4D5350, **opts)
+    assert np.array_equal(xj.numpy(), xh.numpy())
     assert info_h["outer_iters"] == info_d["outer_iters"]
     K = A32.astype(np.float64)
     x = xh.numpy()
