@@ -369,41 +369,49 @@ msp_status msp_pack_upper(msp_ctx* ctx, const float* A, int64_t lda, int64_t n, 
     return MSP_OK;
 }
 
-// Lower 128 x 128 tiles (I, J), J < I, of a symmetric row-major A whose upper
-// tiles (and whole diagonal tiles) are in place: A[I][J] = A[J][I]^T. Tile t of
-// the strictly lower order (row by row: t = I (I - 1) / 2 + J) per block;
-// 32 x 33 shared-memory transposes, coalesced both ways.
+// The lower triangle of a symmetric row-major A from its upper triangle (the
+// diagonal included): A[i][j] = A[j][i] for i > j. One 128 x 128 tile (I, J),
+// J <= I, per block, tile t = I (I + 1) / 2 + J; on a diagonal tile only the
+// entries below the diagonal are written. 32 x 33 shared-memory transposes,
+// coalesced both ways.
 __global__ void __launch_bounds__(256) k_mirror_lower(float* __restrict__ A, int64_t lda, int64_t n, int t0) {
     __shared__ float tr[32][33];
+    // tiles (I, J) with J <= I, tile row after tile row: row I starts at I (I + 1) / 2
     const int t = t0 + (int)blockIdx.x;
-    int I = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)t)) * 0.5f);
-    while (I > 1 && (int64_t)I * (I - 1) / 2 > t) --I;
-    while ((int64_t)(I + 1) * I / 2 <= t) ++I;
-    const int J = t - I * (I - 1) / 2;
+    int I = (int)((sqrtf(1.0f + 8.0f * (float)t) - 1.0f) * 0.5f);
+    while (I > 0 && (int64_t)I * (I + 1) / 2 > t) --I;
+    while ((int64_t)(I + 1) * (I + 2) / 2 <= t) ++I;
+    const int J = t - I * (I + 1) / 2;
+    const bool diag = (I == J);
     const int64_t r0 = (int64_t)I * kTile, c0 = (int64_t)J * kTile;   // destination block (rows r0.., cols c0..)
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;             // 32 x 8
     for (int bi = 0; bi < kTile; bi += 32)
         for (int bj = 0; bj < kTile; bj += 32) {
+            if (diag && bj > bi) continue;          // block-uniform: the upper half of a diagonal tile stays
             // read the source block A[c0 + bj + y][r0 + bi + x] (rows of the upper tile)
             for (int y = ty; y < 32; y += 8) {
                 const int64_t sr = c0 + bj + y, sc = r0 + bi + tx;
                 tr[y][tx] = (sr < n && sc < n) ? A[sr * lda + sc] : 0.f;
             }
             __syncthreads();
+            // on a diagonal tile only the strictly lower entries are written; their
+            // sources lie strictly above the diagonal and are never written
             for (int y = ty; y < 32; y += 8) {
                 const int64_t dr = r0 + bi + y, dc = c0 + bj + tx;
-                if (dr < n && dc < n) A[dr * lda + dc] = tr[tx][y];
+                if (dr < n && dc < n && (!diag || dr > dc)) A[dr * lda + dc] = tr[tx][y];
             }
             __syncthreads();
         }
 }
 
+// Fills the lower triangle of tile rows [I0, I1) (the diagonal tiles included)
+// from the upper triangle, which must already be in place for those rows and
+// for every row above them.
 msp_status msp_mirror_lower_rows(msp_ctx* ctx, float* A, int64_t lda, int64_t n, int64_t I0, int64_t I1) {
     const int64_t nt = (n + kTile - 1) / kTile;
     I1 = std::min(I1, nt);
     if (I0 >= I1) return MSP_OK;
-    const int64_t t0 = I0 * (I0 - 1) / 2, t1 = I1 * (I1 - 1) / 2;
-    if (t1 <= t0) return MSP_OK;
+    const int64_t t0 = I0 * (I0 + 1) / 2, t1 = I1 * (I1 + 1) / 2;
     k_mirror_lower<<<(unsigned)(t1 - t0), 256, 0, ctx->stream>>>(A, lda, n, (int)t0);
     MSP_CHECK_LAUNCH(ctx);
     return MSP_OK;
