@@ -697,7 +697,9 @@ def run_msp(args, rank, world, local):
         torch.cuda.synchronize(dev)
         t1 = time.perf_counter()
         et = max_over_ranks(t1 - t0, dev)
-        e2e = {"value": job_rate(args.steps, world, et), "unit": "solves/s", "h2d_bytes_per_step": 4 * n * n + 8 * n,
+        # a host FP32 A crosses the link as the upper trapezoid of each 128-row block
+        a_bytes = sum(4 * min(128, n - b0) * (n - b0) for b0 in range(0, n, 128))
+        e2e = {"value": job_rate(args.steps, world, et), "unit": "solves/s", "h2d_bytes_per_step": a_bytes + 8 * n,
                "d2h_bytes_per_step": 8 * n, "backward_err": e2e_info["backward_err"]}
 
     batched = None
