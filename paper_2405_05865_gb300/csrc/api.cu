@@ -146,6 +146,7 @@ void msp_destroy(msp_ctx* ctx) {
     DeviceGuard g(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
+    if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
     if (ctx->scratch) cudaFree(ctx->scratch);
     if (ctx->stage) cudaFree(ctx->stage);
     if (ctx->ctl) cudaFree(ctx->ctl);
@@ -176,13 +177,56 @@ msp_status msp_sketch_pattern(msp_ctx* ctx, int64_t n, int64_t rows, int gamma, 
 
 void msp_sketch_destroy(msp_sketch_t* sk) {
     if (!sk) return;
+    if (sk->ready) {
+        cudaStreamWaitEvent(sk->stream, sk->ready, 0);
+        cudaEventDestroy(sk->ready);
+    }
     for (void* p : {(void*)sk->idx, (void*)sk->sgn, (void*)sk->csr_ptr, (void*)sk->csr_ent, sk->C,
-                    (void*)sk->packed})
+                    (void*)sk->packed, (void*)sk->stats})
         if (p) cudaFreeAsync(p, sk->stream);
     delete sk;
 }
 
 }  // extern "C"
+
+// The passes over A that only the solve needs -- the packed upper tiles of an
+// FP32 A (unless the chunked host copy packed them already) and the row
+// statistics of the norm bound -- go to the side stream once C is formed, so
+// that they overlap the Nystrom factor (whose Cholesky leaves hold one SM);
+// sk->ready marks their end.
+static msp_status sketch_side_passes(msp_ctx* ctx, msp_sketch_s* sk, const void* A, msp_dtype dtype,
+                                     int64_t lda, bool do_pack) {
+    const int64_t n = sk->n;
+    MSP_TRY(msp_alloc(ctx, (void**)&sk->stats, (size_t)(3 * n + 1) * 8));
+    if (!ctx->copy_stream && cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->copy_stream = nullptr;
+        return msp_set_error(ctx, MSP_ECUDA, "sketch: side stream creation failed");
+    }
+    cudaEvent_t fork = nullptr;
+    bool ok = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&sk->ready, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventRecord(fork, ctx->stream) == cudaSuccess &&
+              cudaStreamWaitEvent(ctx->copy_stream, fork, 0) == cudaSuccess;
+    if (fork) cudaEventDestroy(fork);
+    if (!ok) {
+        cudaGetLastError();
+        return msp_set_error(ctx, MSP_ECUDA, "sketch: side stream fork failed");
+    }
+    // the launches below are made on the side stream
+    cudaStream_t main_stream = ctx->stream;
+    ctx->stream = ctx->copy_stream;
+    msp_status st = MSP_OK;
+    if (do_pack && sk->packed) st = msp_pack_upper(ctx, (const float*)A, lda, n, sk->packed);
+    if (st == MSP_OK) st = msp_norm_lb_launch(ctx, A, dtype, n, lda, sk->stats, sk->stats + 3 * n);
+    ctx->stream = main_stream;
+    if (st != MSP_OK) return st;
+    if (cudaEventRecord(sk->ready, ctx->copy_stream) != cudaSuccess) {
+        cudaGetLastError();
+        return msp_set_error(ctx, MSP_ECUDA, "sketch: side stream join failed");
+    }
+    return MSP_OK;
+}
 
 msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n,
                            int64_t lda, int64_t s, int gamma, uint64_t seed, bool pack,
@@ -288,8 +332,13 @@ msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t
             return st;
         }
     } else if ((st = msp_sketch_apply(ctx, A, dtype, n, lda, sp, sk->csr_ptr, sk->csr_ent, gamma, sk->C)) !=
-                   MSP_OK ||
-               (sk->packed && (st = msp_pack_upper(ctx, (const float*)A, lda, n, sk->packed)) != MSP_OK)) {
+               MSP_OK) {
+        cudaStreamSynchronize(ctx->stream);
+        msp_sketch_destroy(sk);
+        return st;
+    }
+    if (pack && (st = sketch_side_passes(ctx, sk, A, dtype, host_chunks ? n : lda, !host_chunks)) != MSP_OK) {
+        if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
         cudaStreamSynchronize(ctx->stream);
         msp_sketch_destroy(sk);
         return st;
@@ -472,9 +521,11 @@ static msp_status solve_impl(msp_ctx* ctx, const msp_factor_s* f, const void* A,
         return msp_set_error(ctx, MSP_EINVAL, "solve: bad options");
     const msp_dtype wt = f->dtype;
     const size_t ts = dtype_size(wt);
-    // the sketch's packed upper tiles stand in for A when A is the sketched matrix
-    const float* packed = (dtype == MSP_F32 && f->sk->packed && A == f->sk->A_src)
-                              ? f->sk->packed : nullptr;
+    // the sketch's packed upper tiles and norm-bound statistics stand in for A
+    // when A is the sketched matrix (written on the sketch's side stream)
+    const bool sketched_A = (A == f->sk->A_src);
+    if (sketched_A && f->sk->ready) MSP_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->stream, f->sk->ready, 0));
+    const float* packed = (dtype == MSP_F32 && f->sk->packed && sketched_A) ? f->sk->packed : nullptr;
     if (o->criterion != MSP_STOP_RESIDUAL && o->criterion != MSP_STOP_BACKWARD)
         return msp_set_error(ctx, MSP_EINVAL, "solve: unknown criterion %d", o->criterion);
     const bool crit_bw = o->criterion == MSP_STOP_BACKWARD;
@@ -532,8 +583,14 @@ static msp_status solve_impl(msp_ctx* ctx, const msp_factor_s* f, const void* A,
         return rr <= o->tol * o->tol * bb;
     };
     MSP_CUDA_TRY(ctx, cudaMemsetAsync(scal, 0, 32, ctx->stream));
-    if (crit_bw && (st = msp_norm_lb_launch(ctx, A, dtype, n, lda, nwork, scal + 2)) != MSP_OK)
+    if (crit_bw && sketched_A && f->sk->stats) {
+        if (cudaMemcpyAsync(scal + 2, f->sk->stats + 3 * n, 8, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return finish(msp_set_error(ctx, MSP_ECUDA, "solve: norm bound copy failed"));
+        }
+    } else if (crit_bw && (st = msp_norm_lb_launch(ctx, A, dtype, n, lda, nwork, scal + 2)) != MSP_OK) {
         return finish(st);
+    }
     if ((st = msp_norm2(ctx, b, n, scal + 0)) != MSP_OK) return finish(st);
     MSP_CUDA_TRY(ctx, cudaMemcpyAsync(r64, b, n * 8, cudaMemcpyDeviceToDevice, ctx->stream));
     MSP_CUDA_TRY(ctx, cudaMemcpyAsync(scal + 1, scal + 0, 8, cudaMemcpyDeviceToDevice, ctx->stream));

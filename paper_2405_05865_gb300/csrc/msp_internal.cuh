@@ -35,7 +35,9 @@ struct msp_ctx {
     cudaEvent_t* events = nullptr;
     int n_events = 0;
     // worker contexts (own streams) for concurrent batch set-up, created lazily
-    cudaStream_t copy_stream = nullptr;   // host-to-device copies overlapped with compute
+    // side stream: host-to-device copies, and the passes over A that only the
+    // solve needs (packing, the norm bound), overlapped with the factor
+    cudaStream_t copy_stream = nullptr;
     msp_ctx** lanes = nullptr;
     cudaStream_t* lane_streams = nullptr;
     int n_lanes = 0;
@@ -60,6 +62,12 @@ struct msp_sketch_s {
     void* C = nullptr;           // n x s_pad, dtype
     float* packed = nullptr;     // FP32 A: upper 128 x 128 tiles (see symv.cu)
     const void* A_src = nullptr; // the A the sketch (and packed copy) came from
+    // norm bound of A_src for the backward-error rule: row sums, their
+    // rounding bounds and row squares (3 n), then the bound (see norms.cu)
+    double* stats = nullptr;
+    // recorded on the side stream once packed and stats are written; every
+    // reader (and the destroy) waits on it
+    cudaEvent_t ready = nullptr;
 };
 
 struct msp_factor_s {

@@ -4,12 +4,12 @@
 // both terms at most |A|_2 (a column of A is A e_i; the second is the Rayleigh
 // quotient of the all-ones vector). One pass over A.
 //
-// k_row_stats  one warp per row: the row is summed in chunks of 16 entries
+// k_row_stats  one warp per row: the row is summed in chunks of 64 entries
 //              per lane in FP32 (sum, sum of |.|, sum of squares), chunk
 //              results combined in FP64, with the rounding bound of every
 //              FP32 chunk kept beside it (the FP64 pipe of this part is 1/64
-//              of the FP32 rate, so a per-entry FP64 sum would set the pass's
-//              speed).
+//              of the FP32 rate: with chunks of 16 the FP64 conversions and
+//              sums alone kept it ~80% busy and held the pass to ~4 TB/s).
 // k_norm_lb    one block: max of the row squares and the FP64 sum of the row
 //              sums in a fixed order, each lowered by its rounding bound, so
 //              the result stays at most |A|_2.
@@ -17,11 +17,11 @@
 
 namespace {
 
-// FP32 chunk of 16 terms: |fl(sum) - sum| <= 15 u sum|t| (recursive
-// summation, u = 2^-24); the exact sum of squares (positive terms) is at
-// least (1 - 19 u) of the computed one, FP32 rounding of FP64 entries
-// included.
-constexpr int kChunk = 16;
+// FP32 chunk of kChunk terms: |fl(sum) - sum| <= (kChunk - 1) u sum|t|
+// (recursive summation, u = 2^-24); the exact sum of squares (positive terms)
+// is at least (1 - (kChunk + 3) u) of the computed one, FP32 rounding of FP64
+// entries included.
+constexpr int kChunk = 64;
 constexpr double kU32 = 5.9604644775390625e-8;
 
 template <typename T>
@@ -35,24 +35,28 @@ __global__ void __launch_bounds__(256) k_row_stats(const T* __restrict__ A, int6
     double s = 0.0, e = 0.0, q = 0.0;
     int64_t j = 0;
     if constexpr (sizeof(T) == 4) {
-        // 16-byte loads, four per lane in flight per chunk of 16 entries
+        // 16-byte loads, four per lane in flight; a chunk is four such
+        // rounds (64 entries per lane)
+        static_assert(kChunk == 64, "the vector path sums 4 x 4 float4 per chunk");
         if ((((uintptr_t)row) & 15) == 0) {
             const int64_t n4 = n & ~(int64_t)127;
-            for (; j < n4; j += 4 * 128) {
-                float4 v[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    v[u] = (j + u * 128 < n4) ? __ldcs(reinterpret_cast<const float4*>(row + j + u * 128) + lane)
-                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+            while (j < n4) {
                 float cs = 0.f, ca = 0.f, cq = 0.f;
+                for (int round = 0; round < 4 && j < n4; ++round, j += 4 * 128) {
+                    float4 v[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const float w4[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+                    for (int u = 0; u < 4; ++u)
+                        v[u] = (j + u * 128 < n4) ? __ldcs(reinterpret_cast<const float4*>(row + j + u * 128) + lane)
+                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        cs += w4[c];
-                        ca += fabsf(w4[c]);
-                        cq = fmaf(w4[c], w4[c], cq);
+                    for (int u = 0; u < 4; ++u) {
+                        const float w4[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            cs += w4[c];
+                            ca += fabsf(w4[c]);
+                            cq = fmaf(w4[c], w4[c], cq);
+                        }
                     }
                 }
                 s += (double)cs;
@@ -81,8 +85,8 @@ __global__ void __launch_bounds__(256) k_row_stats(const T* __restrict__ A, int6
     q = msp::warp_sum(q);
     if (lane == 0) {
         rowsum[i] = s;
-        // chunk summation (15 u) plus, for FP64 input, the rounding of each
-        // entry to FP32 (u)
+        // chunk summation ((kChunk - 1) u) plus, for FP64 input, the
+        // rounding of each entry to FP32 (u)
         rowerr[i] = (kChunk + 1) * kU32 * e * (1.0 + 1e-6);
         rowsq[i] = q;
     }
@@ -117,7 +121,7 @@ __global__ void __launch_bounds__(1024) k_norm_lb(const double* __restrict__ row
             te += serr[k];
             tm = fmax(tm, smax[k]);
         }
-        // FP64 combination error (n^2 / 16 chunk terms) is far below the
+        // FP64 combination error (n^2 / kChunk chunk terms) is far below the
         // FP32 chunk bound; 2e-6 covers it with room
         const double col = sqrt(tm * (1.0 - (kChunk + 3) * kU32) * (1.0 - 2e-6));
         const double ones = (ts - te * (1.0 + 2e-6) - 2e-6 * fabs(ts)) / (double)n;
