@@ -213,12 +213,15 @@ static msp_status sketch_side_passes(msp_ctx* ctx, msp_sketch_s* sk, const void*
         cudaGetLastError();
         return msp_set_error(ctx, MSP_ECUDA, "sketch: side stream fork failed");
     }
-    // the launches below are made on the side stream
+    // the launches below are made on the side stream, two blocks per SM each
+    // (grid-stride): a full grid of them would hold every SM and queue the
+    // factor's kernels behind it
     cudaStream_t main_stream = ctx->stream;
     ctx->stream = ctx->copy_stream;
+    const int bg = 2 * std::max(1, ctx->num_sms);
     msp_status st = MSP_OK;
-    if (do_pack && sk->packed) st = msp_pack_upper(ctx, (const float*)A, lda, n, sk->packed);
-    if (st == MSP_OK) st = msp_norm_lb_launch(ctx, A, dtype, n, lda, sk->stats, sk->stats + 3 * n);
+    if (do_pack && sk->packed) st = msp_pack_upper(ctx, (const float*)A, lda, n, sk->packed, bg);
+    if (st == MSP_OK) st = msp_norm_lb_launch(ctx, A, dtype, n, lda, sk->stats, sk->stats + 3 * n, bg);
     ctx->stream = main_stream;
     if (st != MSP_OK) return st;
     if (cudaEventRecord(sk->ready, ctx->copy_stream) != cudaSuccess) {

@@ -24,14 +24,10 @@ namespace {
 constexpr int kChunk = 64;
 constexpr double kU32 = 5.9604644775390625e-8;
 
+// The statistics of one row, by one warp.
 template <typename T>
-__global__ void __launch_bounds__(256) k_row_stats(const T* __restrict__ A, int64_t n, int64_t lda,
-                                                  double* __restrict__ rowsum, double* __restrict__ rowerr,
-                                                  double* __restrict__ rowsq) {
-    const int lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (i >= n) return;
-    const T* row = A + i * lda;
+__device__ __forceinline__ void row_stats_one(const T* __restrict__ row, int64_t n, int lane,
+                                              double* rowsum, double* rowerr, double* rowsq) {
     double s = 0.0, e = 0.0, q = 0.0;
     int64_t j = 0;
     if constexpr (sizeof(T) == 4) {
@@ -84,12 +80,21 @@ __global__ void __launch_bounds__(256) k_row_stats(const T* __restrict__ A, int6
     e = msp::warp_sum(e);
     q = msp::warp_sum(q);
     if (lane == 0) {
-        rowsum[i] = s;
+        *rowsum = s;
         // chunk summation ((kChunk - 1) u) plus, for FP64 input, the
         // rounding of each entry to FP32 (u)
-        rowerr[i] = (kChunk + 1) * kU32 * e * (1.0 + 1e-6);
-        rowsq[i] = q;
+        *rowerr = (kChunk + 1) * kU32 * e * (1.0 + 1e-6);
+        *rowsq = q;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_row_stats(const T* __restrict__ A, int64_t n, int64_t lda,
+                                                  double* __restrict__ rowsum, double* __restrict__ rowerr,
+                                                  double* __restrict__ rowsq) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); i < n; i += (int64_t)gridDim.x * 8)
+        row_stats_one<T>(A + i * lda, n, lane, rowsum + i, rowerr + i, rowsq + i);
 }
 
 __global__ void __launch_bounds__(1024) k_norm_lb(const double* __restrict__ rowsum,
@@ -132,8 +137,10 @@ __global__ void __launch_bounds__(1024) k_norm_lb(const double* __restrict__ row
 }  // namespace
 
 msp_status msp_norm_lb_launch(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t n, int64_t lda,
-                              double* work, double* out_dev) {
-    const unsigned blocks = (unsigned)((n + 7) / 8);
+                              double* work, double* out_dev, int max_blocks) {
+    int64_t nb = (n + 7) / 8;
+    if (max_blocks > 0) nb = std::min<int64_t>(nb, max_blocks);
+    const unsigned blocks = (unsigned)nb;
     if (dt == MSP_F32)
         k_row_stats<float><<<blocks, 256, 0, ctx->stream>>>((const float*)A, n, lda, work, work + n,
                                                            work + 2 * n);

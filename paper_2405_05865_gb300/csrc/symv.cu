@@ -118,30 +118,42 @@ __device__ inline void tile_coords(int t, int nt, int& I, int& J) {
     J = i + (t - (int)((long long)i * nt - (long long)i * (i - 1) / 2));
 }
 
-// Pack the upper tiles of dense row-major A (n x n, lda) into `packed`.
+// Pack the upper tiles [tile0, tile0 + count) of dense row-major A (n x n,
+// lda) into `packed`; a block takes tiles tile0 + blockIdx.x, + gridDim.x, ...
+// (one tile per block, or a few blocks per SM that leave room beside them).
 __global__ void __launch_bounds__(256) k_pack_upper(const float* __restrict__ A, int64_t lda,
-                                                   int64_t n, int nt, int tile0, float* __restrict__ packed) {
-    int I, J;
-    const int tix = tile0 + (int)blockIdx.x;
-    tile_coords(tix, nt, I, J);
-    float* dst = packed + (int64_t)tix * kTile * kTile;
-    const int64_t r0 = (int64_t)I * kTile, c0 = (int64_t)J * kTile;
-    const bool vec = (lda % 4 == 0) && (((uintptr_t)A & 15) == 0) && (c0 + kTile <= n);
-    for (int e = threadIdx.x; e < kTile * kTile / 4; e += blockDim.x) {
-        const int r = e / (kTile / 4), c4 = (e % (kTile / 4)) * 4;
-        const int64_t gr = r0 + r, gc = c0 + c4;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (gr < n) {
-            if (vec) {
-                v = __ldcs(reinterpret_cast<const float4*>(A + gr * lda + gc));
-            } else {
-                if (gc + 0 < n) v.x = A[gr * lda + gc + 0];
-                if (gc + 1 < n) v.y = A[gr * lda + gc + 1];
-                if (gc + 2 < n) v.z = A[gr * lda + gc + 2];
-                if (gc + 3 < n) v.w = A[gr * lda + gc + 3];
+                                                   int64_t n, int nt, int tile0, int count,
+                                                   float* __restrict__ packed) {
+    constexpr int kPer = kTile * kTile / 4 / 256;     // float4 per thread per tile (16)
+    for (int tix = tile0 + (int)blockIdx.x; tix < tile0 + count; tix += (int)gridDim.x) {
+        int I, J;
+        tile_coords(tix, nt, I, J);
+        float* dst = packed + (int64_t)tix * kTile * kTile;
+        const int64_t r0 = (int64_t)I * kTile, c0 = (int64_t)J * kTile;
+        const bool vec = (lda % 4 == 0) && (((uintptr_t)A & 15) == 0) && (c0 + kTile <= n);
+        // four loads in flight per thread before their stores
+        for (int g = 0; g < kPer; g += 4) {
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = (g + u) * 256 + (int)threadIdx.x;
+                const int r = e / (kTile / 4), c4 = (e % (kTile / 4)) * 4;
+                const int64_t gr = r0 + r, gc = c0 + c4;
+                v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (gr < n) {
+                    if (vec) {
+                        v[u] = __ldcs(reinterpret_cast<const float4*>(A + gr * lda + gc));
+                    } else {
+                        if (gc + 0 < n) v[u].x = A[gr * lda + gc + 0];
+                        if (gc + 1 < n) v[u].y = A[gr * lda + gc + 1];
+                        if (gc + 2 < n) v[u].z = A[gr * lda + gc + 2];
+                        if (gc + 3 < n) v[u].w = A[gr * lda + gc + 3];
+                    }
+                }
             }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) reinterpret_cast<float4*>(dst)[(g + u) * 256 + (int)threadIdx.x] = v[u];
         }
-        reinterpret_cast<float4*>(dst)[e] = v;
     }
 }
 
@@ -360,11 +372,12 @@ int64_t msp_packed_tiles(int64_t n) {
     return nt * (nt + 1) / 2;
 }
 
-msp_status msp_pack_upper(msp_ctx* ctx, const float* A, int64_t lda, int64_t n, float* packed) {
+msp_status msp_pack_upper(msp_ctx* ctx, const float* A, int64_t lda, int64_t n, float* packed, int max_blocks) {
     const int64_t nt = (n + kTile - 1) / kTile;
     const int64_t ntiles = nt * (nt + 1) / 2;
     if (ntiles >= (1ll << 31)) return msp_set_error(ctx, MSP_EINVAL, "pack: n too large");
-    k_pack_upper<<<(unsigned)ntiles, 256, 0, ctx->stream>>>(A, lda, n, (int)nt, 0, packed);
+    const int64_t blocks = max_blocks > 0 ? std::min<int64_t>(ntiles, max_blocks) : ntiles;
+    k_pack_upper<<<(unsigned)blocks, 256, 0, ctx->stream>>>(A, lda, n, (int)nt, 0, (int)ntiles, packed);
     MSP_CHECK_LAUNCH(ctx);
     return MSP_OK;
 }
@@ -425,7 +438,7 @@ msp_status msp_pack_upper_rows(msp_ctx* ctx, const float* A, int64_t lda, int64_
     if (I0 < 0 || I1 > nt || I0 >= I1) return MSP_OK;
     auto start = [&](int64_t i) { return i * nt - i * (i - 1) / 2; };
     const int64_t t0 = start(I0), t1 = start(I1);
-    k_pack_upper<<<(unsigned)(t1 - t0), 256, 0, ctx->stream>>>(A, lda, n, (int)nt, (int)t0, packed);
+    k_pack_upper<<<(unsigned)(t1 - t0), 256, 0, ctx->stream>>>(A, lda, n, (int)nt, (int)t0, (int)(t1 - t0), packed);
     MSP_CHECK_LAUNCH(ctx);
     return MSP_OK;
 }
