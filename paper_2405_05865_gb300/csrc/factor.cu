@@ -220,7 +220,8 @@ __global__ void __launch_bounds__(256) k_dgemm(int64_t m, int64_t n, int64_t k, 
 }
 
 constexpr int kLeafSmem = 2 * 64 * 65 * (int)sizeof(double);
-constexpr int kLeafThreads = 128;   // 4 warps: one per SM sub-partition's FP64 unit
+constexpr int kLeafUpd = 128;                 // four update warps (16 x 8 thread grid)
+constexpr int kLeafThreads = kLeafUpd + 32;   // and the pivot warp
 
 // 1/sqrt(d) for a positive normal FP64 d: FP32 reciprocal square root as the
 // seed, then two Newton-Raphson steps y <- y (3 - d y^2) / 2 for f(y) =
@@ -236,81 +237,102 @@ __device__ inline double rsqrt_newton(double d) {
     return y;
 }
 
+// 1/d for a positive normal FP64 d: FP32 reciprocal as the seed, then two
+// Newton-Raphson steps r <- r + r (1 - d r) for f(r) = 1/r - d.
+__device__ inline double rcp_newton(double d) {
+    if (!(d >= 1e-30 && d <= 1e30)) return 1.0 / d;
+    double r = (double)(1.0f / (float)d);
+    r = fma(r, fma(-d, r, 1.0), r);
+    r = fma(r, fma(-d, r, 1.0), r);
+    return r;
+}
+
 // Cholesky and inverse of an nb x nb (nb <= 64) FP64 block on one SM:
 // M = L L^T (lower triangle of M overwritten with L), X = L^{-1}.
-// Right-looking factorisation, two block barriers per pivot: every warp
-// computes the pivot's 1/sqrt itself (no barrier to publish it), scales the
-// column, then the trailing lower triangle is updated. The inverse is a
-// blocked forward substitution over 16-row blocks: the block's right-hand
-// side from the rows already inverted (independent dot products), then a
-// 16-step substitution per column, so the longest dependent chain is ~16 +
-// 48 instead of ~nb^2 / 2.
+// One elimination sweep in LDL^T form: at step k every row i > k takes
+// t_i = a_ik / d_k and updates both its Schur-complement entries,
+// a_ij -= t_i a_jk (k < j < i), and its row of X, x_ij -= t_i x_kj (j <= k),
+// with X starting as the identity -- the same row operations turn the
+// identity into L_u^{-1} for A = L_u D L_u^T. Every update of a step is
+// independent (no substitution chains), and the two parts together keep the
+// work per step near n^2 / 2. The diagonal is kept apart by a fifth warp,
+// which also forms the next pivot d_{k+1} and 1/d_{k+1} while the update
+// warps work, so a step costs one barrier. At the end L = L_u D^{1/2}
+// (l_ik = a_ik / sqrt(d_k), l_kk = sqrt(d_k)) and L^{-1} = D^{-1/2} L_u^{-1}.
+// A pivot that is not positive and finite sets *fail (and is replaced by 1).
 __global__ void __launch_bounds__(kLeafThreads) k_chol_leaf(double* __restrict__ M, double* __restrict__ X,
                                                            int64_t ld, int nb, int* __restrict__ fail) {
     extern __shared__ __align__(16) double leaf_smem[];
     double (*a)[65] = reinterpret_cast<double (*)[65]>(leaf_smem);
     double (*x)[65] = reinterpret_cast<double (*)[65]>(leaf_smem + 64 * 65);
-    __shared__ double inv_d[64], rdiag[64];
+    __shared__ double piv[64], rinv[64], rs[64];
     __shared__ int bad;
     const int tid = threadIdx.x, lane = tid & 31;
+    const bool pivot_warp = tid >= kLeafUpd;
     if (tid == 0) bad = 0;
     for (int e = tid; e < nb * nb; e += kLeafThreads) {
         const int i = e / nb, j = e % nb;
         a[i][j] = (j <= i) ? M[i * ld + j] : 0.0;
-        x[i][j] = 0.0;
+        x[i][j] = (i == j) ? 1.0 : 0.0;
     }
     __syncthreads();
-    const int tx = tid & 7, ty = tid >> 3;      // 16 x 8 thread grid for the trailing update
-    for (int kc = 0; kc < nb; ++kc) {
-        double y = 0.0;
+    // pivot warp: the diagonal of rows lane and lane + 32
+    double dg0 = 1.0, dg1 = 1.0;
+    if (pivot_warp) {
+        if (lane < nb) dg0 = a[lane][lane];
+        if (lane + 32 < nb) dg1 = a[lane + 32][lane + 32];
         if (lane == 0) {
-            double d = a[kc][kc];
+            double d = dg0;
             if (!(d > 0.0) || !isfinite(d)) {
-                if (tid == 0) bad = 1;
+                bad = 1;
                 d = 1.0;
             }
-            y = rsqrt_newton(d);
-            if (tid == 0) {
-                inv_d[kc] = y;
-                rdiag[kc] = d * y;
-            }
+            piv[0] = d;
+            rinv[0] = rcp_newton(d);
         }
-        y = __shfl_sync(0xffffffffu, y, 0);
-        for (int i = kc + 1 + tid; i < nb; i += kLeafThreads) a[i][kc] *= y;
-        __syncthreads();
-        for (int i = kc + 1 + ty; i < nb; i += 16) {
-            const double li = a[i][kc];
-            for (int j = kc + 1 + tx; j <= i; j += 8) a[i][j] = fma(-li, a[j][kc], a[i][j]);
+    }
+    __syncthreads();
+    // update threads: row offsets interleaved over the warps, so that the
+    // last steps (few rows) still use all four
+    const int tx = tid & 7, ty = tid >> 3;
+    const int rr = ((ty & 3) << 2) | (ty >> 2);
+    for (int k = 0; k < nb; ++k) {
+        const double rk = rinv[k];
+        if (!pivot_warp) {
+            for (int i = k + 1 + rr; i < nb; i += 16) {
+                const double ti = a[i][k] * rk;
+                for (int j = tx; j <= k; j += 8) x[i][j] = fma(-ti, x[k][j], x[i][j]);
+                for (int j = k + 1 + tx; j < i; j += 8) a[i][j] = fma(-ti, a[j][k], a[i][j]);
+            }
+        } else if (k + 1 < nb) {
+            if (lane > k && lane < nb) {
+                const double ti = a[lane][k] * rk;
+                dg0 = fma(-ti, a[lane][k], dg0);
+            }
+            if (lane + 32 > k && lane + 32 < nb) {
+                const double ti = a[lane + 32][k] * rk;
+                dg1 = fma(-ti, a[lane + 32][k], dg1);
+            }
+            const int kn = k + 1;
+            if (lane == (kn & 31)) {
+                double d = kn < 32 ? dg0 : dg1;
+                if (!(d > 0.0) || !isfinite(d)) {
+                    bad = 1;
+                    d = 1.0;
+                }
+                piv[kn] = d;
+                rinv[kn] = rcp_newton(d);
+            }
         }
         __syncthreads();
     }
-    // X = L^{-1}, row blocks of 16
-    for (int r0 = 0; r0 < nb; r0 += 16) {
-        const int r1 = min(nb, r0 + 16);
-        // right-hand side of the block's rows for the columns left of it:
-        // x[i][j] = -sum_{q=j}^{r0-1} l_iq x_qj  (scaled by 1/l_ii below)
-        for (int e = tid; e < (r1 - r0) * r0; e += kLeafThreads) {
-            const int i = r0 + e / r0, j = e % r0;
-            double v = 0.0;
-            for (int q = j; q < r0; ++q) v = fma(a[i][q], x[q][j], v);
-            x[i][j] = -v;
-        }
-        __syncthreads();
-        // substitution inside the block, one thread per column j < r1
-        for (int j = tid; j < r1; j += kLeafThreads) {
-            for (int i = max(r0, j); i < r1; ++i) {
-                double v = (i == j) ? 1.0 : x[i][j];
-                for (int q = max(r0, j); q < i; ++q) v = fma(-a[i][q], x[q][j], v);
-                x[i][j] = v * inv_d[i];
-            }
-        }
-        __syncthreads();
-    }
+    for (int k = tid; k < nb; k += kLeafThreads) rs[k] = rsqrt_newton(piv[k]);
+    __syncthreads();
     for (int e = tid; e < nb * nb; e += kLeafThreads) {
         const int i = e / nb, j = e % nb;
-        if (j < i) M[i * ld + j] = a[i][j];
-        else if (j == i) M[i * ld + j] = rdiag[i];
-        X[i * ld + j] = (j <= i) ? x[i][j] : 0.0;
+        if (j < i) M[i * ld + j] = a[i][j] * rs[j];
+        else if (j == i) M[i * ld + j] = piv[i] * rs[i];
+        X[i * ld + j] = (j <= i) ? x[i][j] * rs[i] : 0.0;
     }
     if (tid == 0 && bad) atomicExch(fail, 1);
 }
