@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(256) k_dgemm(int64_t m, int64_t n, int64_t k, 
 }
 
 constexpr int kLeafSmem = 2 * 64 * 65 * (int)sizeof(double);
-constexpr int kLeafUpd = 128;                 // four update warps (16 x 8 thread grid)
+constexpr int kLeafUpd = 256;                 // eight update warps (32 x 8 thread grid)
 constexpr int kLeafThreads = kLeafUpd + 32;   // and the pivot warp
 
 // 1/sqrt(d) for a positive normal FP64 d: FP32 reciprocal square root as the
@@ -293,13 +293,13 @@ __global__ void __launch_bounds__(kLeafThreads) k_chol_leaf(double* __restrict__
     }
     __syncthreads();
     // update threads: row offsets interleaved over the warps, so that the
-    // last steps (few rows) still use all four
+    // last steps (few rows) still use all eight
     const int tx = tid & 7, ty = tid >> 3;
-    const int rr = ((ty & 3) << 2) | (ty >> 2);
+    const int rr = ((ty & 3) << 3) | (ty >> 2);
     for (int k = 0; k < nb; ++k) {
         const double rk = rinv[k];
         if (!pivot_warp) {
-            for (int i = k + 1 + rr; i < nb; i += 16) {
+            for (int i = k + 1 + rr; i < nb; i += 32) {
                 const double ti = a[i][k] * rk;
                 for (int j = tx; j <= k; j += 8) x[i][j] = fma(-ti, x[k][j], x[i][j]);
                 for (int j = k + 1 + tx; j < i; j += 8) a[i][j] = fma(-ti, a[j][k], a[i][j]);
@@ -411,10 +411,12 @@ msp_status dgemm(msp_ctx* ctx, bool ta, bool tb, int64_t m, int64_t n, int64_t k
 }
 
 // Recursive Cholesky + inverse of the n x n block at offset `off` of M (ld),
-// inverse into X (same offsets); T1/T2 are n x n temporaries (ld).
+// inverse into X (same offsets); T1/T2 are n x n temporaries (ld). Leaves of
+// at most 32: a leaf runs on one SM, whose FP64 pipe bounds it (its work
+// grows as nb^3), while the products of the recursion spread over all SMs.
 msp_status chol_inv(msp_ctx* ctx, double* M, double* X, double* T1, double* T2, int64_t ld,
                     int64_t off, int64_t n, int* fail) {
-    if (n <= 64) {
+    if (n <= 32) {
         // set once per device; batch set-up calls this from several threads
         static std::atomic<bool> attr_set[64];
         const int d = ctx->device;
@@ -429,7 +431,7 @@ msp_status chol_inv(msp_ctx* ctx, double* M, double* X, double* T1, double* T2, 
         MSP_CHECK_LAUNCH(ctx);
         return MSP_OK;
     }
-    int64_t n1 = std::max<int64_t>(64, (n / 2) / 64 * 64);
+    int64_t n1 = std::max<int64_t>(32, (n / 2) / 32 * 32);
     int64_t n2 = n - n1;
     double* A21 = M + (off + n1) * ld + off;
     double* A22 = M + (off + n1) * ld + off + n1;
