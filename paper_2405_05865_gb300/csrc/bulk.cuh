@@ -89,11 +89,6 @@ __device__ inline void cp_async16(void* dst, const void* src, bool valid) {
                  : "memory");
 }
 
-// 4-byte async copy global -> shared (both addresses 4-byte aligned).
-__device__ inline void cp_async4(void* dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-
 __device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 
 template <int N>

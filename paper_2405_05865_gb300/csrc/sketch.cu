@@ -5,7 +5,6 @@
 //     ~n*gamma/s source columns from a shared-memory tile of A,
 //   * row gathers out[r,:] = scale * sum_{(j,sign) in list(r)} sign * in[j,:],
 //     which give W = Pi^T C = S C and C~ = Phi C.
-#include "bulk.cuh"
 #include "msp_internal.cuh"
 
 #include <algorithm>
@@ -277,217 +276,6 @@ msp_status launch_sketch_apply_r(msp_ctx* ctx, const T* A, int64_t lda, int64_t 
     return MSP_OK;
 }
 
-// ------------------------------------------------- C = A Pi, FP32, by rows
-//
-// One block per 32 rows of A, one lane per row; the 16 warps split the s_pad
-// output columns (CPW = s_pad / 16 accumulators per lane, in registers). A is
-// walked in chunks of J columns (the rows j of Pi); for every chunk the block
-// stages, double-buffered with async copies:
-//   * the 32 x J tile of A, row-major with a row stride of J + 1 floats, so
-//     that the 32 lanes reading one column jl of the tile hit 32 banks;
-//   * the chunk's entries of Pi^T, column by column (below);
-//   * the start of every sketch column within them.
-// An entry (jl, sign) of the warp's current column is then one broadcast
-// read, one conflict-free 128-byte read of the tile and one add per lane.
-// Each column's entries are summed in increasing j, chunk after chunk -- the
-// order of the column-gather kernel above, so C is the same to the bit. The
-// 32 x s_pad result goes out through shared memory (row stride s_pad + 1) in
-// coalesced rows.
-//
-// Entry layout: for chunk t (columns [tJ, (t+1)J) of A) the entries of
-// sketch column c with j in the chunk, (j - tJ) << 1 | negative, columns in
-// order. Every row of Pi has exactly gamma entries, so the segment of chunk
-// t starts at t J gamma; coff[t * cstride + c] (c = 0..s_pad) is the start of
-// column c within it.
-constexpr int kSkWarps = 16;
-
-// One block of 1024 threads per chunk t: exclusive scan over c of the column
-// counts tab[c][t + 1] - tab[c][t] (s_pad <= 1024).
-__global__ void __launch_bounds__(1024) k_chunk_scan(const int32_t* __restrict__ tab, int nch, int64_t s_pad,
-                                                     int cstride, int32_t* __restrict__ coff) {
-    __shared__ int32_t wsum[32], wscan[32];
-    const int t = blockIdx.x, c = threadIdx.x, lane = c & 31, w = c >> 5;
-    int cnt = 0;
-    if (c < s_pad) cnt = tab[(int64_t)c * (nch + 1) + t + 1] - tab[(int64_t)c * (nch + 1) + t];
-    int v = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += y;
-    }
-    if (lane == 31) wsum[w] = v;
-    __syncthreads();
-    if (w == 0) {
-        int x = (lane < (int)(blockDim.x >> 5)) ? wsum[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        wscan[lane] = x;
-    }
-    __syncthreads();
-    const int excl = (w ? wscan[w - 1] : 0) + v - cnt;
-    if (c < s_pad) coff[(int64_t)t * cstride + c] = excl;
-    if (c == s_pad - 1) coff[(int64_t)t * cstride + s_pad] = excl + cnt;
-}
-
-// One thread per (column c, chunk t): copy column c's entries of chunk t into
-// the chunk-major layout, as chunk-local indices.
-__global__ void k_chunk_fill(const int32_t* __restrict__ tab, const int32_t* __restrict__ ent, int nch,
-                             int64_t s_pad, int J, int gamma, int cstride, const int32_t* __restrict__ coff,
-                             int32_t* __restrict__ E) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= s_pad * nch) return;
-    const int64_t c = e / nch;
-    const int t = (int)(e % nch);
-    const int lo = tab[c * (nch + 1) + t], hi = tab[c * (nch + 1) + t + 1];
-    int32_t* dst = E + (int64_t)t * J * gamma + coff[(int64_t)t * cstride + c];
-    const int32_t jt = t * J;
-    for (int k = lo; k < hi; ++k) {
-        const int32_t v = ent[k];
-        dst[k - lo] = (((v >> 1) - jt) << 1) | (v & 1);
-    }
-}
-
-struct SkRowsArgs {
-    const float* A;
-    int64_t lda, m, n, s_pad;
-    const int32_t* E;
-    const int32_t* coff;
-    int cstride, J, gamma, nch;
-    size_t tile_b, ent_b, stage_b;   // bytes: tile, entries, one stage (tile + entries + offsets)
-    float scale;
-    float* C;
-};
-
-template <int CPW>
-__global__ void __launch_bounds__(kSkWarps * 32, 1) k_sketch_rows(SkRowsArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t i0 = (int64_t)blockIdx.x * 32;
-    const int rows = (int)min((int64_t)32, a.m - i0);
-    const int tstride = a.J + 1;
-    auto stage = [&](int t) { return smem_raw + (size_t)(t & 1) * a.stage_b; };
-    auto issue = [&](int t) {
-        unsigned char* st = stage(t);
-        float* T = reinterpret_cast<float*>(st);
-        int32_t* Eb = reinterpret_cast<int32_t*>(st + a.tile_b);
-        int32_t* Ob = reinterpret_cast<int32_t*>(st + a.tile_b + a.ent_b);
-        const int64_t j0 = (int64_t)t * a.J;
-        const int jl = (int)min((int64_t)a.J, a.n - j0);
-        for (int r = w; r < rows; r += kSkWarps) {
-            const float* src = a.A + (i0 + r) * a.lda + j0;
-            for (int jj = lane; jj < jl; jj += 32) msp::cp_async4(T + r * tstride + jj, src + jj);
-        }
-        const int ne = jl * a.gamma;
-        const int32_t* es = a.E + (int64_t)t * a.J * a.gamma;
-        for (int q = threadIdx.x; q < ne / 4; q += blockDim.x) msp::cp_async16(Eb + 4 * q, es + 4 * q, true);
-        for (int q = (ne / 4) * 4 + threadIdx.x; q < ne; q += blockDim.x) msp::cp_async4(Eb + q, es + q);
-        const int32_t* os = a.coff + (int64_t)t * a.cstride;
-        for (int q = threadIdx.x; q < a.cstride / 4; q += blockDim.x) msp::cp_async16(Ob + 4 * q, os + 4 * q, true);
-    };
-    float acc[CPW];
-#pragma unroll
-    for (int cc = 0; cc < CPW; ++cc) acc[cc] = 0.f;
-    issue(0);
-    msp::cp_async_commit();
-    for (int t = 0; t < a.nch; ++t) {
-        if (t + 1 < a.nch) issue(t + 1);
-        msp::cp_async_commit();
-        msp::cp_async_wait<1>();
-        __syncthreads();
-        const unsigned char* st = stage(t);
-        const float* Tl = reinterpret_cast<const float*>(st) + lane * tstride;
-        const int32_t* Eb = reinterpret_cast<const int32_t*>(st + a.tile_b);
-        const int32_t* Ob = reinterpret_cast<const int32_t*>(st + a.tile_b + a.ent_b) + w * CPW;
-        int e0 = Ob[0];
-#pragma unroll
-        for (int cc = 0; cc < CPW; ++cc) {
-            const int e1 = Ob[cc + 1];
-            float s = acc[cc];
-            for (int e = e0; e < e1; ++e) {
-                const int v = Eb[e];
-                const float x = Tl[v >> 1];
-                s += (v & 1) ? -x : x;
-            }
-            acc[cc] = s;
-            e0 = e1;
-        }
-        __syncthreads();
-    }
-    // the stages are free: stage the 32 x s_pad block of C, then write rows
-    float* Cs = reinterpret_cast<float*>(smem_raw);
-    const int64_t cst = a.s_pad + 1;
-#pragma unroll
-    for (int cc = 0; cc < CPW; ++cc) Cs[lane * cst + w * CPW + cc] = acc[cc] * a.scale;
-    __syncthreads();
-    for (int r = w; r < rows; r += kSkWarps)
-        for (int64_t c = lane; c < a.s_pad; c += 32) a.C[(i0 + r) * a.s_pad + c] = Cs[r * cst + c];
-}
-
-msp_status launch_sketch_rows(msp_ctx* ctx, const float* A, int64_t lda, int64_t m, int64_t n, int64_t s_pad,
-                              const int32_t* ptr, const int32_t* ent, int gamma, float scale, float* C) {
-    const int J = gamma <= 8 ? 512 : std::max(32, (4096 / gamma) / 32 * 32);
-    const int nch = (int)((n + J - 1) / J);
-    const int cstride = (int)((s_pad + 1 + 3) / 4 * 4);
-    auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
-    const size_t b_tab = r256((size_t)s_pad * (nch + 1) * 4);
-    const size_t b_coff = r256((size_t)nch * cstride * 4);
-    const size_t b_E = r256((size_t)nch * J * gamma * 4);
-    void* scr = nullptr;
-    MSP_TRY(msp_scratch(ctx, b_tab + b_coff + b_E, &scr));
-    int32_t* tab = (int32_t*)scr;
-    int32_t* coff = (int32_t*)((char*)scr + b_tab);
-    int32_t* E = (int32_t*)((char*)scr + b_tab + b_coff);
-    {
-        const int64_t cnt = s_pad * (nch + 1);
-        k_chunk_starts<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(ptr, ent, s_pad, J, nch, tab);
-        MSP_CHECK_LAUNCH(ctx);
-        k_chunk_scan<<<(unsigned)nch, 1024, 0, ctx->stream>>>(tab, nch, s_pad, cstride, coff);
-        MSP_CHECK_LAUNCH(ctx);
-        const int64_t pairs = s_pad * nch;
-        k_chunk_fill<<<(unsigned)((pairs + 255) / 256), 256, 0, ctx->stream>>>(tab, ent, nch, s_pad, J, gamma,
-                                                                             cstride, coff, E);
-        MSP_CHECK_LAUNCH(ctx);
-    }
-    SkRowsArgs a;
-    a.A = A; a.lda = lda; a.m = m; a.n = n; a.s_pad = s_pad;
-    a.E = E; a.coff = coff; a.cstride = cstride; a.J = J; a.gamma = gamma; a.nch = nch;
-    a.tile_b = (size_t)32 * (J + 1) * 4;
-    a.tile_b = (a.tile_b + 15) / 16 * 16;
-    a.ent_b = (size_t)J * gamma * 4;
-    a.stage_b = a.tile_b + a.ent_b + (size_t)cstride * 4;
-    a.scale = scale;
-    a.C = C;
-    const size_t smem = std::max(2 * a.stage_b, (size_t)32 * (s_pad + 1) * 4);
-    if (smem > ctx->smem_optin)
-        return msp_set_error(ctx, MSP_EINVAL, "sketch: %zu bytes of shared memory needed", smem);
-    const dim3 grid((unsigned)((m + 31) / 32));
-#define MSP_SKR_CASE(CPWV)                                                                        \
-    case CPWV: {                                                                                  \
-        MSP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_sketch_rows<CPWV>,                               \
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
-        k_sketch_rows<CPWV><<<grid, kSkWarps * 32, smem, ctx->stream>>>(a);                       \
-        break;                                                                                    \
-    }
-    switch ((int)(s_pad / kSkWarps)) {
-        MSP_SKR_CASE(8)
-        MSP_SKR_CASE(16)
-        MSP_SKR_CASE(24)
-        MSP_SKR_CASE(32)
-        MSP_SKR_CASE(40)
-        MSP_SKR_CASE(48)
-        MSP_SKR_CASE(56)
-        MSP_SKR_CASE(64)
-        default:
-            return msp_set_error(ctx, MSP_EINVAL, "sketch: unsupported s_pad %lld", (long long)s_pad);
-    }
-#undef MSP_SKR_CASE
-    MSP_CHECK_LAUNCH(ctx);
-    return MSP_OK;
-}
-
 // ------------------------------------------------------------ row gathers
 
 // out[r, c] = scale * sum_{(j,neg) in list(r)} (+-) in[j, c]; block per output
@@ -573,8 +361,8 @@ msp_status msp_sketch_apply_rows(msp_ctx* ctx, const void* A, msp_dtype dt, int6
         return msp_set_error(ctx, MSP_EINVAL, "sketch: s_pad %lld above 1024 is not supported",
                              (long long)s_pad);
     if (dt == MSP_F32)
-        return launch_sketch_rows(ctx, (const float*)A, lda, m, n, s_pad, ptr, ent, gamma, (float)scale,
-                                  (float*)C);
+        return launch_sketch_apply_r<float, 16>(ctx, (const float*)A, lda, m, n, s_pad, ptr, ent,
+                                                (float)scale, (float*)C);
     return launch_sketch_apply_r<double, 8>(ctx, (const double*)A, lda, m, n, s_pad, ptr, ent,
                                             scale, (double*)C);
 }
