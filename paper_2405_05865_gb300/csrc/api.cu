@@ -177,10 +177,6 @@ msp_status msp_sketch_pattern(msp_ctx* ctx, int64_t n, int64_t rows, int gamma, 
 
 void msp_sketch_destroy(msp_sketch_t* sk) {
     if (!sk) return;
-    if (sk->ready) {
-        cudaStreamWaitEvent(sk->stream, sk->ready, 0);
-        cudaEventDestroy(sk->ready);
-    }
     for (void* p : {(void*)sk->idx, (void*)sk->sgn, (void*)sk->csr_ptr, (void*)sk->csr_ent, sk->C,
                     (void*)sk->packed, (void*)sk->stats})
         if (p) cudaFreeAsync(p, sk->stream);
@@ -189,46 +185,17 @@ void msp_sketch_destroy(msp_sketch_t* sk) {
 
 }  // extern "C"
 
-// The passes over A that only the solve needs -- the packed upper tiles of an
+// The passes over A that only the solve needs: the packed upper tiles of an
 // FP32 A (unless the chunked host copy packed them already) and the row
-// statistics of the norm bound -- go to the side stream once C is formed, so
-// that they overlap the Nystrom factor (whose Cholesky leaves hold one SM);
-// sk->ready marks their end.
-static msp_status sketch_side_passes(msp_ctx* ctx, msp_sketch_s* sk, const void* A, msp_dtype dtype,
-                                     int64_t lda, bool do_pack) {
+// statistics of the norm bound, which every solve with this sketch's
+// factors then reuses. (Run on a side stream beside the factor they gained
+// nothing: their blocks took the SMs the factor's kernels wait for.)
+static msp_status sketch_solve_prep(msp_ctx* ctx, msp_sketch_s* sk, const void* A, msp_dtype dtype,
+                                    int64_t lda, bool do_pack) {
     const int64_t n = sk->n;
     MSP_TRY(msp_alloc(ctx, (void**)&sk->stats, (size_t)(3 * n + 1) * 8));
-    if (!ctx->copy_stream && cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
-        cudaGetLastError();
-        ctx->copy_stream = nullptr;
-        return msp_set_error(ctx, MSP_ECUDA, "sketch: side stream creation failed");
-    }
-    cudaEvent_t fork = nullptr;
-    bool ok = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess &&
-              cudaEventCreateWithFlags(&sk->ready, cudaEventDisableTiming) == cudaSuccess &&
-              cudaEventRecord(fork, ctx->stream) == cudaSuccess &&
-              cudaStreamWaitEvent(ctx->copy_stream, fork, 0) == cudaSuccess;
-    if (fork) cudaEventDestroy(fork);
-    if (!ok) {
-        cudaGetLastError();
-        return msp_set_error(ctx, MSP_ECUDA, "sketch: side stream fork failed");
-    }
-    // the launches below are made on the side stream, two blocks per SM each
-    // (grid-stride): a full grid of them would hold every SM and queue the
-    // factor's kernels behind it
-    cudaStream_t main_stream = ctx->stream;
-    ctx->stream = ctx->copy_stream;
-    const int bg = 2 * std::max(1, ctx->num_sms);
-    msp_status st = MSP_OK;
-    if (do_pack && sk->packed) st = msp_pack_upper(ctx, (const float*)A, lda, n, sk->packed, bg);
-    if (st == MSP_OK) st = msp_norm_lb_launch(ctx, A, dtype, n, lda, sk->stats, sk->stats + 3 * n, bg);
-    ctx->stream = main_stream;
-    if (st != MSP_OK) return st;
-    if (cudaEventRecord(sk->ready, ctx->copy_stream) != cudaSuccess) {
-        cudaGetLastError();
-        return msp_set_error(ctx, MSP_ECUDA, "sketch: side stream join failed");
-    }
-    return MSP_OK;
+    if (do_pack && sk->packed) MSP_TRY(msp_pack_upper(ctx, (const float*)A, lda, n, sk->packed));
+    return msp_norm_lb_launch(ctx, A, dtype, n, lda, sk->stats, sk->stats + 3 * n);
 }
 
 msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n,
@@ -340,8 +307,7 @@ msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t
         msp_sketch_destroy(sk);
         return st;
     }
-    if (pack && (st = sketch_side_passes(ctx, sk, A, dtype, host_chunks ? n : lda, !host_chunks)) != MSP_OK) {
-        if (ctx->copy_stream) cudaStreamSynchronize(ctx->copy_stream);
+    if (pack && (st = sketch_solve_prep(ctx, sk, A, dtype, host_chunks ? n : lda, !host_chunks)) != MSP_OK) {
         cudaStreamSynchronize(ctx->stream);
         msp_sketch_destroy(sk);
         return st;
@@ -525,9 +491,8 @@ static msp_status solve_impl(msp_ctx* ctx, const msp_factor_s* f, const void* A,
     const msp_dtype wt = f->dtype;
     const size_t ts = dtype_size(wt);
     // the sketch's packed upper tiles and norm-bound statistics stand in for A
-    // when A is the sketched matrix (written on the sketch's side stream)
+    // when A is the sketched matrix
     const bool sketched_A = (A == f->sk->A_src);
-    if (sketched_A && f->sk->ready) MSP_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->stream, f->sk->ready, 0));
     const float* packed = (dtype == MSP_F32 && f->sk->packed && sketched_A) ? f->sk->packed : nullptr;
     if (o->criterion != MSP_STOP_RESIDUAL && o->criterion != MSP_STOP_BACKWARD)
         return msp_set_error(ctx, MSP_EINVAL, "solve: unknown criterion %d", o->criterion);

@@ -35,9 +35,7 @@ struct msp_ctx {
     cudaEvent_t* events = nullptr;
     int n_events = 0;
     // worker contexts (own streams) for concurrent batch set-up, created lazily
-    // side stream: host-to-device copies, and the passes over A that only the
-    // solve needs (packing, the norm bound), overlapped with the factor
-    cudaStream_t copy_stream = nullptr;
+    cudaStream_t copy_stream = nullptr;   // host-to-device copies overlapped with compute
     msp_ctx** lanes = nullptr;
     cudaStream_t* lane_streams = nullptr;
     int n_lanes = 0;
@@ -65,9 +63,6 @@ struct msp_sketch_s {
     // norm bound of A_src for the backward-error rule: row sums, their
     // rounding bounds and row squares (3 n), then the bound (see norms.cu)
     double* stats = nullptr;
-    // recorded on the side stream once packed and stats are written; every
-    // reader (and the destroy) waits on it
-    cudaEvent_t ready = nullptr;
 };
 
 struct msp_factor_s {
@@ -267,10 +262,9 @@ msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t
 msp_status msp_nystrom_impl(msp_ctx* ctx, const msp_sketch_s* sk, double lambda, double lambda0,
                             int64_t phi, int gamma_phi, uint64_t seed, msp_factor_s** out);
 
-// norms.cu: L <= |A|_2 into *out_dev; work holds 3n doubles; max_blocks > 0
-// caps the row pass's grid (blocks then loop over rows)
+// norms.cu: L <= |A|_2 into *out_dev; work holds 3n doubles
 msp_status msp_norm_lb_launch(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t n, int64_t lda,
-                              double* work, double* out_dev, int max_blocks = 0);
+                              double* work, double* out_dev);
 
 // factor.cu
 msp_status msp_build_factor(msp_ctx* ctx, msp_factor_s* f, const void* Ct, int64_t phi_rows);
@@ -289,8 +283,7 @@ msp_status msp_gram_inverse(msp_ctx* ctx, const float* X, int64_t rows, int64_t 
 
 // symv.cu
 int64_t msp_packed_tiles(int64_t n);
-// max_blocks > 0: at most that many blocks, each looping over tiles
-msp_status msp_pack_upper(msp_ctx* ctx, const float* A, int64_t lda, int64_t n, float* packed, int max_blocks = 0);
+msp_status msp_pack_upper(msp_ctx* ctx, const float* A, int64_t lda, int64_t n, float* packed);
 msp_status msp_pack_upper_rows(msp_ctx* ctx, const float* A, int64_t lda, int64_t n, int64_t I0, int64_t I1,
                                float* packed);
 // fill the strictly lower 128-tiles of tile rows [I0, I1) from the upper ones

@@ -137,10 +137,8 @@ __global__ void __launch_bounds__(1024) k_norm_lb(const double* __restrict__ row
 }  // namespace
 
 msp_status msp_norm_lb_launch(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t n, int64_t lda,
-                              double* work, double* out_dev, int max_blocks) {
-    int64_t nb = (n + 7) / 8;
-    if (max_blocks > 0) nb = std::min<int64_t>(nb, max_blocks);
-    const unsigned blocks = (unsigned)nb;
+                              double* work, double* out_dev) {
+    const unsigned blocks = (unsigned)((n + 7) / 8);
     if (dt == MSP_F32)
         k_row_stats<float><<<blocks, 256, 0, ctx->stream>>>((const float*)A, n, lda, work, work + n,
                                                            work + 2 * n);

@@ -120,7 +120,6 @@ __device__ inline void tile_coords(int t, int nt, int& I, int& J) {
 
 // Pack the upper tiles [tile0, tile0 + count) of dense row-major A (n x n,
 // lda) into `packed`; a block takes tiles tile0 + blockIdx.x, + gridDim.x, ...
-// (one tile per block, or a few blocks per SM that leave room beside them).
 __global__ void __launch_bounds__(256) k_pack_upper(const float* __restrict__ A, int64_t lda,
                                                    int64_t n, int nt, int tile0, int count,
                                                    float* __restrict__ packed) {
@@ -372,12 +371,11 @@ int64_t msp_packed_tiles(int64_t n) {
     return nt * (nt + 1) / 2;
 }
 
-msp_status msp_pack_upper(msp_ctx* ctx, const float* A, int64_t lda, int64_t n, float* packed, int max_blocks) {
+msp_status msp_pack_upper(msp_ctx* ctx, const float* A, int64_t lda, int64_t n, float* packed) {
     const int64_t nt = (n + kTile - 1) / kTile;
     const int64_t ntiles = nt * (nt + 1) / 2;
     if (ntiles >= (1ll << 31)) return msp_set_error(ctx, MSP_EINVAL, "pack: n too large");
-    const int64_t blocks = max_blocks > 0 ? std::min<int64_t>(ntiles, max_blocks) : ntiles;
-    k_pack_upper<<<(unsigned)blocks, 256, 0, ctx->stream>>>(A, lda, n, (int)nt, 0, (int)ntiles, packed);
+    k_pack_upper<<<(unsigned)ntiles, 256, 0, ctx->stream>>>(A, lda, n, (int)nt, 0, (int)ntiles, packed);
     MSP_CHECK_LAUNCH(ctx);
     return MSP_OK;
 }

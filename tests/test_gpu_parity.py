@@ -308,6 +308,12 @@ def test_solve_backward_error_rule(ctx):
     A64 = np.asarray(w.A, dtype=np.float64)
     Lo = reference.norm_lower_bound(A64)
     assert Lo * (1 - 1e-5) <= info["norm_lb"] <= Lo * (1 + 1e-12)
+    # the bound the sketch took of A (reused by every solve with it) is the
+    # one the stand-alone pass gives, and the one a solve takes itself of a copy
+    assert info["norm_lb"] == ctx.norm_lower_bound(A)
+    _, info_c = ctx.solve(f, A.clone(), _cuda(w.b), lam=w.lam, max_inner=0, criterion="backward", tol=1e-10,
+                          refine_tol=1e-4)
+    assert info_c["norm_lb"] == info["norm_lb"]
     assert info["backward_err"] <= 1e-10
     top = float(np.linalg.eigvalsh(A64)[-1])
     eta = reference.backward_error(A64, x, w.b, w.lam, norm_A=top)
