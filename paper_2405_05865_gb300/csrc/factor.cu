@@ -10,6 +10,7 @@
 //   A22 -= L21 L21^T;   (L22, X22) = f(A22);  X21 = -X22 (L21 X11),
 // with a one-block dense Cholesky + triangular inverse at the 64 x 64 leaves
 // and an FP64 GEMM kernel for the rest.
+#include "bulk.cuh"
 #include "msp_internal.cuh"
 
 #include <atomic>
@@ -113,6 +114,98 @@ __global__ void __launch_bounds__(256, 4) k_gram(const TA* __restrict__ Ct, int6
 
 // M2 = sum_slices P + lam_t W (FP64, fixed order), or + lam_t I when W is
 // NULL; pad rows/cols get identity.
+// The same partial Grams (FP32 input) with 128 x 128 tiles: 512 threads,
+// each 8 rows (ty*4 + i and 64 + ty*4 + i) x 4 columns (tx*4 + j), K chunks
+// of 16 double-buffered in shared memory by 16-byte async copies. Per output
+// the arithmetic is k_gram's -- the same K slices, chunks of 16 summed in
+// FP32 from zero in increasing k, TwoSum into (hi, lo) -- so P is the same
+// to the bit; a thread's 32 outputs per shared-memory read of 12 values (4
+// for k_gram's 16) keep the FP32 pipe, not shared memory, the limit.
+__global__ void __launch_bounds__(512, 1) k_gram128(const float* __restrict__ Ct, int64_t K, int64_t ld,
+                                                    int64_t s_pad, double* __restrict__ P) {
+    __shared__ __align__(16) float As[2][16][128];
+    __shared__ __align__(16) float Bs[2][16][128];
+    const int nt = (int)(s_pad / 128);
+    int ta = 0, rem = blockIdx.x;
+    while (rem >= nt - ta) { rem -= nt - ta; ++ta; }
+    const int tb = ta + rem;
+    const int a0 = ta * 128, b0 = tb * 128;
+    const int64_t kper = ((K + kGramSlices - 1) / kGramSlices + 15) / 16 * 16;
+    const int64_t kbeg = (int64_t)blockIdx.y * kper;
+    const int64_t kend = min(K, kbeg + kper);
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    // loader: thread t copies float4 (t & 31) of row t >> 5 of the chunk, of A and of B
+    const int lk = (int)(threadIdx.x >> 5), lc = (int)(threadIdx.x & 31) * 4;
+    auto issue = [&](int64_t k0, int st) {
+        const int64_t k = k0 + lk;
+        const bool in = k < kend;
+        msp::cp_async16(&As[st][lk][lc], in ? Ct + k * ld + a0 + lc : Ct, in);
+        msp::cp_async16(&Bs[st][lk][lc], in ? Ct + k * ld + b0 + lc : Ct, in);
+    };
+    float hi[8][4], lo[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { hi[i][j] = 0.f; lo[i][j] = 0.f; }
+    if (kbeg < kend) issue(kbeg, 0);
+    msp::cp_async_commit();
+    int st = 0;
+    for (int64_t k0 = kbeg; k0 < kend; k0 += 16) {
+        if (k0 + 16 < kend) issue(k0 + 16, st ^ 1);
+        msp::cp_async_commit();
+        msp::cp_async_wait<1>();
+        __syncthreads();
+        float acc[8][4];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            const float4 x0 = *reinterpret_cast<const float4*>(&As[st][kk][ty * 4]);
+            const float4 x1 = *reinterpret_cast<const float4*>(&As[st][kk][64 + ty * 4]);
+            const float4 y = *reinterpret_cast<const float4*>(&Bs[st][kk][tx * 4]);
+            const float av[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+            const float bv[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) two_sum_add(hi[i][j], lo[i][j], acc[i][j]);
+        __syncthreads();
+        st ^= 1;
+    }
+    double* Ps = P + (int64_t)blockIdx.y * s_pad * s_pad;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t a = a0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4)), b = b0 + tx * 4 + j;
+            const double v = (double)hi[i][j] + (double)lo[i][j];
+            Ps[a * s_pad + b] = v;
+            Ps[b * s_pad + a] = v;
+        }
+}
+
+// Split-K partial Grams of FP32 Ct into P (kGramSlices x s_pad x s_pad).
+msp_status launch_gram_f32(msp_ctx* ctx, const float* Ct, int64_t K, int64_t ld, int64_t sp, double* P) {
+    if (sp % 128 == 0 && ld % 4 == 0 && ((uintptr_t)Ct & 15) == 0) {
+        const int nt = (int)(sp / 128);
+        dim3 grid((unsigned)(nt * (nt + 1) / 2), kGramSlices);
+        k_gram128<<<grid, 512, 0, ctx->stream>>>(Ct, K, ld, sp, P);
+    } else {
+        const int nt = (int)(sp / 64);
+        dim3 grid((unsigned)(nt * (nt + 1) / 2), kGramSlices);
+        k_gram<float><<<grid, 256, 0, ctx->stream>>>(Ct, K, ld, sp, P);
+    }
+    MSP_CHECK_LAUNCH(ctx);
+    return MSP_OK;
+}
+
 template <typename TA>
 __global__ void k_gram_finish(const double* __restrict__ P, const TA* __restrict__ W, double lam_t,
                               int64_t s, int64_t s_pad, double* __restrict__ M2) {
@@ -543,8 +636,7 @@ msp_status msp_build_factor(msp_ctx* ctx, msp_factor_s* f, const void* Ct, int64
         dim3 grid((unsigned)(nt * (nt + 1) / 2), kGramSlices);
         const unsigned fb = (unsigned)((sp * sp + 255) / 256);
         if (f->dtype == MSP_F32) {
-            k_gram<float><<<grid, 256, 0, ctx->stream>>>((const float*)Ct, phi_rows, sp, sp, P);
-            MSP_CHECK_LAUNCH(ctx);
+            MSP_TRY(launch_gram_f32(ctx, (const float*)Ct, phi_rows, sp, sp, P));
             k_gram_finish<float><<<fb, 256, 0, ctx->stream>>>(P, (const float*)f->W, f->lam_tilde,
                                                                f->s, sp, f->M2);
         } else {
@@ -574,10 +666,7 @@ msp_status msp_gram64(msp_ctx* ctx, const float* X, int64_t rows, int64_t ld, in
     void* scr = nullptr;
     MSP_TRY(msp_scratch(ctx, (size_t)kGramSlices * sp * sp * 8, &scr));
     double* P = (double*)scr;
-    const int nt = (int)(sp / 64);
-    dim3 grid((unsigned)(nt * (nt + 1) / 2), kGramSlices);
-    k_gram<float><<<grid, 256, 0, ctx->stream>>>(X, rows, ld, sp, P);
-    MSP_CHECK_LAUNCH(ctx);
+    MSP_TRY(launch_gram_f32(ctx, X, rows, ld, sp, P));
     k_gram_finish<float><<<(unsigned)((sp * sp + 255) / 256), 256, 0, ctx->stream>>>(P, nullptr, diag, s, sp,
                                                                                       G64);
     MSP_CHECK_LAUNCH(ctx);
