@@ -504,8 +504,10 @@ msp_status dgemm(msp_ctx* ctx, bool ta, bool tb, int64_t m, int64_t n, int64_t k
 }
 
 // Recursive Cholesky + inverse of the n x n block at offset `off` of M (ld),
-// inverse into X (same offsets); T1/T2 are n x n temporaries (ld). Leaves of
-// at most 32: a leaf runs on one SM, whose FP64 pipe bounds it (its work
+// inverse into X (same offsets); T1/T2 are n x n temporaries (ld). Only X =
+// L^{-1} is kept: M is scratch (the Schur complements overwrite its lower
+// triangle, the leaves leave their L blocks there, L21 is not stored). Leaves
+// of at most 32: a leaf runs on one SM, whose FP64 pipe bounds it (its work
 // grows as nb^3), while the products of the recursion spread over all SMs.
 msp_status chol_inv(msp_ctx* ctx, double* M, double* X, double* T1, double* T2, int64_t ld,
                     int64_t off, int64_t n, int* fail) {
@@ -540,9 +542,6 @@ msp_status chol_inv(msp_ctx* ctx, double* M, double* X, double* T1, double* T2, 
     // T2 = L21 X11 (X11 lower); X21 = -X22 T2 (X22 lower)
     MSP_TRY(dgemm(ctx, false, false, n2, n1, n1, 1.0, T1, ld, X11, ld, 0.0, T2, ld, 0, 2, 0));
     MSP_TRY(dgemm(ctx, false, false, n2, n1, n2, -1.0, X22, ld, T2, ld, 0.0, X21, ld, 1, 0, 0));
-    // store L21 into M
-    MSP_CUDA_TRY(ctx, cudaMemcpy2DAsync(A21, ld * 8, T1, ld * 8, n1 * 8, n2,
-                                        cudaMemcpyDeviceToDevice, ctx->stream));
     return MSP_OK;
 }
 
