@@ -160,6 +160,8 @@ void msp_destroy(msp_ctx* ctx) {
     delete[] ctx->lanes;
     delete[] ctx->lane_streams;
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    for (cudaStream_t s : ctx->fac_side)
+        if (s) cudaStreamDestroy(s);
     delete ctx;
 }
 

@@ -510,7 +510,7 @@ msp_status dgemm(msp_ctx* ctx, bool ta, bool tb, int64_t m, int64_t n, int64_t k
 // of at most 32: a leaf runs on one SM, whose FP64 pipe bounds it (its work
 // grows as nb^3), while the products of the recursion spread over all SMs.
 msp_status chol_inv(msp_ctx* ctx, double* M, double* X, double* T1, double* T2, int64_t ld,
-                    int64_t off, int64_t n, int* fail) {
+                    int64_t off, int64_t n, int* fail, int depth) {
     if (n <= 32) {
         // set once per device; batch set-up calls this from several threads
         static std::atomic<bool> attr_set[64];
@@ -533,14 +533,52 @@ msp_status chol_inv(msp_ctx* ctx, double* M, double* X, double* T1, double* T2, 
     double* X11 = X + off * ld + off;
     double* X21 = X + (off + n1) * ld + off;
     double* X22 = X + (off + n1) * ld + off + n1;
-    MSP_TRY(chol_inv(ctx, M, X, T1, T2, ld, off, n1, fail));
+    MSP_TRY(chol_inv(ctx, M, X, T1, T2, ld, off, n1, fail, depth + 1));
     // T1 = L21 = A21 X11^T   (n2 x n1; X11^T is upper triangular)
     MSP_TRY(dgemm(ctx, false, true, n2, n1, n1, 1.0, A21, ld, X11, ld, 0.0, T1, ld, 0, 1, 0));
+    // T2 = L21 X11 (X11 lower) needs only T1 and X11, so it runs on the side
+    // stream of this depth while A22 is updated and factored on the main
+    // stream. Disjoint memory: T1 and T2 hold columns [0, n1) of the
+    // temporaries, the second half works in columns [n1, n) of them.
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_t1 = nullptr, ev_t2 = nullptr;
+    if (depth < 8 && (ctx->fac_side[depth] ||
+                      cudaStreamCreateWithFlags(&ctx->fac_side[depth], cudaStreamNonBlocking) == cudaSuccess))
+        side = ctx->fac_side[depth];
+    if (side && (cudaEventCreateWithFlags(&ev_t1, cudaEventDisableTiming) != cudaSuccess ||
+                 cudaEventCreateWithFlags(&ev_t2, cudaEventDisableTiming) != cudaSuccess ||
+                 cudaEventRecord(ev_t1, ctx->stream) != cudaSuccess ||
+                 cudaStreamWaitEvent(side, ev_t1, 0) != cudaSuccess)) {
+        cudaGetLastError();
+        side = nullptr;     // fall back to the main stream
+    }
+    msp_status st = MSP_OK;
+    if (side) {
+        cudaStream_t main_stream = ctx->stream;
+        ctx->stream = side;
+        st = dgemm(ctx, false, false, n2, n1, n1, 1.0, T1, ld, X11, ld, 0.0, T2, ld, 0, 2, 0);
+        ctx->stream = main_stream;
+        if (st == MSP_OK && cudaEventRecord(ev_t2, side) != cudaSuccess)
+            st = msp_set_error(ctx, MSP_ECUDA, "factor: side stream record failed");
+    }
     // A22 -= L21 L21^T (lower triangle is all the recursion reads)
-    MSP_TRY(dgemm(ctx, false, true, n2, n2, n1, -1.0, T1, ld, T1, ld, 1.0, A22, ld, 0, 0, 1));
-    MSP_TRY(chol_inv(ctx, M, X, T1 + n1, T2 + n1, ld, off + n1, n2, fail));
-    // T2 = L21 X11 (X11 lower); X21 = -X22 T2 (X22 lower)
-    MSP_TRY(dgemm(ctx, false, false, n2, n1, n1, 1.0, T1, ld, X11, ld, 0.0, T2, ld, 0, 2, 0));
+    if (st == MSP_OK)
+        st = dgemm(ctx, false, true, n2, n2, n1, -1.0, T1, ld, T1, ld, 1.0, A22, ld, 0, 0, 1);
+    if (st == MSP_OK) st = chol_inv(ctx, M, X, T1 + n1, T2 + n1, ld, off + n1, n2, fail, depth + 1);
+    if (st == MSP_OK) {
+        if (side) {
+            if (cudaStreamWaitEvent(ctx->stream, ev_t2, 0) != cudaSuccess)
+                st = msp_set_error(ctx, MSP_ECUDA, "factor: side stream join failed");
+        } else {
+            st = dgemm(ctx, false, false, n2, n1, n1, 1.0, T1, ld, X11, ld, 0.0, T2, ld, 0, 2, 0);
+        }
+    }
+    if (side && st != MSP_OK) cudaStreamSynchronize(side);
+    // (destroying an event with work pending is safe)
+    if (ev_t1) cudaEventDestroy(ev_t1);
+    if (ev_t2) cudaEventDestroy(ev_t2);
+    MSP_TRY(st);
+    // X21 = -X22 T2 (X22 lower)
     MSP_TRY(dgemm(ctx, false, false, n2, n1, n2, -1.0, X22, ld, T2, ld, 0.0, X21, ld, 1, 0, 0));
     return MSP_OK;
 }
@@ -586,7 +624,7 @@ msp_status factor_shifted(msp_ctx* ctx, const double* M, int64_t s, int64_t sp, 
         MSP_CHECK_LAUNCH(ctx);
         MSP_CUDA_TRY(ctx, cudaMemsetAsync(Linv64, 0, mat, ctx->stream));
         MSP_CUDA_TRY(ctx, cudaMemsetAsync(fail, 0, sizeof(int), ctx->stream));
-        MSP_TRY(chol_inv(ctx, Mw, Linv64, T1, T2, sp, 0, sp, fail));
+        MSP_TRY(chol_inv(ctx, Mw, Linv64, T1, T2, sp, 0, sp, fail, 0));
         MSP_CUDA_TRY(ctx, cudaMemcpyAsync(hflag, fail, sizeof(int), cudaMemcpyDeviceToHost,
                                           ctx->stream));
         MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));

@@ -36,6 +36,8 @@ struct msp_ctx {
     int n_events = 0;
     // worker contexts (own streams) for concurrent batch set-up, created lazily
     cudaStream_t copy_stream = nullptr;   // host-to-device copies overlapped with compute
+    // side streams of the recursive Cholesky, one per recursion depth (lazy)
+    cudaStream_t fac_side[8] = {};
     msp_ctx** lanes = nullptr;
     cudaStream_t* lane_streams = nullptr;
     int n_lanes = 0;
