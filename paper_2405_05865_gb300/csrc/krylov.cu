@@ -65,6 +65,40 @@ __device__ inline double sum_parts(const double* parts, int stride, int G, doubl
     return block_sum(v, red);
 }
 
+// Two block sums at once (red holds 64 doubles): per value the order of
+// block_sum, with one pair of barriers.
+__device__ inline void block_sum2(double& v0, double& v1, double* red) {
+    v0 = msp::warp_sum(v0);
+    v1 = msp::warp_sum(v1);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        red[w] = v0;
+        red[32 + w] = v1;
+    }
+    __syncthreads();
+    double t0 = 0.0, t1 = 0.0;
+    const int nw = blockDim.x >> 5;
+    for (int k = 0; k < nw; ++k) {
+        t0 += red[k];
+        t1 += red[32 + k];
+    }
+    v0 = t0;
+    v1 = t1;
+}
+
+// sum_parts of the entries at offsets o0 and o1 of every block's record.
+__device__ inline void sum_parts2(const double* parts, int stride, int G, double* red, double& s0, double& s1) {
+    double v0 = 0.0, v1 = 0.0;
+    for (int k = threadIdx.x; k < G; k += blockDim.x) {
+        v0 += __ldcg(&parts[(int64_t)k * stride]);
+        v1 += __ldcg(&parts[(int64_t)k * stride + 1]);
+    }
+    block_sum2(v0, v1, red);
+    s0 = v0;
+    s1 = v1;
+}
+
 // ------------------------------------------------------------------ GEMV
 
 // q = (A + lam I) p; warp per row (grid-stride); lane reads 16 B vectors.
@@ -460,6 +494,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_level2(L2Args<T> a) {
     T* swarp = stmp + sp;                         // kNW x sp
     T* srow = swarp + kNW * sp;                   // 2 x kRowChunk (row pass staging)
     __shared__ double red[32];
+    __shared__ double red64[64];
     __shared__ double red2[8 * 32];
     __shared__ double s_rw, s_rzo;
 
@@ -478,38 +513,60 @@ __global__ void __launch_bounds__(kThreads, 1) k_level2(L2Args<T> a) {
     // ---- level-1 update and g = C^T r partials
     double rr = 0.0;
     if (a.mode == MODE_ITER && a.qpart) {
-        // q_i = sum over the packed A pass's slot partials + lam p_i; 32 rows x
-        // 8 slot groups per round, fixed summation order
-        T* sq = swarp;  // 8 x 32 scratch in shared memory (swarp is free here)
+        // q_i = sum over the packed A pass's slot partials + lam p_i, fixed
+        // summation order. Rounds of four 32-row groups: every thread sums
+        // its slot group for the four rows with all their loads in flight,
+        // warp g finishes group g, and warp 0 adds the squares of the new
+        // r_i row by row in group order.
+        constexpr int kGroups = 4;
+        T* sq = swarp;  // kGroups x 8 x 32 scratch (swarp holds 8 s_pad >= 1024 values; free here)
+        T* rnew = reinterpret_cast<T*>(red2);   // kGroups x 32 new r_i (red2 is free here)
         const int rl = threadIdx.x & 31, grp = threadIdx.x >> 5;
-        for (int64_t base = row0; base < row1; base += 32) {
-            const int64_t i = base + rl;
-            T v = T(0);
-            if (i < row1) {
-                // eight independent loads in flight per thread
-                int sl = grp;
-                for (; sl + 7 * kNW < a.q_slots; sl += 8 * kNW) {
-                    T t8[8];
+        for (int64_t base = row0; base < row1; base += 32 * kGroups) {
+            T v[kGroups];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u)
-                        t8[u] = __ldcg(&a.qpart[(int64_t)(sl + u * kNW) * a.q_ld + i]);
+            for (int g = 0; g < kGroups; ++g) {
+                const int64_t i = base + 32 * g + rl;
+                v[g] = T(0);
+                if (i < row1) {
+                    int sl = grp;
+                    for (; sl + 7 * kNW < a.q_slots; sl += 8 * kNW) {
+                        T t8[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) v += t8[u];
+                        for (int u = 0; u < 8; ++u)
+                            t8[u] = __ldcg(&a.qpart[(int64_t)(sl + u * kNW) * a.q_ld + i]);
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) v[g] += t8[u];
+                    }
+                    for (; sl < a.q_slots; sl += kNW) v[g] += __ldcg(&a.qpart[(int64_t)sl * a.q_ld + i]);
                 }
-                for (; sl < a.q_slots; sl += kNW) v += __ldcg(&a.qpart[(int64_t)sl * a.q_ld + i]);
             }
-            sq[grp * 32 + rl] = v;
-            __syncthreads();
-            if (grp == 0 && i < row1) {
-                T qi = T(0);
 #pragma unroll
-                for (int g = 0; g < kNW; ++g) qi += sq[g * 32 + rl];
-                qi += a.lam * a.p[i];
-                T ri = a.r[i];
-                a.x[i] += (T)alpha * a.p[i];
-                ri -= (T)alpha * qi;
-                a.r[i] = ri;
-                rr += (double)ri * (double)ri;
+            for (int g = 0; g < kGroups; ++g) sq[(g * kNW + grp) * 32 + rl] = v[g];
+            __syncthreads();
+            if (grp < kGroups) {
+                const int64_t i = base + 32 * grp + rl;
+                T ri = T(0);
+                if (i < row1) {
+                    T qi = T(0);
+#pragma unroll
+                    for (int g = 0; g < kNW; ++g) qi += sq[(grp * kNW + g) * 32 + rl];
+                    qi += a.lam * a.p[i];
+                    ri = a.r[i];
+                    a.x[i] += (T)alpha * a.p[i];
+                    ri -= (T)alpha * qi;
+                    a.r[i] = ri;
+                }
+                rnew[grp * 32 + rl] = ri;
+            }
+            __syncthreads();
+            if (grp == 0) {
+                for (int g = 0; g < kGroups; ++g) {
+                    if (base + 32 * g + rl < row1) {
+                        const T ri = rnew[g * 32 + rl];
+                        rr += (double)ri * (double)ri;
+                    }
+                }
             }
             __syncthreads();
         }
@@ -570,18 +627,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_level2(L2Args<T> a) {
         __syncthreads();
         rows_dot<T, PL>(a.Bt, sp, c0, c1, stmp, a.zvec);
         __syncthreads();
-        double part = 0.0;
-        for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x)
-            part += (double)sres[c] * (double)a.zvec[c];
-        part = block_sum(part, red);
-        if (threadIdx.x == 0) a.dpart[b * 4 + 2] = part;
+        // z^T res only where the level-2 iteration uses it (rz_out given;
+        // the same in every block)
+        if (rz_out) {
+            double part = 0.0;
+            for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x)
+                part += (double)sres[c] * (double)a.zvec[c];
+            part = block_sum(part, red);
+            if (threadIdx.x == 0) a.dpart[b * 4 + 2] = part;
+        }
         if (!msp::grid_barrier(bc, bg, err)) return false;
-        *rz_out = sum_parts(a.dpart + 2, 4, G, red);
+        if (rz_out) *rz_out = sum_parts(a.dpart + 2, 4, G, red);
         return true;
     };
 
+    // direct level 2 (max_inner == 0) has no level-2 iteration: z^T res unused
     double rz_in = 0.0;
-    if (!precond(&rz_in)) return;
+    if (!precond(a.max_inner > 0 ? &rz_in : nullptr)) return;
     load_full(a.zvec, sd, sp);
     __syncthreads();
     double rres = gg;
@@ -632,8 +694,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_level2(L2Args<T> a) {
     __syncthreads();
     double rw = 0.0, rzo = 0.0;
     row_pass<T, PL>(a, 2, row0, row1, sy, swarp, srow, &rw, &rzo);
-    rw = block_sum(rw, red);
-    rzo = block_sum(rzo, red);
+    block_sum2(rw, rzo, red64);
     if (threadIdx.x == 0) {
         a.dpart[b * 4 + 0] = rw;
         a.dpart[b * 4 + 1] = rzo;
@@ -643,8 +704,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_level2(L2Args<T> a) {
         return;
     }
     if (!msp::grid_barrier(bc, bg, err)) return;
-    rw = sum_parts(a.dpart + 0, 4, G, red);
-    rzo = sum_parts(a.dpart + 1, 4, G, red);
+    sum_parts2(a.dpart + 0, 4, G, red64, rw, rzo);
     T beta = T(0);
     if (a.mode == MODE_ITER) beta = (T)((rw - rzo) / rz_outer);
     for (int64_t i = row0 + threadIdx.x; i < row1; i += blockDim.x)
