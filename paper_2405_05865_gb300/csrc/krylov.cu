@@ -358,14 +358,6 @@ __device__ inline void row_one(const L2Args<T>& a, int kind, int64_t il, const R
 //   kind 1: acc += (c_i . d) c_i               (u = C^T C d)
 //   kind 2: w_i = (r_i - c_i . y) / lam~ into z; per-thread dots r.w, r.z_old
 // Per-warp accumulators are combined through shared memory into part[b].
-// Ask L1 for one row of C (len values): one 128-byte line per lane.
-template <typename T>
-__device__ inline void prefetch_row_l1(const T* row, int64_t len, int lane) {
-    const int64_t lines = (len * (int64_t)sizeof(T) + 127) / 128;
-    for (int64_t l = lane; l < lines; l += 32)
-        asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<const char*>(row) + l * 128));
-}
-
 template <typename T, int PL>
 __device__ void row_pass(const L2Args<T>& a, int kind, int64_t row0, int64_t row1, const T* svec,
                          T* swarp, T* srow, double* rw, double* rzo) {
@@ -385,11 +377,6 @@ __device__ void row_pass(const L2Args<T>& a, int kind, int64_t row0, int64_t row
         }
         int il = w;
         for (; il + kNW < nr; il += 2 * kNW) {
-            // the warp's next row pair heads for L1 while this pair is used
-            // (C is L2-resident; two rows in flight per warp leave the pass
-            // bound by the L2 latency)
-            if (il + 2 * kNW < nr) prefetch_row_l1(a.C + (base + il + 2 * kNW) * a.s_pad, a.s_pad, lane);
-            if (il + 3 * kNW < nr) prefetch_row_l1(a.C + (base + il + 3 * kNW) * a.s_pad, a.s_pad, lane);
             RowSlice<T, PL> c0, c1;
             c0.load(a.C + (base + il) * a.s_pad, lane);
             c1.load(a.C + (base + il + kNW) * a.s_pad, lane);
