@@ -162,6 +162,9 @@ void msp_destroy(msp_ctx* ctx) {
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     for (cudaStream_t s : ctx->fac_side)
         if (s) cudaStreamDestroy(s);
+    for (auto& pair : ctx->fac_ev)
+        for (cudaEvent_t e : pair)
+            if (e) cudaEventDestroy(e);
     delete ctx;
 }
 

@@ -540,18 +540,28 @@ msp_status chol_inv(msp_ctx* ctx, double* M, double* X, double* T1, double* T2, 
     // stream of this depth while A22 is updated and factored on the main
     // stream. Disjoint memory: T1 and T2 hold columns [0, n1) of the
     // temporaries, the second half works in columns [n1, n) of them.
+    // The stream and both events of this depth are the context's (created
+    // once): recursion at one depth is sequential, and every wait on an
+    // event is enqueued before the event is recorded again.
     cudaStream_t side = nullptr;
     cudaEvent_t ev_t1 = nullptr, ev_t2 = nullptr;
-    if (depth < 8 && (ctx->fac_side[depth] ||
-                      cudaStreamCreateWithFlags(&ctx->fac_side[depth], cudaStreamNonBlocking) == cudaSuccess))
-        side = ctx->fac_side[depth];
-    if (side && (cudaEventCreateWithFlags(&ev_t1, cudaEventDisableTiming) != cudaSuccess ||
-                 cudaEventCreateWithFlags(&ev_t2, cudaEventDisableTiming) != cudaSuccess ||
-                 cudaEventRecord(ev_t1, ctx->stream) != cudaSuccess ||
+    if (depth < 8) {
+        cudaEvent_t* ev = ctx->fac_ev[depth];
+        if ((ctx->fac_side[depth] ||
+             cudaStreamCreateWithFlags(&ctx->fac_side[depth], cudaStreamNonBlocking) == cudaSuccess) &&
+            (ev[0] || cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming) == cudaSuccess) &&
+            (ev[1] || cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming) == cudaSuccess)) {
+            side = ctx->fac_side[depth];
+            ev_t1 = ev[0];
+            ev_t2 = ev[1];
+        }
+    }
+    if (side && (cudaEventRecord(ev_t1, ctx->stream) != cudaSuccess ||
                  cudaStreamWaitEvent(side, ev_t1, 0) != cudaSuccess)) {
         cudaGetLastError();
         side = nullptr;     // fall back to the main stream
     }
+    if (!side) cudaGetLastError();
     msp_status st = MSP_OK;
     if (side) {
         cudaStream_t main_stream = ctx->stream;
@@ -574,9 +584,6 @@ msp_status chol_inv(msp_ctx* ctx, double* M, double* X, double* T1, double* T2, 
         }
     }
     if (side && st != MSP_OK) cudaStreamSynchronize(side);
-    // (destroying an event with work pending is safe)
-    if (ev_t1) cudaEventDestroy(ev_t1);
-    if (ev_t2) cudaEventDestroy(ev_t2);
     MSP_TRY(st);
     // X21 = -X22 T2 (X22 lower)
     MSP_TRY(dgemm(ctx, false, false, n2, n1, n2, -1.0, X22, ld, T2, ld, 0.0, X21, ld, 1, 0, 0));

@@ -36,8 +36,11 @@ struct msp_ctx {
     int n_events = 0;
     // worker contexts (own streams) for concurrent batch set-up, created lazily
     cudaStream_t copy_stream = nullptr;   // host-to-device copies overlapped with compute
-    // side streams of the recursive Cholesky, one per recursion depth (lazy)
+    // side streams of the recursive Cholesky, one per recursion depth, and
+    // their fork/join events (created once, lazily; an event is re-recorded
+    // only after every wait on its previous record has been enqueued)
     cudaStream_t fac_side[8] = {};
+    cudaEvent_t fac_ev[8][2] = {};
     msp_ctx** lanes = nullptr;
     cudaStream_t* lane_streams = nullptr;
     int n_lanes = 0;
