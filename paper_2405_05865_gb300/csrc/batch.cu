@@ -1381,6 +1381,9 @@ msp_status ensure_lanes(msp_ctx* ctx, int want) {
             st = msp_set_error(ctx, MSP_ECUDA, "batch: worker context: %s", msp_last_error(nullptr));
             break;
         }
+        // the lanes already factor several instances at once: no side
+        // streams inside each factor
+        l->fac_overlap = false;
         nl[made] = l;
         ns[made] = s;
     }

@@ -545,7 +545,7 @@ msp_status chol_inv(msp_ctx* ctx, double* M, double* X, double* T1, double* T2, 
     // event is enqueued before the event is recorded again.
     cudaStream_t side = nullptr;
     cudaEvent_t ev_t1 = nullptr, ev_t2 = nullptr;
-    if (depth < 8) {
+    if (ctx->fac_overlap && depth < 8) {
         cudaEvent_t* ev = ctx->fac_ev[depth];
         if ((ctx->fac_side[depth] ||
              cudaStreamCreateWithFlags(&ctx->fac_side[depth], cudaStreamNonBlocking) == cudaSuccess) &&

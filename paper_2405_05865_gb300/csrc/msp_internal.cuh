@@ -41,6 +41,7 @@ struct msp_ctx {
     // only after every wait on its previous record has been enqueued)
     cudaStream_t fac_side[8] = {};
     cudaEvent_t fac_ev[8][2] = {};
+    bool fac_overlap = true;     // false: the factor's products stay on the main stream
     msp_ctx** lanes = nullptr;
     cudaStream_t* lane_streams = nullptr;
     int n_lanes = 0;
