@@ -8,8 +8,9 @@
 // The factorisation recursion halves the matrix:
 //   [A11 . ; A21 A22]:  (L11, X11) = f(A11);  L21 = A21 X11^T;
 //   A22 -= L21 L21^T;   (L22, X22) = f(A22);  X21 = -X22 (L21 X11),
-// with a one-block dense Cholesky + triangular inverse at the 64 x 64 leaves
-// and an FP64 GEMM kernel for the rest.
+// with a one-block Cholesky + inverse at the leaves (at most 32 x 32) and an
+// FP64 GEMM kernel for the rest; L21 X11 runs on a side stream beside the
+// factorisation of A22.
 #include "bulk.cuh"
 #include "msp_internal.cuh"
 
@@ -340,7 +341,8 @@ __device__ inline double rcp_newton(double d) {
     return r;
 }
 
-// Cholesky and inverse of an nb x nb (nb <= 64) FP64 block on one SM:
+// Cholesky and inverse of an nb x nb (nb <= 64; the recursion passes at most
+// 32) FP64 block on one SM:
 // M = L L^T (lower triangle of M overwritten with L), X = L^{-1}.
 // One elimination sweep in LDL^T form: at step k every row i > k takes
 // t_i = a_ik / d_k and updates both its Schur-complement entries,
