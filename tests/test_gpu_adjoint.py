@@ -1,4 +1,4 @@
-"""Adjoint (the benchmark spec change (3)): x = (K_ell + lam I)^{-1} b with the RBF
+"""Adjoint of the solve: x = (K_ell + lam I)^{-1} b with the RBF
 kernel; the backward pass is a second MSP solve reusing the factor, plus the
 fused dL/dell pair kernel. Checked against the oracle's FP64 dense-Cholesky
 gradients and central finite differences of the FP64 dense solve."""
