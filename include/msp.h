@@ -184,6 +184,12 @@ MSP_API msp_status msp_sketch_pattern(msp_ctx* ctx, int64_t n, int64_t rows, int
  * A: device, n x n, leading dimension lda >= n, dtype MSP_F32 or MSP_F64.
  * The C of the handle has the dtype of A. s is padded internally to a
  * multiple of 128 with zero columns (sizes reported by msp_sketch_info).
+ * For the solves that follow, the handle also keeps what they need of A:
+ * for an FP32 A its upper 128 x 128 tiles, packed (about n^2 / 2 * 4 bytes
+ * of device memory; A is taken as symmetric), and the row statistics of the
+ * lower bound of |A|_2 used by the backward-error rule (3n doubles). A
+ * solve given the same A pointer uses them, so A must not change between
+ * this call and those solves.
  * Requires 1 <= gamma <= min(s, 64), 16 <= s <= 1024, s <= n. */
 MSP_API msp_status msp_sketch(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n,
                       int64_t lda, int64_t s, int gamma, uint64_t seed,
