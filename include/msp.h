@@ -617,7 +617,11 @@ MSP_API msp_status msp_dot(msp_ctx* ctx, const double* x, const double* y, int64
  *     MSP_EINVAL with a message from msp_last_error(NULL).
  *   - The first call on each device resolves the array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream capture
- *     on that device.
+ *     on that device. The address is kept for the life of the process: after
+ *     cudaDeviceReset on a device it is stale, so do not call this entry
+ *     point on a device that has been reset.
+ *   - A non-NULL stream must belong to the current device (MSP_EINVAL
+ *     otherwise).
  *   - Every call on a device shares the one array, which keeps the last
  *     call's contents; each call clears the counter it needs on its stream.
  *     Calls whose work overlaps on the GPU (different streams, or several

@@ -56,10 +56,13 @@ void msp_free(void* p) {
 
 msp_status msp_scratch(msp_ctx* ctx, size_t bytes, void** out) {
     if (bytes > ctx->scratch_bytes) {
+        // grow geometrically (1.5x the old size at least) so a sequence of
+        // slightly larger requests does not reallocate every time
+        const size_t old = ctx->scratch_bytes;
         free_on(ctx, ctx->scratch);
         ctx->scratch = nullptr;
         ctx->scratch_bytes = 0;
-        size_t want = std::max(bytes, ctx->scratch_bytes + ctx->scratch_bytes / 2);
+        size_t want = std::max(bytes, old + old / 2);
         MSP_TRY(msp_alloc(ctx, &ctx->scratch, want));
         ctx->scratch_bytes = want;
     }

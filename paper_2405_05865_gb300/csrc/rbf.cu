@@ -169,6 +169,15 @@ msp_status msp_rbf_grad_ell_static(const double* points, int64_t n, int dim, dou
         cudaGetLastError();
         return msp_set_error(nullptr, MSP_ECUDA, "rbf_grad_ell_static: no current CUDA device");
     }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (st) {
+        int sdev = -1;
+        if (cudaStreamGetDevice(st, &sdev) != cudaSuccess || sdev != dev) {
+            cudaGetLastError();
+            return msp_set_error(nullptr, MSP_EINVAL,
+                                 "rbf_grad_ell_static: the stream does not belong to the current device %d", dev);
+        }
+    }
     double* scratch = nullptr;
     {
         // set-up, once per device, with that device current: the host-side
@@ -186,7 +195,6 @@ msp_status msp_rbf_grad_ell_static(const double* points, int64_t n, int dim, dou
         }
         scratch = g_static_ptr[dev];
     }
-    cudaStream_t st = (cudaStream_t)stream;
     unsigned int* counter = reinterpret_cast<unsigned int*>(scratch);
     // the counter must start at zero (the array keeps the last call's contents)
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), st);
@@ -222,6 +230,7 @@ msp_status msp_rbf_grad_ell(msp_ctx* ctx, const double* points, int64_t n, int d
     if (!ctx) return msp_set_error(nullptr, MSP_EINVAL, "ctx is NULL");
     if (!points || !a || !x || !out || n < 1 || dim < 1 || dim > 4 || !(ell > 0.0))
         return msp_set_error(ctx, MSP_EINVAL, "rbf_grad_ell: need n >= 1, 1 <= dim <= 4, ell > 0");
+    msp::DeviceGuard guard(ctx->device);
     const unsigned blocks = (unsigned)((n + 7) / 8);
     void* scr = nullptr;
     MSP_TRY(msp_scratch(ctx, (size_t)blocks * 8 + 256, &scr));

@@ -3,6 +3,7 @@ driver (Algorithms 1, 2, 6, 7; Lemma 4.3/4.4; Section 6). Ground truths are
 dense Cholesky/eigendecompositions, scipy's CG, exact algebraic identities and
 special cases that reduce to a textbook computation."""
 
+import dataclasses
 import math
 
 import numpy as np
@@ -327,3 +328,50 @@ def test_backward_error_bound_dominates():
     x = xs + 1e-6 * np.random.default_rng(0).standard_normal(xs.shape)
     exact = ref.backward_error(A, x, w.b, w.lam, norm_A=float(np.linalg.eigvalsh(A)[-1]))
     assert ref.backward_error_bound(A, x, w.b, w.lam) >= exact * (1 - 1e-12)
+
+
+# ---- energy norm of the error (the norm of Theorem 3.2's guarantee)
+
+def test_energy_error_pins():
+    # Pinned by identities that do not use its formula:
+    #  * x = 0 gives exactly 1;
+    #  * x = x* + t q_i (q_i an eigenvector of A) gives |t| sqrt(s_i + lam) / |x*|_E
+    #    with |x*|_E^2 = b^T x* (since (A + lam I) x* = b);
+    #  * |x - x*|_E^2 = r^T (A + lam I)^{-1} r for the residual r = b - (A + lam I) x.
+    n, lam = 150, 0.03
+    A, ev = _psd(n, 21)
+    rng = np.random.default_rng(4)
+    b = rng.standard_normal(n)
+    xs = np.linalg.solve(A + lam * np.eye(n), b)
+    assert reference.energy_error(A, np.zeros(n), xs, lam) == pytest.approx(1.0, rel=1e-12)
+    w, V = np.linalg.eigh(A)
+    i, t = 17, 0.37
+    x = xs + t * V[:, i]
+    want = abs(t) * math.sqrt(w[i] + lam) / math.sqrt(b @ xs)
+    assert reference.energy_error(A, x, xs, lam) == pytest.approx(want, rel=1e-9)
+    x = xs + 1e-3 * rng.standard_normal(n)
+    r = b - (A @ x + lam * x)
+    want = math.sqrt(r @ np.linalg.solve(A + lam * np.eye(n), r) / (b @ xs))
+    assert reference.energy_error(A, x, xs, lam) == pytest.approx(want, rel=1e-8)
+
+
+@pytest.mark.parametrize("outer", ["fcg", "pcg"])
+def test_msp_outer_energy_error_monotone_exact_level2(outer):
+    # Krylov optimality of the outer iteration (Algorithm 1 step 5 with an exact
+    # SolveM1, so M is fixed): |x_t - x*|_{A + lam I} never increases, while
+    # |r_t| may. Outlier workload, n = 1024, the paper's lam0 with l = 32.
+    w = make_workload("outlier", seed=1)
+    lam0 = nystrom.lambda0_from_spectrum(w.sigma, 32)
+    base = msp.MspParams(s=w.s, lam0=lam0, inner="exact", outer=outer, tol=0.0)
+    st = msp.setup(w.A, w.lam, base)
+    xs = reference.solve_dense(w.A, w.b, w.lam)
+    # 25 iterations stay above the FP64 floor of this system (kappa ~ 1e7: the
+    # energy error settles near 4e-10 after ~28 iterations, where rounding,
+    # not the Krylov recurrence, sets the increments)
+    errs = []
+    for t in range(1, 26):
+        p = dataclasses.replace(base, max_outer=t)
+        x, _ = msp.solve(w.A, w.b, w.lam, p, st=st)
+        errs.append(reference.energy_error(w.A, x, xs, w.lam))
+    assert all(errs[i + 1] <= errs[i] * (1 + 1e-9) for i in range(len(errs) - 1))
+    assert errs[-1] <= 1e-8

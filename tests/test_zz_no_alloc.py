@@ -45,6 +45,30 @@ def test_static_variant_matches_allocating_entry_point():
     ctx.close()
 
 
+def test_static_variant_at_the_size_limit():
+    # n = 8 * 65536 - 3: the last scratch slot (block 65535) holds a partial
+    # block of 5 points and the final warp is ragged
+    from paper_2405_05865_gb300 import Context
+    ctx = Context(0)
+    lib = ctx.lib
+    n, ell = 8 * 65536 - 3, 0.05
+    P = torch.from_numpy(rbf_points(n, seed=22)).cuda()
+    rng = np.random.default_rng(22)
+    a = torch.from_numpy(rng.standard_normal(n)).cuda()
+    x = torch.from_numpy(rng.standard_normal(n)).cuda()
+    ref = float(ctx.rbf_grad_ell(P, ell, a, x))
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for _ in range(2):
+        out = torch.full((), float("nan"), dtype=torch.float64, device="cuda")
+        st = lib.msp_rbf_grad_ell_static(ctypes.c_void_p(P.data_ptr()), n, 3, ell,
+                                         ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                         ctypes.c_void_p(out.data_ptr()), stream)
+        assert st == 0, lib.msp_last_error(None)
+        torch.cuda.synchronize()
+        assert float(out) == pytest.approx(ref, rel=1e-12, abs=0.0)
+    ctx.close()
+
+
 def test_static_variant_rejects_oversized_input():
     from paper_2405_05865_gb300 import _lib
     lib = _lib.load()
