@@ -65,7 +65,11 @@ typedef enum {
 
 /* Arithmetic of the Krylov levels (the level-1 outer iteration and the
  * level-2 SolveM1 iteration).
- *   MSP_PREC_FP64  : FP64 A, FP64 sketch data and vectors.
+ *   MSP_PREC_FP64  : FP64 A, FP64 sketch data and vectors. The solve runs
+ *                    to tol; when its recurrence residual has drifted from
+ *                    the true one, further steps correct x from the FP64
+ *                    residual (at most max_refine), each asked for the
+ *                    remaining factor only.
  *   MSP_PREC_FP32  : FP32 A and sketch data, FP32 vectors, FP64 dot
  *                    products; no refinement ("plain FP32").
  *   MSP_PREC_MIXED : the FP32 solve wrapped in FP64 iterative refinement:
@@ -88,7 +92,7 @@ typedef struct {
                              Theorem 1.2 (implies normwise backward error <= tol).
                              Default 1e-10.                                      */
     int max_outer;        /* cap on level-1 iterations per Krylov solve. 2000.   */
-    int max_refine;       /* cap on FP64 refinement steps (MIXED). 20.            */
+    int max_refine;       /* cap on FP64 refinement steps (MIXED, FP64). 20.      */
     double refine_tol;    /* MIXED: each FP32 correction solve stops at relative
                              residual refine_tol. Default 1e-6.                  */
     double inner_tol;     /* level-2 (SolveM1) solve stops at
@@ -190,7 +194,8 @@ MSP_API msp_status msp_sketch_pattern(msp_ctx* ctx, int64_t n, int64_t rows, int
  * lower bound of |A|_2 used by the backward-error rule (3n doubles). A
  * solve given the same A pointer uses them, so A must not change between
  * this call and those solves.
- * Requires 1 <= gamma <= min(s, 64), 16 <= s <= 1024, s <= n. */
+ * Requires 1 <= gamma <= min(s, 64), s <= n, and 16 <= s <= 2048 for an FP32
+ * A (16 <= s <= 1024 for an FP64 A). */
 MSP_API msp_status msp_sketch(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n,
                       int64_t lda, int64_t s, int gamma, uint64_t seed,
                       msp_sketch_t** out);
@@ -254,6 +259,21 @@ MSP_API msp_status msp_solve(msp_ctx* ctx, const msp_factor_t* f, const void* A,
                      msp_dtype dtype, int64_t n, int64_t lda, double lambda,
                      const double* b, double* x, const msp_opts* opts,
                      msp_info* info);
+/* msp_solve with a separate matrix for the FP64 refinement residual. The
+ * paper works in exact arithmetic (Section 2); here the problem is a matrix
+ * given in FP64 whose FP32 rounding the level-1 iteration applies. A (FP32,
+ * the matrix the factor was built from) drives the level-1 iteration;
+ * A_res (device, n x n, ld_res >= n, MSP_F64 or MSP_F32) is the problem
+ * itself: every refinement step forms r = b - (A_res + lambda I) x with FP64
+ * accumulation, and the backward-error rule takes its norm bound from A_res.
+ * Refinement converges while rho = |(A + lambda I)^{-1} (A - A_res)| < 1,
+ * the FP32 rounding of A_res being small next to lambda + lambda_min.
+ * A_res == A is msp_solve. Other arguments and errors as msp_solve. */
+MSP_API msp_status msp_solve_refined(msp_ctx* ctx, const msp_factor_t* f, const void* A,
+                                     msp_dtype dtype, int64_t n, int64_t lda, const void* A_res,
+                                     msp_dtype res_dtype, int64_t ld_res, double lambda,
+                                     const double* b, double* x, const msp_opts* opts,
+                                     msp_info* info);
 /* Several right-hand sides with one factor: column j of B (device FP64,
  * column-major n x m, ldb >= n) is solved exactly as msp_solve would into
  * column j of X (ldx >= n), one after another; infos (host, may be NULL)

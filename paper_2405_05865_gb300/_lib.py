@@ -87,6 +87,8 @@ _SIGS = {
     "msp_solve_m1": (C.c_int, [P, P, P, P, C.POINTER(MspOpts), C.POINTER(C.c_int)]),
     "msp_solve": (C.c_int, [P, P, P, C.c_int, I64, I64, C.c_double, P, P, C.POINTER(MspOpts),
                             C.POINTER(MspInfo)]),
+    "msp_solve_refined": (C.c_int, [P, P, P, C.c_int, I64, I64, P, C.c_int, I64, C.c_double, P, P,
+                                    C.POINTER(MspOpts), C.POINTER(MspInfo)]),
     "msp_solve_full": (C.c_int, [P, P, C.c_int, I64, I64, C.c_double, P, P, I64, C.c_int,
                                  C.c_double, I64, C.c_int, C.c_uint64, C.POINTER(MspOpts),
                                  C.POINTER(MspInfo)]),

@@ -361,6 +361,27 @@ class Context:
             L.check(self.ptr, st)
         return x, info.as_dict()
 
+    def solve_refined(self, f: Factor, A: torch.Tensor, A_res: torch.Tensor, b: torch.Tensor, lam: float,
+                      raise_on_noconv: bool = True, **opts) -> tuple[torch.Tensor, dict]:
+        """msp_solve_refined: the level-1 iteration applies A (FP32, the
+        factor's matrix); each FP64 refinement residual applies A_res (the
+        problem, FP64 or FP32)."""
+        n, lda, dt = _check_matrix(A)
+        nr, ldr, dtr = _check_matrix(A_res)
+        if nr != n:
+            raise ValueError("A and A_res must have the same size")
+        if not b.is_cuda or b.dtype != torch.float64 or b.numel() != n:
+            raise ValueError("b must be a CUDA float64 vector of length n")
+        b = b.contiguous()
+        x = torch.empty_like(b)
+        o = make_opts(self.lib, **opts)
+        info = L.MspInfo()
+        st = self.lib.msp_solve_refined(self.ptr, f.handle, _ptr(A), dt, n, lda, _ptr(A_res), dtr, ldr, lam,
+                                        _ptr(b), _ptr(x), C.byref(o), C.byref(info))
+        if st != 0 and not (st == 5 and not raise_on_noconv):
+            L.check(self.ptr, st)
+        return x, info.as_dict()
+
     def solve_many(self, f: Factor, A: torch.Tensor, B: torch.Tensor, lam: float,
                    raise_on_noconv: bool = True, **opts) -> tuple[torch.Tensor, list[dict]]:
         """Columns of B (CUDA float64 (n, m)) solved one by one with the factor f."""

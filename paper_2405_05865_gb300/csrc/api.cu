@@ -211,12 +211,13 @@ msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t
                            msp_sketch_t** out, const void* host_chunks) {
     if (dtype != MSP_F32 && dtype != MSP_F64)
         return msp_set_error(ctx, MSP_EINVAL, "sketch: dtype must be MSP_F32 or MSP_F64");
-    if (n < 1 || lda < n || s < 16 || s > MSP_MAX_S || s > n || gamma < 1 ||
+    const int64_t s_max = dtype == MSP_F32 ? MSP_MAX_S_SINGLE : MSP_MAX_S;
+    if (n < 1 || lda < n || s < 16 || s > s_max || s > n || gamma < 1 ||
         gamma > MSP_MAX_GAMMA || gamma > s || n >= (1ll << 30))
         return msp_set_error(ctx, MSP_EINVAL,
-                             "sketch: need 16 <= s <= min(n, %d), 1 <= gamma <= min(s, %d), "
+                             "sketch: need 16 <= s <= min(n, %lld), 1 <= gamma <= min(s, %d), "
                              "lda >= n (n=%lld lda=%lld s=%lld gamma=%d)",
-                             MSP_MAX_S, MSP_MAX_GAMMA, (long long)n, (long long)lda,
+                             (long long)s_max, MSP_MAX_GAMMA, (long long)n, (long long)lda,
                              (long long)s, gamma);
     const int64_t sp = round_up(s, MSP_S_ALIGN);
     if (dtype == MSP_F64 && sp > 1024)
@@ -473,9 +474,19 @@ msp_status msp_solve_m1(msp_ctx* ctx, const msp_factor_t* f, const void* r, void
 
 // --------------------------------------------------------------- a6-a8
 
+// A is the matrix the level-1 iteration applies (the factor's working
+// precision); Ares (dtype dres, ld ldres) the matrix of the FP64 refinement
+// residual and of the backward-error bound, A itself unless the caller gives
+// the problem's FP64 matrix beside a reduced working copy.
 static msp_status solve_impl(msp_ctx* ctx, const msp_factor_s* f, const void* A, msp_dtype dtype,
                              int64_t n, int64_t lda, double lambda, const double* b, double* x,
-                             const msp_opts* o, msp_info* info) {
+                             const msp_opts* o, msp_info* info, const void* Ares = nullptr,
+                             msp_dtype dres = MSP_F64, int64_t ldres = 0) {
+    if (!Ares) {
+        Ares = A;
+        dres = dtype;
+        ldres = lda;
+    }
     msp_info inf{};
     inf.lambda_tilde = f->lam_tilde;
     inf.shift = f->shift;
@@ -501,6 +512,8 @@ static msp_status solve_impl(msp_ctx* ctx, const msp_factor_s* f, const void* A,
     // the sketch's packed upper tiles and norm-bound statistics stand in for A
     // when A is the sketched matrix
     const bool sketched_A = (A == f->sk->A_src);
+    const bool same_res = (Ares == A);
+    if (ldres < n) return msp_set_error(ctx, MSP_EINVAL, "solve: residual matrix leading dimension < n");
     const float* packed = (dtype == MSP_F32 && f->sk->packed && sketched_A) ? f->sk->packed : nullptr;
     if (o->criterion != MSP_STOP_RESIDUAL && o->criterion != MSP_STOP_BACKWARD)
         return msp_set_error(ctx, MSP_EINVAL, "solve: unknown criterion %d", o->criterion);
@@ -559,12 +572,12 @@ static msp_status solve_impl(msp_ctx* ctx, const msp_factor_s* f, const void* A,
         return rr <= o->tol * o->tol * bb;
     };
     MSP_CUDA_TRY(ctx, cudaMemsetAsync(scal, 0, 32, ctx->stream));
-    if (crit_bw && sketched_A && f->sk->stats) {
+    if (crit_bw && sketched_A && same_res && f->sk->stats) {
         if (cudaMemcpyAsync(scal + 2, f->sk->stats + 3 * n, 8, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess) {
             cudaGetLastError();
             return finish(msp_set_error(ctx, MSP_ECUDA, "solve: norm bound copy failed"));
         }
-    } else if (crit_bw && (st = msp_norm_lb_launch(ctx, A, dtype, n, lda, nwork, scal + 2)) != MSP_OK) {
+    } else if (crit_bw && (st = msp_norm_lb_launch(ctx, Ares, dres, n, ldres, nwork, scal + 2)) != MSP_OK) {
         return finish(st);
     }
     if ((st = msp_norm2(ctx, b, n, scal + 0)) != MSP_OK) return finish(st);
@@ -578,15 +591,19 @@ static msp_status solve_impl(msp_ctx* ctx, const msp_factor_s* f, const void* A,
         inf.rel_resid = 0.0;
         return finish(MSP_OK);
     }
-    const int max_steps = (prec == MSP_PREC_MIXED) ? o->max_refine + 1 : 1;
-    const double step_tol = (prec == MSP_PREC_MIXED) ? std::max(o->refine_tol, o->tol) : o->tol;
+    // MIXED: every correction solve to refine_tol. FP64: the first solve to
+    // tol; its recurrence residual can drift from the true one, so further
+    // steps correct from the FP64 residual, each asked for just the remaining
+    // factor (with a margin of 2). FP32: one solve.
+    const int max_steps = (prec == MSP_PREC_FP32) ? 1 : o->max_refine + 1;
+    const double mixed_tol = std::max(o->refine_tol, o->tol);
     msp_status kst = MSP_OK;
     bool have_resid = true;   // r64 / rr hold the residual of the current x (x = 0: r = b)
     for (int k = 0; k < max_steps; ++k) {
         if (!have_resid) {
             // r = b - (A + lam I) x, FP64 accumulation
             if ((st = pr.begin(0)) != MSP_OK) return finish(st);
-            if ((st = msp_matvec64(ctx, A, dtype, n, lda, lambda, x, b, r64, scal + 1)) != MSP_OK)
+            if ((st = msp_matvec64(ctx, Ares, dres, n, ldres, lambda, x, b, r64, scal + 1)) != MSP_OK)
                 return finish(st);
             if ((st = pr.end()) != MSP_OK) return finish(st);
             if ((st = pr.finish(&slots[2], 1)) != MSP_OK) return finish(st);
@@ -597,6 +614,10 @@ static msp_status solve_impl(msp_ctx* ctx, const msp_factor_s* f, const void* A,
             have_resid = true;
         }
         if (met()) break;
+        double step_tol = o->tol;
+        if (prec == MSP_PREC_MIXED) step_tol = mixed_tol;
+        else if (prec == MSP_PREC_FP64 && k > 0)
+            step_tol = std::min(0.5, std::max(o->tol, 0.5 * o->tol * std::sqrt(bb / rr)));
         // correction solve on the normalised residual: (A + lam I) d = r / |r|
         if ((st = msp_scale_cast(ctx, r64, scal + 1, n, wt, rhs_w)) != MSP_OK) return finish(st);
         int it = 0, in = 0;
@@ -608,11 +629,11 @@ static msp_status solve_impl(msp_ctx* ctx, const msp_factor_s* f, const void* A,
         if ((st = msp_axpy_back(ctx, x, sol_w, wt, scal + 1, n, k > 0)) != MSP_OK) return finish(st);
         steps = k + 1;
         have_resid = false;
-        if (prec != MSP_PREC_MIXED) break;
+        if (prec == MSP_PREC_FP32) break;
     }
     if (!have_resid) {
         if ((st = pr.begin(0)) != MSP_OK) return finish(st);
-        if ((st = msp_matvec64(ctx, A, dtype, n, lda, lambda, x, b, r64, scal + 1)) != MSP_OK)
+        if ((st = msp_matvec64(ctx, Ares, dres, n, ldres, lambda, x, b, r64, scal + 1)) != MSP_OK)
             return finish(st);
         if ((st = pr.end()) != MSP_OK) return finish(st);
         if ((st = pr.finish(&slots[2], 1)) != MSP_OK) return finish(st);
@@ -639,6 +660,19 @@ msp_status msp_solve(msp_ctx* ctx, const msp_factor_t* f, const void* A, msp_dty
     msp_opts o;
     if (opts) o = *opts; else msp_default_opts(&o);
     return solve_impl(ctx, f, A, dtype, n, lda, lambda, b, x, &o, info);
+}
+
+msp_status msp_solve_refined(msp_ctx* ctx, const msp_factor_t* f, const void* A, msp_dtype dtype,
+                             int64_t n, int64_t lda, const void* A_res, msp_dtype res_dtype, int64_t ld_res,
+                             double lambda, const double* b, double* x, const msp_opts* opts, msp_info* info) {
+    if (!ctx) return msp_set_error(nullptr, MSP_EINVAL, "ctx is NULL");
+    if (!f || !A || !A_res || !b || !x) return msp_set_error(ctx, MSP_EINVAL, "solve_refined: NULL argument");
+    if (res_dtype != MSP_F64 && res_dtype != MSP_F32)
+        return msp_set_error(ctx, MSP_EINVAL, "solve_refined: residual matrix must be MSP_F64 or MSP_F32");
+    DeviceGuard g(ctx->device);
+    msp_opts o;
+    if (opts) o = *opts; else msp_default_opts(&o);
+    return solve_impl(ctx, f, A, dtype, n, lda, lambda, b, x, &o, info, A_res, res_dtype, ld_res);
 }
 
 msp_status msp_solve_many(msp_ctx* ctx, const msp_factor_t* f, const void* A, msp_dtype dtype, int64_t n,

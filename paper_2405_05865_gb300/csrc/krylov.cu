@@ -744,7 +744,8 @@ msp_status launch_level2_pl(msp_ctx* ctx, L2Args<T>& a, int G) {
 
 template <typename T>
 msp_status launch_level2(msp_ctx* ctx, L2Args<T>& a, int G) {
-    // one instantiation per padded sketch size (multiples of 128 up to 1024)
+    // one instantiation per padded sketch size (multiples of 128 up to 1024,
+    // then 1536 and 2048)
     switch (a.s_pad) {
         case 128: return launch_level2_pl<T, 4>(ctx, a, G);
         case 256: return launch_level2_pl<T, 8>(ctx, a, G);
@@ -754,6 +755,8 @@ msp_status launch_level2(msp_ctx* ctx, L2Args<T>& a, int G) {
         case 768: return launch_level2_pl<T, 24>(ctx, a, G);
         case 896: return launch_level2_pl<T, 28>(ctx, a, G);
         case 1024: return launch_level2_pl<T, 32>(ctx, a, G);
+        case 1536: return launch_level2_pl<T, 48>(ctx, a, G);
+        case 2048: return launch_level2_pl<T, 64>(ctx, a, G);
         default: break;
     }
     return msp_set_error(ctx, MSP_EINVAL, "level-2: unsupported padded sketch size %lld",

@@ -10,7 +10,8 @@
 #include "msp.h"
 
 #define MSP_MAX_GAMMA 64
-#define MSP_MAX_S 1024
+#define MSP_MAX_S 1024          // batched, general and FP64 sketches
+#define MSP_MAX_S_SINGLE 2048   // FP32 sketches of a single system (msp_sketch)
 #define MSP_S_ALIGN 128
 
 // ------------------------------------------------------------------ handles

@@ -230,9 +230,9 @@ msp_status launch_sketch_apply_r(msp_ctx* ctx, const T* A, int64_t lda, int64_t 
                                  int64_t s_pad, const int32_t* ptr, const int32_t* ent,
                                  T scale, T* C) {
     // s_pad is a multiple of 128: the smallest NC with s_pad / NC a multiple
-    // of 32 and at most 256 threads (two blocks per SM fit)
+    // of 32 and at most 256 threads (two blocks per SM fit up to NC = 4)
     int nc = 0;
-    for (int cand : {1, 2, 3, 4}) {
+    for (int cand : {1, 2, 3, 4, 6, 8}) {
         if (s_pad % cand == 0 && (s_pad / cand) % 32 == 0 && s_pad / cand <= 256) {
             nc = cand;
             break;
@@ -267,6 +267,8 @@ msp_status launch_sketch_apply_r(msp_ctx* ctx, const T* A, int64_t lda, int64_t 
         MSP_SK_CASE(2)
         MSP_SK_CASE(3)
         MSP_SK_CASE(4)
+        MSP_SK_CASE(6)
+        MSP_SK_CASE(8)
         default:
             return msp_set_error(ctx, MSP_EINVAL, "sketch: unsupported s_pad %lld",
                                  (long long)s_pad);
@@ -357,8 +359,8 @@ msp_status msp_sketch_apply_rows(msp_ctx* ctx, const void* A, msp_dtype dt, int6
                                  const int32_t* ent, int gamma, void* C) {
     // accumulators per thread: R rows x NC columns; R = 4 vectors of 16 bytes
     double scale = 1.0 / sqrt((double)gamma);
-    if (s_pad > 1024)
-        return msp_set_error(ctx, MSP_EINVAL, "sketch: s_pad %lld above 1024 is not supported",
+    if (s_pad > (dt == MSP_F32 ? MSP_MAX_S_SINGLE : 1024))
+        return msp_set_error(ctx, MSP_EINVAL, "sketch: s_pad %lld above the supported maximum",
                              (long long)s_pad);
     if (dt == MSP_F32)
         return launch_sketch_apply_r<float, 16>(ctx, (const float*)A, lda, m, n, s_pad, ptr, ent,

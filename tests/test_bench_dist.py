@@ -69,9 +69,12 @@ def test_reference_arm_prints_on_rank_zero_only():
 def test_reference_arm_line_on_rank_zero():
     env = dict(os.environ, RANK="0", WORLD_SIZE="1", LOCAL_RANK="0")
     p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                        "--steps", "1", "--warmup", "0", "--n", "256", "--s", "64", "--cpu-iters", "1"],
+                        "--steps", "1", "--warmup", "0", "--n", "256", "--s", "64", "--ref-sample-iters", "1"],
                        capture_output=True, text=True, env=env, timeout=300)
     assert p.returncode == 0, p.stderr[-2000:]
     line = json.loads(p.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+    # a complete oracle solve was timed, and the steps' own time is reported
+    assert line["cpu_baseline"]["complete_solve_s"] > 0 and line["cpu_baseline"]["complete_solve_iters"] > 0
+    assert line["ms_per_step"] > 0

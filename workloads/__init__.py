@@ -10,7 +10,10 @@ from .generators import (  # noqa: F401
     outlier_spectrum,
     householder_spectrum,
     spectrum_matrix,
+    gaussian_square,
     householder_matrix,
+    householder_factors,
+    householder_lowrank,
     rbf_points,
     rbf_kernel,
     rhs,

@@ -59,32 +59,66 @@ def householder_spectrum(n: int, k: int, seed: int, hi: float = 1e6,
     return np.concatenate([out, 0.5 + 0.5 * u])
 
 
+def gaussian_square(n: int, seed: int) -> np.ndarray:
+    """The seeded N(0,1) n x n matrix whose orthogonal factor is the Q of
+    ``spectrum_matrix`` (for large n the caller may factor it elsewhere)."""
+    return _rng(seed, _TAG_MATRIX).standard_normal((n, n))
+
+
 def spectrum_matrix(sigma: np.ndarray, seed: int) -> np.ndarray:
     """A = Q diag(sigma) Q^T with Q the orthogonal factor of a seeded N(0,1)
     n x n matrix (numpy.linalg.qr). sigma[i] is attached to column i of Q.
     The result is symmetrised exactly."""
     n = sigma.shape[0]
-    G = _rng(seed, _TAG_MATRIX).standard_normal((n, n))
+    G = gaussian_square(n, seed)
     Q, _ = np.linalg.qr(G)
     A = (Q * sigma[None, :]) @ Q.T
     return 0.5 * (A + A.T)
 
 
+def householder_factors(n: int, seed: int, reflectors: int = 64) -> tuple[np.ndarray, np.ndarray]:
+    """Q = H_1 H_2 ... H_r, H_i = I - tau_i v_i v_i^T, tau_i = 2 / |v_i|^2, v_i ~ N(0, I)
+    (row i of a seeded r x n draw), in compact WY form Q = I - Y T Y^T
+    (Schreiber and Van Loan): Y = [v_1 ... v_r] (n x r) and T upper triangular,
+    T_k = [[T_{k-1}, -tau_k T_{k-1} Y_{k-1}^T v_k], [0, tau_k]]."""
+    V = _rng(seed, _TAG_MATRIX).standard_normal((reflectors, n))
+    Y = np.ascontiguousarray(V.T)
+    T = np.zeros((reflectors, reflectors))
+    for k in range(reflectors):
+        v = Y[:, k]
+        tau = 2.0 / float(v @ v)
+        if k:
+            T[:k, k] = -tau * (T[:k, :k] @ (Y[:, :k].T @ v))
+        T[k, k] = tau
+    return Y, T
+
+
+def householder_lowrank(sigma: np.ndarray, seed: int, reflectors: int = 64) -> tuple[np.ndarray, np.ndarray]:
+    """A = Q diag(sigma) Q^T = diag(sigma) + Z M Z^T with Q = I - Y T Y^T
+    (``householder_factors``): U = Y T, P = diag(sigma) Y, S = Y^T diag(sigma) Y,
+    Z = [U P] (n x 2r) and M = [[S, -I], [-I, 0]]. Returns (Z, M); a product
+    A x then costs O(r n) and forming A one rank-2r update."""
+    n = sigma.shape[0]
+    Y, T = householder_factors(n, seed, reflectors)
+    U = Y @ T
+    P = sigma[:, None] * Y
+    S = Y.T @ P
+    S = 0.5 * (S + S.T)
+    r = reflectors
+    M = np.zeros((2 * r, 2 * r))
+    M[:r, :r] = S
+    M[:r, r:] = -np.eye(r)
+    M[r:, :r] = -np.eye(r)
+    return np.concatenate([U, P], axis=1), M
+
+
 def householder_matrix(sigma: np.ndarray, seed: int, reflectors: int = 64) -> np.ndarray:
     """A = Q diag(sigma) Q^T with Q = H_1 H_2 ... H_r, H_i = I - 2 v v^T / |v|^2,
-    v_i ~ N(0, I). Built by applying the reflectors to diag(sigma) on both sides
-    (O(r n^2)), then symmetrised exactly."""
-    n = sigma.shape[0]
-    V = _rng(seed, _TAG_MATRIX).standard_normal((reflectors, n))
-    A = np.diag(sigma.astype(np.float64))
-    # Q A Q^T with Q = H_1 ... H_r: apply H_r first (innermost), H_1 last.
-    for i in range(reflectors - 1, -1, -1):
-        v = V[i]
-        beta = 2.0 / float(v @ v)
-        Av = A @ v
-        A = A - beta * np.outer(v, Av)          # H A
-        vA = v @ A
-        A = A - beta * np.outer(vA, v)          # (H A) H
+    v_i ~ N(0, I), formed as diag(sigma) + Z M Z^T (``householder_lowrank``,
+    one rank-2r product, O(r n^2)), then symmetrised exactly."""
+    Z, M = householder_lowrank(sigma, seed, reflectors)
+    A = Z @ (M @ Z.T)
+    A[np.diag_indices_from(A)] += sigma
     return 0.5 * (A + A.T)
 
 
