@@ -83,6 +83,10 @@ def parse():
                     help="size of the Householder-product workload (s = n / 16, n / 32 outliers)")
     ap.add_argument("--refined-steps", type=int, default=3)
     ap.add_argument("--no-sketched-level2", action="store_true")
+    ap.add_argument("--schatten-matrix", default="outlier", choices=["outlier", "rbf"],
+                    help="matrix of the --section schatten run (rbf needs no QR to generate)")
+    ap.add_argument("--section", default="all", choices=["all", "schatten", "refined", "sketch"],
+                    help="run one section alone and print its JSON (profiling)")
     ap.add_argument("--ref-sample-iters", type=int, default=3,
                     help="level-1 iterations per bounded oracle sample of the reference arm")
     return ap.parse_args()
@@ -669,12 +673,16 @@ def run_schatten_outlier(args, ctx, dev, rank, peak):
     n = args.n
     k = max(1, 256 * n // 16384)
     sig = workloads.outlier_spectrum(n, k)
-    G = torch.from_numpy(workloads.gaussian_square(n, 13 + rank).astype(np.float32)).to(dev)
-    Q, _ = torch.linalg.qr(G)
-    del G
-    A = (Q * torch.from_numpy(sig).to(dev, torch.float32)[None, :]) @ Q.T
-    del Q
-    A = 0.5 * (A + A.T)
+    if args.schatten_matrix == "rbf":
+        A = torch.from_numpy(make_problem(n, 13 + rank)[0]).to(dev)
+        sig = np.full(n, 1.0)        # K_ii = 1: tr K = n
+    else:
+        G = torch.from_numpy(workloads.gaussian_square(n, 13 + rank).astype(np.float32)).to(dev)
+        Q, _ = torch.linalg.qr(G)
+        del G
+        A = (Q * torch.from_numpy(sig).to(dev, torch.float32)[None, :]) @ Q.T
+        del Q
+        A = 0.5 * (A + A.T)
     trace = float(torch.diagonal(A).to(torch.float64).sum())
     exact = float(np.sum(sig))
     ctx.schatten(A, p=1.0, probes=256)
@@ -692,8 +700,10 @@ def run_schatten_outlier(args, ctx, dev, rank, peak):
     alg = 4.0 * n * (n + 1) / 2
     del A
     torch.cuda.empty_cache()
-    return {"workload": f"A = Q diag(sigma) Q^T, n={n}, Q from QR of a seeded N(0,1) matrix, {k} outliers "
-                        "1e4->1e2, tail i^-1.5, FP32; 256 Rademacher probes",
+    desc = (f"A = Q diag(sigma) Q^T, n={n}, Q from QR of a seeded N(0,1) matrix, {k} outliers 1e4->1e2, "
+            "tail i^-1.5, FP32; 256 Rademacher probes") if args.schatten_matrix == "outlier" else \
+        f"RBF kernel n={n}, l=0.1, FP32 (tr K = n); 256 Rademacher probes"
+    return {"workload": desc,
             "estimate": est, "std_err": se, "sum_sigma": exact, "trace_fp32_A": trace,
             "deviation_in_std_err": (est - exact) / se if se else None,
             "ms_per_estimate": ms, "estimates_per_s": 1000.0 / ms,
@@ -1032,11 +1042,45 @@ def run_msp(args, rank, world, local):
         torch.distributed.destroy_process_group()
 
 
+def run_section(args, local):
+    """One section alone on one GPU (for profiling runs): its JSON only."""
+    import torch
+    from paper_2405_05865_gb300 import Context
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    ctx = Context(local)
+    peak, _ = measured_peaks()
+    if args.section == "schatten":
+        out = run_schatten_outlier(args, ctx, dev, 0, peak)
+    elif args.section == "refined":
+        out = run_refined(args, ctx, dev, 0, peak)
+    else:
+        A32, b, lam = make_problem(args.n, 0)
+        A = torch.from_numpy(A32).to(dev)
+        ms = []
+        for k in range(args.warmup + args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(ctx.stream)
+            sk = ctx.sketch(A, args.s, 8, SEED)
+            e1.record(ctx.stream)
+            torch.cuda.synchronize(dev)
+            if k >= args.warmup:
+                ms.append(e0.elapsed_time(e1))
+            sk.close()
+        out = {"sketch_ms": statistics.median(ms), "n": args.n, "s": args.s}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.section != "all":
+        run_section(args, local)
         return
     run_msp(args, rank, world, local)
 

@@ -34,6 +34,23 @@ def probes(n: int, m: int, seed: int) -> np.ndarray:
     return G
 
 
+def probes_fast(n: int, m: int, seed: int) -> np.ndarray:
+    """``probes`` computed with wrapping uint64 array arithmetic (the same
+    SplitMix64 definition as ``prng``, evaluated for all (i, j) at once), for
+    sizes where the per-entry loop is too slow. Equal to ``probes`` entry for
+    entry (pinned)."""
+    i = np.arange(n, dtype=np.uint64)[:, None]
+    j = np.arange(m, dtype=np.uint64)[None, :]
+    stream = np.uint64(PROBE_STREAM) + np.uint64(2) * (j // np.uint64(256))
+    k = (stream << np.uint64(56)) | (i << np.uint64(8)) | (j % np.uint64(256))
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & prng.MASK64) + (k + np.uint64(1)) * np.uint64(prng.GOLDEN_GAMMA)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    z = z ^ (z >> np.uint64(31))
+    return np.where((z >> np.uint64(63)) != 0, -1.0, 1.0)
+
+
 def quadratic_forms(A: np.ndarray, G: np.ndarray) -> np.ndarray:
     """q_j = g_j^T A g_j in FP64."""
     A = np.asarray(A, dtype=np.float64)

@@ -31,6 +31,18 @@ def rel_residual(A, x, b, lam) -> float:
     return float(np.linalg.norm(residual(A, x, b, lam)) / np.linalg.norm(b))
 
 
+def rel_residual_extended(A, x, b, lam) -> float:
+    """|b - (A + lam I) x| / |b| with the products and sums in numpy's
+    extended type (80-bit on x86, IEEE quad on AArch64): resolves residuals
+    of ill-conditioned systems below the FP64 evaluation floor
+    u sum_j |A_ij x_j|."""
+    Al = np.asarray(A, dtype=np.float64).astype(np.longdouble)
+    xl = np.asarray(x, dtype=np.float64).astype(np.longdouble)
+    bl = np.asarray(b, dtype=np.float64).astype(np.longdouble)
+    r = bl - (Al @ xl + np.longdouble(lam) * xl)
+    return float(np.sqrt(np.sum(r * r)) / np.sqrt(np.sum(bl * bl)))
+
+
 def norm2_power(A: np.ndarray, iters: int = 30, seed: int = 1) -> float:
     """|A|_2 for symmetric PSD A by power iteration (lower bound that converges
     from below; 30 steps)."""

@@ -603,7 +603,7 @@ static msp_status solve_impl(msp_ctx* ctx, const msp_factor_s* f, const void* A,
         if (!have_resid) {
             // r = b - (A + lam I) x, FP64 accumulation
             if ((st = pr.begin(0)) != MSP_OK) return finish(st);
-            if ((st = msp_matvec64(ctx, Ares, dres, n, ldres, lambda, x, b, r64, scal + 1)) != MSP_OK)
+            if ((st = msp_matvec64(ctx, Ares, dres, n, ldres, lambda, x, b, r64, scal + 1, prec == MSP_PREC_FP64)) != MSP_OK)
                 return finish(st);
             if ((st = pr.end()) != MSP_OK) return finish(st);
             if ((st = pr.finish(&slots[2], 1)) != MSP_OK) return finish(st);
@@ -633,7 +633,7 @@ static msp_status solve_impl(msp_ctx* ctx, const msp_factor_s* f, const void* A,
     }
     if (!have_resid) {
         if ((st = pr.begin(0)) != MSP_OK) return finish(st);
-        if ((st = msp_matvec64(ctx, Ares, dres, n, ldres, lambda, x, b, r64, scal + 1)) != MSP_OK)
+        if ((st = msp_matvec64(ctx, Ares, dres, n, ldres, lambda, x, b, r64, scal + 1, prec == MSP_PREC_FP64)) != MSP_OK)
             return finish(st);
         if ((st = pr.end()) != MSP_OK) return finish(st);
         if ((st = pr.finish(&slots[2], 1)) != MSP_OK) return finish(st);

@@ -1007,13 +1007,109 @@ msp_status msp_solve_m1_impl(msp_ctx* ctx, const msp_factor_s* f, const void* r,
     return MSP_OK;
 }
 
+namespace {
+
+// Error-free transformations (Knuth's TwoSum; the FMA form of Dekker's
+// TwoProduct): a + b = s + e and a b = p + e exactly in FP64.
+__device__ inline void two_sum(double a, double b, double& s, double& e) {
+    s = a + b;
+    const double bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ inline void two_prod(double a, double b, double& p, double& e) {
+    p = a * b;
+    e = fma(a, b, -p);
+}
+// (hi, lo) += (p, q), a double-double sum (hi, lo) renormalised
+__device__ inline void dd_add(double& hi, double& lo, double p, double q) {
+    double s, e;
+    two_sum(hi, p, s, e);
+    e += lo + q;
+    hi = s + e;
+    lo = e - (hi - s);
+}
+
+// out = b - (A + lam I) x with double-double accumulation: every product
+// and sum error-free transformed, rounded to FP64 once per row. Its error is
+// a few u |r_i| + u^2 sum_j |A_ij x_j| instead of u sum_j |A_ij x_j|, so the
+// residual of an ill-conditioned system stays resolved below the FP64
+// accumulation floor. |out|^2 into *norm2 as k_matvec64.
+template <typename TA>
+__global__ void __launch_bounds__(256) k_matvec64_dd(const TA* __restrict__ A, int64_t lda, int64_t n, double lam,
+                                                    const double* __restrict__ x, const double* __restrict__ b,
+                                                    double* __restrict__ out, double* __restrict__ part,
+                                                    unsigned int* counter, double* norm2) {
+    __shared__ double red[32];
+    __shared__ bool am_last;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    double nn = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const TA* row = A + i * lda;
+        double hi = 0.0, lo = 0.0;
+        for (int64_t j = lane; j < n; j += 32) {
+            double p, e;
+            two_prod((double)__ldcs(&row[j]), x[j], p, e);
+            dd_add(hi, lo, p, e);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ph = __shfl_xor_sync(0xffffffffu, hi, o);
+            const double pl = __shfl_xor_sync(0xffffffffu, lo, o);
+            dd_add(hi, lo, ph, pl);
+        }
+        if (lane == 0) {
+            double p, e;
+            two_prod(lam, x[i], p, e);
+            dd_add(hi, lo, p, e);
+            double v = hi + lo;
+            if (b) {
+                double rh = b[i], rl = 0.0;
+                dd_add(rh, rl, -hi, -lo);
+                v = rh + rl;
+            }
+            out[i] = v;
+            nn += v * v;
+        }
+    }
+    double tot = block_sum(nn, red);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = tot;
+        __threadfence();
+        unsigned int t = atomicAdd(counter, 1u);
+        am_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    double all = sum_parts(part, 1, gridDim.x, red);
+    if (threadIdx.x == 0) {
+        *counter = 0;
+        if (norm2) *norm2 = all;
+    }
+}
+
+}  // namespace
+
 msp_status msp_matvec64(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t n, int64_t lda,
                         double lambda, const double* x, const double* b, double* out,
-                        double* norm2_out_dev) {
+                        double* norm2_out_dev, bool compensated) {
     const int Gg = gemv_grid(ctx);
     void* scr = nullptr;
     MSP_TRY(msp_scratch(ctx, (size_t)Gg * 8 + 256, &scr));
     CtlBlock* ctl = (CtlBlock*)ctx->ctl;
+    if (compensated) {
+        if (dt == MSP_F32)
+            k_matvec64_dd<float><<<Gg, 256, 0, ctx->stream>>>((const float*)A, lda, n, lambda, x, b, out,
+                                                              (double*)scr, &ctl->last_block_counter,
+                                                              norm2_out_dev);
+        else
+            k_matvec64_dd<double><<<Gg, 256, 0, ctx->stream>>>((const double*)A, lda, n, lambda, x, b, out,
+                                                               (double*)scr, &ctl->last_block_counter,
+                                                               norm2_out_dev);
+        MSP_CHECK_LAUNCH(ctx);
+        return MSP_OK;
+    }
     const bool vec = (dt == MSP_F32) && (lda % 4 == 0) && (n % 4 == 0) &&
                      ((uintptr_t)A % 16 == 0) && ((uintptr_t)x % 16 == 0);
     if (dt == MSP_F32) {

@@ -307,9 +307,11 @@ msp_status msp_krylov_solve(msp_ctx* ctx, const msp_factor_s* f, const void* A,
                             const void* rhs, void* sol, double tol_rel, int max_outer,
                             const msp_opts* o, int* iters, int* inner_iters,
                             ProfSlot* prof, const float* packed);
+// compensated: double-double accumulation (k_matvec64_dd), for residuals
+// below the FP64 accumulation floor
 msp_status msp_matvec64(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t n,
                         int64_t lda, double lambda, const double* x, const double* b,
-                        double* out, double* norm2_out_dev);
+                        double* out, double* norm2_out_dev, bool compensated = false);
 
 // Event timing helper: with `on`, records an event pair around each timed
 // launch; finish() sums the elapsed times (after a stream sync).

@@ -146,13 +146,18 @@ def test_solve_fp64_outlier_workload(ctx):
     x = x.cpu().numpy()
     xs = reference.solve_dense(w.A, w.b, w.lam)
     assert info["rel_resid"] <= 1e-10
-    assert reference.rel_residual(w.A, x, w.b, w.lam) <= 1.5e-10
+    # evaluated in extended precision: in FP64 the residual of this system
+    # (kappa ~ 1e7, |x| ~ 850 |b|) is only resolved to ~2.4e-10
+    assert reference.rel_residual_extended(w.A, x, w.b, w.lam) <= 1.2e-10
     kappa = (w.sigma.max() + w.lam) / (w.sigma.min() + w.lam)
     assert np.linalg.norm(x - xs) / np.linalg.norm(xs) <= kappa * 1e-10
     # oracle with the same parameters takes a similar number of iterations
     p = omsp.MspParams(s=w.s, lam0=lam0, phi=4 * w.s, tol=1e-10, inner_tol=1e-10)
     _, oinfo = omsp.solve(w.A, w.b, w.lam, p)
-    assert abs(info["outer_iters"] - oinfo.outer_iters) <= max(3, 0.15 * oinfo.outer_iters)
+    # (the GPU count includes the refinement steps that correct the drift of
+    # the recurrence residual, a few iterations each)
+    slack = max(3, 0.15 * oinfo.outer_iters)
+    assert oinfo.outer_iters - slack <= info["outer_iters"] <= oinfo.outer_iters + slack + 8 * (info["refine_steps"] - 1)
 
 
 @pytest.mark.parametrize("n", [2048, 3000])

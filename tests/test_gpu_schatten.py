@@ -22,7 +22,11 @@ def ctx():
     c.close()
 
 
-@pytest.mark.parametrize("n,m", [(200, 64), (1000 + 37, 128), (2048, 320)])
+# (n, m): rows 16-byte aligned (n % 4 == 0) take the tensor-core path, the
+# others the SIMT path; 320 probes are two groups (256 + 64), 1000 leaves a
+# ragged last tile row and column
+@pytest.mark.parametrize("n,m", [(200, 64), (1000 + 37, 128), (2048, 320), (1000, 320), (4096 + 128, 256),
+                                 (130, 192)])
 def test_quadratic_forms_match_oracle(ctx, n, m):
     sig = outlier_spectrum(n, max(4, n // 64))
     A = spectrum_matrix(sig, seed=n).astype(np.float32)
@@ -62,3 +66,29 @@ def test_schatten_rejects_other_p(ctx):
     with pytest.raises(MspError) as e:
         ctx.schatten(A, p=0.5)
     assert e.value.status == 1
+
+
+def test_quadratic_forms_full_size(ctx):
+    # the bench's size: n = 16384, 256 probes, every q_j against the FP64
+    # oracle on the same probes (RBF matrix, FP64 values rounded once to FP32)
+    w = make_workload("rbf", seed=2, n=16384)
+    A = np.ascontiguousarray(w.A, dtype=np.float32)
+    q = ctx.hutchinson(torch.from_numpy(A).cuda(), probes=256, seed=SEED).cpu().numpy()
+    G = hutchinson.probes_fast(16384, 256, SEED)
+    A64 = A.astype(np.float64)
+    qo = hutchinson.quadratic_forms(A64, G)
+    bound = 512 * 2.0 ** -24 * np.abs(A64).sum()
+    assert np.all(np.abs(q - qo) <= bound)
+    # and far inside it: the three BF16 terms carry the whole FP32 significand
+    assert np.abs(q - qo).max() <= 1e-5 * np.abs(qo).max()
+
+
+def test_schatten1_outlier_spectrum_tensor_core_sizes(ctx):
+    # |A|_1 = sum sigma of a 4096 x 4096 PSD matrix (64 outliers 1e4 -> 1e2,
+    # tail i^-1.5) within 4 Rademacher standard deviations
+    n = 4096
+    sig = outlier_spectrum(n, 64)
+    A = spectrum_matrix(sig, seed=9)
+    est, se = ctx.schatten(torch.from_numpy(A.astype(np.float32)).cuda(), p=1.0, probes=256)
+    sd = np.sqrt(hutchinson.rademacher_variance(A) / 256)
+    assert abs(est - reference.schatten(sig, 1.0)) <= 4 * sd

@@ -375,3 +375,24 @@ def test_msp_outer_energy_error_monotone_exact_level2(outer):
         errs.append(reference.energy_error(w.A, x, xs, w.lam))
     assert all(errs[i + 1] <= errs[i] * (1 + 1e-9) for i in range(len(errs) - 1))
     assert errs[-1] <= 1e-8
+
+
+def test_extended_residual_exact_on_integers():
+    # integer A (< 2^28) and x (< 2^28), n = 16: every product and partial
+    # sum is an integer below 2^60, exact in the extended type (64-bit or
+    # 113-bit significand) but not in FP64. b is an FP64 number near A x, so
+    # the exact residual r = b - (A + I) x is a small integer vector, computed
+    # here with Python integers; FP64 evaluation misses it by ~2^7 per entry
+    rng = np.random.default_rng(7)
+    n = 16
+    Ai = [[int(v) for v in row] for row in rng.integers(-2**28, 2**28, (n, n))]
+    xi = [int(v) for v in rng.integers(-2**28, 2**28, n)]
+    ax = [sum(Ai[i][j] * xi[j] for j in range(n)) + xi[i] for i in range(n)]
+    b = np.array([float(v) for v in ax])                 # rounded to FP64
+    r = [int(b[i]) - ax[i] for i in range(n)]            # exact
+    want = math.sqrt(sum(v * v for v in r)) / math.sqrt(sum(int(v) ** 2 for v in b))
+    A = np.array(Ai, dtype=np.float64)
+    x = np.array(xi, dtype=np.float64)
+    got = reference.rel_residual_extended(A, x, b, 1.0)
+    assert want > 0 and got == pytest.approx(want, rel=1e-9, abs=0.0)
+    assert reference.rel_residual(A, x, b, 1.0) != pytest.approx(want, rel=1e-3, abs=0.0)
