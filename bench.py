@@ -85,6 +85,9 @@ def parse():
     ap.add_argument("--no-sketched-level2", action="store_true")
     ap.add_argument("--schatten-matrix", default="outlier", choices=["outlier", "rbf"],
                     help="matrix of the --section schatten run (rbf needs no QR to generate)")
+    ap.add_argument("--hutchinson-terms", type=int, default=2, choices=[2, 3],
+                    help="16-bit terms per FP32 entry of A in the tensor-core Hutchinson product "
+                         "(2: FP16, 22 bits; 3: BF16, exact)")
     ap.add_argument("--section", default="all", choices=["all", "schatten", "refined", "sketch"],
                     help="run one section alone and print its JSON (profiling)")
     ap.add_argument("--ref-sample-iters", type=int, default=3,
@@ -685,6 +688,7 @@ def run_schatten_outlier(args, ctx, dev, rank, peak):
         A = 0.5 * (A + A.T)
     trace = float(torch.diagonal(A).to(torch.float64).sum())
     exact = float(np.sum(sig))
+    ctx.set_hutchinson_terms(args.hutchinson_terms)
     ctx.schatten(A, p=1.0, probes=256)
     stream = ctx.stream
     e0 = torch.cuda.Event(enable_timing=True)
@@ -698,6 +702,7 @@ def run_schatten_outlier(args, ctx, dev, rank, peak):
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / args.steps
     alg = 4.0 * n * (n + 1) / 2
+    ctx.set_hutchinson_terms(2)
     del A
     torch.cuda.empty_cache()
     desc = (f"A = Q diag(sigma) Q^T, n={n}, Q from QR of a seeded N(0,1) matrix, {k} outliers 1e4->1e2, "
@@ -706,7 +711,7 @@ def run_schatten_outlier(args, ctx, dev, rank, peak):
     return {"workload": desc,
             "estimate": est, "std_err": se, "sum_sigma": exact, "trace_fp32_A": trace,
             "deviation_in_std_err": (est - exact) / se if se else None,
-            "ms_per_estimate": ms, "estimates_per_s": 1000.0 / ms,
+            "ms_per_estimate": ms, "estimates_per_s": 1000.0 / ms, "terms_16bit": args.hutchinson_terms,
             "tflops": 2.0 * n * n * 256 / 2 / (ms * 1e-3) / 1e12,
             "a_read_gbs": alg / (ms * 1e-3) / 1e9, "a_read_frac": alg / (ms * 1e-3) / 1e9 / peak}
 

@@ -408,7 +408,10 @@ MSP_API msp_status msp_solve_batched(msp_ctx* ctx, int count, const msp_instance
  * Hutchinson's estimator (1/m) sum_j g_j^T A g_j with m = `probes` Rademacher
  * probes (row i of probe j negative iff the top bit of
  * draw(seed, 7 + 2 (j / 256), i, j mod 256) is set). A: device FP32,
- * row-major n x n, lda >= n, symmetric; read once as packed upper tiles.
+ * row-major n x n, lda >= n, symmetric; each of its tiles on one side of
+ * the diagonal is read once per group of up to 256 probes (rows 16-byte
+ * aligned, i.e. lda % 4 == 0 and A 16-byte aligned: on the tensor cores,
+ * by TMA; otherwise packed first and on the FP32 pipe).
  * probes: a multiple of 64 in [64, 4096]. Outputs (host scalars, any may be
  * NULL): norm = the estimate of |A|_1, norm_pow = |A|_1^p (the same for
  * p = 1), std_err = sample standard deviation of the q_j / sqrt(m).
@@ -418,10 +421,25 @@ MSP_API msp_status msp_schatten(msp_ctx* ctx, const void* A, msp_dtype dtype, in
                                 double* norm, double* norm_pow, double* std_err);
 
 /* The per-probe quadratic forms q_j = g_j^T A g_j of msp_schatten (device
- * FP64 array of `probes`), each a sum over the packed tiles of 128-term FP32
- * tile products combined in FP64. */
+ * FP64 array of `probes`). Tensor-core path: every entry of A split into
+ * 16-bit terms (msp_set_hutchinson_terms), products with the +-1 probes
+ * accumulated in FP32 over a row block of 128 rows, then FP32 sums over 32
+ * rows and FP64 beyond. Other path: 128-term FP32 tile products combined
+ * in FP64. Returns after synchronising the stream (a device-side wait that
+ * gave up is reported as MSP_ETIMEOUT). */
 MSP_API msp_status msp_hutchinson(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n,
                                   int64_t lda, int64_t probes, uint64_t seed, double* q);
+
+/* 16-bit terms per FP32 entry of A in the tensor-core Hutchinson product of
+ * this context: 2 (default) = two FP16 terms of s a, s a power of two with
+ * s max_k a_kk <= 2^14, so that every |2 s a_ij| stays inside the FP16 range
+ * when A is PSD; hi + lo carry 22 significant bits (error <= 2^-22 |a|, or
+ * 2^-25 / s absolute for the smallest entries). A matrix with an entry
+ * beyond that range (not PSD) is detected and recomputed with 3 terms.
+ * 3 = three BF16 terms, which hold the whole FP32 significand (exact), at
+ * half again the tensor-core work and shared-memory traffic. MSP_EINVAL for
+ * other values. */
+MSP_API msp_status msp_set_hutchinson_terms(msp_ctx* ctx, int terms);
 
 /* ------------------------------------------ effective dimension d_lambda */
 

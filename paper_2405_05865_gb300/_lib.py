@@ -132,6 +132,7 @@ _SIGS = {
     "msp_schatten": (C.c_int, [P, P, C.c_int, I64, I64, C.c_double, I64, C.c_uint64,
                                C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "msp_hutchinson": (C.c_int, [P, P, C.c_int, I64, I64, I64, C.c_uint64, P]),
+    "msp_set_hutchinson_terms": (C.c_int, [P, C.c_int]),
     "msp_rbf_kernel": (C.c_int, [P, P, I64, C.c_int, C.c_double, P, I64]),
     "msp_rbf_grad_ell": (C.c_int, [P, P, I64, C.c_int, C.c_double, P, P, P]),
     "msp_rbf_grad_ell_static": (C.c_int, [P, I64, C.c_int, C.c_double, P, P, P, P]),

@@ -537,6 +537,10 @@ class Context:
         L.check(self.ptr, self.lib.msp_hutchinson(self.ptr, _ptr(A), dt, n, lda, probes, seed, _ptr(q)))
         return q
 
+    def set_hutchinson_terms(self, terms: int) -> None:
+        """BF16 terms per FP32 entry in the tensor-core Hutchinson product (2 or 3)."""
+        L.check(self.ptr, self.lib.msp_set_hutchinson_terms(self.ptr, int(terms)))
+
     # -- a11: RBF kernels and the adjoint of the length scale
     def rbf_kernel(self, points: torch.Tensor, ell: float) -> torch.Tensor:
         if not points.is_cuda or points.dtype != torch.float64 or points.dim() != 2:

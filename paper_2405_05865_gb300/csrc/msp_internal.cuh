@@ -43,6 +43,7 @@ struct msp_ctx {
     cudaStream_t fac_side[8] = {};
     cudaEvent_t fac_ev[8][2] = {};
     bool fac_overlap = true;     // false: the factor's products stay on the main stream
+    int hutch_terms = 2;         // tensor-core Hutchinson: 2 = two FP16 terms, 3 = three BF16 terms
     msp_ctx** lanes = nullptr;
     cudaStream_t* lane_streams = nullptr;
     int n_lanes = 0;

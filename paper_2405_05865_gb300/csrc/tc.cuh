@@ -10,13 +10,15 @@
 //
 // Layout of a K-major operand tile in shared memory (SWIZZLE_128B): rows of
 // 64 BF16 (128 bytes), 8-row groups of 1024 bytes, the 16-byte chunk c of
-// row r stored at chunk position c ^ (r mod 8). Tiles start on 1024-byte
-// boundaries, so the hardware's address-based swizzle equals this formula.
+// row r stored at chunk position c ^ (r mod 8) (SWIZZLE_64B: rows of 64
+// bytes, c ^ ((r >> 1) mod 4)). Tiles start on 1024-byte boundaries, so the
+// hardware's address-based swizzle equals these formulas.
 #pragma once
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "bulk.cuh"
 
@@ -59,11 +61,27 @@ __device__ inline uint64_t sdesc_kmajor_sw128(uint32_t saddr) {
     return d;
 }
 
+// The same for SWIZZLE_64B (rows of 32 BF16 = 64 bytes, 8-row groups of
+// 512 bytes; 16-byte chunk c of row r at chunk position c ^ ((r >> 1) & 3)).
+__device__ inline uint64_t sdesc_kmajor_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;                             // layout: SWIZZLE_64B
+    return d;
+}
+
 // Instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1),
 // A and B BF16 (bits 7-9 = 1, bits 10-12 = 1), both K-major (bits 15, 16 = 0),
 // N >> 3 in bits 17-22, M >> 4 in bits 24-28.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// The same with A and B FP16 (type fields 0).
+__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 // ------------------------------------------------------ tensor memory

@@ -92,3 +92,43 @@ def test_schatten1_outlier_spectrum_tensor_core_sizes(ctx):
     est, se = ctx.schatten(torch.from_numpy(A.astype(np.float32)).cuda(), p=1.0, probes=256)
     sd = np.sqrt(hutchinson.rademacher_variance(A) / 256)
     assert abs(est - reference.schatten(sig, 1.0)) <= 4 * sd
+
+
+def test_fp16_two_term_and_bf16_three_term_products(ctx):
+    # default: two FP16 terms of s a (22 significant bits); three BF16 terms
+    # hold the FP32 significand exactly; both against the FP64 oracle
+    n, m = 3000, 256
+    sig = outlier_spectrum(n, 40)
+    A = spectrum_matrix(sig, seed=17).astype(np.float32)
+    Ad = torch.from_numpy(A).cuda()
+    q2 = ctx.hutchinson(Ad, probes=m, seed=SEED).cpu().numpy()
+    ctx.set_hutchinson_terms(3)
+    try:
+        q3 = ctx.hutchinson(Ad, probes=m, seed=SEED).cpu().numpy()
+    finally:
+        ctx.set_hutchinson_terms(2)
+    qo = hutchinson.quadratic_forms(A.astype(np.float64), hutchinson.probes_fast(n, m, SEED))
+    s = np.abs(A.astype(np.float64)).sum()
+    # per entry |da| <= 2^-22 |a| + 2^-25 / s_scale, s_scale = 2^(14 - e) with 2^e > max a_kk
+    e = int(np.frexp(float(A.diagonal().max()))[1])
+    floor = 2.0 ** -25 / 2.0 ** (14 - e) * n * n
+    assert np.all(np.abs(q2 - qo) <= (2.0 ** -22 + 64 * 2.0 ** -24) * s + floor)
+    assert np.all(np.abs(q3 - qo) <= 64 * 2.0 ** -24 * s)
+    with pytest.raises(Exception):
+        ctx.set_hutchinson_terms(4)
+
+
+def test_fp16_range_fallback_for_matrices_beyond_the_diagonal_bound(ctx):
+    # symmetric, zero diagonal, large off-diagonal entries: |a_ij| > max a_kk,
+    # so the FP16 terms would overflow; the call must detect it and return
+    # the three-term BF16 result
+    n, m = 640, 64
+    rng = np.random.default_rng(5)
+    B = rng.standard_normal((n, n))
+    A = ((B + B.T) * 1e3).astype(np.float32)
+    np.fill_diagonal(A, 0.0)
+    A[0, 0] = 1e-3
+    q = ctx.hutchinson(torch.from_numpy(A).cuda(), probes=m, seed=SEED).cpu().numpy()
+    qo = hutchinson.quadratic_forms(A.astype(np.float64), hutchinson.probes_fast(n, m, SEED))
+    assert np.all(np.isfinite(q))
+    assert np.all(np.abs(q - qo) <= 64 * 2.0 ** -24 * np.abs(A.astype(np.float64)).sum())
