@@ -570,6 +570,46 @@ def run_batched(args, ctx, dev, rank, peak):
                                 "unconverged instance per pass; device-timer split of the one launch"}}
 
 
+def rho_bf16(ctx, A_hi, lam, solve, iters=10, seed=0):
+    """Refinement whose correction solves apply the BF16 rounding A~ of A
+    (A_hi: the FP32 or FP64 matrix on the device) contracts by the spectral
+    radius of (A~ + lam I)^{-1} E, E = A~ - A. T = (A + lam I)^{-1} E is
+    similar to a symmetric matrix, so its eigenvalues mu are real, and those
+    of the refinement matrix are mu / (1 + mu); A~ + lam I is indefinite when
+    some mu <= -1. Estimates by power iteration (products with FP64
+    accumulation, the inverse by `solve`): rho' = max |mu| from T^2, then
+    mu_max and mu_min from T + rho' I and rho' I - T."""
+    import torch
+    Ab = A_hi.to(torch.bfloat16)
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    v0 = torch.randn(A_hi.shape[0], generator=g, dtype=torch.float64).to(A_hi.device)
+    v0 /= torch.linalg.vector_norm(v0)
+
+    def T(v):
+        return solve(ctx.matvec_f64(Ab, v) - ctx.matvec_f64(A_hi, v))
+
+    def power(op, k):
+        v, nz = v0.clone(), 0.0
+        for _ in range(k):
+            z = op(v)
+            nz = float(torch.linalg.vector_norm(z))
+            if not (nz > 0.0):
+                return 0.0
+            v = z / nz
+        return nz
+
+    rho_p = power(lambda v: T(T(v)), iters) ** 0.5
+    mu_max = power(lambda v: T(v) + rho_p * v, iters) - rho_p
+    mu_min = rho_p - power(lambda v: rho_p * v - T(v), iters)
+    del Ab
+    indefinite = mu_min <= -1.0
+    rho = float("inf") if indefinite else max(abs(mu_max) / (1.0 + mu_max), abs(mu_min) / (1.0 + mu_min))
+    return {"rho_prime": rho_p, "mu_max": mu_max, "mu_min": mu_min, "rho_bf16": rho,
+            "A_bf16_plus_lam_I": "indefinite" if indefinite else "positive definite (estimate)",
+            "bf16_refinement": "diverges" if rho >= 1.0 else "contracts",
+            "power_iterations": iters}
+
+
 def run_refined(args, ctx, dev, rank, peak):
     """The mixed-precision workload: A = Q diag(sigma) Q^T, Q = H_1 ... H_64
     (seeded Householder reflectors), n = 32768, 1024 outliers log-spaced
@@ -657,6 +697,14 @@ def run_refined(args, ctx, dev, rank, peak):
                              "rel_resid_fp32_A": i32["rel_resid"], "status": i32["status"],
                              "level1_iters": i32["outer_iters"], "ms": sum(i32["phase_ms"].values())}
         out["modes"] = res
+        # BF16 storage of A as the operator of the correction solves
+        sk = ctx.sketch(A32, s, 8, SEED)
+        f = ctx.nystrom(sk, lam, lam0, phi=0)
+        out["rho_bf16"] = rho_bf16(ctx, A64, lam, lambda y: ctx.solve_refined(
+            f, A32, A64, y, lam, precision="mixed", tol=1e-6, refine_tol=1e-3, max_inner=0,
+            raise_on_noconv=False)[0])
+        f.close()
+        sk.close()
     except Exception as e:   # report, keep the rest of the bench
         out["error"] = f"{type(e).__name__}: {e}"
     del A64, A32
@@ -770,9 +818,9 @@ def run_msp(args, rank, world, local):
     ctx = Context(local)
     stream = ctx.stream
 
-    def step(prec="mixed", tol=1e-10, profile=0, criterion="backward", refine_tol=None):
+    def step(prec="mixed", tol=1e-10, profile=0, criterion="backward", refine_tol=None, data="fp32"):
         sk = ctx.sketch(A, s, 8, SEED)
-        f = ctx.nystrom(sk, lam, 0.0, phi=phi, gamma_phi=8, seed=SEED)
+        f = ctx.nystrom(sk, lam, 0.0, phi=phi, gamma_phi=8, seed=SEED, data=data)
         rt = args.refine_tol if refine_tol is None else refine_tol
         x, info = ctx.solve(f, A, bd, lam, precision=prec, tol=tol, inner_tol=args.inner_tol,
                             refine_tol=rt, max_inner=args.max_inner, profile=profile,
@@ -821,6 +869,60 @@ def run_msp(args, rank, world, local):
     strict = {"value": job_rate(args.steps, world, ms_r / 1000.0), "unit": "solves/s", "ms_per_step": ms_r / args.steps,
               "rel_resid_max": max(i["rel_resid"] for i in inf_r),
               "outer_iters": inf_r[-1]["outer_iters"], "refine_steps": inf_r[-1]["refine_steps"]}
+
+    # the same solve with the level-2 data C and W stored in BF16 (C rounded
+    # first, W and M2 from the rounded C); A stays FP32 with FP64 refinement
+    step(data="bf16")
+    ms_b, inf_b, _ = timed(args.steps, data="bf16", profile=1)
+    lb = inf_b[-1]
+    bf16_data = {"value": job_rate(args.steps, world, ms_b / 1000.0), "unit": "solves/s",
+                 "ms_per_step": ms_b / args.steps,
+                 "backward_err_max": max(i["backward_err"] for i in inf_b),
+                 "all_converged": all(i["status"] == 0 and i["backward_err"] <= 1e-10 for i in inf_b),
+                 "outer_iters": lb["outer_iters"], "refine_steps": lb["refine_steps"],
+                 "level2_us_per_launch": 1e3 * lb["level2_ms"] / max(1, lb["level2_launches"]),
+                 "level2_us_per_launch_fp32_data": 1e3 * infos[-1]["level2_ms"] / max(1, infos[-1]["level2_launches"]),
+                 "note": "FP32 A (packed tiles), BF16 C and W, FP32 L^-1, FP64 refinement, backward error 1e-10"}
+
+    # the sketch pass reading A stored in BF16 (C in FP32), against the FP32 read
+    sk_times = {}
+    Ab16 = A.to(torch.bfloat16)
+    for name, AA in (("fp32_A_with_packing", A), ("bf16_A", Ab16)):
+        for k in range(4):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            skx = ctx.sketch(AA, s, 8, SEED)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            skx.close()
+            if k > 0:
+                sk_times.setdefault(name, []).append(e0.elapsed_time(e1))
+    sketch_pass = {k: statistics.median(v) for k, v in sk_times.items()}
+    sketch_pass["note"] = ("msp_sketch: pattern, CSR, C = A Pi; the FP32 case also packs the upper tiles and "
+                           "takes the norm-bound statistics the solve reuses")
+
+    # BF16 storage of A as the operator of refinement's correction solves
+    rho = {}
+    skr = ctx.sketch(A, s, 8, SEED)
+    fr = ctx.nystrom(skr, lam, 0.0, phi=0)
+    rho["rbf_n16384"] = rho_bf16(ctx, A, lam, lambda y: ctx.solve(fr, A, y, lam, precision="mixed", tol=1e-6,
+                                                                  refine_tol=1e-3, max_inner=0,
+                                                                  raise_on_noconv=False)[0])
+    fr.close()
+    skr.close()
+    del Ab16
+    from workloads import make_workload as _mk
+    w0 = _mk("outlier", seed=0)
+    A0 = torch.from_numpy(w0.A).to(dev)
+    lam00 = 2.0 / 32 * float(np.sort(w0.sigma)[::-1][32:].sum())
+    sk0 = ctx.sketch(A0, w0.s, 8, SEED)
+    f0 = ctx.nystrom(sk0, w0.lam, lam00, phi=4 * w0.s)
+    rho["outlier_n1024"] = rho_bf16(ctx, A0, w0.lam, lambda y: ctx.solve(f0, A0, y, w0.lam, precision="fp64",
+                                                                         tol=1e-8, inner_tol=1e-10,
+                                                                         raise_on_noconv=False)[0])
+    f0.close()
+    sk0.close()
 
     # plain FP32 (no refinement) to 1e-5 relative residual
     fp32 = None
@@ -1022,6 +1124,9 @@ def run_msp(args, rank, world, local):
                         "outer_iters": last["outer_iters"], "inner_iters": last["inner_iters"],
                         "refine_steps": last["refine_steps"]},
            "rel_resid_1e-10": strict,
+           "mixed_bf16_preconditioner_data": bf16_data,
+           "sketch_pass_ms": sketch_pass,
+           "rho_bf16": rho,
            "fp32_plain": fp32,
            "schatten1": sch,
            "sketched_level2": sk_l2,

@@ -47,7 +47,10 @@ extern "C" {
 
 typedef enum {
     MSP_F64 = 0,   /* IEEE binary64 */
-    MSP_F32 = 1    /* IEEE binary32 */
+    MSP_F32 = 1,   /* IEEE binary32 */
+    MSP_BF16 = 2   /* bfloat16 (8-bit significand, binary32 range); storage
+                      of preconditioner data (msp_nystrom_ex) and of A for
+                      msp_sketch / msp_matvec_f64 */
 } msp_dtype;
 
 typedef enum {
@@ -227,6 +230,20 @@ MSP_API msp_status msp_sketch_get_C(msp_ctx* ctx, const msp_sketch_t* sk, void* 
 MSP_API msp_status msp_nystrom(msp_ctx* ctx, const msp_sketch_t* sk, double lambda,
                        double lambda0, int64_t phi, int gamma_phi, uint64_t seed,
                        msp_factor_t** out);
+/* msp_nystrom with the storage of the level-2 data chosen (Algorithm 1 steps
+ * 3-4 and Algorithm 2 with reduced-precision preconditioner data; the paper
+ * works in exact arithmetic, Section 2). data = MSP_F32 is msp_nystrom.
+ * data = MSP_BF16 (FP32 sketch only): C is rounded to BF16 first, and W,
+ * C~ and M2 are formed from the rounded C (FP32 and FP64 accumulation), so
+ * that M = Cb W^{-1} Cb^T + lambda~ I is exactly the SPD preconditioner the
+ * level-2 iteration applies; the level-2 kernel then streams Cb and Wb (BF16,
+ * half the bytes of C) with FP32 accumulation, and L^{-1} stays FP32. The
+ * outer level-1 iteration still applies the FP32 A, so the refined solution
+ * is unchanged in accuracy; only the preconditioner (and so the iteration
+ * count) differs. MSP_EINVAL for other data types. */
+MSP_API msp_status msp_nystrom_ex(msp_ctx* ctx, const msp_sketch_t* sk, double lambda, double lambda0,
+                                  int64_t phi, int gamma_phi, uint64_t seed, msp_dtype data,
+                                  msp_factor_t** out);
 MSP_API void msp_factor_destroy(msp_factor_t* f);
 /* Copies of the factor's pieces into caller device buffers (FP64, row-major,
  * leading dimension s): W, M2 (before the shift), L^{-1} (lower triangle).

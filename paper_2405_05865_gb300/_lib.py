@@ -15,7 +15,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "lib", "libmsp.so")
 HEADER = os.path.join(os.path.dirname(_PKG), "include", "msp.h")
 
-MSP_F64, MSP_F32 = 0, 1
+MSP_F64, MSP_F32, MSP_BF16 = 0, 1, 2
 MSP_PREC_FP64, MSP_PREC_FP32, MSP_PREC_MIXED = 0, 1, 2
 MSP_STOP_RESIDUAL, MSP_STOP_BACKWARD = 0, 1
 STATUS = {0: "MSP_OK", 1: "MSP_EINVAL", 2: "MSP_ENOMEM", 3: "MSP_ECUDA", 4: "MSP_ENOTPD",
@@ -81,6 +81,8 @@ _SIGS = {
     "msp_sketch_get_C": (C.c_int, [P, P, P, I64]),
     "msp_nystrom": (C.c_int, [P, P, C.c_double, C.c_double, I64, C.c_int, C.c_uint64,
                               C.POINTER(P)]),
+    "msp_nystrom_ex": (C.c_int, [P, P, C.c_double, C.c_double, I64, C.c_int, C.c_uint64, C.c_int,
+                                 C.POINTER(P)]),
     "msp_factor_destroy": (None, [P]),
     "msp_factor_get": (C.c_int, [P, P, P, P, P, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                  C.POINTER(C.c_int)]),

@@ -17,7 +17,7 @@ from . import _lib as L
 
 DEFAULT_SEED = 0x4D5350      # "MSP"
 
-_DT = {torch.float32: L.MSP_F32, torch.float64: L.MSP_F64}
+_DT = {torch.float32: L.MSP_F32, torch.float64: L.MSP_F64, torch.bfloat16: L.MSP_BF16}
 _PREC = {"fp64": L.MSP_PREC_FP64, "fp32": L.MSP_PREC_FP32, "mixed": L.MSP_PREC_MIXED}
 _STOP = {"residual": L.MSP_STOP_RESIDUAL, "backward": L.MSP_STOP_BACKWARD}
 
@@ -46,7 +46,7 @@ def _check_matrix(A: torch.Tensor, need_cuda: bool = True) -> tuple[int, int, in
     if A.dim() != 2 or A.shape[0] != A.shape[1]:
         raise ValueError("A must be a square 2-D tensor")
     if A.dtype not in _DT:
-        raise TypeError("A must be float32 or float64")
+        raise TypeError("A must be float32, float64 or bfloat16")
     if need_cuda and not A.is_cuda:
         raise ValueError("A must be a CUDA tensor")
     if A.stride(1) != 1:
@@ -323,16 +323,20 @@ class Context:
         n, lda, dt = _check_matrix(A)
         h = C.c_void_p()
         L.check(self.ptr, self.lib.msp_sketch(self.ptr, _ptr(A), dt, n, lda, s, gamma, seed, C.byref(h)))
-        return Sketch(self, h, n, s, A.dtype)
+        # a BF16 A is read in BF16; C and what follows are FP32
+        return Sketch(self, h, n, s, torch.float32 if A.dtype == torch.bfloat16 else A.dtype)
 
     # -- a3-a5
     def nystrom(self, sk: Sketch, lam: float, lam0: float = 0.0, phi: int | None = None,
-                gamma_phi: int = 8, seed: int = DEFAULT_SEED) -> Factor:
+                gamma_phi: int = 8, seed: int = DEFAULT_SEED, data: str = "fp32") -> Factor:
+        """Algorithm 1 steps 3-4; data = "bf16" stores the level-2 data C and W
+        in BF16 (msp_nystrom_ex)."""
         if phi is None:
             phi = 4 * sk.s
         h = C.c_void_p()
-        L.check(self.ptr, self.lib.msp_nystrom(self.ptr, sk.handle, lam, lam0, phi, gamma_phi, seed,
-                                               C.byref(h)))
+        dt = {"fp32": L.MSP_F32, "bf16": L.MSP_BF16}[data]
+        L.check(self.ptr, self.lib.msp_nystrom_ex(self.ptr, sk.handle, lam, lam0, phi, gamma_phi, seed, dt,
+                                                  C.byref(h)))
         return Factor(self, h, sk)
 
     def solve_m1(self, f: Factor, r: torch.Tensor, **opts) -> tuple[torch.Tensor, int]:

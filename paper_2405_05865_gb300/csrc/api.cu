@@ -2,6 +2,8 @@
 // staging of host buffers and the FP64 refinement driver.
 #include "msp_internal.cuh"
 
+#include <cuda_bf16.h>
+
 #include <vector>
 
 #include <algorithm>
@@ -209,8 +211,16 @@ static msp_status sketch_solve_prep(msp_ctx* ctx, msp_sketch_s* sk, const void* 
 msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n,
                            int64_t lda, int64_t s, int gamma, uint64_t seed, bool pack,
                            msp_sketch_t** out, const void* host_chunks) {
-    if (dtype != MSP_F32 && dtype != MSP_F64)
-        return msp_set_error(ctx, MSP_EINVAL, "sketch: dtype must be MSP_F32 or MSP_F64");
+    if (dtype != MSP_F32 && dtype != MSP_F64 && dtype != MSP_BF16)
+        return msp_set_error(ctx, MSP_EINVAL, "sketch: dtype must be MSP_F32, MSP_F64 or MSP_BF16");
+    // BF16 A: read in BF16, C and everything after it in FP32; no packed copy
+    // and no norm statistics (a solve applies an FP32 A of its own)
+    const msp_dtype a_dt = dtype;
+    if (dtype == MSP_BF16) {
+        if (host_chunks) return msp_set_error(ctx, MSP_EINVAL, "sketch: a BF16 A must be in device memory");
+        dtype = MSP_F32;
+        pack = false;
+    }
     const int64_t s_max = dtype == MSP_F32 ? MSP_MAX_S_SINGLE : MSP_MAX_S;
     if (n < 1 || lda < n || s < 16 || s > s_max || s > n || gamma < 1 ||
         gamma > MSP_MAX_GAMMA || gamma > s || n >= (1ll << 30))
@@ -310,7 +320,7 @@ msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t
             msp_sketch_destroy(sk);
             return st;
         }
-    } else if ((st = msp_sketch_apply(ctx, A, dtype, n, lda, sp, sk->csr_ptr, sk->csr_ent, gamma, sk->C)) !=
+    } else if ((st = msp_sketch_apply(ctx, A, a_dt, n, lda, sp, sk->csr_ptr, sk->csr_ent, gamma, sk->C)) !=
                MSP_OK) {
         cudaStreamSynchronize(ctx->stream);
         msp_sketch_destroy(sk);
@@ -361,17 +371,35 @@ msp_status msp_sketch_get_C(msp_ctx* ctx, const msp_sketch_t* sk, void* C, int64
 
 void msp_factor_destroy(msp_factor_t* f) {
     if (!f) return;
-    for (void* p : {f->W, f->B, f->Bt, (void*)f->W64, (void*)f->M2, (void*)f->Linv64})
+    for (void* p : {f->W, f->B, f->Bt, (void*)f->W64, (void*)f->M2, (void*)f->Linv64, f->Cb, f->Wb})
         if (p) cudaFreeAsync(p, f->stream);
     delete f;
 }
 
 }  // extern "C"
 
+namespace {
+
+// Cb = bf16(C) (round to nearest even) and Cr = float(Cb), n x s_pad.
+__global__ void k_round_bf16(const float* __restrict__ C, int64_t len, __nv_bfloat16* __restrict__ Cb,
+                             float* __restrict__ Cr) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= len) return;
+    const __nv_bfloat16 v = __float2bfloat16_rn(C[e]);
+    if (Cb) Cb[e] = v;
+    if (Cr) Cr[e] = __bfloat162float(v);
+}
+
+}  // namespace
+
 msp_status msp_nystrom_impl(msp_ctx* ctx, const msp_sketch_s* sk, double lambda, double lambda0,
-                            int64_t phi, int gamma_phi, uint64_t seed, msp_factor_t** out) {
+                            int64_t phi, int gamma_phi, uint64_t seed, msp_factor_t** out, msp_dtype data) {
     if (!(lambda > 0.0) || !(lambda0 >= 0.0) || !std::isfinite(lambda) || !std::isfinite(lambda0))
         return msp_set_error(ctx, MSP_EINVAL, "nystrom: need lambda > 0 and lambda0 >= 0");
+    if (data != MSP_F32 && !(data == MSP_BF16 && sk->dtype == MSP_F32))
+        return msp_set_error(ctx, MSP_EINVAL, "nystrom: preconditioner data must be MSP_F32, or MSP_BF16 for an "
+                                              "FP32 sketch");
+    if (sk->dtype == MSP_F64) data = MSP_F32;
     if (phi < 0 || (phi > 0 && (gamma_phi < 1 || gamma_phi > MSP_MAX_GAMMA || gamma_phi > phi ||
                                 phi >= (1ll << 30))))
         return msp_set_error(ctx, MSP_EINVAL, "nystrom: need phi >= 0 and 1 <= gamma_phi <= min(phi, %d)",
@@ -383,15 +411,30 @@ msp_status msp_nystrom_impl(msp_ctx* ctx, const msp_sketch_s* sk, double lambda,
     f->sk = sk; f->s = sk->s; f->s_pad = sp; f->phi = phi; f->dtype = sk->dtype;
     f->stream = ctx->stream;
     f->lambda = lambda; f->lambda0 = lambda0; f->lam_tilde = lambda + lambda0;
+    f->data = (sk->dtype == MSP_F32) ? data : MSP_F32;
     const size_t mat_t = (size_t)sp * sp * ts, mat_d = (size_t)sp * sp * 8;
     msp_status st = MSP_OK;
     void* phi_mem = nullptr;
+    float* Cr = nullptr;         // BF16 data: float(bf16(C)), the C every later step uses
     auto fail = [&](msp_status s2) {
         cudaStreamSynchronize(ctx->stream);
         if (phi_mem) free_on(ctx, phi_mem);
+        if (Cr) free_on(ctx, Cr);
         msp_factor_destroy(f);
         return s2;
     };
+    const void* Csrc = sk->C;
+    if (f->data == MSP_BF16) {
+        const int64_t len = n * sp;
+        if ((st = msp_alloc(ctx, &f->Cb, (size_t)len * 2)) != MSP_OK ||
+            (st = msp_alloc(ctx, &f->Wb, (size_t)sp * sp * 2)) != MSP_OK ||
+            (st = msp_alloc(ctx, (void**)&Cr, (size_t)len * 4)) != MSP_OK)
+            return fail(st);
+        k_round_bf16<<<(unsigned)((len + 255) / 256), 256, 0, ctx->stream>>>((const float*)sk->C, len,
+                                                                            (__nv_bfloat16*)f->Cb, Cr);
+        MSP_CHECK_LAUNCH(ctx);
+        Csrc = Cr;
+    }
     if ((st = msp_alloc(ctx, &f->W, mat_t)) != MSP_OK || (st = msp_alloc(ctx, &f->B, mat_t)) != MSP_OK ||
         (st = msp_alloc(ctx, &f->Bt, mat_t)) != MSP_OK ||
         (st = msp_alloc(ctx, (void**)&f->W64, mat_d)) != MSP_OK ||
@@ -400,10 +443,10 @@ msp_status msp_nystrom_impl(msp_ctx* ctx, const msp_sketch_s* sk, double lambda,
         return fail(st);
     // W = S C = Pi^T C: row c of W gathers the rows j of C listed for column c
     const double sc = 1.0 / std::sqrt((double)sk->gamma);
-    if ((st = msp_gather_rows(ctx, sk->dtype, sp, sp, sk->csr_ptr, sk->csr_ent, sk->C, sp, sc, f->W,
+    if ((st = msp_gather_rows(ctx, sk->dtype, sp, sp, sk->csr_ptr, sk->csr_ent, Csrc, sp, sc, f->W,
                               sp)) != MSP_OK)
         return fail(st);
-    const void* Ct = sk->C;
+    const void* Ct = Csrc;
     int64_t phi_rows = n;
     if (phi > 0) {
         // Phi: phi x n sparse embedding (stream 2); C~ = Phi C
@@ -422,14 +465,21 @@ msp_status msp_nystrom_impl(msp_ctx* ctx, const msp_sketch_s* sk, double lambda,
         void* ct = c;
         if ((st = msp_pattern_launch(ctx, n, phi, gamma_phi, seed, 2, pidx, psgn, nullptr)) != MSP_OK ||
             (st = msp_build_csr(ctx, n, phi, gamma_phi, pidx, psgn, pptr, pent)) != MSP_OK ||
-            (st = msp_gather_rows(ctx, sk->dtype, phi, sp, pptr, pent, sk->C, sp,
+            (st = msp_gather_rows(ctx, sk->dtype, phi, sp, pptr, pent, Csrc, sp,
                                   1.0 / std::sqrt((double)gamma_phi), ct, sp)) != MSP_OK)
             return fail(st);
         Ct = ct;
         phi_rows = phi;
     }
     if ((st = msp_build_factor(ctx, f, Ct, phi_rows)) != MSP_OK) return fail(st);
+    if (f->data == MSP_BF16) {
+        // Wb = bf16 of the symmetrised W (for the iterative level 2)
+        k_round_bf16<<<(unsigned)((sp * sp + 255) / 256), 256, 0, ctx->stream>>>((const float*)f->W, sp * sp,
+                                                                                (__nv_bfloat16*)f->Wb, nullptr);
+        MSP_CHECK_LAUNCH(ctx);
+    }
     if (phi_mem) free_on(ctx, phi_mem);
+    if (Cr) free_on(ctx, Cr);
     *out = f;
     return MSP_OK;
 }
@@ -443,6 +493,15 @@ msp_status msp_nystrom(msp_ctx* ctx, const msp_sketch_t* sk, double lambda, doub
     DeviceGuard g(ctx->device);
     *out = nullptr;
     return msp_nystrom_impl(ctx, sk, lambda, lambda0, phi, gamma_phi, seed, out);
+}
+
+msp_status msp_nystrom_ex(msp_ctx* ctx, const msp_sketch_t* sk, double lambda, double lambda0, int64_t phi,
+                          int gamma_phi, uint64_t seed, msp_dtype data, msp_factor_t** out) {
+    if (!ctx) return msp_set_error(nullptr, MSP_EINVAL, "ctx is NULL");
+    if (!sk || !out) return msp_set_error(ctx, MSP_EINVAL, "nystrom: NULL argument");
+    DeviceGuard g(ctx->device);
+    *out = nullptr;
+    return msp_nystrom_impl(ctx, sk, lambda, lambda0, phi, gamma_phi, seed, out, data);
 }
 
 msp_status msp_factor_get(msp_ctx* ctx, const msp_factor_t* f, double* W, double* M2, double* Linv,

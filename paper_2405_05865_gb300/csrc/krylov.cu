@@ -15,6 +15,8 @@
 // grid barriers always matches. Reductions use fixed orders (deterministic).
 #include "msp_internal.cuh"
 
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cmath>
 
@@ -35,6 +37,23 @@ __device__ inline void load16(const T* p, T* out) {
     if constexpr (Vec16<T>::W == 4) { out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w; }
     else { out[0] = v.x; out[1] = v.y; }
 }
+
+// One vector load of a row slice: 16 bytes of FP32 / FP64, or 8 bytes of
+// BF16 (4 values, widened to FP32 exactly), so that every storage type puts
+// the same 4 (FP64: 2) consecutive values in each lane step.
+template <typename T>
+__device__ inline void load_vec(const T* p, T* out) { load16(p, out); }
+__device__ inline void load_vec(const __nv_bfloat16* p, float* out) {
+    const uint2 v = *reinterpret_cast<const uint2*>(p);
+    out[0] = __uint_as_float(v.x << 16);
+    out[1] = __uint_as_float(v.x & 0xFFFF0000u);
+    out[2] = __uint_as_float(v.y << 16);
+    out[3] = __uint_as_float(v.y & 0xFFFF0000u);
+}
+
+// Values per vector load of a storage type.
+template <typename TS> struct StoreW { static constexpr int W = 16 / (int)sizeof(TS); };
+template <> struct StoreW<__nv_bfloat16> { static constexpr int W = 4; };
 
 // Streaming (evict-first) 16-byte load: A is read once per pass, so it should
 // not displace the sketch C, which the level-2 iteration re-reads from L2.
@@ -189,6 +208,11 @@ __device__ inline double widen_f32(float f) {
     return __longlong_as_double((long long)bits);
 }
 
+// A entry widened to FP64 (exact for every storage type).
+__device__ inline double wide64(double v) { return v; }
+__device__ inline double wide64(float v) { return (double)v; }
+__device__ inline double wide64(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+
 // out = b - (A + lam I) x  (or (A + lam I) x if b == nullptr), FP64
 // accumulation; |out|^2 into *norm2 (last block, fixed order). The FP64 FMA
 // rate bounds this kernel on this part (two FMAs per clock per SM): loads are
@@ -235,7 +259,7 @@ __global__ void __launch_bounds__(256) k_matvec64(const TA* __restrict__ A, int6
                 acc0 = fma(widen_f32(a0.w), x[j + 3], acc0);
             }
         } else {
-            for (int64_t j = lane; j < n; j += 32) acc0 = fma((double)__ldcs(&row[j]), x[j], acc0);
+            for (int64_t j = lane; j < n; j += 32) acc0 = fma(wide64(__ldcs(&row[j])), x[j], acc0);
         }
         double acc = msp::warp_sum(acc0 + acc1);
         if (lane == 0) {
@@ -264,12 +288,13 @@ __global__ void __launch_bounds__(256) k_matvec64(const TA* __restrict__ A, int6
 
 // ---------------------------------------------------------- level 2
 
-template <typename T>
+// TC: storage type of C and W (T, or BF16 preconditioner data with T = float)
+template <typename T, typename TC = T>
 struct L2Args {
     int64_t n, s_pad;
     int mode;
-    const T* C;
-    const T* W;
+    const TC* C;
+    const TC* W;
     const T* B;
     const T* Bt;
     T lam_t;
@@ -295,16 +320,17 @@ struct L2Args {
     double* dpart;          // G x 4
 };
 
-// Per-lane slice of an s_pad row: PL elements as PL/W vectors of W elements,
-// element index of vector v, component e: v*32*W + lane*W + e.
-template <typename T, int PL>
+// Per-lane slice of an s_pad row stored as TS: PL elements as PL/W vectors of
+// W elements (one vector load each), element index of vector v, component
+// e: v*32*W + lane*W + e; values held as T.
+template <typename T, int PL, typename TS = T>
 struct RowSlice {
-    static constexpr int W = Vec16<T>::W;
+    static constexpr int W = StoreW<TS>::W;
     static constexpr int NVEC = PL / W;
     T v[PL];
-    __device__ inline void load(const T* row, int lane) {
+    __device__ inline void load(const TS* row, int lane) {
 #pragma unroll
-        for (int k = 0; k < NVEC; ++k) load16(row + k * 32 * W + lane * W, v + k * W);
+        for (int k = 0; k < NVEC; ++k) load_vec(row + k * 32 * W + lane * W, v + k * W);
     }
     __device__ inline T dot_smem(const T* s, int lane) const {
         T a = T(0);
@@ -316,9 +342,9 @@ struct RowSlice {
     }
 };
 
-template <typename T, int PL>
+template <typename T, int PL, typename TS = T>
 __device__ inline void store_slice(T* dst, const T* src, int lane) {
-    constexpr int W = Vec16<T>::W;
+    constexpr int W = StoreW<TS>::W;
 #pragma unroll
     for (int k = 0; k < PL / W; ++k)
 #pragma unroll
@@ -332,8 +358,8 @@ __device__ inline void store_slice(T* dst, const T* src, int lane) {
 // Per-warp accumulators are combined through shared memory into part[b].
 constexpr int kRowChunk = 256;   // rows of C staged per round (r, z, w in shared memory)
 
-template <typename T, int PL>
-__device__ inline void row_one(const L2Args<T>& a, int kind, int64_t il, const RowSlice<T, PL>& c,
+template <typename T, typename TC, int PL>
+__device__ inline void row_one(const L2Args<T, TC>& a, int kind, int64_t il, const RowSlice<T, PL, TC>& c,
                                const T* svec, T* acc, const T* sr, T* sw, int lane) {
     T coef;
     if (kind == 0) {
@@ -358,8 +384,8 @@ __device__ inline void row_one(const L2Args<T>& a, int kind, int64_t il, const R
 //   kind 1: acc += (c_i . d) c_i               (u = C^T C d)
 //   kind 2: w_i = (r_i - c_i . y) / lam~ into z; per-thread dots r.w, r.z_old
 // Per-warp accumulators are combined through shared memory into part[b].
-template <typename T, int PL>
-__device__ void row_pass(const L2Args<T>& a, int kind, int64_t row0, int64_t row1, const T* svec,
+template <typename T, typename TC, int PL>
+__device__ void row_pass(const L2Args<T, TC>& a, int kind, int64_t row0, int64_t row1, const T* svec,
                          T* swarp, T* srow, double* rw, double* rzo) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     T* sr = srow;                 // kRowChunk
@@ -377,16 +403,16 @@ __device__ void row_pass(const L2Args<T>& a, int kind, int64_t row0, int64_t row
         }
         int il = w;
         for (; il + kNW < nr; il += 2 * kNW) {
-            RowSlice<T, PL> c0, c1;
+            RowSlice<T, PL, TC> c0, c1;
             c0.load(a.C + (base + il) * a.s_pad, lane);
             c1.load(a.C + (base + il + kNW) * a.s_pad, lane);
-            row_one<T, PL>(a, kind, il, c0, svec, acc, sr, sw, lane);
-            row_one<T, PL>(a, kind, il + kNW, c1, svec, acc, sr, sw, lane);
+            row_one<T, TC, PL>(a, kind, il, c0, svec, acc, sr, sw, lane);
+            row_one<T, TC, PL>(a, kind, il + kNW, c1, svec, acc, sr, sw, lane);
         }
         if (il < nr) {
-            RowSlice<T, PL> c0;
+            RowSlice<T, PL, TC> c0;
             c0.load(a.C + (base + il) * a.s_pad, lane);
-            row_one<T, PL>(a, kind, il, c0, svec, acc, sr, sw, lane);
+            row_one<T, TC, PL>(a, kind, il, c0, svec, acc, sr, sw, lane);
         }
         if (kind != 1) __syncthreads();
         if (kind == 2) {
@@ -405,12 +431,12 @@ __device__ void row_pass(const L2Args<T>& a, int kind, int64_t row0, int64_t row
         *rzo = d_rzo;
         return;
     }
-    store_slice<T, PL>(swarp + (int64_t)w * a.s_pad, acc, lane);
+    store_slice<T, PL, TC>(swarp + (int64_t)w * a.s_pad, acc, lane);
 }
 
 // part[b][c] = sum over warps of swarp[w][c]
-template <typename T>
-__device__ inline void combine_warps(const L2Args<T>& a, const T* swarp, int b) {
+template <typename T, typename TC>
+__device__ inline void combine_warps(const L2Args<T, TC>& a, const T* swarp, int b) {
     __syncthreads();
     for (int64_t c = threadIdx.x; c < a.s_pad; c += blockDim.x) {
         T v = T(0);
@@ -421,12 +447,12 @@ __device__ inline void combine_warps(const L2Args<T>& a, const T* swarp, int b) 
 }
 
 // out[c] = M[c,:] . svec for c in [c0, c1) (warp per row)
-template <typename T, int PL>
-__device__ inline void rows_dot(const T* M, int64_t s_pad, int64_t c0, int64_t c1, const T* svec,
+template <typename T, int PL, typename TS = T>
+__device__ inline void rows_dot(const TS* M, int64_t s_pad, int64_t c0, int64_t c1, const T* svec,
                                 T* out) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int64_t c = c0 + w; c < c1; c += kNW) {
-        RowSlice<T, PL> m;
+        RowSlice<T, PL, TS> m;
         m.load(M + c * s_pad, lane);
         T t = msp::warp_sum(m.dot_smem(svec, lane));
         if (lane == 0) out[c] = t;
@@ -483,8 +509,8 @@ __device__ inline void load_full(const T* g, T* s, int64_t m) {
     for (int64_t c = threadIdx.x; c < m; c += blockDim.x) s[c] = __ldcg(&g[c]);
 }
 
-template <typename T, int PL>
-__global__ void __launch_bounds__(kThreads, 1) k_level2(L2Args<T> a) {
+template <typename T, typename TC, int PL>
+__global__ void __launch_bounds__(kThreads, 1) k_level2(L2Args<T, TC> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t sp = a.s_pad;
     T* sd = reinterpret_cast<T*>(smem_raw);       // d (search direction)
@@ -586,7 +612,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_level2(L2Args<T> a) {
         if (threadIdx.x == 0) a.dpart[b * 4 + 0] = rr;
     }
     __syncthreads();
-    row_pass<T, PL>(a, 0, row0, row1, nullptr, swarp, srow, nullptr, nullptr);
+    row_pass<T, TC, PL>(a, 0, row0, row1, nullptr, swarp, srow, nullptr, nullptr);
     combine_warps(a, swarp, b);
     if (!msp::grid_barrier(bc, bg, err)) return;
 
@@ -657,9 +683,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_level2(L2Args<T> a) {
     }
     while (k < a.max_inner && rres > tin2) {
         // P1: partial u = C^T (C d) over this block's rows; wd = W d (columns)
-        row_pass<T, PL>(a, 1, row0, row1, sd, swarp, srow, nullptr, nullptr);
+        row_pass<T, TC, PL>(a, 1, row0, row1, sd, swarp, srow, nullptr, nullptr);
         combine_warps(a, swarp, b);
-        rows_dot<T, PL>(a.W, sp, c0, c1, sd, a.wdvec);
+        rows_dot<T, PL, TC>(a.W, sp, c0, c1, sd, a.wdvec);
         if (!msp::grid_barrier(bc, bg, err)) return;
         // P2: u over this block's columns; d.u partial
         double du = 0.0;
@@ -693,7 +719,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_level2(L2Args<T> a) {
     // ---- w = (r - C y) / lam~ into z; dots for the level-1 beta
     __syncthreads();
     double rw = 0.0, rzo = 0.0;
-    row_pass<T, PL>(a, 2, row0, row1, sy, swarp, srow, &rw, &rzo);
+    row_pass<T, TC, PL>(a, 2, row0, row1, sy, swarp, srow, &rw, &rzo);
     block_sum2(rw, rzo, red64);
     if (threadIdx.x == 0) {
         a.dpart[b * 4 + 0] = rw;
@@ -723,9 +749,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_level2(L2Args<T> a) {
     (void)s_rzo;
 }
 
-template <typename T, int PL>
-msp_status launch_level2_pl(msp_ctx* ctx, L2Args<T>& a, int G) {
-    auto kern = k_level2<T, PL>;
+template <typename T, typename TC, int PL>
+msp_status launch_level2_pl(msp_ctx* ctx, L2Args<T, TC>& a, int G) {
+    auto kern = k_level2<T, TC, PL>;
     size_t smem = ((size_t)(4 + kNW) * a.s_pad + 2 * kRowChunk) * sizeof(T);
     MSP_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem));
@@ -742,21 +768,25 @@ msp_status launch_level2_pl(msp_ctx* ctx, L2Args<T>& a, int G) {
     return MSP_OK;
 }
 
-template <typename T>
-msp_status launch_level2(msp_ctx* ctx, L2Args<T>& a, int G) {
+template <typename T, typename TC>
+msp_status launch_level2(msp_ctx* ctx, L2Args<T, TC>& a, int G) {
     // one instantiation per padded sketch size (multiples of 128 up to 1024,
     // then 1536 and 2048)
     switch (a.s_pad) {
-        case 128: return launch_level2_pl<T, 4>(ctx, a, G);
-        case 256: return launch_level2_pl<T, 8>(ctx, a, G);
-        case 384: return launch_level2_pl<T, 12>(ctx, a, G);
-        case 512: return launch_level2_pl<T, 16>(ctx, a, G);
-        case 640: return launch_level2_pl<T, 20>(ctx, a, G);
-        case 768: return launch_level2_pl<T, 24>(ctx, a, G);
-        case 896: return launch_level2_pl<T, 28>(ctx, a, G);
-        case 1024: return launch_level2_pl<T, 32>(ctx, a, G);
-        case 1536: return launch_level2_pl<T, 48>(ctx, a, G);
-        case 2048: return launch_level2_pl<T, 64>(ctx, a, G);
+        case 128: return launch_level2_pl<T, TC, 4>(ctx, a, G);
+        case 256: return launch_level2_pl<T, TC, 8>(ctx, a, G);
+        case 384: return launch_level2_pl<T, TC, 12>(ctx, a, G);
+        case 512: return launch_level2_pl<T, TC, 16>(ctx, a, G);
+        case 640: return launch_level2_pl<T, TC, 20>(ctx, a, G);
+        case 768: return launch_level2_pl<T, TC, 24>(ctx, a, G);
+        case 896: return launch_level2_pl<T, TC, 28>(ctx, a, G);
+        case 1024: return launch_level2_pl<T, TC, 32>(ctx, a, G);
+        case 1536:
+            if constexpr (sizeof(T) == 4) return launch_level2_pl<T, TC, 48>(ctx, a, G);
+            break;
+        case 2048:
+            if constexpr (sizeof(T) == 4) return launch_level2_pl<T, TC, 64>(ctx, a, G);
+            break;
         default: break;
     }
     return msp_set_error(ctx, MSP_EINVAL, "level-2: unsupported padded sketch size %lld",
@@ -798,13 +828,14 @@ msp_status get_workspace(msp_ctx* ctx, int64_t n, int64_t sp, int G, int Gg, boo
     return MSP_OK;
 }
 
-template <typename T>
-void fill_l2(L2Args<T>& a, const msp_factor_s* f, int64_t n, const Workspace& ws, CtlBlock* ctl) {
+template <typename T, typename TC>
+void fill_l2(L2Args<T, TC>& a, const msp_factor_s* f, int64_t n, const Workspace& ws, CtlBlock* ctl) {
     const int64_t sp = f->s_pad;
     a.n = n;
     a.s_pad = sp;
-    a.C = (const T*)f->sk->C;
-    a.W = (const T*)f->W;
+    // BF16 preconditioner data: the factor's rounded copies of C and W
+    a.C = (const TC*)(f->data == MSP_BF16 ? f->Cb : f->sk->C);
+    a.W = (const TC*)(f->data == MSP_BF16 ? f->Wb : f->W);
     a.B = (const T*)f->B;
     a.Bt = (const T*)f->Bt;
     a.lam_t = (T)f->lam_tilde;
@@ -825,7 +856,7 @@ void fill_l2(L2Args<T>& a, const msp_factor_s* f, int64_t n, const Workspace& ws
 int level2_grid(msp_ctx* ctx) { return 2 * ctx->num_sms; }
 int gemv_grid(msp_ctx* ctx) { return ctx->num_sms * 8; }
 
-template <typename T>
+template <typename T, typename TC = T>
 msp_status krylov_solve_t(msp_ctx* ctx, const msp_factor_s* f, const void* A, msp_dtype dt,
                           int64_t n, int64_t lda, double lambda, const T* rhs, T* sol,
                           double tol_rel, int max_outer, const msp_opts* o, int* iters,
@@ -850,7 +881,7 @@ msp_status krylov_solve_t(msp_ctx* ctx, const msp_factor_s* f, const void* A, ms
     MSP_CUDA_TRY(ctx, cudaMemsetAsync(x, 0, 5 * np * sizeof(T), ctx->stream));
     MSP_CUDA_TRY(ctx, cudaMemcpyAsync(r, rhs, n * sizeof(T), cudaMemcpyDeviceToDevice, ctx->stream));
 
-    L2Args<T> a{};
+    L2Args<T, TC> a{};
     fill_l2(a, f, n, ws, ctl);
     a.tol_rel2 = tol_rel * tol_rel;
     a.inner_tol2 = o->inner_tol * o->inner_tol;
@@ -916,6 +947,9 @@ msp_status msp_krylov_solve(msp_ctx* ctx, const msp_factor_s* f, const void* A, 
                             int64_t n, int64_t lda, double lambda, const void* rhs, void* sol,
                             double tol_rel, int max_outer, const msp_opts* o, int* iters,
                             int* inner_iters, ProfSlot* prof, const float* packed) {
+    if (f->dtype == MSP_F32 && f->data == MSP_BF16)
+        return krylov_solve_t<float, __nv_bfloat16>(ctx, f, A, dt, n, lda, lambda, (const float*)rhs, (float*)sol,
+                                                    tol_rel, max_outer, o, iters, inner_iters, prof, packed);
     if (f->dtype == MSP_F32)
         return krylov_solve_t<float>(ctx, f, A, dt, n, lda, lambda, (const float*)rhs, (float*)sol,
                                      tol_rel, max_outer, o, iters, inner_iters, prof, packed);
@@ -976,7 +1010,18 @@ msp_status msp_solve_m1_impl(msp_ctx* ctx, const msp_factor_s* f, const void* r,
     CtlBlock* ctl = (CtlBlock*)ctx->ctl;
     MSP_CUDA_TRY(ctx, cudaMemsetAsync(ctl, 0, sizeof(CtlBlock), ctx->stream));
     int* hf = (int*)ctx->host_flags;
-    if (f->dtype == MSP_F32) {
+    if (f->dtype == MSP_F32 && f->data == MSP_BF16) {
+        Workspace ws;
+        MSP_TRY(get_workspace<float>(ctx, n, f->s_pad, G, Gg, false, &ws));
+        L2Args<float, __nv_bfloat16> a{};
+        fill_l2(a, f, n, ws, ctl);
+        a.inner_tol2 = o->inner_tol * o->inner_tol;
+        a.max_inner = o->max_inner;
+        a.r = (float*)r;
+        a.z = (float*)w;
+        a.mode = MODE_APPLY;
+        MSP_TRY(launch_level2(ctx, a, G));
+    } else if (f->dtype == MSP_F32) {
         Workspace ws;
         MSP_TRY(get_workspace<float>(ctx, n, f->s_pad, G, Gg, false, &ws));
         L2Args<float> a{};
@@ -1049,7 +1094,7 @@ __global__ void __launch_bounds__(256) k_matvec64_dd(const TA* __restrict__ A, i
         double hi = 0.0, lo = 0.0;
         for (int64_t j = lane; j < n; j += 32) {
             double p, e;
-            two_prod((double)__ldcs(&row[j]), x[j], p, e);
+            two_prod(wide64(__ldcs(&row[j])), x[j], p, e);
             dd_add(hi, lo, p, e);
         }
 #pragma unroll
@@ -1098,6 +1143,20 @@ msp_status msp_matvec64(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t n, in
     void* scr = nullptr;
     MSP_TRY(msp_scratch(ctx, (size_t)Gg * 8 + 256, &scr));
     CtlBlock* ctl = (CtlBlock*)ctx->ctl;
+    if (dt == MSP_BF16) {
+        // BF16 A (the matvec of a BF16-stored matrix, e.g. to measure its
+        // rounding against an FP32 or FP64 copy)
+        if (compensated)
+            k_matvec64_dd<__nv_bfloat16><<<Gg, 256, 0, ctx->stream>>>((const __nv_bfloat16*)A, lda, n, lambda, x, b,
+                                                                      out, (double*)scr, &ctl->last_block_counter,
+                                                                      norm2_out_dev);
+        else
+            k_matvec64<__nv_bfloat16, false><<<Gg, 256, 0, ctx->stream>>>((const __nv_bfloat16*)A, lda, n, lambda, x,
+                                                                          b, out, (double*)scr,
+                                                                          &ctl->last_block_counter, norm2_out_dev);
+        MSP_CHECK_LAUNCH(ctx);
+        return MSP_OK;
+    }
     if (compensated) {
         if (dt == MSP_F32)
             k_matvec64_dd<float><<<Gg, 256, 0, ctx->stream>>>((const float*)A, lda, n, lambda, x, b, out,

@@ -86,6 +86,13 @@ struct msp_factor_s {
     double* W64 = nullptr;      // s_pad x s_pad
     double* M2 = nullptr;       // s_pad x s_pad, before shift
     double* Linv64 = nullptr;   // s_pad x s_pad
+    // storage of the level-2 data C and W: MSP_F32 (the sketch's C and W
+    // above) or MSP_BF16 (Cb, Wb: BF16 roundings; W, M2 and L^{-1} are then
+    // formed from the rounded C, so that M = Cb W^{-1} Cb^T + lambda~ I is the
+    // preconditioner the level-2 iteration applies)
+    msp_dtype data = MSP_F32;
+    void* Cb = nullptr;         // n x s_pad BF16
+    void* Wb = nullptr;         // s_pad x s_pad BF16
 };
 
 // Device control block layout (one per context).
@@ -268,7 +275,8 @@ msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t
                            int64_t s, int gamma, uint64_t seed, bool pack, msp_sketch_s** out,
                            const void* host_chunks = nullptr);
 msp_status msp_nystrom_impl(msp_ctx* ctx, const msp_sketch_s* sk, double lambda, double lambda0,
-                            int64_t phi, int gamma_phi, uint64_t seed, msp_factor_s** out);
+                            int64_t phi, int gamma_phi, uint64_t seed, msp_factor_s** out,
+                            msp_dtype data = MSP_F32);
 
 // norms.cu: L <= |A|_2 into *out_dev; work holds 3n doubles
 msp_status msp_norm_lb_launch(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t n, int64_t lda,

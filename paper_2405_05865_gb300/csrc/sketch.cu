@@ -7,6 +7,8 @@
 //     which give W = Pi^T C = S C and C~ = Phi C.
 #include "msp_internal.cuh"
 
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cmath>
 
@@ -151,9 +153,14 @@ __global__ void k_chunk_starts(const int32_t* __restrict__ ptr, const int32_t* _
     tab[e] = lo;
 }
 
-template <typename T, int R, int NC>
+// A entry widened to the accumulation type (BF16 storage: exact).
+__device__ inline float widen(float v) { return v; }
+__device__ inline double widen(double v) { return v; }
+__device__ inline float widen(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename T, int R, int NC, typename TA = T>
 __global__ void __launch_bounds__(256) k_sketch_apply(
-    const T* __restrict__ A, int64_t lda, int64_t m, int64_t n, int64_t s_pad,
+    const TA* __restrict__ A, int64_t lda, int64_t m, int64_t n, int64_t s_pad,
     const int32_t* __restrict__ tab, int nch, const int32_t* __restrict__ ent, T scale,
     T* __restrict__ C, int J) {
     using VT = typename V16<T>::type;
@@ -177,7 +184,7 @@ __global__ void __launch_bounds__(256) k_sketch_apply(
             T v[R];
 #pragma unroll
             for (int r = 0; r < R; ++r)
-                v[r] = (i0 + r < m) ? __ldcs(&A[(i0 + r) * lda + j0 + jj]) : T(0);
+                v[r] = (i0 + r < m) ? (T)widen(__ldcs(&A[(i0 + r) * lda + j0 + jj])) : T(0);
             const int sw = (jj >> 1) & 3;
 #pragma unroll
             for (int q = 0; q < NV; ++q) {
@@ -225,8 +232,8 @@ __global__ void __launch_bounds__(256) k_sketch_apply(
     }
 }
 
-template <typename T, int R>
-msp_status launch_sketch_apply_r(msp_ctx* ctx, const T* A, int64_t lda, int64_t m, int64_t n,
+template <typename T, int R, typename TA = T>
+msp_status launch_sketch_apply_r(msp_ctx* ctx, const TA* A, int64_t lda, int64_t m, int64_t n,
                                  int64_t s_pad, const int32_t* ptr, const int32_t* ent,
                                  T scale, T* C) {
     // s_pad is a multiple of 128: the smallest NC with s_pad / NC a multiple
@@ -255,7 +262,7 @@ msp_status launch_sketch_apply_r(msp_ctx* ctx, const T* A, int64_t lda, int64_t 
     }
 #define MSP_SK_CASE(NCV)                                                              \
     case NCV: {                                                                       \
-        auto kern = k_sketch_apply<T, R, NCV>;                                        \
+        auto kern = k_sketch_apply<T, R, NCV, TA>;                                    \
         MSP_CUDA_TRY(ctx, cudaFuncSetAttribute(kern,                                  \
                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));        \
         kern<<<grid, threads, smem, ctx->stream>>>(A, lda, m, n, s_pad, tab, nch, ent, \
@@ -359,12 +366,15 @@ msp_status msp_sketch_apply_rows(msp_ctx* ctx, const void* A, msp_dtype dt, int6
                                  const int32_t* ent, int gamma, void* C) {
     // accumulators per thread: R rows x NC columns; R = 4 vectors of 16 bytes
     double scale = 1.0 / sqrt((double)gamma);
-    if (s_pad > (dt == MSP_F32 ? MSP_MAX_S_SINGLE : 1024))
+    if (s_pad > (dt != MSP_F64 ? MSP_MAX_S_SINGLE : 1024))
         return msp_set_error(ctx, MSP_EINVAL, "sketch: s_pad %lld above the supported maximum",
                              (long long)s_pad);
     if (dt == MSP_F32)
         return launch_sketch_apply_r<float, 16>(ctx, (const float*)A, lda, m, n, s_pad, ptr, ent,
                                                 (float)scale, (float*)C);
+    if (dt == MSP_BF16)   // BF16 A read, FP32 accumulation and C
+        return launch_sketch_apply_r<float, 16, __nv_bfloat16>(ctx, (const __nv_bfloat16*)A, lda, m, n, s_pad,
+                                                               ptr, ent, (float)scale, (float*)C);
     return launch_sketch_apply_r<double, 8>(ctx, (const double*)A, lda, m, n, s_pad, ptr, ent,
                                             scale, (double*)C);
 }
