@@ -276,6 +276,17 @@ MSP_API msp_status msp_solve(msp_ctx* ctx, const msp_factor_t* f, const void* A,
                      msp_dtype dtype, int64_t n, int64_t lda, double lambda,
                      const double* b, double* x, const msp_opts* opts,
                      msp_info* info);
+/* Wall-clock limit of the grid-wide barriers of the level-1 / level-2
+ * kernels (msp_solve, msp_solve_refined, msp_solve_many, msp_solve_m1) on
+ * the context's device, in seconds; 0 restores the default of 2 s. A block
+ * that waits longer gives up and the call returns MSP_ETIMEOUT (the context
+ * stays usable: every solve resets its control block). Meant for tests of
+ * that error path and for callers that want a solve that cannot stall for
+ * long; a limit below a barrier's normal duration (a few microseconds) makes
+ * every solve fail. Not part of the method (the paper has no counterpart).
+ * MSP_EINVAL outside [0, 60]. */
+MSP_API msp_status msp_set_grid_wait_limit(msp_ctx* ctx, double seconds);
+
 /* msp_solve with a separate matrix for the FP64 refinement residual. The
  * paper works in exact arithmetic (Section 2); here the problem is a matrix
  * given in FP64 whose FP32 rounding the level-1 iteration applies. A (FP32,

@@ -89,6 +89,7 @@ _SIGS = {
     "msp_solve_m1": (C.c_int, [P, P, P, P, C.POINTER(MspOpts), C.POINTER(C.c_int)]),
     "msp_solve": (C.c_int, [P, P, P, C.c_int, I64, I64, C.c_double, P, P, C.POINTER(MspOpts),
                             C.POINTER(MspInfo)]),
+    "msp_set_grid_wait_limit": (C.c_int, [P, C.c_double]),
     "msp_solve_refined": (C.c_int, [P, P, P, C.c_int, I64, I64, P, C.c_int, I64, C.c_double, P, P,
                                     C.POINTER(MspOpts), C.POINTER(MspInfo)]),
     "msp_solve_full": (C.c_int, [P, P, C.c_int, I64, I64, C.c_double, P, P, I64, C.c_int,

@@ -365,6 +365,10 @@ class Context:
             L.check(self.ptr, st)
         return x, info.as_dict()
 
+    def set_grid_wait_limit(self, seconds: float) -> None:
+        """Limit of the level-1 / level-2 grid barriers (0: the default 2 s)."""
+        L.check(self.ptr, self.lib.msp_set_grid_wait_limit(self.ptr, float(seconds)))
+
     def solve_refined(self, f: Factor, A: torch.Tensor, A_res: torch.Tensor, b: torch.Tensor, lam: float,
                       raise_on_noconv: bool = True, **opts) -> tuple[torch.Tensor, dict]:
         """msp_solve_refined: the level-1 iteration applies A (FP32, the

@@ -721,6 +721,15 @@ msp_status msp_solve(msp_ctx* ctx, const msp_factor_t* f, const void* A, msp_dty
     return solve_impl(ctx, f, A, dtype, n, lda, lambda, b, x, &o, info);
 }
 
+msp_status msp_set_grid_wait_limit(msp_ctx* ctx, double seconds) {
+    if (!ctx) return msp_set_error(nullptr, MSP_EINVAL, "ctx is NULL");
+    if (!(seconds >= 0.0) || seconds > 60.0)
+        return msp_set_error(ctx, MSP_EINVAL, "grid wait limit must be in [0, 60] s (0: the default)");
+    DeviceGuard g(ctx->device);
+    const unsigned long long ns = (unsigned long long)(seconds * 1e9);
+    return msp_grid_wait_limit_krylov(ctx, seconds > 0.0 && ns == 0 ? 1ull : ns);
+}
+
 msp_status msp_solve_refined(msp_ctx* ctx, const msp_factor_t* f, const void* A, msp_dtype dtype,
                              int64_t n, int64_t lda, const void* A_res, msp_dtype res_dtype, int64_t ld_res,
                              double lambda, const double* b, double* x, const msp_opts* opts, msp_info* info) {

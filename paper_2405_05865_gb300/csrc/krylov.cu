@@ -943,6 +943,14 @@ msp_status krylov_solve_t(msp_ctx* ctx, const msp_factor_s* f, const void* A, ms
 
 }  // namespace
 
+// The grid-barrier limit of this unit's kernels (the level-1 and level-2
+// iterations) on the current device; 0 restores the default.
+msp_status msp_grid_wait_limit_krylov(msp_ctx* ctx, unsigned long long ns) {
+    const unsigned long long v = ns ? ns : msp::kWaitLimitNs;
+    MSP_CUDA_TRY(ctx, cudaMemcpyToSymbol(msp::g_grid_wait_limit_ns, &v, sizeof v));
+    return MSP_OK;
+}
+
 msp_status msp_krylov_solve(msp_ctx* ctx, const msp_factor_s* f, const void* A, msp_dtype dt,
                             int64_t n, int64_t lda, double lambda, const void* rhs, void* sol,
                             double tol_rel, int max_outer, const msp_opts* o, int* iters,

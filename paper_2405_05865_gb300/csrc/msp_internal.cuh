@@ -201,6 +201,16 @@ __device__ inline uint64_t globaltimer_ns() {
 // Wall-clock limit of every device-side wait (ns).
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
+// Limit of the grid-wide barriers below, per translation unit (default
+// kWaitLimitNs); a unit may let callers lower it (msp_set_grid_wait_limit).
+// Read as volatile: the device code never writes it, and a plain read of an
+// internal-linkage variable may be folded to its initial value.
+static __device__ unsigned long long g_grid_wait_limit_ns = kWaitLimitNs;
+
+__device__ inline unsigned long long grid_wait_limit_ns() {
+    return *reinterpret_cast<volatile unsigned long long*>(&g_grid_wait_limit_ns);
+}
+
 // Grid-wide barrier for a cooperative (co-resident) launch. Sense via a
 // generation counter; bounded in wall-clock time: on timeout it records
 // MSP_ETIMEOUT in *err and returns false. All blocks must call it equally
@@ -220,20 +230,20 @@ __device__ inline bool grid_barrier(unsigned int* count, unsigned int* gen, int*
             asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" :: "l"(count) : "memory");
             asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(gen) : "memory");
         } else {
-            uint64_t t0 = globaltimer_ns();
+            const uint64_t t0 = globaltimer_ns();
+            const unsigned long long limit = grid_wait_limit_ns();
             unsigned int cur;
             int spins = 0;
             while (true) {
                 asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(gen) : "memory");
                 if (cur != g) break;
-                if (++spins > 64) {
-                    __nanosleep(40);
-                    if ((spins & 255) == 0 && globaltimer_ns() - t0 > kWaitLimitNs) {
-                        atomicExch(err, (int)MSP_ETIMEOUT);
-                        ok = 0;
-                        break;
-                    }
+                // the clock after every unsuccessful poll (one register read)
+                if (globaltimer_ns() - t0 > limit) {
+                    atomicExch(err, (int)MSP_ETIMEOUT);
+                    ok = 0;
+                    break;
                 }
+                if (++spins > 16) __nanosleep(40);
             }
         }
         __threadfence();
@@ -308,6 +318,7 @@ msp_status msp_symv_packed(msp_ctx* ctx, const float* packed, int64_t n, float l
                            float* part, double* dpart, int grid);
 
 // krylov.cu
+msp_status msp_grid_wait_limit_krylov(msp_ctx* ctx, unsigned long long ns);
 // prof: null, or two slots (A-pass GEMV, level-2 kernel) to accumulate
 // event-timed durations into (opts->profile).
 // packed: null (dense A pass over A) or the sketch's packed upper tiles.
