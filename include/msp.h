@@ -230,6 +230,16 @@ MSP_API msp_status msp_sketch_get_C(msp_ctx* ctx, const msp_sketch_t* sk, void* 
 MSP_API msp_status msp_nystrom(msp_ctx* ctx, const msp_sketch_t* sk, double lambda,
                        double lambda0, int64_t phi, int gamma_phi, uint64_t seed,
                        msp_factor_t** out);
+/* Where msp_nystrom forms the Gram C~^T C~ of an FP32 sketch: on = 1
+ * (default): on the tensor cores (tcgen05, TMA-staged): every entry of C~ is
+ * split into two FP16 terms of q c (q a power of two with q max|c| <= 2^14),
+ * the three largest of the four term products are accumulated in FP32 in
+ * tensor memory over slices of at most 2048 rows, and the slices are added in
+ * FP64 (error about 2^-22 of |C~|^T|C~| per entry); on = 0: on the FP32
+ * pipe with compensated (TwoSum) sums. Not part of the method (the paper
+ * has no counterpart; it selects an implementation). */
+MSP_API msp_status msp_set_gram_tensor_cores(msp_ctx* ctx, int on);
+
 /* msp_nystrom with the storage of the level-2 data chosen (Algorithm 1 steps
  * 3-4 and Algorithm 2 with reduced-precision preconditioner data; the paper
  * works in exact arithmetic, Section 2). data = MSP_F32 is msp_nystrom.

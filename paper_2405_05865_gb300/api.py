@@ -365,6 +365,10 @@ class Context:
             L.check(self.ptr, st)
         return x, info.as_dict()
 
+    def set_gram_tensor_cores(self, on: bool) -> None:
+        """M2 Gram on the tensor cores (default) or on the FP32 pipe."""
+        L.check(self.ptr, self.lib.msp_set_gram_tensor_cores(self.ptr, int(bool(on))))
+
     def set_grid_wait_limit(self, seconds: float) -> None:
         """Limit of the level-1 / level-2 grid barriers (0: the default 2 s)."""
         L.check(self.ptr, self.lib.msp_set_grid_wait_limit(self.ptr, float(seconds)))

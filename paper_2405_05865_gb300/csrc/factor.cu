@@ -672,9 +672,12 @@ msp_status msp_build_factor(msp_ctx* ctx, msp_factor_s* f, const void* Ct, int64
             k_symmetrize<double><<<grid, blk, 0, ctx->stream>>>((double*)f->W, f->W64, sp);
         MSP_CHECK_LAUNCH(ctx);
     }
-    // M2 = Ct^T Ct + lam_t W: split-K partial Grams (upper tiles, mirrored),
-    // then the fixed-order FP64 combination
-    {
+    // M2 = Ct^T Ct + lam_t W: on the tensor cores (FP32 data), else split-K
+    // partial Grams (upper tiles, mirrored) then the fixed-order FP64
+    // combination
+    if (f->dtype == MSP_F32 && ctx->gram_tc && msp_gram_tc_ok(sp)) {
+        MSP_TRY(msp_gram_tc(ctx, (const float*)Ct, phi_rows, sp, f->s, sp, (const float*)f->W, f->lam_tilde, f->M2));
+    } else {
         void* scr = nullptr;
         MSP_TRY(msp_scratch(ctx, (size_t)kGramSlices * sp * sp * 8, &scr));
         double* P = (double*)scr;

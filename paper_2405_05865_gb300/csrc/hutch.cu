@@ -646,12 +646,8 @@ template <int MODE>
 msp_status hutch_tc_launch(msp_ctx* ctx, const CUtensorMap& tmA, const CUtensorMap& tmG, const float* scale,
                            const uint32_t* bits, int wpr, int p0, int N, int64_t ntiles, int grid, double* part,
                            int* err, int* ovf) {
-    static bool attr = false;
-    if (!attr) {
-        MSP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_hutch_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)kTcSmem));
-        attr = true;
-    }
+    // per call: the attribute belongs to the current device
+    MSP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_hutch_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
     k_hutch_tc<MODE><<<grid, kTcThreads, kTcSmem, ctx->stream>>>(tmA, tmG, scale, bits, wpr, p0, N, ntiles, part,
                                                                   err, ovf);
     MSP_CHECK_LAUNCH(ctx);
@@ -786,12 +782,7 @@ msp_status hutch_simt(msp_ctx* ctx, const float* A, int64_t n, int64_t lda, int6
     MSP_TRY(msp_pack_upper(ctx, A, lda, n, packed));
     k_probes<<<(unsigned)((n_pad * m + 255) / 256), 256, 0, ctx->stream>>>(n, n_pad, (int)m, seed, G);
     MSP_CHECK_LAUNCH(ctx);
-    static bool attr = false;
-    if (!attr) {
-        MSP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_hutch_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)kHutchSmem));
-        attr = true;
-    }
+    MSP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_hutch_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kHutchSmem));
     k_hutch_tile<<<(unsigned)ntiles, 256, kHutchSmem, ctx->stream>>>(packed, (int)nt, G, (int)m, part);
     MSP_CHECK_LAUNCH(ctx);
     k_hutch_reduce<<<(unsigned)m, 256, 0, ctx->stream>>>(part, (int)ntiles, (int)nt, (int)m, q_dev);

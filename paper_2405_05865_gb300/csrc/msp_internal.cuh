@@ -43,6 +43,7 @@ struct msp_ctx {
     cudaStream_t fac_side[8] = {};
     cudaEvent_t fac_ev[8][2] = {};
     bool fac_overlap = true;     // false: the factor's products stay on the main stream
+    bool gram_tc = true;         // M2 Gram on the tensor cores (false: FP32 pipe, compensated)
     int hutch_terms = 2;         // tensor-core Hutchinson: 2 = two FP16 terms, 3 = three BF16 terms
     msp_ctx** lanes = nullptr;
     cudaStream_t* lane_streams = nullptr;
@@ -291,6 +292,13 @@ msp_status msp_nystrom_impl(msp_ctx* ctx, const msp_sketch_s* sk, double lambda,
 // norms.cu: L <= |A|_2 into *out_dev; work holds 3n doubles
 msp_status msp_norm_lb_launch(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t n, int64_t lda,
                               double* work, double* out_dev);
+
+// gram_tc.cu: M2 = X^T X + lam W (W null: + lam I) on the tensor cores
+// (two FP16 terms per entry, FP64 across K slices); MSP_EINVAL when the
+// tensor-core path is unavailable
+msp_status msp_gram_tc(msp_ctx* ctx, const float* X, int64_t K, int64_t ld, int64_t s, int64_t s_pad,
+                       const float* W, double lam, double* M2);
+bool msp_gram_tc_ok(int64_t s_pad);
 
 // factor.cu
 msp_status msp_build_factor(msp_ctx* ctx, msp_factor_s* f, const void* Ct, int64_t phi_rows);

@@ -19,6 +19,8 @@
 // Every wait on an mbarrier is bounded in wall-clock time (MSP_ETIMEOUT).
 #include "msp_internal.cuh"
 
+#include <atomic>
+
 namespace {
 
 constexpr int kTile = 128;
@@ -443,12 +445,14 @@ msp_status msp_pack_upper_rows(msp_ctx* ctx, const float* A, int64_t lda, int64_
 
 msp_status msp_symv_packed(msp_ctx* ctx, const float* packed, int64_t n, float lam, const float* p,
                            float* part, double* dpart, int grid) {
-    static bool attr = false;
-    if (!attr) {
+    // the attribute belongs to a device: set once per device (bit of a mask)
+    static std::atomic<uint64_t> attr_set{0};
+    const uint64_t bit = 1ull << (ctx->device & 63);
+    if (!(attr_set.load() & bit)) {
         MSP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_symv_packed,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)kSymvSmem));
-        attr = true;
+        attr_set.fetch_or(bit);
     }
     SymvArgs a;
     a.packed = packed;
