@@ -230,6 +230,16 @@ MSP_API msp_status msp_sketch_get_C(msp_ctx* ctx, const msp_sketch_t* sk, void* 
 MSP_API msp_status msp_nystrom(msp_ctx* ctx, const msp_sketch_t* sk, double lambda,
                        double lambda0, int64_t phi, int gamma_phi, uint64_t seed,
                        msp_factor_t** out);
+/* How msp_sketch reads an FP32 A in device memory (16-byte aligned, lda a
+ * multiple of 4, n >= 64, gamma <= 8): on = 1 (default): one pass over A
+ * that forms C = A Pi as A^T Pi (A is symmetric by this call's contract)
+ * from 128-column blocks of A staged by TMA, and stores the packed upper
+ * tiles and the row statistics of the norm bound from the same staged
+ * blocks; on = 0: the row-wise C pass, then the packing and the statistics
+ * as passes of their own. Both give C within the same rounding bound. Not
+ * part of the method (it selects an implementation). */
+MSP_API msp_status msp_set_sketch_one_pass(msp_ctx* ctx, int on);
+
 /* Where msp_nystrom forms the Gram C~^T C~ of an FP32 sketch: on = 1
  * (default): on the tensor cores (tcgen05, TMA-staged): every entry of C~ is
  * split into two FP16 terms of q c (q a power of two with q max|c| <= 2^14),

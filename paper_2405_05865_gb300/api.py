@@ -365,6 +365,10 @@ class Context:
             L.check(self.ptr, st)
         return x, info.as_dict()
 
+    def set_sketch_one_pass(self, on: bool) -> None:
+        """FP32 sketch pass: one pass over the symmetric A (default) or separate passes."""
+        L.check(self.ptr, self.lib.msp_set_sketch_one_pass(self.ptr, int(bool(on))))
+
     def set_gram_tensor_cores(self, on: bool) -> None:
         """M2 Gram on the tensor cores (default) or on the FP32 pipe."""
         L.check(self.ptr, self.lib.msp_set_gram_tensor_cores(self.ptr, int(bool(on))))

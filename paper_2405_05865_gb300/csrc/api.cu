@@ -238,6 +238,7 @@ msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t
     sk->stream = ctx->stream;
     const size_t ts = dtype_size(dtype);
     msp_status st = MSP_OK;
+    bool prep_done = false;    // packed tiles and statistics already formed by the one-pass kernel
     if ((st = msp_alloc(ctx, (void**)&sk->idx, (size_t)n * gamma * 4)) != MSP_OK ||
         (st = msp_alloc(ctx, (void**)&sk->sgn, (size_t)n * gamma)) != MSP_OK ||
         (st = msp_alloc(ctx, (void**)&sk->csr_ptr, (size_t)(sp + 1) * 4)) != MSP_OK ||
@@ -274,6 +275,10 @@ msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t
         // A); the lower tiles are mirrored on the device once their source
         // rows have landed. FP64: whole rows.
         const bool half = (dtype == MSP_F32);
+        // FP32: the one-pass kernel runs once every row has landed and the
+        // lower tiles are mirrored (the same kernel, hence bit for bit the
+        // result of a device-resident A); the copies still overlap the mirroring
+        const bool one_pass = half && ctx->sketch_sym && msp_sketch_sym_ok(A, n, n, sp, gamma);
         for (int k = 0; ok && k < nchunk; ++k) {
             const int64_t r0 = k * rows, nr = std::min(rows, n - r0);
             ok = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming) == cudaSuccess;
@@ -299,12 +304,22 @@ msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t
                 ok = false;
                 break;
             }
+            if (one_pass) continue;
             if ((st = msp_sketch_apply_rows(ctx, (const char*)A + (size_t)r0 * n * ts, dtype, nr, n, n, sp,
                                             sk->csr_ptr, sk->csr_ent, gamma, (char*)sk->C + (size_t)r0 * sp * ts)) !=
                     MSP_OK ||
                 (sk->packed && (st = msp_pack_upper_rows(ctx, (const float*)A, n, n, r0 / 128, (r0 + nr + 127) / 128,
                                                          sk->packed)) != MSP_OK))
                 ok = false;
+        }
+        if (ok && one_pass) {
+            if (pack) st = msp_alloc(ctx, (void**)&sk->stats, (size_t)(3 * n + 1) * 8);
+            if (st == MSP_OK)
+                st = msp_sketch_sym_pass(ctx, (const float*)A, n, n, sp, sk->csr_ptr, sk->csr_ent, gamma,
+                                         (float*)sk->C, pack ? sk->packed : nullptr, pack ? sk->stats : nullptr);
+            if (st == MSP_OK && pack) st = msp_norm_lb_finish(ctx, sk->stats, n, sk->stats + 3 * n);
+            ok = (st == MSP_OK);
+            prep_done = true;
         }
         if (!ok && st == MSP_OK) {
             cudaGetLastError();
@@ -320,13 +335,28 @@ msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t
             msp_sketch_destroy(sk);
             return st;
         }
+    } else if (a_dt == MSP_F32 && ctx->sketch_sym && msp_sketch_sym_ok(A, n, lda, sp, gamma)) {
+        // one pass over the symmetric A: C, the packed tiles and the row
+        // statistics together
+        if (pack) st = msp_alloc(ctx, (void**)&sk->stats, (size_t)(3 * n + 1) * 8);
+        if (st == MSP_OK)
+            st = msp_sketch_sym_pass(ctx, (const float*)A, n, lda, sp, sk->csr_ptr, sk->csr_ent, gamma,
+                                     (float*)sk->C, pack ? sk->packed : nullptr, pack ? sk->stats : nullptr);
+        if (st == MSP_OK && pack) st = msp_norm_lb_finish(ctx, sk->stats, n, sk->stats + 3 * n);
+        if (st != MSP_OK) {
+            cudaStreamSynchronize(ctx->stream);
+            msp_sketch_destroy(sk);
+            return st;
+        }
+        prep_done = true;
     } else if ((st = msp_sketch_apply(ctx, A, a_dt, n, lda, sp, sk->csr_ptr, sk->csr_ent, gamma, sk->C)) !=
                MSP_OK) {
         cudaStreamSynchronize(ctx->stream);
         msp_sketch_destroy(sk);
         return st;
     }
-    if (pack && (st = sketch_solve_prep(ctx, sk, A, dtype, host_chunks ? n : lda, !host_chunks)) != MSP_OK) {
+    if (pack && !prep_done &&
+        (st = sketch_solve_prep(ctx, sk, A, dtype, host_chunks ? n : lda, !host_chunks)) != MSP_OK) {
         cudaStreamSynchronize(ctx->stream);
         msp_sketch_destroy(sk);
         return st;

@@ -1082,6 +1082,113 @@ __device__ inline void dd_add(double& hi, double& lo, double p, double q) {
     lo = e - (hi - s);
 }
 
+// x = xh + xl with xh = fl32(x), xl = fl32(x - xh) (x - xh exact in FP64):
+// |x - xh - xl| <= 2^-48 |x|.
+__global__ void k_split_x(const double* __restrict__ x, int64_t n, float* __restrict__ xh, float* __restrict__ xl) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const double v = x[j];
+        const float h = (float)v;
+        xh[j] = h;
+        xl[j] = (float)(v - (double)h);
+    }
+}
+
+// (hi, lo) += p + t (|t| small): TwoSum (Knuth) of hi and p, the error, lo
+// and t added, then renormalised by Fast2Sum (Dekker) so that |lo| stays
+// within half an ulp of hi; each call adds at most about 2^-47 |hi| of error.
+__device__ __forceinline__ void ff_acc(float& hi, float& lo, float p, float t) {
+    const float s = __fadd_rn(hi, p);
+    const float bp = __fsub_rn(s, hi);
+    float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+    e = __fadd_rn(e, __fadd_rn(lo, t));
+    hi = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+
+// out = b - (A + lam I) x for an FP32 A in float-float arithmetic on the FP32
+// pipe (the FP64 pipe of this part, two FMAs per clock per SM, held the FP64
+// version to a third of the HBM rate). Per element: a xh exactly as p + e
+// (TwoProd by FMA), a xl + e rounded (at most about 2^-47 |a x|), both added
+// to a per-lane float-float pair (ff_acc). Four pairs per lane (one per
+// float4 component), n / 128 elements each; the pairs are added in FP64 in a
+// fixed order. Error at most about (n / 128 + 2) 2^-47 sum_j |a_ij x_j|
+// (2^-40 at n = 16384), with the split of x: far below the backward errors
+// the refinement resolves (1e-10 ~ 2^-33). |out|^2 into *norm2 as k_matvec64.
+// Requires lda, n multiples of 4 and 16-byte aligned A.
+__global__ void __launch_bounds__(256, 2) k_matvec64_ff(const float* __restrict__ A, int64_t lda, int64_t n,
+                                                    double lam, const float* __restrict__ xh,
+                                                    const float* __restrict__ xl, const double* __restrict__ x,
+                                                    const double* __restrict__ b, double* __restrict__ out,
+                                                    double* __restrict__ part, unsigned int* counter,
+                                                    double* norm2) {
+    __shared__ double red[32];
+    __shared__ bool am_last;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    double nn = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += warps) {
+        const float* row = A + i * lda;
+        float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+        int64_t j = (int64_t)lane * 4;
+        for (; j + 128 < n; j += 256) {
+            const float4 a0 = __ldcs(reinterpret_cast<const float4*>(row + j));
+            const float4 a1 = __ldcs(reinterpret_cast<const float4*>(row + j + 128));
+            const float4 h0 = __ldg(reinterpret_cast<const float4*>(xh + j));
+            const float4 h1 = __ldg(reinterpret_cast<const float4*>(xh + j + 128));
+            const float4 l0 = __ldg(reinterpret_cast<const float4*>(xl + j));
+            const float4 l1 = __ldg(reinterpret_cast<const float4*>(xl + j + 128));
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float hv[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+            const float lv[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const float p = __fmul_rn(av[k], hv[k]);
+                const float e = __fmaf_rn(av[k], hv[k], -p);
+                ff_acc(hi[k & 3], lo[k & 3], p, __fmaf_rn(av[k], lv[k], e));
+            }
+        }
+        for (; j < n; j += 128) {
+            const float4 a0 = __ldcs(reinterpret_cast<const float4*>(row + j));
+            const float4 h0 = __ldg(reinterpret_cast<const float4*>(xh + j));
+            const float4 l0 = __ldg(reinterpret_cast<const float4*>(xl + j));
+            const float av[4] = {a0.x, a0.y, a0.z, a0.w};
+            const float hv[4] = {h0.x, h0.y, h0.z, h0.w};
+            const float lv[4] = {l0.x, l0.y, l0.z, l0.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float p = __fmul_rn(av[k], hv[k]);
+                const float e = __fmaf_rn(av[k], hv[k], -p);
+                ff_acc(hi[k], lo[k], p, __fmaf_rn(av[k], lv[k], e));
+            }
+        }
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc += (double)hi[k] + (double)lo[k];
+        acc = msp::warp_sum(acc);
+        if (lane == 0) {
+            double v = acc + lam * x[i];
+            if (b) v = b[i] - v;
+            out[i] = v;
+            nn += v * v;
+        }
+    }
+    double tot = block_sum(nn, red);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = tot;
+        __threadfence();
+        unsigned int t = atomicAdd(counter, 1u);
+        am_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    double all = sum_parts(part, 1, gridDim.x, red);
+    if (threadIdx.x == 0) {
+        *counter = 0;
+        if (norm2) *norm2 = all;
+    }
+}
+
 // out = b - (A + lam I) x with double-double accumulation: every product
 // and sum error-free transformed, rounded to FP64 once per row. Its error is
 // a few u |r_i| + u^2 sum_j |A_ij x_j| instead of u sum_j |A_ij x_j|, so the
@@ -1149,7 +1256,8 @@ msp_status msp_matvec64(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t n, in
                         double* norm2_out_dev, bool compensated) {
     const int Gg = gemv_grid(ctx);
     void* scr = nullptr;
-    MSP_TRY(msp_scratch(ctx, (size_t)Gg * 8 + 256, &scr));
+    const size_t b_part = round_up((int64_t)Gg * 8, 256), b_x = round_up(n * 4, 256);
+    MSP_TRY(msp_scratch(ctx, b_part + 2 * b_x + 256, &scr));
     CtlBlock* ctl = (CtlBlock*)ctx->ctl;
     if (dt == MSP_BF16) {
         // BF16 A (the matvec of a BF16-stored matrix, e.g. to measure its
@@ -1180,11 +1288,15 @@ msp_status msp_matvec64(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t n, in
     const bool vec = (dt == MSP_F32) && (lda % 4 == 0) && (n % 4 == 0) &&
                      ((uintptr_t)A % 16 == 0) && ((uintptr_t)x % 16 == 0);
     if (dt == MSP_F32) {
-        if (vec)
-            k_matvec64<float, true><<<Gg, 256, 0, ctx->stream>>>((const float*)A, lda, n, lambda, x, b,
-                                                                 out, (double*)scr,
-                                                                 &ctl->last_block_counter, norm2_out_dev);
-        else
+        if (vec) {
+            float* xh = (float*)((char*)scr + b_part);
+            float* xl = (float*)((char*)scr + b_part + b_x);
+            k_split_x<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4 * ctx->num_sms), 256, 0, ctx->stream>>>(
+                x, n, xh, xl);
+            MSP_CHECK_LAUNCH(ctx);
+            k_matvec64_ff<<<Gg, 256, 0, ctx->stream>>>((const float*)A, lda, n, lambda, xh, xl, x, b, out,
+                                                       (double*)scr, &ctl->last_block_counter, norm2_out_dev);
+        } else
             k_matvec64<float, false><<<Gg, 256, 0, ctx->stream>>>((const float*)A, lda, n, lambda, x, b,
                                                                   out, (double*)scr,
                                                                   &ctl->last_block_counter, norm2_out_dev);

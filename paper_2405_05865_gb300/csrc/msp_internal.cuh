@@ -43,7 +43,8 @@ struct msp_ctx {
     cudaStream_t fac_side[8] = {};
     cudaEvent_t fac_ev[8][2] = {};
     bool fac_overlap = true;     // false: the factor's products stay on the main stream
-    bool gram_tc = true;         // M2 Gram on the tensor cores (false: FP32 pipe, compensated)
+    bool gram_tc = true;
+    bool sketch_sym = true;     // FP32 sketch pass by the symmetric one-pass kernel         // M2 Gram on the tensor cores (false: FP32 pipe, compensated)
     int hutch_terms = 2;         // tensor-core Hutchinson: 2 = two FP16 terms, 3 = three BF16 terms
     msp_ctx** lanes = nullptr;
     cudaStream_t* lane_streams = nullptr;
@@ -272,6 +273,19 @@ msp_status msp_sketch_apply(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t n
 msp_status msp_sketch_apply_rows(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t m, int64_t n,
                                  int64_t lda, int64_t s_pad, const int32_t* ptr,
                                  const int32_t* ent, int gamma, void* C);
+// tab[c * (nch + 1) + t] = first entry of column c with row >= t J
+msp_status msp_chunk_starts(msp_ctx* ctx, const int32_t* ptr, const int32_t* ent, int64_t s_pad, int J, int nch,
+                            int32_t* tab);
+// One pass over a symmetric FP32 A (device, 16-byte aligned, lda % 4 == 0,
+// n >= 64, gamma <= 8):
+// C = A Pi, and optionally the packed upper tiles and the row statistics
+// (rowsum, rowerr, rowsq: 3 n doubles) of the norm bound.
+bool msp_sketch_sym_ok(const void* A, int64_t n, int64_t lda, int64_t s_pad, int gamma);
+msp_status msp_sketch_sym_pass(msp_ctx* ctx, const float* A, int64_t n, int64_t lda, int64_t s_pad,
+                               const int32_t* ptr, const int32_t* ent, int gamma, float* C, float* packed,
+                               double* stats);
+// the norm bound from row statistics already in work (3 n doubles)
+msp_status msp_norm_lb_finish(msp_ctx* ctx, double* work, int64_t n, double* out_dev);
 msp_status msp_gather_rows(msp_ctx* ctx, msp_dtype dt, int64_t rows_out, int64_t width,
                            const int32_t* ptr, const int32_t* ent, const void* in,
                            int64_t ld_in, double scale, void* out, int64_t ld_out);

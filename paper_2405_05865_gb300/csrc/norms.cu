@@ -151,6 +151,12 @@ msp_status msp_norm_lb_launch(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t
     return MSP_OK;
 }
 
+msp_status msp_norm_lb_finish(msp_ctx* ctx, double* work, int64_t n, double* out_dev) {
+    k_norm_lb<<<1, 1024, 0, ctx->stream>>>(work, work + n, work + 2 * n, n, out_dev);
+    MSP_CHECK_LAUNCH(ctx);
+    return MSP_OK;
+}
+
 extern "C" msp_status msp_norm_lower_bound(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t n,
                                            int64_t lda, double* out) {
     if (!ctx) return msp_set_error(nullptr, MSP_EINVAL, "ctx is NULL");

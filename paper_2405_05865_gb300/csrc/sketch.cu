@@ -379,6 +379,14 @@ msp_status msp_sketch_apply_rows(msp_ctx* ctx, const void* A, msp_dtype dt, int6
                                             scale, (double*)C);
 }
 
+msp_status msp_chunk_starts(msp_ctx* ctx, const int32_t* ptr, const int32_t* ent, int64_t s_pad, int J, int nch,
+                            int32_t* tab) {
+    const int64_t cnt = s_pad * (nch + 1);
+    k_chunk_starts<<<(unsigned)((cnt + 255) / 256), 256, 0, ctx->stream>>>(ptr, ent, s_pad, J, nch, tab);
+    MSP_CHECK_LAUNCH(ctx);
+    return MSP_OK;
+}
+
 msp_status msp_gather_rows(msp_ctx* ctx, msp_dtype dt, int64_t rows_out, int64_t width,
                            const int32_t* ptr, const int32_t* ent, const void* in,
                            int64_t ld_in, double scale, void* out, int64_t ld_out) {

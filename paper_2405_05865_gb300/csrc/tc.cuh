@@ -38,6 +38,20 @@ __device__ inline void tma_load_2d(void* dst, const CUtensorMap* map, int32_t x,
         : "memory");
 }
 
+// 2-D tiled bulk store of the shared-memory box at src to the tensor map at
+// (x, y), in the calling thread's bulk group.
+__device__ inline void tma_store_2d(const CUtensorMap* map, int32_t x, int32_t y, const void* src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(smem_u32(src))
+                 : "memory");
+}
+__device__ inline void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the shared-memory reads of every committed bulk store are done
+__device__ inline void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// every committed bulk store is complete
+__device__ inline void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 __device__ inline void prefetch_tensormap(const CUtensorMap* map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }

@@ -215,7 +215,7 @@ def test_packed_and_dense_A_pass_agree(ctx, n):
     assert abs(ip["outer_iters"] - idn["outer_iters"]) <= 2 + 0.05 * idn["outer_iters"]
 
 
-@pytest.mark.parametrize("n", [257, 4096])
+@pytest.mark.parametrize("n", [257, 4096, 4100])
 def test_fp64_residual_operator(ctx, n):
     # y = (A + lam I) x with FP64 accumulation from FP32 A (the refinement's
     # residual operator): exact widening of each A entry (zeros, subnormals
@@ -232,6 +232,29 @@ def test_fp64_residual_operator(ctx, n):
     ref = A64 @ x + 0.37 * x
     scale = np.abs(A64) @ np.abs(x) + 0.37 * np.abs(x)
     assert np.all(np.abs(y - ref) <= 4 * n * 2.0 ** -53 * scale)
+
+
+@pytest.mark.parametrize("n", [4096, 16384 + 4])
+def test_fp64_residual_operator_float_float_bound(ctx, n):
+    # FP32 A with n and lda multiples of 4: the FP32-pipe float-float kernel.
+    # Against an extended-precision product its error stays within
+    # (n / 128 + 2) 2^-47 sum_j |a_ij x_j| (plus the FP64 rounding of y).
+    rng = np.random.default_rng(n + 1)
+    m = 512                                   # rows checked (a row block of A)
+    A = rng.standard_normal((m, n)).astype(np.float32)
+    A[:, ::7] *= np.float32(1e3)              # mixed magnitudes within a row
+    full = np.zeros((n, n), dtype=np.float32)
+    full[:m] = A
+    x = rng.standard_normal(n) * np.exp(rng.uniform(-5, 5, n))
+    y = ctx.matvec_f64(_cuda(full), _cuda(x), lam=0.5).cpu().numpy()[:m]
+    Al = A.astype(np.float64).astype(np.longdouble)
+    xl = x.astype(np.longdouble)
+    ref = Al @ xl + np.longdouble(0.5) * xl[:m]
+    scale = np.abs(A.astype(np.float64)) @ np.abs(x) + 0.5 * np.abs(x[:m])
+    err = np.abs(y.astype(np.longdouble) - ref).astype(np.float64)
+    assert np.all(err <= (n / 128 + 2) * 2.0 ** -47 * scale + 2.0 ** -52 * np.abs(y))
+    # and typically near the FP64 rounding of the result
+    assert np.median(err / scale) < 2.0 ** -46
 
 
 def test_solve_plain_fp32_rbf(ctx):
@@ -314,12 +337,16 @@ def test_solve_backward_error_rule(ctx):
     A64 = np.asarray(w.A, dtype=np.float64)
     Lo = reference.norm_lower_bound(A64)
     assert Lo * (1 - 1e-5) <= info["norm_lb"] <= Lo * (1 + 1e-12)
-    # the bound the sketch took of A (reused by every solve with it) is the
-    # one the stand-alone pass gives, and the one a solve takes itself of a copy
-    assert info["norm_lb"] == ctx.norm_lower_bound(A)
+    # the bound the sketch took of A in its one pass (reused by every solve
+    # with it) is, to the rounding of the FP32 chunk sums, the one the
+    # stand-alone row pass gives and the one a solve takes itself of a copy;
+    # all of them certified (at most |A|_2)
+    lb_rows = ctx.norm_lower_bound(A)
+    assert info["norm_lb"] == pytest.approx(lb_rows, rel=1e-6)
     _, info_c = ctx.solve(f, A.clone(), _cuda(w.b), lam=w.lam, max_inner=0, criterion="backward", tol=1e-10,
                           refine_tol=1e-4)
-    assert info_c["norm_lb"] == info["norm_lb"]
+    assert info_c["norm_lb"] == lb_rows
+    assert max(lb_rows, info["norm_lb"]) <= Lo * (1 + 1e-12)
     assert info["backward_err"] <= 1e-10
     top = float(np.linalg.eigvalsh(A64)[-1])
     eta = reference.backward_error(A64, x, w.b, w.lam, norm_A=top)
