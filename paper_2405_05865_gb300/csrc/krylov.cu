@@ -434,6 +434,91 @@ __device__ void row_pass(const L2Args<T, TC>& a, int kind, int64_t row0, int64_t
     store_slice<T, PL, TC>(swarp + (int64_t)w * a.s_pad, acc, lane);
 }
 
+// Butterfly reduce-scatter: lane l ends with the sum over the 32 lanes of
+// v[l] (31 shuffles, v overwritten).
+template <typename T>
+__device__ inline T reduce_scatter32(T* v, int lane) {
+#pragma unroll
+    for (int wd = 16; wd >= 1; wd >>= 1) {
+        const bool upper = (lane & wd) != 0;
+#pragma unroll
+        for (int i = 0; i < wd; ++i) {
+            const T send = upper ? v[i] : v[i + wd];
+            const T keep = upper ? v[i + wd] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, wd);
+        }
+    }
+    return v[0];
+}
+
+// Row pass of kind 2 (w_i = (r_i - c_i . y) / lam~, dots r.w and r.z_old)
+// for PL <= 32: a warp takes the rows w, w + kNW, ... of a chunk (at most 32
+// when kRowChunk = 32 kNW), holds its slice of y in registers, keeps one
+// partial dot per row and reduces all of them at once by a reduce-scatter, so
+// no per-row warp reduction sits in a dependency chain (the per-row
+// reductions of row_one held this pass to the latency of one shuffle chain
+// per row).
+template <typename T, typename TC, int PL>
+__device__ void row_pass_w(const L2Args<T, TC>& a, int64_t row0, int64_t row1, const T* svec, T* srow,
+                           double* rw, double* rzo) {
+    static_assert(PL <= 32, "y slice and 32 partial dots in registers");
+    static_assert(kRowChunk == 32 * kNW, "a warp's rows of a chunk fit one reduce-scatter");
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    constexpr int W = StoreW<TC>::W;
+    T* sr = srow;
+    T* sw = srow + kRowChunk;
+    T ys[PL];
+#pragma unroll
+    for (int k = 0; k < PL / W; ++k)
+#pragma unroll
+        for (int e = 0; e < W; ++e) ys[k * W + e] = svec[k * 32 * W + lane * W + e];
+    double d_rw = 0.0, d_rzo = 0.0;
+    for (int64_t base = row0; base < row1; base += kRowChunk) {
+        const int64_t end = min(row1, base + kRowChunk);
+        const int nr = (int)(end - base);
+        for (int e = threadIdx.x; e < nr; e += blockDim.x) sr[e] = a.r[base + e];
+        __syncthreads();
+        const int cnt = nr > w ? (nr - w + kNW - 1) / kNW : 0;   // this warp's rows: w + kNW t, t < cnt
+        T part[32];
+#pragma unroll
+        for (int t = 0; t < 32; ++t) part[t] = T(0);
+#pragma unroll
+        for (int t = 0; t < 32; t += 2) {
+            if (t < cnt) {
+                RowSlice<T, PL, TC> c0, c1;
+                c0.load(a.C + (base + w + (int64_t)kNW * t) * a.s_pad, lane);
+                const bool two = t + 1 < cnt;
+                if (two) c1.load(a.C + (base + w + (int64_t)kNW * (t + 1)) * a.s_pad, lane);
+                T d0 = T(0), d1 = T(0);
+#pragma unroll
+                for (int k = 0; k < PL; ++k) d0 += c0.v[k] * ys[k];
+                part[t] = d0;
+                if (two) {
+#pragma unroll
+                    for (int k = 0; k < PL; ++k) d1 += c1.v[k] * ys[k];
+                    part[t + 1] = d1;
+                }
+            }
+        }
+        const T dot = reduce_scatter32<T>(part, lane);
+        if (lane < cnt) {
+            const int il = w + kNW * lane;
+            sw[il] = (sr[il] - dot) / a.lam_t;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < nr; e += blockDim.x) {
+            const T ri = sr[e], wi = sw[e];
+            const T zo = a.z[base + e];
+            d_rw += (double)ri * (double)wi;
+            d_rzo += (double)ri * (double)zo;
+            a.z[base + e] = wi;
+        }
+        __syncthreads();
+    }
+    *rw = d_rw;
+    *rzo = d_rzo;
+}
+
 // part[b][c] = sum over warps of swarp[w][c]
 template <typename T, typename TC>
 __device__ inline void combine_warps(const L2Args<T, TC>& a, const T* swarp, int b) {
@@ -719,7 +804,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_level2(L2Args<T, TC> a) {
     // ---- w = (r - C y) / lam~ into z; dots for the level-1 beta
     __syncthreads();
     double rw = 0.0, rzo = 0.0;
-    row_pass<T, TC, PL>(a, 2, row0, row1, sy, swarp, srow, &rw, &rzo);
+    if constexpr (PL <= 32 && (sizeof(T) == 4 || PL <= 16)) row_pass_w<T, TC, PL>(a, row0, row1, sy, srow, &rw, &rzo);
+    else row_pass<T, TC, PL>(a, 2, row0, row1, sy, swarp, srow, &rw, &rzo);
     block_sum2(rw, rzo, red64);
     if (threadIdx.x == 0) {
         a.dpart[b * 4 + 0] = rw;
