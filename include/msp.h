@@ -108,8 +108,10 @@ typedef struct {
     int check_every;      /* level-1 iterations between host checks of the
                              device-side convergence flag. Default 8.            */
     int profile;          /* 1: time every A-pass and level-2 launch with CUDA
-                             events on the context stream (msp_info *_ms).
-                             Default 0.                                          */
+                             events on the context stream (msp_info *_ms);
+                             launches queued after the device flagged
+                             convergence (they return at once) are not
+                             counted. Default 0.                                 */
     int criterion;        /* stopping rule of the solve (the last refinement
                              step in MSP_PREC_MIXED), msp_criterion. Default
                              MSP_STOP_RESIDUAL.                                  */
@@ -145,7 +147,7 @@ typedef struct {
     int gemv_launches;    /* q = (A + lam I) p passes (level 1)                  */
     int level2_launches;  /* persistent level-1 update + SolveM1 kernels         */
     int resid_launches;   /* FP64 residual passes (refinement)                   */
-    int pad_;
+    int level1_graph_iters; /* level-1 iterations run as CUDA-graph replays      */
     double gemv_ms;
     double level2_ms;
     double resid_ms;
@@ -231,9 +233,10 @@ MSP_API msp_status msp_nystrom(msp_ctx* ctx, const msp_sketch_t* sk, double lamb
                        double lambda0, int64_t phi, int gamma_phi, uint64_t seed,
                        msp_factor_t** out);
 /* How msp_sketch reads an FP32 A in device memory (16-byte aligned, lda a
- * multiple of 4, n >= 64, gamma <= 8): on = 1 (default): one pass over A
- * that forms C = A Pi as A^T Pi (A is symmetric by this call's contract)
- * from 128-column blocks of A staged by TMA, and stores the packed upper
+ * multiple of 4, n >= 32; other FP32 inputs take the row-wise passes):
+ * on = 1 (default): one pass over A that forms C = A Pi as A^T Pi (A is
+ * symmetric by this call's contract) from 32-column blocks of A staged by
+ * TMA in chunks of 512 rows, and stores the packed upper
  * tiles and the row statistics of the norm bound from the same staged
  * blocks; on = 0: the row-wise C pass, then the packing and the statistics
  * as passes of their own. Both give C within the same rounding bound. Not
@@ -249,6 +252,20 @@ MSP_API msp_status msp_set_sketch_one_pass(msp_ctx* ctx, int on);
  * pipe with compensated (TwoSum) sums. Not part of the method (the paper
  * has no counterpart; it selects an implementation). */
 MSP_API msp_status msp_set_gram_tensor_cores(msp_ctx* ctx, int on);
+
+/* How msp_solve issues its level-1 iterations (Algorithm 2's outer loop:
+ * the A pass, then the level-2 kernel with the step, SolveM1 and the new
+ * direction): on = 1 (default): the two launches of one iteration are
+ * captured once into a CUDA graph (with event-record nodes when
+ * opts.profile = 1) and replayed check_every times between host reads of
+ * the device convergence flag; the executable is kept by the context and
+ * rebuilt when the solve's arguments or buffers change. on = 0: two stream
+ * launches per iteration. The same kernels run in the same order with the
+ * same arguments, so both give the same x bit for bit; where a capture is
+ * not possible the solve launches on the stream (msp_info.level1_graph_iters
+ * counts the replayed iterations). Not part of the method (it selects how
+ * the launches are issued). */
+MSP_API msp_status msp_set_level1_graphs(msp_ctx* ctx, int on);
 
 /* msp_nystrom with the storage of the level-2 data chosen (Algorithm 1 steps
  * 3-4 and Algorithm 2 with reduced-precision preconditioner data; the paper

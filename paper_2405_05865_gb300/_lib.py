@@ -34,7 +34,7 @@ class MspInfo(C.Structure):
                 ("shift_retries", C.c_int), ("rel_resid", C.c_double),
                 ("lambda_tilde", C.c_double), ("shift", C.c_double), ("status", C.c_int),
                 ("gemv_launches", C.c_int), ("level2_launches", C.c_int), ("resid_launches", C.c_int),
-                ("pad_", C.c_int), ("gemv_ms", C.c_double), ("level2_ms", C.c_double),
+                ("level1_graph_iters", C.c_int), ("gemv_ms", C.c_double), ("level2_ms", C.c_double),
                 ("resid_ms", C.c_double), ("backward_err", C.c_double), ("norm_lb", C.c_double)]
 
     def as_dict(self) -> dict:
@@ -91,6 +91,7 @@ _SIGS = {
                             C.POINTER(MspInfo)]),
     "msp_set_grid_wait_limit": (C.c_int, [P, C.c_double]),
     "msp_set_gram_tensor_cores": (C.c_int, [P, C.c_int]),
+    "msp_set_level1_graphs": (C.c_int, [P, C.c_int]),
     "msp_set_sketch_one_pass": (C.c_int, [P, C.c_int]),
     "msp_solve_refined": (C.c_int, [P, P, P, C.c_int, I64, I64, P, C.c_int, I64, C.c_double, P, P,
                                     C.POINTER(MspOpts), C.POINTER(MspInfo)]),

@@ -369,6 +369,10 @@ class Context:
         """FP32 sketch pass: one pass over the symmetric A (default) or separate passes."""
         L.check(self.ptr, self.lib.msp_set_sketch_one_pass(self.ptr, int(bool(on))))
 
+    def set_level1_graphs(self, on: bool) -> None:
+        """Level-1 iterations replayed as a CUDA graph (default) or launched one by one."""
+        L.check(self.ptr, self.lib.msp_set_level1_graphs(self.ptr, int(bool(on))))
+
     def set_gram_tensor_cores(self, on: bool) -> None:
         """M2 Gram on the tensor cores (default) or on the FP32 pipe."""
         L.check(self.ptr, self.lib.msp_set_gram_tensor_cores(self.ptr, int(bool(on))))

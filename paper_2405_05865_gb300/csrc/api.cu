@@ -156,6 +156,8 @@ void msp_destroy(msp_ctx* ctx) {
     if (ctx->stage) cudaFree(ctx->stage);
     if (ctx->ctl) cudaFree(ctx->ctl);
     if (ctx->host_flags) cudaFreeHost(ctx->host_flags);
+    msp_l1_graph_release(ctx);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (int i = 0; i < ctx->n_events; ++i) cudaEventDestroy(ctx->events[i]);
     delete[] ctx->events;
     for (int i = 0; i < ctx->n_lanes; ++i) {
@@ -627,8 +629,10 @@ static msp_status solve_impl(msp_ctx* ctx, const msp_factor_s* f, const void* A,
     pr.ctx = ctx;
     pr.on = o->profile != 0;
     if (pr.on) MSP_TRY(msp_profiler_reserve(ctx, 4096));
+    const int64_t graph_iters0 = ctx->l1_graph_iters;
     auto finish = [&](msp_status s2) {
         cudaStreamSynchronize(ctx->stream);
+        inf.level1_graph_iters = (int)(ctx->l1_graph_iters - graph_iters0);
         if (pr.on) {
             inf.gemv_launches = slots[0].launches;
             inf.gemv_ms = slots[0].ms;

@@ -103,7 +103,7 @@ struct BInst {
 };
 
 struct BCtl {
-    unsigned int bar_count, bar_gen;
+    unsigned int bar_word, bar_spare;     // grid barrier: generation << 16 | arrivals
     int error;
     int ctrA, ctrR;
     int active[2];
@@ -1237,7 +1237,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_batch_solve(BArgs a) {
     const bool timer = blockIdx.x == 0 && tid == 0;
 #define MSP_GBAR(cls)                                                                  \
     do {                                                                               \
-        if (!msp::grid_barrier(&ctl->bar_count, &ctl->bar_gen, &ctl->error)) return;   \
+        if (!msp::grid_barrier(&ctl->bar_word, &ctl->error)) return;   \
         if (ld_volatile(&ctl->error)) return;                                          \
         if (timer) {                                                                   \
             const uint64_t now = msp::globaltimer_ns();                                \

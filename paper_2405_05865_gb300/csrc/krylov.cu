@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 namespace {
 
@@ -549,30 +550,47 @@ __device__ inline void rows_dot(const TS* M, int64_t s_pad, int64_t c0, int64_t 
 // warps in index order. Returns sum_c out[c] * dvec[c] (dvec in shared memory,
 // may be null) and sum_c out[c]^2 through *sq (may be null). Columns are
 // processed 8 at a time so all loads of a chunk are in flight together.
+// With `pre` (stride pre_stride, G entries), its sum is formed alongside, its
+// loads in flight with the first chunk's, in the order of sum_parts (same
+// value), into *pre_out for every thread; red2 then holds 9 x 32 doubles.
 template <typename T>
 __device__ inline void reduce_cols(const T* part, int G, int64_t sp, int64_t c0, int64_t c1,
                                    const T* addend, T add_scale, T* out, const T* dvec,
-                                   double* dot_out, double* sq_out, double* red2 /*8*32*/) {
+                                   double* dot_out, double* sq_out, double* red2 /*8*32*/,
+                                   const double* pre = nullptr, int pre_stride = 0,
+                                   double* pre_out = nullptr) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     double dot = 0.0, sq = 0.0;
-    for (int64_t cb = c0; cb < c1; cb += 8) {
-        const int nc = (int)min((int64_t)8, c1 - cb);
+    bool first = true;
+    for (int64_t cb = c0; first || cb < c1; cb += 8) {
+        const int nc = (int)max((int64_t)0, min((int64_t)8, c1 - cb));
+        const bool with_pre = first && pre != nullptr;
+        first = false;
         T v[8];
+        double pv = 0.0;
 #pragma unroll
         for (int c = 0; c < 8; ++c) v[c] = T(0);
         for (int k = threadIdx.x; k < G; k += blockDim.x) {
 #pragma unroll
             for (int c = 0; c < 8; ++c)
                 if (c < nc) v[c] += __ldcg(&part[(int64_t)k * sp + cb + c]);
+            if (with_pre) pv += __ldcg(&pre[(int64_t)k * pre_stride]);
         }
 #pragma unroll
         for (int c = 0; c < 8; ++c) v[c] = msp::warp_sum(v[c]);
+        if (with_pre) pv = msp::warp_sum(pv);
         __syncthreads();
         if (lane == 0) {
 #pragma unroll
             for (int c = 0; c < 8; ++c) red2[c * 32 + w] = (double)v[c];
+            if (with_pre) red2[8 * 32 + w] = pv;
         }
         __syncthreads();
+        if (with_pre) {
+            double t = 0.0;
+            for (int k = 0; k < nw; ++k) t += red2[8 * 32 + k];
+            *pre_out = t;
+        }
         if (threadIdx.x < nc) {
             const int c = threadIdx.x;
             double acc = 0.0;
@@ -606,19 +624,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_level2(L2Args<T, TC> a) {
     T* srow = swarp + kNW * sp;                   // 2 x kRowChunk (row pass staging)
     __shared__ double red[32];
     __shared__ double red64[64];
-    __shared__ double red2[8 * 32];
+    __shared__ double red2[9 * 32];
     __shared__ double s_rw, s_rzo;
 
     CtlBlock* ctl = a.ctl;
-    if (ctl->done | ctl->error) return;
-    const int G = gridDim.x, b = blockIdx.x;
-    const int64_t row0 = a.n * b / G, row1 = a.n * (b + 1) / G;
-    const int64_t c0 = sp * b / G, c1 = sp * (b + 1) / G;
+    // the control words in one round trip
+    const int c_done = ctl->done, c_err = ctl->error;
     const double alpha = ctl->alpha;
     const double rz_outer = ctl->rz;
     const double tol2 = ctl->tol2;
-    unsigned int* bc = &ctl->bar_count;
-    unsigned int* bg = &ctl->bar_gen;
+    if (c_done | c_err) return;
+    const int G = gridDim.x, b = blockIdx.x;
+    const int64_t row0 = a.n * b / G, row1 = a.n * (b + 1) / G;
+    const int64_t c0 = sp * b / G, c1 = sp * (b + 1) / G;
+    unsigned int* bw = &ctl->bar_word;
     int* err = &ctl->error;
 
     // ---- level-1 update and g = C^T r partials
@@ -699,10 +718,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_level2(L2Args<T, TC> a) {
     __syncthreads();
     row_pass<T, TC, PL>(a, 0, row0, row1, nullptr, swarp, srow, nullptr, nullptr);
     combine_warps(a, swarp, b);
-    if (!msp::grid_barrier(bc, bg, err)) return;
+    if (!msp::grid_barrier(bw, err)) return;
 
+    // ---- g reduced over this block's columns, with |r|^2 (the convergence
+    // test) summed alongside; |g|^2 only where the level-2 iteration's
+    // tolerance needs it
+    const bool inner = a.max_inner > 0;
+    double gg = 0.0;
+    reduce_cols<T>(a.part, G, sp, c0, c1, nullptr, T(0), a.gvec, nullptr, nullptr, inner ? &gg : nullptr, red2,
+                   a.mode != MODE_APPLY ? a.dpart + 0 : nullptr, 4, &rr);
     if (a.mode != MODE_APPLY) {
-        rr = sum_parts(a.dpart + 0, 4, G, red);
         if (!isfinite(rr)) {
             if (b == 0 && threadIdx.x == 0) ctl->error = MSP_ENONFINITE;
             return;
@@ -719,13 +744,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_level2(L2Args<T, TC> a) {
             return;
         }
     }
-    // ---- g reduced over this block's columns
-    double gg = 0.0;
-    reduce_cols<T>(a.part, G, sp, c0, c1, nullptr, T(0), a.gvec, nullptr, nullptr, &gg, red2);
-    gg = block_sum(gg, red);
-    if (threadIdx.x == 0) a.dpart[b * 4 + 1] = gg;
-    if (!msp::grid_barrier(bc, bg, err)) return;
-    gg = sum_parts(a.dpart + 1, 4, G, red);
+    if (inner) {
+        gg = block_sum(gg, red);
+        if (threadIdx.x == 0) a.dpart[b * 4 + 1] = gg;
+    }
+    if (!msp::grid_barrier(bw, err)) return;
+    if (inner) gg = sum_parts(a.dpart + 1, 4, G, red);
     load_full(a.gvec, sres, sp);
     for (int64_t c = threadIdx.x; c < sp; c += blockDim.x) sy[c] = T(0);
     __syncthreads();
@@ -733,7 +757,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_level2(L2Args<T, TC> a) {
     // ---- z = M2^{-1} res = B^T (B res)
     auto precond = [&](double* rz_out) -> bool {
         rows_dot<T, PL>(a.B, sp, c0, c1, sres, a.tvec);
-        if (!msp::grid_barrier(bc, bg, err)) return false;
+        if (!msp::grid_barrier(bw, err)) return false;
         load_full(a.tvec, stmp, sp);
         __syncthreads();
         rows_dot<T, PL>(a.Bt, sp, c0, c1, stmp, a.zvec);
@@ -747,37 +771,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_level2(L2Args<T, TC> a) {
             part = block_sum(part, red);
             if (threadIdx.x == 0) a.dpart[b * 4 + 2] = part;
         }
-        if (!msp::grid_barrier(bc, bg, err)) return false;
+        if (!msp::grid_barrier(bw, err)) return false;
         if (rz_out) *rz_out = sum_parts(a.dpart + 2, 4, G, red);
         return true;
     };
 
     // direct level 2 (max_inner == 0) has no level-2 iteration: z^T res unused
     double rz_in = 0.0;
-    if (!precond(a.max_inner > 0 ? &rz_in : nullptr)) return;
-    load_full(a.zvec, sd, sp);
+    if (!precond(inner ? &rz_in : nullptr)) return;
+    // direct level 2: M2 is the level-2 operator itself (Phi = I), so
+    // y = M2^{-1} C^T r with no correction steps
+    load_full(a.zvec, inner ? sd : sy, sp);
     __syncthreads();
     double rres = gg;
     const double tin2 = a.inner_tol2 * gg;
     int k = 0;
-    if (a.max_inner == 0) {
-        // direct level 2: M2 is the level-2 operator itself (Phi = I), so
-        // y = M2^{-1} C^T r with no correction steps
-        for (int64_t c = threadIdx.x; c < sp; c += blockDim.x) sy[c] = sd[c];
-        __syncthreads();
-    }
     while (k < a.max_inner && rres > tin2) {
         // P1: partial u = C^T (C d) over this block's rows; wd = W d (columns)
         row_pass<T, TC, PL>(a, 1, row0, row1, sd, swarp, srow, nullptr, nullptr);
         combine_warps(a, swarp, b);
         rows_dot<T, PL, TC>(a.W, sp, c0, c1, sd, a.wdvec);
-        if (!msp::grid_barrier(bc, bg, err)) return;
+        if (!msp::grid_barrier(bw, err)) return;
         // P2: u over this block's columns; d.u partial
         double du = 0.0;
         reduce_cols<T>(a.part, G, sp, c0, c1, a.wdvec, a.lam_t, a.uvec, sd, &du, nullptr, red2);
         du = block_sum(du, red);
         if (threadIdx.x == 0) a.dpart[b * 4 + 3] = du;
-        if (!msp::grid_barrier(bc, bg, err)) return;
+        if (!msp::grid_barrier(bw, err)) return;
         // P3: step
         du = sum_parts(a.dpart + 3, 4, G, red);
         if (!(du > 0.0)) break;   // breakdown (same decision in every block)
@@ -815,12 +835,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_level2(L2Args<T, TC> a) {
         if (b == 0 && threadIdx.x == 0) atomicAdd(&ctl->inner_iters, k);
         return;
     }
-    if (!msp::grid_barrier(bc, bg, err)) return;
+    if (!msp::grid_barrier(bw, err)) return;
+    // this thread's first row of z and p, in flight with the dot partials
+    const int64_t i_first = row0 + threadIdx.x;
+    T z_first = T(0), p_first = T(0);
+    if (i_first < row1) {
+        z_first = a.z[i_first];
+        p_first = a.p[i_first];
+    }
     sum_parts2(a.dpart + 0, 4, G, red64, rw, rzo);
     T beta = T(0);
     if (a.mode == MODE_ITER) beta = (T)((rw - rzo) / rz_outer);
-    for (int64_t i = row0 + threadIdx.x; i < row1; i += blockDim.x)
-        a.p[i] = a.z[i] + beta * (a.mode == MODE_ITER ? a.p[i] : T(0));
+    for (int64_t i = i_first; i < row1; i += blockDim.x) {
+        const T zi = (i == i_first) ? z_first : a.z[i];
+        const T pi = (i == i_first) ? p_first : a.p[i];
+        a.p[i] = zi + beta * (a.mode == MODE_ITER ? pi : T(0));
+    }
     if (b == 0 && threadIdx.x == 0) {
         ctl->rz = rw;
         ctl->beta = (double)beta;
@@ -942,6 +972,101 @@ void fill_l2(L2Args<T, TC>& a, const msp_factor_s* f, int64_t n, const Workspace
 int level2_grid(msp_ctx* ctx) { return 2 * ctx->num_sms; }
 int gemv_grid(msp_ctx* ctx) { return ctx->num_sms * 8; }
 
+// ------------------------------------------------ level-1 graph replay
+//
+// One level-1 iteration is two launches whose arguments do not change from
+// one iteration to the next (the A pass and the cooperative level-2 kernel;
+// the scalars travel through the control block). It is captured once into a
+// CUDA graph and replayed, which removes the per-launch host work and most
+// of the gap between the two kernels. The executable is cached in the
+// context under a key of everything the launches were built from (argument
+// structs, buffers, grid sizes); any change rebuilds it.
+
+constexpr int kL1Timed = 4;     // event-record nodes of a timed iteration graph
+
+// Captures iter(true) (launches on ctx->stream, redirected to the capture
+// stream) as the context's level-1 graph for `key`. With `timed`, iter
+// brackets each launch by event-record nodes on ctx->events[0..3], found
+// again here by their events so that each replay can point them at fresh
+// events. Leaves ctx->l1_exec null where capture is not possible; the
+// caller then launches on the stream.
+template <typename F>
+msp_status ensure_l1_graph(msp_ctx* ctx, const void* key, size_t klen, bool timed, F&& iter) {
+    if (ctx->l1_exec && ctx->l1_key_len == klen && std::memcmp(ctx->l1_key, key, klen) == 0)
+        return MSP_OK;
+    msp_l1_graph_release(ctx);
+    if (klen > sizeof(ctx->l1_key)) return MSP_OK;
+    if (!ctx->cap_stream &&
+        cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->cap_stream = nullptr;
+        return MSP_OK;
+    }
+    if (cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        cudaGetLastError();
+        return MSP_OK;
+    }
+    const cudaStream_t saved = ctx->stream;
+    const int64_t l0 = ctx->launches;
+    ctx->stream = ctx->cap_stream;
+    const msp_status st = iter(true);
+    ctx->stream = saved;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    const int kernels = (int)(ctx->launches - l0);
+    ctx->launches = l0;
+    bool ok = st == MSP_OK && ce == cudaSuccess && graph != nullptr;
+    cudaGraphNode_t evn[kL1Timed] = {};
+    if (ok && timed) {
+        size_t nn = 0;
+        ok = cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn > 0 && nn <= 64;
+        cudaGraphNode_t nodes[64];
+        if (ok) ok = cudaGraphGetNodes(graph, nodes, &nn) == cudaSuccess;
+        for (size_t i = 0; ok && i < nn; ++i) {
+            cudaGraphNodeType ty;
+            if (cudaGraphNodeGetType(nodes[i], &ty) != cudaSuccess) { ok = false; break; }
+            if (ty != cudaGraphNodeTypeEventRecord) continue;
+            cudaEvent_t ev = nullptr;
+            if (cudaGraphEventRecordNodeGetEvent(nodes[i], &ev) != cudaSuccess) { ok = false; break; }
+            for (int k = 0; k < kL1Timed; ++k)
+                if (ev == ctx->events[k]) evn[k] = nodes[i];
+        }
+        for (int k = 0; ok && k < kL1Timed; ++k) ok = evn[k] != nullptr;
+    }
+    if (ok && cudaGraphInstantiate(&ctx->l1_exec, graph, 0) != cudaSuccess) {
+        ctx->l1_exec = nullptr;
+        ok = false;
+    }
+    if (!ok) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return MSP_OK;
+    }
+    ctx->l1_graph = graph;
+    std::memcpy(ctx->l1_key, key, klen);
+    ctx->l1_key_len = klen;
+    for (int k = 0; k < kL1Timed; ++k) ctx->l1_ev_nodes[k] = evn[k];
+    ctx->l1_kernels = kernels;
+    return MSP_OK;
+}
+
+// Points the event-record nodes of the timed graph at the profiler's next
+// two event pairs (the spare events past the pool once it is full), then
+// replays one iteration. Already queued replays keep their events.
+msp_status replay_l1(msp_ctx* ctx, Profiler& pr) {
+    if (pr.on) {
+        cudaEvent_t e[kL1Timed];
+        for (int k = 0; k < kL1Timed; ++k) e[k] = ctx->events[ctx->n_events - kL1Timed + k];
+        if (pr.take(0, &e[0], &e[1])) pr.take(1, &e[2], &e[3]);
+        for (int k = 0; k < kL1Timed; ++k)
+            MSP_CUDA_TRY(ctx, cudaGraphExecEventRecordNodeSetEvent(ctx->l1_exec, ctx->l1_ev_nodes[k], e[k]));
+    }
+    MSP_CUDA_TRY(ctx, cudaGraphLaunch(ctx->l1_exec, ctx->stream));
+    ctx->launches += ctx->l1_kernels;
+    ++ctx->l1_graph_iters;
+    return MSP_OK;
+}
+
 template <typename T, typename TC = T>
 msp_status krylov_solve_t(msp_ctx* ctx, const msp_factor_s* f, const void* A, msp_dtype dt,
                           int64_t n, int64_t lda, double lambda, const T* rhs, T* sol,
@@ -967,7 +1092,9 @@ msp_status krylov_solve_t(msp_ctx* ctx, const msp_factor_s* f, const void* A, ms
     MSP_CUDA_TRY(ctx, cudaMemsetAsync(x, 0, 5 * np * sizeof(T), ctx->stream));
     MSP_CUDA_TRY(ctx, cudaMemcpyAsync(r, rhs, n * sizeof(T), cudaMemcpyDeviceToDevice, ctx->stream));
 
-    L2Args<T, TC> a{};
+    // zeroed bytes (padding included): the struct is part of the graph key
+    L2Args<T, TC> a;
+    std::memset(&a, 0, sizeof a);
     fill_l2(a, f, n, ws, ctl);
     a.tol_rel2 = tol_rel * tol_rel;
     a.inner_tol2 = o->inner_tol * o->inner_tol;
@@ -983,37 +1110,96 @@ msp_status krylov_solve_t(msp_ctx* ctx, const msp_factor_s* f, const void* A, ms
 
     const bool vec = (lda % (16 / dtype_size(dt)) == 0) &&
                      ((uintptr_t)A % 16 == 0) && (n % (16 / dtype_size(dt)) == 0);
-    int* hf = (int*)ctx->host_flags;
-    const int check = std::max(1, o->check_every);
-    for (int it = 0; it < max_outer; ++it) {
-        MSP_TRY(pr.begin(0));
+    // one level-1 iteration: the A pass q = (A + lam I) p, then the level-2
+    // kernel (the step, SolveM1, the new direction); `cap`: inside a graph
+    // capture, where event-record nodes take the profiler's place
+    auto mark = [&](bool cap, int k) -> msp_status {
+        if (!pr.on) return MSP_OK;
+        if (cap) {
+            MSP_CUDA_TRY(ctx, cudaEventRecordWithFlags(ctx->events[k], ctx->stream, cudaEventRecordExternal));
+            return MSP_OK;
+        }
+        return (k & 1) ? pr.end() : pr.begin(k >> 1);
+    };
+    auto iteration = [&](bool cap) -> msp_status {
+        MSP_TRY(mark(cap, 0));
         if (use_packed) {
             MSP_TRY(msp_symv_packed(ctx, packed, n, (float)lambda, (const float*)p, ws.qpart,
                                     ws.gpart, ctx->num_sms));
-        } else if (dt == MSP_F32) {
-            if (vec) k_gemv<float, T, true><<<Gg, 256, 0, ctx->stream>>>((const float*)A, lda, n, lambda, p, q, ws.gpart, ctl);
-            else k_gemv<float, T, false><<<Gg, 256, 0, ctx->stream>>>((const float*)A, lda, n, lambda, p, q, ws.gpart, ctl);
         } else {
-            if (vec) k_gemv<double, T, true><<<Gg, 256, 0, ctx->stream>>>((const double*)A, lda, n, lambda, p, q, ws.gpart, ctl);
-            else k_gemv<double, T, false><<<Gg, 256, 0, ctx->stream>>>((const double*)A, lda, n, lambda, p, q, ws.gpart, ctl);
+            if (dt == MSP_F32) {
+                if (vec) k_gemv<float, T, true><<<Gg, 256, 0, ctx->stream>>>((const float*)A, lda, n, lambda, p, q, ws.gpart, ctl);
+                else k_gemv<float, T, false><<<Gg, 256, 0, ctx->stream>>>((const float*)A, lda, n, lambda, p, q, ws.gpart, ctl);
+            } else {
+                if (vec) k_gemv<double, T, true><<<Gg, 256, 0, ctx->stream>>>((const double*)A, lda, n, lambda, p, q, ws.gpart, ctl);
+                else k_gemv<double, T, false><<<Gg, 256, 0, ctx->stream>>>((const double*)A, lda, n, lambda, p, q, ws.gpart, ctl);
+            }
+            MSP_CHECK_LAUNCH(ctx);
         }
-        if (!use_packed) MSP_CHECK_LAUNCH(ctx);
-        MSP_TRY(pr.end());
-        MSP_TRY(pr.begin(1));
+        MSP_TRY(mark(cap, 1));
+        MSP_TRY(mark(cap, 2));
         MSP_TRY(launch_level2(ctx, a, G));
-        MSP_TRY(pr.end());
-        if ((it + 1) % check == 0 || it + 1 == max_outer) {
-            MSP_CUDA_TRY(ctx, cudaMemcpyAsync(hf, &ctl->done, 5 * sizeof(int),
-                                              cudaMemcpyDeviceToHost, ctx->stream));
-            MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-            if (hf[0] || hf[1]) break;
+        MSP_TRY(mark(cap, 3));
+        return MSP_OK;
+    };
+    bool graphed = false;
+    if (ctx->l1_graphs) {
+        struct Key {
+            int tag, dt, use_packed, vec, G, Gg, timed, pad;
+            const void* A;
+            int64_t lda;
+            const float* packed;
+            double lambda;
+            const void* qpart;
+            const void* gpart;
+            L2Args<T, TC> a;
+        } key;
+        static_assert(sizeof(Key) <= sizeof(ctx->l1_key), "level-1 graph key too large");
+        std::memset(&key, 0, sizeof key);
+        key.tag = (int)(10 * sizeof(T) + sizeof(TC));
+        key.dt = (int)dt;
+        key.use_packed = use_packed;
+        key.vec = vec;
+        key.G = G;
+        key.Gg = Gg;
+        key.timed = pr.on;
+        key.A = A;
+        key.lda = lda;
+        key.packed = packed;
+        key.lambda = lambda;
+        key.qpart = ws.qpart;
+        key.gpart = ws.gpart;
+        std::memcpy(&key.a, &a, sizeof a);
+        MSP_TRY(ensure_l1_graph(ctx, &key, sizeof key, pr.on, iteration));
+        graphed = ctx->l1_exec != nullptr;
+    }
+    int* hf = (int*)ctx->host_flags;
+    const int check = std::max(1, o->check_every);
+    // profiler entries of iterations known to have run to completion with
+    // work (every iteration before a check that found no flag): read while
+    // the next interval runs, not after it
+    int settled = 0;
+    for (int it = 0; it < max_outer;) {
+        const int nrun = std::min(check, max_outer - it);
+        for (int i = 0; i < nrun; ++i) {
+            if (graphed) MSP_TRY(replay_l1(ctx, pr));
+            else MSP_TRY(iteration(false));
         }
+        it += nrun;
+        MSP_CUDA_TRY(ctx, cudaMemcpyAsync(hf, &ctl->done, 5 * sizeof(int), cudaMemcpyDeviceToHost,
+                                          ctx->stream));
+        MSP_TRY(pr.harvest(prof, 2, settled));
+        MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        if (hf[0] || hf[1]) break;
+        settled = pr.used;
     }
     MSP_CUDA_TRY(ctx, cudaMemcpyAsync(hf, &ctl->done, 5 * sizeof(int), cudaMemcpyDeviceToHost,
                                       ctx->stream));
     MSP_CUDA_TRY(ctx, cudaMemcpyAsync(sol, x, n * sizeof(T), cudaMemcpyDeviceToDevice, ctx->stream));
     MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-    if (pr.on) MSP_TRY(pr.finish(prof, 2));
+    // the iterations that did work: ctl->iters counts them, and every launch
+    // queued after the flag returned at once
+    if (pr.on) MSP_TRY(pr.finish(prof, 2, 2 * hf[2]));
     // hf: done, error, iters, inner_iters, pad
     if (iters) *iters = hf[2];
     if (inner_iters) *inner_iters = hf[3];
@@ -1028,6 +1214,23 @@ msp_status krylov_solve_t(msp_ctx* ctx, const msp_factor_s* f, const void* A, ms
 }
 
 }  // namespace
+
+void msp_l1_graph_release(msp_ctx* ctx) {
+    if (ctx->l1_exec) cudaGraphExecDestroy(ctx->l1_exec);
+    if (ctx->l1_graph) cudaGraphDestroy(ctx->l1_graph);
+    ctx->l1_exec = nullptr;
+    ctx->l1_graph = nullptr;
+    ctx->l1_key_len = 0;
+    for (cudaGraphNode_t& nd : ctx->l1_ev_nodes) nd = nullptr;
+    ctx->l1_kernels = 0;
+}
+
+extern "C" msp_status msp_set_level1_graphs(msp_ctx* ctx, int on) {
+    if (!ctx) return msp_set_error(nullptr, MSP_EINVAL, "ctx is NULL");
+    ctx->l1_graphs = on != 0;
+    if (!ctx->l1_graphs) msp_l1_graph_release(ctx);
+    return MSP_OK;
+}
 
 // The grid-barrier limit of this unit's kernels (the level-1 and level-2
 // iterations) on the current device; 0 restores the default.
@@ -1053,13 +1256,16 @@ msp_status msp_krylov_solve(msp_ctx* ctx, const msp_factor_s* f, const void* A, 
 
 // ---------------------------------------------------------------- profiler
 
+// `pairs` event pairs plus four spare events at the end (the sinks of a
+// timed level-1 graph once the pairs are used up)
 msp_status msp_profiler_reserve(msp_ctx* ctx, int pairs) {
-    if (ctx->n_events >= 2 * pairs) return MSP_OK;
+    const int want = 2 * pairs + 4;
+    if (ctx->n_events >= want) return MSP_OK;
     for (int i = 0; i < ctx->n_events; ++i) cudaEventDestroy(ctx->events[i]);
     delete[] ctx->events;
-    ctx->events = new cudaEvent_t[2 * pairs];
+    ctx->events = new cudaEvent_t[want];
     ctx->n_events = 0;
-    for (int i = 0; i < 2 * pairs; ++i) {
+    for (int i = 0; i < want; ++i) {
         MSP_CUDA_TRY(ctx, cudaEventCreate(&ctx->events[i]));
         ctx->n_events = i + 1;
     }
@@ -1068,7 +1274,7 @@ msp_status msp_profiler_reserve(msp_ctx* ctx, int pairs) {
 
 msp_status Profiler::begin(int slot) {
     if (!on) return MSP_OK;
-    if (used >= 4096 || 2 * used + 1 >= ctx->n_events) return MSP_OK;
+    if (used >= 4096 || 2 * used + 1 >= ctx->n_events - 4) return MSP_OK;
     slot_of[used] = slot;
     MSP_CUDA_TRY(ctx, cudaEventRecord(ctx->events[2 * used], ctx->stream));
     return MSP_OK;
@@ -1076,24 +1282,41 @@ msp_status Profiler::begin(int slot) {
 
 msp_status Profiler::end() {
     if (!on) return MSP_OK;
-    if (used >= 4096 || 2 * used + 1 >= ctx->n_events) return MSP_OK;
+    if (used >= 4096 || 2 * used + 1 >= ctx->n_events - 4) return MSP_OK;
     MSP_CUDA_TRY(ctx, cudaEventRecord(ctx->events[2 * used + 1], ctx->stream));
     ++used;
     return MSP_OK;
 }
 
-msp_status Profiler::finish(ProfSlot* slots, int nslots) {
+bool Profiler::take(int slot, cudaEvent_t* b, cudaEvent_t* e) {
+    if (!on || used >= 4096 || 2 * used + 1 >= ctx->n_events - 4) return false;
+    slot_of[used] = slot;
+    *b = ctx->events[2 * used];
+    *e = ctx->events[2 * used + 1];
+    ++used;
+    return true;
+}
+
+msp_status Profiler::harvest(ProfSlot* slots, int nslots, int upto) {
     if (!on) return MSP_OK;
-    MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-    for (int i = 0; i < used; ++i) {
+    for (int i = harvested; i < upto && i < used; ++i) {
         float ms = 0.f;
         MSP_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->events[2 * i], ctx->events[2 * i + 1]));
         if (slot_of[i] < nslots) {
             slots[slot_of[i]].ms += ms;
             slots[slot_of[i]].launches += 1;
         }
+        harvested = i + 1;
     }
+    return MSP_OK;
+}
+
+msp_status Profiler::finish(ProfSlot* slots, int nslots, int keep) {
+    if (!on) return MSP_OK;
+    MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    MSP_TRY(harvest(slots, nslots, (keep >= 0 && keep < used) ? keep : used));
     used = 0;
+    harvested = 0;
     return MSP_OK;
 }
 

@@ -43,8 +43,19 @@ struct msp_ctx {
     cudaStream_t fac_side[8] = {};
     cudaEvent_t fac_ev[8][2] = {};
     bool fac_overlap = true;     // false: the factor's products stay on the main stream
-    bool gram_tc = true;
-    bool sketch_sym = true;     // FP32 sketch pass by the symmetric one-pass kernel         // M2 Gram on the tensor cores (false: FP32 pipe, compensated)
+    bool gram_tc = true;         // M2 Gram on the tensor cores (false: FP32 pipe, compensated)
+    bool sketch_sym = true;      // FP32 sketch pass by the symmetric one-pass kernel
+    // level-1 iterations of msp_solve replayed as a CUDA graph (capture
+    // stream, cached executable, its key and profiling event nodes)
+    bool l1_graphs = true;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t l1_graph = nullptr;
+    cudaGraphExec_t l1_exec = nullptr;
+    unsigned char l1_key[512] = {};
+    size_t l1_key_len = 0;
+    cudaGraphNode_t l1_ev_nodes[4] = {};
+    int l1_kernels = 0;
+    int64_t l1_graph_iters = 0;  // level-1 iterations replayed from the graph
     int hutch_terms = 2;         // tensor-core Hutchinson: 2 = two FP16 terms, 3 = three BF16 terms
     msp_ctx** lanes = nullptr;
     cudaStream_t* lane_streams = nullptr;
@@ -99,8 +110,8 @@ struct msp_factor_s {
 
 // Device control block layout (one per context).
 struct CtlBlock {
-    unsigned int bar_count;
-    unsigned int bar_gen;
+    unsigned int bar_word;      // grid barrier: generation << 16 | arrivals
+    unsigned int bar_spare;
     unsigned int last_block_counter;
     int done;           // level-1 solve converged
     int error;          // msp_status-like error code set on device
@@ -213,32 +224,36 @@ __device__ inline unsigned long long grid_wait_limit_ns() {
     return *reinterpret_cast<volatile unsigned long long*>(&g_grid_wait_limit_ns);
 }
 
-// Grid-wide barrier for a cooperative (co-resident) launch. Sense via a
-// generation counter; bounded in wall-clock time: on timeout it records
+// Grid-wide barrier for a cooperative (co-resident) launch. One word holds
+// the arrival count (low 16 bits) and the generation (high 16 bits): thread
+// 0 of every block arrives with one acq_rel atomic add, the last arrival
+// adds 2^16 - G (count back to zero, generation + 1) with release
+// semantics, the others poll the word with acquire loads until the
+// generation moves. One round trip to L2 per arrival (no separate read of
+// the generation) and no fence after the wait (the acquire load orders the
+// block's later reads); the block barriers on both sides carry the order to
+// the other threads. Bounded in wall-clock time: on timeout it records
 // MSP_ETIMEOUT in *err and returns false. All blocks must call it equally
-// often. Uses acquire/release atomics at device scope.
-__device__ inline bool grid_barrier(unsigned int* count, unsigned int* gen, int* err) {
+// often; at most 65535 blocks.
+__device__ inline bool grid_barrier(unsigned int* word, int* err) {
     __syncthreads();
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
         int ok = 1;
-        unsigned int g;
+        const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
         __threadfence();
-        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(gen) : "memory");
-        unsigned int arrived;
-        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
-                     : "=r"(arrived) : "l"(count) : "memory");
-        if (arrived == gridDim.x * gridDim.y * gridDim.z - 1) {
-            asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" :: "l"(count) : "memory");
-            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" :: "l"(gen) : "memory");
+        unsigned int old;
+        asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(word) : "memory");
+        if ((old & 0xFFFFu) == nb - 1) {
+            asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(word), "r"(0x10000u - nb) : "memory");
         } else {
             const uint64_t t0 = globaltimer_ns();
             const unsigned long long limit = grid_wait_limit_ns();
             unsigned int cur;
             int spins = 0;
             while (true) {
-                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(gen) : "memory");
-                if (cur != g) break;
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(word) : "memory");
+                if ((cur ^ old) >> 16) break;
                 // the clock after every unsuccessful poll (one register read)
                 if (globaltimer_ns() - t0 > limit) {
                     atomicExch(err, (int)MSP_ETIMEOUT);
@@ -248,7 +263,6 @@ __device__ inline bool grid_barrier(unsigned int* count, unsigned int* gen, int*
                 if (++spins > 16) __nanosleep(40);
             }
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();
@@ -364,9 +378,19 @@ struct Profiler {
     int slot_of[4096];
     msp_status begin(int slot);
     msp_status end();
-    msp_status finish(ProfSlot* slots, int nslots);
+    // the event pair of the next timed launch, for the event-record nodes of
+    // a graph (false once the pool is full: that launch goes untimed)
+    bool take(int slot, cudaEvent_t* b, cudaEvent_t* e);
+    // adds the launches [harvested, upto) to the slots; their events must
+    // have completed (the host may call it while later work runs)
+    int harvested = 0;
+    msp_status harvest(ProfSlot* slots, int nslots, int upto);
+    // syncs, then sums the first `keep` timed launches (all when keep < 0)
+    msp_status finish(ProfSlot* slots, int nslots, int keep = -1);
 };
 msp_status msp_profiler_reserve(msp_ctx* ctx, int pairs);
+// frees the context's level-1 graph (deferred by CUDA while replays run)
+void msp_l1_graph_release(msp_ctx* ctx);
 msp_status msp_norm2(msp_ctx* ctx, const double* v, int64_t n, double* out_dev);
 msp_status msp_scale_cast(msp_ctx* ctx, const double* src, const double* nrm2, int64_t n,
                           msp_dtype dt, void* dst);

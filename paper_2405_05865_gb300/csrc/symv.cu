@@ -354,9 +354,18 @@ __global__ void __launch_bounds__(kSymvThreads, 1) k_symv_packed(SymvArgs a) {
     __syncthreads();
     if (!am_last) return;
     __threadfence();
+    // the G block partials with all loads in flight together (not one
+    // thread's chain of L2 round trips): strided per thread, then the warp
+    // tree and the warps in order (a fixed order)
+    double all = 0.0;
+    for (int b = threadIdx.x; b < G; b += blockDim.x) all += __ldcg(&a.dpart[b]);
+    all = msp::warp_sum(all);
+    __syncthreads();
+    if (lane == 0) red[warp] = all;
+    __syncthreads();
     if (threadIdx.x == 0) {
-        double all = 0.0;
-        for (int b = 0; b < G; ++b) all += __ldcg(&a.dpart[b]);
+        all = 0.0;
+        for (int w = 0; w < kConsumerWarps + 1; ++w) all += red[w];
         ctl->last_block_counter = 0;
         ctl->pq = all;
         if (s_abort) { /* error already recorded */ }
