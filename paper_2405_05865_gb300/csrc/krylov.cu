@@ -645,47 +645,62 @@ __global__ void __launch_bounds__(kThreads, 1) k_level2(L2Args<T, TC> a) {
     if (a.mode == MODE_ITER && a.qpart) {
         // q_i = sum over the packed A pass's slot partials + lam p_i, fixed
         // summation order. Rounds of four 32-row groups: every thread sums
-        // its slot group for the four rows with all their loads in flight,
-        // warp g finishes group g, and warp 0 adds the squares of the new
-        // r_i row by row in group order.
+        // its slot group for the four rows, the loads of all four rows in
+        // flight together (eight slots per row at a time), warp g finishes
+        // group g (its p_i, r_i, x_i loaded before the slot partials), and
+        // warp 0 adds the squares of the new r_i row by row in group order.
         constexpr int kGroups = 4;
         T* sq = swarp;  // kGroups x 8 x 32 scratch (swarp holds 8 s_pad >= 1024 values; free here)
         T* rnew = reinterpret_cast<T*>(red2);   // kGroups x 32 new r_i (red2 is free here)
         const int rl = threadIdx.x & 31, grp = threadIdx.x >> 5;
         for (int64_t base = row0; base < row1; base += 32 * kGroups) {
+            const int64_t i_own = base + 32 * grp + rl;      // the row this thread finishes (grp < kGroups)
+            const bool own = grp < kGroups && i_own < row1;
+            T p_own = T(0), r_own = T(0), x_own = T(0);
+            if (own) {
+                p_own = a.p[i_own];
+                r_own = a.r[i_own];
+                x_own = a.x[i_own];
+            }
             T v[kGroups];
 #pragma unroll
-            for (int g = 0; g < kGroups; ++g) {
-                const int64_t i = base + 32 * g + rl;
-                v[g] = T(0);
-                if (i < row1) {
-                    int sl = grp;
-                    for (; sl + 7 * kNW < a.q_slots; sl += 8 * kNW) {
-                        T t8[8];
+            for (int g = 0; g < kGroups; ++g) v[g] = T(0);
+            int sl = grp;
+            for (; sl + 7 * kNW < a.q_slots; sl += 8 * kNW) {
+                T t8[kGroups][8];
 #pragma unroll
-                        for (int u = 0; u < 8; ++u)
-                            t8[u] = __ldcg(&a.qpart[(int64_t)(sl + u * kNW) * a.q_ld + i]);
+                for (int g = 0; g < kGroups; ++g) {
+                    const int64_t i = base + 32 * g + rl;
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) v[g] += t8[u];
-                    }
-                    for (; sl < a.q_slots; sl += kNW) v[g] += __ldcg(&a.qpart[(int64_t)sl * a.q_ld + i]);
+                    for (int u = 0; u < 8; ++u)
+                        t8[g][u] = (i < row1) ? __ldcg(&a.qpart[(int64_t)(sl + u * kNW) * a.q_ld + i]) : T(0);
+                }
+#pragma unroll
+                for (int g = 0; g < kGroups; ++g)
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) v[g] += t8[g][u];
+            }
+            for (; sl < a.q_slots; sl += kNW) {
+#pragma unroll
+                for (int g = 0; g < kGroups; ++g) {
+                    const int64_t i = base + 32 * g + rl;
+                    if (i < row1) v[g] += __ldcg(&a.qpart[(int64_t)sl * a.q_ld + i]);
                 }
             }
 #pragma unroll
             for (int g = 0; g < kGroups; ++g) sq[(g * kNW + grp) * 32 + rl] = v[g];
             __syncthreads();
             if (grp < kGroups) {
-                const int64_t i = base + 32 * grp + rl;
                 T ri = T(0);
-                if (i < row1) {
+                if (own) {
                     T qi = T(0);
 #pragma unroll
                     for (int g = 0; g < kNW; ++g) qi += sq[(grp * kNW + g) * 32 + rl];
-                    qi += a.lam * a.p[i];
-                    ri = a.r[i];
-                    a.x[i] += (T)alpha * a.p[i];
+                    qi += a.lam * p_own;
+                    ri = r_own;
+                    a.x[i_own] = x_own + (T)alpha * p_own;
                     ri -= (T)alpha * qi;
-                    a.r[i] = ri;
+                    a.r[i_own] = ri;
                 }
                 rnew[grp * 32 + rl] = ri;
             }
@@ -982,14 +997,14 @@ int gemv_grid(msp_ctx* ctx) { return ctx->num_sms * 8; }
 // context under a key of everything the launches were built from (argument
 // structs, buffers, grid sizes); any change rebuilds it.
 
-constexpr int kL1Timed = 4;     // event-record nodes of a timed iteration graph
+constexpr int kL1Timed = 2;     // event-record nodes of a timed iteration graph
 
 // Captures iter(true) (launches on ctx->stream, redirected to the capture
-// stream) as the context's level-1 graph for `key`. With `timed`, iter
-// brackets each launch by event-record nodes on ctx->events[0..3], found
-// again here by their events so that each replay can point them at fresh
-// events. Leaves ctx->l1_exec null where capture is not possible; the
-// caller then launches on the stream.
+// stream) as the context's level-1 graph for `key`. With `timed`, iter puts
+// an event-record node before the A pass and one between the A pass and the
+// level-2 kernel (ctx->events[0..1]), found again here by their events so
+// that each replay can point them at fresh events. Leaves ctx->l1_exec null
+// where capture is not possible; the caller then launches on the stream.
 template <typename F>
 msp_status ensure_l1_graph(msp_ctx* ctx, const void* key, size_t klen, bool timed, F&& iter) {
     if (ctx->l1_exec && ctx->l1_key_len == klen && std::memcmp(ctx->l1_key, key, klen) == 0)
@@ -1050,20 +1065,47 @@ msp_status ensure_l1_graph(msp_ctx* ctx, const void* key, size_t klen, bool time
     return MSP_OK;
 }
 
-// Points the event-record nodes of the timed graph at the profiler's next
-// two event pairs (the spare events past the pool once it is full), then
-// replays one iteration. Already queued replays keep their events.
-msp_status replay_l1(msp_ctx* ctx, Profiler& pr) {
+// Replays one level-1 iteration. Timed: the graph's two event-record nodes
+// get fresh events b (before the A pass) and e (after it); the A pass is
+// the entry (b, e), and the level-2 kernel of the iteration before, whose
+// end the new b marks, the entry (e_prev, b): two events per iteration.
+// *l2_open holds e of the last replay until then (-1: none); the spare
+// events past the pool stand in once it is used up. Already queued replays
+// keep their events.
+msp_status replay_l1(msp_ctx* ctx, Profiler& pr, int* l2_open) {
     if (pr.on) {
-        cudaEvent_t e[kL1Timed];
-        for (int k = 0; k < kL1Timed; ++k) e[k] = ctx->events[ctx->n_events - kL1Timed + k];
-        if (pr.take(0, &e[0], &e[1])) pr.take(1, &e[2], &e[3]);
-        for (int k = 0; k < kL1Timed; ++k)
-            MSP_CUDA_TRY(ctx, cudaGraphExecEventRecordNodeSetEvent(ctx->l1_exec, ctx->l1_ev_nodes[k], e[k]));
+        cudaEvent_t eb = ctx->events[ctx->n_events - 2], ee = ctx->events[ctx->n_events - 1];
+        int ib = -1, ie = -1;
+        const bool fresh = pr.take(&eb, &ib) && pr.take(&ee, &ie);
+        if (!fresh) {
+            eb = ctx->events[ctx->n_events - 2];
+            ee = ctx->events[ctx->n_events - 1];
+        }
+        MSP_CUDA_TRY(ctx, cudaGraphExecEventRecordNodeSetEvent(ctx->l1_exec, ctx->l1_ev_nodes[0], eb));
+        MSP_CUDA_TRY(ctx, cudaGraphExecEventRecordNodeSetEvent(ctx->l1_exec, ctx->l1_ev_nodes[1], ee));
+        if (fresh) {
+            if (*l2_open >= 0) pr.add(1, *l2_open, ib);
+            pr.add(0, ib, ie);
+        }
+        *l2_open = fresh ? ie : -1;
     }
     MSP_CUDA_TRY(ctx, cudaGraphLaunch(ctx->l1_exec, ctx->stream));
     ctx->launches += ctx->l1_kernels;
     ++ctx->l1_graph_iters;
+    return MSP_OK;
+}
+
+// Ends the timing chain after the last replay of a check interval: an event
+// on the stream closes the open level-2 entry.
+msp_status close_l1_chain(msp_ctx* ctx, Profiler& pr, int* l2_open) {
+    if (!pr.on || *l2_open < 0) return MSP_OK;
+    cudaEvent_t ev;
+    int idx;
+    if (pr.take(&ev, &idx)) {
+        MSP_CUDA_TRY(ctx, cudaEventRecord(ev, ctx->stream));
+        pr.add(1, *l2_open, idx);
+    }
+    *l2_open = -1;
     return MSP_OK;
 }
 
@@ -1116,7 +1158,9 @@ msp_status krylov_solve_t(msp_ctx* ctx, const msp_factor_s* f, const void* A, ms
     auto mark = [&](bool cap, int k) -> msp_status {
         if (!pr.on) return MSP_OK;
         if (cap) {
-            MSP_CUDA_TRY(ctx, cudaEventRecordWithFlags(ctx->events[k], ctx->stream, cudaEventRecordExternal));
+            // event-record nodes before the A pass and between the launches
+            if (k < kL1Timed)
+                MSP_CUDA_TRY(ctx, cudaEventRecordWithFlags(ctx->events[k], ctx->stream, cudaEventRecordExternal));
             return MSP_OK;
         }
         return (k & 1) ? pr.end() : pr.begin(k >> 1);
@@ -1178,13 +1222,14 @@ msp_status krylov_solve_t(msp_ctx* ctx, const msp_factor_s* f, const void* A, ms
     // profiler entries of iterations known to have run to completion with
     // work (every iteration before a check that found no flag): read while
     // the next interval runs, not after it
-    int settled = 0;
+    int settled = 0, l2_open = -1;
     for (int it = 0; it < max_outer;) {
         const int nrun = std::min(check, max_outer - it);
         for (int i = 0; i < nrun; ++i) {
-            if (graphed) MSP_TRY(replay_l1(ctx, pr));
+            if (graphed) MSP_TRY(replay_l1(ctx, pr, &l2_open));
             else MSP_TRY(iteration(false));
         }
+        if (graphed) MSP_TRY(close_l1_chain(ctx, pr, &l2_open));
         it += nrun;
         MSP_CUDA_TRY(ctx, cudaMemcpyAsync(hf, &ctl->done, 5 * sizeof(int), cudaMemcpyDeviceToHost,
                                           ctx->stream));
@@ -1273,35 +1318,45 @@ msp_status msp_profiler_reserve(msp_ctx* ctx, int pairs) {
 }
 
 msp_status Profiler::begin(int slot) {
-    if (!on) return MSP_OK;
-    if (used >= 4096 || 2 * used + 1 >= ctx->n_events - 4) return MSP_OK;
+    open = false;
+    if (!on || used >= 4096 || next_ev + 2 > ctx->n_events - 4) return MSP_OK;
     slot_of[used] = slot;
-    MSP_CUDA_TRY(ctx, cudaEventRecord(ctx->events[2 * used], ctx->stream));
+    ev_b[used] = next_ev++;
+    open = true;
+    MSP_CUDA_TRY(ctx, cudaEventRecord(ctx->events[ev_b[used]], ctx->stream));
     return MSP_OK;
 }
 
 msp_status Profiler::end() {
-    if (!on) return MSP_OK;
-    if (used >= 4096 || 2 * used + 1 >= ctx->n_events - 4) return MSP_OK;
-    MSP_CUDA_TRY(ctx, cudaEventRecord(ctx->events[2 * used + 1], ctx->stream));
+    // closes the entry of the last begin() that went through
+    if (!open) return MSP_OK;
+    open = false;
+    ev_e[used] = next_ev++;
+    MSP_CUDA_TRY(ctx, cudaEventRecord(ctx->events[ev_e[used]], ctx->stream));
     ++used;
     return MSP_OK;
 }
 
-bool Profiler::take(int slot, cudaEvent_t* b, cudaEvent_t* e) {
-    if (!on || used >= 4096 || 2 * used + 1 >= ctx->n_events - 4) return false;
-    slot_of[used] = slot;
-    *b = ctx->events[2 * used];
-    *e = ctx->events[2 * used + 1];
-    ++used;
+bool Profiler::take(cudaEvent_t* ev, int* idx) {
+    if (!on || next_ev + 1 > ctx->n_events - 4) return false;
+    *idx = next_ev++;
+    *ev = ctx->events[*idx];
     return true;
+}
+
+void Profiler::add(int slot, int b, int e) {
+    if (!on || used >= 4096) return;
+    slot_of[used] = slot;
+    ev_b[used] = b;
+    ev_e[used] = e;
+    ++used;
 }
 
 msp_status Profiler::harvest(ProfSlot* slots, int nslots, int upto) {
     if (!on) return MSP_OK;
     for (int i = harvested; i < upto && i < used; ++i) {
         float ms = 0.f;
-        MSP_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->events[2 * i], ctx->events[2 * i + 1]));
+        MSP_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, ctx->events[ev_b[i]], ctx->events[ev_e[i]]));
         if (slot_of[i] < nslots) {
             slots[slot_of[i]].ms += ms;
             slots[slot_of[i]].launches += 1;
@@ -1317,6 +1372,7 @@ msp_status Profiler::finish(ProfSlot* slots, int nslots, int keep) {
     MSP_TRY(harvest(slots, nslots, (keep >= 0 && keep < used) ? keep : used));
     used = 0;
     harvested = 0;
+    next_ev = 0;
     return MSP_OK;
 }
 

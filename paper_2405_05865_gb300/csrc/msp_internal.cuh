@@ -53,7 +53,7 @@ struct msp_ctx {
     cudaGraphExec_t l1_exec = nullptr;
     unsigned char l1_key[512] = {};
     size_t l1_key_len = 0;
-    cudaGraphNode_t l1_ev_nodes[4] = {};
+    cudaGraphNode_t l1_ev_nodes[2] = {};
     int l1_kernels = 0;
     int64_t l1_graph_iters = 0;  // level-1 iterations replayed from the graph
     int hutch_terms = 2;         // tensor-core Hutchinson: 2 = two FP16 terms, 3 = three BF16 terms
@@ -370,22 +370,29 @@ msp_status msp_matvec64(msp_ctx* ctx, const void* A, msp_dtype dt, int64_t n,
                         double* out, double* norm2_out_dev, bool compensated = false);
 
 // Event timing helper: with `on`, records an event pair around each timed
-// launch; finish() sums the elapsed times (after a stream sync).
+// launch; finish() sums the elapsed times (after a stream sync). An entry is
+// a (begin, end) pair of indices into the context's event pool; entries of a
+// graph's event-record nodes may share an event (one event ends a launch and
+// begins the next).
 struct Profiler {
     msp_ctx* ctx = nullptr;
     bool on = false;
-    int used = 0;
+    int used = 0;                  // entries
+    int next_ev = 0;               // events handed out from the pool
+    bool open = false;             // begin() recorded, end() not yet
     int slot_of[4096];
+    int ev_b[4096], ev_e[4096];
     msp_status begin(int slot);
     msp_status end();
-    // the event pair of the next timed launch, for the event-record nodes of
-    // a graph (false once the pool is full: that launch goes untimed)
-    bool take(int slot, cudaEvent_t* b, cudaEvent_t* e);
-    // adds the launches [harvested, upto) to the slots; their events must
+    // the next event of the pool (false once it is used up)
+    bool take(cudaEvent_t* ev, int* idx);
+    // an entry of two events taken before
+    void add(int slot, int b, int e);
+    // adds the entries [harvested, upto) to the slots; their events must
     // have completed (the host may call it while later work runs)
     int harvested = 0;
     msp_status harvest(ProfSlot* slots, int nslots, int upto);
-    // syncs, then sums the first `keep` timed launches (all when keep < 0)
+    // syncs, then sums the first `keep` entries (all when keep < 0)
     msp_status finish(ProfSlot* slots, int nslots, int keep = -1);
 };
 msp_status msp_profiler_reserve(msp_ctx* ctx, int pairs);
