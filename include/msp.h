@@ -253,6 +253,17 @@ MSP_API msp_status msp_set_sketch_one_pass(msp_ctx* ctx, int on);
  * has no counterpart; it selects an implementation). */
 MSP_API msp_status msp_set_gram_tensor_cores(msp_ctx* ctx, int on);
 
+/* How msp_nystrom factors M2 + nu I of an FP32 sketch (Algorithm 1, step 4:
+ * the Cholesky factor and its inverse, the triangular factor the level-2
+ * kernel applies as B = L^{-1} and B^T in FP32): on = 1 (default): in
+ * float-float arithmetic on the FP32 pipe (pairs of floats, products by FMA,
+ * sums by TwoSum, about 2^-46 relative per operation) on M2 scaled by a
+ * power of four; its backward error, a small multiple of s 2^-46 |M2|, stays
+ * far below the shift nu = 2^-24 |M2|_F the FP32 data needs, and the result
+ * is rounded to FP32. on = 0: in FP64. FP64 sketches always use FP64. Not
+ * part of the method (it selects an implementation). */
+MSP_API msp_status msp_set_factor_float_float(msp_ctx* ctx, int on);
+
 /* How msp_solve issues its level-1 iterations (Algorithm 2's outer loop:
  * the A pass, then the level-2 kernel with the step, SolveM1 and the new
  * direction): on = 1 (default): the two launches of one iteration are

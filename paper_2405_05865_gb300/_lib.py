@@ -92,6 +92,7 @@ _SIGS = {
     "msp_set_grid_wait_limit": (C.c_int, [P, C.c_double]),
     "msp_set_gram_tensor_cores": (C.c_int, [P, C.c_int]),
     "msp_set_level1_graphs": (C.c_int, [P, C.c_int]),
+    "msp_set_factor_float_float": (C.c_int, [P, C.c_int]),
     "msp_set_sketch_one_pass": (C.c_int, [P, C.c_int]),
     "msp_solve_refined": (C.c_int, [P, P, P, C.c_int, I64, I64, P, C.c_int, I64, C.c_double, P, P,
                                     C.POINTER(MspOpts), C.POINTER(MspInfo)]),

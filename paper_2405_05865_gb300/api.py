@@ -373,6 +373,10 @@ class Context:
         """Level-1 iterations replayed as a CUDA graph (default) or launched one by one."""
         L.check(self.ptr, self.lib.msp_set_level1_graphs(self.ptr, int(bool(on))))
 
+    def set_factor_float_float(self, on: bool) -> None:
+        """Cholesky of an FP32 factor in float-float (default) or in FP64."""
+        L.check(self.ptr, self.lib.msp_set_factor_float_float(self.ptr, int(bool(on))))
+
     def set_gram_tensor_cores(self, on: bool) -> None:
         """M2 Gram on the tensor cores (default) or on the FP32 pipe."""
         L.check(self.ptr, self.lib.msp_set_gram_tensor_cores(self.ptr, int(bool(on))))

@@ -313,6 +313,143 @@ __global__ void __launch_bounds__(256) k_dgemm(int64_t m, int64_t n, int64_t k, 
         }
 }
 
+// ----------------------------------------------------- float-float kernels
+//
+// The factor of an FP32 sketch runs in float-float arithmetic on the FP32
+// pipe: a value is the unevaluated sum hi + lo of two floats (|lo| <= ulp(hi)
+// / 2 once normalised), a product is exact by FMA (TwoProduct, Dekker), a sum
+// by TwoSum (Knuth), about 2^-46 relative per operation. FP64 runs at 2
+// lanes per clock per SM on this part, the FP32 pipe at 128. Every operation
+// below uses the _rn intrinsics, which the compiler never contracts.
+
+__device__ __forceinline__ float2 ff_fast2sum(float a, float b) {   // needs |a| >= |b| or a = 0
+    const float s = __fadd_rn(a, b);
+    return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+__device__ __forceinline__ float2 ff_2sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+
+// (sh, sl) += a b, sl collecting the low parts until the next ff_norm
+__device__ __forceinline__ void ff_fma_acc(float& sh, float& sl, float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    const float2 t = ff_2sum(sh, p);
+    sh = t.x;
+    sl = __fadd_rn(sl, __fadd_rn(t.y, e));
+}
+
+__device__ __forceinline__ float2 ff_norm(float sh, float sl) { return ff_2sum(sh, sl); }
+
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    return ff_fast2sum(p, e);
+}
+
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+    const float2 s = ff_2sum(a.x, b.x);
+    return ff_fast2sum(s.x, __fadd_rn(s.y, __fadd_rn(a.y, b.y)));
+}
+
+__device__ __forceinline__ float2 ff_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ float2 ff_from_double(double v) {
+    const float h = __double2float_rn(v);
+    return make_float2(h, __double2float_rn(v - (double)h));
+}
+
+__device__ __forceinline__ double ff_to_double(float2 a) { return (double)a.x + (double)a.y; }
+
+// k_dgemm in float-float: the same tiling, triangular limits and lower_out,
+// operands and result stored as float2 (hi, lo). alpha is +-1 and beta 0 or
+// 1 (what the recursion uses): Cm = beta Cm +- op(A) op(B). The accumulators
+// are renormalised after every K chunk of 16.
+template <bool TA_, bool TB_, int TS>
+__global__ void __launch_bounds__(256) k_ffgemm(int64_t m, int64_t n, int64_t k, float alpha,
+                                               const float2* __restrict__ A, int64_t lda,
+                                               const float2* __restrict__ B, int64_t ldb,
+                                               int beta, float2* __restrict__ Cm, int64_t ldc,
+                                               int tri_a, int tri_b, int lower_out) {
+    constexpr int PT = TS / 16;
+    __shared__ float2 As[16][TS + 1];
+    __shared__ float2 Bs[16][TS + 1];
+    const int64_t i0 = (int64_t)blockIdx.y * TS, j0 = (int64_t)blockIdx.x * TS;
+    if (lower_out && j0 > i0 + TS - 1) return;
+    int64_t kbeg = 0, kend = k;
+    if (tri_a == 1) kend = min(kend, i0 + TS);
+    if (tri_b == 1) kend = min(kend, j0 + TS);
+    if (tri_b == 2) kbeg = (j0 / 16) * 16;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float sh[PT][PT], sl[PT][PT];
+#pragma unroll
+    for (int i = 0; i < PT; ++i)
+#pragma unroll
+        for (int j = 0; j < PT; ++j) sh[i][j] = sl[i][j] = 0.f;
+    const float2 zero = make_float2(0.f, 0.f);
+    for (int64_t k0 = kbeg; k0 < kend; k0 += 16) {
+        for (int e = threadIdx.x; e < 16 * TS; e += 256) {
+            int kk, ii;
+            if (TA_) { ii = e % TS; kk = e / TS; }
+            else { kk = e & 15; ii = e >> 4; }
+            const int64_t gi = i0 + ii, gk = k0 + kk;
+            float2 v = zero;
+            if (gi < m && gk < kend) v = TA_ ? A[gk * lda + gi] : A[gi * lda + gk];
+            As[kk][ii] = v;
+        }
+        for (int e = threadIdx.x; e < 16 * TS; e += 256) {
+            int kk, jj;
+            if (TB_) { kk = e & 15; jj = e >> 4; }
+            else { jj = e % TS; kk = e / TS; }
+            const int64_t gj = j0 + jj, gk = k0 + kk;
+            float2 v = zero;
+            if (gj < n && gk < kend) v = TB_ ? B[gj * ldb + gk] : B[gk * ldb + gj];
+            Bs[kk][jj] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+            float2 av[PT], bv[PT];
+#pragma unroll
+            for (int i = 0; i < PT; ++i) av[i] = As[kk][ty * PT + i];
+#pragma unroll
+            for (int j = 0; j < PT; ++j) bv[j] = Bs[kk][tx * PT + j];
+#pragma unroll
+            for (int i = 0; i < PT; ++i)
+#pragma unroll
+                for (int j = 0; j < PT; ++j) ff_fma_acc(sh[i][j], sl[i][j], av[i], bv[j]);
+        }
+#pragma unroll
+        for (int i = 0; i < PT; ++i)
+#pragma unroll
+            for (int j = 0; j < PT; ++j) {
+                const float2 t = ff_norm(sh[i][j], sl[i][j]);
+                sh[i][j] = t.x;
+                sl[i][j] = t.y;
+            }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < PT; ++i)
+#pragma unroll
+        for (int j = 0; j < PT; ++j) {
+            const int64_t gi = i0 + ty * PT + i, gj = j0 + tx * PT + j;
+            if (gi < m && gj < n) {
+                float2 r = make_float2(sh[i][j], sl[i][j]);
+                if (alpha < 0.f) r = ff_neg(r);
+                if (beta) r = ff_add(Cm[gi * ldc + gj], r);
+                Cm[gi * ldc + gj] = r;
+            }
+        }
+}
+
 constexpr int kLeafSmem = 2 * 64 * 65 * (int)sizeof(double);
 constexpr int kLeafUpd = 256;                 // eight update warps (32 x 8 thread grid)
 constexpr int kLeafThreads = kLeafUpd + 32;   // and the pivot warp
@@ -432,12 +569,133 @@ __global__ void __launch_bounds__(kLeafThreads) k_chol_leaf(double* __restrict__
     if (tid == 0 && bad) atomicExch(fail, 1);
 }
 
+// 1/d in float-float for a positive normal d: the FP32 reciprocal r0, then
+// one Newton-Raphson step r = r0 + r0 (1 - d r0) with the residual 1 - d r0
+// formed exactly to first order (1 - hi(d r0) is exact: d r0 is within
+// 2^-23 of 1), ~2^-46 relative.
+__device__ __forceinline__ float2 ff_rcp(float2 d) {
+    const float r0 = __frcp_rn(d.x);
+    const float p = __fmul_rn(d.x, r0);
+    const float pe = __fmaf_rn(d.y, r0, __fmaf_rn(d.x, r0, -p));
+    const float res = __fsub_rn(__fsub_rn(1.0f, p), pe);
+    return ff_fast2sum(r0, __fmul_rn(r0, res));
+}
+
+// k_chol_leaf in float-float (same elimination, thread layout and pivot
+// warp; the block and its inverse in shared memory as float2): M = L L^T,
+// X = L^{-1}, both float2 with leading dimension ld. d_k^{-1/2} is formed in
+// FP64 (once per pivot), the final scaling in float-float.
+__global__ void __launch_bounds__(kLeafThreads) k_chol_leaf_ff(float2* __restrict__ M, float2* __restrict__ X,
+                                                              int64_t ld, int nb, int* __restrict__ fail) {
+    extern __shared__ __align__(16) float2 leaf_smem_ff[];
+    float2 (*a)[65] = reinterpret_cast<float2 (*)[65]>(leaf_smem_ff);
+    float2 (*x)[65] = reinterpret_cast<float2 (*)[65]>(leaf_smem_ff + 64 * 65);
+    __shared__ float2 piv[64], rinv[64], rs[64];
+    __shared__ int bad;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const bool pivot_warp = tid >= kLeafUpd;
+    const float2 zero = make_float2(0.f, 0.f), one = make_float2(1.f, 0.f);
+    if (tid == 0) bad = 0;
+    for (int e = tid; e < nb * nb; e += kLeafThreads) {
+        const int i = e / nb, j = e % nb;
+        a[i][j] = (j <= i) ? M[i * ld + j] : zero;
+        x[i][j] = (i == j) ? one : zero;
+    }
+    __syncthreads();
+    auto pivot_ok = [](float2 d) { return d.x > 0.f && isfinite(d.x); };
+    float2 dg0 = one, dg1 = one;
+    if (pivot_warp) {
+        if (lane < nb) dg0 = a[lane][lane];
+        if (lane + 32 < nb) dg1 = a[lane + 32][lane + 32];
+        if (lane == 0) {
+            float2 d = dg0;
+            if (!pivot_ok(d)) {
+                bad = 1;
+                d = one;
+            }
+            piv[0] = d;
+            rinv[0] = ff_rcp(d);
+        }
+    }
+    __syncthreads();
+    const int tx = tid & 7, ty = tid >> 3;
+    const int rr = ((ty & 3) << 3) | (ty >> 2);
+    for (int k = 0; k < nb; ++k) {
+        const float2 rk = rinv[k];
+        if (!pivot_warp) {
+            for (int i = k + 1 + rr; i < nb; i += 32) {
+                const float2 nti = ff_neg(ff_mul(a[i][k], rk));
+                for (int j = tx; j <= k; j += 8) {
+                    float h = x[i][j].x, l = x[i][j].y;
+                    ff_fma_acc(h, l, nti, x[k][j]);
+                    x[i][j] = ff_norm(h, l);
+                }
+                for (int j = k + 1 + tx; j < i; j += 8) {
+                    float h = a[i][j].x, l = a[i][j].y;
+                    ff_fma_acc(h, l, nti, a[j][k]);
+                    a[i][j] = ff_norm(h, l);
+                }
+            }
+        } else if (k + 1 < nb) {
+            if (lane > k && lane < nb) {
+                const float2 nti = ff_neg(ff_mul(a[lane][k], rk));
+                float h = dg0.x, l = dg0.y;
+                ff_fma_acc(h, l, nti, a[lane][k]);
+                dg0 = ff_norm(h, l);
+            }
+            if (lane + 32 > k && lane + 32 < nb) {
+                const float2 nti = ff_neg(ff_mul(a[lane + 32][k], rk));
+                float h = dg1.x, l = dg1.y;
+                ff_fma_acc(h, l, nti, a[lane + 32][k]);
+                dg1 = ff_norm(h, l);
+            }
+            const int kn = k + 1;
+            if (lane == (kn & 31)) {
+                float2 d = kn < 32 ? dg0 : dg1;
+                if (!pivot_ok(d)) {
+                    bad = 1;
+                    d = one;
+                }
+                piv[kn] = d;
+                rinv[kn] = ff_rcp(d);
+            }
+        }
+        __syncthreads();
+    }
+    for (int k = tid; k < nb; k += kLeafThreads) rs[k] = ff_from_double(rsqrt_newton(ff_to_double(piv[k])));
+    __syncthreads();
+    for (int e = tid; e < nb * nb; e += kLeafThreads) {
+        const int i = e / nb, j = e % nb;
+        if (j < i) M[i * ld + j] = ff_mul(a[i][j], rs[j]);
+        else if (j == i) M[i * ld + j] = ff_mul(piv[i], rs[i]);
+        X[i * ld + j] = (j <= i) ? ff_mul(x[i][j], rs[i]) : zero;
+    }
+    if (tid == 0 && bad) atomicExch(fail, 1);
+}
+
 __global__ void k_copy_add_diag(const double* __restrict__ src, double* __restrict__ dst,
                                 int64_t s_pad, double nu) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= s_pad * s_pad) return;
     int64_t i = e / s_pad, j = e % s_pad;
     dst[e] = src[e] + ((i == j) ? nu : 0.0);
+}
+
+// dst = float-float of (src + nu I) scale (scale a power of two: exact)
+__global__ void k_copy_add_diag_ff(const double* __restrict__ src, float2* __restrict__ dst,
+                                   int64_t s_pad, double nu, double scale) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= s_pad * s_pad) return;
+    int64_t i = e / s_pad, j = e % s_pad;
+    dst[e] = ff_from_double((src[e] + ((i == j) ? nu : 0.0)) * scale);
+}
+
+// dst = src scale in FP64 (scale a power of two)
+__global__ void k_ff_to_double(const float2* __restrict__ src, double* __restrict__ dst, int64_t count,
+                               double scale) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= count) return;
+    dst[e] = ff_to_double(src[e]) * scale;
 }
 
 // Frobenius norm^2 partials (single block, deterministic order).
@@ -505,39 +763,87 @@ msp_status dgemm(msp_ctx* ctx, bool ta, bool tb, int64_t m, int64_t n, int64_t k
     return MSP_OK;
 }
 
+template <int TS>
+void launch_ffgemm_ts(msp_ctx* ctx, bool ta, bool tb, int64_t m, int64_t n, int64_t k, float alpha,
+                      const float2* A, int64_t lda, const float2* B, int64_t ldb, int beta,
+                      float2* Cm, int64_t ldc, int tri_a, int tri_b, int lower_out) {
+    dim3 grid((unsigned)((n + TS - 1) / TS), (unsigned)((m + TS - 1) / TS));
+    if (!ta && !tb) k_ffgemm<false, false, TS><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, A, lda, B, ldb, beta, Cm, ldc, tri_a, tri_b, lower_out);
+    else if (!ta && tb) k_ffgemm<false, true, TS><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, A, lda, B, ldb, beta, Cm, ldc, tri_a, tri_b, lower_out);
+    else if (ta && !tb) k_ffgemm<true, false, TS><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, A, lda, B, ldb, beta, Cm, ldc, tri_a, tri_b, lower_out);
+    else k_ffgemm<true, true, TS><<<grid, 256, 0, ctx->stream>>>(m, n, k, alpha, A, lda, B, ldb, beta, Cm, ldc, tri_a, tri_b, lower_out);
+}
+
+// The recursion's products on the two storages: FP64, or float-float
+// (alpha +-1, beta 0 or 1).
+msp_status gemm_s(msp_ctx* ctx, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha,
+                  const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                  double* Cm, int64_t ldc, int tri_a, int tri_b, int lower_out) {
+    return dgemm(ctx, ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, Cm, ldc, tri_a, tri_b, lower_out);
+}
+
+msp_status gemm_s(msp_ctx* ctx, bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha,
+                  const float2* A, int64_t lda, const float2* B, int64_t ldb, double beta,
+                  float2* Cm, int64_t ldc, int tri_a, int tri_b, int lower_out) {
+    if (!(alpha == 1.0 || alpha == -1.0) || !(beta == 0.0 || beta == 1.0))
+        return msp_set_error(ctx, MSP_EINVAL, "factor: float-float product needs alpha = +-1, beta = 0 or 1");
+    // the FP32 pipe has room for the larger tile once it fills the SMs
+    const int64_t tiles32 = ((m + 31) / 32) * ((n + 31) / 32);
+    if (tiles32 >= ctx->num_sms)
+        launch_ffgemm_ts<32>(ctx, ta, tb, m, n, k, (float)alpha, A, lda, B, ldb, (int)beta, Cm, ldc, tri_a, tri_b, lower_out);
+    else
+        launch_ffgemm_ts<16>(ctx, ta, tb, m, n, k, (float)alpha, A, lda, B, ldb, (int)beta, Cm, ldc, tri_a, tri_b, lower_out);
+    MSP_CHECK_LAUNCH(ctx);
+    return MSP_OK;
+}
+
+template <typename Kern>
+msp_status leaf_attr(msp_ctx* ctx, Kern kern, std::atomic<bool>* attr_set) {
+    // set once per device; batch set-up calls this from several threads
+    const int d = ctx->device;
+    if (d < 0 || d >= 64 || !attr_set[d].load()) {
+        MSP_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kLeafSmem));
+        if (d >= 0 && d < 64) attr_set[d] = true;
+    }
+    return MSP_OK;
+}
+
+msp_status leaf_s(msp_ctx* ctx, double* M, double* X, int64_t ld, int64_t n, int* fail) {
+    static std::atomic<bool> attr_set[64];
+    MSP_TRY(leaf_attr(ctx, k_chol_leaf, attr_set));
+    k_chol_leaf<<<1, kLeafThreads, kLeafSmem, ctx->stream>>>(M, X, ld, (int)n, fail);
+    MSP_CHECK_LAUNCH(ctx);
+    return MSP_OK;
+}
+
+msp_status leaf_s(msp_ctx* ctx, float2* M, float2* X, int64_t ld, int64_t n, int* fail) {
+    static std::atomic<bool> attr_set[64];
+    MSP_TRY(leaf_attr(ctx, k_chol_leaf_ff, attr_set));
+    k_chol_leaf_ff<<<1, kLeafThreads, kLeafSmem, ctx->stream>>>(M, X, ld, (int)n, fail);
+    MSP_CHECK_LAUNCH(ctx);
+    return MSP_OK;
+}
+
 // Recursive Cholesky + inverse of the n x n block at offset `off` of M (ld),
 // inverse into X (same offsets); T1/T2 are n x n temporaries (ld). Only X =
 // L^{-1} is kept: M is scratch (the Schur complements overwrite its lower
 // triangle, the leaves leave their L blocks there, L21 is not stored). Leaves
 // of at most 32: a leaf runs on one SM, whose FP64 pipe bounds it (its work
 // grows as nb^3), while the products of the recursion spread over all SMs.
-msp_status chol_inv(msp_ctx* ctx, double* M, double* X, double* T1, double* T2, int64_t ld,
+template <typename S>
+msp_status chol_inv(msp_ctx* ctx, S* M, S* X, S* T1, S* T2, int64_t ld,
                     int64_t off, int64_t n, int* fail, int depth) {
-    if (n <= 32) {
-        // set once per device; batch set-up calls this from several threads
-        static std::atomic<bool> attr_set[64];
-        const int d = ctx->device;
-        if (d < 0 || d >= 64 || !attr_set[d].load()) {
-            MSP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_chol_leaf,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   kLeafSmem));
-            if (d >= 0 && d < 64) attr_set[d] = true;
-        }
-        k_chol_leaf<<<1, kLeafThreads, kLeafSmem, ctx->stream>>>(M + off * ld + off, X + off * ld + off, ld,
-                                                         (int)n, fail);
-        MSP_CHECK_LAUNCH(ctx);
-        return MSP_OK;
-    }
+    if (n <= 32) return leaf_s(ctx, M + off * ld + off, X + off * ld + off, ld, n, fail);
     int64_t n1 = std::max<int64_t>(32, (n / 2) / 32 * 32);
     int64_t n2 = n - n1;
-    double* A21 = M + (off + n1) * ld + off;
-    double* A22 = M + (off + n1) * ld + off + n1;
-    double* X11 = X + off * ld + off;
-    double* X21 = X + (off + n1) * ld + off;
-    double* X22 = X + (off + n1) * ld + off + n1;
+    S* A21 = M + (off + n1) * ld + off;
+    S* A22 = M + (off + n1) * ld + off + n1;
+    S* X11 = X + off * ld + off;
+    S* X21 = X + (off + n1) * ld + off;
+    S* X22 = X + (off + n1) * ld + off + n1;
     MSP_TRY(chol_inv(ctx, M, X, T1, T2, ld, off, n1, fail, depth + 1));
     // T1 = L21 = A21 X11^T   (n2 x n1; X11^T is upper triangular)
-    MSP_TRY(dgemm(ctx, false, true, n2, n1, n1, 1.0, A21, ld, X11, ld, 0.0, T1, ld, 0, 1, 0));
+    MSP_TRY(gemm_s(ctx, false, true, n2, n1, n1, 1.0, A21, ld, X11, ld, 0.0, T1, ld, 0, 1, 0));
     // T2 = L21 X11 (X11 lower) needs only T1 and X11, so it runs on the side
     // stream of this depth while A22 is updated and factored on the main
     // stream. Disjoint memory: T1 and T2 hold columns [0, n1) of the
@@ -568,27 +874,27 @@ msp_status chol_inv(msp_ctx* ctx, double* M, double* X, double* T1, double* T2, 
     if (side) {
         cudaStream_t main_stream = ctx->stream;
         ctx->stream = side;
-        st = dgemm(ctx, false, false, n2, n1, n1, 1.0, T1, ld, X11, ld, 0.0, T2, ld, 0, 2, 0);
+        st = gemm_s(ctx, false, false, n2, n1, n1, 1.0, T1, ld, X11, ld, 0.0, T2, ld, 0, 2, 0);
         ctx->stream = main_stream;
         if (st == MSP_OK && cudaEventRecord(ev_t2, side) != cudaSuccess)
             st = msp_set_error(ctx, MSP_ECUDA, "factor: side stream record failed");
     }
     // A22 -= L21 L21^T (lower triangle is all the recursion reads)
     if (st == MSP_OK)
-        st = dgemm(ctx, false, true, n2, n2, n1, -1.0, T1, ld, T1, ld, 1.0, A22, ld, 0, 0, 1);
+        st = gemm_s(ctx, false, true, n2, n2, n1, -1.0, T1, ld, T1, ld, 1.0, A22, ld, 0, 0, 1);
     if (st == MSP_OK) st = chol_inv(ctx, M, X, T1 + n1, T2 + n1, ld, off + n1, n2, fail, depth + 1);
     if (st == MSP_OK) {
         if (side) {
             if (cudaStreamWaitEvent(ctx->stream, ev_t2, 0) != cudaSuccess)
                 st = msp_set_error(ctx, MSP_ECUDA, "factor: side stream join failed");
         } else {
-            st = dgemm(ctx, false, false, n2, n1, n1, 1.0, T1, ld, X11, ld, 0.0, T2, ld, 0, 2, 0);
+            st = gemm_s(ctx, false, false, n2, n1, n1, 1.0, T1, ld, X11, ld, 0.0, T2, ld, 0, 2, 0);
         }
     }
     if (side && st != MSP_OK) cudaStreamSynchronize(side);
     MSP_TRY(st);
     // X21 = -X22 T2 (X22 lower)
-    MSP_TRY(dgemm(ctx, false, false, n2, n1, n2, -1.0, X22, ld, T2, ld, 0.0, X21, ld, 1, 0, 0));
+    MSP_TRY(gemm_s(ctx, false, false, n2, n1, n2, -1.0, X22, ld, T2, ld, 0.0, X21, ld, 1, 0, 0));
     return MSP_OK;
 }
 
@@ -600,13 +906,19 @@ msp_status chol_inv(msp_ctx* ctx, double* M, double* X, double* T1, double* T2, 
 // Then nu x 100 per retry, at most 4 retries, else MSP_ENOTPD.
 msp_status factor_shifted(msp_ctx* ctx, const double* M, int64_t s, int64_t sp, bool fp32_data,
                           double* Linv64, double* shift_out, int* retries_out) {
+    // FP32 data: the factorisation in float-float (its backward error, a
+    // small multiple of s 2^-46 |M|, stays far below the shift 2^-24 |M|_F
+    // the data needs), on M scaled by a power of four to |M|_F in [1, 4) so
+    // that no float range limit is near
+    const bool ff = fp32_data && ctx->factor_ff;
     void* scr = nullptr;
     size_t mat = (size_t)sp * sp * 8;
-    MSP_TRY(msp_scratch(ctx, 3 * mat + 2048, &scr));
+    MSP_TRY(msp_scratch(ctx, (ff ? 4 : 3) * mat + 2048, &scr));
     double* Mw = (double*)scr;
     double* T1 = Mw + sp * sp;
     double* T2 = T1 + sp * sp;
-    int* fail = (int*)(T2 + sp * sp);
+    float2* Xff = reinterpret_cast<float2*>(T2 + sp * sp);       // ff only
+    int* fail = (int*)(T2 + (ff ? 2 : 1) * sp * sp);
     double* fro = (double*)(fail + 16);
     double* fro_part = fro + 2;
     int* hflag = (int*)ctx->host_flags;
@@ -622,22 +934,37 @@ msp_status factor_shifted(msp_ctx* ctx, const double* M, int64_t s, int64_t sp, 
         return MSP_OK;
     };
     double nu = 0.0;
+    int scale_k = 0;            // M scaled by 4^scale_k, L^{-1} by 2^-scale_k
     if (fp32_data) {
         double fn = 0.0;
         MSP_TRY(fro_norm(&fn));
         nu = std::ldexp(1.0, -24) * fn;
+        if (ff && fn > 0.0 && std::isfinite(fn)) scale_k = -(std::ilogb(fn) / 2);
     }
     for (int attempt = 0; attempt <= 4; ++attempt) {
         unsigned blocks = (unsigned)((sp * sp + 255) / 256);
-        k_copy_add_diag<<<blocks, 256, 0, ctx->stream>>>(M, Mw, sp, nu);
-        MSP_CHECK_LAUNCH(ctx);
-        MSP_CUDA_TRY(ctx, cudaMemsetAsync(Linv64, 0, mat, ctx->stream));
         MSP_CUDA_TRY(ctx, cudaMemsetAsync(fail, 0, sizeof(int), ctx->stream));
-        MSP_TRY(chol_inv(ctx, Mw, Linv64, T1, T2, sp, 0, sp, fail, 0));
+        if (ff) {
+            k_copy_add_diag_ff<<<blocks, 256, 0, ctx->stream>>>(M, reinterpret_cast<float2*>(Mw), sp, nu,
+                                                                std::ldexp(1.0, 2 * scale_k));
+            MSP_CHECK_LAUNCH(ctx);
+            MSP_CUDA_TRY(ctx, cudaMemsetAsync(Xff, 0, mat, ctx->stream));
+            MSP_TRY(chol_inv(ctx, reinterpret_cast<float2*>(Mw), Xff, reinterpret_cast<float2*>(T1),
+                             reinterpret_cast<float2*>(T2), sp, 0, sp, fail, 0));
+        } else {
+            k_copy_add_diag<<<blocks, 256, 0, ctx->stream>>>(M, Mw, sp, nu);
+            MSP_CHECK_LAUNCH(ctx);
+            MSP_CUDA_TRY(ctx, cudaMemsetAsync(Linv64, 0, mat, ctx->stream));
+            MSP_TRY(chol_inv(ctx, Mw, Linv64, T1, T2, sp, 0, sp, fail, 0));
+        }
         MSP_CUDA_TRY(ctx, cudaMemcpyAsync(hflag, fail, sizeof(int), cudaMemcpyDeviceToHost,
                                           ctx->stream));
         MSP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
         if (hflag[0] == 0) {
+            if (ff) {
+                k_ff_to_double<<<blocks, 256, 0, ctx->stream>>>(Xff, Linv64, sp * sp, std::ldexp(1.0, scale_k));
+                MSP_CHECK_LAUNCH(ctx);
+            }
             *shift_out = nu;
             *retries_out = attempt;
             return MSP_OK;
@@ -829,5 +1156,11 @@ msp_status msp_gemm_tn(msp_ctx* ctx, const float* X, int64_t ldx, int64_t ncx, c
     const int64_t len = nx_pad * ny_pad;
     k_sum_slices_f32<<<(unsigned)((len + 255) / 256), 256, 0, ctx->stream>>>(P, len, C);
     MSP_CHECK_LAUNCH(ctx);
+    return MSP_OK;
+}
+
+extern "C" msp_status msp_set_factor_float_float(msp_ctx* ctx, int on) {
+    if (!ctx) return msp_set_error(nullptr, MSP_EINVAL, "ctx is NULL");
+    ctx->factor_ff = on != 0;
     return MSP_OK;
 }

@@ -44,6 +44,7 @@ struct msp_ctx {
     cudaEvent_t fac_ev[8][2] = {};
     bool fac_overlap = true;     // false: the factor's products stay on the main stream
     bool gram_tc = true;         // M2 Gram on the tensor cores (false: FP32 pipe, compensated)
+    bool factor_ff = true;       // Cholesky of an FP32 factor in float-float (false: FP64)
     bool sketch_sym = true;      // FP32 sketch pass by the symmetric one-pass kernel
     // level-1 iterations of msp_solve replayed as a CUDA graph (capture
     // stream, cached executable, its key and profiling event nodes)
