@@ -157,6 +157,7 @@ void msp_destroy(msp_ctx* ctx) {
     if (ctx->ctl) cudaFree(ctx->ctl);
     if (ctx->host_flags) cudaFreeHost(ctx->host_flags);
     msp_l1_graph_release(ctx);
+    msp_fac_graph_release(ctx);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (int i = 0; i < ctx->n_events; ++i) cudaEventDestroy(ctx->events[i]);
     delete[] ctx->events;

@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 namespace {
@@ -394,26 +395,40 @@ __global__ void __launch_bounds__(256) k_ffgemm(int64_t m, int64_t n, int64_t k,
 #pragma unroll
         for (int j = 0; j < PT; ++j) sh[i][j] = sl[i][j] = 0.f;
     const float2 zero = make_float2(0.f, 0.f);
-    for (int64_t k0 = kbeg; k0 < kend; k0 += 16) {
-        for (int e = threadIdx.x; e < 16 * TS; e += 256) {
+    // the K chunk's operands, loaded into registers one chunk ahead
+    constexpr int LD = 16 * TS / 256;        // elements per thread per operand
+    float2 ra[LD], rb[LD];
+    auto fetch = [&](int64_t k0) {
+#pragma unroll
+        for (int u = 0; u < LD; ++u) {
+            const int e = threadIdx.x + 256 * u;
             int kk, ii;
             if (TA_) { ii = e % TS; kk = e / TS; }
             else { kk = e & 15; ii = e >> 4; }
             const int64_t gi = i0 + ii, gk = k0 + kk;
-            float2 v = zero;
-            if (gi < m && gk < kend) v = TA_ ? A[gk * lda + gi] : A[gi * lda + gk];
-            As[kk][ii] = v;
-        }
-        for (int e = threadIdx.x; e < 16 * TS; e += 256) {
-            int kk, jj;
+            ra[u] = (gi < m && gk < kend) ? (TA_ ? A[gk * lda + gi] : A[gi * lda + gk]) : zero;
+            int jj;
             if (TB_) { kk = e & 15; jj = e >> 4; }
             else { jj = e % TS; kk = e / TS; }
-            const int64_t gj = j0 + jj, gk = k0 + kk;
-            float2 v = zero;
-            if (gj < n && gk < kend) v = TB_ ? B[gj * ldb + gk] : B[gk * ldb + gj];
-            Bs[kk][jj] = v;
+            const int64_t gj = j0 + jj, gk2 = k0 + kk;
+            rb[u] = (gj < n && gk2 < kend) ? (TB_ ? B[gj * ldb + gk2] : B[gk2 * ldb + gj]) : zero;
+        }
+    };
+    if (kbeg < kend) fetch(kbeg);
+    for (int64_t k0 = kbeg; k0 < kend; k0 += 16) {
+#pragma unroll
+        for (int u = 0; u < LD; ++u) {
+            const int e = threadIdx.x + 256 * u;
+            int kk, ii, jj;
+            if (TA_) { ii = e % TS; kk = e / TS; }
+            else { kk = e & 15; ii = e >> 4; }
+            As[kk][ii] = ra[u];
+            if (TB_) { kk = e & 15; jj = e >> 4; }
+            else { jj = e % TS; kk = e / TS; }
+            Bs[kk][jj] = rb[u];
         }
         __syncthreads();
+        if (k0 + 16 < kend) fetch(k0 + 16);
 #pragma unroll
         for (int kk = 0; kk < 16; ++kk) {
             float2 av[PT], bv[PT];
@@ -581,11 +596,29 @@ __device__ __forceinline__ float2 ff_rcp(float2 d) {
     return ff_fast2sum(r0, __fmul_rn(r0, res));
 }
 
-// k_chol_leaf in float-float (same elimination, thread layout and pivot
-// warp; the block and its inverse in shared memory as float2): M = L L^T,
-// X = L^{-1}, both float2 with leading dimension ld. d_k^{-1/2} is formed in
-// FP64 (once per pivot), the final scaling in float-float.
-__global__ void __launch_bounds__(kLeafThreads) k_chol_leaf_ff(float2* __restrict__ M, float2* __restrict__ X,
+// d^{-1/2} in float-float for a positive normal d: the FP32 rsqrtf r0, then
+// one Newton-Raphson step r = r0 + r0 (1 - d r0^2) / 2 with the residual
+// 1 - d r0^2 formed to first order exactly (r0^2 and d r0^2 by TwoProduct;
+// d r0^2 is within about 2^-21 of 1), ~2^-43 relative.
+__device__ __forceinline__ float2 ff_rsqrt(float2 d) {
+    const float r0 = rsqrtf(d.x);
+    const float th = __fmul_rn(r0, r0), tl = __fmaf_rn(r0, r0, -th);
+    const float p = __fmul_rn(d.x, th);
+    const float pe = __fmaf_rn(d.y, th, __fmaf_rn(d.x, tl, __fmaf_rn(d.x, th, -p)));
+    const float res = __fsub_rn(__fsub_rn(1.0f, p), pe);
+    return ff_fast2sum(r0, __fmul_rn(__fmul_rn(0.5f, r0), res));
+}
+
+// k_chol_leaf in float-float (the same elimination and pivot warp; the
+// block and its inverse in shared memory as float2; 31 update warps take a
+// row each, a lane per element, so that a step of a 32-wide leaf is one
+// dependent chain per lane, where the FP64 version is bound by the FP64
+// pipe): M = L L^T,
+// X = L^{-1}, both float2 with leading dimension ld.
+constexpr int kFFUpd = 31 * 32;              // update warps of the float-float leaf
+constexpr int kFFThreads = kFFUpd + 32;       // and its pivot warp
+
+__global__ void __launch_bounds__(kFFThreads) k_chol_leaf_ff(float2* __restrict__ M, float2* __restrict__ X,
                                                               int64_t ld, int nb, int* __restrict__ fail) {
     extern __shared__ __align__(16) float2 leaf_smem_ff[];
     float2 (*a)[65] = reinterpret_cast<float2 (*)[65]>(leaf_smem_ff);
@@ -593,10 +626,10 @@ __global__ void __launch_bounds__(kLeafThreads) k_chol_leaf_ff(float2* __restric
     __shared__ float2 piv[64], rinv[64], rs[64];
     __shared__ int bad;
     const int tid = threadIdx.x, lane = tid & 31;
-    const bool pivot_warp = tid >= kLeafUpd;
+    const bool pivot_warp = tid >= kFFUpd;
     const float2 zero = make_float2(0.f, 0.f), one = make_float2(1.f, 0.f);
     if (tid == 0) bad = 0;
-    for (int e = tid; e < nb * nb; e += kLeafThreads) {
+    for (int e = tid; e < nb * nb; e += kFFThreads) {
         const int i = e / nb, j = e % nb;
         a[i][j] = (j <= i) ? M[i * ld + j] : zero;
         x[i][j] = (i == j) ? one : zero;
@@ -618,22 +651,24 @@ __global__ void __launch_bounds__(kLeafThreads) k_chol_leaf_ff(float2* __restric
         }
     }
     __syncthreads();
-    const int tx = tid & 7, ty = tid >> 3;
-    const int rr = ((ty & 3) << 3) | (ty >> 2);
+    const int warp = tid >> 5;
     for (int k = 0; k < nb; ++k) {
         const float2 rk = rinv[k];
         if (!pivot_warp) {
-            for (int i = k + 1 + rr; i < nb; i += 32) {
+            // one warp per row i = k + 1 + w, + 31, ...: lane j < i updates
+            // its element of the row, x[i][j] (j <= k) or a[i][j] (k < j <
+            // i), so the step's updates spread evenly over the lanes (no
+            // store of the step touches row k or column k)
+            for (int i = k + 1 + warp; i < nb; i += kFFUpd / 32) {
                 const float2 nti = ff_neg(ff_mul(a[i][k], rk));
-                for (int j = tx; j <= k; j += 8) {
-                    float h = x[i][j].x, l = x[i][j].y;
-                    ff_fma_acc(h, l, nti, x[k][j]);
-                    x[i][j] = ff_norm(h, l);
-                }
-                for (int j = k + 1 + tx; j < i; j += 8) {
-                    float h = a[i][j].x, l = a[i][j].y;
-                    ff_fma_acc(h, l, nti, a[j][k]);
-                    a[i][j] = ff_norm(h, l);
+                for (int j = lane; j < i; j += 32) {
+                    const bool xs = j <= k;
+                    const float2 src = xs ? x[k][j] : a[j][k];
+                    float2* dst = xs ? &x[i][j] : &a[i][j];
+                    const float2 v = *dst;
+                    float h = v.x, l = v.y;
+                    ff_fma_acc(h, l, nti, src);
+                    *dst = ff_norm(h, l);
                 }
             }
         } else if (k + 1 < nb) {
@@ -662,9 +697,9 @@ __global__ void __launch_bounds__(kLeafThreads) k_chol_leaf_ff(float2* __restric
         }
         __syncthreads();
     }
-    for (int k = tid; k < nb; k += kLeafThreads) rs[k] = ff_from_double(rsqrt_newton(ff_to_double(piv[k])));
+    for (int k = tid; k < nb; k += kFFThreads) rs[k] = ff_rsqrt(piv[k]);
     __syncthreads();
-    for (int e = tid; e < nb * nb; e += kLeafThreads) {
+    for (int e = tid; e < nb * nb; e += kFFThreads) {
         const int i = e / nb, j = e % nb;
         if (j < i) M[i * ld + j] = ff_mul(a[i][j], rs[j]);
         else if (j == i) M[i * ld + j] = ff_mul(piv[i], rs[i]);
@@ -819,7 +854,7 @@ msp_status leaf_s(msp_ctx* ctx, double* M, double* X, int64_t ld, int64_t n, int
 msp_status leaf_s(msp_ctx* ctx, float2* M, float2* X, int64_t ld, int64_t n, int* fail) {
     static std::atomic<bool> attr_set[64];
     MSP_TRY(leaf_attr(ctx, k_chol_leaf_ff, attr_set));
-    k_chol_leaf_ff<<<1, kLeafThreads, kLeafSmem, ctx->stream>>>(M, X, ld, (int)n, fail);
+    k_chol_leaf_ff<<<1, kFFThreads, kLeafSmem, ctx->stream>>>(M, X, ld, (int)n, fail);
     MSP_CHECK_LAUNCH(ctx);
     return MSP_OK;
 }
@@ -898,6 +933,62 @@ msp_status chol_inv(msp_ctx* ctx, S* M, S* X, S* T1, S* T2, int64_t ld,
     return MSP_OK;
 }
 
+// One float-float factor attempt (chol_inv on scratch buffers) replayed
+// from a CUDA graph: the recursion issues about 130 launches of a few
+// microseconds each, whose host-side cost would otherwise pace the GPU. The
+// executable is keyed by the buffers and the size; the side-stream forks of
+// the recursion become parallel branches of the graph. Where capture is
+// not possible the recursion launches on the stream.
+msp_status chol_inv_ff_graphed(msp_ctx* ctx, float2* M, float2* X, float2* T1, float2* T2, int64_t sp,
+                               int* fail) {
+    struct Key {
+        const void *M, *X, *T1, *T2, *fail;
+        int64_t sp;
+        int overlap, device;
+    } key;
+    std::memset(&key, 0, sizeof key);
+    key.M = M; key.X = X; key.T1 = T1; key.T2 = T2; key.fail = fail;
+    key.sp = sp;
+    key.overlap = ctx->fac_overlap;
+    key.device = ctx->device;
+    static_assert(sizeof(Key) <= sizeof(ctx->fac_key), "factor graph key too large");
+    const bool hit = ctx->fac_exec && ctx->fac_key_len == sizeof key &&
+                     std::memcmp(ctx->fac_key, &key, sizeof key) == 0;
+    if (!hit) {
+        msp_fac_graph_release(ctx);
+        bool ok = ctx->cap_stream != nullptr ||
+                  cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+        if (ok) ok = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+        if (ok) {
+            const cudaStream_t saved = ctx->stream;
+            const int64_t l0 = ctx->launches;
+            ctx->stream = ctx->cap_stream;
+            const msp_status st = chol_inv(ctx, M, X, T1, T2, sp, 0, sp, fail, 0);
+            ctx->stream = saved;
+            cudaGraph_t graph = nullptr;
+            const cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &graph);
+            const int kernels = (int)(ctx->launches - l0);
+            ctx->launches = l0;
+            ok = st == MSP_OK && ce == cudaSuccess && graph != nullptr &&
+                 cudaGraphInstantiate(&ctx->fac_exec, graph, 0) == cudaSuccess;
+            if (ok) {
+                ctx->fac_graph = graph;
+                std::memcpy(ctx->fac_key, &key, sizeof key);
+                ctx->fac_key_len = sizeof key;
+                ctx->fac_kernels = kernels;
+            } else {
+                ctx->fac_exec = nullptr;
+                if (graph) cudaGraphDestroy(graph);
+            }
+        }
+        cudaGetLastError();
+        if (!ok) return chol_inv(ctx, M, X, T1, T2, sp, 0, sp, fail, 0);
+    }
+    MSP_CUDA_TRY(ctx, cudaGraphLaunch(ctx->fac_exec, ctx->stream));
+    ctx->launches += ctx->fac_kernels;
+    return MSP_OK;
+}
+
 // Cholesky inverse of M + nu I (lower L^{-1} into Linv64), s_pad x s_pad
 // FP64 M with identity padding. FP32 data: M carries rounding errors of
 // about 2^-24 |M|_F (its operands are FP32), which leave it indefinite by
@@ -949,8 +1040,8 @@ msp_status factor_shifted(msp_ctx* ctx, const double* M, int64_t s, int64_t sp, 
                                                                 std::ldexp(1.0, 2 * scale_k));
             MSP_CHECK_LAUNCH(ctx);
             MSP_CUDA_TRY(ctx, cudaMemsetAsync(Xff, 0, mat, ctx->stream));
-            MSP_TRY(chol_inv(ctx, reinterpret_cast<float2*>(Mw), Xff, reinterpret_cast<float2*>(T1),
-                             reinterpret_cast<float2*>(T2), sp, 0, sp, fail, 0));
+            MSP_TRY(chol_inv_ff_graphed(ctx, reinterpret_cast<float2*>(Mw), Xff, reinterpret_cast<float2*>(T1),
+                                        reinterpret_cast<float2*>(T2), sp, fail));
         } else {
             k_copy_add_diag<<<blocks, 256, 0, ctx->stream>>>(M, Mw, sp, nu);
             MSP_CHECK_LAUNCH(ctx);
@@ -1163,4 +1254,13 @@ extern "C" msp_status msp_set_factor_float_float(msp_ctx* ctx, int on) {
     if (!ctx) return msp_set_error(nullptr, MSP_EINVAL, "ctx is NULL");
     ctx->factor_ff = on != 0;
     return MSP_OK;
+}
+
+void msp_fac_graph_release(msp_ctx* ctx) {
+    if (ctx->fac_exec) cudaGraphExecDestroy(ctx->fac_exec);
+    if (ctx->fac_graph) cudaGraphDestroy(ctx->fac_graph);
+    ctx->fac_exec = nullptr;
+    ctx->fac_graph = nullptr;
+    ctx->fac_key_len = 0;
+    ctx->fac_kernels = 0;
 }

@@ -57,6 +57,14 @@ struct msp_ctx {
     cudaGraphNode_t l1_ev_nodes[2] = {};
     int l1_kernels = 0;
     int64_t l1_graph_iters = 0;  // level-1 iterations replayed from the graph
+    // the float-float Cholesky inverse of one factor attempt as a CUDA graph
+    // (its buffers are scratch, so the executable serves every factor of a
+    // size until the scratch moves)
+    cudaGraph_t fac_graph = nullptr;
+    cudaGraphExec_t fac_exec = nullptr;
+    unsigned char fac_key[64] = {};
+    size_t fac_key_len = 0;
+    int fac_kernels = 0;
     int hutch_terms = 2;         // tensor-core Hutchinson: 2 = two FP16 terms, 3 = three BF16 terms
     msp_ctx** lanes = nullptr;
     cudaStream_t* lane_streams = nullptr;
@@ -399,6 +407,8 @@ struct Profiler {
 msp_status msp_profiler_reserve(msp_ctx* ctx, int pairs);
 // frees the context's level-1 graph (deferred by CUDA while replays run)
 void msp_l1_graph_release(msp_ctx* ctx);
+// frees the context's factor graph
+void msp_fac_graph_release(msp_ctx* ctx);
 msp_status msp_norm2(msp_ctx* ctx, const double* v, int64_t n, double* out_dev);
 msp_status msp_scale_cast(msp_ctx* ctx, const double* src, const double* nrm2, int64_t n,
                           msp_dtype dt, void* dst);
