@@ -236,11 +236,11 @@ MSP_API msp_status msp_nystrom(msp_ctx* ctx, const msp_sketch_t* sk, double lamb
  * multiple of 4, n >= 32; other FP32 inputs take the row-wise passes):
  * on = 1 (default): one pass over A that forms C = A Pi as A^T Pi (A is
  * symmetric by this call's contract) from 32-column blocks of A staged by
- * TMA in chunks of 512 rows, and stores the packed upper
- * tiles and the row statistics of the norm bound from the same staged
- * blocks; on = 0: the row-wise C pass, then the packing and the statistics
- * as passes of their own. Both give C within the same rounding bound. Not
- * part of the method (it selects an implementation). */
+ * TMA in chunks of 512 rows, and stores the packed upper tiles from the
+ * same staged blocks; on = 0: the row-wise C pass, then the packing as a
+ * pass of its own. The row statistics of the norm bound are a pass of their
+ * own either way. Both give C within the same rounding bound. Not part of
+ * the method (it selects an implementation). */
 MSP_API msp_status msp_set_sketch_one_pass(msp_ctx* ctx, int on);
 
 /* Where msp_nystrom forms the Gram C~^T C~ of an FP32 sketch: on = 1

@@ -241,7 +241,7 @@ msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t
     sk->stream = ctx->stream;
     const size_t ts = dtype_size(dtype);
     msp_status st = MSP_OK;
-    bool prep_done = false;    // packed tiles and statistics already formed by the one-pass kernel
+    bool prep_done = false;    // packed tiles (one-pass kernel) and statistics (their pass) formed
     if ((st = msp_alloc(ctx, (void**)&sk->idx, (size_t)n * gamma * 4)) != MSP_OK ||
         (st = msp_alloc(ctx, (void**)&sk->sgn, (size_t)n * gamma)) != MSP_OK ||
         (st = msp_alloc(ctx, (void**)&sk->csr_ptr, (size_t)(sp + 1) * 4)) != MSP_OK ||
@@ -319,8 +319,8 @@ msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t
             if (pack) st = msp_alloc(ctx, (void**)&sk->stats, (size_t)(3 * n + 1) * 8);
             if (st == MSP_OK)
                 st = msp_sketch_sym_pass(ctx, (const float*)A, n, n, sp, sk->csr_ptr, sk->csr_ent, gamma,
-                                         (float*)sk->C, pack ? sk->packed : nullptr, pack ? sk->stats : nullptr);
-            if (st == MSP_OK && pack) st = msp_norm_lb_finish(ctx, sk->stats, n, sk->stats + 3 * n);
+                                         (float*)sk->C, pack ? sk->packed : nullptr);
+            if (st == MSP_OK && pack) st = msp_norm_lb_launch(ctx, A, dtype, n, n, sk->stats, sk->stats + 3 * n);
             ok = (st == MSP_OK);
             prep_done = true;
         }
@@ -339,13 +339,13 @@ msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t
             return st;
         }
     } else if (a_dt == MSP_F32 && ctx->sketch_sym && msp_sketch_sym_ok(A, n, lda, sp, gamma)) {
-        // one pass over the symmetric A: C, the packed tiles and the row
-        // statistics together
+        // one pass over the symmetric A: C and the packed tiles together;
+        // the norm-bound row statistics are a pass of their own
         if (pack) st = msp_alloc(ctx, (void**)&sk->stats, (size_t)(3 * n + 1) * 8);
         if (st == MSP_OK)
             st = msp_sketch_sym_pass(ctx, (const float*)A, n, lda, sp, sk->csr_ptr, sk->csr_ent, gamma,
-                                     (float*)sk->C, pack ? sk->packed : nullptr, pack ? sk->stats : nullptr);
-        if (st == MSP_OK && pack) st = msp_norm_lb_finish(ctx, sk->stats, n, sk->stats + 3 * n);
+                                     (float*)sk->C, pack ? sk->packed : nullptr);
+        if (st == MSP_OK && pack) st = msp_norm_lb_launch(ctx, A, dtype, n, lda, sk->stats, sk->stats + 3 * n);
         if (st != MSP_OK) {
             cudaStreamSynchronize(ctx->stream);
             msp_sketch_destroy(sk);

@@ -300,13 +300,10 @@ msp_status msp_sketch_apply_rows(msp_ctx* ctx, const void* A, msp_dtype dt, int6
 msp_status msp_chunk_starts(msp_ctx* ctx, const int32_t* ptr, const int32_t* ent, int64_t s_pad, int J, int nch,
                             int32_t* tab);
 // One pass over a symmetric FP32 A (device, 16-byte aligned, lda % 4 == 0,
-// n >= 64, gamma <= 8):
-// C = A Pi, and optionally the packed upper tiles and the row statistics
-// (rowsum, rowerr, rowsq: 3 n doubles) of the norm bound.
+// n >= 32, s_pad <= 2048): C = A Pi, and optionally the packed upper tiles.
 bool msp_sketch_sym_ok(const void* A, int64_t n, int64_t lda, int64_t s_pad, int gamma);
 msp_status msp_sketch_sym_pass(msp_ctx* ctx, const float* A, int64_t n, int64_t lda, int64_t s_pad,
-                               const int32_t* ptr, const int32_t* ent, int gamma, float* C, float* packed,
-                               double* stats);
+                               const int32_t* ptr, const int32_t* ent, int gamma, float* C, float* packed);
 // the norm bound from row statistics already in work (3 n doubles)
 msp_status msp_norm_lb_finish(msp_ctx* ctx, double* work, int64_t n, double* out_dev);
 msp_status msp_gather_rows(msp_ctx* ctx, msp_dtype dt, int64_t rows_out, int64_t width,

@@ -1,5 +1,5 @@
 // The sketch pass over a symmetric FP32 A in device memory (Algorithm 1,
-// steps 2-3, with what the solves keep of A), in one read of A:
+// steps 2-3, with the packed tiles the solves keep of A), in one read of A:
 //   C = A Pi           computed as A^T Pi: the CTA for rows [i0, i0 + 32) of
 //                      C reads the column block A[:, i0 .. i0 + 32) in chunks
 //                      of kSJ rows by TMA (box {32, 256}, twice per chunk;
@@ -9,10 +9,9 @@
 //   packed tiles       the 128 x 128 upper tiles of A the packed A pass reads,
 //                      stored from the staged chunks by TMA (the column block
 //                      is a 32-column slice of one tile column);
-//   row statistics     sum, sum of |.| and sum of squares of every row of A
-//                      (by symmetry, of its column in the block), FP32 chunks
-//                      of 64 terms added in FP64, as the lower bound of |A|_2
-//                      of the backward-error rule needs them.
+// (The norm-bound row statistics of the backward-error rule are a pass of
+// their own: taken from the staged chunks here they cost more issue slots
+// in this gather-bound kernel than a separate HBM-bound pass over A.)
 // Gathers: one thread per column c of C, 32 accumulators (the block's rows).
 // An entry (j, sign) of column c reads the 128-byte row j of the chunk as
 // eight 16-byte pieces; lane l reads them in the order (q + l) mod 8, so the
@@ -37,8 +36,6 @@ constexpr int kSBox = 256;                         // rows per TMA box
 constexpr int kSStages = 2;
 constexpr uint32_t kSStageBytes = kSJ * kSR * 4;   // 64 KB
 constexpr int kSTile = 128;                        // packed tile side
-constexpr int kSChunk = 64;                        // FP32 terms per statistics chunk
-constexpr double kSU32 = 5.9604644775390625e-8;
 
 struct SymArgs {
     int64_t n, s_pad;
@@ -48,7 +45,6 @@ struct SymArgs {
     const int32_t* ent;      // (j << 1) | negative, CSR by column
     float scale;
     float* C;
-    double* stats;           // rowsum[n], rowerr[n], rowsq[n] or null
     int* err;
 };
 
@@ -75,9 +71,7 @@ k_sketch_sym(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     const uint32_t pad = (1024u - (msp::smem_u32(smem_raw) & 1023u)) & 1023u;
     uint8_t* sm = smem_raw + pad;
-    // FP64 statistics partials of every thread: [3][blockDim.x]
-    double* sdst = reinterpret_cast<double*>(sm + kSStages * kSStageBytes);
-    uint64_t* full = reinterpret_cast<uint64_t*>(sdst + 3 * blockDim.x);
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + kSStages * kSStageBytes);
     volatile int* s_abort = reinterpret_cast<volatile int*>(full + kSStages);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -85,7 +79,7 @@ k_sketch_sym(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     // so the block's repeated reads of A are served by L2); blockIdx.y: row block
     const int64_t i0 = (int64_t)blockIdx.y * kSR;
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + tid;      // column of C
-    const bool lead = (blockIdx.x == 0);                            // packs and takes statistics
+    const bool lead = (blockIdx.x == 0);                            // packs the tiles
     const int Jt = (int)(i0 / kSTile);                              // tile column of the block
     const int nch = a.nch;
 
@@ -95,7 +89,6 @@ k_sketch_sym(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             msp::tc::tma_load_2d(sm + st * kSStageBytes + b * kSBox * kSR * 4, &tmA, (int32_t)i0,
                                  k * kSJ + b * kSBox, &full[st]);
     };
-    for (int e = tid; e < 3 * (int)blockDim.x; e += blockDim.x) sdst[e] = 0.0;
     if (tid == 0) {
         for (int s = 0; s < kSStages; ++s) msp::mbar_init(&full[s], 1);
         *s_abort = 0;
@@ -112,10 +105,6 @@ k_sketch_sym(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         for (int t = 0; t < 4; ++t) acc[q][t] = 0.f;
     // this lane's rotation of the pieces (bytes within a 128-byte row)
     const uint32_t lrot = (uint32_t)lane * 16u;
-    // statistics: lane = row i0 + lane of A, warp w sums rows j = w mod nw of
-    // each chunk; FP32 chunks of kSChunk terms go into the FP64 partials
-    float cs = 0.f, ca = 0.f, cq = 0.f;
-    int terms = 0;
 
     const bool col_ok = c < a.s_pad;
     int e0 = col_ok ? __ldg(&a.tab[c * (nch + 1)]) : 0;
@@ -162,24 +151,6 @@ k_sketch_sym(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
             gather_row(acc, stage + ((v >> 1) - (int32_t)j0) * (kSR * 4), lrot, (v & 1) ? -1.f : 1.f);
         }
         e0 = e1;
-        // row statistics (rows j < n only; the chunk is zero beyond n)
-        if (a.stats && lead) {
-            const float* sf = reinterpret_cast<const float*>(stage);
-            for (int r = warp; r < kSJ; r += nw) {
-                if (j0 + r >= a.n) break;
-                const float x = sf[r * kSR + lane];
-                cs += x;
-                ca += fabsf(x);
-                cq = fmaf(x, x, cq);
-                if (++terms == kSChunk) {
-                    sdst[tid] += (double)cs;
-                    sdst[blockDim.x + tid] += (double)ca;
-                    sdst[2 * blockDim.x + tid] += (double)cq;
-                    cs = ca = cq = 0.f;
-                    terms = 0;
-                }
-            }
-        }
         __syncthreads();
         // every warp is past chunk k: refill its stage with chunk k + kSStages
         if (tid == 0 && k + kSStages < nch) {
@@ -209,27 +180,6 @@ k_sketch_sym(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                 if (r0 + t < a.n) a.C[(r0 + t) * a.s_pad + c] = acc[q][t] * a.scale;
         }
     }
-    if (a.stats && lead) {
-        sdst[tid] += (double)cs;
-        sdst[blockDim.x + tid] += (double)ca;
-        sdst[2 * blockDim.x + tid] += (double)cq;
-        __syncthreads();
-        if (tid < 32 && i0 + tid < a.n) {
-            // lane tid of every warp, in warp order
-            double s = 0.0, ab = 0.0, q = 0.0;
-            for (int w = 0; w < nw; ++w) {
-                s += sdst[w * 32 + tid];
-                ab += sdst[blockDim.x + w * 32 + tid];
-                q += sdst[2 * blockDim.x + w * 32 + tid];
-            }
-            const int64_t i = i0 + tid;
-            a.stats[i] = s;
-            // FP32 chunks of at most kSChunk terms: (kSChunk - 1) u sum |.|,
-            // plus u for an entry's own rounding, as the row-wise statistics
-            a.stats[a.n + i] = (kSChunk + 1) * kSU32 * ab * (1.0 + 1e-6);
-            a.stats[2 * a.n + i] = q;
-        }
-    }
 }
 
 }  // namespace
@@ -242,8 +192,7 @@ bool msp_sketch_sym_ok(const void* A, int64_t n, int64_t lda, int64_t s_pad, int
 }
 
 msp_status msp_sketch_sym_pass(msp_ctx* ctx, const float* A, int64_t n, int64_t lda, int64_t s_pad,
-                               const int32_t* ptr, const int32_t* ent, int gamma, float* C, float* packed,
-                               double* stats) {
+                               const int32_t* ptr, const int32_t* ent, int gamma, float* C, float* packed) {
     auto enc = msp_tensor_map_encoder();
     if (!enc || !msp_sketch_sym_ok(A, n, lda, s_pad, gamma))
         return msp_set_error(ctx, MSP_EINVAL, "sketch_sym: unsupported arguments");
@@ -292,10 +241,9 @@ msp_status msp_sketch_sym_pass(msp_ctx* ctx, const float* A, int64_t n, int64_t 
     a.ent = ent;
     a.scale = (float)(1.0 / std::sqrt((double)gamma));
     a.C = C;
-    a.stats = stats;
     CtlBlock* ctl = (CtlBlock*)ctx->ctl;
     a.err = &ctl->error;
-    const size_t smem = (size_t)kSStages * kSStageBytes + 3 * 8 * (size_t)threads + 64 + 1024;
+    const size_t smem = (size_t)kSStages * kSStageBytes + 64 + 1024;
     MSP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_sketch_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     MSP_CUDA_TRY(ctx, cudaMemsetAsync(&ctl->error, 0, sizeof(int), ctx->stream));
     // grid: column groups x every 32-column block up to the last tile column
