@@ -17,8 +17,8 @@
 // eight 16-byte pieces; lane l reads them in the order (q + l) mod 8, so the
 // 32 lanes of a warp hit every bank group four times per instruction whatever
 // their rows j are (no bank conflicts), and accumulator slot q holds the
-// rows of piece (q + l) mod 8. A thread's entries of a chunk are read four at
-// a time, all loads in flight together. The threads of a warp have different
+// rows of piece (q + l) mod 8. A thread's first three entries of a chunk are
+// read with all loads in flight together. The threads of a warp have different
 // numbers of entries in a chunk (about 4 on average at s = 1024, kSJ = 512),
 // so a warp runs as many gather steps as its busiest thread: long chunks
 // narrow that spread. Chunks stream through kSStages stages of shared memory;
@@ -74,7 +74,7 @@ k_sketch_sym(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     uint64_t* full = reinterpret_cast<uint64_t*>(sm + kSStages * kSStageBytes);
     volatile int* s_abort = reinterpret_cast<volatile int*>(full + kSStages);
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     // blockIdx.x: column group (the groups of a row block run side by side,
     // so the block's repeated reads of A are served by L2); blockIdx.y: row block
     const int64_t i0 = (int64_t)blockIdx.y * kSR;
@@ -114,10 +114,11 @@ k_sketch_sym(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         const int st = k % kSStages;
         const int e1 = e1n;
         if (col_ok && k + 1 < nch) e1n = __ldg(&a.tab[c * (nch + 1) + k + 2]);
-        // this chunk's first four entries, loads in flight together
-        int32_t v4[4];
+        // this chunk's first three entries, loads in flight together (a
+        // fourth one spills at the 64-register limit of 1024 threads)
+        int32_t v3[3];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) v4[u] = (e0 + u < e1) ? __ldg(&a.ent[e0 + u]) : 0;
+        for (int u = 0; u < 3; ++u) v3[u] = (e0 + u < e1) ? __ldg(&a.ent[e0 + u]) : 0;
         bool ok = true;
         if (*s_abort == 0) ok = msp::mbar_wait_timed(&full[st], (uint32_t)((k / kSStages) & 1), a.err);
         if (!__syncthreads_and(ok)) {
@@ -140,13 +141,13 @@ k_sketch_sym(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
         }
         // gathers of this column's entries in the chunk
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 3; ++u) {
             if (e0 + u < e1) {
-                const int32_t v = v4[u];
+                const int32_t v = v3[u];
                 gather_row(acc, stage + ((v >> 1) - (int32_t)j0) * (kSR * 4), lrot, (v & 1) ? -1.f : 1.f);
             }
         }
-        for (int e = e0 + 4; e < e1; ++e) {
+        for (int e = e0 + 3; e < e1; ++e) {
             const int32_t v = __ldg(&a.ent[e]);
             gather_row(acc, stage + ((v >> 1) - (int32_t)j0) * (kSR * 4), lrot, (v & 1) ? -1.f : 1.f);
         }
