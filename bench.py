@@ -861,6 +861,14 @@ def run_msp(args, rank, world, local):
     total = args.steps * world
     value = job_rate(args.steps, world, ms / 1000.0)
     ok = all(i["backward_err"] <= 1e-10 and i["status"] == 0 for i in infos)
+    # the same steps without the per-launch events (context for `value`,
+    # which is timed with them on so that the roofline comes from its region)
+    ms_np, infos_np, _ = timed(args.steps, profile=0)
+    unprofiled = {"value": job_rate(args.steps, world, ms_np / 1000.0), "unit": "solves/s",
+                  "ms_per_step": ms_np / args.steps,
+                  "backward_err_max": max(i["backward_err"] for i in infos_np),
+                  "note": "the same steps with opts.profile = 0: no event-record nodes between the "
+                          "level-1 kernels"}
 
     # the stricter rule: relative residual |r| / |b| <= 1e-10
     for _ in range(1):
@@ -1123,6 +1131,7 @@ def run_msp(args, rank, world, local):
                         "rel_resid_max": max(i["rel_resid"] for i in infos), "all_converged": ok,
                         "outer_iters": last["outer_iters"], "inner_iters": last["inner_iters"],
                         "refine_steps": last["refine_steps"]},
+           "unprofiled": unprofiled,
            "rel_resid_1e-10": strict,
            "mixed_bf16_preconditioner_data": bf16_data,
            "sketch_pass_ms": sketch_pass,
