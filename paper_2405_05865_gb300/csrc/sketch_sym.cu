@@ -17,12 +17,17 @@
 // eight 16-byte pieces; lane l reads them in the order (q + l) mod 8, so the
 // 32 lanes of a warp hit every bank group four times per instruction whatever
 // their rows j are (no bank conflicts), and accumulator slot q holds the
-// rows of piece (q + l) mod 8. A thread's first three entries of a chunk are
-// read with all loads in flight together. The threads of a warp have different
-// numbers of entries in a chunk (about 4 on average at s = 1024, kSJ = 512),
-// so a warp runs as many gather steps as its busiest thread: long chunks
-// narrow that spread. Chunks stream through kSStages stages of shared memory;
-// thread 0 refills a stage once every warp has passed it.
+// rows of piece (q + l) mod 8.
+// Chunks: kSWin chunks of kSJ rows are resident at once. A thread walks its
+// column's CSR entries in order (ascending j), and a lane whose next entry
+// lies in a later resident chunk goes on with it while its warp-mates finish
+// the earlier one: a warp's gather steps follow its busiest lane over the
+// window, not over each chunk (entries per column are Poisson-like, about 4
+// per chunk at s = 1024 and 12 per window, so the busiest of 32 lanes is
+// far above the mean for one chunk and less so for three). A warp releases a
+// chunk once all its lanes are past it; the last warp of the block to release
+// chunk k stores its packed tiles and refills the stage with chunk k + kSWin.
+// Each accumulator takes its FMAs in the order of the column's entries.
 #include "msp_internal.cuh"
 #include "tc.cuh"
 
@@ -33,7 +38,7 @@ namespace {
 constexpr int kSR = 32;                            // rows of C per CTA (columns of A)
 constexpr int kSJ = 512;                           // rows of A per chunk
 constexpr int kSBox = 256;                         // rows per TMA box
-constexpr int kSStages = 2;
+constexpr int kSWin = 3;                           // resident chunks (stages)
 constexpr uint32_t kSStageBytes = kSJ * kSR * 4;   // 64 KB
 constexpr int kSTile = 128;                        // packed tile side
 
@@ -41,7 +46,7 @@ struct SymArgs {
     int64_t n, s_pad;
     int nch;                 // chunks (cover the tile rows up to nt * 128)
     int nt;                  // tiles per side
-    const int32_t* tab;      // [s_pad][nch + 1] first entry of column c in chunk k
+    const int32_t* ptr;      // [s_pad + 1] CSR column starts
     const int32_t* ent;      // (j << 1) | negative, CSR by column
     float scale;
     float* C;
@@ -65,22 +70,34 @@ __device__ __forceinline__ void gather_row(float (&acc)[8][4], const uint8_t* ro
     }
 }
 
+// Non-blocking test of the phase of the given parity (acquire on success).
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(msp::smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 __global__ void __launch_bounds__(1024, 1)
 k_sketch_sym(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmP, SymArgs a,
              int pack) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     const uint32_t pad = (1024u - (msp::smem_u32(smem_raw) & 1023u)) & 1023u;
     uint8_t* sm = smem_raw + pad;
-    uint64_t* full = reinterpret_cast<uint64_t*>(sm + kSStages * kSStageBytes);
-    volatile int* s_abort = reinterpret_cast<volatile int*>(full + kSStages);
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + kSWin * kSStageBytes);
+    int* rel = reinterpret_cast<int*>(full + kSWin);        // [kSWin] warps past the stage's chunks
+    int* s_issued = rel + kSWin;                             // chunks issued
+    volatile int* s_abort = reinterpret_cast<volatile int*>(s_issued + 1);
 
-    const int tid = threadIdx.x, lane = tid & 31;
-    // blockIdx.x: column group (the groups of a row block run side by side,
-    // so the block's repeated reads of A are served by L2); blockIdx.y: row block
+    const int tid = threadIdx.x, lane = tid & 31, nw = (int)(blockDim.x >> 5);
     const int64_t i0 = (int64_t)blockIdx.y * kSR;
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + tid;      // column of C
     const bool lead = (blockIdx.x == 0);                            // packs the tiles
-    const int Jt = (int)(i0 / kSTile);                              // tile column of the block
+    const int Jt = (int)(i0 / kSTile);
     const int nch = a.nch;
 
     auto issue = [&](int k, int st) {
@@ -90,88 +107,117 @@ k_sketch_sym(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
                                  k * kSJ + b * kSBox, &full[st]);
     };
     if (tid == 0) {
-        for (int s = 0; s < kSStages; ++s) msp::mbar_init(&full[s], 1);
+        for (int s = 0; s < kSWin; ++s) {
+            msp::mbar_init(&full[s], 1);
+            rel[s] = 0;
+        }
+        *s_issued = nch < kSWin ? nch : kSWin;
         *s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         msp::tc::prefetch_tensormap(&tmA);
-        for (int k = 0; k < (nch < kSStages ? nch : kSStages); ++k) issue(k, k);
+        for (int k = 0; k < (nch < kSWin ? nch : kSWin); ++k) issue(k, k);
     }
     __syncthreads();
+
+    // bounded wait for chunk k (every lane; false for the whole warp if any
+    // lane gave up or another warp has)
+    auto wait_chunk = [&](int k) -> bool {
+        bool ok = (*s_abort == 0) &&
+                  msp::mbar_wait_sleep(&full[k % kSWin], (uint32_t)((k / kSWin) & 1), a.err);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok && lane == 0) *s_abort = 1;
+        return ok;
+    };
+    // chunk k is done with in this warp; the block's last warp stores its
+    // packed tiles and refills the stage
+    auto release = [&](int k) {
+        __syncwarp();
+        if (lane == 0) {
+            const int st = k % kSWin;
+            __threadfence_block();
+            const int old = atomicAdd(&rel[st], 1);
+            if (old == nw * (k / kSWin + 1) - 1) {
+                __threadfence_block();
+                if (pack && lead) {
+                    const int64_t j0 = (int64_t)k * kSJ;
+                    for (int h = 0; h < kSJ / kSTile; ++h) {
+                        const int I = (int)(j0 / kSTile) + h;
+                        if (I <= Jt && I < a.nt)
+                            msp::tc::tma_store_2d(&tmP, (int32_t)(i0 % kSTile),
+                                                  (int32_t)(tile_index(I, Jt, a.nt) * kSTile),
+                                                  sm + st * kSStageBytes + h * kSTile * kSR * 4);
+                    }
+                    msp::tc::bulk_commit();
+                    msp::tc::bulk_wait_read();
+                }
+                if (k + kSWin < nch && *s_abort == 0) {
+                    msp::tc::fence_proxy_async();
+                    issue(k + kSWin, st);
+                    atomicMax(s_issued, k + kSWin + 1);
+                }
+            }
+        }
+        __syncwarp();
+    };
 
     float acc[8][4];
 #pragma unroll
     for (int q = 0; q < 8; ++q)
 #pragma unroll
         for (int t = 0; t < 4; ++t) acc[q][t] = 0.f;
-    // this lane's rotation of the pieces (bytes within a 128-byte row)
     const uint32_t lrot = (uint32_t)lane * 16u;
 
     const bool col_ok = c < a.s_pad;
-    int e0 = col_ok ? __ldg(&a.tab[c * (nch + 1)]) : 0;
-    int e1n = col_ok ? __ldg(&a.tab[c * (nch + 1) + 1]) : 0;
-    int issued = nch < kSStages ? nch : kSStages, k_stop = nch;
-    for (int k = 0; k < nch; ++k) {
-        const int st = k % kSStages;
-        const int e1 = e1n;
-        if (col_ok && k + 1 < nch) e1n = __ldg(&a.tab[c * (nch + 1) + k + 2]);
-        // this chunk's first three entries, loads in flight together (a
-        // fourth one spills at the 64-register limit of 1024 threads)
-        int32_t v3[3];
-#pragma unroll
-        for (int u = 0; u < 3; ++u) v3[u] = (e0 + u < e1) ? __ldg(&a.ent[e0 + u]) : 0;
-        bool ok = true;
-        if (*s_abort == 0) ok = msp::mbar_wait_timed(&full[st], (uint32_t)((k / kSStages) & 1), a.err);
-        if (!__syncthreads_and(ok)) {
-            if (tid == 0) *s_abort = 1;
-            k_stop = k;
-            break;
-        }
-        const uint8_t* stage = sm + st * kSStageBytes;
-        const int64_t j0 = (int64_t)k * kSJ;
-        // packed tiles: rows j0 .. j0 + kSJ cover tile rows j0 / 128 ..; the
-        // slice of tile (I, Jt) for I <= Jt
-        if (pack && lead && tid == 0) {
-            for (int h = 0; h < kSJ / kSTile; ++h) {
-                const int I = (int)(j0 / kSTile) + h;
-                if (I <= Jt && I < a.nt)
-                    msp::tc::tma_store_2d(&tmP, (int32_t)(i0 % kSTile), (int32_t)(tile_index(I, Jt, a.nt) * kSTile),
-                                          stage + h * kSTile * kSR * 4);
+    int e = col_ok ? __ldg(&a.ptr[c]) : 0;
+    const int e_end = col_ok ? __ldg(&a.ptr[c + 1]) : 0;
+    // the next three entries, loads in flight ahead of their gathers
+    int32_t v0 = (e < e_end) ? __ldg(&a.ent[e]) : 0;
+    int32_t v1 = (e + 1 < e_end) ? __ldg(&a.ent[e + 1]) : 0;
+    int32_t v2 = (e + 2 < e_end) ? __ldg(&a.ent[e + 2]) : 0;
+    int loaded = 0, released = 0;       // warp-uniform: chunks seen complete, chunks released
+    bool ok = true;
+    for (;;) {
+        const int kl = (e < e_end) ? ((v0 >> 1) / kSJ) : nch;      // chunk of this lane's next entry
+        const int kmin = (int)__reduce_min_sync(0xffffffffu, (unsigned)kl);
+        while (released < kmin) {
+            if (loaded <= released) {
+                if (!(ok = wait_chunk(released))) break;
+                loaded = released + 1;
             }
-            msp::tc::bulk_commit();
+            release(released);
+            ++released;
         }
-        // gathers of this column's entries in the chunk
-#pragma unroll
-        for (int u = 0; u < 3; ++u) {
-            if (e0 + u < e1) {
-                const int32_t v = v3[u];
-                gather_row(acc, stage + ((v >> 1) - (int32_t)j0) * (kSR * 4), lrot, (v & 1) ? -1.f : 1.f);
-            }
+        if (!ok || kmin >= nch) break;
+        if (loaded <= kmin) {
+            if (!(ok = wait_chunk(kmin))) break;
+            loaded = kmin + 1;
+        } else if (loaded < nch && loaded < kmin + kSWin && __any_sync(0xffffffffu, kl >= loaded)) {
+            // a later chunk may have landed: lanes there need not wait
+            const bool t = mbar_test(&full[loaded % kSWin], (uint32_t)((loaded / kSWin) & 1));
+            if (__all_sync(0xffffffffu, t)) ++loaded;
         }
-        for (int e = e0 + 3; e < e1; ++e) {
-            const int32_t v = __ldg(&a.ent[e]);
-            gather_row(acc, stage + ((v >> 1) - (int32_t)j0) * (kSR * 4), lrot, (v & 1) ? -1.f : 1.f);
-        }
-        e0 = e1;
-        __syncthreads();
-        // every warp is past chunk k: refill its stage with chunk k + kSStages
-        if (tid == 0 && k + kSStages < nch) {
-            if (pack && lead) msp::tc::bulk_wait_read();
-            msp::tc::fence_proxy_async();
-            issue(k + kSStages, st);
-            issued = k + kSStages + 1;
+        if (kl < loaded) {
+            const int32_t jr = (v0 >> 1) - kl * kSJ;
+            gather_row(acc, sm + (kl % kSWin) * kSStageBytes + jr * (kSR * 4), lrot, (v0 & 1) ? -1.f : 1.f);
+            ++e;
+            v0 = v1;
+            v1 = v2;
+            v2 = (e + 2 < e_end) ? __ldg(&a.ent[e + 2]) : 0;
         }
     }
+    __syncthreads();
     if (*s_abort) {
-        // bounded waits for the loads still in flight (chunks k_stop ..
-        // issued - 1, none of them waited for yet) before the block exits
-        if (tid == 0)
-            for (int k = k_stop; k < issued; ++k)
-                msp::mbar_wait_timed(&full[k % kSStages], (uint32_t)((k / kSStages) & 1), a.err);
-        if (tid == 0 && pack && lead) msp::tc::bulk_wait_all();
+        // bounded waits for the loads that may still be in flight (the last
+        // kSWin chunks issued; every earlier one was waited for) before exit
+        if (tid == 0) {
+            const int iss = *s_issued;
+            for (int k = iss > kSWin ? iss - kSWin : 0; k < iss; ++k)
+                msp::mbar_wait_timed(&full[k % kSWin], (uint32_t)((k / kSWin) & 1), a.err);
+        }
+        if (lane == 0 && pack && lead) msp::tc::bulk_wait_all();
         return;
     }
-    if (tid == 0 && pack && lead) msp::tc::bulk_wait_all();
-    // C rows i0 + 4 ((q + lane) mod 8) + t of column c
+    if (lane == 0 && pack && lead) msp::tc::bulk_wait_all();
     if (col_ok) {
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -204,10 +250,6 @@ msp_status msp_sketch_sym_pass(msp_ctx* ctx, const float* A, int64_t n, int64_t 
     // column groups of at most 1024 columns, each a multiple of 32
     const int groups = (int)((s_pad + 1023) / 1024);
     const int threads = (int)(s_pad / groups);
-    void* scr = nullptr;
-    MSP_TRY(msp_scratch(ctx, (size_t)s_pad * (nch + 1) * 4, &scr));
-    int32_t* tab = (int32_t*)scr;
-    MSP_TRY(msp_chunk_starts(ctx, ptr, ent, s_pad, kSJ, nch, tab));
     CUtensorMap tmA, tmP;
     {
         const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)n};
@@ -238,13 +280,13 @@ msp_status msp_sketch_sym_pass(msp_ctx* ctx, const float* A, int64_t n, int64_t 
     a.s_pad = s_pad;
     a.nch = nch;
     a.nt = nt;
-    a.tab = tab;
+    a.ptr = ptr;
     a.ent = ent;
     a.scale = (float)(1.0 / std::sqrt((double)gamma));
     a.C = C;
     CtlBlock* ctl = (CtlBlock*)ctx->ctl;
     a.err = &ctl->error;
-    const size_t smem = (size_t)kSStages * kSStageBytes + 64 + 1024;
+    const size_t smem = (size_t)kSWin * kSStageBytes + 64 + 1024;
     MSP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_sketch_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     MSP_CUDA_TRY(ctx, cudaMemsetAsync(&ctl->error, 0, sizeof(int), ctx->stream));
     // grid: column groups x every 32-column block up to the last tile column
