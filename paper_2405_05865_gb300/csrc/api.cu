@@ -168,6 +168,9 @@ void msp_destroy(msp_ctx* ctx) {
     delete[] ctx->lanes;
     delete[] ctx->lane_streams;
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
+    for (cudaEvent_t e : ctx->aux_ev)
+        if (e) cudaEventDestroy(e);
     for (cudaStream_t s : ctx->fac_side)
         if (s) cudaStreamDestroy(s);
     for (auto& pair : ctx->fac_ev)
@@ -187,6 +190,47 @@ msp_status msp_sketch_pattern(msp_ctx* ctx, int64_t n, int64_t rows, int gamma, 
 }
 
 // --------------------------------------------------------------- a1-a2
+
+// The one-pass sketch of a symmetric FP32 A, then (with stats) the
+// norm-bound row statistics. Both only read A. The statistics pass is
+// HBM-bound with many small blocks, while the sketch kernel holds one
+// 1024-thread block per SM and runs n / 32 blocks in waves, the last one
+// partly filled (512 blocks on 152 SMs at n = 16384). So the statistics are
+// enqueued on a side stream that forks from the main stream before the
+// sketch launch and joins it after: their blocks take the SMs the sketch's
+// last wave leaves idle. The sketch is submitted first.
+static msp_status sym_pass_and_stats(msp_ctx* ctx, const float* A, msp_dtype dtype, int64_t n, int64_t lda,
+                                     int64_t sp, const int32_t* ptr, const int32_t* ent, int gamma, float* C,
+                                     float* packed, double* stats) {
+    cudaStream_t side = nullptr;
+    if (stats) {
+        if ((ctx->aux_stream ||
+             cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking) == cudaSuccess) &&
+            (ctx->aux_ev[0] || cudaEventCreateWithFlags(&ctx->aux_ev[0], cudaEventDisableTiming) == cudaSuccess) &&
+            (ctx->aux_ev[1] || cudaEventCreateWithFlags(&ctx->aux_ev[1], cudaEventDisableTiming) == cudaSuccess) &&
+            cudaEventRecord(ctx->aux_ev[0], ctx->stream) == cudaSuccess &&
+            cudaStreamWaitEvent(ctx->aux_stream, ctx->aux_ev[0], 0) == cudaSuccess)
+            side = ctx->aux_stream;
+        else
+            cudaGetLastError();   // the statistics stay on the main stream
+    }
+    msp_status st = msp_sketch_sym_pass(ctx, A, n, lda, sp, ptr, ent, gamma, C, packed);
+    if (stats && st == MSP_OK) {
+        if (side) {
+            cudaStream_t main_stream = ctx->stream;
+            ctx->stream = side;
+            st = msp_norm_lb_launch(ctx, A, dtype, n, lda, stats, stats + 3 * n);
+            ctx->stream = main_stream;
+            if (st == MSP_OK && (cudaEventRecord(ctx->aux_ev[1], side) != cudaSuccess ||
+                                 cudaStreamWaitEvent(ctx->stream, ctx->aux_ev[1], 0) != cudaSuccess))
+                st = msp_set_error(ctx, MSP_ECUDA, "sketch: side stream join failed");
+        } else {
+            st = msp_norm_lb_launch(ctx, A, dtype, n, lda, stats, stats + 3 * n);
+        }
+    }
+    if (side && st != MSP_OK) cudaStreamSynchronize(side);
+    return st;
+}
 
 void msp_sketch_destroy(msp_sketch_t* sk) {
     if (!sk) return;
@@ -318,9 +362,8 @@ msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t
         if (ok && one_pass) {
             if (pack) st = msp_alloc(ctx, (void**)&sk->stats, (size_t)(3 * n + 1) * 8);
             if (st == MSP_OK)
-                st = msp_sketch_sym_pass(ctx, (const float*)A, n, n, sp, sk->csr_ptr, sk->csr_ent, gamma,
-                                         (float*)sk->C, pack ? sk->packed : nullptr);
-            if (st == MSP_OK && pack) st = msp_norm_lb_launch(ctx, A, dtype, n, n, sk->stats, sk->stats + 3 * n);
+                st = sym_pass_and_stats(ctx, (const float*)A, dtype, n, n, sp, sk->csr_ptr, sk->csr_ent, gamma,
+                                        (float*)sk->C, pack ? sk->packed : nullptr, pack ? sk->stats : nullptr);
             ok = (st == MSP_OK);
             prep_done = true;
         }
@@ -343,9 +386,8 @@ msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t
         // the norm-bound row statistics are a pass of their own
         if (pack) st = msp_alloc(ctx, (void**)&sk->stats, (size_t)(3 * n + 1) * 8);
         if (st == MSP_OK)
-            st = msp_sketch_sym_pass(ctx, (const float*)A, n, lda, sp, sk->csr_ptr, sk->csr_ent, gamma,
-                                     (float*)sk->C, pack ? sk->packed : nullptr);
-        if (st == MSP_OK && pack) st = msp_norm_lb_launch(ctx, A, dtype, n, lda, sk->stats, sk->stats + 3 * n);
+            st = sym_pass_and_stats(ctx, (const float*)A, dtype, n, lda, sp, sk->csr_ptr, sk->csr_ent, gamma,
+                                    (float*)sk->C, pack ? sk->packed : nullptr, pack ? sk->stats : nullptr);
         if (st != MSP_OK) {
             cudaStreamSynchronize(ctx->stream);
             msp_sketch_destroy(sk);

@@ -42,6 +42,10 @@ struct msp_ctx {
     // only after every wait on its previous record has been enqueued)
     cudaStream_t fac_side[8] = {};
     cudaEvent_t fac_ev[8][2] = {};
+    // side stream and fork/join events of the sketch's row statistics
+    // (created once, lazily)
+    cudaStream_t aux_stream = nullptr;
+    cudaEvent_t aux_ev[2] = {};
     bool fac_overlap = true;     // false: the factor's products stay on the main stream
     bool gram_tc = true;         // M2 Gram on the tensor cores (false: FP32 pipe, compensated)
     bool factor_ff = true;       // Cholesky of an FP32 factor in float-float (false: FP64)
