@@ -2,6 +2,8 @@
 // staging of host buffers and the FP64 refinement driver.
 #include "msp_internal.cuh"
 
+#include <cstdint>
+
 #include <cuda_bf16.h>
 
 #include <vector>
@@ -322,10 +324,27 @@ msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t
         // A); the lower tiles are mirrored on the device once their source
         // rows have landed. FP64: whole rows.
         const bool half = (dtype == MSP_F32);
-        // FP32: the one-pass kernel runs once every row has landed and the
-        // lower tiles are mirrored (the same kernel, hence bit for bit the
-        // result of a device-resident A); the copies still overlap the mirroring
+        // FP32 one-pass: once chunk k has landed, the lower tiles of its tile
+        // columns are mirrored from its own rows, which completes the column
+        // block A[:, r0 .. r0 + nr); the one-pass kernel then forms those rows
+        // of C and the packed tiles of those columns on a side stream, while
+        // the later chunks are still being copied. The same kernel on the same
+        // blocks: bit for bit the result of a device-resident A.
         const bool one_pass = half && ctx->sketch_sym && msp_sketch_sym_ok(A, n, n, sp, gamma);
+        cudaStream_t side = nullptr;
+        if (one_pass) {
+            if ((ctx->aux_stream ||
+                 cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking) == cudaSuccess) &&
+                (ctx->aux_ev[0] || cudaEventCreateWithFlags(&ctx->aux_ev[0], cudaEventDisableTiming) == cudaSuccess) &&
+                (ctx->aux_ev[1] || cudaEventCreateWithFlags(&ctx->aux_ev[1], cudaEventDisableTiming) == cudaSuccess))
+                side = ctx->aux_stream;
+            else
+                cudaGetLastError();   // the sketch launches stay on the main stream
+            if (pack) {
+                st = msp_alloc(ctx, (void**)&sk->stats, (size_t)(3 * n + 1) * 8);
+                ok = ok && st == MSP_OK;
+            }
+        }
         for (int k = 0; ok && k < nchunk; ++k) {
             const int64_t r0 = k * rows, nr = std::min(rows, n - r0);
             ok = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming) == cudaSuccess;
@@ -347,11 +366,39 @@ msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t
             const int64_t r0 = k * rows, nr = std::min(rows, n - r0);
             ok = cudaStreamWaitEvent(ctx->stream, ev[k], 0) == cudaSuccess;
             if (!ok) break;
+            if (one_pass) {
+                if ((st = msp_mirror_lower_cols(ctx, (float*)A, n, n, r0 / 128, (r0 + nr + 127) / 128)) != MSP_OK) {
+                    ok = false;
+                    break;
+                }
+                // 32-row blocks of C: this chunk's; the last chunk also takes
+                // the padding blocks up to the last tile column
+                const int64_t ib0 = r0 / 32, ib1 = (k == nchunk - 1) ? INT64_MAX : (r0 + nr) / 32;
+                if (side) {
+                    if (cudaEventRecord(ctx->aux_ev[0], ctx->stream) != cudaSuccess ||
+                        cudaStreamWaitEvent(side, ctx->aux_ev[0], 0) != cudaSuccess) {
+                        ok = false;
+                        break;
+                    }
+                    cudaStream_t main_stream = ctx->stream;
+                    ctx->stream = side;
+                    st = msp_sketch_sym_blocks(ctx, (const float*)A, n, n, sp, sk->csr_ptr, sk->csr_ent, gamma,
+                                               (float*)sk->C, pack ? sk->packed : nullptr, ib0, ib1);
+                    ctx->stream = main_stream;
+                } else {
+                    st = msp_sketch_sym_blocks(ctx, (const float*)A, n, n, sp, sk->csr_ptr, sk->csr_ent, gamma,
+                                               (float*)sk->C, pack ? sk->packed : nullptr, ib0, ib1);
+                }
+                if (st != MSP_OK) {
+                    ok = false;
+                    break;
+                }
+                continue;
+            }
             if (half && (st = msp_mirror_lower_rows(ctx, (float*)A, n, n, r0 / 128, (r0 + nr + 127) / 128)) != MSP_OK) {
                 ok = false;
                 break;
             }
-            if (one_pass) continue;
             if ((st = msp_sketch_apply_rows(ctx, (const char*)A + (size_t)r0 * n * ts, dtype, nr, n, n, sp,
                                             sk->csr_ptr, sk->csr_ent, gamma, (char*)sk->C + (size_t)r0 * sp * ts)) !=
                     MSP_OK ||
@@ -360,10 +407,14 @@ msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t
                 ok = false;
         }
         if (ok && one_pass) {
-            if (pack) st = msp_alloc(ctx, (void**)&sk->stats, (size_t)(3 * n + 1) * 8);
-            if (st == MSP_OK)
-                st = sym_pass_and_stats(ctx, (const float*)A, dtype, n, n, sp, sk->csr_ptr, sk->csr_ent, gamma,
-                                        (float*)sk->C, pack ? sk->packed : nullptr, pack ? sk->stats : nullptr);
+            // every row has landed and every lower tile is mirrored: the row
+            // statistics on the main stream, beside the side stream's last
+            // sketch launches, then the join
+            if (pack) st = msp_norm_lb_launch(ctx, A, dtype, n, n, sk->stats, sk->stats + 3 * n);
+            if (st == MSP_OK && side &&
+                (cudaEventRecord(ctx->aux_ev[1], side) != cudaSuccess ||
+                 cudaStreamWaitEvent(ctx->stream, ctx->aux_ev[1], 0) != cudaSuccess))
+                st = msp_set_error(ctx, MSP_ECUDA, "sketch: side stream join failed");
             ok = (st == MSP_OK);
             prep_done = true;
         }
@@ -377,6 +428,7 @@ msp_status msp_sketch_impl(msp_ctx* ctx, const void* A, msp_dtype dtype, int64_t
         if (ready) cudaEventDestroy(ready);
         if (st != MSP_OK) {
             cudaStreamSynchronize(ctx->copy_stream);
+            if (side) cudaStreamSynchronize(side);
             cudaStreamSynchronize(ctx->stream);
             msp_sketch_destroy(sk);
             return st;

@@ -308,6 +308,13 @@ msp_status msp_chunk_starts(msp_ctx* ctx, const int32_t* ptr, const int32_t* ent
 bool msp_sketch_sym_ok(const void* A, int64_t n, int64_t lda, int64_t s_pad, int gamma);
 msp_status msp_sketch_sym_pass(msp_ctx* ctx, const float* A, int64_t n, int64_t lda, int64_t s_pad,
                                const int32_t* ptr, const int32_t* ent, int gamma, float* C, float* packed);
+// The same pass for the 32-row blocks [ib0, ib1) of C only (clamped to the
+// blocks up to the last tile column): each block reads the column block
+// A[:, 32 ib .. 32 ib + 32), which must be complete. Launches over
+// consecutive ranges, in order on one stream, form the whole pass.
+msp_status msp_sketch_sym_blocks(msp_ctx* ctx, const float* A, int64_t n, int64_t lda, int64_t s_pad,
+                                 const int32_t* ptr, const int32_t* ent, int gamma, float* C, float* packed,
+                                 int64_t ib0, int64_t ib1);
 // the norm bound from row statistics already in work (3 n doubles)
 msp_status msp_norm_lb_finish(msp_ctx* ctx, double* work, int64_t n, double* out_dev);
 msp_status msp_gather_rows(msp_ctx* ctx, msp_dtype dt, int64_t rows_out, int64_t width,
@@ -360,6 +367,7 @@ msp_status msp_pack_upper_rows(msp_ctx* ctx, const float* A, int64_t lda, int64_
                                float* packed);
 // fill the strictly lower 128-tiles of tile rows [I0, I1) from the upper ones
 msp_status msp_mirror_lower_rows(msp_ctx* ctx, float* A, int64_t lda, int64_t n, int64_t I0, int64_t I1);
+msp_status msp_mirror_lower_cols(msp_ctx* ctx, float* A, int64_t lda, int64_t n, int64_t J0, int64_t J1);
 msp_status msp_symv_packed(msp_ctx* ctx, const float* packed, int64_t n, float lam, const float* p,
                            float* part, double* dpart, int grid);
 

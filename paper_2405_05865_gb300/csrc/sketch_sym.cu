@@ -32,6 +32,7 @@
 #include "tc.cuh"
 
 #include <algorithm>
+#include <cstdint>
 
 namespace {
 
@@ -46,6 +47,7 @@ struct SymArgs {
     int64_t n, s_pad;
     int nch;                 // chunks (cover the tile rows up to nt * 128)
     int nt;                  // tiles per side
+    int ib0;                 // first 32-row block of C of this launch
     const int32_t* ptr;      // [s_pad + 1] CSR column starts
     const int32_t* ent;      // (j << 1) | negative, CSR by column
     float scale;
@@ -94,7 +96,7 @@ k_sketch_sym(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     volatile int* s_abort = reinterpret_cast<volatile int*>(s_issued + 1);
 
     const int tid = threadIdx.x, lane = tid & 31, nw = (int)(blockDim.x >> 5);
-    const int64_t i0 = (int64_t)blockIdx.y * kSR;
+    const int64_t i0 = ((int64_t)a.ib0 + blockIdx.y) * kSR;
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + tid;      // column of C
     const bool lead = (blockIdx.x == 0);                            // packs the tiles
     const int Jt = (int)(i0 / kSTile);
@@ -238,8 +240,9 @@ bool msp_sketch_sym_ok(const void* A, int64_t n, int64_t lda, int64_t s_pad, int
            gamma >= 1 && n < (1ll << 30);
 }
 
-msp_status msp_sketch_sym_pass(msp_ctx* ctx, const float* A, int64_t n, int64_t lda, int64_t s_pad,
-                               const int32_t* ptr, const int32_t* ent, int gamma, float* C, float* packed) {
+msp_status msp_sketch_sym_blocks(msp_ctx* ctx, const float* A, int64_t n, int64_t lda, int64_t s_pad,
+                                 const int32_t* ptr, const int32_t* ent, int gamma, float* C, float* packed,
+                                 int64_t ib0, int64_t ib1) {
     auto enc = msp_tensor_map_encoder();
     if (!enc || !msp_sketch_sym_ok(A, n, lda, s_pad, gamma))
         return msp_set_error(ctx, MSP_EINVAL, "sketch_sym: unsupported arguments");
@@ -280,6 +283,11 @@ msp_status msp_sketch_sym_pass(msp_ctx* ctx, const float* A, int64_t n, int64_t 
     a.s_pad = s_pad;
     a.nch = nch;
     a.nt = nt;
+    // row blocks of C (32 rows each) up to the last tile column (blocks past n
+    // only write the zero padding of the packed tiles)
+    ib1 = std::min<int64_t>(ib1, (int64_t)nt * kSTile / kSR);
+    if (ib0 < 0 || ib0 >= ib1) return MSP_OK;
+    a.ib0 = (int)ib0;
     a.ptr = ptr;
     a.ent = ent;
     a.scale = (float)(1.0 / std::sqrt((double)gamma));
@@ -288,13 +296,19 @@ msp_status msp_sketch_sym_pass(msp_ctx* ctx, const float* A, int64_t n, int64_t 
     a.err = &ctl->error;
     const size_t smem = (size_t)kSWin * kSStageBytes + 64 + 1024;
     MSP_CUDA_TRY(ctx, cudaFuncSetAttribute(k_sketch_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    MSP_CUDA_TRY(ctx, cudaMemsetAsync(&ctl->error, 0, sizeof(int), ctx->stream));
-    // grid: column groups x every 32-column block up to the last tile column
-    // (blocks past n only write the zero padding of the packed tiles)
-    dim3 grid((unsigned)groups, (unsigned)((int64_t)nt * kSTile / kSR));
+    // the first launch of a pass clears the error word (a pass may come in
+    // several launches over consecutive block ranges, in order on one stream)
+    if (ib0 == 0) MSP_CUDA_TRY(ctx, cudaMemsetAsync(&ctl->error, 0, sizeof(int), ctx->stream));
+    // grid: column groups x the 32-column blocks [ib0, ib1)
+    dim3 grid((unsigned)groups, (unsigned)(ib1 - ib0));
     k_sketch_sym<<<grid, threads, smem, ctx->stream>>>(tmA, tmP, a, packed ? 1 : 0);
     MSP_CHECK_LAUNCH(ctx);
     return MSP_OK;
+}
+
+msp_status msp_sketch_sym_pass(msp_ctx* ctx, const float* A, int64_t n, int64_t lda, int64_t s_pad,
+                               const int32_t* ptr, const int32_t* ent, int gamma, float* C, float* packed) {
+    return msp_sketch_sym_blocks(ctx, A, n, lda, s_pad, ptr, ent, gamma, C, packed, 0, INT64_MAX);
 }
 
 extern "C" msp_status msp_set_sketch_one_pass(msp_ctx* ctx, int on) {
