@@ -231,7 +231,52 @@ k_sketch_sym(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CU
     }
 }
 
+// The lower triangle of tile column J = J0 + blockIdx.y of a symmetric
+// row-major A from its upper triangle: tile (I, J), I = blockIdx.x >= J, is
+// the transpose of tile (J, I) (blocks with I < J return at once); on the
+// diagonal tile only the entries below the diagonal are written. 32 x 33
+// shared-memory transposes, coalesced both ways. It reads only tile rows J
+// and writes only tile column J, so it completes the column block of A that
+// the one-pass kernel stages for the rows of C in that tile column.
+__global__ void __launch_bounds__(256) k_mirror_lower_cols(float* __restrict__ A, int64_t lda, int64_t n, int J0) {
+    __shared__ float tr[32][33];
+    const int J = J0 + (int)blockIdx.y, I = (int)blockIdx.x;
+    if (I < J) return;
+    const bool diag = (I == J);
+    const int64_t r0 = (int64_t)I * kSTile, c0 = (int64_t)J * kSTile;   // destination (rows r0.., cols c0..)
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;               // 32 x 8
+    for (int bi = 0; bi < kSTile; bi += 32)
+        for (int bj = 0; bj < kSTile; bj += 32) {
+            if (diag && bj > bi) continue;          // block-uniform: the upper half of a diagonal tile stays
+            // source block A[c0 + bj + y][r0 + bi + x] (rows of the upper tile (J, I))
+            for (int y = ty; y < 32; y += 8) {
+                const int64_t sr = c0 + bj + y, sc = r0 + bi + tx;
+                tr[y][tx] = (sr < n && sc < n) ? A[sr * lda + sc] : 0.f;
+            }
+            __syncthreads();
+            // strictly lower entries only on the diagonal tile; their sources
+            // lie strictly above the diagonal and are never written
+            for (int y = ty; y < 32; y += 8) {
+                const int64_t dr = r0 + bi + y, dc = c0 + bj + tx;
+                if (dr < n && dc < n && (!diag || dr > dc)) A[dr * lda + dc] = tr[tx][y];
+            }
+            __syncthreads();
+        }
+}
+
 }  // namespace
+
+// Fills the lower triangle of tile columns [J0, J1) (the diagonal tiles
+// included) from the upper triangle, which must already be in place in tile
+// rows [J0, J1). Afterwards the columns [J0, J1) * 128 of A are complete.
+msp_status msp_mirror_lower_cols(msp_ctx* ctx, float* A, int64_t lda, int64_t n, int64_t J0, int64_t J1) {
+    const int64_t nt = (n + kSTile - 1) / kSTile;
+    J1 = std::min(J1, nt);
+    if (J0 < 0 || J0 >= J1) return MSP_OK;
+    k_mirror_lower_cols<<<dim3((unsigned)nt, (unsigned)(J1 - J0)), 256, 0, ctx->stream>>>(A, lda, n, (int)J0);
+    MSP_CHECK_LAUNCH(ctx);
+    return MSP_OK;
+}
 
 bool msp_sketch_sym_ok(const void* A, int64_t n, int64_t lda, int64_t s_pad, int gamma) {
     const int64_t groups = (s_pad + 1023) / 1024;

@@ -396,8 +396,14 @@ msp_status msp_pack_upper(msp_ctx* ctx, const float* A, int64_t lda, int64_t n, 
 // J <= I, per block, tile t = I (I + 1) / 2 + J; on a diagonal tile only the
 // entries below the diagonal are written. 32 x 33 shared-memory transposes,
 // coalesced both ways.
-__device__ void mirror_tile(float* __restrict__ A, int64_t lda, int64_t n, int I, int J) {
+__global__ void __launch_bounds__(256) k_mirror_lower(float* __restrict__ A, int64_t lda, int64_t n, int t0) {
     __shared__ float tr[32][33];
+    // tiles (I, J) with J <= I, tile row after tile row: row I starts at I (I + 1) / 2
+    const int t = t0 + (int)blockIdx.x;
+    int I = (int)((sqrtf(1.0f + 8.0f * (float)t) - 1.0f) * 0.5f);
+    while (I > 0 && (int64_t)I * (I + 1) / 2 > t) --I;
+    while ((int64_t)(I + 1) * (I + 2) / 2 <= t) ++I;
+    const int J = t - I * (I + 1) / 2;
     const bool diag = (I == J);
     const int64_t r0 = (int64_t)I * kTile, c0 = (int64_t)J * kTile;   // destination block (rows r0.., cols c0..)
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;             // 32 x 8
@@ -420,24 +426,6 @@ __device__ void mirror_tile(float* __restrict__ A, int64_t lda, int64_t n, int I
         }
 }
 
-__global__ void __launch_bounds__(256) k_mirror_lower(float* __restrict__ A, int64_t lda, int64_t n, int t0) {
-    // tiles (I, J) with J <= I, tile row after tile row: row I starts at I (I + 1) / 2
-    const int t = t0 + (int)blockIdx.x;
-    int I = (int)((sqrtf(1.0f + 8.0f * (float)t) - 1.0f) * 0.5f);
-    while (I > 0 && (int64_t)I * (I + 1) / 2 > t) --I;
-    while ((int64_t)(I + 1) * (I + 2) / 2 <= t) ++I;
-    const int J = t - I * (I + 1) / 2;
-    mirror_tile(A, lda, n, I, J);
-}
-
-// The lower tiles of tile columns J0 + blockIdx.y: tile (I, J) for
-// I = blockIdx.x >= J (blocks with I < J return at once).
-__global__ void __launch_bounds__(256) k_mirror_lower_cols(float* __restrict__ A, int64_t lda, int64_t n, int J0) {
-    const int J = J0 + (int)blockIdx.y, I = (int)blockIdx.x;
-    if (I < J) return;
-    mirror_tile(A, lda, n, I, J);
-}
-
 // Fills the lower triangle of tile rows [I0, I1) (the diagonal tiles included)
 // from the upper triangle, which must already be in place for those rows and
 // for every row above them.
@@ -447,19 +435,6 @@ msp_status msp_mirror_lower_rows(msp_ctx* ctx, float* A, int64_t lda, int64_t n,
     if (I0 >= I1) return MSP_OK;
     const int64_t t0 = I0 * (I0 + 1) / 2, t1 = I1 * (I1 + 1) / 2;
     k_mirror_lower<<<(unsigned)(t1 - t0), 256, 0, ctx->stream>>>(A, lda, n, (int)t0);
-    MSP_CHECK_LAUNCH(ctx);
-    return MSP_OK;
-}
-
-// Fills the lower triangle of tile columns [J0, J1) (the diagonal tiles
-// included) from the upper triangle, which must already be in place for
-// tile rows [J0, J1) (the sources: tile (I, J) is the transpose of (J, I)).
-// Afterwards the columns [J0, J1) * 128 of A are complete.
-msp_status msp_mirror_lower_cols(msp_ctx* ctx, float* A, int64_t lda, int64_t n, int64_t J0, int64_t J1) {
-    const int64_t nt = (n + kTile - 1) / kTile;
-    J1 = std::min(J1, nt);
-    if (J0 >= J1) return MSP_OK;
-    k_mirror_lower_cols<<<dim3((unsigned)nt, (unsigned)(J1 - J0)), 256, 0, ctx->stream>>>(A, lda, n, (int)J0);
     MSP_CHECK_LAUNCH(ctx);
     return MSP_OK;
 }
