@@ -284,6 +284,65 @@ def oracle_bounded_sample(A32: np.ndarray, b: np.ndarray, lam: float, s: int, it
     return {"setup_s": t1 - t0, "iter_s": (t2 - t1) / iters, "seconds": t2 - t0}
 
 
+_CFG0_SCRIPT = """
+import json, sys, time
+sys.path.insert(0, {root!r})
+from oracle import msp, nystrom
+from workloads import make_workload
+w = make_workload("outlier", seed=0)
+p = msp.MspParams(s=w.s, lam0=nystrom.lambda0_from_spectrum(w.sigma, 32), tol=1e-10)
+t0 = time.perf_counter()
+x, info = msp.solve(w.A, w.b, w.lam, p)
+print(json.dumps({{"seconds": time.perf_counter() - t0, "iters": info.outer_iters,
+                  "converged": bool(info.converged)}}))
+"""
+
+_ONE_THREAD = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
+               "VECLIB_MAXIMUM_THREADS", "NUMEXPR_NUM_THREADS")
+
+
+def oracle_config0_timing() -> dict:
+    """The FP64 oracle on the n = 1024 outlier system (32 outliers 1e4 -> 1e2,
+    tail i^-1.5, lam = 1e-3, s = 64, gamma = 8, lam0 from the spectrum with
+    l = 32, relative residual 1e-10; the pattern, sketch and level-2 sketch
+    included in the time): in this process (every BLAS thread) and in a child
+    process with one BLAS thread. Failures are reported, not raised."""
+    out = {"workload": "A = Q diag(sigma) Q^T, n=1024, 32 outliers 1e4->1e2, tail i^-1.5, lam=1e-3, "
+                       "s=64, gamma=8, FP64 oracle to relative residual 1e-10"}
+    try:
+        res = subprocess.run([sys.executable, "-c", _CFG0_SCRIPT.format(root=ROOT)], capture_output=True,
+                             text=True, timeout=60)
+        out["all_threads"] = json.loads(res.stdout.strip().splitlines()[-1])
+        env1 = {**os.environ, **{k: "1" for k in _ONE_THREAD}}
+        res = subprocess.run([sys.executable, "-c", _CFG0_SCRIPT.format(root=ROOT)], capture_output=True,
+                             text=True, timeout=60, env=env1)
+        out["one_thread"] = json.loads(res.stdout.strip().splitlines()[-1])
+        for k in ("all_threads", "one_thread"):
+            out[k]["solves_per_s"] = 1.0 / out[k]["seconds"]
+    except Exception as e:  # noqa: BLE001 - a baseline that could not run is reported as such
+        out["error"] = f"{type(e).__name__}: {e}"[:200]
+    return out
+
+
+def oracle_hutchinson_timing(A_host32: np.ndarray, seed: int) -> dict:
+    """The FP64 oracle's Hutchinson estimate (quadratic forms g^T A g of 256
+    Rademacher probes from the same counter-based generator) on the same FP32
+    matrix widened to FP64, timed on the host's cores: probe generation plus
+    the product. Failures are reported, not raised."""
+    try:
+        from oracle import hutchinson
+        n = A_host32.shape[0]
+        A64 = A_host32.astype(np.float64)
+        t0 = time.perf_counter()
+        G = hutchinson.probes_fast(n, 256, seed)
+        est, se = hutchinson.estimate(A64, G)
+        sec = time.perf_counter() - t0
+        return {"seconds": sec, "estimates_per_s": 1.0 / sec, "estimate": est, "std_err": se,
+                "cores": os.cpu_count()}
+    except Exception as e:  # noqa: BLE001
+        return {"error": f"{type(e).__name__}: {e}"[:200]}
+
+
 def backward_equiv_tol(info: dict) -> float:
     """The relative residual the GPU solve's stopping rule allows,
     |r| <= 1e-10 ((L + lam)|x| + |b|), from the GPU's final x:
@@ -736,6 +795,13 @@ def run_schatten_outlier(args, ctx, dev, rank, peak):
         A = 0.5 * (A + A.T)
     trace = float(torch.diagonal(A).to(torch.float64).sum())
     exact = float(np.sum(sig))
+    # the FP64 oracle on the same matrix and probes, on the host's cores
+    oracle_cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            oracle_cpu = oracle_hutchinson_timing(A.cpu().numpy(), SEED)
+        except Exception as e:  # noqa: BLE001 - reported, never fatal to the GPU arm
+            oracle_cpu = {"error": f"{type(e).__name__}: {e}"[:200]}
     ctx.set_hutchinson_terms(args.hutchinson_terms)
     ctx.schatten(A, p=1.0, probes=256)
     stream = ctx.stream
@@ -761,7 +827,8 @@ def run_schatten_outlier(args, ctx, dev, rank, peak):
             "deviation_in_std_err": (est - exact) / se if se else None,
             "ms_per_estimate": ms, "estimates_per_s": 1000.0 / ms, "terms_16bit": args.hutchinson_terms,
             "tflops": 2.0 * n * n * 256 / 2 / (ms * 1e-3) / 1e12,
-            "a_read_gbs": alg / (ms * 1e-3) / 1e9, "a_read_frac": alg / (ms * 1e-3) / 1e9 / peak}
+            "a_read_gbs": alg / (ms * 1e-3) / 1e9, "a_read_frac": alg / (ms * 1e-3) / 1e9 / peak,
+            "oracle_cpu": oracle_cpu}
 
 
 def run_sketched_level2(args, ctx, dev, rank, A, bd, lam):
@@ -1113,7 +1180,7 @@ def run_msp(args, rank, world, local):
                           f"relative residual {tol_eq:.3g} (the GPU rule's backward error 1e-10 for this x): "
                           f"set-up {full['setup_s']:.2f} s + {full['iters']} level-1 iterations"),
                "seconds": full["seconds"], "iters": full["iters"], "converged": full["converged"],
-               "cpu_model": hc["model"]}
+               "cpu_model": hc["model"], "config0": oracle_config0_timing()}
 
     last = infos[-1]
     out = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,

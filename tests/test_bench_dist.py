@@ -78,3 +78,23 @@ def test_reference_arm_line_on_rank_zero():
     # a complete oracle solve was timed, and the steps' own time is reported
     assert line["cpu_baseline"]["complete_solve_s"] > 0 and line["cpu_baseline"]["complete_solve_iters"] > 0
     assert line["ms_per_step"] > 0
+
+
+def test_oracle_baselines_of_the_other_configs():
+    """The cpu_baseline leg's oracle timings beside the headline one: the
+    n = 1024 outlier system solved to 1e-10 with every BLAS thread and with
+    one (child processes), and the oracle's Hutchinson estimate on a given
+    matrix with the probes the GPU draws (the trace estimator's mean is the
+    trace; checked on a small diagonal matrix, where every probe gives it)."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.oracle_config0_timing()
+    assert "error" not in r, r
+    for k in ("all_threads", "one_thread"):
+        assert r[k]["converged"] and r[k]["iters"] > 0 and r[k]["solves_per_s"] > 0
+    d = np.linspace(1.0, 2.0, 300).astype(np.float32)
+    h = bench.oracle_hutchinson_timing(np.diag(d), bench.SEED)
+    assert "error" not in h, h
+    assert abs(h["estimate"] - float(d.astype(np.float64).sum())) <= 1e-9 * d.sum()
+    assert h["std_err"] <= 1e-9 * d.sum() and h["estimates_per_s"] > 0
